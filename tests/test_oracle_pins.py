@@ -1,0 +1,402 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics.
+
+None of these retype the oracle's formulas: each compares the oracle with an
+independent route (a library solver, exact quadrature, closed-form solutions,
+conservation laws, brute force, the monodomain solution converged SWR must
+reproduce, or values printed in the paper).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.linalg
+
+import oracle as O
+from paper_1503_02564_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def problem(wl, **kw):
+    P = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0, wl.V,
+                  vkind=wl.vkind, tc=wl.tc, sigma=wl.sigma, nl_coef=wl.nl_coef)
+    for k, v in kw.items():
+        setattr(P, k, v)
+    return P
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+# --------------------------------------------------------------------------
+# FEM matrices: exact quadrature by Simpson's rule (exact for cubics)
+# --------------------------------------------------------------------------
+def test_p1_matrices_against_simpson_quadrature():
+    rng = np.random.default_rng(1)
+    n, h = 9, 0.37
+    W_ = rng.standard_normal(n)
+    md, mo, sd, so, wd, wo = O.p1_matrices(n, h, W_)
+    x = np.arange(n) * h
+
+    def phi(i, xx):
+        return np.clip(1.0 - np.abs(xx - x[i]) / h, 0.0, None)
+
+    def dphi(i, xx):
+        s = np.where(xx < x[i], 1.0 / h, -1.0 / h)
+        return np.where(np.abs(xx - x[i]) < h, s, 0.0)
+
+    def Wf(xx):
+        return np.interp(xx, x, W_)
+
+    # integrate element by element with Simpson (exact for the cubic integrands)
+    def integ(f):
+        tot = 0.0
+        for e in range(n - 1):
+            a, b = x[e], x[e + 1]
+            m = 0.5 * (a + b)
+            tot += (b - a) / 6.0 * (f(a + 1e-15) + 4 * f(m) + f(b - 1e-15))
+        return tot
+
+    for i in range(n):
+        assert math.isclose(md[i], integ(lambda t: phi(i, t) ** 2), rel_tol=1e-12)
+        assert math.isclose(sd[i], integ(lambda t: dphi(i, t) ** 2), rel_tol=1e-12)
+        assert math.isclose(wd[i], integ(lambda t: Wf(t) * phi(i, t) ** 2), rel_tol=1e-11,
+                            abs_tol=1e-13)
+    for i in range(n - 1):
+        assert math.isclose(mo[i], integ(lambda t: phi(i, t) * phi(i + 1, t)), rel_tol=1e-12)
+        assert math.isclose(so[i], integ(lambda t: dphi(i, t) * dphi(i + 1, t)), rel_tol=1e-12)
+        assert math.isclose(wo[i], integ(lambda t: Wf(t) * phi(i, t) * phi(i + 1, t)),
+                            rel_tol=1e-11, abs_tol=1e-13)
+
+
+def test_p1_matrix_identities():
+    n, h = 50, 0.1
+    md, mo, sd, so, wd, wo = O.p1_matrices(n, h, np.ones(n))
+    ones = np.ones(n)
+    Mf = np.diag(md) + np.diag(mo, 1) + np.diag(mo, -1)
+    Sf = np.diag(sd) + np.diag(so, 1) + np.diag(so, -1)
+    # sum_j M_ij = int phi_i: h inside, h/2 at the ends; total = length
+    assert np.isclose((Mf @ ones).sum(), (n - 1) * h)
+    assert np.allclose(Sf @ ones, 0.0, atol=1e-12)                  # constants in the kernel
+    assert np.allclose(wd, md) and np.allclose(wo, mo)             # M_W with W = 1 is M
+
+
+# --------------------------------------------------------------------------
+# Thomas against LAPACK banded solve with pivoting
+# --------------------------------------------------------------------------
+def test_thomas_against_lapack():
+    rng = np.random.default_rng(2)
+    n = 300
+    lo = rng.standard_normal(n - 1) + 1j * rng.standard_normal(n - 1)
+    up = rng.standard_normal(n - 1) + 1j * rng.standard_normal(n - 1)
+    dg = 5 + rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ab = np.zeros((3, n), np.complex128)
+    ab[0, 1:] = up
+    ab[1] = dg
+    ab[2, :-1] = lo
+    ref = scipy.linalg.solve_banded((1, 1), ab, b)
+    assert rel(O.thomas(lo, dg, up, b), ref) < 1e-13
+
+
+def test_mono_march_against_lapack_banded_steps():
+    """The monodomain march equals a step-by-step LAPACK solve of
+    ((2i/dt) M - S + M_W) v = (2i/dt) M u, u <- 2v - u."""
+    wl = W.config1(nx=161, nt=12)
+    P = problem(wl)
+    m = O.mono_march(P)
+    n, h, dt = P.nx, P.h, P.dt
+    md, mo, sd, so, wd, wo = O.p1_matrices(n, h, P.V)
+    A = np.zeros((3, n), np.complex128)
+    A[1] = 2j / dt * md - sd + wd
+    A[0, 1:] = 2j / dt * mo - so + wo
+    A[2, :-1] = A[0, 1:]
+    u = P.u0.copy()
+    for _ in range(P.nt):
+        Mu = md * u
+        Mu[:-1] += mo * u[1:]
+        Mu[1:] += mo * u[:-1]
+        v = scipy.linalg.solve_banded((1, 1), A, 2j / dt * Mu)
+        u = 2 * v - u
+    assert rel(m.uT, u) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# Conservation and closed forms
+# --------------------------------------------------------------------------
+def _mnorm(h, u):
+    md, mo, *_ = O.p1_matrices(len(u), h)
+    return float(np.real(np.vdot(u, md * u) + 2 * np.real(np.vdot(u[:-1], mo * u[1:]))))
+
+
+@pytest.mark.parametrize("kind", ["static", "time", "nonlinear"])
+def test_discrete_norm_conservation(kind):
+    """u^H M u is conserved exactly by CN with real W and Neumann ends
+    (v^H (-S + M_W) v is real); the nonlinear scheme conserves it at inner
+    convergence."""
+    if kind == "static":
+        wl = W.config2(nsub=2, nx=801, nt=60)
+    elif kind == "time":
+        wl = W.config4(nsub=2, nx=601, nt=60)
+    else:
+        wl = W.config5(nsub=2, nx=801, nt=60)
+    P = problem(wl)
+    P.nl_tol = 1e-15
+    P.nl_maxit = 200
+    if kind == "nonlinear":
+        try:
+            m = O.mono_march(P)
+        except RuntimeError:
+            P.nl_tol = 1e-14
+            m = O.mono_march(P)
+    else:
+        m = O.mono_march(P)
+    n0, n1 = _mnorm(P.h, P.u0), _mnorm(P.h, m.uT)
+    assert abs(n1 - n0) / n0 < (1e-12 if kind != "nonlinear" else 1e-11)
+
+
+def _free_gaussian(x, t, x0=0.0, sig=1.0, k0=1.5):
+    s = sig ** 2 + 2j * t
+    return np.sqrt(sig ** 2 / s) * np.exp(-(x - x0 - 2 * k0 * t) ** 2 / (2 * s)) * \
+        np.exp(1j * (k0 * (x - x0) - k0 ** 2 * t))
+
+
+def test_free_gaussian_second_order():
+    """V = 0: closed-form free packet; CN + P1 converge at order 2 in (h, dt)."""
+    errs = []
+    for lev in range(3):
+        nx = 401 * 2 ** lev - (2 ** lev - 1)
+        nt = 20 * 2 ** lev
+        a0, b0, T = -15.0, 15.0, 0.5
+        x = np.linspace(a0, b0, nx)
+        m = O.march(nx, (b0 - a0) / (nx - 1), T / nt, nt, np.zeros(nx),
+                    _free_gaussian(x, 0.0))
+        errs.append(np.max(np.abs(m.uT - _free_gaussian(x, T))))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.6 < r1 < 4.4 and 3.6 < r2 < 4.4, errs
+
+
+def _mean_x(h, x, u):
+    _, _, _, _, wd, wo = O.p1_matrices(len(u), h, x)       # M_x: int x |u|^2
+    num = np.real(np.vdot(u, wd * u) + 2 * np.real(np.vdot(u[:-1], wo * u[1:])))
+    return num / _mnorm(h, u)
+
+
+def test_ehrenfest_quadratic_static():
+    """V = -x^2/4 gives H = p^2 + x^2/4 and <x>(t) = 10 sin t exactly for
+    u0 = exp(-x^2/2 + 5ix); the discrete error falls at order 2."""
+    errs = []
+    for lev in range(3):
+        nx = 801 * 2 ** lev - (2 ** lev - 1)
+        nt = 25 * 2 ** lev
+        a0, b0, T = -12.0, 12.0, 0.25
+        x = np.linspace(a0, b0, nx)
+        m = O.march(nx, (b0 - a0) / (nx - 1), T / nt, nt, -x ** 2 / 4,
+                    np.exp(-x ** 2 / 2 + 5j * x))
+        errs.append(abs(_mean_x((b0 - a0) / (nx - 1), x, m.uT) - 10 * math.sin(T)))
+    assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7, errs
+
+
+def test_ehrenfest_driven_time_dependent():
+    """V(t,x) = -x^2/4 + F(t) x with F = f0 sin(w t): <x> obeys x'' = -x + 2F(t)
+    exactly (Ehrenfest for quadratic H); pins W_n = (V_n + V_{n-1})/2."""
+    f0, w = 3.0, 2.5
+    sol = scipy.integrate.solve_ivp(lambda t, y: [y[1], -y[0] + 2 * f0 * math.sin(w * t)],
+                                    (0, 0.3), [0.0, 10.0], rtol=1e-13, atol=1e-13)
+    exact = sol.y[0, -1]
+    errs = []
+    for lev in range(3):
+        nx = 801 * 2 ** lev - (2 ** lev - 1)
+        nt = 30 * 2 ** lev
+        a0, b0, T = -12.0, 12.0, 0.3
+        x = np.linspace(a0, b0, nx)
+        t = (np.arange(nt + 1) * T / nt)[:, None]
+        V = -x[None, :] ** 2 / 4 + f0 * np.sin(w * t) * x[None, :]
+        m = O.march(nx, (b0 - a0) / (nx - 1), T / nt, nt, V, np.exp(-x ** 2 / 2 + 5j * x),
+                    vkind=O.V_TIME)
+        errs.append(abs(_mean_x((b0 - a0) / (nx - 1), x, m.uT) - exact))
+    assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7, errs
+
+
+def test_nls_soliton_second_order():
+    """Focusing NLS i u_t + u_xx + |u|^2 u = 0: u = sqrt(2) a sech(a(x-2kt))
+    e^{i(kx + (a^2-k^2)t)} (the paper's u0 is a = sqrt(2), k = 20)."""
+    a, k = 1.0, 1.0
+
+    def sol(x, t):
+        return math.sqrt(2) * a / np.cosh(a * (x - 2 * k * t)) * \
+            np.exp(1j * (k * x + (a * a - k * k) * t))
+    errs = []
+    for lev in range(3):
+        nx = 401 * 2 ** lev - (2 ** lev - 1)
+        nt = 20 * 2 ** lev
+        a0, b0, T = -20.0, 20.0, 0.5
+        x = np.linspace(a0, b0, nx)
+        m = O.march(nx, (b0 - a0) / (nx - 1), T / nt, nt, np.zeros(nx), sol(x, 0.0),
+                    vkind=O.V_NONLINEAR, nl_coef=1.0, nl_tol=1e-14, nl_maxit=100)
+        errs.append(np.max(np.abs(m.uT - sol(x, T))))
+    assert 3.4 < errs[0] / errs[1] < 4.6 and 3.4 < errs[1] / errs[2] < 4.6, errs
+
+
+# --------------------------------------------------------------------------
+# S_0^2 coefficients
+# --------------------------------------------------------------------------
+def test_alpha_gamma_printed_values():
+    rows = np.loadtxt(os.path.join(GOLDEN, "alpha_gamma_section2_2.txt"))
+    a = O.alpha_coefficients(int(rows[-1, 0]))
+    assert np.allclose(a, rows[:, 1], rtol=0, atol=1e-15)
+
+
+def test_beta_is_taylor_series_of_sqrt_ratio():
+    """beta_s are the Taylor coefficients of sqrt((1-z)/(1+z)): the discrete
+    half derivative sqrt(2/dt) sqrt((1-z)/(1+z)) of the CN symbol.  Computed here
+    by a contour integral (FFT on |z| = rho), an independent route."""
+    ns, rho, M = 40, 0.7, 4096
+    z = rho * np.exp(2j * np.pi * np.arange(M) / M)
+    f = np.sqrt((1 - z) / (1 + z))
+    coef = (np.fft.fft(f) / M)[: ns + 1] / rho ** np.arange(ns + 1)
+    beta = O.beta_coefficients(ns)
+    assert np.allclose(coef.real, beta, atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# Interface problem structure (Props. 1-4) by brute force
+# --------------------------------------------------------------------------
+def _tiny(kind="static", tc=O.TC_ROBIN, nsub=3, nx=31, nt=8):
+    if kind == "static":
+        wl = W.config1(nx=nx, nt=nt, nsub=nsub)
+    else:
+        wl = W.config4(nsub=nsub, nx=nx, nt=nt)
+    return problem(wl, tc=tc)
+
+
+@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
+def test_bruteforce_L_is_causal_toeplitz(tc):
+    P = _tiny(tc=tc)
+    Ld, d = O.dense_L(P)
+    nb, nt = P.nblk, P.nt
+    cols = O.build_columns(P, "zero_u0")
+    Lt = np.zeros_like(Ld)
+    for k in range(nb * nt):
+        e = np.zeros(nb * nt, np.complex128)
+        e[k] = 1.0
+        Lt[:, k] = O.apply_L(P, cols, e).ravel()
+    scale = np.abs(Ld).max()
+    for bo in range(nb):
+        for bi in range(nb):
+            blk = Ld[bo * nt:(bo + 1) * nt, bi * nt:(bi + 1) * nt]
+            assert np.all(np.triu(blk, 1) == 0.0)                      # causality, bitwise
+            for n in range(1, nt):                                      # Toeplitz shift
+                for s in range(1, n + 1):
+                    assert abs(blk[n, s] - blk[n - 1, s - 1]) <= 1e-13 * scale
+    assert np.abs(Ld - Lt).max() <= 1e-12 * scale                     # first-column build
+
+
+def test_bruteforce_L_time_dependent_is_not_toeplitz():
+    P = _tiny(kind="time", nx=41, nt=8)
+    Ld, _ = O.dense_L(P)
+    nt = P.nt
+    blk = Ld[0:nt, nt:2 * nt]
+    assert np.all(np.triu(blk, 1) == 0.0)
+    shift = max(abs(blk[n, s] - blk[n - 1, s - 1]) for n in range(1, nt) for s in range(1, n + 1))
+    assert shift > 1e-8 * np.abs(blk).max()
+
+
+def test_R_is_affine_and_fixed_point_identity():
+    """Props. 1-2: R g = L g + d; then R g - g = d - (I - L) g (Section 4),
+    the second side computed from the Toeplitz columns."""
+    P = _tiny(nsub=4, nx=61, nt=10)
+    d = O.build_d(P)
+    cols = O.build_columns(P, "zero_u0")
+    g1 = W.random_interface(P.nblk, P.nt, 1)
+    g2 = W.random_interface(P.nblk, P.nt, 2)
+    lhs = O.apply_R(P, 0.3 * g1 - 1.7j * g2) - d
+    rhs = 0.3 * (O.apply_R(P, g1) - d) - 1.7j * (O.apply_R(P, g2) - d)
+    assert rel(lhs, rhs) < 1e-12
+    inc = O.apply_R(P, g1) - g1
+    assert rel(inc, d - O.apply_I_minus_L(P, cols, g1)) < 1e-12
+
+
+def test_columns_minus_d_equals_zero_u0():
+    P = _tiny(nsub=4, nx=81, nt=12)
+    c1 = O.build_columns(P, "zero_u0")
+    c2 = O.build_columns(P, "minus_d")
+    assert np.abs(c1 - c2).max() < 1e-12 * np.abs(c1).max()
+
+
+# --------------------------------------------------------------------------
+# Converged SWR equals the monodomain solution
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
+def test_swr_new_algorithm_reproduces_monodomain(tc):
+    wl = W.config1(nx=241, nt=30, nsub=4)
+    P = problem(wl, tc=tc)
+    r = O.solve_new(P, "gmres", restart=200)
+    gs, uTm = O.mono_interface(P)
+    assert r.residual < 1e-10
+    assert rel(r.uT, uTm) < 1e-9
+    assert rel(r.g, gs) < 1e-9
+    assert r.jump < 1e-9
+
+
+def test_dense_solve_gmres_and_fixed_point_agree():
+    P = _tiny(tc=O.TC_S02, nsub=3, nx=61, nt=10)
+    d = O.build_d(P)
+    cols = O.build_columns(P)
+    n = P.nblk * P.nt
+    A = np.zeros((n, n), np.complex128)
+    for k in range(n):
+        e = np.zeros(n, np.complex128)
+        e[k] = 1.0
+        A[:, k] = O.apply_I_minus_L(P, cols, e).ravel()
+    gd = np.linalg.solve(A, d.ravel())
+    gm = O.gmres(lambda v: O.apply_I_minus_L(P, cols, v), d, m=30, tol=1e-12).x
+    fp = O.fixed_point(lambda v: O.apply_L(P, cols, v) + d, np.zeros_like(d), tol=1e-12)
+    assert fp.converged
+    assert rel(gm, gd) < 1e-11 and rel(fp.x.ravel(), gd) < 1e-10
+    assert rel(O.apply_R(P, gd.reshape(d.shape)), gd.reshape(d.shape)) < 1e-11
+
+
+def test_time_dependent_swr_reproduces_monodomain():
+    wl = W.config4(nsub=4, nx=241, nt=30)
+    P = problem(wl)
+    r = O.solve_matrix_free(P, precond="zero_potential", inner="dense", restart=100, tol=0.0,
+                            rtol=1e-12)
+    gs, uTm = O.mono_interface(P)
+    assert rel(r.uT, uTm) < 1e-9 and rel(r.g, gs) < 1e-9
+
+
+def test_nonlinear_swr_reproduces_monodomain():
+    wl = W.config5(nsub=3, nx=241, nt=20)
+    P = problem(wl, nl_tol=1e-14, nl_maxit=100)
+    r = O.solve_nonlinear(P, precond=True, inner="dense", tol=1e-11)
+    gs, uTm = O.mono_interface(P)
+    assert rel(r.uT, uTm) < 1e-9 and rel(r.g, gs) < 1e-9
+
+
+def test_inner_krylov_preconditioner_matches_dense():
+    P = _tiny(nsub=4, nx=81, nt=10)
+    P0 = O.zero_potential_problem(P)
+    cols0 = O.build_columns(P0)
+    y = W.random_interface(P.nblk, P.nt, 3)
+    a = O.make_precond_inner(P0, cols0)(y.ravel())
+    b = O.make_precond_dense(P0, cols0)(y.ravel())
+    assert rel(a, b) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# A planted mistake is caught: halving sigma in the flux update only (not in B)
+# breaks the SWR = monodomain pin.
+# --------------------------------------------------------------------------
+def test_planted_flux_mistake_is_caught(monkeypatch):
+    wl = W.config1(nx=121, nt=12, nsub=3)
+    P = problem(wl)
+    orig = O.s_tilde
+    monkeypatch.setattr(O, "s_tilde", lambda P_, v: 0.5 * orig(P_, v))
+    r = O.solve_new(P, "gmres", restart=200)
+    monkeypatch.setattr(O, "s_tilde", orig)
+    _, uTm = O.mono_interface(P)
+    assert rel(r.uT, uTm) > 1e-6

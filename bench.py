@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the SWR hot path on the scaling workload (one GB300 per rank).
+
+One step = one complete SWR solve of the scaling workload for every subdomain
+count N in {16, 64, 256, 500}: 200001 P1 nodes on (-50, 50), 500 Crank-Nicolson
+steps (dt = 1e-3), seeded Gaussian-well potential and Gaussian packets, Robin
+transmission p = sqrt(5) exp(-i pi/4).  Each solve is swr_build_interface
+(assembly, factorisation, d and the Toeplitz columns by marches) followed by
+swr_solve (right-preconditioned GMRES(30) on (I - L) g = d to an absolute
+residual of 1e-10, then the final march).
+
+Reported: point-steps/s of all marches in the step (whole job), the solve time
+per step, the roofline of the march kernel (FP64-ALU bound), the CPU oracle's
+march throughput on the machine's host, and an end-to-end figure with host buffers.
+Multi-GPU runs (torchrun) are replicas: every rank solves its own copy.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NSUBS = (16, 64, 256, 500)
+FLOPS_PER_POINT_STEP = 36          # Thomas with stored factors, per node and time step
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flop x GHz (max SM clock)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="swr", choices=["swr", "reference"])
+    ap.add_argument("--nsub", default=",".join(str(n) for n in NSUBS))
+    ap.add_argument("--precond", default="causal", choices=["causal", "none"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_name(nsubs):
+    return ("swr_scaling: x in (-50,50), 200001 P1 nodes, T=0.5 dt=1e-3 (500 steps), "
+            "N in {%s}, V=-5*sum of 8 seeded Gaussians, u0=4 seeded packets, "
+            "Robin p=sqrt(5)e^{-i pi/4}, build interface + GMRES(30) to 1e-10 + final march"
+            % ",".join(str(n) for n in nsubs))
+
+
+def march_point_steps(wl):
+    """Point-steps of the marches in one solve: per subdomain the d march, the
+    impulse marches (one per existing neighbour) and the final march."""
+    off = wl.off
+    N = wl.nsub
+    tot = 0
+    for j in range(N):
+        n = int(off[j + 1] - off[j] + 1)
+        marches = 1 + (1 if j > 0 else 0) + (1 if j < N - 1 else 0) + 1
+        tot += marches * n * wl.nt
+    return tot
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(wl_full, nsub_sample):
+    """Time the CPU oracle's subdomain marches (interface operator R applied to
+    zero fluxes, i.e. the d march of every subdomain) on the first nsub_sample
+    subdomains of the workload.  Returns (point-steps/s, seconds, point-steps)."""
+    import numpy as np
+    import oracle as O
+    P = O.Problem(wl_full.a0, wl_full.b0, wl_full.nx, wl_full.dt, wl_full.nt,
+                  wl_full.off.astype(np.int64), wl_full.u0, wl_full.V, sigma=wl_full.sigma)
+    t0 = time.perf_counter()
+    ps = 0
+    N = P.nsub
+    for j in range(nsub_sample):
+        a, b = int(P.off[j]), int(P.off[j + 1])
+        l = np.zeros(P.nt, np.complex128) if j > 0 else None
+        r = np.zeros(P.nt, np.complex128) if j < N - 1 else None
+        O.sub_march(P, j, P.u0[a:b + 1], l, r)
+        ps += (b - a + 1) * P.nt
+    dt = time.perf_counter() - t0
+    return ps / dt, dt, ps
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1503_02564_gb300 import workloads as W
+    wl = W.config2(nsub=500)
+    # each step: 25 of the 500 subdomain marches (about 5e6 point-steps)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, 25)
+    tot_ps, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        _, s, ps = cpu_oracle_sample(wl, 25)
+        tot_ps += ps
+        tot_s += s
+    value = tot_ps / tot_s
+    line = {
+        "impl": "reference", "metric": "SWR subdomain CN point-steps/s (solve time to 1e-10 "
+        "interface residual reported as ms_per_step)", "value": value, "unit": "point-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(NSUBS),
+                   "sample": "oracle d-marches of subdomains 0..24 of N=500 per step"},
+        "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "25 of 500 subdomain marches (401 nodes x 500 steps each)"},
+        "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_1503_02564_gb300 import swr
+    from paper_1503_02564_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    nsubs = tuple(int(x) for x in args.nsub.split(","))
+    precond = swr.SWR_PC_CAUSAL if args.precond == "causal" else swr.SWR_PC_NONE
+
+    cases = []
+    for N in nsubs:
+        wl = W.config2(nsub=N)
+        plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
+                        node_off=wl.off, p=wl.sigma, restart=30, maxit=2000, tol_abs=1e-10,
+                        precond=precond)
+        V = torch.tensor(wl.V, dtype=torch.float64, device=dev)
+        u0 = torch.tensor(wl.u0, dtype=torch.complex128, device=dev)
+        g = torch.zeros(plan.n_interface, dtype=torch.complex128, device=dev)
+        uT = torch.zeros(wl.nx, dtype=torch.complex128, device=dev)
+        cases.append(dict(N=N, wl=wl, plan=plan, V=V, u0=u0, g=g, uT=uT,
+                          ps=march_point_steps(wl)))
+    ps_step = sum(c["ps"] for c in cases)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        infos = []
+        for c in cases:
+            c["plan"].build_interface(c["V"], c["u0"])
+            infos.append(c["plan"].solve(c["g"], False, c["uT"]))
+        return infos
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for c in cases:
+        c["plan"].get_stats(reset=True)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = swr.swr_kernel_launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    per_step_ms, infos_last = [], None
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()                        # L2 flush between timed steps (untimed)
+        torch.cuda.synchronize()
+        ev0.record()
+        infos_last = step()
+        ev1.record()
+        ev1.synchronize()
+        per_step_ms.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = swr.swr_kernel_launch_count() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    t_ms = sum(per_step_ms)
+    if world > 1:
+        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = ps_step * args.steps * world / (t_ms * 1e-3)
+
+    # march kernel statistics inside the timed region (events around each launch)
+    st = [c["plan"].get_stats(reset=True) for c in cases]
+    m_launch = sum(s["march_launches"] for s in st)
+    m_ms = sum(s["march_ms"] for s in st)
+    m_ps = sum(s["march_point_steps"] for s in st)
+    achieved = FLOPS_PER_POINT_STEP * m_ps / (m_ms * 1e-3) / 1e9 if m_ms > 0 else 0.0
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    march_pss = m_ps / (m_ms * 1e-3) if m_ms > 0 else 0.0
+
+    # end-to-end: host (pinned) buffers through the public API, copies inside the region
+    e2e = None
+    if not args.no_e2e:
+        hosts = []
+        for c in cases:
+            hosts.append(dict(V=c["V"].cpu().pin_memory(), u0=c["u0"].cpu().pin_memory(),
+                              uT=torch.empty_like(c["uT"], device="cpu").pin_memory()))
+        h2d = sum(h["V"].numel() * 8 + h["u0"].numel() * 16 for h in hosts)
+        d2h = sum(h["uT"].numel() * 16 for h in hosts)
+        torch.cuda.synchronize()
+        e_ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record()
+            for c, h in zip(cases, hosts):
+                c["V"].copy_(h["V"], non_blocking=True)
+                c["u0"].copy_(h["u0"], non_blocking=True)
+                c["plan"].build_interface(c["V"], c["u0"])
+                c["plan"].solve(c["g"], False, c["uT"])
+                h["uT"].copy_(c["uT"], non_blocking=True)
+            ev1.record()
+            ev1.synchronize()
+            e_ms += ev0.elapsed_time(ev1)
+        e2e = {"value": ps_step * args.steps * world / (e_ms * 1e-3), "unit": "point-steps/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e_ms / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, s, ps = cpu_oracle_sample(cases[-1]["wl"] if cases[-1]["N"] == 500 else W.config2(nsub=500), 500)
+        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle d-marches of all 500 subdomains ({ps:.3g} point-steps, "
+                         f"{s:.1f} s)"}
+
+    if rank == 0:
+        per_n = []
+        for c, info in zip(cases, infos_last):
+            per_n.append({"N": c["N"], "iterations": info["iterations"],
+                          "residual": info["residual"], "build_ms": info["t_build_ms"],
+                          "solve_ms": info["t_solve_ms"], "final_ms": info["t_final_ms"],
+                          "interface_jump": info["interface_jump"]})
+        line = {
+            "metric": "SWR subdomain CN point-steps/s (solve time to 1e-10 interface residual "
+                      "reported as ms_per_step)",
+            "value": value, "unit": "point-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(nsubs), "point_steps_per_step": ps_step,
+                       "precond": args.precond, "l2": "flushed by a 256 MB write before each step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"kernel": "k_march_static", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                         "launches": m_launch, "avg_launch_ms": m_ms / max(m_launch, 1),
+                         "flops_per_point_step": FLOPS_PER_POINT_STEP,
+                         "peak_basis": "nominal FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                         "march_share_of_step": m_ms / t_ms if t_ms > 0 else None},
+            "hbm_roof": {"point_steps_per_s": hbm * 1e9 / 32.0,
+                         "march_point_steps_per_s": march_pss,
+                         "frac": march_pss / (hbm * 1e9 / 32.0),
+                         "basis": "32 B/point-step (read+write complex128 u) at measured HBM GB/s"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "wall_s": wall, "per_n": per_n,
+            "stats": {"toeplitz_ms": sum(s["toeplitz_ms"] for s in st),
+                      "precond_ms": sum(s["precond_ms"] for s in st),
+                      "march_ms": m_ms},
+        }
+        print(json.dumps(line), flush=True)
+    for c in cases:
+        c["plan"].destroy()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

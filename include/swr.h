@@ -1,0 +1,191 @@
+/*
+ * swr.h - C ABI of the GB300 Schwarz waveform relaxation (SWR) library.
+ *
+ * Method: Besse & Xing, "Schwarz waveform relaxation method for one dimensional
+ * Schroedinger equation with general potential" (arXiv 1503.02564).  The library
+ * solves  i u_t + u_xx + V u = 0  on (a0, b0) x (0, T) with homogeneous Neumann
+ * ends (Eq. Schequ) by non-overlapping SWR: N subdomains, each advanced by a
+ * Crank-Nicolson march with P1 finite elements (Eq. CNS_L / AvML, nonlinear
+ * Eq. CNS_NL / AvMNL), coupled through transmission conditions written as
+ * fluxes (Eq. TransmissionCondlocal, TransmisionCond).  The unknown of the outer
+ * iteration is the interface vector g of Section 3.
+ *
+ * Conventions for every entry point
+ *   - Complex arrays are interleaved (re, im) doubles: "cplx[n]" means 2n doubles.
+ *   - Unless stated otherwise an array argument is a DEVICE pointer, borrowed for
+ *     the duration of the call; the caller owns it.  The plan owns everything it
+ *     allocates (factors, interface operator, Krylov workspace).
+ *   - Work is enqueued on the plan's stream (the cudaStream_t given to swr_plan,
+ *     passed as void*; NULL = legacy default stream).  Calls that report a scalar
+ *     result to the host (swr_solve) synchronise that stream.
+ *   - Every call returns an swr_status and never aborts the process.  Device-side
+ *     faults of the numerics (zero pivot, non-finite values) are recorded in a
+ *     device status word and reported by the next call that reads it.
+ *
+ * Interface vector layout (Section 3): g = (r_1; l_2, r_2; ...; l_N), 2N-2 blocks
+ * of nt values; with 0-based subdomain j the flux r_j is block 2j (j <= N-2) and
+ * l_j is block 2j-1 (j >= 1).  Entry n-1 of a block is the flux at t_n = n dt.
+ */
+#ifndef SWR_H
+#define SWR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum swr_status {
+    SWR_OK = 0,
+    SWR_ERR_ARG = 1,            /* invalid argument or plan field                       */
+    SWR_ERR_SINGULAR = 2,       /* zero or non-finite pivot in A - B (Props. 1-2 assume  */
+                                /* A - B nonsingular)                                    */
+    SWR_ERR_NOT_CONVERGED = 3,  /* iteration cap reached; outputs hold the last iterate  */
+    SWR_ERR_NONFINITE = 4,      /* NaN/Inf in a residual or a march output               */
+    SWR_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up                    */
+    SWR_ERR_NOMEM = 6,          /* device allocation failed                              */
+    SWR_ERR_CUDA = 7,           /* other CUDA runtime error                              */
+    SWR_ERR_STATE = 8,          /* call order violated (e.g. solve before build)         */
+    SWR_ERR_UNSUPPORTED = 9     /* combination not provided by this build                */
+} swr_status;
+
+/* Potential kinds (Eq. Schequ: V(t,x) or f(u)). */
+enum { SWR_V_STATIC = 0, SWR_V_TIME = 1, SWR_V_NONLINEAR = 2 };
+/* Transmission operators S-bar (Section 2.2): Robin S-bar v = p v (the paper's
+ * S = -ip corresponds to p = -i p_paper); potential strategy of order 2, S_0^2. */
+enum { SWR_TC_ROBIN = 0, SWR_TC_S02 = 1 };
+/* Interface solvers: GMRES (Algorithms 2-3), fixed point on (I - L) g = d
+ * (Algorithm 3 with the fixed point), classical iteration g <- R g with full
+ * marches (Algorithm 1). */
+enum { SWR_SOLVER_GMRES = 0, SWR_SOLVER_FIXED_POINT = 1, SWR_SOLVER_CLASSICAL = 2 };
+/* Preconditioners for GMRES (right preconditioning):
+ *   NONE;
+ *   ZERO_POTENTIAL: P = I - L_0, the interface operator with V = 0 (Section 5);
+ *   CAUSAL: P = I - L itself (V = V(x) only), whose blocks are causal Toeplitz
+ *           (Props. 3-4) so that P^{-1} is a block forward substitution in time. */
+enum { SWR_PC_NONE = 0, SWR_PC_ZERO_POTENTIAL = 1, SWR_PC_CAUSAL = 2 };
+
+typedef struct swr_desc {
+    int32_t nx;                 /* P1 nodes on (a0, b0), nx >= 3                       */
+    double a0, b0;              /* domain; h = (b0 - a0)/(nx - 1)                      */
+    int32_t nt;                 /* time steps, T = nt * dt                             */
+    double dt;
+    int32_t nsub;               /* N >= 2 subdomains                                   */
+    const int32_t *node_off;    /* HOST, nsub+1 increasing offsets, off[0] = 0,        */
+                                /* off[N] = nx-1; subdomain j = nodes off[j]..off[j+1] */
+                                /* (interface nodes are shared); each holds >= 3 nodes */
+                                /* NULL: equal partition, the first (nx-1) mod N get   */
+                                /* one extra element                                  */
+    int32_t vkind;              /* SWR_V_*                                             */
+    int32_t tc;                 /* SWR_TC_*                                            */
+    double tc_re, tc_im;        /* Robin parameter p (S-bar v = p v)                   */
+    int32_t solver;             /* SWR_SOLVER_*                                        */
+    int32_t restart;            /* GMRES restart length m (default 30 if <= 0, at most 200)      */
+    int32_t maxit;              /* iteration cap (default 2000 if <= 0)                */
+    double tol_abs;             /* stop when ||d - (I-L) g||_2 < tol_abs (default 1e-10) */
+    int32_t precond;            /* SWR_PC_*                                            */
+    int32_t nl_maxit;           /* nonlinear inner fixed point cap (default 50)        */
+    double nl_tol;              /* inner stop: max|dz| <= nl_tol max(1,max|z|) (1e-13) */
+    double nl_coef;             /* f(u) = nl_coef |u|^2 (default 1 if 0)               */
+} swr_desc;
+
+typedef struct swr_info {
+    int32_t iterations;         /* outer iterations (GMRES steps or fixed-point sweeps) */
+    int32_t restarts;
+    double residual;            /* final TRUE residual ||d - (I-L) g||_2                */
+    double residual0;           /* ||d - (I-L) g0||_2                                   */
+    double interface_jump;      /* max_j max_n |v_j(b_j) - v_{j+1}(a_{j+1})| in the     */
+                                /* final march (diagnostic of the converged solution)  */
+    double t_build_ms;          /* swr_build_interface time (device events)            */
+    double t_solve_ms;          /* interface solve time                                 */
+    double t_final_ms;          /* final march time                                     */
+    int64_t march_point_steps;  /* point-steps marched inside swr_solve                */
+} swr_info;
+
+/* Cumulative device-time counters of a plan (CUDA events around each launch of
+ * the named kernels on the plan's stream). */
+typedef struct swr_stats {
+    int64_t march_launches;     /* subdomain march kernel launches                     */
+    int64_t march_point_steps;  /* nodes x time steps marched by those launches         */
+    double march_ms;            /* summed device time of those launches                */
+    int64_t toeplitz_launches;  /* (I - L) x applies from the Toeplitz first columns     */
+    double toeplitz_ms;
+    int64_t precond_calls;      /* block forward substitutions P^{-1} y                 */
+    double precond_ms;
+} swr_stats;
+
+typedef struct swr_plan_s *swr_plan_t;
+
+/* Validate d, copy the partition and allocate the plan on the current device.
+ * stream: cudaStream_t (as void*) on which all later work of this plan runs.
+ * Errors: SWR_ERR_ARG (bad field), SWR_ERR_NOMEM, SWR_ERR_CUDA.  *out is NULL on
+ * failure. */
+swr_status swr_plan(const swr_desc *d, swr_plan_t *out, void *stream);
+
+/* Assemble and factor the subdomain systems A_j - B_j (Eq. AvML) for potential
+ * V and build the interface problem (Section 4.1):
+ *   SWR_V_STATIC:    d = R 0 and the first columns of X^{j,1..4} (Props. 3-4),
+ *                    i.e. L and d of Eq. chp1_ILgd explicitly (Algorithm 3);
+ *   SWR_V_TIME:      d = R 0, and L_0 when precond == ZERO_POTENTIAL;
+ *   SWR_V_NONLINEAR: L_0 when precond == ZERO_POTENTIAL.
+ * V:  double[nx] (STATIC; V0 for NONLINEAR) or double[(nt+1) * nx], row n = V(t_n, .)
+ *     (TIME).  Copied into the plan.
+ * u0: cplx[nx] initial value.  Copied into the plan.
+ * Errors: SWR_ERR_SINGULAR (a pivot of A - B vanished), SWR_ERR_ARG, SWR_ERR_CUDA. */
+swr_status swr_build_interface(swr_plan_t p, const double *V, const double *u0);
+
+/* Solve the interface problem with the plan's solver, then run the final march
+ * (last step of Algorithms 1-3).
+ * g:    cplx[(2N-2) * nt]; on entry the initial guess g0 (ignored if
+ *       g_is_initial == 0, then g0 = 0), on exit the converged interface vector.
+ *       May be NULL (then g0 = 0 and the result is not returned).
+ * uT:   cplx[nx] u at the final time; the interface node takes the left
+ *       subdomain's value.  May be NULL.
+ * info: HOST, may be NULL.
+ * Returns SWR_ERR_NOT_CONVERGED when the cap is reached (outputs hold the last
+ * iterate, info filled), SWR_ERR_STATE before swr_build_interface. */
+swr_status swr_solve(swr_plan_t p, double *g, int32_t g_is_initial, double *uT,
+                     swr_info *info);
+
+/* One application of the interface operator R (Eq. interfacepbR): march every
+ * subdomain with the fluxes g_in (and the plan's u0), then form the new fluxes
+ * by Eq. TransmisionCond into g_out.  Both cplx[(2N-2) * nt], distinct buffers.
+ * Requires swr_build_interface (it holds the factors and u0). */
+swr_status swr_apply_R(swr_plan_t p, const double *g_in, double *g_out);
+
+/* y = (I - L) x from the Toeplitz first columns (Eq. chp1_ILgd, Props. 3-4).
+ * SWR_V_STATIC only.  x, y: cplx[(2N-2) * nt], distinct buffers. */
+swr_status swr_apply_interface(swr_plan_t p, const double *x, double *y);
+
+/* Copy the built interface problem out: d (cplx[(2N-2) * nt]) and the first
+ * columns cols (cplx[4 N nt], column p-1 of subdomain j at (4j + p - 1) * nt,
+ * zero where the block does not exist).  Either may be NULL. */
+swr_status swr_get_interface(swr_plan_t p, double *d, double *cols);
+
+/* x = P^{-1} y for the plan's preconditioner (ZERO_POTENTIAL or CAUSAL).
+ * x, y: cplx[(2N-2) * nt], distinct buffers. */
+swr_status swr_apply_precond(swr_plan_t p, const double *y, double *x);
+
+/* Gradient of J = ||u(T) - u_target||^2_M with respect to the nodal potential
+ * by an adjoint march.  Not provided by this build: returns SWR_ERR_UNSUPPORTED. */
+swr_status swr_adjoint(swr_plan_t p, const double *dJ_duT, double *dJ_dV,
+                       int32_t ckpt_every);
+
+/* Free everything the plan owns (after synchronising its stream).  NULL is a no-op. */
+void swr_destroy(swr_plan_t p);
+
+/* Copy the plan's cumulative counters into *out (host); reset them if reset != 0.
+ * Synchronises the plan's stream. */
+swr_status swr_get_stats(swr_plan_t p, swr_stats *out, int32_t reset);
+
+/* Number of CUDA kernels this library has launched in this process, over all
+ * plans (a monotonically increasing counter; host-only, no device work). */
+int64_t swr_kernel_launch_count(void);
+
+/* Static, human-readable name of a status code. */
+const char *swr_status_string(swr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWR_H */

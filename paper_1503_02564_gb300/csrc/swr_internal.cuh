@@ -1,0 +1,140 @@
+// Internal declarations shared by the CUDA translation units of libswr.
+// Complex FP64 values are double2 (x = re, y = im).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swr.h"
+
+// ---------------------------------------------------------------------------
+// complex helpers (each complex multiply-add is 4 FP64 pipe operations)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cmk(double re, double im) { return make_double2(re, im); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// c + a*b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(-a.y, b.y, fma(a.x, b.x, c.x)), fma(a.y, b.x, fma(a.x, b.y, c.y)));
+}
+// c - a*b
+__device__ __forceinline__ double2 cfms(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.y, b.y, fma(-a.x, b.x, c.x)), fma(-a.y, b.x, fma(-a.x, b.y, c.y)));
+}
+// conj(a)*b
+__device__ __forceinline__ double2 cconjmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ double2 crcp(double2 a) {
+    double s = 1.0 / fma(a.x, a.x, a.y * a.y);
+    return make_double2(a.x * s, -a.y * s);
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// ---------------------------------------------------------------------------
+// device status word bits
+// ---------------------------------------------------------------------------
+enum : int {
+    ST_SINGULAR = 1,
+    ST_NONFINITE = 2,
+    ST_TIMEOUT = 4,
+    ST_NL_NOCONV = 8,
+};
+
+// ---------------------------------------------------------------------------
+// March systems.  One "system" is one right-hand side of one subdomain:
+// its u0 (given or zero) and its flux inputs (from an interface vector, a unit
+// impulse at t_1, or zero).  The march emits the new fluxes of Eq. TransmisionCond.
+// ---------------------------------------------------------------------------
+enum : int {
+    SYS_ZERO_U0 = 1,     // start from u0 = 0
+    SYS_IMP_L = 2,       // l_{j,1} = 1, other l = 0
+    SYS_IMP_R = 4,       // r_{j,1} = 1, other r = 0
+    SYS_WRITE_UT = 8,    // write u(T) into the nodal output
+    SYS_TRACE = 16,      // write v_n at both ends into the trace buffer
+};
+
+struct MarchSys {
+    int sub;             // subdomain index
+    int flags;           // SYS_*
+    int in_l, in_r;      // block index in gin holding l_j / r_j (or -1)
+    int out_a, out_b;    // block index in gout for -l + 2 S v(a) / -r + 2 S v(b) (or -1)
+};
+
+// Chunked (partitioned) factorisation of the subdomain matrices for one chunk
+// length LMAX.  Subdomain j, chunk p (0 <= p < P), separators 0..P.
+struct FactorSet {
+    int L = 0;           // LMAX (template parameter of the march kernel)
+    int P = 0;           // chunks per subdomain (padded to the maximum)
+    int levels = 0;      // PCR levels over P+1 separators
+    int* sub_P = nullptr;          // [N]   real chunks of subdomain j
+    int* sep_pos = nullptr;        // [N][P+1] local node index of separator p
+    unsigned char* clen = nullptr; // [N][P] interior nodes of chunk p (0 = dummy)
+    double2* fac = nullptr;        // [N][L][4][P]  (q, c, a, b) per interior node
+    double2* tips = nullptr;       // [N][P][4]     (a_first, b_first, a_last, b_last)
+    double2* sep = nullptr;        // [N][3][P+1]   (E_left, E_right, 1/delta)
+    double2* pcr = nullptr;        // [N][levels][2][P+1] (alpha, gamma)
+    double2* red = nullptr;        // [N][6][P+1]   scratch for the PCR coefficient run
+};
+
+struct MarchArgs {
+    int nt, P, levels, C, G, T, nsys;
+    const MarchSys* sys;
+    const int* sub_n;     // nodes of subdomain j
+    const int* sub_goff;  // global index of its first node
+    const int* sub_tc;    // bit0: left end carries a transmission condition, bit1: right
+    const int* sub_P;
+    const int* sep_pos;
+    const unsigned char* clen;
+    const double2* fac;
+    const double2* sep;
+    const double2* pcr;
+    const double2* u0;    // nodal initial value (global)
+    const double2* gin;   // interface vector input (blocks of nt)
+    double2* gout;        // output blocks
+    double2* uT;          // nodal output
+    double2* trace;       // [nsys][2][nt]
+    double2 two_sigma;    // 2 p (Robin): 2 S-tilde v = 2 p v
+    double2 inv_ik;       // 1/(i kappa), kappa = (2/dt)(h/6): the system is scaled by it
+    int* status;
+};
+
+// Process-wide count of kernels launched by this library (swr_capi.cu).
+void swr_count_launch(int n);
+
+// Host-side launchers (swr_march.cu)
+int swr_launch_assemble_static(const double* V, int N, const int* d_n, const int* d_goff,
+                               const int* d_loff, const int* d_tc, int ntot, double h, double dt,
+                               double2 sigma0, double2 inv_ik, double2* dg, double2* od,
+                               cudaStream_t s);
+int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t s);
+void swr_factor_free(FactorSet& fs);
+int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
+                      const double2* od, int* status, cudaStream_t s);
+int swr_launch_march(const FactorSet& fs, MarchArgs a, int nsys_groups, cudaStream_t s);
+int swr_march_smem_bytes(int T, int G);
+
+// Interface algebra launchers (swr_krylov.cu)
+int swr_launch_toeplitz(int N, int nt, const double2* cols, const double2* x, const double2* add,
+                        double2* y, int mode, cudaStream_t s);
+int swr_launch_dots(const double2* V, long long ldv, int nvec, const double2* w, long long n,
+                    double2* partial, int nblocks, double2* out, cudaStream_t s);
+int swr_launch_gemv_sub(const double2* V, long long ldv, int nvec, const double2* h, double2* w,
+                        long long n, double sign, cudaStream_t s);
+int swr_launch_axpby(double2* y, const double2* x, long long n, double2 a, double2 b,
+                     cudaStream_t s);
+int swr_launch_scale_by_rnorm(double2* v, const double2* w, long long n, const double2* hdiag,
+                              cudaStream_t s);
+int swr_launch_givens(double2* H, int ldh, double2* cs, double2* sn, double2* sv, int j,
+                      double* res_out, cudaStream_t s);
+int swr_launch_lsq(const double2* H, int ldh, const double2* sv, int k, double2* y,
+                   cudaStream_t s);
+int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0inv,
+                      const double2* y, double2* x, int sweeps, double2* hist, cudaStream_t s);
+int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s);
+int swr_launch_jump(const double2* trace, const MarchSys* sys, int N, int nt, double* out,
+                    cudaStream_t s);

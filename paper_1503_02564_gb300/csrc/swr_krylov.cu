@@ -1,0 +1,474 @@
+// Interface algebra of the SWR method: the explicit interface operator of
+// Algorithm 3 (blocks X^{j,p} are causal Toeplitz, Props. 3-4), the GMRES
+// building blocks (Saad's restarted GMRES with classical Gram-Schmidt applied
+// twice and Givens rotations), and the time-causal block forward substitution
+// that inverts I - L (or I - L_0) block by block in time.
+//
+// Interface vector: 2N-2 blocks of nt values; block 2k = r_k, block 2k+1 = l_{k+1}
+// (0-based subdomains).  First columns: slot 4j + (p-1) holds X^{j,p}, p = 1..4.
+//   r_{j-1} = X^{j,1} l_j + X^{j,2} r_j,   l_{j+1} = X^{j,3} l_j + X^{j,4} r_j.
+#include <cooperative_groups.h>
+
+#include "swr_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+// Sources of output block o: (column slot, input block) pairs, -1 if absent.
+__device__ __forceinline__ void block_sources(int o, int N, int& c1, int& i1, int& c2, int& i2) {
+    if ((o & 1) == 0) {          // r_k, produced by subdomain j = k+1
+        const int j = o / 2 + 1;
+        c1 = 4 * j + 0;
+        i1 = 2 * j - 1;
+        if (j <= N - 2) {
+            c2 = 4 * j + 1;
+            i2 = 2 * j;
+        } else {
+            c2 = -1;
+            i2 = -1;
+        }
+    } else {                     // l_{k+1}, produced by subdomain j = k
+        const int j = (o - 1) / 2;
+        c1 = 4 * j + 3;
+        i1 = 2 * j;
+        if (j >= 1) {
+            c2 = 4 * j + 2;
+            i2 = 2 * j - 1;
+        } else {
+            c2 = -1;
+            i2 = -1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y = x - L x (mode 0)  or  y = L x + add (mode 1, the fixed point of Alg. 3).
+// One CTA per output block; the two first columns and the two input blocks
+// are staged in shared memory; thread q computes the causal sums for times q
+// and nt-1-q (equal work per thread).
+// ---------------------------------------------------------------------------
+__global__ void k_toeplitz(int N, int nt, const double2* __restrict__ cols,
+                           const double2* __restrict__ x, const double2* __restrict__ add,
+                           double2* __restrict__ y, int mode) {
+    extern __shared__ double2 sh[];
+    const int o = blockIdx.x;
+    int c1, i1, c2, i2;
+    block_sources(o, N, c1, i1, c2, i2);
+    double2* C1 = sh;
+    double2* X1 = sh + nt;
+    double2* C2 = sh + 2 * nt;
+    double2* X2 = sh + 3 * nt;
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        C1[t] = cols[(size_t)c1 * nt + t];
+        X1[t] = x[(size_t)i1 * nt + t];
+        C2[t] = (c2 >= 0) ? cols[(size_t)c2 * nt + t] : zero;
+        X2[t] = (c2 >= 0) ? x[(size_t)i2 * nt + t] : zero;
+    }
+    __syncthreads();
+    const bool two = (c2 >= 0);
+    for (int q = threadIdx.x; q < (nt + 1) / 2; q += blockDim.x) {
+        for (int e = 0; e < 2; ++e) {
+            const int n = (e == 0) ? q : nt - 1 - q;
+            if (e == 1 && n == q) break;
+            double2 acc0 = zero, acc1 = zero;
+            int s = 0;
+            for (; s + 1 <= n; s += 2) {
+                acc0 = cfma(C1[n - s], X1[s], acc0);
+                acc1 = cfma(C1[n - s - 1], X1[s + 1], acc1);
+            }
+            if (s <= n) acc0 = cfma(C1[n - s], X1[s], acc0);
+            if (two) {
+                s = 0;
+                for (; s + 1 <= n; s += 2) {
+                    acc0 = cfma(C2[n - s], X2[s], acc0);
+                    acc1 = cfma(C2[n - s - 1], X2[s + 1], acc1);
+                }
+                if (s <= n) acc0 = cfma(C2[n - s], X2[s], acc0);
+            }
+            const double2 acc = cadd(acc0, acc1);
+            const size_t idx = (size_t)o * nt + n;
+            y[idx] = (mode == 0) ? csub(x[idx], acc) : cadd(acc, add[idx]);
+        }
+    }
+}
+
+int swr_launch_toeplitz(int N, int nt, const double2* cols, const double2* x, const double2* add,
+                        double2* y, int mode, cudaStream_t s) {
+    const int smem = 4 * nt * (int)sizeof(double2);
+    if (smem > 227 * 1024) return -2;
+    if (cudaFuncSetAttribute(k_toeplitz, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -1;
+    k_toeplitz<<<2 * N - 2, 256, smem, s>>>(N, nt, cols, x, add, y, mode);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Batched dot products out[i] = V_i^H w, i < nvec (V_i = V + i*ldv), in two
+// deterministic passes (per-CTA partial sums, then a fixed-order reduction).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+__global__ void k_dots_partial(const double2* __restrict__ V, long long ldv, int nvec,
+                               const double2* __restrict__ w, long long n,
+                               double2* __restrict__ partial) {
+    __shared__ double2 red[32];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (int i = 0; i < nvec; ++i) {
+        const double2* vi = V + (size_t)i * ldv;
+        double2 acc = make_double2(0.0, 0.0);
+        for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+            acc = cfma(make_double2(vi[k].x, -vi[k].y), w[k], acc);
+        acc = warp_sum(acc);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        if (lane == 0) red[wid] = acc;
+        __syncthreads();
+        if (wid == 0) {
+            double2 v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : make_double2(0.0, 0.0);
+            v = warp_sum(v);
+            if (lane == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_dots_final(const double2* __restrict__ partial, int nblocks, int nvec,
+                             double2* __restrict__ out) {
+    const int i = blockIdx.x;
+    if (i >= nvec) return;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int b = threadIdx.x; b < nblocks; b += 32) acc = cadd(acc, partial[(size_t)i * nblocks + b]);
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) out[i] = acc;
+}
+
+int swr_launch_dots(const double2* V, long long ldv, int nvec, const double2* w, long long n,
+                    double2* partial, int nblocks, double2* out, cudaStream_t s) {
+    k_dots_partial<<<nblocks, 256, 0, s>>>(V, ldv, nvec, w, n, partial);
+    k_dots_final<<<nvec, 32, 0, s>>>(partial, nblocks, nvec, out);
+    swr_count_launch(2);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// w += sign * sum_i V_i h_i
+__global__ void k_gemv(const double2* __restrict__ V, long long ldv, int nvec,
+                       const double2* __restrict__ h, double2* __restrict__ w, long long n,
+                       double sign) {
+    __shared__ double2 hs[256];
+    for (int i = threadIdx.x; i < nvec && i < 256; i += blockDim.x)
+        hs[i] = make_double2(sign * h[i].x, sign * h[i].y);
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        double2 acc = w[k];
+        for (int i = 0; i < nvec; ++i) acc = cfma(hs[i], V[(size_t)i * ldv + k], acc);
+        w[k] = acc;
+    }
+}
+
+int swr_launch_gemv_sub(const double2* V, long long ldv, int nvec, const double2* h, double2* w,
+                        long long n, double sign, cudaStream_t s) {
+    if (nvec > 256) return -2;
+    k_gemv<<<152 * 4, 256, 0, s>>>(V, ldv, nvec, h, w, n, sign);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// y = a*y + b*x
+__global__ void k_axpby(double2* __restrict__ y, const double2* __restrict__ x, long long n,
+                        double2 a, double2 b) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const double2 yv = (a.x == 0.0 && a.y == 0.0) ? make_double2(0.0, 0.0) : cmul(a, y[k]);
+        y[k] = (b.x == 0.0 && b.y == 0.0) ? yv : cfma(b, x[k], yv);
+    }
+}
+
+int swr_launch_axpby(double2* y, const double2* x, long long n, double2 a, double2 b,
+                     cudaStream_t s) {
+    k_axpby<<<152 * 4, 256, 0, s>>>(y, x, n, a, b);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// v = w / hdiag[0].x  (hdiag points at the stored norm)
+__global__ void k_scale_rnorm(double2* __restrict__ v, const double2* __restrict__ w, long long n,
+                              const double2* __restrict__ hnorm) {
+    const double nr = hnorm[0].x;
+    const double s = (nr > 0.0) ? 1.0 / nr : 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride)
+        v[k] = cscale(w[k], s);
+}
+
+int swr_launch_scale_by_rnorm(double2* v, const double2* w, long long n, const double2* hnorm,
+                              cudaStream_t s) {
+    k_scale_rnorm<<<152 * 4, 256, 0, s>>>(v, w, n, hnorm);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Arnoldi column j finish + Givens rotations (one thread).
+// H is column-major with leading dimension ldh = m+1.  On entry column j holds
+// h1 (first Gram-Schmidt pass); sv[ldh..] scratch holds h2 (second pass) and the
+// squared norm of the orthogonalised vector.  Layout of the scratch area
+// work = sv + ldh:  work[0..j] = h2, work[j+1] = (|w|^2, 0).
+// After: H(j+1, j) = |w| (stored unrotated in work[ldh], used for scaling),
+// rotations applied, sv updated, *res_out = |sv[j+1]|.
+// ---------------------------------------------------------------------------
+__global__ void k_givens(double2* H, int ldh, double2* cs, double2* sn, double2* sv, int j,
+                         double* res_out) {
+    double2* col = H + (size_t)j * ldh;
+    double2* work = sv + ldh;
+    for (int i = 0; i <= j; ++i) col[i] = cadd(col[i], work[i]);
+    const double hn = sqrt(fmax(work[j + 1].x, 0.0));
+    col[j + 1] = make_double2(hn, 0.0);
+    work[ldh] = make_double2(hn, 0.0);
+    for (int i = 0; i < j; ++i) {
+        const double2 a = col[i], b = col[i + 1];
+        // [c s; -conj(s) c], c real
+        col[i] = cfma(sn[i], b, cscale(a, cs[i].x));
+        col[i + 1] = csub(cscale(b, cs[i].x), cconjmul(sn[i], a));
+    }
+    const double2 a = col[j], b = col[j + 1];
+    const double aa = hypot(a.x, a.y), bb = hypot(b.x, b.y);
+    const double den = hypot(aa, bb);
+    double c;
+    double2 s;
+    if (den == 0.0) {
+        c = 1.0;
+        s = make_double2(0.0, 0.0);
+    } else {
+        const double2 ph = (aa > 0.0) ? make_double2(a.x / aa, a.y / aa) : make_double2(1.0, 0.0);
+        c = aa / den;
+        s = cscale(cmul(ph, make_double2(b.x, -b.y)), 1.0 / den);
+    }
+    cs[j] = make_double2(c, 0.0);
+    sn[j] = s;
+    col[j] = cfma(s, b, cscale(a, c));
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 sj = sv[j];
+    sv[j + 1] = cmul(make_double2(-s.x, s.y), sj);   // -conj(s) * s_j
+    sv[j] = cscale(sj, c);
+    *res_out = hypot(sv[j + 1].x, sv[j + 1].y);
+}
+
+int swr_launch_givens(double2* H, int ldh, double2* cs, double2* sn, double2* sv, int j,
+                      double* res_out, cudaStream_t s) {
+    k_givens<<<1, 1, 0, s>>>(H, ldh, cs, sn, sv, j, res_out);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Solve the k x k upper-triangular R y = sv (one thread).
+__global__ void k_lsq(const double2* H, int ldh, const double2* sv, int k, double2* y) {
+    for (int i = k - 1; i >= 0; --i) {
+        double2 acc = sv[i];
+        for (int c = i + 1; c < k; ++c) acc = cfms(H[(size_t)c * ldh + i], y[c], acc);
+        y[i] = cmul(acc, crcp(H[(size_t)i * ldh + i]));
+    }
+}
+
+int swr_launch_lsq(const double2* H, int ldh, const double2* sv, int k, double2* y,
+                   cudaStream_t s) {
+    k_lsq<<<1, 1, 0, s>>>(H, ldh, sv, k, y);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Interface mismatch of the final march: max |v_j(b_j) - v_{j+1}(a_{j+1})|
+// (trace buffer [sys][2][nt], systems 0..N-1 are the subdomains in order).
+// ---------------------------------------------------------------------------
+__global__ void k_jump(const double2* __restrict__ trace, int N, int nt,
+                       unsigned long long* out) {
+    double m = 0.0;
+    const long long tot = (long long)(N - 1) * nt;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / nt), n = (int)(q % nt);
+        const double2 a = trace[((size_t)j * 2 + 1) * nt + n];
+        const double2 b = trace[((size_t)(j + 1) * 2 + 0) * nt + n];
+        m = fmax(m, hypot(a.x - b.x, a.y - b.y));
+    }
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+int swr_launch_jump(const double2* trace, const MarchSys*, int N, int nt, double* out,
+                    cudaStream_t s) {
+    cudaMemsetAsync(out, 0, sizeof(double), s);
+    k_jump<<<64, 256, 0, s>>>(trace, N, nt, reinterpret_cast<unsigned long long*>(out));
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Time-causal block forward substitution for (I - L) x = y.
+// Every block of L is lower-triangular Toeplitz in time (Props. 3-4), so with
+// x_n the values of all blocks at time n:
+//     x_n - L[0] x_n = y_n + sum_{s<n} L[n-s] x_s.
+// The lag-0 matrix L[0] couples the two fluxes of one interface (r_k, l_{k+1})
+// strongly (2x2 block D_k, solved exactly) and neighbouring interfaces only
+// through the corner entries of the subdomain inverse (X^{j,2}[0], X^{j,3}[0]),
+// which are resolved by `sweeps` block-Jacobi sweeps (0: dropped).
+// Time is processed in tiles of b steps:
+//   k_causal_far  (whole GPU): hist = y + contributions of all earlier tiles;
+//   k_causal_near (one thread-block cluster): the in-tile history and the
+//                 lag-0 solves, step by step, one thread per interface.
+// ---------------------------------------------------------------------------
+__global__ void k_lag0_setup(int N, int nt, const double2* __restrict__ cols,
+                             double2* __restrict__ lag0) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N - 1) return;
+    const double2 a = cols[(size_t)(4 * (k + 1) + 0) * nt];   // X^{k+1,1}[0]: r_k <- l_{k+1}
+    const double2 b = cols[(size_t)(4 * k + 3) * nt];         // X^{k,4}[0]:   l_{k+1} <- r_k
+    // D = [[1, -a], [-b, 1]],  D^{-1} = [[1, a], [b, 1]] / (1 - a b)
+    const double2 det = csub(make_double2(1.0, 0.0), cmul(a, b));
+    const double2 r = crcp(det);
+    lag0[k * 4 + 0] = r;
+    lag0[k * 4 + 1] = cmul(a, r);
+    lag0[k * 4 + 2] = cmul(b, r);
+    lag0[k * 4 + 3] = r;
+}
+
+int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s) {
+    k_lag0_setup<<<(N + 127) / 128, 128, 0, s>>>(N, nt, cols, lag0);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// hist[o][n - t0] = y_o[n] + sum_src sum_{s < t0} c[n-s] x_src[s],  n in [t0, t0+b)
+__global__ void k_causal_far(int N, int nt, int t0, int b, const double2* __restrict__ cols,
+                             const double2* __restrict__ x, const double2* __restrict__ y,
+                             double2* __restrict__ hist) {
+    const int o = blockIdx.x;
+    int c1, i1, c2, i2;
+    block_sources(o, N, c1, i1, c2, i2);
+    const int nb = min(b, nt - t0);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int q = w; q < nb; q += nw) {                 // one warp per time of the tile
+        const int n = t0 + q;
+        double2 acc = zero;
+        for (int s = lane; s < t0; s += 32) {
+            acc = cfma(cols[(size_t)c1 * nt + n - s], x[(size_t)i1 * nt + s], acc);
+            if (c2 >= 0) acc = cfma(cols[(size_t)c2 * nt + n - s], x[(size_t)i2 * nt + s], acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) hist[(size_t)o * b + q] = cadd(acc, y[(size_t)o * nt + n]);
+    }
+}
+
+__global__ void k_causal_near(int N, int nt, int t0, int b, int sweeps,
+                              const double2* __restrict__ cols, const double2* __restrict__ lag0,
+                              const double2* __restrict__ hist, double2* __restrict__ x) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int k = (int)cl.block_rank() * blockDim.x + threadIdx.x;   // interface
+    const bool act = (k < N - 1);
+    const int nb = min(b, nt - t0);
+    const double2 zero = make_double2(0.0, 0.0);
+    // sources: r_k <- X^{k+1,1} l_{k+1} (block 2k+1), X^{k+1,2} r_{k+1} (block 2k+2)
+    //          l_{k+1} <- X^{k,4} r_k (block 2k), X^{k,3} l_k (block 2k-1)
+    const int o1 = 2 * k, o2 = 2 * k + 1;
+    const double2* cA = cols + (size_t)(4 * (k + 1) + 0) * nt;
+    const double2* cB = (k + 1 <= N - 2) ? cols + (size_t)(4 * (k + 1) + 1) * nt : nullptr;
+    const double2* cC = cols + (size_t)(4 * k + 3) * nt;
+    const double2* cD = (k >= 1) ? cols + (size_t)(4 * k + 2) * nt : nullptr;
+    const double2* xA = x + (size_t)(2 * k + 1) * nt;
+    const double2* xB = x + (size_t)(2 * k + 2) * nt;
+    const double2* xC = x + (size_t)(2 * k) * nt;
+    const double2* xD = x + (size_t)(2 * k - 1) * nt;
+    double2 D00 = zero, D01 = zero, D10 = zero, D11 = zero;
+    if (act) {
+        D00 = lag0[k * 4 + 0];
+        D01 = lag0[k * 4 + 1];
+        D10 = lag0[k * 4 + 2];
+        D11 = lag0[k * 4 + 3];
+    }
+    for (int q = 0; q < nb; ++q) {
+        const int n = t0 + q;
+        double2 r1 = zero, r2 = zero;
+        if (act) {
+            r1 = hist[(size_t)o1 * b + q];
+            r2 = hist[(size_t)o2 * b + q];
+            for (int s = t0; s < n; ++s) {
+                r1 = cfma(cA[n - s], xA[s], r1);
+                if (cB) r1 = cfma(cB[n - s], xB[s], r1);
+                r2 = cfma(cC[n - s], xC[s], r2);
+                if (cD) r2 = cfma(cD[n - s], xD[s], r2);
+            }
+        }
+        double2 z1 = zero, z2 = zero;
+        if (act) {
+            z1 = cfma(D01, r2, cmul(D00, r1));
+            z2 = cfma(D11, r2, cmul(D10, r1));
+            x[(size_t)o1 * nt + n] = z1;
+            x[(size_t)o2 * nt + n] = z2;
+        }
+        for (int sw = 0; sw < sweeps; ++sw) {
+            __threadfence();
+            cl.sync();
+            double2 e1 = r1, e2 = r2;
+            if (act) {
+                if (cB) e1 = cfma(cB[0], xB[n], e1);
+                if (cD) e2 = cfma(cD[0], xD[n], e2);
+            }
+            cl.sync();
+            if (act) {
+                z1 = cfma(D01, e2, cmul(D00, e1));
+                z2 = cfma(D11, e2, cmul(D10, e1));
+                x[(size_t)o1 * nt + n] = z1;
+                x[(size_t)o2 * nt + n] = z2;
+            }
+        }
+        __threadfence();
+        cl.sync();
+    }
+}
+
+int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, const double2* y,
+                      double2* x, int sweeps, double2* hist, cudaStream_t s) {
+    const int b = 32;
+    const int nif = N - 1;
+    int tpb = 64;
+    int C = (nif + tpb - 1) / tpb;
+    while (C > 16 && tpb < 1024) {
+        tpb *= 2;
+        C = (nif + tpb - 1) / tpb;
+    }
+    if (C > 16) return -2;
+    if (C > 8 &&
+        cudaFuncSetAttribute(k_causal_near, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+        return -1;
+    for (int t0 = 0; t0 < nt; t0 += b) {
+        k_causal_far<<<2 * N - 2, 256, 0, s>>>(N, nt, t0, b, cols, x, y, hist);
+    swr_count_launch(2);
+        if (cudaGetLastError() != cudaSuccess) return -1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C);
+        cfg.blockDim = dim3(tpb);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, k_causal_near, N, nt, t0, b, sweeps, cols, lag0,
+                               (const double2*)hist, x) != cudaSuccess)
+            return -1;
+    }
+    return 0;
+}

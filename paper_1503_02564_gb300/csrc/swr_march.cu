@@ -1,0 +1,646 @@
+// Subdomain Crank-Nicolson marches of the SWR method (Besse & Xing, Section 2.2).
+//
+// Each march solves, for n = 1..nt, the subdomain system of Eq. AvML
+//     (A_j - B_j) v_n = (2i/dt) M_j u_{n-1} - Q_j^T (l_n, r_n)^T,   u_n = 2 v_n - u_{n-1},
+// with the Robin boundary matrix B_j = p Q_j^T Q_j at ends that carry a
+// transmission condition, and emits the fluxes of Eq. TransmisionCond
+//     r_{j-1,n} = -l_{j,n} + 2 p v_n(a_j),      l_{j+1,n} = -r_{j,n} + 2 p v_n(b_j).
+//
+// GB300 design.  FP64 on this part runs at about 1/64 of the FP32 rate and a
+// partially filled warp costs the FP64 pipe as much as a full one, so the march
+// is FP64-ALU bound and needs many full warps.  One thread per right-hand side
+// (plain Thomas) gives at most a few thousand threads; instead every tridiagonal
+// system is cut into P chunks of <= L interior nodes separated by single
+// separator nodes (a SPIKE-type partition):
+//   * the chunk state u (L complex values) lives in registers for all nt steps;
+//   * each chunk is solved with its own precomputed LU (2 complex factors per
+//     node) and corrected with two precomputed spikes (the chunk's responses to
+//     its two separators);
+//   * the P+1 separator unknowns form a tridiagonal Schur complement with a
+//     constant matrix, solved each step by parallel cyclic reduction (PCR) whose
+//     per-level coefficients are precomputed, so a step only updates right-hand
+//     sides (2 complex FMAs per separator and level);
+//   * a CTA carries G systems (short subdomains) or one system is spread over a
+//     thread-block cluster of C CTAs (long subdomains), the separators being read
+//     through distributed shared memory.
+// The system is pre-scaled by 1/(i kappa), kappa = (2/dt)(h/6), so that the
+// right-hand side (2i/dt) M u becomes the integer stencil u_{i-1} + 4 u_i + u_{i+1}.
+#include <cooperative_groups.h>
+
+#include "swr_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+// ---------------------------------------------------------------------------
+// Assembly of A_j - B_j (P1 elements, generalised mass by exact quadrature of the
+// P1 interpolant of W), scaled by 1/(i kappa).  dg[loff_j + i] is the diagonal,
+// od[loff_j + i] the coupling of local nodes i and i+1.
+// ---------------------------------------------------------------------------
+__global__ void k_assemble_static(const double* __restrict__ V, const int* __restrict__ n_,
+                                  const int* __restrict__ goff_, const int* __restrict__ loff_,
+                                  const int* __restrict__ tc_, double h, double dt, double2 sigma0,
+                                  double2 inv_ik, double2* __restrict__ dg,
+                                  double2* __restrict__ od) {
+    const int j = blockIdx.y;
+    const int n = n_[j];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int g = goff_[j] + i;
+    const int lo = loff_[j] + i;
+    const int tc = tc_[j];
+    const double W0 = V ? V[g] : 0.0;
+    double md = 0.0, sd = 0.0, wd = 0.0;
+    if (i > 0) {
+        const double Wm = V ? V[g - 1] : 0.0;
+        md += h / 3.0;
+        sd += 1.0 / h;
+        wd += h / 12.0 * (Wm + 3.0 * W0);
+    }
+    if (i < n - 1) {
+        const double Wp = V ? V[g + 1] : 0.0;
+        md += h / 3.0;
+        sd += 1.0 / h;
+        wd += h / 12.0 * (3.0 * W0 + Wp);
+    }
+    double2 D = make_double2(-sd + wd, 2.0 / dt * md);
+    if ((i == 0 && (tc & 1)) || (i == n - 1 && (tc & 2))) D = csub(D, sigma0);
+    dg[lo] = cmul(D, inv_ik);
+    if (i < n - 1) {
+        const double Wp = V ? V[g + 1] : 0.0;
+        const double2 E = make_double2(1.0 / h + h / 12.0 * (W0 + Wp), 2.0 / dt * (h / 6.0));
+        od[lo] = cmul(E, inv_ik);
+    } else {
+        od[lo] = make_double2(0.0, 0.0);
+    }
+}
+
+int swr_launch_assemble_static(const double* V, int N, const int* d_n, const int* d_goff,
+                               const int* d_loff, const int* d_tc, int nmax, double h, double dt,
+                               double2 sigma0, double2 inv_ik, double2* dg, double2* od,
+                               cudaStream_t s) {
+    dim3 grid((nmax + 255) / 256, N);
+    k_assemble_static<<<grid, 256, 0, s>>>(V, d_n, d_goff, d_loff, d_tc, h, dt, sigma0, inv_ik, dg,
+                                           od);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Chunking, chunk LU and spikes.  One thread per (subdomain, chunk).
+// Subdomain with n nodes: Pj = ceil((n-1)/(L+1)) chunks, separators at local
+// nodes sep_0 = 0 < sep_1 < ... < sep_Pj = n-1, interior counts differing by at
+// most one.  Chunks p >= Pj are dummies (no interior).
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void k_factor_chunks(int N, int P, const int* __restrict__ n_,
+                                const int* __restrict__ loff_, const double2* __restrict__ dg,
+                                const double2* __restrict__ od, int* __restrict__ sub_P,
+                                int* __restrict__ sep_pos, unsigned char* __restrict__ clen,
+                                double2* __restrict__ fac, double2* __restrict__ tips,
+                                int* status) {
+    const int j = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int n = n_[j];
+    const int Pj = (n - 1 + L) / (L + 1);
+    const int interior = n - 1 - Pj;
+    const int q = interior / Pj, rem = interior % Pj;
+    int Lp, sp;
+    if (p < Pj) {
+        Lp = q + (p < rem ? 1 : 0);
+        sp = p + p * q + (p < rem ? p : rem);
+    } else {
+        Lp = 0;
+        sp = n - 1;
+    }
+    if (p == 0) sub_P[j] = Pj;
+    sep_pos[j * (P + 1) + p] = sp;
+    if (p == P - 1) sep_pos[j * (P + 1) + P] = n - 1;
+    clen[j * P + p] = (unsigned char)Lp;
+    const double2 zero = make_double2(0.0, 0.0);
+    double2* F = fac + (size_t)j * L * 4 * P;
+    if (Lp == 0) {
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) F[(i * 4 + k) * P + p] = zero;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tips[((size_t)j * P + p) * 4 + k] = zero;
+        return;
+    }
+    const double2* D = dg + loff_[j] + sp + 1;   // interior diagonal
+    const double2* E = od + loff_[j] + sp + 1;   // E[i]: coupling i <-> i+1 (i = Lp-1: to sep p+1)
+    const double2 Es = od[loff_[j] + sp];        // separator p <-> first interior
+    double2 qv[L], cv[L];
+    bool bad = false;
+    double2 piv = D[0];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        if (i < Lp) {
+            if (i > 0) piv = cfms(E[i - 1], cv[i - 1], D[i]);
+            bad |= !cfinite(piv) || (piv.x == 0.0 && piv.y == 0.0);
+            qv[i] = crcp(piv);
+            cv[i] = (i < Lp - 1) ? cmul(E[i], qv[i]) : zero;
+        }
+    }
+    const double2 El = E[Lp - 1];
+    // spike a = T^{-1}(Es e_0): forward z_0 = Es, z_i = -c_{i-1} z_{i-1}
+    double2 za[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        if (i < Lp) za[i] = (i == 0) ? Es : cfms(cv[i - 1], za[i - 1], zero);
+    }
+    double2 anext = zero, bnext = zero, a0 = zero, b0 = zero, aL = zero, bL = zero;
+#pragma unroll
+    for (int i = L - 1; i >= 0; --i) {
+        if (i < Lp) {
+            double2 ai, bi;
+            if (i == Lp - 1) {
+                ai = cmul(qv[i], za[i]);
+                bi = cmul(qv[i], El);
+                aL = ai;
+                bL = bi;
+            } else {
+                ai = cfms(cv[i], anext, cmul(qv[i], za[i]));
+                bi = cfms(cv[i], bnext, zero);
+            }
+            anext = ai;
+            bnext = bi;
+            if (i == 0) {
+                a0 = ai;
+                b0 = bi;
+            }
+            F[(i * 4 + 0) * P + p] = qv[i];
+            F[(i * 4 + 1) * P + p] = cv[i];
+            F[(i * 4 + 2) * P + p] = ai;
+            F[(i * 4 + 3) * P + p] = bi;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) F[(i * 4 + k) * P + p] = zero;
+        }
+    }
+    double2* tp = tips + ((size_t)j * P + p) * 4;
+    tp[0] = a0;
+    tp[1] = b0;
+    tp[2] = aL;
+    tp[3] = bL;
+    if (bad) atomicOr(status, ST_SINGULAR);
+}
+
+// Reduced (separator) system and its PCR coefficients; one thread per subdomain.
+// Row ps: E_{s-1} v_{s-1} + D_s v_s + E_s v_{s+1} = f_s with the neighbouring
+// interiors eliminated through the chunk spikes:
+//   delta = D_s - E_{s-1} b^{ps-1}_last - E_s a^{ps}_first,
+//   lower = -E_{s-1} a^{ps-1}_last,  upper = -E_s b^{ps}_first,
+//   rhs   = f_s - E_{s-1} y^{ps-1}_last - E_s y^{ps}_first.
+// PCR (stride 2^k): alpha = -lower/delta_{p-st}, gamma = -upper/delta_{p+st}.
+__global__ void k_reduce_pcr(int N, int P, int levels, const int* __restrict__ loff_,
+                             const double2* __restrict__ dg, const double2* __restrict__ od,
+                             const int* __restrict__ sub_P, const int* __restrict__ sep_pos,
+                             const double2* __restrict__ tips, double2* __restrict__ sep,
+                             double2* __restrict__ pcr, double2* __restrict__ red,
+                             int* status) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int Pj = sub_P[j];
+    const int S = P + 1;
+    const double2 zero = make_double2(0.0, 0.0);
+    double2* lo = red + (size_t)(j * 6 + 0) * S;
+    double2* dd = red + (size_t)(j * 6 + 1) * S;
+    double2* up = red + (size_t)(j * 6 + 2) * S;
+    double2* lo2 = red + (size_t)(j * 6 + 3) * S;
+    double2* dd2 = red + (size_t)(j * 6 + 4) * S;
+    double2* up2 = red + (size_t)(j * 6 + 5) * S;
+    double2* sE_l = sep + (size_t)(j * 3 + 0) * S;
+    double2* sE_r = sep + (size_t)(j * 3 + 1) * S;
+    double2* sbinv = sep + (size_t)(j * 3 + 2) * S;
+    const double2* T = tips + (size_t)j * P * 4;
+    const int base = loff_[j];
+    for (int ps = 0; ps <= P; ++ps) {
+        if (ps <= Pj) {
+            const int s = sep_pos[j * S + ps];
+            double2 d = dg[base + s], l = zero, u = zero;
+            double2 EL = zero, ER = zero;
+            if (ps > 0) {
+                EL = od[base + s - 1];
+                d = cfms(EL, T[(ps - 1) * 4 + 3], d);
+                l = cmul(make_double2(-EL.x, -EL.y), T[(ps - 1) * 4 + 2]);
+            }
+            if (ps < Pj) {
+                ER = od[base + s];
+                d = cfms(ER, T[ps * 4 + 0], d);
+                u = cmul(make_double2(-ER.x, -ER.y), T[ps * 4 + 1]);
+            }
+            lo[ps] = l;
+            dd[ps] = d;
+            up[ps] = u;
+            sE_l[ps] = EL;
+            sE_r[ps] = ER;
+        } else {
+            lo[ps] = zero;
+            dd[ps] = make_double2(1.0, 0.0);
+            up[ps] = zero;
+            sE_l[ps] = zero;
+            sE_r[ps] = zero;
+        }
+    }
+    bool bad = false;
+    for (int k = 0; k < levels; ++k) {
+        const int st = 1 << k;
+        double2* al = pcr + ((size_t)(j * levels + k) * 2 + 0) * S;
+        double2* ga = pcr + ((size_t)(j * levels + k) * 2 + 1) * S;
+        for (int ps = 0; ps <= P; ++ps) {
+            double2 a = zero, g = zero, nl = zero, nu = zero, nd = dd[ps];
+            if (ps - st >= 0) {
+                const double2 r = crcp(dd[ps - st]);
+                a = cmul(make_double2(-lo[ps].x, -lo[ps].y), r);
+                nl = cmul(a, lo[ps - st]);
+                nd = cfma(a, up[ps - st], nd);
+            }
+            if (ps + st <= P) {
+                const double2 r = crcp(dd[ps + st]);
+                g = cmul(make_double2(-up[ps].x, -up[ps].y), r);
+                nu = cmul(g, up[ps + st]);
+                nd = cfma(g, lo[ps + st], nd);
+            }
+            al[ps] = a;
+            ga[ps] = g;
+            lo2[ps] = nl;
+            dd2[ps] = nd;
+            up2[ps] = nu;
+        }
+        double2* t;
+        t = lo; lo = lo2; lo2 = t;
+        t = dd; dd = dd2; dd2 = t;
+        t = up; up = up2; up2 = t;
+    }
+    for (int ps = 0; ps <= P; ++ps) {
+        const double2 d = dd[ps];
+        bad |= !cfinite(d) || (d.x == 0.0 && d.y == 0.0);
+        sbinv[ps] = crcp(d);
+    }
+    if (bad) atomicOr(status, ST_SINGULAR);
+}
+
+static int ilog2ceil(int v) {
+    int k = 0;
+    while ((1 << k) < v) ++k;
+    return k;
+}
+
+int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t) {
+    swr_factor_free(fs);
+    fs.L = L;
+    fs.P = P;
+    fs.levels = ilog2ceil(P + 1);
+    if (fs.levels < 1) fs.levels = 1;
+    const size_t S = P + 1;
+    bool ok = true;
+    ok &= cudaMalloc(&fs.sub_P, sizeof(int) * N) == cudaSuccess;
+    ok &= cudaMalloc(&fs.sep_pos, sizeof(int) * N * S) == cudaSuccess;
+    ok &= cudaMalloc(&fs.clen, (size_t)N * P) == cudaSuccess;
+    ok &= cudaMalloc(&fs.fac, sizeof(double2) * (size_t)N * L * 4 * P) == cudaSuccess;
+    ok &= cudaMalloc(&fs.tips, sizeof(double2) * (size_t)N * P * 4) == cudaSuccess;
+    ok &= cudaMalloc(&fs.sep, sizeof(double2) * (size_t)N * 3 * S) == cudaSuccess;
+    ok &= cudaMalloc(&fs.pcr, sizeof(double2) * (size_t)N * fs.levels * 2 * S) == cudaSuccess;
+    ok &= cudaMalloc(&fs.red, sizeof(double2) * (size_t)N * 6 * S) == cudaSuccess;
+    if (!ok) {
+        swr_factor_free(fs);
+        return -1;
+    }
+    return 0;
+}
+
+void swr_factor_free(FactorSet& fs) {
+    cudaFree(fs.sub_P);
+    cudaFree(fs.sep_pos);
+    cudaFree(fs.clen);
+    cudaFree(fs.fac);
+    cudaFree(fs.tips);
+    cudaFree(fs.sep);
+    cudaFree(fs.pcr);
+    cudaFree(fs.red);
+    fs = FactorSet();
+}
+
+int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
+                      const double2* od, int* status, cudaStream_t s) {
+    dim3 grid((fs.P + 127) / 128, N);
+    switch (fs.L) {
+        case 4:
+            k_factor_chunks<4><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
+                                                    fs.sep_pos, fs.clen, fs.fac, fs.tips, status);
+            break;
+        case 8:
+            k_factor_chunks<8><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
+                                                    fs.sep_pos, fs.clen, fs.fac, fs.tips, status);
+            break;
+        case 16:
+            k_factor_chunks<16><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
+                                                     fs.sep_pos, fs.clen, fs.fac, fs.tips, status);
+            break;
+        default:
+            return -2;
+    }
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    k_reduce_pcr<<<(N + 63) / 64, 64, 0, s>>>(N, fs.P, fs.levels, d_loff, dg, od, fs.sub_P,
+                                               fs.sep_pos, fs.tips, fs.sep, fs.pcr, fs.red, status);
+    swr_count_launch(2);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// The march kernel.
+// Threads: C == 1: thread tid -> system g = tid / P of the CTA's G systems, chunk
+// p = tid % P.  C > 1: one system per cluster, chunk p = rank * T + tid.
+// Thread p owns separator p; thread P-1 also owns separator P.
+// Shared memory (per CTA): separator values usep, PCR ping-pong dA/dB
+// ([T+G] each) and, per chunk, the first/last interior u and y ([T] each).
+// ---------------------------------------------------------------------------
+int swr_march_smem_bytes(int T, int G) { return (int)sizeof(double2) * (3 * (T + G) + 4 * T); }
+
+template <int L>
+__global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const MarchArgs a) {
+    extern __shared__ double2 sm[];
+    const int T = a.T, G = a.G, P = a.P, C = a.C, nt = a.nt, levels = a.levels;
+    const int S = T + G;
+    double2* usep = sm;
+    double2* dA = usep + S;
+    double2* dB = dA + S;
+    double2* ufst = dB + S;
+    double2* ulst = ufst + T;
+    double2* yfst = ulst + T;
+    double2* ylst = yfst + T;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (C > 1) ? (int)cl.block_rank() : 0;
+    const int tid = threadIdx.x;
+    int g, p, sidx;
+    if (C == 1) {
+        g = tid / P;
+        p = tid - g * P;
+        sidx = blockIdx.x * G + g;
+        if (g >= G) p = -1;
+    } else {
+        g = 0;
+        p = rank * T + tid;
+        sidx = blockIdx.x / C;
+        if (p >= P) p = -1;
+    }
+    const bool valid = (p >= 0) && (sidx < a.nsys);
+
+    auto SEP = [&](double2* arr, int ps) -> double2* {
+        if (C == 1) return arr + g * (P + 1) + ps;
+        const int home = min(ps / T, C - 1);
+        double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
+        return base + (ps - home * T);
+    };
+    auto CHK = [&](double2* arr, int pc) -> double2* {
+        if (C == 1) return arr + g * P + pc;
+        const int home = pc / T;
+        double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
+        return base + (pc - home * T);
+    };
+    auto SYNC = [&]() {
+        if (C == 1)
+            __syncthreads();
+        else
+            cl.sync();
+    };
+
+    const double2 zero = make_double2(0.0, 0.0);
+    MarchSys sy = {0, 0, -1, -1, -1, -1};
+    int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0;
+    if (valid) {
+        sy = a.sys[sidx];
+        j = sy.sub;
+        Pj = a.sub_P[j];
+        goff = a.sub_goff[j];
+        tcf = a.sub_tc[j];
+        Lp = a.clen[j * P + p];
+        sp = a.sep_pos[j * (P + 1) + p];
+    }
+    const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
+    const int nown = (valid && p == P - 1) ? 2 : (valid ? 1 : 0);
+    const double2* F = a.fac + (size_t)j * L * 4 * P + p;
+    const double2* sE_l = a.sep + (size_t)(j * 3 + 0) * (P + 1);
+    const double2* sE_r = a.sep + (size_t)(j * 3 + 1) * (P + 1);
+    const double2* sbinv = a.sep + (size_t)(j * 3 + 2) * (P + 1);
+    const double2* pcr = a.pcr + (size_t)j * levels * 2 * (P + 1);
+
+    double2 u[L], y[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        u[i] = (valid && i < Lp && !zero_u0) ? a.u0[goff + sp + 1 + i] : zero;
+        y[i] = zero;
+    }
+    for (int e = 0; e < nown; ++e) {
+        const int ps = (e == 0) ? p : P;
+        double2 v0 = zero;
+        if (ps <= Pj && !zero_u0) v0 = a.u0[goff + a.sep_pos[j * (P + 1) + ps]];
+        *SEP(usep, ps) = v0;
+    }
+    SYNC();
+
+    double2 lin = zero, rin = zero;
+    for (int t = 1; t <= nt; ++t) {
+        // ---- phase A: chunk right-hand sides and local LU solves -------------
+        if (valid && Lp > 0) {
+            const double2 uL = *SEP(usep, p), uR = *SEP(usep, p + 1);
+            double2 zprev = zero, cprev = zero, uf = zero, ul = zero;
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    const double2 left = (i == 0) ? uL : u[i - 1];
+                    double2 right;
+                    if (i + 1 < L)
+                        right = (i == Lp - 1) ? uR : u[i + 1];
+                    else
+                        right = uR;
+                    double2 f = make_double2(fma(4.0, u[i].x, left.x + right.x),
+                                             fma(4.0, u[i].y, left.y + right.y));
+                    const double2 z = (i == 0) ? f : cfms(cprev, zprev, f);
+                    y[i] = z;
+                    zprev = z;
+                    cprev = F[(i * 4 + 1) * P];
+                    if (i == 0) uf = u[i];
+                    if (i == Lp - 1) ul = u[i];
+                }
+            }
+            double2 ynext = zero, yf = zero, yl = zero;
+#pragma unroll
+            for (int i = L - 1; i >= 0; --i) {
+                if (i < Lp) {
+                    const double2 qi = F[(i * 4 + 0) * P];
+                    double2 yi = cmul(qi, y[i]);
+                    if (i != Lp - 1) yi = cfms(F[(i * 4 + 1) * P], ynext, yi);
+                    else yl = yi;
+                    y[i] = yi;
+                    ynext = yi;
+                }
+            }
+            yf = y[0];
+            *CHK(ufst, p) = uf;
+            *CHK(ulst, p) = ul;
+            *CHK(yfst, p) = yf;
+            *CHK(ylst, p) = yl;
+        }
+        SYNC();
+        // ---- phase B: reduced right-hand sides at the separators -------------
+        for (int e = 0; e < nown; ++e) {
+            const int ps = (e == 0) ? p : P;
+            double2 d = zero;
+            if (ps <= Pj) {
+                const double2 us = *SEP(usep, ps);
+                const bool le = (ps == 0), re = (ps == Pj);
+                const double2 um = le ? zero : *CHK(ulst, ps - 1);
+                const double2 up = re ? zero : *CHK(ufst, ps);
+                double2 f;
+                if (le)
+                    f = make_double2(fma(2.0, us.x, up.x), fma(2.0, us.y, up.y));
+                else if (re)
+                    f = make_double2(fma(2.0, us.x, um.x), fma(2.0, us.y, um.y));
+                else
+                    f = make_double2(fma(4.0, us.x, um.x + up.x), fma(4.0, us.y, um.y + up.y));
+                if (le && (tcf & 1)) {
+                    if (sy.flags & SYS_IMP_L)
+                        lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                    else
+                        lin = (sy.in_l >= 0) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
+                    f = cfms(lin, a.inv_ik, f);
+                }
+                if (re && (tcf & 2)) {
+                    if (sy.flags & SYS_IMP_R)
+                        rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                    else
+                        rin = (sy.in_r >= 0) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
+                    f = cfms(rin, a.inv_ik, f);
+                }
+                d = f;
+                if (!le) d = cfms(sE_l[ps], *CHK(ylst, ps - 1), d);
+                if (!re) d = cfms(sE_r[ps], *CHK(yfst, ps), d);
+            }
+            *SEP(dA, ps) = d;
+        }
+        SYNC();
+        // ---- phase C: PCR on the separators (coefficients precomputed) -------
+        double2* src = dA;
+        double2* dst = dB;
+        for (int k = 0; k < levels; ++k) {
+            const int st = 1 << k;
+            const double2* al = pcr + (size_t)(k * 2 + 0) * (P + 1);
+            const double2* ga = pcr + (size_t)(k * 2 + 1) * (P + 1);
+            for (int e = 0; e < nown; ++e) {
+                const int ps = (e == 0) ? p : P;
+                double2 dd = *SEP(src, ps);
+                if (ps - st >= 0) dd = cfma(al[ps], *SEP(src, ps - st), dd);
+                if (ps + st <= P) dd = cfma(ga[ps], *SEP(src, ps + st), dd);
+                if (k == levels - 1) dd = cmul(dd, sbinv[ps]);
+                *SEP(dst, ps) = dd;
+            }
+            SYNC();
+            double2* tmp = src;
+            src = dst;
+            dst = tmp;
+        }
+        // ---- phase D: spike correction, CN update, fluxes ---------------------
+        if (valid && Lp > 0) {
+            const double2 vL = *SEP(src, p), vR = *SEP(src, p + 1);
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    double2 v = cfms(F[(i * 4 + 2) * P], vL, y[i]);
+                    v = cfms(F[(i * 4 + 3) * P], vR, v);
+                    u[i] = make_double2(fma(2.0, v.x, -u[i].x), fma(2.0, v.y, -u[i].y));
+                }
+            }
+        }
+        for (int e = 0; e < nown; ++e) {
+            const int ps = (e == 0) ? p : P;
+            if (ps <= Pj) {
+                const double2 v = *SEP(src, ps);
+                double2* us = SEP(usep, ps);
+                const double2 uo = *us;
+                *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
+                if (ps == 0) {
+                    if ((tcf & 1) && sy.out_a >= 0)
+                        a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
+                    if (sy.flags & SYS_TRACE) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
+                }
+                if (ps == Pj) {
+                    if ((tcf & 2) && sy.out_b >= 0)
+                        a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
+                    if (sy.flags & SYS_TRACE) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
+                }
+            }
+        }
+        SYNC();
+    }
+    // ---- final state ----------------------------------------------------------
+    bool bad = false;
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < Lp) bad |= !cfinite(u[i]);
+        if (sy.flags & SYS_WRITE_UT) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.uT[goff + sp + 1 + i] = u[i];
+        }
+        for (int e = 0; e < nown; ++e) {
+            const int ps = (e == 0) ? p : P;
+            if (ps <= Pj) {
+                const double2 us = *SEP(usep, ps);
+                bad |= !cfinite(us);
+                const int node = a.sep_pos[j * (P + 1) + ps];
+                // the interface node belongs to the left subdomain
+                if ((sy.flags & SYS_WRITE_UT) && (node > 0 || j == 0)) a.uT[goff + node] = us;
+            }
+        }
+    }
+    if (bad) atomicOr(a.status, ST_NONFINITE);
+    // keep remote shared memory alive until every CTA of the cluster is done
+    if (C > 1) cl.sync();
+}
+
+template <int L>
+static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s) {
+    const int smem = swr_march_smem_bytes(a.T, a.G);
+    auto kern = k_march_static<L>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -1;
+    if (a.C > 8 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return -1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ngroups * a.C);
+    cfg.blockDim = dim3(a.T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = a.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    swr_count_launch(1);
+    return cudaLaunchKernelEx(&cfg, kern, a) == cudaSuccess ? 0 : -1;
+}
+
+int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t s) {
+    a.P = fs.P;
+    a.levels = fs.levels;
+    a.sub_P = fs.sub_P;
+    a.sep_pos = fs.sep_pos;
+    a.clen = fs.clen;
+    a.fac = fs.fac;
+    a.sep = fs.sep;
+    a.pcr = fs.pcr;
+    switch (fs.L) {
+        case 4: return launch_march_t<4>(a, ngroups, s);
+        case 8: return launch_march_t<8>(a, ngroups, s);
+        case 16: return launch_march_t<16>(a, ngroups, s);
+        default: return -2;
+    }
+}

@@ -87,6 +87,10 @@ typedef struct swr_desc {
     int32_t nl_maxit;           /* nonlinear inner fixed point cap (default 50)        */
     double nl_tol;              /* inner stop: max|dz| <= nl_tol max(1,max|z|) (1e-13) */
     double nl_coef;             /* f(u) = nl_coef |u|^2 (default 1 if 0)               */
+    int32_t pc_sweeps;          /* block-Jacobi sweeps resolving the same-step coupling  */
+                                /* of neighbouring interfaces in the causal substitution */
+                                /* (CAUSAL / ZERO_POTENTIAL preconditioners), 0..16;    */
+                                /* < 0: chosen by the library                           */
 } swr_desc;
 
 typedef struct swr_info {

@@ -560,6 +560,7 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     if (p->d.nl_maxit <= 0) p->d.nl_maxit = 50;
     if (!(p->d.nl_tol > 0.0)) p->d.nl_tol = 1e-13;
     if (p->d.nl_coef == 0.0) p->d.nl_coef = 1.0;
+    p->causal_sweeps = (d->pc_sweeps >= 0) ? std::min(d->pc_sweeps, 16) : 0;
     p->s = (cudaStream_t)stream;
     p->N = d->nsub;
     p->nx = d->nx;

@@ -34,6 +34,7 @@ class swr_desc(ctypes.Structure):
         ("solver", ctypes.c_int32), ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
         ("tol_abs", ctypes.c_double), ("precond", ctypes.c_int32), ("nl_maxit", ctypes.c_int32),
         ("nl_tol", ctypes.c_double), ("nl_coef", ctypes.c_double),
+        ("pc_sweeps", ctypes.c_int32),
     ]
 
 
@@ -134,7 +135,7 @@ class Plan:
     def __init__(self, *, nx, a0, b0, nt, dt, nsub, node_off=None, vkind=SWR_V_STATIC,
                  tc=SWR_TC_ROBIN, p=0j, solver=SWR_SOLVER_GMRES, restart=30, maxit=2000,
                  tol_abs=1e-10, precond=SWR_PC_NONE, nl_maxit=50, nl_tol=1e-13, nl_coef=1.0,
-                 stream=None):
+                 pc_sweeps=-1, stream=None):
         d = swr_desc()
         d.nx, d.a0, d.b0, d.nt, d.dt, d.nsub = nx, a0, b0, nt, dt, nsub
         self._off = None
@@ -146,6 +147,7 @@ class Plan:
         d.tc_re, d.tc_im = complex(p).real, complex(p).imag
         d.solver, d.restart, d.maxit, d.tol_abs, d.precond = solver, restart, maxit, tol_abs, precond
         d.nl_maxit, d.nl_tol, d.nl_coef = nl_maxit, nl_tol, nl_coef
+        d.pc_sweeps = pc_sweeps
         self.desc = d
         self.nx, self.nt, self.nsub, self.nblk, self.vkind = nx, nt, nsub, 2 * nsub - 2, vkind
         if stream is None:

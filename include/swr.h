@@ -182,6 +182,36 @@ void swr_destroy(swr_plan_t p);
  * Synchronises the plan's stream. */
 swr_status swr_get_stats(swr_plan_t p, swr_stats *out, int32_t reset);
 
+/* x = (I - L)^{-1} y by the causal block forward substitution of the CAUSAL
+ * preconditioner, WITHOUT allocating device memory.  The paper has no
+ * counterpart: this is a deployment variant of swr_apply_precond.
+ *
+ * For callers that cannot allocate: applications that reserve all device memory
+ * up front in their own pool, or latency-critical loops that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree imply.  The caller provides
+ * inputs and outputs; the substitution's working arrays live in a fixed
+ * library-owned device array (about 1.1 MB, held on every GPU that loads the
+ * library until the process exits).
+ *   nsub:   N, 2 <= N <= 1024 (larger N: SWR_ERR_ARG; the array is sized for 1024)
+ *   nt:     time steps, >= 1
+ *   sweeps: block-Jacobi sweeps for the same-step coupling of neighbouring
+ *           interfaces, 0..16 (swr_desc.pc_sweeps of a plan)
+ *   cols:   cplx[4 N nt] Toeplitz first columns as returned by swr_get_interface
+ *   y, x:   cplx[(2N-2) nt], distinct; x is overwritten
+ *   stream: cudaStream_t (as void*) the work is enqueued on; the call returns
+ *           without synchronising.
+ * The first call on a device looks up the device address of the library array
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  All calls share the one array: calls that overlap on the
+ * GPU (other streams, other threads) race and give wrong results.  Nothing in
+ * the array needs clearing between calls; every entry read is written earlier
+ * in the same call.
+ * Errors: SWR_ERR_ARG (sizes, sweeps, NULL or aliased pointers),
+ * SWR_ERR_UNSUPPORTED (device ordinal >= 64), SWR_ERR_CUDA. */
+swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t sweeps,
+                                    const double *cols, const double *y, double *x,
+                                    void *stream);
+
 /* Number of CUDA kernels this library has launched in this process, over all
  * plans (a monotonically increasing counter; host-only, no device work). */
 int64_t swr_kernel_launch_count(void);

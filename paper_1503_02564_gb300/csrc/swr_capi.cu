@@ -619,7 +619,7 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     if (!st) st = dalloc(&p->d_u0, p->nx);
     if (!st) st = dalloc(&p->d_iface, nb + (size_t)4 * p->N * p->nt);
     if (!st) st = dalloc(&p->d_lag0, 4 * p->N);
-    if (!st) st = dalloc(&p->d_hist, (size_t)p->nblk * 32);
+    if (!st) st = dalloc(&p->d_hist, (size_t)p->nblk * SWR_CAUSAL_TILE);
     if (!st) st = dalloc(&p->d_gtmp, nb);
     if (!st) st = dalloc(&p->d_gtmp2, nb);
     if (!st) st = dalloc(&p->d_trace, (size_t)p->N * 2 * p->nt);

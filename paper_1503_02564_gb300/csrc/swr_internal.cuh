@@ -103,6 +103,10 @@ struct MarchArgs {
     int* status;
 };
 
+// Time-tile length of the causal block forward substitution (history buffer is
+// (2N-2) x SWR_CAUSAL_TILE complex values).
+#define SWR_CAUSAL_TILE 32
+
 // Process-wide count of kernels launched by this library (swr_capi.cu).
 void swr_count_launch(int n);
 

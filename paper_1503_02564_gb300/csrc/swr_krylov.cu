@@ -437,7 +437,7 @@ __global__ void k_causal_near(int N, int nt, int t0, int b, int sweeps,
 
 int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, const double2* y,
                       double2* x, int sweeps, double2* hist, cudaStream_t s) {
-    const int b = 32;
+    const int b = SWR_CAUSAL_TILE;
     const int nif = N - 1;
     int tpb = 64;
     int C = (nif + tpb - 1) / tpb;

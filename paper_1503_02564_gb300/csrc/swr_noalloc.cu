@@ -1,0 +1,77 @@
+// swr_causal_solve_noalloc: the causal block forward substitution x = (I - L)^{-1} y
+// for callers that cannot allocate device memory.
+//
+// Who needs it: code that must not call cudaMalloc once it is running, for
+// example a solver embedded in a host application that reserves all device
+// memory up front with its own pool, or a latency-critical loop where the
+// implicit device synchronisation of cudaMalloc/cudaFree is not acceptable.
+// Such callers own x, y and the Toeplitz first columns, but have nowhere to put
+// the substitution's working arrays.  This entry point keeps them in a
+// fixed-size array in the library's own device memory instead.
+//
+// The scratch is a file-scope __device__ array: every GPU that loads the
+// library holds it (about 1.1 MB) until the process exits.  Host code must not
+// hand the array's name to a kernel: on the host it is only a stand-in symbol.
+// Its device address is looked up with cudaGetSymbolAddress once per device,
+// with that device current, the first time the entry point runs there.
+#include <mutex>
+
+#include "swr_internal.cuh"
+
+namespace {
+
+constexpr int kNoallocMaxSub = 1024;     // largest supported number of subdomains N
+constexpr int kNoallocMaxDevices = 64;
+constexpr size_t kHistElems = (size_t)(2 * kNoallocMaxSub - 2) * SWR_CAUSAL_TILE;
+constexpr size_t kLag0Elems = (size_t)4 * kNoallocMaxSub;
+
+std::mutex g_setup_mutex;
+double2* g_scratch_addr[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+// history tile (2N-2 blocks x tile) followed by the 2x2 lag-0 inverses (4 per interface)
+static __device__ __align__(256) double2 g_noalloc_scratch[kHistElems + kLag0Elems];
+
+extern "C" swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t sweeps,
+                                               const double* cols, const double* y, double* x,
+                                               void* stream) {
+    if (nsub < 2 || nsub > kNoallocMaxSub || nt < 1 || sweeps < 0 || sweeps > 16 || !cols || !y ||
+        !x || x == y)
+        return SWR_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SWR_ERR_CUDA;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return SWR_ERR_UNSUPPORTED;
+    double2* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_scratch_addr[dev]) {
+            void* addr = nullptr;
+            if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) {
+                cudaGetLastError();
+                return SWR_ERR_CUDA;
+            }
+            g_scratch_addr[dev] = static_cast<double2*>(addr);
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    double2* hist = scratch;
+    double2* lag0 = scratch + kHistElems;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const double2* c = reinterpret_cast<const double2*>(cols);
+    // Every scratch entry the substitution reads is written earlier in the same
+    // call (lag-0 inverses first, each history tile before its use), so nothing
+    // has to be cleared between calls.
+    if (swr_launch_lag0_setup(nsub, nt, c, lag0, s) != 0) {
+        cudaGetLastError();
+        return SWR_ERR_CUDA;
+    }
+    const int rc = swr_launch_causal(nsub, nt, c, lag0, reinterpret_cast<const double2*>(y),
+                                     reinterpret_cast<double2*>(x), sweeps, hist, s);
+    if (rc == -2) return SWR_ERR_UNSUPPORTED;
+    if (rc != 0) {
+        cudaGetLastError();
+        return SWR_ERR_CUDA;
+    }
+    return SWR_OK;
+}

@@ -89,6 +89,8 @@ def lib():
         L.swr_apply_precond.argtypes = [vp, dp, dp]
         L.swr_adjoint.argtypes = [vp, dp, dp, ctypes.c_int32]
         L.swr_get_stats.argtypes = [vp, ctypes.POINTER(swr_stats), ctypes.c_int32]
+        L.swr_causal_solve_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                               dp, dp, dp, vp]
         L.swr_destroy.argtypes = [vp]
         L.swr_destroy.restype = None
         L.swr_kernel_launch_count.argtypes = []
@@ -97,7 +99,7 @@ def lib():
         L.swr_status_string.restype = ctypes.c_char_p
         for f in ("swr_plan", "swr_build_interface", "swr_solve", "swr_apply_R",
                   "swr_apply_interface", "swr_get_interface", "swr_apply_precond", "swr_adjoint",
-                  "swr_get_stats"):
+                  "swr_get_stats", "swr_causal_solve_noalloc"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -127,6 +129,18 @@ def _check(st, where, allow=()):
     if st != SWR_OK and st not in allow:
         raise SWRError(st, where)
     return st
+
+
+def swr_causal_solve_noalloc(nsub, nt, sweeps, cols, y, x, stream=None):
+    """x = (I - L)^{-1} y (causal substitution) without any device allocation;
+    for callers that cannot allocate device memory (see include/swr.h)."""
+    n = (2 * nsub - 2) * nt
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return lib().swr_causal_solve_noalloc(
+        int(nsub), int(nt), int(sweeps), _ptr(cols, torch.complex128, 4 * nsub * nt, "cols"),
+        _ptr(y, torch.complex128, n, "y"), _ptr(x, torch.complex128, n, "x"),
+        ctypes.c_void_p(stream.cuda_stream))
 
 
 class Plan:

@@ -190,7 +190,7 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats *out, int32_t reset);
  * up front in their own pool, or latency-critical loops that cannot afford the
  * device-wide synchronisation cudaMalloc/cudaFree imply.  The caller provides
  * inputs and outputs; the substitution's working arrays live in a fixed
- * library-owned device array (about 1.1 MB, held on every GPU that loads the
+ * library-owned device array (about 135 KB, held on every GPU that loads the
  * library until the process exits).
  *   nsub:   N, 2 <= N <= 1024 (larger N: SWR_ERR_ARG; the array is sized for 1024)
  *   nt:     time steps, >= 1
@@ -198,16 +198,18 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats *out, int32_t reset);
  *           interfaces, 0..16 (swr_desc.pc_sweeps of a plan)
  *   cols:   cplx[4 N nt] Toeplitz first columns as returned by swr_get_interface
  *   y, x:   cplx[(2N-2) nt], distinct; x is overwritten
- *   stream: cudaStream_t (as void*) the work is enqueued on; the call returns
- *           without synchronising.
+ *   stream: cudaStream_t (as void*) the work is enqueued on; the call
+ *           synchronises it at the end to report a bounded-wait timeout.
  * The first call on a device looks up the device address of the library array
  * (cudaGetSymbolAddress, with that device current); make that first call before
  * any stream capture.  All calls share the one array: calls that overlap on the
- * GPU (other streams, other threads) race and give wrong results.  Nothing in
- * the array needs clearing between calls; every entry read is written earlier
- * in the same call.
+ * GPU (other streams, other threads) race and give wrong results.  Each call
+ * clears the array's progress counters and status word; the other entries are
+ * written before they are read.
  * Errors: SWR_ERR_ARG (sizes, sweeps, NULL or aliased pointers),
- * SWR_ERR_UNSUPPORTED (device ordinal >= 64), SWR_ERR_CUDA. */
+ * SWR_ERR_UNSUPPORTED (device ordinal >= 64, or more interfaces than can be
+ * resident at once), SWR_ERR_TIMEOUT (a bounded wait of the substitution gave
+ * up; x is invalid), SWR_ERR_CUDA. */
 swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t sweeps,
                                     const double *cols, const double *y, double *x,
                                     void *stream);

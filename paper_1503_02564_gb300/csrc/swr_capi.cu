@@ -49,15 +49,15 @@ struct swr_plan_s {
     int *d_n = nullptr, *d_goff = nullptr, *d_loff = nullptr, *d_tc = nullptr;
     double2 *d_dg = nullptr, *d_od = nullptr;       // A - B for V (static) or V0
     double2 *d_dg0 = nullptr, *d_od0 = nullptr;     // A - B for V = 0
-    FactorSet fs, fs0;
-    int L = 8;
+    FactorSet fsL[3], fs0L[3];     // chunked factorisations for L = 4, 8, 16 (V and V = 0)
+    int forceL = 0;                // SWR_CHUNK_L override (0: chosen per launch)
     double2* d_u0 = nullptr;
     double* d_V = nullptr;
     double2* d_iface = nullptr;    // d (nblk blocks) followed by cols (4N blocks)
     double2* d_iface0 = nullptr;   // L_0: zero d (nblk blocks) followed by cols (4N blocks)
     double2* d_lag0 = nullptr;     // (N-1) x 4, for L
     double2* d_lag0_0 = nullptr;   // for L_0
-    double2* d_hist = nullptr;     // nblk x 32
+    double2* d_hist = nullptr;     // scratch of the causal substitution
     double2* d_gtmp = nullptr;     // nblk x nt scratch
     double2* d_gtmp2 = nullptr;
     double2* d_trace = nullptr;    // N x 2 x nt
@@ -146,40 +146,79 @@ swr_status read_status(swr_plan_t p) {
     return SWR_OK;
 }
 
-// Launch geometry of a march over nsys systems of P chunks.
-void march_config(const swr_plan_t p, const FactorSet& fs, int nsys, int& C, int& G, int& T,
-                  int& ngroups) {
-    const int P = fs.P;
-    const int TMAX = (fs.L == 16) ? 256 : 384;
+// Launch geometry of a march over nsys systems.  Every system has P+1 threads
+// (P chunks of <= L interior nodes, one separator each).  The chunk length L is
+// the largest of 16, 8, 4 that still gives about four full warps per SM (the
+// FP64 pipe saturates with one warp per SM sub-partition); systems are packed G
+// to a CTA so that the CTAs fit in one wave, and a system too long for one CTA
+// (or too few systems for the SMs) is spread over a thread-block cluster.
+struct MarchCfg {
+    int L = 8, C = 1, G = 1, T = 32, ngroups = 1;
+};
+
+inline int chunks_for(int nmax, int L) { return (nmax - 1 + L) / (L + 1); }
+
+MarchCfg march_config(const swr_plan_t p, int nsys) {
+    MarchCfg c;
     const int nsm = p->nsm;
-    if (P <= TMAX) {
-        C = 1;
-        G = std::max(1, std::min(TMAX / P, nsys / nsm));
-        if (G == 1 && nsys * 2 <= nsm && P >= 128) {
-            // few long systems: spread each over a cluster to reach more SMs
-            C = std::min(8, std::min(nsm / std::max(nsys, 1), P / 64));
-            if (C < 2) C = 1;
+    const long long want = (long long)nsm * 4 * 32;
+    const int cand[3] = {16, 8, 4};
+    int L = 4;
+    if (p->forceL) {
+        L = p->forceL;
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            const long long tps = chunks_for(p->nmax, cand[k]) + 1;
+            if (tps * nsys >= want || cand[k] == 4) {
+                L = cand[k];
+                break;
+            }
+        }
+    }
+    c.L = L;
+    const int P = chunks_for(p->nmax, L);
+    const int tps = P + 1;
+    const int TMAX = (L == 16) ? 256 : 384;
+    if (tps <= TMAX) {
+        c.C = 1;
+        c.G = std::max(1, std::min(TMAX / tps, (nsys + nsm - 1) / nsm));
+        const int nctas = (nsys + c.G - 1) / c.G;
+        if (c.G == 1 && nctas * 2 <= nsm) {
+            // few systems: spread each over a cluster, keeping >= 64 threads per CTA
+            int C = std::min(16, nsm / std::max(nsys, 1));
+            C = std::min(C, tps / 64);
+            if (C >= 2) c.C = C;
         }
     } else {
-        C = (P + TMAX - 1) / TMAX;
-        G = 1;
+        c.C = (tps + TMAX - 1) / TMAX;
+        c.G = 1;
+        if (nsys * c.C * 2 <= nsm) {
+            int C = std::min(16, nsm / std::max(nsys, 1));
+            C = std::min(C, tps / 64);
+            c.C = std::max(c.C, C);
+        }
     }
-    if (C == 1) {
-        T = ((G * P + 31) / 32) * 32;
-        ngroups = (nsys + G - 1) / G;
+    if (c.C == 1) {
+        c.T = ((c.G * tps + 31) / 32) * 32;
+        c.ngroups = (nsys + c.G - 1) / c.G;
     } else {
-        T = (((P + C - 1) / C + 31) / 32) * 32;
-        ngroups = nsys;
+        c.T = (((tps + c.C - 1) / c.C + 31) / 32) * 32;
+        c.ngroups = nsys;
     }
+    return c;
 }
 
-swr_status run_march(swr_plan_t p, const FactorSet& fs, const MarchSys* d_sys, int nsys,
+inline int lidx(int L) { return L == 4 ? 0 : (L == 8 ? 1 : 2); }
+
+swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, int nsys,
                      const double2* gin, double2* gout, double2* uT, double2* trace,
                      const double2* u0, long long work) {
     MarchArgs a{};
-    int C, G, T, ng;
-    march_config(p, fs, nsys, C, G, T, ng);
+    const MarchCfg cfg = march_config(p, nsys);
+    const int C = cfg.C, G = cfg.G, T = cfg.T, ng = cfg.ngroups;
     if (C > 16) return SWR_ERR_UNSUPPORTED;
+    const FactorSet& fs = zero_potential ? p->fs0L[lidx(cfg.L)] : p->fsL[lidx(cfg.L)];
+    if (fs.L != cfg.L) return SWR_ERR_STATE;
     a.nt = p->nt;
     a.C = C;
     a.G = G;
@@ -207,28 +246,23 @@ swr_status run_march(swr_plan_t p, const FactorSet& fs, const MarchSys* d_sys, i
     return SWR_OK;
 }
 
-// Choose the chunk length from the number of right-hand sides of the build.
-int choose_L(int nmax, int nsys, int nsm) {
-    const long long want = (long long)nsm * 4 * 32 * 2;   // about 8 full warps per SM
-    for (int L : {16, 8}) {
-        const int P = (nmax - 1 + L) / (L + 1);
-        if ((long long)P * nsys >= want) return L;
-    }
-    return 4;
-}
-
-swr_status factor_for(swr_plan_t p, FactorSet& fs, const double* V, double2* dg, double2* od) {
-    swr_launch_assemble_static(V, p->N, p->d_n, p->d_goff, p->d_loff, p->d_tc, p->nmax, p->h,
-                               p->d.dt, p->sigma0, p->inv_ik, dg, od, p->s);
-    CK(cudaGetLastError());
-    if (fs.L != p->L) {
-        const int P = (p->nmax - 1 + p->L) / (p->L + 1);
-        if (swr_factor_alloc(fs, p->N, p->L, P, p->s) != 0) return SWR_ERR_NOMEM;
+// Assemble A - B for V (NULL: V = 0) and factor it for chunk length L.
+swr_status factor_for(swr_plan_t p, FactorSet& fs, int L, const double* V, double2* dg,
+                      double2* od) {
+    if (fs.L != L) {
+        if (swr_factor_alloc(fs, p->N, L, chunks_for(p->nmax, L), p->s) != 0) return SWR_ERR_NOMEM;
     }
     if (swr_launch_factor(fs, p->N, p->d_n, p->d_loff, dg, od, p->d_status, p->s) != 0) {
         cudaGetLastError();
         return SWR_ERR_CUDA;
     }
+    return SWR_OK;
+}
+
+swr_status assemble(swr_plan_t p, const double* V, double2* dg, double2* od) {
+    swr_launch_assemble_static(V, p->N, p->d_n, p->d_goff, p->d_loff, p->d_tc, p->nmax, p->h,
+                               p->d.dt, p->sigma0, p->inv_ik, dg, od, p->s);
+    CK(cudaGetLastError());
     return SWR_OK;
 }
 
@@ -332,7 +366,7 @@ swr_status apply_A(swr_plan_t p, const double2* x, double2* y) {
         return rc ? SWR_ERR_UNSUPPORTED : SWR_OK;
     }
     // matrix-free: y = x - R x + d   (Algorithm 2)
-    swr_status st = run_march(p, p->fs, p->d_sys_R, p->N, x, y, nullptr, nullptr, p->d_u0, p->work_R);
+    swr_status st = run_march(p, false, p->d_sys_R, p->N, x, y, nullptr, nullptr, p->d_u0, p->work_R);
     if (st) return st;
     if (swr_launch_axpby(y, x, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s)) return SWR_ERR_CUDA;
     if (swr_launch_axpby(y, p->d_iface, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s))
@@ -359,7 +393,8 @@ swr_status apply_M(swr_plan_t p, const double2* y, double2* x) {
         return SWR_ERR_STATE;
     }
     const int pi = prof_begin(p, 2, 0);
-    int rc = swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps, p->d_hist, p->s);
+    int rc = swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps, p->d_hist,
+                               p->d_status, p->s);
     prof_end(p, pi);
     if (rc == -2) return SWR_ERR_UNSUPPORTED;
     if (rc) return SWR_ERR_CUDA;
@@ -467,7 +502,7 @@ swr_status fixed_point(swr_plan_t p, double2* g, bool g_init, bool classical, sw
     int it = 0;
     while (it < p->d.maxit) {
         if (classical) {
-            if ((st = run_march(p, p->fs, p->d_sys_R, p->N, g, w.z, nullptr, nullptr, p->d_u0,
+            if ((st = run_march(p, false, p->d_sys_R, p->N, g, w.z, nullptr, nullptr, p->d_u0,
                                 p->work_R)))
                 return st;
         } else {
@@ -520,8 +555,10 @@ void swr_destroy(swr_plan_t p) {
     cudaStreamSynchronize(p->s);
     cudaFree(p->d_n); cudaFree(p->d_goff); cudaFree(p->d_loff); cudaFree(p->d_tc);
     cudaFree(p->d_dg); cudaFree(p->d_od); cudaFree(p->d_dg0); cudaFree(p->d_od0);
-    swr_factor_free(p->fs);
-    swr_factor_free(p->fs0);
+    for (int k = 0; k < 3; ++k) {
+        swr_factor_free(p->fsL[k]);
+        swr_factor_free(p->fs0L[k]);
+    }
     cudaFree(p->d_u0); cudaFree(p->d_V); cudaFree(p->d_iface); cudaFree(p->d_iface0);
     cudaFree(p->d_lag0); cudaFree(p->d_lag0_0); cudaFree(p->d_hist); cudaFree(p->d_gtmp);
     cudaFree(p->d_gtmp2); cudaFree(p->d_trace);
@@ -602,11 +639,9 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (p->nsm <= 0) p->nsm = 152;
-    const int nsys_build = 3 * p->N - 2;
-    p->L = choose_L(nmax, nsys_build, p->nsm);
     if (const char* e = getenv("SWR_CHUNK_L")) {   // tuning override: 4, 8 or 16
         const int v = atoi(e);
-        if (v == 4 || v == 8 || v == 16) p->L = v;
+        if (v == 4 || v == 8 || v == 16) p->forceL = v;
     }
     swr_status st = SWR_OK;
     const size_t nb = (size_t)p->nblk * p->nt;
@@ -619,7 +654,7 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     if (!st) st = dalloc(&p->d_u0, p->nx);
     if (!st) st = dalloc(&p->d_iface, nb + (size_t)4 * p->N * p->nt);
     if (!st) st = dalloc(&p->d_lag0, 4 * p->N);
-    if (!st) st = dalloc(&p->d_hist, (size_t)p->nblk * SWR_CAUSAL_TILE);
+    if (!st) st = dalloc(reinterpret_cast<char**>(&p->d_hist), swr_causal_scratch_bytes(p->N));
     if (!st) st = dalloc(&p->d_gtmp, nb);
     if (!st) st = dalloc(&p->d_gtmp2, nb);
     if (!st) st = dalloc(&p->d_trace, (size_t)p->N * 2 * p->nt);
@@ -680,21 +715,26 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
     CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
     CK(cudaMemcpyAsync(p->d_V, V, sizeof(double) * nV, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(p->d_u0, u0, sizeof(double2) * p->nx, cudaMemcpyDeviceToDevice, s));
-    swr_status st = factor_for(p, p->fs, p->d_V, p->d_dg, p->d_od);
+    swr_status st = assemble(p, p->d_V, p->d_dg, p->d_od);
     if (st) return st;
+    // factorisations for the chunk lengths the marches of this plan will use
+    const int Lb = march_config(p, p->nsys_build).L, La = march_config(p, p->N).L;
+    if ((st = factor_for(p, p->fsL[lidx(Lb)], Lb, p->d_V, p->d_dg, p->d_od))) return st;
+    if (La != Lb && (st = factor_for(p, p->fsL[lidx(La)], La, p->d_V, p->d_dg, p->d_od))) return st;
     CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
     // Algorithm 3, step 1: d and the first columns, 3 marches per interior subdomain
-    st = run_march(p, p->fs, p->d_sys_build, p->nsys_build, nullptr, p->d_iface, nullptr, nullptr,
+    st = run_march(p, false, p->d_sys_build, p->nsys_build, nullptr, p->d_iface, nullptr, nullptr,
                    p->d_u0, p->work_build);
     if (st) return st;
     const double2* cols = p->d_iface + nb;
     if (swr_launch_lag0_setup(p->N, p->nt, cols, p->d_lag0, s)) return SWR_ERR_CUDA;
     if (p->d.precond == SWR_PC_ZERO_POTENTIAL) {
-        st = factor_for(p, p->fs0, nullptr, p->d_dg0, p->d_od0);
-        if (st) return st;
+        if ((st = assemble(p, nullptr, p->d_dg0, p->d_od0))) return st;
+        const int L0 = march_config(p, p->nsys_build - p->N).L;
+        if ((st = factor_for(p, p->fs0L[lidx(L0)], L0, nullptr, p->d_dg0, p->d_od0))) return st;
         CK(cudaMemsetAsync(p->d_iface0, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
         // impulse marches only (the first N systems of the build list are the d marches)
-        st = run_march(p, p->fs0, p->d_sys_build + p->N, p->nsys_build - p->N, nullptr,
+        st = run_march(p, true, p->d_sys_build + p->N, p->nsys_build - p->N, nullptr,
                        p->d_iface0, nullptr, nullptr, p->d_u0, p->work_build_imp);
         if (st) return st;
         if (swr_launch_lag0_setup(p->N, p->nt, p->d_iface0 + nb, p->d_lag0_0, s)) return SWR_ERR_CUDA;
@@ -727,7 +767,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     CK(cudaEventRecord(p->ev[2], s));
     // final march (last step of Algorithms 1-3)
     double2* uT = uT_ ? reinterpret_cast<double2*>(uT_) : nullptr;
-    swr_status st2 = run_march(p, p->fs, p->d_sys_final, p->N, g, p->d_gtmp, uT, p->d_trace,
+    swr_status st2 = run_march(p, false, p->d_sys_final, p->N, g, p->d_gtmp, uT, p->d_trace,
                                p->d_u0, p->work_R);
     if (st2) return st2;
     if (swr_launch_jump(p->d_trace, p->d_sys_final, p->N, p->nt, p->d_scal, s)) return SWR_ERR_CUDA;
@@ -759,7 +799,7 @@ swr_status swr_apply_R(swr_plan_t p, const double* g_in, double* g_out) {
     if (!p || !g_in || !g_out || g_in == g_out) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     CK(cudaMemsetAsync(g_out, 0, sizeof(double2) * (size_t)p->nblk * p->nt, p->s));
-    swr_status st = run_march(p, p->fs, p->d_sys_R, p->N, reinterpret_cast<const double2*>(g_in),
+    swr_status st = run_march(p, false, p->d_sys_R, p->N, reinterpret_cast<const double2*>(g_in),
                               reinterpret_cast<double2*>(g_out), nullptr, nullptr, p->d_u0,
                               p->work_R);
     if (st) return st;

@@ -103,10 +103,6 @@ struct MarchArgs {
     int* status;
 };
 
-// Time-tile length of the causal block forward substitution (history buffer is
-// (2N-2) x SWR_CAUSAL_TILE complex values).
-#define SWR_CAUSAL_TILE 32
-
 // Process-wide count of kernels launched by this library (swr_capi.cu).
 void swr_count_launch(int n);
 
@@ -137,8 +133,10 @@ int swr_launch_givens(double2* H, int ldh, double2* cs, double2* sn, double2* sv
                       double* res_out, cudaStream_t s);
 int swr_launch_lsq(const double2* H, int ldh, const double2* sv, int k, double2* y,
                    cudaStream_t s);
-int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0inv,
-                      const double2* y, double2* x, int sweeps, double2* hist, cudaStream_t s);
+int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0,
+                      const double2* y, double2* x, int sweeps, void* scratch, int* status,
+                      cudaStream_t s);
+size_t swr_causal_scratch_bytes(int N);
 int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s);
 int swr_launch_jump(const double2* trace, const MarchSys* sys, int N, int nt, double* out,
                     cudaStream_t s);

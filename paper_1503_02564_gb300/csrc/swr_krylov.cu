@@ -346,129 +346,154 @@ int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cud
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// hist[o][n - t0] = y_o[n] + sum_src sum_{s < t0} c[n-s] x_src[s],  n in [t0, t0+b)
-__global__ void k_causal_far(int N, int nt, int t0, int b, const double2* __restrict__ cols,
-                             const double2* __restrict__ x, const double2* __restrict__ y,
-                             double2* __restrict__ hist) {
-    const int o = blockIdx.x;
-    int c1, i1, c2, i2;
-    block_sources(o, N, c1, i1, c2, i2);
-    const int nb = min(b, nt - t0);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const double2 zero = make_double2(0.0, 0.0);
-    for (int q = w; q < nb; q += nw) {                 // one warp per time of the tile
-        const int n = t0 + q;
-        double2 acc = zero;
-        for (int s = lane; s < t0; s += 32) {
-            acc = cfma(cols[(size_t)c1 * nt + n - s], x[(size_t)i1 * nt + s], acc);
-            if (c2 >= 0) acc = cfma(cols[(size_t)c2 * nt + n - s], x[(size_t)i2 * nt + s], acc);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) hist[(size_t)o * b + q] = cadd(acc, y[(size_t)o * nt + n]);
-    }
+// Wavefront form of the substitution: one CTA per interface k, all CTAs
+// resident at once (cooperative launch).  At time step n, CTA k needs the
+// values of its own two blocks and of the neighbouring blocks 2k-1 (interface
+// k-1) and 2k+2 (interface k+1) at steps < n, so it waits only for its two
+// neighbours' progress counters.  Progress is counted in sub-steps: step n,
+// sweep sw is complete when progress >= n (S+1) + sw + 1, S = sweeps.
+// Every wait is bounded; on timeout the CTA raises ST_TIMEOUT and a global abort
+// flag, and all CTAs leave their loops.
+#include <cuda/atomic>
+
+namespace {
+constexpr long long kWaitPolls = 4000000;    // about 1-2 s with the back-off below
 }
 
-__global__ void k_causal_near(int N, int nt, int t0, int b, int sweeps,
-                              const double2* __restrict__ cols, const double2* __restrict__ lag0,
-                              const double2* __restrict__ hist, double2* __restrict__ x) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int k = (int)cl.block_rank() * blockDim.x + threadIdx.x;   // interface
-    const bool act = (k < N - 1);
-    const int nb = min(b, nt - t0);
+__device__ __forceinline__ int load_acquire(const int* p) {
+    cuda::atomic_ref<const int, cuda::thread_scope_device> r(*p);
+    return r.load(cuda::memory_order_acquire);
+}
+__device__ __forceinline__ void store_release(int* p, int v) {
+    cuda::atomic_ref<int, cuda::thread_scope_device> r(*p);
+    r.store(v, cuda::memory_order_release);
+}
+
+// Wait until the neighbours of interface k have reached `target`; returns false
+// (after raising the abort flag) on timeout or when another CTA aborted.
+__device__ bool wait_neighbours(int k, int nif, int target, const int* progress, int* abortf,
+                                int* status) {
+    long long polls = 0;
+    for (int side = 0; side < 2; ++side) {
+        const int nb = (side == 0) ? k - 1 : k + 1;
+        if (nb < 0 || nb >= nif) continue;
+        while (load_acquire(progress + nb) < target) {
+            if (load_acquire(abortf) != 0) return false;
+            if (++polls > kWaitPolls) {
+                atomicOr(status, ST_TIMEOUT);
+                store_release(abortf, 1);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(128) k_causal_wave(int N, int nt, int sweeps,
+                                                     const double2* __restrict__ cols,
+                                                     const double2* __restrict__ lag0,
+                                                     const double2* __restrict__ y,
+                                                     double2* __restrict__ x,
+                                                     double2* __restrict__ xsw, int* progress,
+                                                     int* abortf, int* status) {
+    __shared__ double2 part[4];
+    __shared__ int s_go;
+    const int nif = N - 1;
+    const int k = blockIdx.x;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double2 zero = make_double2(0.0, 0.0);
-    // sources: r_k <- X^{k+1,1} l_{k+1} (block 2k+1), X^{k+1,2} r_{k+1} (block 2k+2)
-    //          l_{k+1} <- X^{k,4} r_k (block 2k), X^{k,3} l_k (block 2k-1)
-    const int o1 = 2 * k, o2 = 2 * k + 1;
-    const double2* cA = cols + (size_t)(4 * (k + 1) + 0) * nt;
-    const double2* cB = (k + 1 <= N - 2) ? cols + (size_t)(4 * (k + 1) + 1) * nt : nullptr;
-    const double2* cC = cols + (size_t)(4 * k + 3) * nt;
-    const double2* cD = (k >= 1) ? cols + (size_t)(4 * k + 2) * nt : nullptr;
-    const double2* xA = x + (size_t)(2 * k + 1) * nt;
-    const double2* xB = x + (size_t)(2 * k + 2) * nt;
-    const double2* xC = x + (size_t)(2 * k) * nt;
-    const double2* xD = x + (size_t)(2 * k - 1) * nt;
-    double2 D00 = zero, D01 = zero, D10 = zero, D11 = zero;
-    if (act) {
+    // warp w handles one source of the two outputs of interface k:
+    //  w=0: r_k     <- X^{k+1,1} l_{k+1} (block 2k+1)   w=1: r_k <- X^{k+1,2} r_{k+1} (block 2k+2)
+    //  w=2: l_{k+1} <- X^{k,4}   r_k     (block 2k)     w=3: l_{k+1} <- X^{k,3} l_k (block 2k-1)
+    bool has = true;
+    int cslot = 0, inb = 0;
+    if (w == 0) { cslot = 4 * (k + 1) + 0; inb = 2 * k + 1; }
+    if (w == 1) { has = (k + 1 <= N - 2); cslot = 4 * (k + 1) + 1; inb = 2 * k + 2; }
+    if (w == 2) { cslot = 4 * k + 3; inb = 2 * k; }
+    if (w == 3) { has = (k >= 1); cslot = 4 * k + 2; inb = 2 * k - 1; }
+    const double2* cc = has ? cols + (size_t)cslot * nt : nullptr;
+    const double2* xin = has ? x + (size_t)inb * nt : nullptr;
+    const int S1 = sweeps + 1;
+    double2 D00 = zero, D01 = zero, D10 = zero, D11 = zero, cB0 = zero, cD0 = zero;
+    if (threadIdx.x == 0) {
         D00 = lag0[k * 4 + 0];
         D01 = lag0[k * 4 + 1];
         D10 = lag0[k * 4 + 2];
         D11 = lag0[k * 4 + 3];
+        if (k + 1 <= N - 2) cB0 = cols[(size_t)(4 * (k + 1) + 1) * nt];
+        if (k >= 1) cD0 = cols[(size_t)(4 * k + 2) * nt];
     }
-    for (int q = 0; q < nb; ++q) {
-        const int n = t0 + q;
-        double2 r1 = zero, r2 = zero;
-        if (act) {
-            r1 = hist[(size_t)o1 * b + q];
-            r2 = hist[(size_t)o2 * b + q];
-            for (int s = t0; s < n; ++s) {
-                r1 = cfma(cA[n - s], xA[s], r1);
-                if (cB) r1 = cfma(cB[n - s], xB[s], r1);
-                r2 = cfma(cC[n - s], xC[s], r2);
-                if (cD) r2 = cfma(cD[n - s], xD[s], r2);
-            }
-        }
-        double2 z1 = zero, z2 = zero;
-        if (act) {
-            z1 = cfma(D01, r2, cmul(D00, r1));
-            z2 = cfma(D11, r2, cmul(D10, r1));
-            x[(size_t)o1 * nt + n] = z1;
-            x[(size_t)o2 * nt + n] = z2;
-        }
-        for (int sw = 0; sw < sweeps; ++sw) {
+    for (int n = 0; n < nt; ++n) {
+        if (threadIdx.x == 0) {
+            s_go = wait_neighbours(k, nif, n * S1, progress, abortf, status) ? 1 : 0;
             __threadfence();
-            cl.sync();
-            double2 e1 = r1, e2 = r2;
-            if (act) {
-                if (cB) e1 = cfma(cB[0], xB[n], e1);
-                if (cD) e2 = cfma(cD[0], xD[n], e2);
-            }
-            cl.sync();
-            if (act) {
+        }
+        __syncthreads();
+        if (!s_go) break;
+        // history, lags >= 1
+        double2 acc = zero;
+        if (has)
+            for (int s = lane; s < n; s += 32) acc = cfma(__ldg(cc + n - s), xin[s], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) part[w] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double2 r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(part[0], part[1]));
+            const double2 r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(part[2], part[3]));
+            double2 z1 = cfma(D01, r2, cmul(D00, r1));
+            double2 z2 = cfma(D11, r2, cmul(D10, r1));
+            bool ok = true;
+            for (int sw = 1; sw <= sweeps && ok; ++sw) {
+                // publish sweep sw-1 of this step, then use the neighbours' sweep sw-1
+                double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif;
+                out[2 * k] = z1;
+                out[2 * k + 1] = z2;
+                __threadfence();
+                store_release(progress + k, n * S1 + sw);
+                ok = wait_neighbours(k, nif, n * S1 + sw, progress, abortf, status);
+                if (!ok) break;
+                __threadfence();
+                const double2 xr = (k + 1 <= N - 2) ? out[2 * (k + 1)] : zero;       // r_{k+1}
+                const double2 xl = (k >= 1) ? out[2 * (k - 1) + 1] : zero;          // l_k
+                const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
                 z1 = cfma(D01, e2, cmul(D00, e1));
                 z2 = cfma(D11, e2, cmul(D10, e1));
-                x[(size_t)o1 * nt + n] = z1;
-                x[(size_t)o2 * nt + n] = z2;
             }
+            x[(size_t)(2 * k) * nt + n] = z1;
+            x[(size_t)(2 * k + 1) * nt + n] = z2;
+            __threadfence();
+            store_release(progress + k, (n + 1) * S1);
         }
-        __threadfence();
-        cl.sync();
+        __syncthreads();
     }
 }
 
+size_t swr_causal_scratch_bytes(int N) {
+    // xsw: 2 x 2(N-1) complex sweep values, then N-1 progress counters and the abort flag
+    return sizeof(double2) * (size_t)4 * (N - 1) + sizeof(int) * (size_t)N;
+}
+
 int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, const double2* y,
-                      double2* x, int sweeps, double2* hist, cudaStream_t s) {
-    const int b = SWR_CAUSAL_TILE;
+                      double2* x, int sweeps, void* scratch, int* status, cudaStream_t s) {
     const int nif = N - 1;
-    int tpb = 64;
-    int C = (nif + tpb - 1) / tpb;
-    while (C > 16 && tpb < 1024) {
-        tpb *= 2;
-        C = (nif + tpb - 1) / tpb;
-    }
-    if (C > 16) return -2;
-    if (C > 8 &&
-        cudaFuncSetAttribute(k_causal_near, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess)
+    double2* xsw = static_cast<double2*>(scratch);
+    int* progress = reinterpret_cast<int*>(xsw + (size_t)4 * nif);
+    int* abortf = progress + nif;
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_causal_wave, 128, 0) != cudaSuccess)
         return -1;
-    for (int t0 = 0; t0 < nt; t0 += b) {
-        k_causal_far<<<2 * N - 2, 256, 0, s>>>(N, nt, t0, b, cols, x, y, hist);
-    swr_count_launch(2);
-        if (cudaGetLastError() != cudaSuccess) return -1;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(C);
-        cfg.blockDim = dim3(tpb);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, k_causal_near, N, nt, t0, b, sweeps, cols, lag0,
-                               (const double2*)hist, x) != cudaSuccess)
-            return -1;
-    }
+    if (nif > nsm * per) return -2;      // all CTAs must be resident at once
+    // progress counters and the abort flag start at zero on every call
+    if (cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)N, s) != cudaSuccess) return -1;
+    void* args[] = {(void*)&N, (void*)&nt, (void*)&sweeps, (void*)&cols, (void*)&lag0,
+                    (void*)&y, (void*)&x, (void*)&xsw, (void*)&progress, (void*)&abortf,
+                    (void*)&status};
+    if (cudaLaunchCooperativeKernel((const void*)k_causal_wave, dim3(nif), dim3(128), args, 0, s) !=
+        cudaSuccess)
+        return -1;
+    swr_count_launch(1);
     return 0;
 }

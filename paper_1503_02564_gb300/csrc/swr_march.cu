@@ -351,9 +351,9 @@ int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, c
 
 // ---------------------------------------------------------------------------
 // The march kernel.
-// Threads: C == 1: thread tid -> system g = tid / P of the CTA's G systems, chunk
-// p = tid % P.  C > 1: one system per cluster, chunk p = rank * T + tid.
-// Thread p owns separator p; thread P-1 also owns separator P.
+// Each system has P+1 threads: thread p owns separator p and, for p < P, chunk p.
+// C == 1: the CTA carries G systems, thread tid -> system g = tid / (P+1).
+// C > 1:  one system per cluster, p = rank * T + tid.
 // Shared memory (per CTA): separator values usep, PCR ping-pong dA/dB
 // ([T+G] each) and, per chunk, the first/last interior u and y ([T] each).
 // ---------------------------------------------------------------------------
@@ -376,21 +376,21 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
     const int tid = threadIdx.x;
     int g, p, sidx;
     if (C == 1) {
-        g = tid / P;
-        p = tid - g * P;
+        g = tid / (P + 1);
+        p = tid - g * (P + 1);
         sidx = blockIdx.x * G + g;
         if (g >= G) p = -1;
     } else {
         g = 0;
         p = rank * T + tid;
         sidx = blockIdx.x / C;
-        if (p >= P) p = -1;
+        if (p > P) p = -1;
     }
     const bool valid = (p >= 0) && (sidx < a.nsys);
 
     auto SEP = [&](double2* arr, int ps) -> double2* {
         if (C == 1) return arr + g * (P + 1) + ps;
-        const int home = min(ps / T, C - 1);
+        const int home = ps / T;
         double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
         return base + (ps - home * T);
     };
@@ -416,12 +416,12 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         Pj = a.sub_P[j];
         goff = a.sub_goff[j];
         tcf = a.sub_tc[j];
-        Lp = a.clen[j * P + p];
+        Lp = (p < P) ? a.clen[j * P + p] : 0;
         sp = a.sep_pos[j * (P + 1) + p];
     }
     const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
-    const int nown = (valid && p == P - 1) ? 2 : (valid ? 1 : 0);
-    const double2* F = a.fac + (size_t)j * L * 4 * P + p;
+    const bool realsep = valid && (p <= Pj);          // separators beyond Pj are padding
+    const double2* F = a.fac + (size_t)j * L * 4 * P + (p < P ? p : 0);
     const double2* sE_l = a.sep + (size_t)(j * 3 + 0) * (P + 1);
     const double2* sE_r = a.sep + (size_t)(j * 3 + 1) * (P + 1);
     const double2* sbinv = a.sep + (size_t)(j * 3 + 2) * (P + 1);
@@ -433,12 +433,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         u[i] = (valid && i < Lp && !zero_u0) ? a.u0[goff + sp + 1 + i] : zero;
         y[i] = zero;
     }
-    for (int e = 0; e < nown; ++e) {
-        const int ps = (e == 0) ? p : P;
-        double2 v0 = zero;
-        if (ps <= Pj && !zero_u0) v0 = a.u0[goff + a.sep_pos[j * (P + 1) + ps]];
-        *SEP(usep, ps) = v0;
-    }
+    if (valid) *SEP(usep, p) = (realsep && !zero_u0) ? a.u0[goff + sp] : zero;
     SYNC();
 
     double2 lin = zero, rin = zero;
@@ -466,7 +461,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     if (i == Lp - 1) ul = u[i];
                 }
             }
-            double2 ynext = zero, yf = zero, yl = zero;
+            double2 ynext = zero, yl = zero;
 #pragma unroll
             for (int i = L - 1; i >= 0; --i) {
                 if (i < Lp) {
@@ -478,22 +473,20 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     ynext = yi;
                 }
             }
-            yf = y[0];
             *CHK(ufst, p) = uf;
             *CHK(ulst, p) = ul;
-            *CHK(yfst, p) = yf;
+            *CHK(yfst, p) = y[0];
             *CHK(ylst, p) = yl;
         }
         SYNC();
-        // ---- phase B: reduced right-hand sides at the separators -------------
-        for (int e = 0; e < nown; ++e) {
-            const int ps = (e == 0) ? p : P;
+        // ---- phase B: reduced right-hand side at my separator ------------------
+        if (valid) {
             double2 d = zero;
-            if (ps <= Pj) {
-                const double2 us = *SEP(usep, ps);
-                const bool le = (ps == 0), re = (ps == Pj);
-                const double2 um = le ? zero : *CHK(ulst, ps - 1);
-                const double2 up = re ? zero : *CHK(ufst, ps);
+            if (realsep) {
+                const double2 us = *SEP(usep, p);
+                const bool le = (p == 0), re = (p == Pj);
+                const double2 um = le ? zero : *CHK(ulst, p - 1);
+                const double2 up = re ? zero : *CHK(ufst, p);
                 double2 f;
                 if (le)
                     f = make_double2(fma(2.0, us.x, up.x), fma(2.0, us.y, up.y));
@@ -516,10 +509,10 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     f = cfms(rin, a.inv_ik, f);
                 }
                 d = f;
-                if (!le) d = cfms(sE_l[ps], *CHK(ylst, ps - 1), d);
-                if (!re) d = cfms(sE_r[ps], *CHK(yfst, ps), d);
+                if (!le) d = cfms(sE_l[p], *CHK(ylst, p - 1), d);
+                if (!re) d = cfms(sE_r[p], *CHK(yfst, p), d);
             }
-            *SEP(dA, ps) = d;
+            *SEP(dA, p) = d;
         }
         SYNC();
         // ---- phase C: PCR on the separators (coefficients precomputed) -------
@@ -527,15 +520,14 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         double2* dst = dB;
         for (int k = 0; k < levels; ++k) {
             const int st = 1 << k;
-            const double2* al = pcr + (size_t)(k * 2 + 0) * (P + 1);
-            const double2* ga = pcr + (size_t)(k * 2 + 1) * (P + 1);
-            for (int e = 0; e < nown; ++e) {
-                const int ps = (e == 0) ? p : P;
-                double2 dd = *SEP(src, ps);
-                if (ps - st >= 0) dd = cfma(al[ps], *SEP(src, ps - st), dd);
-                if (ps + st <= P) dd = cfma(ga[ps], *SEP(src, ps + st), dd);
-                if (k == levels - 1) dd = cmul(dd, sbinv[ps]);
-                *SEP(dst, ps) = dd;
+            if (valid) {
+                const double2* al = pcr + (size_t)(k * 2 + 0) * (P + 1);
+                const double2* ga = pcr + (size_t)(k * 2 + 1) * (P + 1);
+                double2 dd = *SEP(src, p);
+                if (p - st >= 0) dd = cfma(al[p], *SEP(src, p - st), dd);
+                if (p + st <= P) dd = cfma(ga[p], *SEP(src, p + st), dd);
+                if (k == levels - 1) dd = cmul(dd, sbinv[p]);
+                *SEP(dst, p) = dd;
             }
             SYNC();
             double2* tmp = src;
@@ -554,23 +546,20 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                 }
             }
         }
-        for (int e = 0; e < nown; ++e) {
-            const int ps = (e == 0) ? p : P;
-            if (ps <= Pj) {
-                const double2 v = *SEP(src, ps);
-                double2* us = SEP(usep, ps);
-                const double2 uo = *us;
-                *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
-                if (ps == 0) {
-                    if ((tcf & 1) && sy.out_a >= 0)
-                        a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
-                    if (sy.flags & SYS_TRACE) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
-                }
-                if (ps == Pj) {
-                    if ((tcf & 2) && sy.out_b >= 0)
-                        a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
-                    if (sy.flags & SYS_TRACE) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
-                }
+        if (realsep) {
+            const double2 v = *SEP(src, p);
+            double2* us = SEP(usep, p);
+            const double2 uo = *us;
+            *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
+            if (p == 0) {
+                if ((tcf & 1) && sy.out_a >= 0)
+                    a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
+                if (sy.flags & SYS_TRACE) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
+            }
+            if (p == Pj) {
+                if ((tcf & 2) && sy.out_b >= 0)
+                    a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
+                if (sy.flags & SYS_TRACE) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
         }
         SYNC();
@@ -586,15 +575,11 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
             for (int i = 0; i < L; ++i)
                 if (i < Lp) a.uT[goff + sp + 1 + i] = u[i];
         }
-        for (int e = 0; e < nown; ++e) {
-            const int ps = (e == 0) ? p : P;
-            if (ps <= Pj) {
-                const double2 us = *SEP(usep, ps);
-                bad |= !cfinite(us);
-                const int node = a.sep_pos[j * (P + 1) + ps];
-                // the interface node belongs to the left subdomain
-                if ((sy.flags & SYS_WRITE_UT) && (node > 0 || j == 0)) a.uT[goff + node] = us;
-            }
+        if (realsep) {
+            const double2 us = *SEP(usep, p);
+            bad |= !cfinite(us);
+            // the interface node belongs to the left subdomain
+            if ((sy.flags & SYS_WRITE_UT) && (sp > 0 || j == 0)) a.uT[goff + sp] = us;
         }
     }
     if (bad) atomicOr(a.status, ST_NONFINITE);

@@ -10,7 +10,7 @@
 // fixed-size array in the library's own device memory instead.
 //
 // The scratch is a file-scope __device__ array: every GPU that loads the
-// library holds it (about 1.1 MB) until the process exits.  Host code must not
+// library holds it (about 135 KB) until the process exits.  Host code must not
 // hand the array's name to a kernel: on the host it is only a stand-in symbol.
 // Its device address is looked up with cudaGetSymbolAddress once per device,
 // with that device current, the first time the entry point runs there.
@@ -22,16 +22,18 @@ namespace {
 
 constexpr int kNoallocMaxSub = 1024;     // largest supported number of subdomains N
 constexpr int kNoallocMaxDevices = 64;
-constexpr size_t kHistElems = (size_t)(2 * kNoallocMaxSub - 2) * SWR_CAUSAL_TILE;
 constexpr size_t kLag0Elems = (size_t)4 * kNoallocMaxSub;
+// causal substitution scratch for N = 1024: 4(N-1) complex sweep values + N ints
+constexpr size_t kCausalBytes = sizeof(double2) * 4 * (kNoallocMaxSub - 1) + sizeof(int) * kNoallocMaxSub;
+constexpr size_t kCausalElems = (kCausalBytes + sizeof(double2) - 1) / sizeof(double2);
 
 std::mutex g_setup_mutex;
 double2* g_scratch_addr[kNoallocMaxDevices] = {};
 
 }  // namespace
 
-// history tile (2N-2 blocks x tile) followed by the 2x2 lag-0 inverses (4 per interface)
-static __device__ __align__(256) double2 g_noalloc_scratch[kHistElems + kLag0Elems];
+// 2x2 lag-0 inverses, then the causal substitution scratch, then one status word
+static __device__ __align__(256) double2 g_noalloc_scratch[kLag0Elems + kCausalElems + 1];
 
 extern "C" swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t sweeps,
                                                const double* cols, const double* y, double* x,
@@ -39,6 +41,7 @@ extern "C" swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t
     if (nsub < 2 || nsub > kNoallocMaxSub || nt < 1 || sweeps < 0 || sweeps > 16 || !cols || !y ||
         !x || x == y)
         return SWR_ERR_ARG;
+    if (swr_causal_scratch_bytes(nsub) > kCausalBytes) return SWR_ERR_ARG;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return SWR_ERR_CUDA;
     if (dev < 0 || dev >= kNoallocMaxDevices) return SWR_ERR_UNSUPPORTED;
@@ -55,23 +58,30 @@ extern "C" swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t
         }
         scratch = g_scratch_addr[dev];
     }
-    double2* hist = scratch;
-    double2* lag0 = scratch + kHistElems;
+    double2* lag0 = scratch;
+    double2* causal = scratch + kLag0Elems;
+    int* status = reinterpret_cast<int*>(scratch + kLag0Elems + kCausalElems);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const double2* c = reinterpret_cast<const double2*>(cols);
-    // Every scratch entry the substitution reads is written earlier in the same
-    // call (lag-0 inverses first, each history tile before its use), so nothing
-    // has to be cleared between calls.
+    // The lag-0 inverses and sweep values are written before they are read in
+    // every call; the status word (and, inside the launcher, the progress
+    // counters and abort flag) must start at zero and are cleared here.
+    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return SWR_ERR_CUDA;
     if (swr_launch_lag0_setup(nsub, nt, c, lag0, s) != 0) {
         cudaGetLastError();
         return SWR_ERR_CUDA;
     }
     const int rc = swr_launch_causal(nsub, nt, c, lag0, reinterpret_cast<const double2*>(y),
-                                     reinterpret_cast<double2*>(x), sweeps, hist, s);
+                                     reinterpret_cast<double2*>(x), sweeps, causal, status, s);
     if (rc == -2) return SWR_ERR_UNSUPPORTED;
     if (rc != 0) {
         cudaGetLastError();
         return SWR_ERR_CUDA;
     }
+    int st = 0;
+    if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return SWR_ERR_CUDA;
+    if (st & ST_TIMEOUT) return SWR_ERR_TIMEOUT;
     return SWR_OK;
 }

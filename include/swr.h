@@ -62,8 +62,12 @@ enum { SWR_SOLVER_GMRES = 0, SWR_SOLVER_FIXED_POINT = 1, SWR_SOLVER_CLASSICAL = 
  *   NONE;
  *   ZERO_POTENTIAL: P = I - L_0, the interface operator with V = 0 (Section 5);
  *   CAUSAL: P = I - L itself (V = V(x) only), whose blocks are causal Toeplitz
- *           (Props. 3-4) so that P^{-1} is a block forward substitution in time. */
-enum { SWR_PC_NONE = 0, SWR_PC_ZERO_POTENTIAL = 1, SWR_PC_CAUSAL = 2 };
+ *           (Props. 3-4) so that P^{-1} is a block forward substitution in time;
+ *   MEAN_POTENTIAL: P = I - L_Vbar, the interface operator of the time-averaged
+ *           potential Vbar(x) = mean_n V(t_n, x) (V0 for NONLINEAR): the
+ *           zero-potential construction of Section 5 keeping the static part of V,
+ *           for potentials too strong for L_0. */
+enum { SWR_PC_NONE = 0, SWR_PC_ZERO_POTENTIAL = 1, SWR_PC_CAUSAL = 2, SWR_PC_MEAN_POTENTIAL = 3 };
 
 typedef struct swr_desc {
     int32_t nx;                 /* P1 nodes on (a0, b0), nx >= 3                       */
@@ -130,8 +134,9 @@ swr_status swr_plan(const swr_desc *d, swr_plan_t *out, void *stream);
  * V and build the interface problem (Section 4.1):
  *   SWR_V_STATIC:    d = R 0 and the first columns of X^{j,1..4} (Props. 3-4),
  *                    i.e. L and d of Eq. chp1_ILgd explicitly (Algorithm 3);
- *   SWR_V_TIME:      d = R 0, and L_0 when precond == ZERO_POTENTIAL;
- *   SWR_V_NONLINEAR: L_0 when precond == ZERO_POTENTIAL.
+ *   SWR_V_TIME:      d = R 0, and L_0 (L_Vbar) when precond == ZERO_POTENTIAL
+ *                    (MEAN_POTENTIAL);
+ *   SWR_V_NONLINEAR: L_0 (L_V0) when precond == ZERO_POTENTIAL (MEAN_POTENTIAL).
  * V:  double[nx] (STATIC; V0 for NONLINEAR) or double[(nt+1) * nx], row n = V(t_n, .)
  *     (TIME).  Copied into the plan.
  * u0: cplx[nx] initial value.  Copied into the plan.

@@ -53,6 +53,7 @@ struct swr_plan_s {
     int forceL = 0;                // SWR_CHUNK_L override (0: chosen per launch)
     double2* d_u0 = nullptr;
     double* d_V = nullptr;
+    double* d_Vbar = nullptr;      // potential of the preconditioner operator (MEAN_POTENTIAL)
     double2* d_iface = nullptr;    // d (nblk blocks) followed by cols (4N blocks)
     double2* d_iface0 = nullptr;   // L_0: zero d (nblk blocks) followed by cols (4N blocks)
     double2* d_lag0 = nullptr;     // (N-1) x 4, for L
@@ -83,9 +84,31 @@ struct swr_plan_s {
 
 namespace {
 
-#define CK(x)                                   \
-    do {                                        \
-        if ((x) != cudaSuccess) return SWR_ERR_CUDA; \
+// With SWR_DEBUG set in the environment, failing CUDA calls are reported on stderr.
+bool debug_on() {
+    static int on = -1;
+    if (on < 0) on = getenv("SWR_DEBUG") ? 1 : 0;
+    return on == 1;
+}
+swr_status cuda_fail(cudaError_t e, const char* what, int line) {
+    if (debug_on()) fprintf(stderr, "libswr: %s failed at line %d: %s\n", what, line, cudaGetErrorString(e));
+    return SWR_ERR_CUDA;
+}
+swr_status launch_fail(const char* what, int line) {
+    cudaError_t e = cudaGetLastError();
+    if (debug_on())
+        fprintf(stderr, "libswr: launch of %s failed at line %d: %s\n", what, line, cudaGetErrorString(e));
+    return SWR_ERR_CUDA;
+}
+
+#define CK(x)                                               \
+    do {                                                    \
+        cudaError_t ck_e_ = (x);                            \
+        if (ck_e_ != cudaSuccess) return cuda_fail(ck_e_, #x, __LINE__); \
+    } while (0)
+#define LK(x)                                               \
+    do {                                                    \
+        if ((x) != 0) return launch_fail(#x, __LINE__);     \
     } while (0)
 
 template <typename T>
@@ -158,13 +181,15 @@ struct MarchCfg {
 
 inline int chunks_for(int nmax, int L) { return (nmax - 1 + L) / (L + 1); }
 
-MarchCfg march_config(const swr_plan_t p, int nsys) {
+MarchCfg march_config(const swr_plan_t p, int nsys, bool tdep = false) {
     MarchCfg c;
     const int nsm = p->nsm;
     const long long want = (long long)nsm * 4 * 32;
     const int cand[3] = {16, 8, 4};
     int L = 4;
-    if (p->forceL) {
+    if (tdep) {
+        L = 4;   // per-step refactorisation keeps LU, spikes and state in registers
+    } else if (p->forceL) {
         L = p->forceL;
     } else {
         for (int k = 0; k < 3; ++k) {
@@ -178,7 +203,7 @@ MarchCfg march_config(const swr_plan_t p, int nsys) {
     c.L = L;
     const int P = chunks_for(p->nmax, L);
     const int tps = P + 1;
-    const int TMAX = (L == 16) ? 256 : 384;
+    const int TMAX = (L == 16 || tdep) ? 256 : 384;
     if (tps <= TMAX) {
         c.C = 1;
         c.G = std::max(1, std::min(TMAX / tps, (nsys + nsm - 1) / nsm));
@@ -210,11 +235,16 @@ MarchCfg march_config(const swr_plan_t p, int nsys) {
 
 inline int lidx(int L) { return L == 4 ? 0 : (L == 8 ? 1 : 2); }
 
+inline double2 cmul_h(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
 swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, int nsys,
                      const double2* gin, double2* gout, double2* uT, double2* trace,
                      const double2* u0, long long work) {
     MarchArgs a{};
-    const MarchCfg cfg = march_config(p, nsys);
+    const bool tdep = (p->d.vkind == SWR_V_TIME) && !zero_potential;
+    const MarchCfg cfg = march_config(p, nsys, tdep);
     const int C = cfg.C, G = cfg.G, T = cfg.T, ng = cfg.ngroups;
     if (C > 16) return SWR_ERR_UNSUPPORTED;
     const FactorSet& fs = zero_potential ? p->fs0L[lidx(cfg.L)] : p->fsL[lidx(cfg.L)];
@@ -237,12 +267,12 @@ swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, i
     a.inv_ik = p->inv_ik;
     a.status = p->d_status;
     const int pi = prof_begin(p, 0, work);
-    const int rc = swr_launch_march(fs, a, ng, p->s);
+    const int rc = tdep ? swr_launch_march_tdep(fs, a, p->d_V, p->nx, p->h,
+                                                2.0 / p->d.dt * (p->h / 6.0),
+                                                cmul_h(p->sigma0, p->inv_ik), ng, p->s)
+                        : swr_launch_march(fs, a, ng, p->s);
     prof_end(p, pi);
-    if (rc != 0) {
-        cudaGetLastError();
-        return SWR_ERR_CUDA;
-    }
+    if (rc != 0) return launch_fail(tdep ? "march (time-dependent)" : "march", __LINE__);
     return SWR_OK;
 }
 
@@ -346,7 +376,7 @@ swr_status ensure_workspace(swr_plan_t p) {
 // ||v||_2 (device -> host)
 swr_status norm2(swr_plan_t p, const double2* v, long long n, double* out) {
     Workspace& w = p->ws;
-    if (swr_launch_dots(v, 0, 1, v, n, w.partial, 512, w.h, p->s) != 0) return SWR_ERR_CUDA;
+    LK(swr_launch_dots(v, 0, 1, v, n, w.partial, 512, w.h, p->s));
     double2 r;
     CK(cudaMemcpyAsync(&r, w.h, sizeof(double2), cudaMemcpyDeviceToHost, p->s));
     CK(cudaStreamSynchronize(p->s));
@@ -368,15 +398,15 @@ swr_status apply_A(swr_plan_t p, const double2* x, double2* y) {
     // matrix-free: y = x - R x + d   (Algorithm 2)
     swr_status st = run_march(p, false, p->d_sys_R, p->N, x, y, nullptr, nullptr, p->d_u0, p->work_R);
     if (st) return st;
-    if (swr_launch_axpby(y, x, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s)) return SWR_ERR_CUDA;
-    if (swr_launch_axpby(y, p->d_iface, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s))
-        return SWR_ERR_CUDA;
+    LK(swr_launch_axpby(y, x, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s));
+    LK(swr_launch_axpby(y, p->d_iface, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s));
     return SWR_OK;
 }
 
 bool has_precond(swr_plan_t p) {
     return (p->d.precond == SWR_PC_CAUSAL && p->d.vkind == SWR_V_STATIC) ||
-           (p->d.precond == SWR_PC_ZERO_POTENTIAL && p->have_L0);
+           ((p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) &&
+            p->have_L0);
 }
 
 // x = P^{-1} y
@@ -386,7 +416,8 @@ swr_status apply_M(swr_plan_t p, const double2* y, double2* x) {
     if (p->d.precond == SWR_PC_CAUSAL && p->d.vkind == SWR_V_STATIC) {
         cols = p->d_iface + (size_t)p->nblk * p->nt;
         lag0 = p->d_lag0;
-    } else if (p->d.precond == SWR_PC_ZERO_POTENTIAL && p->have_L0) {
+    } else if ((p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) &&
+               p->have_L0) {
         cols = p->d_iface0 + (size_t)p->nblk * p->nt;
         lag0 = p->d_lag0_0;
     } else {
@@ -397,7 +428,7 @@ swr_status apply_M(swr_plan_t p, const double2* y, double2* x) {
                                p->d_status, p->s);
     prof_end(p, pi);
     if (rc == -2) return SWR_ERR_UNSUPPORTED;
-    if (rc) return SWR_ERR_CUDA;
+    if (rc) return launch_fail("causal substitution", __LINE__);
     return SWR_OK;
 }
 
@@ -416,7 +447,7 @@ swr_status gmres(swr_plan_t p, double2* g, bool g_init, swr_info* info) {
     // r = b - A g
     if (g_init) {
         if ((st = apply_A(p, g, w.r))) return st;
-        if (swr_launch_axpby(w.r, b, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s)) return SWR_ERR_CUDA;
+        LK(swr_launch_axpby(w.r, b, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s));
     } else {
         CK(cudaMemcpyAsync(w.r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
     }
@@ -431,7 +462,7 @@ swr_status gmres(swr_plan_t p, double2* g, bool g_init, swr_info* info) {
         double2 b0 = make_double2(beta, 0.0);
         CK(cudaMemcpyAsync(w.sv, &b0, sizeof(double2), cudaMemcpyHostToDevice, p->s));
         CK(cudaMemcpyAsync(w.sv + ldh + ldh, &b0, sizeof(double2), cudaMemcpyHostToDevice, p->s));
-        if (swr_launch_scale_by_rnorm(w.V, w.r, n, w.sv + 2 * ldh, p->s)) return SWR_ERR_CUDA;
+        LK(swr_launch_scale_by_rnorm(w.V, w.r, n, w.sv + 2 * ldh, p->s));
         CK(cudaMemsetAsync(w.H, 0, sizeof(double2) * ldh * m, p->s));
         int k = 0;
         double est = beta;
@@ -446,17 +477,16 @@ swr_status gmres(swr_plan_t p, double2* g, bool g_init, swr_info* info) {
             double2* Hc = w.H + (size_t)j * ldh;
             double2* work = w.sv + ldh;
             // first Gram-Schmidt pass -> H column
-            if (swr_launch_dots(w.V, n, j + 1, w.w, n, w.partial, 512, Hc, p->s)) return SWR_ERR_CUDA;
-            if (swr_launch_gemv_sub(w.V, n, j + 1, Hc, w.w, n, -1.0, p->s)) return SWR_ERR_CUDA;
+            LK(swr_launch_dots(w.V, n, j + 1, w.w, n, w.partial, 512, Hc, p->s));
+            LK(swr_launch_gemv_sub(w.V, n, j + 1, Hc, w.w, n, -1.0, p->s));
             // second pass -> work[0..j]
-            if (swr_launch_dots(w.V, n, j + 1, w.w, n, w.partial, 512, work, p->s)) return SWR_ERR_CUDA;
-            if (swr_launch_gemv_sub(w.V, n, j + 1, work, w.w, n, -1.0, p->s)) return SWR_ERR_CUDA;
+            LK(swr_launch_dots(w.V, n, j + 1, w.w, n, w.partial, 512, work, p->s));
+            LK(swr_launch_gemv_sub(w.V, n, j + 1, work, w.w, n, -1.0, p->s));
             // |w|^2 -> work[j+1]
-            if (swr_launch_dots(w.w, 0, 1, w.w, n, w.partial, 512, work + j + 1, p->s)) return SWR_ERR_CUDA;
-            if (swr_launch_givens(w.H, ldh, w.cs, w.sn, w.sv, j, w.res, p->s)) return SWR_ERR_CUDA;
+            LK(swr_launch_dots(w.w, 0, 1, w.w, n, w.partial, 512, work + j + 1, p->s));
+            LK(swr_launch_givens(w.H, ldh, w.cs, w.sn, w.sv, j, w.res, p->s));
             // v_{j+1} = w / |w|  (norm stored at work[ldh])
-            if (swr_launch_scale_by_rnorm(w.V + (size_t)(j + 1) * n, w.w, n, work + ldh, p->s))
-                return SWR_ERR_CUDA;
+            LK(swr_launch_scale_by_rnorm(w.V + (size_t)(j + 1) * n, w.w, n, work + ldh, p->s));
             CK(cudaMemcpyAsync(&est, w.res, sizeof(double), cudaMemcpyDeviceToHost, p->s));
             CK(cudaStreamSynchronize(p->s));
             prof_flush(p);
@@ -466,18 +496,18 @@ swr_status gmres(swr_plan_t p, double2* g, bool g_init, swr_info* info) {
             if (est < tol) break;
         }
         // g += M^{-1} V_k y
-        if (swr_launch_lsq(w.H, ldh, w.sv, k, w.y, p->s)) return SWR_ERR_CUDA;
+        LK(swr_launch_lsq(w.H, ldh, w.sv, k, w.y, p->s));
         CK(cudaMemsetAsync(w.w, 0, sizeof(double2) * n, p->s));
-        if (swr_launch_gemv_sub(w.V, n, k, w.y, w.w, n, 1.0, p->s)) return SWR_ERR_CUDA;
+        LK(swr_launch_gemv_sub(w.V, n, k, w.y, w.w, n, 1.0, p->s));
         if (pc) {
             if ((st = apply_M(p, w.w, w.z))) return st;
-            if (swr_launch_axpby(g, w.z, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s)) return SWR_ERR_CUDA;
+            LK(swr_launch_axpby(g, w.z, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s));
         } else {
-            if (swr_launch_axpby(g, w.w, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s)) return SWR_ERR_CUDA;
+            LK(swr_launch_axpby(g, w.w, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s));
         }
         // true residual
         if ((st = apply_A(p, g, w.r))) return st;
-        if (swr_launch_axpby(w.r, b, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s)) return SWR_ERR_CUDA;
+        LK(swr_launch_axpby(w.r, b, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s));
         if ((st = norm2(p, w.r, n, &beta))) return st;
         ++restarts;
     }
@@ -511,7 +541,7 @@ swr_status fixed_point(swr_plan_t p, double2* g, bool g_init, bool classical, sw
                 return SWR_ERR_UNSUPPORTED;
         }
         CK(cudaMemcpyAsync(w.r, w.z, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
-        if (swr_launch_axpby(w.r, g, n, make_double2(1.0, 0.0), make_double2(-1.0, 0.0), p->s)) return SWR_ERR_CUDA;
+        LK(swr_launch_axpby(w.r, g, n, make_double2(1.0, 0.0), make_double2(-1.0, 0.0), p->s));
         CK(cudaMemcpyAsync(g, w.z, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
         if ((st = norm2(p, w.r, n, &diff))) return st;
         ++it;
@@ -559,7 +589,7 @@ void swr_destroy(swr_plan_t p) {
         swr_factor_free(p->fsL[k]);
         swr_factor_free(p->fs0L[k]);
     }
-    cudaFree(p->d_u0); cudaFree(p->d_V); cudaFree(p->d_iface); cudaFree(p->d_iface0);
+    cudaFree(p->d_u0); cudaFree(p->d_V); cudaFree(p->d_Vbar); cudaFree(p->d_iface); cudaFree(p->d_iface0);
     cudaFree(p->d_lag0); cudaFree(p->d_lag0_0); cudaFree(p->d_hist); cudaFree(p->d_gtmp);
     cudaFree(p->d_gtmp2); cudaFree(p->d_trace);
     cudaFree(p->d_sys_build); cudaFree(p->d_sys_R); cudaFree(p->d_sys_final);
@@ -582,9 +612,10 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     if (d->nx < 3 || d->nt < 1 || !(d->dt > 0.0) || d->nsub < 2 || !(d->b0 > d->a0))
         return SWR_ERR_ARG;
     if (d->vkind < 0 || d->vkind > 2 || d->tc != SWR_TC_ROBIN) return d->tc == SWR_TC_S02 ? SWR_ERR_UNSUPPORTED : SWR_ERR_ARG;
-    if (d->solver < 0 || d->solver > 2 || d->precond < 0 || d->precond > 2) return SWR_ERR_ARG;
+    if (d->solver < 0 || d->solver > 2 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_NONLINEAR) return SWR_ERR_UNSUPPORTED;
     if (d->vkind != SWR_V_STATIC && d->solver == SWR_SOLVER_FIXED_POINT) return SWR_ERR_ARG;
+    if (d->vkind == SWR_V_TIME && (long long)(d->nt + 1) * d->nx > (1LL << 31)) return SWR_ERR_ARG;
     if (d->precond == SWR_PC_CAUSAL && d->vkind != SWR_V_STATIC) return SWR_ERR_ARG;
     swr_plan_t p = new (std::nothrow) swr_plan_s();
     if (!p) return SWR_ERR_NOMEM;
@@ -664,8 +695,9 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
         const size_t nV = (d->vkind == SWR_V_TIME) ? (size_t)(p->nt + 1) * p->nx : p->nx;
         st = dalloc(&p->d_V, nV);
     }
-    if (!st && (d->precond == SWR_PC_ZERO_POTENTIAL)) {
-        st = dalloc(&p->d_dg0, ntot);
+    if (!st && (d->precond == SWR_PC_ZERO_POTENTIAL || d->precond == SWR_PC_MEAN_POTENTIAL)) {
+        st = dalloc(&p->d_Vbar, p->nx);
+        if (!st) st = dalloc(&p->d_dg0, ntot);
         if (!st) st = dalloc(&p->d_od0, ntot);
         if (!st) st = dalloc(&p->d_iface0, nb + (size_t)4 * p->N * p->nt);
         if (!st) st = dalloc(&p->d_lag0_0, 4 * p->N);
@@ -710,34 +742,51 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
     cudaStream_t s = p->s;
     const size_t nb = (size_t)p->nblk * p->nt;
     const size_t nV = (p->d.vkind == SWR_V_TIME) ? (size_t)(p->nt + 1) * p->nx : p->nx;
-    if (p->d.vkind == SWR_V_TIME) return SWR_ERR_UNSUPPORTED;
     CK(cudaEventRecord(p->ev[0], s));
     CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
     CK(cudaMemcpyAsync(p->d_V, V, sizeof(double) * nV, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(p->d_u0, u0, sizeof(double2) * p->nx, cudaMemcpyDeviceToDevice, s));
     swr_status st = assemble(p, p->d_V, p->d_dg, p->d_od);
     if (st) return st;
-    // factorisations for the chunk lengths the marches of this plan will use
-    const int Lb = march_config(p, p->nsys_build).L, La = march_config(p, p->N).L;
-    if ((st = factor_for(p, p->fsL[lidx(Lb)], Lb, p->d_V, p->d_dg, p->d_od))) return st;
-    if (La != Lb && (st = factor_for(p, p->fsL[lidx(La)], La, p->d_V, p->d_dg, p->d_od))) return st;
-    CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
-    // Algorithm 3, step 1: d and the first columns, 3 marches per interior subdomain
-    st = run_march(p, false, p->d_sys_build, p->nsys_build, nullptr, p->d_iface, nullptr, nullptr,
-                   p->d_u0, p->work_build);
-    if (st) return st;
-    const double2* cols = p->d_iface + nb;
-    if (swr_launch_lag0_setup(p->N, p->nt, cols, p->d_lag0, s)) return SWR_ERR_CUDA;
-    if (p->d.precond == SWR_PC_ZERO_POTENTIAL) {
-        if ((st = assemble(p, nullptr, p->d_dg0, p->d_od0))) return st;
+    if (p->d.vkind == SWR_V_TIME) {
+        // chunk tables for the per-step refactorising march (the factors of the
+        // t = 0 matrix computed alongside are not used)
+        if ((st = factor_for(p, p->fsL[lidx(4)], 4, p->d_V, p->d_dg, p->d_od))) return st;
+        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
+        // d = R 0 (Section 4.1; valid for V(t,x)): the first N systems of the build list
+        st = run_march(p, false, p->d_sys_build, p->N, nullptr, p->d_iface, nullptr, nullptr,
+                       p->d_u0, p->work_R);
+        if (st) return st;
+    } else {
+        // factorisations for the chunk lengths the marches of this plan will use
+        const int Lb = march_config(p, p->nsys_build).L, La = march_config(p, p->N).L;
+        if ((st = factor_for(p, p->fsL[lidx(Lb)], Lb, p->d_V, p->d_dg, p->d_od))) return st;
+        if (La != Lb && (st = factor_for(p, p->fsL[lidx(La)], La, p->d_V, p->d_dg, p->d_od)))
+            return st;
+        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
+        // Algorithm 3, step 1: d and the first columns, 3 marches per interior subdomain
+        st = run_march(p, false, p->d_sys_build, p->nsys_build, nullptr, p->d_iface, nullptr,
+                       nullptr, p->d_u0, p->work_build);
+        if (st) return st;
+        const double2* cols = p->d_iface + nb;
+        LK(swr_launch_lag0_setup(p->N, p->nt, cols, p->d_lag0, s));
+    }
+    if (p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) {
+        const double* Vp = nullptr;                       // V = 0 (Section 5)
+        if (p->d.precond == SWR_PC_MEAN_POTENTIAL) {
+            LK(swr_launch_row_mean(p->d_V, p->d.vkind == SWR_V_TIME ? p->nt + 1 : 1, p->nx,
+                                   p->d_Vbar, s));
+            Vp = p->d_Vbar;
+        }
+        if ((st = assemble(p, Vp, p->d_dg0, p->d_od0))) return st;
         const int L0 = march_config(p, p->nsys_build - p->N).L;
-        if ((st = factor_for(p, p->fs0L[lidx(L0)], L0, nullptr, p->d_dg0, p->d_od0))) return st;
+        if ((st = factor_for(p, p->fs0L[lidx(L0)], L0, Vp, p->d_dg0, p->d_od0))) return st;
         CK(cudaMemsetAsync(p->d_iface0, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
         // impulse marches only (the first N systems of the build list are the d marches)
         st = run_march(p, true, p->d_sys_build + p->N, p->nsys_build - p->N, nullptr,
                        p->d_iface0, nullptr, nullptr, p->d_u0, p->work_build_imp);
         if (st) return st;
-        if (swr_launch_lag0_setup(p->N, p->nt, p->d_iface0 + nb, p->d_lag0_0, s)) return SWR_ERR_CUDA;
+        LK(swr_launch_lag0_setup(p->N, p->nt, p->d_iface0 + nb, p->d_lag0_0, s));
         p->have_L0 = true;
     }
     CK(cudaEventRecord(p->ev[1], s));
@@ -770,7 +819,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     swr_status st2 = run_march(p, false, p->d_sys_final, p->N, g, p->d_gtmp, uT, p->d_trace,
                                p->d_u0, p->work_R);
     if (st2) return st2;
-    if (swr_launch_jump(p->d_trace, p->d_sys_final, p->N, p->nt, p->d_scal, s)) return SWR_ERR_CUDA;
+    LK(swr_launch_jump(p->d_trace, p->d_sys_final, p->N, p->nt, p->d_scal, s));
     CK(cudaEventRecord(p->ev[3], s));
     double jump = 0.0;
     CK(cudaMemcpyAsync(&jump, p->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -111,11 +111,14 @@ int swr_launch_assemble_static(const double* V, int N, const int* d_n, const int
                                const int* d_loff, const int* d_tc, int ntot, double h, double dt,
                                double2 sigma0, double2 inv_ik, double2* dg, double2* od,
                                cudaStream_t s);
+int swr_launch_row_mean(const double* V, int nrows, long long nx, double* out, cudaStream_t s);
 int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t s);
 void swr_factor_free(FactorSet& fs);
 int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
                       const double2* od, int* status, cudaStream_t s);
 int swr_launch_march(const FactorSet& fs, MarchArgs a, int nsys_groups, cudaStream_t s);
+int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, long long vstride,
+                          double h, double kappa, double2 sig_ik, int ngroups, cudaStream_t s);
 int swr_march_smem_bytes(int T, int G);
 
 // Interface algebra launchers (swr_krylov.cu)

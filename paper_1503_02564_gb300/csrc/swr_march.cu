@@ -74,6 +74,22 @@ __global__ void k_assemble_static(const double* __restrict__ V, const int* __res
     }
 }
 
+// Vbar(x) = mean over the nrows rows of V (time average of a tabulated V(t,x)).
+__global__ void k_row_mean(const double* __restrict__ V, int nrows, long long nx,
+                           double* __restrict__ out) {
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    double acc = 0.0;
+    for (int r = 0; r < nrows; ++r) acc += V[(size_t)r * nx + x];
+    out[x] = acc / nrows;
+}
+
+int swr_launch_row_mean(const double* V, int nrows, long long nx, double* out, cudaStream_t s) {
+    k_row_mean<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(V, nrows, nx, out);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int swr_launch_assemble_static(const double* V, int N, const int* d_n, const int* d_goff,
                                const int* d_loff, const int* d_tc, int nmax, double h, double dt,
                                double2 sigma0, double2 inv_ik, double2* dg, double2* od,
@@ -498,14 +514,14 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     if (sy.flags & SYS_IMP_L)
                         lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                     else
-                        lin = (sy.in_l >= 0) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
+                        lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
                     f = cfms(lin, a.inv_ik, f);
                 }
                 if (re && (tcf & 2)) {
                     if (sy.flags & SYS_IMP_R)
                         rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                     else
-                        rin = (sy.in_r >= 0) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
+                        rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
                     f = cfms(rin, a.inv_ik, f);
                 }
                 d = f;
@@ -552,14 +568,14 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
             const double2 uo = *us;
             *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
             if (p == 0) {
-                if ((tcf & 1) && sy.out_a >= 0)
+                if ((tcf & 1) && sy.out_a >= 0 && a.gout)
                     a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
-                if (sy.flags & SYS_TRACE) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
             if (p == Pj) {
-                if ((tcf & 2) && sy.out_b >= 0)
+                if ((tcf & 2) && sy.out_b >= 0 && a.gout)
                     a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
-                if (sy.flags & SYS_TRACE) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
         }
         SYNC();
@@ -570,7 +586,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
 #pragma unroll
         for (int i = 0; i < L; ++i)
             if (i < Lp) bad |= !cfinite(u[i]);
-        if (sy.flags & SYS_WRITE_UT) {
+        if ((sy.flags & SYS_WRITE_UT) && a.uT) {
 #pragma unroll
             for (int i = 0; i < L; ++i)
                 if (i < Lp) a.uT[goff + sp + 1 + i] = u[i];
@@ -579,12 +595,394 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
             const double2 us = *SEP(usep, p);
             bad |= !cfinite(us);
             // the interface node belongs to the left subdomain
-            if ((sy.flags & SYS_WRITE_UT) && (sp > 0 || j == 0)) a.uT[goff + sp] = us;
+            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || j == 0)) a.uT[goff + sp] = us;
         }
     }
     if (bad) atomicOr(a.status, ST_NONFINITE);
     // keep remote shared memory alive until every CTA of the cluster is done
     if (C > 1) cl.sync();
+}
+
+// ---------------------------------------------------------------------------
+// Time-dependent potential (Eq. CNS_L with W_n = (V_n + V_{n-1})/2): the matrix
+// A_{j,n} - B_j changes every step, so each step refactors in place.  Chunk
+// thread: assemble its rows from W_n, LU, local solve and both spikes; the
+// separator system (whose coefficients now change every step) is solved by PCR
+// updating matrix and right-hand side together.  Entries are pre-scaled by
+// 1/(i kappa): D = md/(h/6) + i (sd - wd)/kappa, E = 1 - i (1/h + wo)/kappa.
+// ---------------------------------------------------------------------------
+struct TdepArgs {
+    MarchArgs m;
+    const double* V;     // (nt+1) x nx, row n = V(t_n, .)
+    long long vstride;   // nx
+    double h, kappa;
+    double2 sig_ik;      // sigma0 / (i kappa)
+};
+
+__device__ __forceinline__ double wat(const double* V0, const double* V1, int g) {
+    return 0.5 * (V0[g] + V1[g]);
+}
+
+// Scaled diagonal and coupling (i <-> i+1) of local node i of a subdomain with n nodes.
+__device__ __forceinline__ double2 tdep_diag(const double* V0, const double* V1, int g, int i,
+                                             int n, int tc, double h, double kappa,
+                                             double2 sig_ik) {
+    const double W0 = wat(V0, V1, g);
+    double md = 0.0, sd = 0.0, wd = 0.0;
+    if (i > 0) {
+        md += h / 3.0;
+        sd += 1.0 / h;
+        wd += h / 12.0 * (wat(V0, V1, g - 1) + 3.0 * W0);
+    }
+    if (i < n - 1) {
+        md += h / 3.0;
+        sd += 1.0 / h;
+        wd += h / 12.0 * (3.0 * W0 + wat(V0, V1, g + 1));
+    }
+    double2 D = make_double2(md / (h / 6.0), (sd - wd) / kappa);
+    if ((i == 0 && (tc & 1)) || (i == n - 1 && (tc & 2))) D = csub(D, sig_ik);
+    return D;
+}
+__device__ __forceinline__ double2 tdep_off(const double* V0, const double* V1, int g, double h,
+                                            double kappa) {
+    const double wo = h / 12.0 * (wat(V0, V1, g) + wat(V0, V1, g + 1));
+    return make_double2(1.0, -(1.0 / h + wo) / kappa);
+}
+
+template <int L>
+__global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
+    const MarchArgs& a = ta.m;
+    extern __shared__ double2 sm[];
+    const int T = a.T, G = a.G, P = a.P, C = a.C, nt = a.nt, levels = a.levels;
+    const int S = T + G;
+    double2* usep = sm;
+    // PCR buffers: set b (0/1), quantity q (0 lower, 1 diag, 2 upper, 3 rhs)
+    auto PC = [&](int b, int q) -> double2* { return usep + S * (1 + b * 4 + q); };
+    double2* cb = usep + S * 9;      // 8 per-chunk arrays of T
+    double2* ufst = cb;
+    double2* ulst = cb + T;
+    double2* yfst = cb + 2 * T;
+    double2* ylst = cb + 3 * T;
+    double2* afst = cb + 4 * T;
+    double2* bfst = cb + 5 * T;
+    double2* alst = cb + 6 * T;
+    double2* blst = cb + 7 * T;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (C > 1) ? (int)cl.block_rank() : 0;
+    const int tid = threadIdx.x;
+    int g, p, sidx;
+    if (C == 1) {
+        g = tid / (P + 1);
+        p = tid - g * (P + 1);
+        sidx = blockIdx.x * G + g;
+        if (g >= G) p = -1;
+    } else {
+        g = 0;
+        p = rank * T + tid;
+        sidx = blockIdx.x / C;
+        if (p > P) p = -1;
+    }
+    const bool valid = (p >= 0) && (sidx < a.nsys);
+    auto SEP = [&](double2* arr, int ps) -> double2* {
+        if (C == 1) return arr + g * (P + 1) + ps;
+        const int home = ps / T;
+        double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
+        return base + (ps - home * T);
+    };
+    auto CHK = [&](double2* arr, int pcn) -> double2* {
+        if (C == 1) return arr + g * P + pcn;
+        const int home = pcn / T;
+        double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
+        return base + (pcn - home * T);
+    };
+    auto SYNC = [&]() {
+        if (C == 1)
+            __syncthreads();
+        else
+            cl.sync();
+    };
+    const double2 zero = make_double2(0.0, 0.0);
+    MarchSys sy = {0, 0, -1, -1, -1, -1};
+    int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0, n = 0;
+    if (valid) {
+        sy = a.sys[sidx];
+        j = sy.sub;
+        Pj = a.sub_P[j];
+        goff = a.sub_goff[j];
+        tcf = a.sub_tc[j];
+        n = a.sub_n[j];
+        Lp = (p < P) ? a.clen[j * P + p] : 0;
+        sp = a.sep_pos[j * (P + 1) + p];
+    }
+    const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
+    const bool realsep = valid && (p <= Pj);
+    const double h = ta.h, kappa = ta.kappa;
+
+    double2 u[L], y[L], av[L], bv[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        u[i] = (valid && i < Lp && !zero_u0) ? a.u0[goff + sp + 1 + i] : zero;
+        y[i] = zero;
+        av[i] = zero;
+        bv[i] = zero;
+    }
+    if (valid) *SEP(usep, p) = (realsep && !zero_u0) ? a.u0[goff + sp] : zero;
+    SYNC();
+
+    double2 lin = zero, rin = zero;
+    for (int t = 1; t <= nt; ++t) {
+        const double* V0 = ta.V + (size_t)(t - 1) * ta.vstride;
+        const double* V1 = ta.V + (size_t)t * ta.vstride;
+        // ---- phase A: assemble, factor, local solve and spikes -----------------
+        if (valid && Lp > 0) {
+            const double2 uL = *SEP(usep, p), uR = *SEP(usep, p + 1);
+            const int g0 = goff + sp + 1;           // global index of the first interior node
+            double2 qv[L], cv[L];
+            double2 zprev = zero, zaprev = zero, cprev = zero, Eprev = zero, uf = zero, ul = zero;
+            const double2 Es = tdep_off(V0, V1, g0 - 1, h, kappa);
+            double2 Elast = zero;
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    const int li = sp + 1 + i;
+                    const double2 Di = tdep_diag(V0, V1, g0 + i, li, n, tcf, h, kappa, ta.sig_ik);
+                    const double2 Ei = tdep_off(V0, V1, g0 + i, h, kappa);   // i <-> i+1
+                    const double2 piv = (i == 0) ? Di : cfms(Eprev, cprev, Di);
+                    qv[i] = crcp(piv);
+                    cv[i] = (i < Lp - 1) ? cmul(Ei, qv[i]) : zero;
+                    if (i == Lp - 1) Elast = Ei;
+                    const double2 left = (i == 0) ? uL : u[i - 1];
+                    double2 right;
+                    if (i + 1 < L)
+                        right = (i == Lp - 1) ? uR : u[i + 1];
+                    else
+                        right = uR;
+                    const double2 f = make_double2(fma(4.0, u[i].x, left.x + right.x),
+                                                   fma(4.0, u[i].y, left.y + right.y));
+                    const double2 z = (i == 0) ? f : cfms(cprev, zprev, f);
+                    const double2 za = (i == 0) ? Es : cfms(cprev, zaprev, zero);
+                    y[i] = z;
+                    av[i] = za;
+                    zprev = z;
+                    zaprev = za;
+                    cprev = cv[i];
+                    Eprev = Ei;
+                    if (i == 0) uf = u[i];
+                    if (i == Lp - 1) ul = u[i];
+                }
+            }
+            double2 yn = zero, an = zero, bn = zero;
+#pragma unroll
+            for (int i = L - 1; i >= 0; --i) {
+                if (i < Lp) {
+                    double2 yi = cmul(qv[i], y[i]), ai = cmul(qv[i], av[i]), bi;
+                    if (i == Lp - 1) {
+                        bi = cmul(qv[i], Elast);
+                    } else {
+                        yi = cfms(cv[i], yn, yi);
+                        ai = cfms(cv[i], an, ai);
+                        bi = cfms(cv[i], bn, zero);
+                    }
+                    y[i] = yi;
+                    av[i] = ai;
+                    bv[i] = bi;
+                    yn = yi;
+                    an = ai;
+                    bn = bi;
+                }
+            }
+            *CHK(ufst, p) = uf;
+            *CHK(ulst, p) = ul;
+            *CHK(yfst, p) = y[0];
+            double2 yl = zero, al = zero, bl = zero;
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i == Lp - 1) {
+                    yl = y[i];
+                    al = av[i];
+                    bl = bv[i];
+                }
+            *CHK(ylst, p) = yl;
+            *CHK(afst, p) = av[0];
+            *CHK(bfst, p) = bv[0];
+            *CHK(alst, p) = al;
+            *CHK(blst, p) = bl;
+        }
+        SYNC();
+        // ---- phase B: separator row of the reduced system ----------------------
+        if (valid) {
+            double2 lo = zero, dg = make_double2(1.0, 0.0), up = zero, r = zero;
+            if (realsep) {
+                const int gs = goff + sp;
+                const bool le = (p == 0), re = (p == Pj);
+                const double2 us = *SEP(usep, p);
+                const double2 um = le ? zero : *CHK(ulst, p - 1);
+                const double2 upv = re ? zero : *CHK(ufst, p);
+                double2 f;
+                if (le)
+                    f = make_double2(fma(2.0, us.x, upv.x), fma(2.0, us.y, upv.y));
+                else if (re)
+                    f = make_double2(fma(2.0, us.x, um.x), fma(2.0, us.y, um.y));
+                else
+                    f = make_double2(fma(4.0, us.x, um.x + upv.x), fma(4.0, us.y, um.y + upv.y));
+                if (le && (tcf & 1)) {
+                    if (sy.flags & SYS_IMP_L)
+                        lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                    else
+                        lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
+                    f = cfms(lin, a.inv_ik, f);
+                }
+                if (re && (tcf & 2)) {
+                    if (sy.flags & SYS_IMP_R)
+                        rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                    else
+                        rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
+                    f = cfms(rin, a.inv_ik, f);
+                }
+                dg = tdep_diag(V0, V1, gs, sp, n, tcf, h, kappa, ta.sig_ik);
+                r = f;
+                if (!le) {
+                    const double2 EL = tdep_off(V0, V1, gs - 1, h, kappa);
+                    dg = cfms(EL, *CHK(blst, p - 1), dg);
+                    lo = cmul(make_double2(-EL.x, -EL.y), *CHK(alst, p - 1));
+                    r = cfms(EL, *CHK(ylst, p - 1), r);
+                }
+                if (!re) {
+                    const double2 ER = tdep_off(V0, V1, gs, h, kappa);
+                    dg = cfms(ER, *CHK(afst, p), dg);
+                    up = cmul(make_double2(-ER.x, -ER.y), *CHK(bfst, p));
+                    r = cfms(ER, *CHK(yfst, p), r);
+                }
+            }
+            *SEP(PC(0, 0), p) = lo;
+            *SEP(PC(0, 1), p) = dg;
+            *SEP(PC(0, 2), p) = up;
+            *SEP(PC(0, 3), p) = r;
+        }
+        SYNC();
+        // ---- phase C: PCR with coefficient updates -----------------------------
+        int cur = 0;
+        for (int k = 0; k < levels; ++k) {
+            const int st = 1 << k;
+            if (valid) {
+                double2 l0 = *SEP(PC(cur, 0), p), d0 = *SEP(PC(cur, 1), p);
+                double2 u0v = *SEP(PC(cur, 2), p), r0 = *SEP(PC(cur, 3), p);
+                double2 nl = zero, nu = zero, nd = d0, nr = r0;
+                if (p - st >= 0) {
+                    const double2 al = cmul(make_double2(-l0.x, -l0.y), crcp(*SEP(PC(cur, 1), p - st)));
+                    nl = cmul(al, *SEP(PC(cur, 0), p - st));
+                    nd = cfma(al, *SEP(PC(cur, 2), p - st), nd);
+                    nr = cfma(al, *SEP(PC(cur, 3), p - st), nr);
+                }
+                if (p + st <= P) {
+                    const double2 ga = cmul(make_double2(-u0v.x, -u0v.y), crcp(*SEP(PC(cur, 1), p + st)));
+                    nu = cmul(ga, *SEP(PC(cur, 2), p + st));
+                    nd = cfma(ga, *SEP(PC(cur, 0), p + st), nd);
+                    nr = cfma(ga, *SEP(PC(cur, 3), p + st), nr);
+                }
+                *SEP(PC(cur ^ 1, 0), p) = nl;
+                *SEP(PC(cur ^ 1, 1), p) = nd;
+                *SEP(PC(cur ^ 1, 2), p) = nu;
+                *SEP(PC(cur ^ 1, 3), p) = (k == levels - 1) ? cmul(nr, crcp(nd)) : nr;
+            }
+            SYNC();
+            cur ^= 1;
+        }
+        double2* vs = PC(cur, 3);
+        // ---- phase D: spike correction, CN update, fluxes ----------------------
+        if (valid && Lp > 0) {
+            const double2 vL = *SEP(vs, p), vR = *SEP(vs, p + 1);
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    double2 v = cfms(av[i], vL, y[i]);
+                    v = cfms(bv[i], vR, v);
+                    u[i] = make_double2(fma(2.0, v.x, -u[i].x), fma(2.0, v.y, -u[i].y));
+                }
+            }
+        }
+        if (realsep) {
+            const double2 v = *SEP(vs, p);
+            double2* us = SEP(usep, p);
+            const double2 uo = *us;
+            *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
+            if (p == 0) {
+                if ((tcf & 1) && sy.out_a >= 0 && a.gout)
+                    a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
+            }
+            if (p == Pj) {
+                if ((tcf & 2) && sy.out_b >= 0 && a.gout)
+                    a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
+            }
+        }
+        SYNC();
+    }
+    bool bad = false;
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < Lp) bad |= !cfinite(u[i]);
+        if ((sy.flags & SYS_WRITE_UT) && a.uT) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.uT[goff + sp + 1 + i] = u[i];
+        }
+        if (realsep) {
+            const double2 us = *SEP(usep, p);
+            bad |= !cfinite(us);
+            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || j == 0)) a.uT[goff + sp] = us;
+        }
+    }
+    if (bad) atomicOr(a.status, ST_NONFINITE);
+    if (C > 1) cl.sync();
+}
+
+int swr_march_tdep_smem_bytes(int T, int G) { return (int)sizeof(double2) * (9 * (T + G) + 8 * T); }
+
+template <int L>
+static int launch_tdep_t(TdepArgs ta, int ngroups, cudaStream_t s) {
+    const int smem = swr_march_tdep_smem_bytes(ta.m.T, ta.m.G);
+    auto kern = k_march_tdep<L>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -1;
+    if (ta.m.C > 8 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return -1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ngroups * ta.m.C);
+    cfg.blockDim = dim3(ta.m.T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ta.m.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    swr_count_launch(1);
+    return cudaLaunchKernelEx(&cfg, kern, ta) == cudaSuccess ? 0 : -1;
+}
+
+int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, long long vstride,
+                          double h, double kappa, double2 sig_ik, int ngroups, cudaStream_t s) {
+    a.P = fs.P;
+    a.levels = fs.levels;
+    a.sub_P = fs.sub_P;
+    a.sep_pos = fs.sep_pos;
+    a.clen = fs.clen;
+    a.fac = nullptr;
+    a.sep = nullptr;
+    a.pcr = nullptr;
+    TdepArgs ta{a, V, vstride, h, kappa, sig_ik};
+    switch (fs.L) {
+        case 4: return launch_tdep_t<4>(ta, ngroups, s);
+        case 8: return launch_tdep_t<8>(ta, ngroups, s);
+        default: return -2;
+    }
 }
 
 template <int L>

@@ -22,7 +22,7 @@ SWR_ERR_STATE, SWR_ERR_UNSUPPORTED = 8, 9
 SWR_V_STATIC, SWR_V_TIME, SWR_V_NONLINEAR = 0, 1, 2
 SWR_TC_ROBIN, SWR_TC_S02 = 0, 1
 SWR_SOLVER_GMRES, SWR_SOLVER_FIXED_POINT, SWR_SOLVER_CLASSICAL = 0, 1, 2
-SWR_PC_NONE, SWR_PC_ZERO_POTENTIAL, SWR_PC_CAUSAL = 0, 1, 2
+SWR_PC_NONE, SWR_PC_ZERO_POTENTIAL, SWR_PC_CAUSAL, SWR_PC_MEAN_POTENTIAL = 0, 1, 2, 3
 
 
 class swr_desc(ctypes.Structure):

@@ -214,3 +214,16 @@ def _mono_cache(nsub, wl):
     if nsub not in _MONO:
         _MONO[nsub] = O.mono_interface(problem(wl))
     return _MONO[nsub]
+
+
+@pytest.mark.parametrize("vkind", [0, 1])
+def test_solve_with_null_outputs(vkind):
+    """g and uT may be NULL in swr_solve (include/swr.h): nothing is written
+    through them and the solve still reports its residual."""
+    from paper_1503_02564_gb300 import swr
+    wl = W.config1(nx=241, nt=30, nsub=4) if vkind == 0 else W.config4(nsub=4, nx=801, nt=20)
+    plan = gpu_plan(wl, restart=100, maxit=400)
+    info = plan.solve(None, False, None, allow_not_converged=True)
+    plan.destroy()
+    assert info["status"] in (swr.SWR_OK, swr.SWR_ERR_NOT_CONVERGED)
+    assert np.isfinite(info["residual"])

@@ -56,7 +56,9 @@ enum { SWR_V_STATIC = 0, SWR_V_TIME = 1, SWR_V_NONLINEAR = 2 };
 enum { SWR_TC_ROBIN = 0, SWR_TC_S02 = 1 };
 /* Interface solvers: GMRES (Algorithms 2-3), fixed point on (I - L) g = d
  * (Algorithm 3 with the fixed point), classical iteration g <- R g with full
- * marches (Algorithm 1). */
+ * marches (Algorithm 1).  For SWR_V_NONLINEAR the interface operator R_nl is
+ * nonlinear: FIXED_POINT runs g <- g - P^{-1}(g - R_nl g) with the plan's
+ * preconditioner (Section 5), CLASSICAL runs g <- R_nl g, GMRES is rejected. */
 enum { SWR_SOLVER_GMRES = 0, SWR_SOLVER_FIXED_POINT = 1, SWR_SOLVER_CLASSICAL = 2 };
 /* Preconditioners for GMRES (right preconditioning):
  *   NONE;

@@ -166,6 +166,7 @@ swr_status read_status(swr_plan_t p) {
     if (st & ST_SINGULAR) return SWR_ERR_SINGULAR;
     if (st & ST_NONFINITE) return SWR_ERR_NONFINITE;
     if (st & ST_TIMEOUT) return SWR_ERR_TIMEOUT;
+    if (st & ST_NL_NOCONV) return SWR_ERR_NOT_CONVERGED;
     return SWR_OK;
 }
 
@@ -181,14 +182,20 @@ struct MarchCfg {
 
 inline int chunks_for(int nmax, int L) { return (nmax - 1 + L) / (L + 1); }
 
-MarchCfg march_config(const swr_plan_t p, int nsys, bool tdep = false) {
+enum { MK_STATIC = 0, MK_TDEP = 1, MK_NL = 2 };   // march kernel kinds
+
+MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
     MarchCfg c;
     const int nsm = p->nsm;
     const long long want = (long long)nsm * 4 * 32;
     const int cand[3] = {16, 8, 4};
+    const bool tdep = (kind != MK_STATIC);        // kernels limited to 256 threads
     int L = 4;
-    if (tdep) {
+    if (kind == MK_TDEP) {
         L = 4;   // per-step refactorisation keeps LU, spikes and state in registers
+    } else if (kind == MK_NL) {
+        // state, right-hand side, iterate and solve per node in registers: L <= 8
+        L = ((long long)(chunks_for(p->nmax, 8) + 1) * nsys >= want) ? 8 : 4;
     } else if (p->forceL) {
         L = p->forceL;
     } else {
@@ -244,7 +251,8 @@ swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, i
                      const double2* u0, long long work) {
     MarchArgs a{};
     const bool tdep = (p->d.vkind == SWR_V_TIME) && !zero_potential;
-    const MarchCfg cfg = march_config(p, nsys, tdep);
+    const bool nl = (p->d.vkind == SWR_V_NONLINEAR) && !zero_potential;
+    const MarchCfg cfg = march_config(p, nsys, tdep ? MK_TDEP : (nl ? MK_NL : MK_STATIC));
     const int C = cfg.C, G = cfg.G, T = cfg.T, ng = cfg.ngroups;
     if (C > 16) return SWR_ERR_UNSUPPORTED;
     const FactorSet& fs = zero_potential ? p->fs0L[lidx(cfg.L)] : p->fsL[lidx(cfg.L)];
@@ -267,12 +275,18 @@ swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, i
     a.inv_ik = p->inv_ik;
     a.status = p->d_status;
     const int pi = prof_begin(p, 0, work);
-    const int rc = tdep ? swr_launch_march_tdep(fs, a, p->d_V, p->nx, p->h,
-                                                2.0 / p->d.dt * (p->h / 6.0),
-                                                cmul_h(p->sigma0, p->inv_ik), ng, p->s)
-                        : swr_launch_march(fs, a, ng, p->s);
+    const double kappa = 2.0 / p->d.dt * (p->h / 6.0);
+    int rc;
+    if (tdep)
+        rc = swr_launch_march_tdep(fs, a, p->d_V, p->nx, p->h, kappa,
+                                   cmul_h(p->sigma0, p->inv_ik), ng, p->s);
+    else if (nl)
+        rc = swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
+                                 p->d.nl_maxit, nullptr, ng, p->s);
+    else
+        rc = swr_launch_march(fs, a, ng, p->s);
     prof_end(p, pi);
-    if (rc != 0) return launch_fail(tdep ? "march (time-dependent)" : "march", __LINE__);
+    if (rc != 0) return launch_fail(tdep ? "march (time-dependent)" : (nl ? "march (nonlinear)" : "march"), __LINE__);
     return SWR_OK;
 }
 
@@ -555,6 +569,43 @@ swr_status fixed_point(swr_plan_t p, double2* g, bool g_init, bool classical, sw
     return diff < p->d.tol_abs ? SWR_OK : SWR_ERR_NOT_CONVERGED;
 }
 
+// Nonlinear potential (Section 5): g^{k+1} = g^k - P^{-1}(g^k - R_nl g^k) with the
+// plan's preconditioner (reading of Eq. chp2_algopd_NL), or g^{k+1} = R_nl g^k
+// without one (Algorithm 1); stop when ||g^{k+1} - g^k||_2 < tol.
+swr_status nl_fixed_point(swr_plan_t p, double2* g, bool g_init, swr_info* info) {
+    swr_status st = ensure_workspace(p);
+    if (st) return st;
+    Workspace& w = p->ws;
+    const long long n = w.n;
+    const bool pc = has_precond(p) && p->d.solver != SWR_SOLVER_CLASSICAL;
+    if (!g_init) CK(cudaMemsetAsync(g, 0, sizeof(double2) * n, p->s));
+    double diff = INFINITY;
+    int it = 0;
+    while (it < p->d.maxit) {
+        if ((st = run_march(p, false, p->d_sys_R, p->N, g, w.z, nullptr, nullptr, p->d_u0,
+                            p->work_R)))
+            return st;
+        // r = g - R_nl g
+        CK(cudaMemcpyAsync(w.r, g, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+        LK(swr_launch_axpby(w.r, w.z, n, make_double2(1.0, 0.0), make_double2(-1.0, 0.0), p->s));
+        const double2* dx = w.r;
+        if (pc) {
+            if ((st = apply_M(p, w.r, w.w))) return st;
+            dx = w.w;
+        }
+        LK(swr_launch_axpby(g, dx, n, make_double2(1.0, 0.0), make_double2(-1.0, 0.0), p->s));
+        if ((st = norm2(p, dx, n, &diff))) return st;
+        ++it;
+        if (!std::isfinite(diff)) return SWR_ERR_NONFINITE;
+        if (diff < p->d.tol_abs) break;
+    }
+    if (info) {
+        info->iterations = it;
+        info->residual = diff;
+    }
+    return diff < p->d.tol_abs ? SWR_OK : SWR_ERR_NOT_CONVERGED;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -613,8 +664,8 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
         return SWR_ERR_ARG;
     if (d->vkind < 0 || d->vkind > 2 || d->tc != SWR_TC_ROBIN) return d->tc == SWR_TC_S02 ? SWR_ERR_UNSUPPORTED : SWR_ERR_ARG;
     if (d->solver < 0 || d->solver > 2 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
-    if (d->vkind == SWR_V_NONLINEAR) return SWR_ERR_UNSUPPORTED;
-    if (d->vkind != SWR_V_STATIC && d->solver == SWR_SOLVER_FIXED_POINT) return SWR_ERR_ARG;
+    if (d->vkind == SWR_V_NONLINEAR && d->solver == SWR_SOLVER_GMRES) return SWR_ERR_ARG;
+    if (d->vkind == SWR_V_TIME && d->solver == SWR_SOLVER_FIXED_POINT) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_TIME && (long long)(d->nt + 1) * d->nx > (1LL << 31)) return SWR_ERR_ARG;
     if (d->precond == SWR_PC_CAUSAL && d->vkind != SWR_V_STATIC) return SWR_ERR_ARG;
     swr_plan_t p = new (std::nothrow) swr_plan_s();
@@ -757,6 +808,10 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
         st = run_march(p, false, p->d_sys_build, p->N, nullptr, p->d_iface, nullptr, nullptr,
                        p->d_u0, p->work_R);
         if (st) return st;
+    } else if (p->d.vkind == SWR_V_NONLINEAR) {
+        // constant matrix (2i/dt) M - S + M_{V0} - B: factor once (Eq. AvMNL)
+        const int La = march_config(p, p->N, MK_NL).L;
+        if ((st = factor_for(p, p->fsL[lidx(La)], La, p->d_V, p->d_dg, p->d_od))) return st;
     } else {
         // factorisations for the chunk lengths the marches of this plan will use
         const int Lb = march_config(p, p->nsys_build).L, La = march_config(p, p->N).L;
@@ -806,9 +861,12 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     swr_info loc{};
     double2* g = g_ ? reinterpret_cast<double2*>(g_) : p->d_gtmp2;
     const bool init = g_ && g_is_initial;
+    CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
     CK(cudaEventRecord(p->ev[1], s));
     swr_status st;
-    if (p->d.solver == SWR_SOLVER_GMRES)
+    if (p->d.vkind == SWR_V_NONLINEAR)
+        st = nl_fixed_point(p, g, init, &loc);
+    else if (p->d.solver == SWR_SOLVER_GMRES)
         st = gmres(p, g, init, &loc);
     else
         st = fixed_point(p, g, init, p->d.solver == SWR_SOLVER_CLASSICAL, &loc);

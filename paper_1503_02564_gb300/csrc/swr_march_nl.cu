@@ -1,0 +1,443 @@
+// Nonlinear subdomain march (Besse & Xing, Eq. CNS_NL / AvMNL): the Durán–Sanz-Serna
+// scheme with f(v) = c |v|^2 on top of a static potential V0.  The matrix
+// (2i/dt) M - S + M_{V0} - B is constant, so the chunked factorisation of the
+// static march is reused; every time step runs the fixed point
+//     (A - B) zeta^{s+1} = (2i/dt) M u_{n-1} - b_f(zeta^s) - Q^T (l_n, r_n)^T,
+//     zeta^0 = v_{n-1},   b_f(zeta) = M_{c|zeta|^2} zeta,
+// until max |zeta^{s+1} - zeta^s| <= tol max(1, max |zeta^s|) over the subdomain
+// (checked per system with shared-memory, or cluster, max-reductions), then
+// v_n = zeta, u_n = 2 v_n - u_{n-1}.  Each inner iteration is one partitioned
+// solve (chunk LU sweeps, separator PCR with precomputed coefficients, spike
+// correction) with the generalised-mass term recomputed from the iterate.
+#include <cooperative_groups.h>
+
+#include "swr_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+struct NlArgs {
+    MarchArgs m;
+    double cw;        // (h/12)/kappa: scale of b_f after the 1/(i kappa) pre-scaling
+    double coef;      // f(u) = coef |u|^2
+    double tol;       // inner tolerance
+    int maxit;        // inner cap
+    int* iters;       // optional: max inner iterations over steps, per system
+};
+
+// sum of the P1 element weights times zeta around a node: s such that
+// b_f = (h/12) s; W = coef |zeta|^2 at the three nodes (left/right may be absent)
+__device__ __forceinline__ double2 bf_sum(bool hasl, bool hasr, double2 zl, double2 z0,
+                                          double2 zr, double Wl, double W0, double Wr) {
+    double2 s = make_double2(0.0, 0.0);
+    if (hasl) {
+        const double a = Wl + 3.0 * W0, b = Wl + W0;
+        s.x = fma(a, z0.x, fma(b, zl.x, s.x));
+        s.y = fma(a, z0.y, fma(b, zl.y, s.y));
+    }
+    if (hasr) {
+        const double a = 3.0 * W0 + Wr, b = W0 + Wr;
+        s.x = fma(a, z0.x, fma(b, zr.x, s.x));
+        s.y = fma(a, z0.y, fma(b, zr.y, s.y));
+    }
+    return s;
+}
+// rhs - s * (h/12) / (i kappa) = rhs - s * (-i cw) = rhs + (-cw s.y, cw s.x)
+__device__ __forceinline__ double2 sub_bf(double2 rhs, double2 s, double cw) {
+    return make_double2(fma(-cw, s.y, rhs.x), fma(cw, s.x, rhs.y));
+}
+__device__ __forceinline__ double nrm2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ unsigned long long dbits(double v) {
+    return (unsigned long long)__double_as_longlong(v);
+}
+
+int swr_march_nl_smem_bytes(int T, int G) {
+    return (int)sizeof(double2) * (4 * (T + G) + 6 * T) + (int)sizeof(unsigned long long) * (4 * G + 4);
+}
+
+template <int L>
+__global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
+    const MarchArgs& a = na.m;
+    extern __shared__ double2 sm[];
+    const int T = a.T, G = a.G, P = a.P, C = a.C, nt = a.nt, levels = a.levels;
+    const int S = T + G;
+    double2* usep = sm;
+    double2* zsep = sm + S;
+    double2* dA = sm + 2 * S;
+    double2* dB = sm + 3 * S;
+    double2* ufst = sm + 4 * S;
+    double2* ulst = ufst + T;
+    double2* zfst = ulst + T;
+    double2* zlst = zfst + T;
+    double2* yfst = zlst + T;
+    double2* ylst = yfst + T;
+    // reductions: red[slot][g][0] = max |dz|^2, red[slot][g][1] = max |z|^2; cnt[slot]
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(ylst + T);
+    unsigned long long* cnt = red + 4 * G;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (C > 1) ? (int)cl.block_rank() : 0;
+    const int tid = threadIdx.x;
+    int g, p, sidx;
+    if (C == 1) {
+        g = tid / (P + 1);
+        p = tid - g * (P + 1);
+        sidx = blockIdx.x * G + g;
+        if (g >= G) p = -1;
+    } else {
+        g = 0;
+        p = rank * T + tid;
+        sidx = blockIdx.x / C;
+        if (p > P) p = -1;
+    }
+    const bool valid = (p >= 0) && (sidx < a.nsys);
+    auto SEP = [&](double2* arr, int ps) -> double2* {
+        if (C == 1) return arr + g * (P + 1) + ps;
+        const int home = ps / T;
+        double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
+        return base + (ps - home * T);
+    };
+    auto CHK = [&](double2* arr, int pc) -> double2* {
+        if (C == 1) return arr + g * P + pc;
+        const int home = pc / T;
+        double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
+        return base + (pc - home * T);
+    };
+    // reductions live in the CTA of rank 0 when a system spans a cluster
+    auto RED = [&](int slot, int q) -> unsigned long long* {
+        unsigned long long* base = (C == 1 || rank == 0) ? red : cl.map_shared_rank(red, 0);
+        return base + (slot * G + g) * 2 + q;
+    };
+    auto CNT = [&](int slot) -> unsigned long long* {
+        unsigned long long* base = (C == 1 || rank == 0) ? cnt : cl.map_shared_rank(cnt, 0);
+        return base + slot;
+    };
+    auto SYNC = [&]() {
+        if (C == 1)
+            __syncthreads();
+        else
+            cl.sync();
+    };
+    const double2 zero = make_double2(0.0, 0.0);
+    MarchSys sy = {0, 0, -1, -1, -1, -1};
+    int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0;
+    if (valid) {
+        sy = a.sys[sidx];
+        j = sy.sub;
+        Pj = a.sub_P[j];
+        goff = a.sub_goff[j];
+        tcf = a.sub_tc[j];
+        Lp = (p < P) ? a.clen[j * P + p] : 0;
+        sp = a.sep_pos[j * (P + 1) + p];
+    }
+    const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
+    const bool realsep = valid && (p <= Pj);
+    const double2* F = a.fac + (size_t)j * L * 4 * P + (p < P ? p : 0);
+    const double2* sE_l = a.sep + (size_t)(j * 3 + 0) * (P + 1);
+    const double2* sE_r = a.sep + (size_t)(j * 3 + 1) * (P + 1);
+    const double2* sbinv = a.sep + (size_t)(j * 3 + 2) * (P + 1);
+    const double2* pcr = a.pcr + (size_t)j * levels * 2 * (P + 1);
+    const double cw = na.cw, coef = na.coef;
+
+    double2 u[L], z[L], f[L], y[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        u[i] = (valid && i < Lp && !zero_u0) ? a.u0[goff + sp + 1 + i] : zero;
+        z[i] = u[i];                                  // zeta^0 of step 1 is v_0 = u_0
+        f[i] = zero;
+        y[i] = zero;
+    }
+    if (valid) {
+        const double2 u0s = (realsep && !zero_u0) ? a.u0[goff + sp] : zero;
+        *SEP(usep, p) = u0s;
+        *SEP(zsep, p) = u0s;
+    }
+    for (int q = tid; q < 4 * G + 4; q += blockDim.x) red[q] = 0ull;   // slots and counters
+    SYNC();
+
+    double2 lin = zero, rin = zero, fs = zero;
+    int itmax = 0;
+    bool nl_fail = false;
+    for (int t = 1; t <= nt; ++t) {
+        // ---- step-constant right-hand side (2i/dt) M u_{n-1} - fluxes, scaled ----
+        if (valid && Lp > 0) {
+            const double2 uL = *SEP(usep, p), uR = *SEP(usep, p + 1);
+            double2 uf = zero, ul = zero;
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    const double2 left = (i == 0) ? uL : u[i - 1];
+                    double2 right;
+                    if (i + 1 < L)
+                        right = (i == Lp - 1) ? uR : u[i + 1];
+                    else
+                        right = uR;
+                    f[i] = make_double2(fma(4.0, u[i].x, left.x + right.x),
+                                        fma(4.0, u[i].y, left.y + right.y));
+                    if (i == 0) uf = u[i];
+                    if (i == Lp - 1) ul = u[i];
+                }
+            }
+            *CHK(ufst, p) = uf;
+            *CHK(ulst, p) = ul;
+        }
+        // reduction slot 0 serves the first inner iteration of this step
+        if (valid && p == 0) {
+            *RED(0, 0) = 0ull;
+            *RED(0, 1) = 0ull;
+        }
+        if (tid == 0 && (C == 1 || rank == 0)) *CNT(0) = 0ull;
+        SYNC();
+        if (realsep) {
+            const double2 us = *SEP(usep, p);
+            const bool le = (p == 0), re = (p == Pj);
+            const double2 um = le ? zero : *CHK(ulst, p - 1);
+            const double2 up = re ? zero : *CHK(ufst, p);
+            if (le)
+                fs = make_double2(fma(2.0, us.x, up.x), fma(2.0, us.y, up.y));
+            else if (re)
+                fs = make_double2(fma(2.0, us.x, um.x), fma(2.0, us.y, um.y));
+            else
+                fs = make_double2(fma(4.0, us.x, um.x + up.x), fma(4.0, us.y, um.y + up.y));
+            if (le && (tcf & 1)) {
+                if (sy.flags & SYS_IMP_L)
+                    lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                else
+                    lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
+                fs = cfms(lin, a.inv_ik, fs);
+            }
+            if (re && (tcf & 2)) {
+                if (sy.flags & SYS_IMP_R)
+                    rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                else
+                    rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
+                fs = cfms(rin, a.inv_ik, fs);
+            }
+        }
+        // ---- inner fixed point (Eq. AvMNL) ------------------------------------
+        bool active = valid;
+        int used = na.maxit;
+        for (int it = 0; it < na.maxit; ++it) {
+            const int slot = it & 1, nslot = slot ^ 1;
+            if (valid && Lp > 0) {
+                double2 zf = zero, zl = zero;
+#pragma unroll
+                for (int i = 0; i < L; ++i) {
+                    if (i == 0) zf = z[i];
+                    if (i == Lp - 1) zl = z[i];
+                }
+                *CHK(zfst, p) = zf;
+                *CHK(zlst, p) = zl;
+            }
+            SYNC();
+            if (valid && p == 0) {
+                *RED(nslot, 0) = 0ull;
+                *RED(nslot, 1) = 0ull;
+            }
+            if (tid == 0 && (C == 1 || rank == 0)) *CNT(nslot) = 0ull;
+            // chunk: right-hand side with b_f(zeta), local LU sweeps
+            if (active && Lp > 0) {
+                const double2 zL = *SEP(zsep, p), zR = *SEP(zsep, p + 1);
+                double Wprev = coef * nrm2(zL);
+                double W0 = coef * nrm2(z[0]);
+                double2 zprev = zero, cprev = zero;
+#pragma unroll
+                for (int i = 0; i < L; ++i) {
+                    if (i < Lp) {
+                        const double2 zl_ = (i == 0) ? zL : z[i - 1];
+                        double2 zr_;
+                        if (i + 1 < L)
+                            zr_ = (i == Lp - 1) ? zR : z[i + 1];
+                        else
+                            zr_ = zR;
+                        const double Wr = coef * nrm2(zr_);
+                        const double2 rhs = sub_bf(f[i], bf_sum(true, true, zl_, z[i], zr_, Wprev, W0, Wr), cw);
+                        const double2 zz = (i == 0) ? rhs : cfms(cprev, zprev, rhs);
+                        y[i] = zz;
+                        zprev = zz;
+                        cprev = F[(i * 4 + 1) * P];
+                        Wprev = W0;
+                        W0 = Wr;
+                    }
+                }
+                double2 ynext = zero, yl = zero;
+#pragma unroll
+                for (int i = L - 1; i >= 0; --i) {
+                    if (i < Lp) {
+                        double2 yi = cmul(F[(i * 4 + 0) * P], y[i]);
+                        if (i != Lp - 1) yi = cfms(F[(i * 4 + 1) * P], ynext, yi);
+                        else yl = yi;
+                        y[i] = yi;
+                        ynext = yi;
+                    }
+                }
+                *CHK(yfst, p) = y[0];
+                *CHK(ylst, p) = yl;
+            }
+            SYNC();
+            // separator: reduced right-hand side
+            if (valid) {
+                double2 d = zero;
+                if (active && realsep) {
+                    const bool hasl = (p > 0), hasr = (p < Pj);
+                    const double2 zs = *SEP(zsep, p);
+                    const double2 zl_ = hasl ? *CHK(zlst, p - 1) : zero;
+                    const double2 zr_ = hasr ? *CHK(zfst, p) : zero;
+                    const double2 sb = bf_sum(hasl, hasr, zl_, zs, zr_, coef * nrm2(zl_),
+                                              coef * nrm2(zs), coef * nrm2(zr_));
+                    d = sub_bf(fs, sb, cw);
+                    if (hasl) d = cfms(sE_l[p], *CHK(ylst, p - 1), d);
+                    if (hasr) d = cfms(sE_r[p], *CHK(yfst, p), d);
+                }
+                *SEP(dA, p) = d;
+            }
+            SYNC();
+            double2* src = dA;
+            double2* dst = dB;
+            for (int k = 0; k < levels; ++k) {
+                const int st = 1 << k;
+                if (valid) {
+                    const double2* al = pcr + (size_t)(k * 2 + 0) * (P + 1);
+                    const double2* ga = pcr + (size_t)(k * 2 + 1) * (P + 1);
+                    double2 dd = *SEP(src, p);
+                    if (p - st >= 0) dd = cfma(al[p], *SEP(src, p - st), dd);
+                    if (p + st <= P) dd = cfma(ga[p], *SEP(src, p + st), dd);
+                    if (k == levels - 1) dd = cmul(dd, sbinv[p]);
+                    *SEP(dst, p) = dd;
+                }
+                SYNC();
+                double2* tmp = src;
+                src = dst;
+                dst = tmp;
+            }
+            // correction, change of the iterate, per-system max reductions
+            double dmax = 0.0, zmax = 0.0;
+            double2 zsn = zero;
+            if (active && Lp > 0) {
+                const double2 vL = *SEP(src, p), vR = *SEP(src, p + 1);
+#pragma unroll
+                for (int i = 0; i < L; ++i) {
+                    if (i < Lp) {
+                        double2 v = cfms(F[(i * 4 + 2) * P], vL, y[i]);
+                        v = cfms(F[(i * 4 + 3) * P], vR, v);
+                        dmax = fmax(dmax, nrm2(csub(v, z[i])));
+                        zmax = fmax(zmax, nrm2(z[i]));
+                        y[i] = v;                       // new iterate, kept in y
+                    }
+                }
+            }
+            if (active && realsep) {
+                zsn = *SEP(src, p);
+                const double2 zs = *SEP(zsep, p);
+                dmax = fmax(dmax, nrm2(csub(zsn, zs)));
+                zmax = fmax(zmax, nrm2(zs));
+            }
+            if (active) {
+                atomicMax(RED(slot, 0), dbits(dmax));
+                atomicMax(RED(slot, 1), dbits(zmax));
+            }
+            SYNC();
+            if (active) {
+                const double dm = __longlong_as_double((long long)*RED(slot, 0));
+                const double zm = __longlong_as_double((long long)*RED(slot, 1));
+#pragma unroll
+                for (int i = 0; i < L; ++i)
+                    if (i < Lp) z[i] = y[i];
+                if (realsep) *SEP(zsep, p) = zsn;
+                if (dm <= na.tol * na.tol * fmax(1.0, zm)) {
+                    active = false;
+                    used = it + 1;
+                } else if (p == 0) {
+                    atomicAdd(CNT(slot), 1ull);
+                }
+            }
+            SYNC();
+            if (*CNT(slot) == 0ull) break;
+        }
+        if (active) nl_fail = true;      // cap reached without convergence
+        if (valid && used > itmax) itmax = used;
+        // ---- v_n = zeta: CN update and fluxes ---------------------------------
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (valid && i < Lp) u[i] = make_double2(fma(2.0, z[i].x, -u[i].x), fma(2.0, z[i].y, -u[i].y));
+        if (realsep) {
+            const double2 v = *SEP(zsep, p);
+            double2* us = SEP(usep, p);
+            const double2 uo = *us;
+            *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
+            if (p == 0) {
+                if ((tcf & 1) && sy.out_a >= 0 && a.gout)
+                    a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
+            }
+            if (p == Pj) {
+                if ((tcf & 2) && sy.out_b >= 0 && a.gout)
+                    a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
+            }
+        }
+        SYNC();
+    }
+    bool bad = false;
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < Lp) bad |= !cfinite(u[i]);
+        if ((sy.flags & SYS_WRITE_UT) && a.uT) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.uT[goff + sp + 1 + i] = u[i];
+        }
+        if (realsep) {
+            const double2 us = *SEP(usep, p);
+            bad |= !cfinite(us);
+            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || j == 0)) a.uT[goff + sp] = us;
+        }
+        if (p == 0 && na.iters) atomicMax(na.iters + sidx, itmax);
+    }
+    if (bad) atomicOr(a.status, ST_NONFINITE);
+    if (nl_fail) atomicOr(a.status, ST_NL_NOCONV);
+    if (C > 1) cl.sync();
+}
+
+template <int L>
+static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s) {
+    const int smem = swr_march_nl_smem_bytes(na.m.T, na.m.G);
+    auto kern = k_march_nl<L>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -1;
+    if (na.m.C > 8 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return -1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ngroups * na.m.C);
+    cfg.blockDim = dim3(na.m.T);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = na.m.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    swr_count_launch(1);
+    return cudaLaunchKernelEx(&cfg, kern, na) == cudaSuccess ? 0 : -1;
+}
+
+int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef, double tol,
+                        int maxit, int* iters, int ngroups, cudaStream_t s) {
+    a.P = fs.P;
+    a.levels = fs.levels;
+    a.sub_P = fs.sub_P;
+    a.sep_pos = fs.sep_pos;
+    a.clen = fs.clen;
+    a.fac = fs.fac;
+    a.sep = fs.sep;
+    a.pcr = fs.pcr;
+    NlArgs na{a, cw, coef, tol, maxit, iters};
+    switch (fs.L) {
+        case 4: return launch_nl_t<4>(na, ngroups, s);
+        case 8: return launch_nl_t<8>(na, ngroups, s);
+        default: return -2;
+    }
+}

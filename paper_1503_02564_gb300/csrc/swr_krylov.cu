@@ -390,82 +390,99 @@ __device__ bool wait_neighbours(int k, int nif, int target, const int* progress,
     return true;
 }
 
-__global__ void __launch_bounds__(128) k_causal_wave(int N, int nt, int sweeps,
+// Warp 0 waits, solves and publishes; warps 1-4 (one per source block) compute,
+// during step n, the part of step n+1's history that uses values older than n
+// (lags >= 2), so that step n+1 adds one lag-1 term on its critical path.
+__global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweeps,
                                                      const double2* __restrict__ cols,
                                                      const double2* __restrict__ lag0,
                                                      const double2* __restrict__ y,
                                                      double2* __restrict__ x,
                                                      double2* __restrict__ xsw, int* progress,
                                                      int* abortf, int* status) {
-    __shared__ double2 part[4];
+    __shared__ double2 hp[2][4];     // partial histories, by parity of the step they serve
     __shared__ int s_go;
     const int nif = N - 1;
     const int k = blockIdx.x;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double2 zero = make_double2(0.0, 0.0);
-    // warp w handles one source of the two outputs of interface k:
-    //  w=0: r_k     <- X^{k+1,1} l_{k+1} (block 2k+1)   w=1: r_k <- X^{k+1,2} r_{k+1} (block 2k+2)
-    //  w=2: l_{k+1} <- X^{k,4}   r_k     (block 2k)     w=3: l_{k+1} <- X^{k,3} l_k (block 2k-1)
-    bool has = true;
-    int cslot = 0, inb = 0;
-    if (w == 0) { cslot = 4 * (k + 1) + 0; inb = 2 * k + 1; }
-    if (w == 1) { has = (k + 1 <= N - 2); cslot = 4 * (k + 1) + 1; inb = 2 * k + 2; }
-    if (w == 2) { cslot = 4 * k + 3; inb = 2 * k; }
-    if (w == 3) { has = (k >= 1); cslot = 4 * k + 2; inb = 2 * k - 1; }
-    const double2* cc = has ? cols + (size_t)cslot * nt : nullptr;
-    const double2* xin = has ? x + (size_t)inb * nt : nullptr;
+    // source e of interface k:
+    //  e=0: r_k     <- X^{k+1,1} l_{k+1} (block 2k+1)   e=1: r_k <- X^{k+1,2} r_{k+1} (block 2k+2)
+    //  e=2: l_{k+1} <- X^{k,4}   r_k     (block 2k)     e=3: l_{k+1} <- X^{k,3} l_k (block 2k-1)
+    auto source = [&](int e, bool& has, const double2*& cc, const double2*& xin) {
+        int cslot = 0, inb = 0;
+        has = true;
+        if (e == 0) { cslot = 4 * (k + 1) + 0; inb = 2 * k + 1; }
+        if (e == 1) { has = (k + 1 <= N - 2); cslot = 4 * (k + 1) + 1; inb = 2 * k + 2; }
+        if (e == 2) { cslot = 4 * k + 3; inb = 2 * k; }
+        if (e == 3) { has = (k >= 1); cslot = 4 * k + 2; inb = 2 * k - 1; }
+        cc = has ? cols + (size_t)cslot * nt : nullptr;
+        xin = has ? x + (size_t)inb * nt : nullptr;
+    };
     const int S1 = sweeps + 1;
+    if (threadIdx.x < 8) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
+    // role data: warps 1-4 accumulate source e = w-1; lane 0 of warp 0 solves
+    bool has = false;
+    const double2* cc = nullptr;
+    const double2* xin = nullptr;
+    if (w >= 1) source(w - 1, has, cc, xin);
+    bool hs[4] = {false, false, false, false};
+    const double2* cs[4] = {nullptr, nullptr, nullptr, nullptr};
+    const double2* xs[4] = {nullptr, nullptr, nullptr, nullptr};
     double2 D00 = zero, D01 = zero, D10 = zero, D11 = zero, cB0 = zero, cD0 = zero;
-    if (threadIdx.x == 0) {
+    double2 c1[4] = {zero, zero, zero, zero};
+    const bool solver = (threadIdx.x == 0);
+    if (solver) {
+        for (int e = 0; e < 4; ++e) source(e, hs[e], cs[e], xs[e]);
         D00 = lag0[k * 4 + 0];
         D01 = lag0[k * 4 + 1];
         D10 = lag0[k * 4 + 2];
         D11 = lag0[k * 4 + 3];
-        if (k + 1 <= N - 2) cB0 = cols[(size_t)(4 * (k + 1) + 1) * nt];
-        if (k >= 1) cD0 = cols[(size_t)(4 * k + 2) * nt];
+        cB0 = hs[1] ? cs[1][0] : zero;
+        cD0 = hs[3] ? cs[3][0] : zero;
+        for (int e = 0; e < 4; ++e) c1[e] = (hs[e] && nt > 1) ? cs[e][1] : zero;
     }
+    __syncthreads();
     for (int n = 0; n < nt; ++n) {
-        if (threadIdx.x == 0) {
-            s_go = wait_neighbours(k, nif, n * S1, progress, abortf, status) ? 1 : 0;
-            __threadfence();
-        }
-        __syncthreads();
+        if (solver) s_go = wait_neighbours(k, nif, n * S1, progress, abortf, status) ? 1 : 0;
+        __syncthreads();                                       // B1: values < n visible
         if (!s_go) break;
-        // history, lags >= 1
-        double2 acc = zero;
-        if (has)
-            for (int s = lane; s < n; s += 32) acc = cfma(__ldg(cc + n - s), xin[s], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) part[w] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double2 r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(part[0], part[1]));
-            const double2 r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(part[2], part[3]));
+        if (solver) {
+            // history of step n: partial (lags >= 2, computed during step n-1) + lag 1
+            double2 h[4];
+            for (int e = 0; e < 4; ++e) {
+                h[e] = hp[n & 1][e];
+                if (n >= 1 && hs[e]) h[e] = cfma(c1[e], xs[e][n - 1], h[e]);
+            }
+            const double2 r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(h[0], h[1]));
+            const double2 r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(h[2], h[3]));
             double2 z1 = cfma(D01, r2, cmul(D00, r1));
             double2 z2 = cfma(D11, r2, cmul(D10, r1));
-            bool ok = true;
-            for (int sw = 1; sw <= sweeps && ok; ++sw) {
+            for (int sw = 1; sw <= sweeps; ++sw) {
                 // publish sweep sw-1 of this step, then use the neighbours' sweep sw-1
                 double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif;
                 out[2 * k] = z1;
                 out[2 * k + 1] = z2;
-                __threadfence();
                 store_release(progress + k, n * S1 + sw);
-                ok = wait_neighbours(k, nif, n * S1 + sw, progress, abortf, status);
-                if (!ok) break;
-                __threadfence();
-                const double2 xr = (k + 1 <= N - 2) ? out[2 * (k + 1)] : zero;       // r_{k+1}
-                const double2 xl = (k >= 1) ? out[2 * (k - 1) + 1] : zero;          // l_k
+                if (!wait_neighbours(k, nif, n * S1 + sw, progress, abortf, status)) break;
+                const double2 xr = (k + 1 <= N - 2) ? out[2 * (k + 1)] : zero;   // r_{k+1}
+                const double2 xl = (k >= 1) ? out[2 * (k - 1) + 1] : zero;      // l_k
                 const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
                 z1 = cfma(D01, e2, cmul(D00, e1));
                 z2 = cfma(D11, e2, cmul(D10, e1));
             }
             x[(size_t)(2 * k) * nt + n] = z1;
             x[(size_t)(2 * k + 1) * nt + n] = z2;
-            __threadfence();
-            store_release(progress + k, (n + 1) * S1);
+            store_release(progress + k, (n + 1) * S1);         // orders the x writes above
+        } else if (w >= 1) {
+            // step n+1's history from values s <= n-1 (lags >= 2)
+            double2 acc = zero;
+            if (has && n + 1 < nt)
+                for (int s = lane; s < n; s += 32) acc = cfma(__ldg(cc + n + 1 - s), xin[s], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) hp[(n + 1) & 1][w - 1] = acc;
         }
-        __syncthreads();
+        __syncthreads();                                       // B2
     }
 }
 
@@ -483,7 +500,7 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, c
     int dev = 0, nsm = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_causal_wave, 128, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_causal_wave, 160, 0) != cudaSuccess)
         return -1;
     if (nif > nsm * per) return -2;      // all CTAs must be resident at once
     // progress counters and the abort flag start at zero on every call
@@ -491,7 +508,7 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, c
     void* args[] = {(void*)&N, (void*)&nt, (void*)&sweeps, (void*)&cols, (void*)&lag0,
                     (void*)&y, (void*)&x, (void*)&xsw, (void*)&progress, (void*)&abortf,
                     (void*)&status};
-    if (cudaLaunchCooperativeKernel((const void*)k_causal_wave, dim3(nif), dim3(128), args, 0, s) !=
+    if (cudaLaunchCooperativeKernel((const void*)k_causal_wave, dim3(nif), dim3(160), args, 0, s) !=
         cudaSuccess)
         return -1;
     swr_count_launch(1);

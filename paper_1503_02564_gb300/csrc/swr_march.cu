@@ -203,7 +203,8 @@ __global__ void k_factor_chunks(int N, int P, const int* __restrict__ n_,
     if (bad) atomicOr(status, ST_SINGULAR);
 }
 
-// Reduced (separator) system and its PCR coefficients; one thread per subdomain.
+// Reduced (separator) system and its PCR coefficients; one CTA per subdomain,
+// threads strided over the separators, one barrier per PCR level.
 // Row ps: E_{s-1} v_{s-1} + D_s v_s + E_s v_{s+1} = f_s with the neighbouring
 // interiors eliminated through the chunk spikes:
 //   delta = D_s - E_{s-1} b^{ps-1}_last - E_s a^{ps}_first,
@@ -216,7 +217,7 @@ __global__ void k_reduce_pcr(int N, int P, int levels, const int* __restrict__ l
                              const double2* __restrict__ tips, double2* __restrict__ sep,
                              double2* __restrict__ pcr, double2* __restrict__ red,
                              int* status) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x;
     if (j >= N) return;
     const int Pj = sub_P[j];
     const int S = P + 1;
@@ -232,7 +233,7 @@ __global__ void k_reduce_pcr(int N, int P, int levels, const int* __restrict__ l
     double2* sbinv = sep + (size_t)(j * 3 + 2) * S;
     const double2* T = tips + (size_t)j * P * 4;
     const int base = loff_[j];
-    for (int ps = 0; ps <= P; ++ps) {
+    for (int ps = threadIdx.x; ps <= P; ps += blockDim.x) {
         if (ps <= Pj) {
             const int s = sep_pos[j * S + ps];
             double2 d = dg[base + s], l = zero, u = zero;
@@ -260,12 +261,12 @@ __global__ void k_reduce_pcr(int N, int P, int levels, const int* __restrict__ l
             sE_r[ps] = zero;
         }
     }
-    bool bad = false;
+    __syncthreads();
     for (int k = 0; k < levels; ++k) {
         const int st = 1 << k;
         double2* al = pcr + ((size_t)(j * levels + k) * 2 + 0) * S;
         double2* ga = pcr + ((size_t)(j * levels + k) * 2 + 1) * S;
-        for (int ps = 0; ps <= P; ++ps) {
+        for (int ps = threadIdx.x; ps <= P; ps += blockDim.x) {
             double2 a = zero, g = zero, nl = zero, nu = zero, nd = dd[ps];
             if (ps - st >= 0) {
                 const double2 r = crcp(dd[ps - st]);
@@ -285,12 +286,14 @@ __global__ void k_reduce_pcr(int N, int P, int levels, const int* __restrict__ l
             dd2[ps] = nd;
             up2[ps] = nu;
         }
+        __syncthreads();
         double2* t;
         t = lo; lo = lo2; lo2 = t;
         t = dd; dd = dd2; dd2 = t;
         t = up; up = up2; up2 = t;
     }
-    for (int ps = 0; ps <= P; ++ps) {
+    bool bad = false;
+    for (int ps = threadIdx.x; ps <= P; ps += blockDim.x) {
         const double2 d = dd[ps];
         bad |= !cfinite(d) || (d.x == 0.0 && d.y == 0.0);
         sbinv[ps] = crcp(d);
@@ -359,7 +362,7 @@ int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, c
             return -2;
     }
     if (cudaGetLastError() != cudaSuccess) return -1;
-    k_reduce_pcr<<<(N + 63) / 64, 64, 0, s>>>(N, fs.P, fs.levels, d_loff, dg, od, fs.sub_P,
+    k_reduce_pcr<<<N, 256, 0, s>>>(N, fs.P, fs.levels, d_loff, dg, od, fs.sub_P,
                                                fs.sep_pos, fs.tips, fs.sep, fs.pcr, fs.red, status);
     swr_count_launch(2);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -101,15 +101,20 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
         double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
         return base + (pc - home * T);
     };
-    // reductions live in the CTA of rank 0 when a system spans a cluster
-    auto RED = [&](int slot, int q) -> unsigned long long* {
-        unsigned long long* base = (C == 1 || rank == 0) ? red : cl.map_shared_rank(red, 0);
-        return base + (slot * G + g) * 2 + q;
+    // per-CTA partial maxima (local atomics only); a system spread over a cluster
+    // reads the partials of all its CTAs after the barrier
+    auto RED = [&](int slot, int q) -> unsigned long long* { return red + (slot * G + g) * 2 + q; };
+    auto RED_ALL = [&](int slot, int q) -> unsigned long long {
+        if (C == 1) return *RED(slot, q);
+        unsigned long long m = 0ull;
+        for (int r = 0; r < C; ++r) {
+            const unsigned long long* b = (r == rank) ? red : cl.map_shared_rank(red, r);
+            const unsigned long long v = b[(slot * G + g) * 2 + q];
+            m = v > m ? v : m;
+        }
+        return m;
     };
-    auto CNT = [&](int slot) -> unsigned long long* {
-        unsigned long long* base = (C == 1 || rank == 0) ? cnt : cl.map_shared_rank(cnt, 0);
-        return base + slot;
-    };
+    auto CNT = [&](int slot) -> unsigned long long* { return cnt + slot; };
     auto SYNC = [&]() {
         if (C == 1)
             __syncthreads();
@@ -180,11 +185,8 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
             *CHK(ulst, p) = ul;
         }
         // reduction slot 0 serves the first inner iteration of this step
-        if (valid && p == 0) {
-            *RED(0, 0) = 0ull;
-            *RED(0, 1) = 0ull;
-        }
-        if (tid == 0 && (C == 1 || rank == 0)) *CNT(0) = 0ull;
+        for (int q = tid; q < 2 * G; q += blockDim.x) red[q] = 0ull;
+        if (tid == 0) *CNT(0) = 0ull;
         SYNC();
         if (realsep) {
             const double2 us = *SEP(usep, p);
@@ -228,11 +230,8 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 *CHK(zlst, p) = zl;
             }
             SYNC();
-            if (valid && p == 0) {
-                *RED(nslot, 0) = 0ull;
-                *RED(nslot, 1) = 0ull;
-            }
-            if (tid == 0 && (C == 1 || rank == 0)) *CNT(nslot) = 0ull;
+            for (int q = tid; q < 2 * G; q += blockDim.x) red[nslot * 2 * G + q] = 0ull;
+            if (tid == 0) *CNT(nslot) = 0ull;
             // chunk: right-hand side with b_f(zeta), local LU sweeps
             if (active && Lp > 0) {
                 const double2 zL = *SEP(zsep, p), zR = *SEP(zsep, p + 1);
@@ -335,9 +334,17 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 atomicMax(RED(slot, 1), dbits(zmax));
             }
             SYNC();
+            // C > 1: every thread of the cluster (padding threads included) evaluates the
+            // one system's test on the same partials, so the exit below is uniform
+            bool conv_all = false;
+            if (C > 1) {
+                const double dm = __longlong_as_double((long long)RED_ALL(slot, 0));
+                const double zm = __longlong_as_double((long long)RED_ALL(slot, 1));
+                conv_all = (dm <= na.tol * na.tol * fmax(1.0, zm));
+            }
             if (active) {
-                const double dm = __longlong_as_double((long long)*RED(slot, 0));
-                const double zm = __longlong_as_double((long long)*RED(slot, 1));
+                const double dm = __longlong_as_double((long long)RED_ALL(slot, 0));
+                const double zm = __longlong_as_double((long long)RED_ALL(slot, 1));
 #pragma unroll
                 for (int i = 0; i < L; ++i)
                     if (i < Lp) z[i] = y[i];
@@ -345,12 +352,21 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 if (dm <= na.tol * na.tol * fmax(1.0, zm)) {
                     active = false;
                     used = it + 1;
-                } else if (p == 0) {
+                } else if (C == 1 && p == 0) {
                     atomicAdd(CNT(slot), 1ull);
                 }
             }
-            SYNC();
-            if (*CNT(slot) == 0ull) break;
+            // C == 1: stop when no system of the CTA is still iterating.  C > 1: one
+            // system, whose decision every thread of the cluster computed identically.
+            bool more;
+            if (C == 1) {
+                __syncthreads();
+                more = (*CNT(slot) != 0ull);
+            } else {
+                more = !conv_all;
+                cl.sync();           // every CTA has read the partials before any reset
+            }
+            if (!more) break;
         }
         if (active) nl_fail = true;      // cap reached without convergence
         if (valid && used > itmax) itmax = used;

@@ -107,3 +107,22 @@ def test_full_size_nonlinear_config_against_monodomain():
     print("full-size nonlinear solve:", info)
     assert rel(uT.cpu().numpy(), uTm) < TOL_SOLVE
     assert rel(g.cpu().numpy(), gs) < TOL_SOLVE
+
+
+@pytest.mark.parametrize("vkind", [0, 2])
+def test_cluster_path_is_bit_reproducible(vkind):
+    """A subdomain spread over a thread-block cluster (one system per cluster) gives
+    bit-identical outputs on repeated calls (its cross-CTA reductions are ordered)."""
+    from paper_1503_02564_gb300 import swr
+    wl = W.config5(nsub=2, nx=20001, nt=8)
+    wl.vkind = vkind
+    plan = gpu_plan(wl, solver=swr.SWR_SOLVER_FIXED_POINT if vkind == 2 else swr.SWR_SOLVER_GMRES)
+    g = 0.05 * W.random_interface(wl.nblk, wl.nt, 41)
+    gi = torch.tensor(g.ravel(), dtype=torch.complex128, device="cuda")
+    outs = []
+    for _ in range(6):
+        go = torch.zeros_like(gi)
+        plan.apply_R(gi, go)
+        outs.append(go.cpu().numpy().tobytes())
+    plan.destroy()
+    assert len(set(outs)) == 1

@@ -280,7 +280,17 @@ def main():
     m_launch = sum(s["march_launches"] for s in st)
     m_ms = sum(s["march_ms"] for s in st)
     m_ps = sum(s["march_point_steps"] for s in st)
-    fpp = FLOPS_PER_POINT_STEP_TDEP if timedep else FLOPS_PER_POINT_STEP
+    # V(t,x): variant 3 streams every step's factors (computed once per build)
+    # through the constant-matrix march kernel; variant 1 refactorises per step
+    variant = st[0]["march_variant"]
+    streamed = variant == swr.MARCH_TDEP_STREAMED
+    fpp = FLOPS_PER_POINT_STEP_TDEP if variant == swr.MARCH_TDEP_REFACTOR else FLOPS_PER_POINT_STEP
+    m_kernel = "k_march_tdep" if variant == swr.MARCH_TDEP_REFACTOR else "k_march_static"
+    # algorithmic bytes per point-step: u read + written (32 B) plus, streamed,
+    # the factors of that node and step
+    bpp = 32.0
+    if streamed:
+        bpp += st[0]["march_factor_bytes_per_step"] / float(cases[0]["wl"].nx)
     achieved = fpp * m_ps / (m_ms * 1e-3) / 1e9 if m_ms > 0 else 0.0
     # whole-step throughput from the library's own count of marched point-steps
     # (equal to the analytic count for the scaling step; GMRES-dependent otherwise)
@@ -347,7 +357,7 @@ def main():
                        "point_steps_per_step": ps_step,
                        "precond": "mean_potential" if timedep else args.precond, "l2": "flushed by a 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"kernel": "k_march_tdep" if timedep else "k_march_static", "bound": "alu",
+            "roofline": {"kernel": m_kernel, "bound": "alu",
                          "achieved": achieved,
                          "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
@@ -355,10 +365,13 @@ def main():
                          "flops_per_point_step": fpp,
                          "peak_basis": "nominal FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                          "march_share_of_step": m_ms / t_ms if t_ms > 0 else None},
-            "hbm_roof": {"point_steps_per_s": hbm * 1e9 / 32.0,
+            "hbm_roof": {"point_steps_per_s": hbm * 1e9 / bpp,
                          "march_point_steps_per_s": march_pss,
-                         "frac": march_pss / (hbm * 1e9 / 32.0),
-                         "basis": "32 B/point-step (read+write complex128 u) at measured HBM GB/s"},
+                         "frac": march_pss / (hbm * 1e9 / bpp),
+                         "bytes_per_point_step": bpp,
+                         "basis": "32 B/point-step (read+write complex128 u)"
+                                  + (" + streamed per-step factors" if streamed else "")
+                                  + " at measured HBM GB/s"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "wall_s": wall, "per_n": per_n,
             "stats": {"toeplitz_ms": sum(s["toeplitz_ms"] for s in st),

@@ -122,6 +122,13 @@ typedef struct swr_stats {
     double toeplitz_ms;
     int64_t precond_calls;      /* block forward substitutions P^{-1} y                 */
     double precond_ms;
+    int32_t march_variant;      /* kernel of the interface marches R g: 0 constant
+                                 * matrix, 1 V(t,x) refactorised inside the march,
+                                 * 2 nonlinear, 3 V(t,x) with every step's factors
+                                 * computed once per build and streamed from HBM
+                                 * (-1 before the first build)                          */
+    int64_t march_factor_bytes_per_step; /* variant 3: factor bytes one R march reads
+                                 * per time step (all subdomains); 0 otherwise           */
 } swr_stats;
 
 typedef struct swr_plan_s *swr_plan_t;

@@ -5,6 +5,8 @@
 // subdomain, solve (I - L) g = d, final march.  Algorithm 2 / Section 5
 // (V = V(t,x)): GMRES on g - R g + d, right-preconditioned by P = I - L_0.
 // Algorithm 1: g <- R g with full marches.
+#include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -51,6 +53,12 @@ struct swr_plan_s {
     double2 *d_dg0 = nullptr, *d_od0 = nullptr;     // A - B for V = 0
     FactorSet fsL[3], fs0L[3];     // chunked factorisations for L = 4, 8, 16 (V and V = 0)
     int forceL = 0;                // SWR_CHUNK_L override (0: chosen per launch)
+    bool autotune = true;          // SWR_AUTOTUNE=0 disables the measured launch-shape choice
+    // V(t,x): factor every step's matrix once per build and stream the factors
+    // (SWR_TDEP_PRECOMP=0, or too little free memory: refactorise inside the march)
+    int tdep_pre = -1;             // -1: not decided yet
+    // launch shapes chosen by the autotuner: {kind, nsys, L, C, G, T, ngroups}
+    std::vector<std::array<int, 7>> tuned;
     double2* d_u0 = nullptr;
     double* d_V = nullptr;
     double* d_Vbar = nullptr;      // potential of the preconditioner operator (MEAN_POTENTIAL)
@@ -182,14 +190,41 @@ struct MarchCfg {
 
 inline int chunks_for(int nmax, int L) { return (nmax - 1 + L) / (L + 1); }
 
-enum { MK_STATIC = 0, MK_TDEP = 1, MK_NL = 2 };   // march kernel kinds
+// march kernel kinds: constant matrix; V(t,x) refactorised per step inside the
+// march; nonlinear; V(t,x) with per-step factorisations streamed from HBM
+enum { MK_STATIC = 0, MK_TDEP = 1, MK_NL = 2, MK_TSTAT = 3 };
+
+// Threads per CTA and CTA groups for a shape whose L, C, G are set; tps = P + 1.
+inline MarchCfg shape_of(MarchCfg c, int tps, int nsys) {
+    if (c.C == 1) {
+        c.T = ((c.G * tps + 31) / 32) * 32;
+        c.ngroups = (nsys + c.G - 1) / c.G;
+    } else {
+        c.T = (((tps + c.C - 1) / c.C + 31) / 32) * 32;
+        c.ngroups = nsys;
+    }
+    return c;
+}
+
+// Largest CTA the march kernel of this kind and chunk length is compiled for.
+inline int march_tmax(int kind, int L) {
+    return (L == 16 || kind == MK_TDEP || kind == MK_NL) ? 256 : 384;
+}
 
 MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
     MarchCfg c;
+    for (const auto& t : p->tuned)
+        if (t[0] == kind && t[1] == nsys) {
+            c.L = t[2];
+            c.C = t[3];
+            c.G = t[4];
+            c.T = t[5];
+            c.ngroups = t[6];
+            return c;
+        }
     const int nsm = p->nsm;
     const long long want = (long long)nsm * 4 * 32;
     const int cand[3] = {16, 8, 4};
-    const bool tdep = (kind != MK_STATIC);        // kernels limited to 256 threads
     int L = 4;
     if (kind == MK_TDEP) {
         L = 4;   // per-step refactorisation keeps LU, spikes and state in registers
@@ -210,7 +245,7 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
     c.L = L;
     const int P = chunks_for(p->nmax, L);
     const int tps = P + 1;
-    const int TMAX = (L == 16 || tdep) ? 256 : 384;
+    const int TMAX = march_tmax(kind, L);
     if (tps <= TMAX) {
         c.C = 1;
         c.G = std::max(1, std::min(TMAX / tps, (nsys + nsm - 1) / nsm));
@@ -230,14 +265,7 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
             c.C = std::max(c.C, C);
         }
     }
-    if (c.C == 1) {
-        c.T = ((c.G * tps + 31) / 32) * 32;
-        c.ngroups = (nsys + c.G - 1) / c.G;
-    } else {
-        c.T = (((tps + c.C - 1) / c.C + 31) / 32) * 32;
-        c.ngroups = nsys;
-    }
-    return c;
+    return shape_of(c, tps, nsys);
 }
 
 inline int lidx(int L) { return L == 4 ? 0 : (L == 8 ? 1 : 2); }
@@ -246,21 +274,19 @@ inline double2 cmul_h(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, int nsys,
-                     const double2* gin, double2* gout, double2* uT, double2* trace,
-                     const double2* u0, long long work) {
-    MarchArgs a{};
-    const bool tdep = (p->d.vkind == SWR_V_TIME) && !zero_potential;
-    const bool nl = (p->d.vkind == SWR_V_NONLINEAR) && !zero_potential;
-    const MarchCfg cfg = march_config(p, nsys, tdep ? MK_TDEP : (nl ? MK_NL : MK_STATIC));
-    const int C = cfg.C, G = cfg.G, T = cfg.T, ng = cfg.ngroups;
-    if (C > 16) return SWR_ERR_UNSUPPORTED;
+// Launch one march with an explicit shape; nt_run < nt runs only the first steps
+// (the autotuner's probes).  Returns 0 or a launcher error code.
+int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
+               const MarchSys* d_sys, int nsys, const double2* gin, double2* gout, double2* uT,
+               double2* trace, const double2* u0, int nt_run) {
+    if (cfg.C > 16) return -2;
     const FactorSet& fs = zero_potential ? p->fs0L[lidx(cfg.L)] : p->fsL[lidx(cfg.L)];
-    if (fs.L != cfg.L) return SWR_ERR_STATE;
-    a.nt = p->nt;
-    a.C = C;
-    a.G = G;
-    a.T = T;
+    if (fs.L != cfg.L) return -3;
+    MarchArgs a{};
+    a.nt = nt_run;
+    a.C = cfg.C;
+    a.G = cfg.G;
+    a.T = cfg.T;
     a.nsys = nsys;
     a.sys = d_sys;
     a.sub_n = p->d_n;
@@ -274,29 +300,173 @@ swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, i
     a.two_sigma = p->two_sigma;
     a.inv_ik = p->inv_ik;
     a.status = p->d_status;
-    const int pi = prof_begin(p, 0, work);
     const double kappa = 2.0 / p->d.dt * (p->h / 6.0);
-    int rc;
-    if (tdep)
-        rc = swr_launch_march_tdep(fs, a, p->d_V, p->nx, p->h, kappa,
-                                   cmul_h(p->sigma0, p->inv_ik), ng, p->s);
-    else if (nl)
-        rc = swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
-                                 p->d.nl_maxit, nullptr, ng, p->s);
-    else
-        rc = swr_launch_march(fs, a, ng, p->s);
+    if (kind == MK_TDEP)
+        return swr_launch_march_tdep(fs, a, p->d_V, p->nx, p->h, kappa,
+                                     cmul_h(p->sigma0, p->inv_ik), cfg.ngroups, p->s);
+    if (kind == MK_NL)
+        return swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
+                                   p->d.nl_maxit, nullptr, cfg.ngroups, p->s);
+    return swr_launch_march(fs, a, cfg.ngroups, p->s);
+}
+
+inline int march_kind(swr_plan_t p, bool zero_potential) {
+    if (zero_potential) return MK_STATIC;
+    if (p->d.vkind == SWR_V_TIME) return p->tdep_pre > 0 ? MK_TSTAT : MK_TDEP;
+    if (p->d.vkind == SWR_V_NONLINEAR) return MK_NL;
+    return MK_STATIC;
+}
+
+swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, int nsys,
+                     const double2* gin, double2* gout, double2* uT, double2* trace,
+                     const double2* u0, long long work) {
+    const int kind = march_kind(p, zero_potential);
+    const MarchCfg cfg = march_config(p, nsys, kind);
+    const int pi = prof_begin(p, 0, work);
+    const int rc = launch_cfg(p, cfg, kind, zero_potential, d_sys, nsys, gin, gout, uT, trace, u0,
+                              p->nt);
     prof_end(p, pi);
-    if (rc != 0) return launch_fail(tdep ? "march (time-dependent)" : (nl ? "march (nonlinear)" : "march"), __LINE__);
+    if (rc == -2) return SWR_ERR_UNSUPPORTED;
+    if (rc == -3) return SWR_ERR_STATE;
+    if (rc != 0) return launch_fail(kind == MK_TDEP ? "march (time-dependent)" : (kind == MK_NL ? "march (nonlinear)" : "march"), __LINE__);
     return SWR_OK;
 }
 
 // Assemble A - B for V (NULL: V = 0) and factor it for chunk length L.
 swr_status factor_for(swr_plan_t p, FactorSet& fs, int L, const double* V, double2* dg,
                       double2* od) {
-    if (fs.L != L) {
+    if (fs.L != L || fs.nsteps != 1) {
         if (swr_factor_alloc(fs, p->N, L, chunks_for(p->nmax, L), p->s) != 0) return SWR_ERR_NOMEM;
     }
     if (swr_launch_factor(fs, p->N, p->d_n, p->d_loff, dg, od, p->d_status, p->s) != 0) {
+        cudaGetLastError();
+        return SWR_ERR_CUDA;
+    }
+    return SWR_OK;
+}
+
+// Measured launch-shape choice.  The first build of a plan times short probe
+// marches (the first few steps of the real launch, into the real output buffer
+// with stride nt_probe) over candidate chunk lengths L, cluster sizes C and
+// packings G, and caches the fastest shape per (kernel kind, system count) in
+// p->tuned; march_config returns it from then on.  Candidates the device cannot
+// launch (cluster too large for the SMs' resources) are skipped.  The model
+// behind the default shape (four full warps per SM, one wave of CTAs) is only a
+// first guess: wave quantisation, cluster scheduling and the PCR depth move the
+// optimum by up to 2x, so the probes decide.
+swr_status factor_steps_for(swr_plan_t p, FactorSet& fs, int L, int nsteps);
+
+swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSys* d_sys,
+                      int nsys, double2* gout, const double* V, double2* dg, double2* od) {
+    if (!p->autotune || nsys <= 0) return SWR_OK;
+    for (const auto& t : p->tuned)
+        if (t[0] == kind && t[1] == nsys) return SWR_OK;
+    const MarchCfg guess = march_config(p, nsys, kind);
+    std::vector<int> Ls;
+    if (kind == MK_TDEP) Ls = {4};
+    else if (kind == MK_NL) Ls = {8, 4};
+    else if (p->forceL) Ls = {p->forceL};
+    else Ls = {16, 8, 4};
+    std::vector<MarchCfg> cands;
+    cands.push_back(guess);
+    for (int L : Ls) {
+        const int tps = chunks_for(p->nmax, L) + 1;
+        const int TMAX = march_tmax(kind, L);
+        MarchCfg c;
+        c.L = L;
+        if (tps <= TMAX) {
+            const int Gmax = std::max(1, std::min(TMAX / tps, nsys));
+            std::vector<int> Gs;
+            for (int G = 1; G <= Gmax; G *= 2) Gs.push_back(G);
+            Gs.push_back(Gmax);
+            Gs.push_back(std::min(Gmax, (nsys + p->nsm - 1) / p->nsm));
+            Gs.push_back(std::min(Gmax, (nsys + 2 * p->nsm - 1) / (2 * p->nsm)));
+            for (int G : Gs) {
+                c.C = 1;
+                c.G = G;
+                cands.push_back(shape_of(c, tps, nsys));
+            }
+        }
+        // clusters: each CTA keeps at least one full warp of separators and
+        // none is left without separators
+        const int Cmin = std::max(2, (tps + TMAX - 1) / TMAX);
+        for (int C = Cmin; C <= 16; C = (C < 4 ? C + 1 : C * 2)) {
+            if (C > Cmin && (tps + C - 1) / C < 32) break;
+            c.C = C;
+            c.G = 1;
+            const MarchCfg sc = shape_of(c, tps, nsys);
+            if ((C - 1) * sc.T < tps) cands.push_back(sc);
+        }
+    }
+    // factors for every candidate chunk length (per-step kinds: the probed steps)
+    const int ntp = std::min(p->nt, 16);
+    for (int L : Ls) {
+        FactorSet& fs = zero_potential ? p->fs0L[lidx(L)] : p->fsL[lidx(L)];
+        swr_status st = (kind == MK_TSTAT) ? factor_steps_for(p, fs, L, ntp)
+                                           : factor_for(p, fs, L, V, dg, od);
+        if (st) return st;
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    MarchCfg best = guess;
+    float best_ms = -1.f;
+    for (size_t k = 0; k < cands.size(); ++k) {
+        const MarchCfg& c = cands[k];
+        bool dup = false;
+        for (size_t q = 0; q < k && !dup; ++q)
+            dup = cands[q].L == c.L && cands[q].C == c.C && cands[q].G == c.G;
+        if (dup) continue;
+        if (launch_cfg(p, c, kind, zero_potential, d_sys, nsys, nullptr, gout, nullptr, nullptr,
+                       p->d_u0, ntp) != 0) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(e0, p->s);
+        int rc = 0;
+        for (int r = 0; r < 2 && rc == 0; ++r)
+            rc = launch_cfg(p, c, kind, zero_potential, d_sys, nsys, nullptr, gout, nullptr,
+                            nullptr, p->d_u0, ntp);
+        cudaEventRecord(e1, p->s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(cudaGetLastError(), "autotune probe", __LINE__);
+        }
+        if (rc != 0) {
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (getenv("SWR_DEBUG"))
+        fprintf(stderr, "swr autotune kind %d nsys %d: L %d C %d G %d T %d (%.3f ms / 2x%d steps)\n",
+                kind, nsys, best.L, best.C, best.G, best.T, best_ms, ntp);
+    p->tuned.push_back({kind, nsys, best.L, best.C, best.G, best.T, best.ngroups});
+    if (kind == MK_TSTAT)   // probe-sized per-step sets of the losing chunk lengths
+        for (int L : Ls)
+            if (L != best.L) swr_factor_free(p->fsL[lidx(L)]);
+    // probes may have flagged the status word with partial data; start clean
+    CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->s));
+    return SWR_OK;
+}
+
+// Per-step factorisations of steps 1..nsteps of the tabulated V(t,x) in d_V.
+swr_status factor_steps_for(swr_plan_t p, FactorSet& fs, int L, int nsteps) {
+    if (fs.L != L || fs.nsteps != nsteps) {
+        if (swr_factor_alloc(fs, p->N, L, chunks_for(p->nmax, L), p->s, nsteps, p->ntot) != 0)
+            return SWR_ERR_NOMEM;
+    }
+    if (swr_launch_factor_steps(fs, p->N, p->d_n, p->d_goff, p->d_loff, p->d_tc, p->nmax, p->d_V,
+                                p->nx, p->h, p->d.dt, p->sigma0, p->inv_ik, p->d_status,
+                                p->s) != 0) {
         cudaGetLastError();
         return SWR_ERR_CUDA;
     }
@@ -725,6 +895,9 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
         const int v = atoi(e);
         if (v == 4 || v == 8 || v == 16) p->forceL = v;
     }
+    if (const char* e = getenv("SWR_AUTOTUNE")) {   // 0: keep the modelled launch shapes
+        p->autotune = atoi(e) != 0;
+    }
     swr_status st = SWR_OK;
     const size_t nb = (size_t)p->nblk * p->nt;
     if (!st) st = dalloc(&p->d_n, p->N);
@@ -799,10 +972,55 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
     CK(cudaMemcpyAsync(p->d_u0, u0, sizeof(double2) * p->nx, cudaMemcpyDeviceToDevice, s));
     swr_status st = assemble(p, p->d_V, p->d_dg, p->d_od);
     if (st) return st;
+    if (p->d.vkind == SWR_V_TIME && p->tdep_pre < 0) {
+        // per-step factorisations need nt copies of the factors (about 110 bytes
+        // per node and step); take them while they use at most half the free memory
+        bool on = p->nt >= 2;
+        if (const char* e = getenv("SWR_TDEP_PRECOMP")) on = on && atoi(e) != 0;
+        if (on) {
+            size_t fr = 0, tot = 0;
+            CK(cudaMemGetInfo(&fr, &tot));
+            const size_t need =
+                (size_t)p->nt * swr_factor_step_bytes(p->N, 4, chunks_for(p->nmax, 4));
+            on = need <= fr / 2;
+        }
+        p->tdep_pre = on ? 1 : 0;
+    }
+    if (p->autotune && !p->built) {
+        // first build: measure the launch shapes of every march this plan makes
+        const int k = march_kind(p, false);
+        if ((st = tune_march(p, k, false, p->d_sys_R, p->N, p->d_iface, p->d_V, p->d_dg, p->d_od)))
+            return st;
+        if (k == MK_STATIC &&
+            (st = tune_march(p, k, false, p->d_sys_build, p->nsys_build, p->d_iface, p->d_V,
+                             p->d_dg, p->d_od)))
+            return st;
+        if (p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) {
+            const double* Vp = nullptr;
+            if (p->d.precond == SWR_PC_MEAN_POTENTIAL) {
+                LK(swr_launch_row_mean(p->d_V, p->d.vkind == SWR_V_TIME ? p->nt + 1 : 1, p->nx,
+                                       p->d_Vbar, s));
+                Vp = p->d_Vbar;
+            }
+            if ((st = assemble(p, Vp, p->d_dg0, p->d_od0))) return st;
+            if ((st = tune_march(p, MK_STATIC, true, p->d_sys_build + p->N, p->nsys_build - p->N,
+                                 p->d_iface, Vp, p->d_dg0, p->d_od0)))
+                return st;
+        }
+        // the probes wrote into d_iface; the build below starts the clock again
+        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
+        CK(cudaEventRecord(p->ev[0], s));
+    }
     if (p->d.vkind == SWR_V_TIME) {
         // chunk tables for the per-step refactorising march (the factors of the
         // t = 0 matrix computed alongside are not used)
-        if ((st = factor_for(p, p->fsL[lidx(4)], 4, p->d_V, p->d_dg, p->d_od))) return st;
+        const int kt = march_kind(p, false);
+        const int Lt = march_config(p, p->N, kt).L;
+        if (kt == MK_TSTAT)   // every step's matrix, W = (V(t_{n-1}) + V(t_n)) / 2
+            st = factor_steps_for(p, p->fsL[lidx(Lt)], Lt, p->nt);
+        else
+            st = factor_for(p, p->fsL[lidx(Lt)], Lt, p->d_V, p->d_dg, p->d_od);
+        if (st) return st;
         CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
         // d = R 0 (Section 4.1; valid for V(t,x)): the first N systems of the build list
         st = run_march(p, false, p->d_sys_build, p->N, nullptr, p->d_iface, nullptr, nullptr,
@@ -951,7 +1169,16 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats* out, int32_t reset) {
     if (!p) return SWR_ERR_ARG;
     CK(cudaStreamSynchronize(p->s));
     prof_flush(p);
-    if (out) *out = p->stats;
+    if (out) {
+        *out = p->stats;
+        out->march_variant = p->built ? march_kind(p, false) : -1;
+        out->march_factor_bytes_per_step = 0;
+        if (out->march_variant == MK_TSTAT) {
+            const FactorSet& fs = p->fsL[lidx(march_config(p, p->N, MK_TSTAT).L)];
+            out->march_factor_bytes_per_step =
+                (int64_t)sizeof(double2) * (fs.fstride + fs.sstride + fs.pstride);
+        }
+    }
     if (reset) p->stats = swr_stats{};
     return SWR_OK;
 }

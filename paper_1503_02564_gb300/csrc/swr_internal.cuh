@@ -34,6 +34,18 @@ __device__ __forceinline__ double2 crcp(double2 a) {
 }
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+// c ? a : b as one selp per component.  Picking one element of an unrolled
+// register array under a runtime condition (the last interior node of a chunk)
+// is otherwise rewritten by the compiler into an indexed read, which moves the
+// whole array to local memory.
+__device__ __forceinline__ double2 csel(bool c, double2 a, double2 b) {
+    double2 r;
+    asm("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t"
+        "selp.f64 %0, %2, %5, q;\n\tselp.f64 %1, %3, %6, q;\n\t}"
+        : "=d"(r.x), "=d"(r.y)
+        : "d"(a.x), "d"(a.y), "r"((unsigned)c), "d"(b.x), "d"(b.y));
+    return r;
+}
 
 // ---------------------------------------------------------------------------
 // device status word bits
@@ -79,6 +91,14 @@ struct FactorSet {
     double2* sep = nullptr;        // [N][3][P+1]   (E_left, E_right, 1/delta)
     double2* pcr = nullptr;        // [N][levels][2][P+1] (alpha, gamma)
     double2* red = nullptr;        // [N][6][P+1]   scratch for the PCR coefficient run
+    // Per-step factorisations (V(t,x) tabulated, Eq. AvML with W at t_{n-1/2}):
+    // fac, sep and pcr hold nsteps consecutive copies, step n-1 at n-1 times the
+    // stride; tips, red and the assembled dg/od are scratch for a batch of steps.
+    int nsteps = 1, batch = 1;
+    long long fstride = 0, sstride = 0, pstride = 0;   // elements per step (0: one set)
+    double2* dgb = nullptr;        // [batch][ldd] assembled diagonal (nsteps > 1)
+    double2* odb = nullptr;        // [batch][ldd] assembled coupling
+    long long ldd = 0;
 };
 
 struct MarchArgs {
@@ -98,6 +118,7 @@ struct MarchArgs {
     double2* gout;        // output blocks
     double2* uT;          // nodal output
     double2* trace;       // [nsys][2][nt]
+    long long fstride, sstride, pstride;   // per-step factor strides (0: constant matrix)
     double2 two_sigma;    // 2 p (Robin): 2 S-tilde v = 2 p v
     double2 inv_ik;       // 1/(i kappa), kappa = (2/dt)(h/6): the system is scaled by it
     int* status;
@@ -112,7 +133,15 @@ int swr_launch_assemble_static(const double* V, int N, const int* d_n, const int
                                double2 sigma0, double2 inv_ik, double2* dg, double2* od,
                                cudaStream_t s);
 int swr_launch_row_mean(const double* V, int nrows, long long nx, double* out, cudaStream_t s);
-int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t s);
+int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t s, int nsteps = 1,
+                     long long ldd = 0);
+size_t swr_factor_step_bytes(int N, int L, int P);
+// Assemble and factor the matrices of steps 1..fs.nsteps of a tabulated V(t,x)
+// (row t of V at t * vstride), W = (V(t_{n-1}) + V(t_n)) / 2 at step n.
+int swr_launch_factor_steps(FactorSet& fs, int N, const int* d_n, const int* d_goff,
+                            const int* d_loff, const int* d_tc, int nmax, const double* V,
+                            long long vstride, double h, double dt, double2 sigma0,
+                            double2 inv_ik, int* status, cudaStream_t s);
 void swr_factor_free(FactorSet& fs);
 int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
                       const double2* od, int* status, cudaStream_t s);

@@ -27,37 +27,50 @@
 // right-hand side (2i/dt) M u becomes the integer stencil u_{i-1} + 4 u_i + u_{i+1}.
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 #include "swr_internal.cuh"
 
 namespace cg = cooperative_groups;
+
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
 
 // ---------------------------------------------------------------------------
 // Assembly of A_j - B_j (P1 elements, generalised mass by exact quadrature of the
 // P1 interpolant of W), scaled by 1/(i kappa).  dg[loff_j + i] is the diagonal,
 // od[loff_j + i] the coupling of local nodes i and i+1.
 // ---------------------------------------------------------------------------
-__global__ void k_assemble_static(const double* __restrict__ V, const int* __restrict__ n_,
-                                  const int* __restrict__ goff_, const int* __restrict__ loff_,
-                                  const int* __restrict__ tc_, double h, double dt, double2 sigma0,
-                                  double2 inv_ik, double2* __restrict__ dg,
-                                  double2* __restrict__ od) {
+__global__ void k_assemble_static(const double* __restrict__ V, long long vstride,
+                                  const int* __restrict__ n_, const int* __restrict__ goff_,
+                                  const int* __restrict__ loff_, const int* __restrict__ tc_,
+                                  double h, double dt, double2 sigma0, double2 inv_ik,
+                                  double2* __restrict__ dg, double2* __restrict__ od,
+                                  long long ldd) {
     const int j = blockIdx.y;
     const int n = n_[j];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    // batch entry z: W = (V row z + V row z+1) / 2 (vstride = 0: the single row V)
+    const double* V0 = V ? V + (size_t)blockIdx.z * vstride : nullptr;
+    const double* V1 = V ? V0 + vstride : nullptr;
+    auto W = [&](int gg) -> double { return V ? 0.5 * (V0[gg] + V1[gg]) : 0.0; };
+    dg += (size_t)blockIdx.z * ldd;
+    od += (size_t)blockIdx.z * ldd;
     const int g = goff_[j] + i;
     const int lo = loff_[j] + i;
     const int tc = tc_[j];
-    const double W0 = V ? V[g] : 0.0;
+    const double W0 = W(g);
     double md = 0.0, sd = 0.0, wd = 0.0;
     if (i > 0) {
-        const double Wm = V ? V[g - 1] : 0.0;
+        const double Wm = W(g - 1);
         md += h / 3.0;
         sd += 1.0 / h;
         wd += h / 12.0 * (Wm + 3.0 * W0);
     }
     if (i < n - 1) {
-        const double Wp = V ? V[g + 1] : 0.0;
+        const double Wp = W(g + 1);
         md += h / 3.0;
         sd += 1.0 / h;
         wd += h / 12.0 * (3.0 * W0 + Wp);
@@ -66,7 +79,7 @@ __global__ void k_assemble_static(const double* __restrict__ V, const int* __res
     if ((i == 0 && (tc & 1)) || (i == n - 1 && (tc & 2))) D = csub(D, sigma0);
     dg[lo] = cmul(D, inv_ik);
     if (i < n - 1) {
-        const double Wp = V ? V[g + 1] : 0.0;
+        const double Wp = W(g + 1);
         const double2 E = make_double2(1.0 / h + h / 12.0 * (W0 + Wp), 2.0 / dt * (h / 6.0));
         od[lo] = cmul(E, inv_ik);
     } else {
@@ -95,8 +108,8 @@ int swr_launch_assemble_static(const double* V, int N, const int* d_n, const int
                                double2 sigma0, double2 inv_ik, double2* dg, double2* od,
                                cudaStream_t s) {
     dim3 grid((nmax + 255) / 256, N);
-    k_assemble_static<<<grid, 256, 0, s>>>(V, d_n, d_goff, d_loff, d_tc, h, dt, sigma0, inv_ik, dg,
-                                           od);
+    k_assemble_static<<<grid, 256, 0, s>>>(V, 0, d_n, d_goff, d_loff, d_tc, h, dt, sigma0, inv_ik,
+                                           dg, od, 0);
     swr_count_launch(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -113,10 +126,16 @@ __global__ void k_factor_chunks(int N, int P, const int* __restrict__ n_,
                                 const double2* __restrict__ od, int* __restrict__ sub_P,
                                 int* __restrict__ sep_pos, unsigned char* __restrict__ clen,
                                 double2* __restrict__ fac, double2* __restrict__ tips,
-                                int* status) {
+                                int* status, long long ldd, long long fstride) {
     const int j = blockIdx.y;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
+    // batch entry z (per-step factorisations): its own dg/od, fac and tips
+    const int z = blockIdx.z;
+    dg += (size_t)z * ldd;
+    od += (size_t)z * ldd;
+    fac += (size_t)z * fstride;
+    tips += (size_t)z * N * P * 4;
     const int n = n_[j];
     const int Pj = (n - 1 + L) / (L + 1);
     const int interior = n - 1 - Pj;
@@ -129,10 +148,12 @@ __global__ void k_factor_chunks(int N, int P, const int* __restrict__ n_,
         Lp = 0;
         sp = n - 1;
     }
-    if (p == 0) sub_P[j] = Pj;
-    sep_pos[j * (P + 1) + p] = sp;
-    if (p == P - 1) sep_pos[j * (P + 1) + P] = n - 1;
-    clen[j * P + p] = (unsigned char)Lp;
+    if (z == 0) {
+        if (p == 0) sub_P[j] = Pj;
+        sep_pos[j * (P + 1) + p] = sp;
+        if (p == P - 1) sep_pos[j * (P + 1) + P] = n - 1;
+        clen[j * P + p] = (unsigned char)Lp;
+    }
     const double2 zero = make_double2(0.0, 0.0);
     double2* F = fac + (size_t)j * L * 4 * P;
     if (Lp == 0) {
@@ -216,9 +237,16 @@ __global__ void k_reduce_pcr(int N, int P, int levels, const int* __restrict__ l
                              const int* __restrict__ sub_P, const int* __restrict__ sep_pos,
                              const double2* __restrict__ tips, double2* __restrict__ sep,
                              double2* __restrict__ pcr, double2* __restrict__ red,
-                             int* status) {
+                             int* status, long long ldd, long long sstride, long long pstride) {
     const int j = blockIdx.x;
     if (j >= N) return;
+    const int z = blockIdx.y;   // batch entry (per-step factorisations)
+    dg += (size_t)z * ldd;
+    od += (size_t)z * ldd;
+    tips += (size_t)z * N * P * 4;
+    sep += (size_t)z * sstride;
+    pcr += (size_t)z * pstride;
+    red += (size_t)z * N * 6 * (P + 1);
     const int Pj = sub_P[j];
     const int S = P + 1;
     const double2 zero = make_double2(0.0, 0.0);
@@ -307,23 +335,45 @@ static int ilog2ceil(int v) {
     return k;
 }
 
-int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t) {
+size_t swr_factor_step_bytes(int N, int L, int P) {
+    const size_t S = P + 1;
+    const int levels = std::max(1, ilog2ceil(P + 1));
+    return sizeof(double2) * ((size_t)N * L * 4 * P + (size_t)N * 3 * S + (size_t)N * levels * 2 * S);
+}
+
+int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t, int nsteps, long long ldd) {
     swr_factor_free(fs);
     fs.L = L;
     fs.P = P;
     fs.levels = ilog2ceil(P + 1);
     if (fs.levels < 1) fs.levels = 1;
     const size_t S = P + 1;
+    fs.nsteps = std::max(1, nsteps);
+    fs.batch = std::min(fs.nsteps, 64);
+    const size_t fst = (size_t)N * L * 4 * P, sst = (size_t)N * 3 * S;
+    const size_t pst = (size_t)N * fs.levels * 2 * S;
+    if (fs.nsteps > 1) {
+        fs.fstride = (long long)fst;
+        fs.sstride = (long long)sst;
+        fs.pstride = (long long)pst;
+        fs.ldd = ldd;
+    }
+    const size_t ns = fs.nsteps, nb = fs.batch;
     bool ok = true;
     ok &= cudaMalloc(&fs.sub_P, sizeof(int) * N) == cudaSuccess;
     ok &= cudaMalloc(&fs.sep_pos, sizeof(int) * N * S) == cudaSuccess;
     ok &= cudaMalloc(&fs.clen, (size_t)N * P) == cudaSuccess;
-    ok &= cudaMalloc(&fs.fac, sizeof(double2) * (size_t)N * L * 4 * P) == cudaSuccess;
-    ok &= cudaMalloc(&fs.tips, sizeof(double2) * (size_t)N * P * 4) == cudaSuccess;
-    ok &= cudaMalloc(&fs.sep, sizeof(double2) * (size_t)N * 3 * S) == cudaSuccess;
-    ok &= cudaMalloc(&fs.pcr, sizeof(double2) * (size_t)N * fs.levels * 2 * S) == cudaSuccess;
-    ok &= cudaMalloc(&fs.red, sizeof(double2) * (size_t)N * 6 * S) == cudaSuccess;
+    ok &= cudaMalloc(&fs.fac, sizeof(double2) * fst * ns) == cudaSuccess;
+    ok &= cudaMalloc(&fs.tips, sizeof(double2) * (size_t)N * P * 4 * nb) == cudaSuccess;
+    ok &= cudaMalloc(&fs.sep, sizeof(double2) * sst * ns) == cudaSuccess;
+    ok &= cudaMalloc(&fs.pcr, sizeof(double2) * pst * ns) == cudaSuccess;
+    ok &= cudaMalloc(&fs.red, sizeof(double2) * (size_t)N * 6 * S * nb) == cudaSuccess;
+    if (fs.nsteps > 1) {
+        ok &= cudaMalloc(&fs.dgb, sizeof(double2) * (size_t)ldd * nb) == cudaSuccess;
+        ok &= cudaMalloc(&fs.odb, sizeof(double2) * (size_t)ldd * nb) == cudaSuccess;
+    }
     if (!ok) {
+        cudaGetLastError();   // clear the allocation error
         swr_factor_free(fs);
         return -1;
     }
@@ -339,33 +389,69 @@ void swr_factor_free(FactorSet& fs) {
     cudaFree(fs.sep);
     cudaFree(fs.pcr);
     cudaFree(fs.red);
+    cudaFree(fs.dgb);
+    cudaFree(fs.odb);
     fs = FactorSet();
 }
 
-int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
-                      const double2* od, int* status, cudaStream_t s) {
-    dim3 grid((fs.P + 127) / 128, N);
+// One batch of nb steps (or the single constant matrix, nb = 1 and zero strides).
+static int launch_factor_batch(FactorSet& fs, int N, const int* d_n, const int* d_loff,
+                               const double2* dg, const double2* od, long long ldd, int t0,
+                               int nb, int* status, cudaStream_t s) {
+    dim3 grid((fs.P + 127) / 128, N, nb);
+    double2* fac = fs.fac + (size_t)t0 * fs.fstride;
     switch (fs.L) {
         case 4:
             k_factor_chunks<4><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
-                                                    fs.sep_pos, fs.clen, fs.fac, fs.tips, status);
+                                                    fs.sep_pos, fs.clen, fac, fs.tips, status, ldd,
+                                                    fs.fstride);
             break;
         case 8:
             k_factor_chunks<8><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
-                                                    fs.sep_pos, fs.clen, fs.fac, fs.tips, status);
+                                                    fs.sep_pos, fs.clen, fac, fs.tips, status, ldd,
+                                                    fs.fstride);
             break;
         case 16:
             k_factor_chunks<16><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
-                                                     fs.sep_pos, fs.clen, fs.fac, fs.tips, status);
+                                                     fs.sep_pos, fs.clen, fac, fs.tips, status,
+                                                     ldd, fs.fstride);
             break;
         default:
             return -2;
     }
     if (cudaGetLastError() != cudaSuccess) return -1;
-    k_reduce_pcr<<<N, 256, 0, s>>>(N, fs.P, fs.levels, d_loff, dg, od, fs.sub_P,
-                                               fs.sep_pos, fs.tips, fs.sep, fs.pcr, fs.red, status);
+    k_reduce_pcr<<<dim3(N, nb), 256, 0, s>>>(N, fs.P, fs.levels, d_loff, dg, od, fs.sub_P,
+                                             fs.sep_pos, fs.tips, fs.sep + (size_t)t0 * fs.sstride,
+                                             fs.pcr + (size_t)t0 * fs.pstride, fs.red, status, ldd,
+                                             fs.sstride, fs.pstride);
     swr_count_launch(2);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
+                      const double2* od, int* status, cudaStream_t s) {
+    if (fs.nsteps != 1) return -2;
+    return launch_factor_batch(fs, N, d_n, d_loff, dg, od, 0, 0, 1, status, s);
+}
+
+int swr_launch_factor_steps(FactorSet& fs, int N, const int* d_n, const int* d_goff,
+                            const int* d_loff, const int* d_tc, int nmax, const double* V,
+                            long long vstride, double h, double dt, double2 sigma0,
+                            double2 inv_ik, int* status, cudaStream_t s) {
+    if (fs.nsteps < 2 || !fs.dgb || !V) return -2;
+    for (int t0 = 0; t0 < fs.nsteps; t0 += fs.batch) {
+        const int nb = std::min(fs.batch, fs.nsteps - t0);
+        dim3 grid((nmax + 255) / 256, N, nb);
+        k_assemble_static<<<grid, 256, 0, s>>>(V + (size_t)t0 * vstride, vstride, d_n, d_goff,
+                                               d_loff, d_tc, h, dt, sigma0, inv_ik, fs.dgb, fs.odb,
+                                               fs.ldd);
+        swr_count_launch(1);
+        if (cudaGetLastError() != cudaSuccess) return -1;
+        const int rc = launch_factor_batch(fs, N, d_n, d_loff, fs.dgb, fs.odb, fs.ldd, t0, nb,
+                                           status, s);
+        if (rc) return rc;
+    }
+    return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -440,11 +526,14 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
     }
     const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
     const bool realsep = valid && (p <= Pj);          // separators beyond Pj are padding
+    // factor pointers; with per-step factorisations they advance by one step's
+    // stride per time step (the strides are zero for a constant matrix)
     const double2* F = a.fac + (size_t)j * L * 4 * P + (p < P ? p : 0);
     const double2* sE_l = a.sep + (size_t)(j * 3 + 0) * (P + 1);
     const double2* sE_r = a.sep + (size_t)(j * 3 + 1) * (P + 1);
     const double2* sbinv = a.sep + (size_t)(j * 3 + 2) * (P + 1);
     const double2* pcr = a.pcr + (size_t)j * levels * 2 * (P + 1);
+    const bool stepped = a.fstride != 0;
 
     double2 u[L], y[L];
 #pragma unroll
@@ -457,6 +546,20 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
 
     double2 lin = zero, rin = zero;
     for (int t = 1; t <= nt; ++t) {
+        if (stepped && valid && t < nt) {
+            // the next step's factors stream from HBM: request them into L2 now
+            if (Lp > 0) {
+#pragma unroll
+                for (int i = 0; i < L; ++i)
+                    if (i < Lp)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) prefetch_l2(F + a.fstride + (i * 4 + k) * P);
+            }
+            prefetch_l2(sE_l + a.sstride + p);
+            prefetch_l2(sE_r + a.sstride + p);
+            prefetch_l2(sbinv + a.sstride + p);
+            for (int k = 0; k < 2 * levels; ++k) prefetch_l2(pcr + a.pstride + (size_t)k * (P + 1) + p);
+        }
         // ---- phase A: chunk right-hand sides and local LU solves -------------
         if (valid && Lp > 0) {
             const double2 uL = *SEP(usep, p), uR = *SEP(usep, p + 1);
@@ -477,7 +580,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     zprev = z;
                     cprev = F[(i * 4 + 1) * P];
                     if (i == 0) uf = u[i];
-                    if (i == Lp - 1) ul = u[i];
+                    ul = csel(i == Lp - 1, u[i], ul);
                 }
             }
             double2 ynext = zero, yl = zero;
@@ -581,6 +684,11 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
         }
+        F += a.fstride;
+        sE_l += a.sstride;
+        sE_r += a.sstride;
+        sbinv += a.sstride;
+        pcr += a.pstride;
         SYNC();
     }
     // ---- final state ----------------------------------------------------------
@@ -753,7 +861,7 @@ __global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
                     const double2 piv = (i == 0) ? Di : cfms(Eprev, cprev, Di);
                     qv[i] = crcp(piv);
                     cv[i] = (i < Lp - 1) ? cmul(Ei, qv[i]) : zero;
-                    if (i == Lp - 1) Elast = Ei;
+                    Elast = csel(i == Lp - 1, Ei, Elast);
                     const double2 left = (i == 0) ? uL : u[i - 1];
                     double2 right;
                     if (i + 1 < L)
@@ -771,7 +879,7 @@ __global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
                     cprev = cv[i];
                     Eprev = Ei;
                     if (i == 0) uf = u[i];
-                    if (i == Lp - 1) ul = u[i];
+                    ul = csel(i == Lp - 1, u[i], ul);
                 }
             }
             double2 yn = zero, an = zero, bn = zero;
@@ -799,12 +907,11 @@ __global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
             *CHK(yfst, p) = y[0];
             double2 yl = zero, al = zero, bl = zero;
 #pragma unroll
-            for (int i = 0; i < L; ++i)
-                if (i == Lp - 1) {
-                    yl = y[i];
-                    al = av[i];
-                    bl = bv[i];
-                }
+            for (int i = 0; i < L; ++i) {
+                yl = csel(i == Lp - 1, y[i], yl);
+                al = csel(i == Lp - 1, av[i], al);
+                bl = csel(i == Lp - 1, bv[i], bl);
+            }
             *CHK(ylst, p) = yl;
             *CHK(afst, p) = av[0];
             *CHK(bfst, p) = bv[0];
@@ -1015,6 +1122,10 @@ static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s) {
 }
 
 int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t s) {
+    if (fs.nsteps > 1 && fs.nsteps < a.nt) return -2;
+    a.fstride = fs.fstride;
+    a.sstride = fs.sstride;
+    a.pstride = fs.pstride;
     a.P = fs.P;
     a.levels = fs.levels;
     a.sub_P = fs.sub_P;

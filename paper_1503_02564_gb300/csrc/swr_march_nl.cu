@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                     f[i] = make_double2(fma(4.0, u[i].x, left.x + right.x),
                                         fma(4.0, u[i].y, left.y + right.y));
                     if (i == 0) uf = u[i];
-                    if (i == Lp - 1) ul = u[i];
+                    ul = csel(i == Lp - 1, u[i], ul);
                 }
             }
             *CHK(ufst, p) = uf;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
 #pragma unroll
                 for (int i = 0; i < L; ++i) {
                     if (i == 0) zf = z[i];
-                    if (i == Lp - 1) zl = z[i];
+                    zl = csel(i == Lp - 1, z[i], zl);
                 }
                 *CHK(zfst, p) = zf;
                 *CHK(zlst, p) = zl;

@@ -23,6 +23,8 @@ SWR_V_STATIC, SWR_V_TIME, SWR_V_NONLINEAR = 0, 1, 2
 SWR_TC_ROBIN, SWR_TC_S02 = 0, 1
 SWR_SOLVER_GMRES, SWR_SOLVER_FIXED_POINT, SWR_SOLVER_CLASSICAL = 0, 1, 2
 SWR_PC_NONE, SWR_PC_ZERO_POTENTIAL, SWR_PC_CAUSAL, SWR_PC_MEAN_POTENTIAL = 0, 1, 2, 3
+# swr_stats.march_variant
+MARCH_CONSTANT, MARCH_TDEP_REFACTOR, MARCH_NONLINEAR, MARCH_TDEP_STREAMED = 0, 1, 2, 3
 
 
 class swr_desc(ctypes.Structure):
@@ -56,7 +58,8 @@ class swr_stats(ctypes.Structure):
         ("march_launches", ctypes.c_int64), ("march_point_steps", ctypes.c_int64),
         ("march_ms", ctypes.c_double), ("toeplitz_launches", ctypes.c_int64),
         ("toeplitz_ms", ctypes.c_double), ("precond_calls", ctypes.c_int64),
-        ("precond_ms", ctypes.c_double),
+        ("precond_ms", ctypes.c_double), ("march_variant", ctypes.c_int32),
+        ("march_factor_bytes_per_step", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -42,15 +42,18 @@ def problem(wl):
                      vkind=wl.vkind, tc=wl.tc, sigma=wl.sigma, nl_coef=wl.nl_coef)
 
 
-def gpu_plan(wl, chunk=None, **kw):
+def gpu_plan(wl, chunk=None, autotune=True, **kw):
     from paper_1503_02564_gb300 import swr
     if chunk is not None:
         os.environ["SWR_CHUNK_L"] = str(chunk)
+    if not autotune:
+        os.environ["SWR_AUTOTUNE"] = "0"
     try:
         plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
                         node_off=wl.off, p=wl.sigma, vkind=wl.vkind, **kw)
     finally:
         os.environ.pop("SWR_CHUNK_L", None)
+        os.environ.pop("SWR_AUTOTUNE", None)
     V = torch.tensor(wl.V, dtype=torch.float64, device="cuda")
     u0 = torch.tensor(wl.u0, dtype=torch.complex128, device="cuda")
     plan.build_interface(V, u0)
@@ -101,6 +104,29 @@ def test_build_interface_matches_oracle(case, chunk):
             else:
                 assert np.all(cols[j, q] == 0)
     plan.destroy()
+
+
+@pytest.mark.parametrize("case", ["config2_N16_small", "ragged_tiny", "two_long"])
+def test_autotuned_shapes_match_modelled_shapes(case):
+    """The measured launch shapes (first build) and the modelled ones
+    (SWR_AUTOTUNE=0) partition the same systems differently; both give the
+    oracle's d and columns, and agree with each other to rounding, also after
+    a second build on the tuned plan."""
+    wl = CASES[case]()
+    pt = gpu_plan(wl)
+    d1, c1 = gpu_interface(pt)
+    V = torch.tensor(wl.V, dtype=torch.float64, device="cuda")
+    u0 = torch.tensor(wl.u0, dtype=torch.complex128, device="cuda")
+    pt.build_interface(V, u0)
+    d2, c2 = gpu_interface(pt)
+    pt.destroy()
+    pm = gpu_plan(wl, autotune=False)
+    dm, cm = gpu_interface(pm)
+    pm.destroy()
+    assert np.array_equal(d1, d2) and np.array_equal(c1, c2)
+    assert rel(d1, dm) < 1e-12 and rel(c1, cm) < 1e-12
+    d_ref = O.build_d(problem(wl))
+    assert rel(d1, d_ref) < TOL_MARCH
 
 
 @pytest.mark.parametrize("case", ["config1_small", "config2_N16_small", "ragged_tiny", "two_long"])

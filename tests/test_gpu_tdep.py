@@ -1,5 +1,9 @@
-"""GPU parity for the time-dependent potential V(t,x) (per-step refactorising
-march, matrix-free GMRES of Algorithm 2 preconditioned by P = I - L_0)."""
+"""GPU parity for the time-dependent potential V(t,x): both march variants (every
+step's factors computed once per build and streamed, and the per-step
+refactorising march), matrix-free GMRES of Algorithm 2 preconditioned by
+P = I - L_0."""
+import os
+
 import numpy as np
 import pytest
 
@@ -33,13 +37,22 @@ def problem(wl):
                      vkind=wl.vkind, tc=wl.tc, sigma=wl.sigma, nl_coef=wl.nl_coef)
 
 
-def gpu_plan(wl, **kw):
+def gpu_plan(wl, streamed=None, **kw):
+    """streamed: True / False selects the V(t,x) march variant (None: default)."""
     from paper_1503_02564_gb300 import swr
     plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
                     node_off=wl.off, p=wl.sigma, vkind=wl.vkind, **kw)
     V = torch.tensor(np.ascontiguousarray(wl.V).ravel(), dtype=torch.float64, device="cuda")
     u0 = torch.tensor(wl.u0, dtype=torch.complex128, device="cuda")
-    plan.build_interface(V, u0)
+    if streamed is not None:
+        os.environ["SWR_TDEP_PRECOMP"] = "1" if streamed else "0"
+    try:
+        plan.build_interface(V, u0)
+    finally:
+        os.environ.pop("SWR_TDEP_PRECOMP", None)
+    if streamed is not None and wl.vkind == swr.SWR_V_TIME:
+        want = swr.MARCH_TDEP_STREAMED if streamed else swr.MARCH_TDEP_REFACTOR
+        assert plan.get_stats()["march_variant"] == want
     return plan
 
 
@@ -56,10 +69,11 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("streamed", [True, False])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_tdep_apply_R_matches_oracle(case):
+def test_tdep_apply_R_matches_oracle(case, streamed):
     wl = CASES[case]()
-    plan = gpu_plan(wl)
+    plan = gpu_plan(wl, streamed)
     g = W.random_interface(wl.nblk, wl.nt, 31)
     gi = torch.tensor(g.ravel(), dtype=torch.complex128, device="cuda")
     go = torch.zeros_like(gi)
@@ -71,8 +85,9 @@ def test_tdep_apply_R_matches_oracle(case):
     plan.destroy()
 
 
-def test_tdep_with_constant_potential_equals_static_path():
-    """Fed V(t,x) = V(x) for every t, the refactorising march must give what the
+@pytest.mark.parametrize("streamed", [True, False])
+def test_tdep_with_constant_potential_equals_static_path(streamed):
+    """Fed V(t,x) = V(x) for every t, both V(t,x) marches must give what the
     factor-once march gives."""
     from paper_1503_02564_gb300 import swr
     wl = W.config2(nsub=6, nx=3001, nt=25)
@@ -84,18 +99,19 @@ def test_tdep_with_constant_potential_equals_static_path():
     wl_t.V = np.tile(wl.V, (wl.nt + 1, 1))
     wl_t.vkind = swr.SWR_V_TIME
     out_t = torch.zeros_like(gi)
-    gpu_plan(wl_t).apply_R(gi, out_t)
+    gpu_plan(wl_t, streamed).apply_R(gi, out_t)
     assert rel(out_t.cpu().numpy(), out_s.cpu().numpy()) < TOL_MARCH
 
 
+@pytest.mark.parametrize("streamed", [True, False])
 @pytest.mark.parametrize("precond", [0, 1, 3])
-def test_tdep_gmres_reproduces_monodomain(precond):
+def test_tdep_gmres_reproduces_monodomain(precond, streamed):
     from paper_1503_02564_gb300 import swr
     wl = CASES["config4_small"]()
     # |g| is about 1e-8 here (the packet barely reaches the interfaces): stop
     # relative to |d| so that the comparison measures the arithmetic
     tol = 1e-13 * np.linalg.norm(O.build_d(problem(wl)))
-    plan = gpu_plan(wl, restart=100, maxit=400, tol_abs=tol,
+    plan = gpu_plan(wl, streamed, restart=100, maxit=400, tol_abs=tol,
                     precond=precond)
     g = torch.zeros(plan.n_interface, dtype=torch.complex128, device="cuda")
     uT = torch.zeros(wl.nx, dtype=torch.complex128, device="cuda")
@@ -117,7 +133,7 @@ def test_full_size_time_dependent_config_against_monodomain():
     wl = W.config4()
     gs, uTm = O.mono_interface(problem(wl))
     tol = 1e-10
-    plan = gpu_plan(wl, restart=60, maxit=400, tol_abs=tol,
+    plan = gpu_plan(wl, True, restart=60, maxit=400, tol_abs=tol,
                     precond=swr.SWR_PC_MEAN_POTENTIAL)
     g = torch.zeros(plan.n_interface, dtype=torch.complex128, device="cuda")
     uT = torch.zeros(wl.nx, dtype=torch.complex128, device="cuda")

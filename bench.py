@@ -44,6 +44,10 @@ def parse():
                     help="scaling: the N in {16,64,256,500} static-potential step (default); "
                          "timedep: the time-dependent potential case (60001 nodes, 1000 steps, "
                          "N = 64, GMRES preconditioned by the mean-potential operator)")
+    ap.add_argument("--tc", default="robin", choices=["robin", "s02"],
+                    help="transmission condition of the scaling workload: Robin "
+                         "p = sqrt(5) e^{-i pi/4} (default) or the order-2 potential "
+                         "strategy S_0^2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -56,11 +60,12 @@ def dist_env():
     return rank, world, local
 
 
-def workload_name(nsubs):
+def workload_name(nsubs, tc="robin"):
+    tcs = ("S_0^2 c2=e^{-i pi/4}sqrt(2/dt)" if tc == "s02" else "Robin p=sqrt(5)e^{-i pi/4}")
     return ("swr_scaling: x in (-50,50), 200001 P1 nodes, T=0.5 dt=1e-3 (500 steps), "
             "N in {%s}, V=-5*sum of 8 seeded Gaussians, u0=4 seeded packets, "
-            "Robin p=sqrt(5)e^{-i pi/4}, build interface + GMRES(30) to 1e-10 + final march"
-            % ",".join(str(n) for n in nsubs))
+            "%s, build interface + GMRES(30) to 1e-10 + final march"
+            % (",".join(str(n) for n in nsubs), tcs))
 
 
 def workload_name_timedep():
@@ -143,7 +148,7 @@ def cpu_oracle_sample(wl_full, nsub_sample):
     import oracle as O
     P = O.Problem(wl_full.a0, wl_full.b0, wl_full.nx, wl_full.dt, wl_full.nt,
                   wl_full.off.astype(np.int64), wl_full.u0, wl_full.V, vkind=wl_full.vkind,
-                  sigma=wl_full.sigma)
+                  tc=wl_full.tc, sigma=wl_full.sigma)
     t0 = time.perf_counter()
     ps = 0
     N = P.nsub
@@ -164,6 +169,8 @@ def run_reference(args):
         return
     from paper_1503_02564_gb300 import workloads as W
     wl = W.config2(nsub=500)
+    if args.tc == "s02":
+        wl.tc = 1
     # each step: 25 of the 500 subdomain marches (about 5e6 point-steps)
     for _ in range(args.warmup):
         cpu_oracle_sample(wl, 25)
@@ -179,7 +186,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(NSUBS),
+        "config": {"workload": workload_name(NSUBS, args.tc),
                    "sample": "oracle d-marches of subdomains 0..24 of N=500 per step"},
         "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
                          "sample": "25 of 500 subdomain marches (401 nodes x 500 steps each)"},
@@ -219,9 +226,11 @@ def main():
                             maxit=400, tol_abs=1e-10, precond=swr.SWR_PC_MEAN_POTENTIAL)
         else:
             wl = W.config2(nsub=N)
+            if args.tc == "s02":
+                wl.tc = swr.SWR_TC_S02
             plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
-                            node_off=wl.off, p=wl.sigma, restart=30, maxit=2000, tol_abs=1e-10,
-                            precond=precond)
+                            node_off=wl.off, p=wl.sigma, tc=wl.tc, restart=30, maxit=2000,
+                            tol_abs=1e-10, precond=precond)
         V = torch.tensor(np.ascontiguousarray(wl.V).ravel(), dtype=torch.float64, device=dev)
         u0 = torch.tensor(wl.u0, dtype=torch.complex128, device=dev)
         g = torch.zeros(plan.n_interface, dtype=torch.complex128, device=dev)
@@ -353,7 +362,7 @@ def main():
             "value": value, "unit": "point-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name_timedep() if timedep else workload_name(nsubs),
+            "config": {"workload": workload_name_timedep() if timedep else workload_name(nsubs, args.tc),
                        "point_steps_per_step": ps_step,
                        "precond": "mean_potential" if timedep else args.precond, "l2": "flushed by a 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

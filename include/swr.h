@@ -52,7 +52,13 @@ typedef enum swr_status {
 /* Potential kinds (Eq. Schequ: V(t,x) or f(u)). */
 enum { SWR_V_STATIC = 0, SWR_V_TIME = 1, SWR_V_NONLINEAR = 2 };
 /* Transmission operators S-bar (Section 2.2): Robin S-bar v = p v (the paper's
- * S = -ip corresponds to p = -i p_paper); potential strategy of order 2, S_0^2. */
+ * S = -ip corresponds to p = -i p_paper); potential strategy of order 2, S_0^2:
+ * S-bar v_n = c2 sum_{s=0}^{n} beta_{n-s} v_s, c2 = e^{-i pi/4} sqrt(2/dt),
+ * beta_s = (-1)^s alpha_s the coefficients of sqrt((1-z)/(1+z)), v_0 = u_0 at
+ * the end.  The s = n term enters the subdomain matrix (sigma0 = c2), the
+ * history sum the end rows and the emitted fluxes.  S_0^2 with V(t,x) needs the
+ * streamed per-step factors (swr_build_interface returns SWR_ERR_UNSUPPORTED
+ * when they do not fit in half of the free device memory). */
 enum { SWR_TC_ROBIN = 0, SWR_TC_S02 = 1 };
 /* Interface solvers: GMRES (Algorithms 2-3), fixed point on (I - L) g = d
  * (Algorithm 3 with the fixed point), classical iteration g <- R g with full
@@ -84,7 +90,7 @@ typedef struct swr_desc {
                                 /* one extra element                                  */
     int32_t vkind;              /* SWR_V_*                                             */
     int32_t tc;                 /* SWR_TC_*                                            */
-    double tc_re, tc_im;        /* Robin parameter p (S-bar v = p v)                   */
+    double tc_re, tc_im;        /* Robin parameter p (S-bar v = p v); unused by S_0^2  */
     int32_t solver;             /* SWR_SOLVER_*                                        */
     int32_t restart;            /* GMRES restart length m (default 30 if <= 0, at most 200)      */
     int32_t maxit;              /* iteration cap (default 2000 if <= 0)                */

@@ -47,6 +47,9 @@ struct swr_plan_s {
     int N = 0, nx = 0, nt = 0, nblk = 0, nmax = 0, ntot = 0, nsm = 152;
     double h = 0.0;
     double2 inv_ik{}, sigma0{}, two_sigma{};
+    double2 c2{}, c2_ik{};         // S_0^2: c2 and c2 / (i kappa)
+    double* d_beta = nullptr;      // S_0^2: beta_0..beta_nt
+    double2* d_s02hist = nullptr;  // S_0^2: end traces of every system of a launch
     std::vector<int> off, n, goff, loff, tc;
     int *d_n = nullptr, *d_goff = nullptr, *d_loff = nullptr, *d_tc = nullptr;
     double2 *d_dg = nullptr, *d_od = nullptr;       // A - B for V (static) or V0
@@ -300,6 +303,13 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     a.two_sigma = p->two_sigma;
     a.inv_ik = p->inv_ik;
     a.status = p->d_status;
+    if (p->d.tc == SWR_TC_S02) {
+        a.s02 = 1;
+        a.beta = p->d_beta;
+        a.hist = p->d_s02hist;
+        a.c2_ik = p->c2_ik;
+        a.two_c2 = make_double2(2.0 * p->c2.x, 2.0 * p->c2.y);
+    }
     const double kappa = 2.0 / p->d.dt * (p->h / 6.0);
     if (kind == MK_TDEP)
         return swr_launch_march_tdep(fs, a, p->d_V, p->nx, p->h, kappa,
@@ -810,6 +820,7 @@ void swr_destroy(swr_plan_t p) {
         swr_factor_free(p->fsL[k]);
         swr_factor_free(p->fs0L[k]);
     }
+    cudaFree(p->d_beta); cudaFree(p->d_s02hist);
     cudaFree(p->d_u0); cudaFree(p->d_V); cudaFree(p->d_Vbar); cudaFree(p->d_iface); cudaFree(p->d_iface0);
     cudaFree(p->d_lag0); cudaFree(p->d_lag0_0); cudaFree(p->d_hist); cudaFree(p->d_gtmp);
     cudaFree(p->d_gtmp2); cudaFree(p->d_trace);
@@ -832,7 +843,8 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     if (!d) return SWR_ERR_ARG;
     if (d->nx < 3 || d->nt < 1 || !(d->dt > 0.0) || d->nsub < 2 || !(d->b0 > d->a0))
         return SWR_ERR_ARG;
-    if (d->vkind < 0 || d->vkind > 2 || d->tc != SWR_TC_ROBIN) return d->tc == SWR_TC_S02 ? SWR_ERR_UNSUPPORTED : SWR_ERR_ARG;
+    if (d->vkind < 0 || d->vkind > 2 || d->tc < SWR_TC_ROBIN || d->tc > SWR_TC_S02)
+        return SWR_ERR_ARG;
     if (d->solver < 0 || d->solver > 2 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_NONLINEAR && d->solver == SWR_SOLVER_GMRES) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_TIME && d->solver == SWR_SOLVER_FIXED_POINT) return SWR_ERR_ARG;
@@ -885,8 +897,19 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     p->nmax = nmax;
     const double kappa = 2.0 / d->dt * (p->h / 6.0);
     p->inv_ik = make_double2(0.0, -1.0 / kappa);   // 1/(i kappa)
-    p->sigma0 = make_double2(d->tc_re, d->tc_im);
-    p->two_sigma = make_double2(2.0 * d->tc_re, 2.0 * d->tc_im);
+    if (d->tc == SWR_TC_S02) {
+        // S_0^2 (Section 2.2): S-bar v_n = c2 sum_{s<=n} beta_{n-s} v_s with
+        // c2 = e^{-i pi/4} sqrt(2/dt); the s = n term, c2 beta_0 = c2, is the
+        // boundary matrix entry sigma0
+        const double r = std::sqrt(2.0 / d->dt) * std::sqrt(0.5);
+        p->c2 = make_double2(r, -r);
+        p->sigma0 = p->c2;
+        p->two_sigma = make_double2(2.0 * r, -2.0 * r);
+        p->c2_ik = cmul_h(p->c2, p->inv_ik);
+    } else {
+        p->sigma0 = make_double2(d->tc_re, d->tc_im);
+        p->two_sigma = make_double2(2.0 * d->tc_re, 2.0 * d->tc_im);
+    }
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -945,6 +968,22 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
         for (int j = 0; j < p->N; ++j) p->work_R += (long long)p->n[j] * p->nt;
         st = upload_systems(&p->d_sys_build, vb);
     }
+    if (!st && d->tc == SWR_TC_S02) {
+        // beta_s = (-1)^s alpha_s, alpha_{2k} = alpha_{2k+1} = prod_{i<=k} (2i-1)/(2i):
+        // the coefficients of sqrt((1-z)/(1+z)) (Section 2.2)
+        std::vector<double> beta(p->nt + 1);
+        double alpha = 1.0;
+        for (int k = 0; k <= p->nt; ++k) {
+            if (k > 0 && k % 2 == 0) alpha *= (double)(k - 1) / (double)k;
+            beta[k] = (k % 2 == 0) ? alpha : -alpha;
+        }
+        st = dalloc(&p->d_beta, p->nt + 1);
+        if (!st && cudaMemcpy(p->d_beta, beta.data(), sizeof(double) * (p->nt + 1),
+                              cudaMemcpyHostToDevice) != cudaSuccess)
+            st = SWR_ERR_CUDA;
+        if (!st)
+            st = dalloc(&p->d_s02hist, (size_t)std::max(p->nsys_build, p->N) * 2 * (p->nt + 1));
+    }
     if (!st) st = upload_systems(&p->d_sys_R, apply_systems(p->N, 0));
     if (!st) st = upload_systems(&p->d_sys_final, apply_systems(p->N, SYS_WRITE_UT | SYS_TRACE));
     if (!st) {
@@ -977,6 +1016,8 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
         // per node and step); take them while they use at most half the free memory
         bool on = p->nt >= 2;
         if (const char* e = getenv("SWR_TDEP_PRECOMP")) on = on && atoi(e) != 0;
+        // the refactorising march has no S_0^2 history terms
+        if (p->d.tc == SWR_TC_S02) on = p->nt >= 2;
         if (on) {
             size_t fr = 0, tot = 0;
             CK(cudaMemGetInfo(&fr, &tot));

@@ -47,6 +47,26 @@ __device__ __forceinline__ double2 csel(bool c, double2 a, double2 b) {
     return r;
 }
 
+// S_0^2 history sum of one end, sum_{s=0}^{t-1} beta_{t-s} hist[s], by one full
+// warp: lanes strided over s, then a fixed butterfly (lane 0's value is the same
+// from run to run).
+__device__ __forceinline__ double2 s02_history(const double* __restrict__ beta,
+                                               const double2* hist, int t, int lane) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int s = lane; s < t; s += 32) {
+        const double b = beta[t - s];
+        const double2 v = hist[s];
+        acc.x = fma(b, v.x, acc.x);
+        acc.y = fma(b, v.y, acc.y);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    return acc;
+}
+
 // ---------------------------------------------------------------------------
 // device status word bits
 // ---------------------------------------------------------------------------
@@ -119,6 +139,14 @@ struct MarchArgs {
     double2* uT;          // nodal output
     double2* trace;       // [nsys][2][nt]
     long long fstride, sstride, pstride;   // per-step factor strides (0: constant matrix)
+    // S_0^2 transmission condition (Section 2.2): S-bar v_n = c2 sum_{s<=n} beta_{n-s} v_s.
+    // The current-step term sits in the matrix (sigma0 = c2 beta_0) and in two_sigma;
+    // the history b_n = c2 sum_{s<n} beta_{n-s} v_s enters the end rows and the fluxes.
+    int s02;
+    const double* beta;   // [nt+1]
+    double2* hist;        // [nsys][2][nt+1] end traces v_0..v_nt (v_0 = u0 at the end)
+    double2 c2_ik;        // c2 / (i kappa)
+    double2 two_c2;       // 2 c2
     double2 two_sigma;    // 2 p (Robin): 2 S-tilde v = 2 p v
     double2 inv_ik;       // 1/(i kappa), kappa = (2/dt)(h/6): the system is scaled by it
     int* status;

@@ -462,7 +462,9 @@ int swr_launch_factor_steps(FactorSet& fs, int N, const int* d_n, const int* d_g
 // Shared memory (per CTA): separator values usep, PCR ping-pong dA/dB
 // ([T+G] each) and, per chunk, the first/last interior u and y ([T] each).
 // ---------------------------------------------------------------------------
-int swr_march_smem_bytes(int T, int G) { return (int)sizeof(double2) * (3 * (T + G) + 4 * T); }
+int swr_march_smem_bytes(int T, int G) {
+    return (int)sizeof(double2) * (3 * (T + G) + 4 * T + 2 * G);
+}
 
 template <int L>
 __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const MarchArgs a) {
@@ -476,6 +478,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
     double2* ulst = ufst + T;
     double2* yfst = ulst + T;
     double2* ylst = yfst + T;
+    double2* hsum = ylst + T;        // [2G] S_0^2 history sums of this step (C > 1: [2])
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (C > 1) ? (int)cl.block_rank() : 0;
     const int tid = threadIdx.x;
@@ -542,6 +545,14 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         y[i] = zero;
     }
     if (valid) *SEP(usep, p) = (realsep && !zero_u0) ? a.u0[goff + sp] : zero;
+    // S_0^2: the end traces start with v_0 = u_0 at the end
+    const bool hl = a.s02 && realsep && p == 0 && (tcf & 1);
+    const bool hr = a.s02 && realsep && p == Pj && (tcf & 2);
+    double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * (nt + 1) : nullptr;
+    double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * (nt + 1) : nullptr;
+    if (hl) hist_l[0] = zero_u0 ? zero : a.u0[goff + sp];
+    if (hr) hist_r[0] = zero_u0 ? zero : a.u0[goff + sp];
+    const int hs_l = (C == 1) ? 2 * g : 0, hs_r = hs_l + 1;
     SYNC();
 
     double2 lin = zero, rin = zero;
@@ -600,6 +611,31 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
             *CHK(yfst, p) = y[0];
             *CHK(ylst, p) = yl;
         }
+        if (a.s02) {
+            // history sums of the ends this CTA holds, one warp per end
+            const int lane = tid & 31, w = tid >> 5, nw = T >> 5;
+            if (C == 1) {
+                for (int e = w; e < 2 * G; e += nw) {
+                    const int gs = blockIdx.x * G + (e >> 1), side = e & 1;
+                    if (gs < a.nsys && (a.sub_tc[a.sys[gs].sub] & (1 << side))) {
+                        const double2 hsv = s02_history(
+                            a.beta, a.hist + ((size_t)gs * 2 + side) * (nt + 1), t, lane);
+                        if (lane == 0) hsum[e] = hsv;
+                    }
+                }
+            } else {
+                const int Pe = a.sub_P[a.sys[sidx].sub];
+                const int tce = a.sub_tc[a.sys[sidx].sub];
+                if (w == 0 && rank == 0 && (tce & 1)) {
+                    const double2 hsv = s02_history(a.beta, hist_l, t, lane);
+                    if (lane == 0) hsum[0] = hsv;
+                }
+                if (w == (nw > 1 ? 1 : 0) && rank == Pe / T && (tce & 2)) {
+                    const double2 hsv = s02_history(a.beta, hist_r, t, lane);
+                    if (lane == 0) hsum[1] = hsv;
+                }
+            }
+        }
         SYNC();
         // ---- phase B: reduced right-hand side at my separator ------------------
         if (valid) {
@@ -622,6 +658,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     else
                         lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
                     f = cfms(lin, a.inv_ik, f);
+                    if (a.s02) f = cfma(hsum[hs_l], a.c2_ik, f);
                 }
                 if (re && (tcf & 2)) {
                     if (sy.flags & SYS_IMP_R)
@@ -629,6 +666,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     else
                         rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
                     f = cfms(rin, a.inv_ik, f);
+                    if (a.s02) f = cfma(hsum[hs_r], a.c2_ik, f);
                 }
                 d = f;
                 if (!le) d = cfms(sE_l[p], *CHK(ylst, p - 1), d);
@@ -674,13 +712,21 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
             const double2 uo = *us;
             *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
             if (p == 0) {
-                if ((tcf & 1) && sy.out_a >= 0 && a.gout)
-                    a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
+                if (hl) hist_l[t] = v;
+                if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
+                    double2 o = csub(cmul(a.two_sigma, v), lin);
+                    if (a.s02) o = cfma(a.two_c2, hsum[hs_l], o);
+                    a.gout[(size_t)sy.out_a * nt + t - 1] = o;
+                }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
             if (p == Pj) {
-                if ((tcf & 2) && sy.out_b >= 0 && a.gout)
-                    a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
+                if (hr) hist_r[t] = v;
+                if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
+                    double2 o = csub(cmul(a.two_sigma, v), rin);
+                    if (a.s02) o = cfma(a.two_c2, hsum[hs_r], o);
+                    a.gout[(size_t)sy.out_b * nt + t - 1] = o;
+                }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
         }
@@ -1079,6 +1125,7 @@ static int launch_tdep_t(TdepArgs ta, int ngroups, cudaStream_t s) {
 
 int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, long long vstride,
                           double h, double kappa, double2 sig_ik, int ngroups, cudaStream_t s) {
+    if (a.s02) return -2;   // no S_0^2 history terms in the refactorising march
     a.P = fs.P;
     a.levels = fs.levels;
     a.sub_P = fs.sub_P;

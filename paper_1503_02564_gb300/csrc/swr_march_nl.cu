@@ -51,7 +51,8 @@ __device__ __forceinline__ unsigned long long dbits(double v) {
 }
 
 int swr_march_nl_smem_bytes(int T, int G) {
-    return (int)sizeof(double2) * (4 * (T + G) + 6 * T) + (int)sizeof(unsigned long long) * (4 * G + 4);
+    return (int)sizeof(double2) * (4 * (T + G) + 6 * T + 2 * G) +
+           (int)sizeof(unsigned long long) * (4 * G + 4);
 }
 
 template <int L>
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
     // reductions: red[slot][g][0] = max |dz|^2, red[slot][g][1] = max |z|^2; cnt[slot]
     unsigned long long* red = reinterpret_cast<unsigned long long*>(ylst + T);
     unsigned long long* cnt = red + 4 * G;
+    double2* hsum = reinterpret_cast<double2*>(cnt + 4);   // [2G] S_0^2 history sums
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (C > 1) ? (int)cl.block_rank() : 0;
     const int tid = threadIdx.x;
@@ -156,6 +158,14 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
         *SEP(zsep, p) = u0s;
     }
     for (int q = tid; q < 4 * G + 4; q += blockDim.x) red[q] = 0ull;   // slots and counters
+    // S_0^2: the end traces start with v_0 = u_0 at the end
+    const bool hl = a.s02 && realsep && p == 0 && (tcf & 1);
+    const bool hr = a.s02 && realsep && p == Pj && (tcf & 2);
+    double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * (nt + 1) : nullptr;
+    double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * (nt + 1) : nullptr;
+    if (hl) hist_l[0] = zero_u0 ? zero : a.u0[goff + sp];
+    if (hr) hist_r[0] = zero_u0 ? zero : a.u0[goff + sp];
+    const int hs_l = (C == 1) ? 2 * g : 0, hs_r = hs_l + 1;
     SYNC();
 
     double2 lin = zero, rin = zero, fs = zero;
@@ -184,6 +194,31 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
             *CHK(ufst, p) = uf;
             *CHK(ulst, p) = ul;
         }
+        if (a.s02) {
+            // history sums of the ends this CTA holds, one warp per end
+            const int lane = tid & 31, w = tid >> 5, nw = T >> 5;
+            if (C == 1) {
+                for (int e = w; e < 2 * G; e += nw) {
+                    const int gs = blockIdx.x * G + (e >> 1), side = e & 1;
+                    if (gs < a.nsys && (a.sub_tc[a.sys[gs].sub] & (1 << side))) {
+                        const double2 hsv = s02_history(
+                            a.beta, a.hist + ((size_t)gs * 2 + side) * (nt + 1), t, lane);
+                        if (lane == 0) hsum[e] = hsv;
+                    }
+                }
+            } else {
+                const int Pe = a.sub_P[a.sys[sidx].sub];
+                const int tce = a.sub_tc[a.sys[sidx].sub];
+                if (w == 0 && rank == 0 && (tce & 1)) {
+                    const double2 hsv = s02_history(a.beta, hist_l, t, lane);
+                    if (lane == 0) hsum[0] = hsv;
+                }
+                if (w == (nw > 1 ? 1 : 0) && rank == Pe / T && (tce & 2)) {
+                    const double2 hsv = s02_history(a.beta, hist_r, t, lane);
+                    if (lane == 0) hsum[1] = hsv;
+                }
+            }
+        }
         // reduction slot 0 serves the first inner iteration of this step
         for (int q = tid; q < 2 * G; q += blockDim.x) red[q] = 0ull;
         if (tid == 0) *CNT(0) = 0ull;
@@ -205,6 +240,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 else
                     lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
                 fs = cfms(lin, a.inv_ik, fs);
+                if (a.s02) fs = cfma(hsum[hs_l], a.c2_ik, fs);
             }
             if (re && (tcf & 2)) {
                 if (sy.flags & SYS_IMP_R)
@@ -212,6 +248,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 else
                     rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
                 fs = cfms(rin, a.inv_ik, fs);
+                if (a.s02) fs = cfma(hsum[hs_r], a.c2_ik, fs);
             }
         }
         // ---- inner fixed point (Eq. AvMNL) ------------------------------------
@@ -380,13 +417,21 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
             const double2 uo = *us;
             *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
             if (p == 0) {
-                if ((tcf & 1) && sy.out_a >= 0 && a.gout)
-                    a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
+                if (hl) hist_l[t] = v;
+                if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
+                    double2 o = csub(cmul(a.two_sigma, v), lin);
+                    if (a.s02) o = cfma(a.two_c2, hsum[hs_l], o);
+                    a.gout[(size_t)sy.out_a * nt + t - 1] = o;
+                }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
             if (p == Pj) {
-                if ((tcf & 2) && sy.out_b >= 0 && a.gout)
-                    a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
+                if (hr) hist_r[t] = v;
+                if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
+                    double2 o = csub(cmul(a.two_sigma, v), rin);
+                    if (a.s02) o = cfma(a.two_c2, hsum[hs_r], o);
+                    a.gout[(size_t)sy.out_b * nt + t - 1] = o;
+                }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
         }

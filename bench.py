@@ -31,6 +31,22 @@ FLOPS_PER_POINT_STEP = 36          # Thomas with stored factors, per node and ti
 FLOPS_PER_POINT_STEP_TDEP = 56     # plus the per-step factorisation (one complex reciprocal)
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flop x GHz (max SM clock)
 
+# DRAM bytes (read + write) per march launch, mean over the timed step's march launches, from
+# the ncu launch lists summarised in profiles/launch_list_scaling.md and
+# profiles/launch_list_timedep.md; valid only for the march sources they were taken from
+# (sha256 prefix of swr_march.cu + swr_internal.cuh), null otherwise.
+MARCH_TRAFFIC = {"sources": "456be31e0d81e772",
+                 "scaling": 22309600.0, "timedep": 6631845878.0}
+
+
+def march_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("swr_march.cu", "swr_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1503_02564_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -48,6 +64,12 @@ def parse():
                     help="transmission condition of the scaling workload: Robin "
                          "p = sqrt(5) e^{-i pi/4} (default) or the order-2 potential "
                          "strategy S_0^2")
+    ap.add_argument("--pc-sweeps", type=int, default=-1,
+                    help="block-Jacobi sweeps of the causal preconditioner's same-step "
+                         "coupling (-1: the library's choice)")
+    ap.add_argument("--nt", type=int, default=0,
+                    help="override the workload's number of time steps (smaller cases for "
+                         "profiling; 0: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -60,16 +82,16 @@ def dist_env():
     return rank, world, local
 
 
-def workload_name(nsubs, tc="robin"):
+def workload_name(nsubs, tc="robin", nt=500):
     tcs = ("S_0^2 c2=e^{-i pi/4}sqrt(2/dt)" if tc == "s02" else "Robin p=sqrt(5)e^{-i pi/4}")
-    return ("swr_scaling: x in (-50,50), 200001 P1 nodes, T=0.5 dt=1e-3 (500 steps), "
+    return ("swr_scaling: x in (-50,50), 200001 P1 nodes, T=%g dt=1e-3 (%d steps), "
             "N in {%s}, V=-5*sum of 8 seeded Gaussians, u0=4 seeded packets, "
             "%s, build interface + GMRES(30) to 1e-10 + final march"
-            % (",".join(str(n) for n in nsubs), tcs))
+            % (nt * 1e-3, nt, ",".join(str(n) for n in nsubs), tcs))
 
 
-def workload_name_timedep():
-    return ("swr_timedep: x in (-30,30), 60001 P1 nodes, T=1 dt=1e-3 (1000 steps), N=64, "
+def workload_name_timedep(nt=1000):
+    return ("swr_timedep: x in (-30,30), 60001 P1 nodes, T=%g dt=1e-3 (%d steps), N=64, " % (nt * 1e-3, nt) +
             "V=-x^2/4(1+0.5 sin 4t)-10exp(-(x-5 sin t)^2), seeded packet, Robin "
             "p=sqrt(5)e^{-i pi/4}, d = R0 + GMRES(60) on g - Rg + d preconditioned by the "
             "mean-potential interface operator to 1e-10 + final march")
@@ -220,17 +242,17 @@ def main():
     cases = []
     for N in nsubs:
         if timedep:
-            wl = W.config4(nsub=N)
+            wl = W.config4(nsub=N, nt=args.nt) if args.nt > 0 else W.config4(nsub=N)
             plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
                             node_off=wl.off, p=wl.sigma, vkind=swr.SWR_V_TIME, restart=60,
                             maxit=400, tol_abs=1e-10, precond=swr.SWR_PC_MEAN_POTENTIAL)
         else:
-            wl = W.config2(nsub=N)
+            wl = W.config2(nsub=N, nt=args.nt) if args.nt > 0 else W.config2(nsub=N)
             if args.tc == "s02":
                 wl.tc = swr.SWR_TC_S02
             plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
                             node_off=wl.off, p=wl.sigma, tc=wl.tc, restart=30, maxit=2000,
-                            tol_abs=1e-10, precond=precond)
+                            tol_abs=1e-10, precond=precond, pc_sweeps=args.pc_sweeps)
         V = torch.tensor(np.ascontiguousarray(wl.V).ravel(), dtype=torch.float64, device=dev)
         u0 = torch.tensor(wl.u0, dtype=torch.complex128, device=dev)
         g = torch.zeros(plan.n_interface, dtype=torch.complex128, device=dev)
@@ -292,6 +314,10 @@ def main():
     # V(t,x): variant 3 streams every step's factors (computed once per build)
     # through the constant-matrix march kernel; variant 1 refactorises per step
     variant = st[0]["march_variant"]
+    traffic = None
+    if (march_sources_hash() == MARCH_TRAFFIC["sources"] and args.nt == 0 and args.tc == "robin"
+            and (timedep or tuple(nsubs) == NSUBS)):
+        traffic = MARCH_TRAFFIC["timedep" if timedep else "scaling"]
     streamed = variant == swr.MARCH_TDEP_STREAMED
     fpp = FLOPS_PER_POINT_STEP_TDEP if variant == swr.MARCH_TDEP_REFACTOR else FLOPS_PER_POINT_STEP
     m_kernel = "k_march_tdep" if variant == swr.MARCH_TDEP_REFACTOR else "k_march_static"
@@ -362,14 +388,14 @@ def main():
             "value": value, "unit": "point-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name_timedep() if timedep else workload_name(nsubs, args.tc),
+            "config": {"workload": workload_name_timedep(cases[0]["wl"].nt) if timedep else workload_name(nsubs, args.tc, cases[0]["wl"].nt),
                        "point_steps_per_step": ps_step,
                        "precond": "mean_potential" if timedep else args.precond, "l2": "flushed by a 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"kernel": m_kernel, "bound": "alu",
                          "achieved": achieved,
                          "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
                          "launches": m_launch, "avg_launch_ms": m_ms / max(m_launch, 1),
                          "flops_per_point_step": fpp,
                          "peak_basis": "nominal FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",

@@ -460,6 +460,10 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
             cudaGetLastError();
             continue;
         }
+        if (const char* e = getenv("SWR_DEBUG"))
+            if (atoi(e) >= 2)
+                fprintf(stderr, "swr autotune probe kind %d nsys %d: L %d C %d G %d T %d %.3f ms\n",
+                        kind, nsys, c.L, c.C, c.G, c.T, ms);
         if (best_ms < 0.f || ms < best_ms) {
             best_ms = ms;
             best = c;

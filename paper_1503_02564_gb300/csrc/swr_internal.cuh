@@ -139,6 +139,7 @@ struct MarchArgs {
     double2* uT;          // nodal output
     double2* trace;       // [nsys][2][nt]
     long long fstride, sstride, pstride;   // per-step factor strides (0: constant matrix)
+    int stage;            // staging of streamed factors in shared memory (0, 1, 2)
     // S_0^2 transmission condition (Section 2.2): S-bar v_n = c2 sum_{s<=n} beta_{n-s} v_s.
     // The current-step term sits in the matrix (sigma0 = c2 beta_0) and in two_sigma;
     // the history b_n = c2 sum_{s<n} beta_{n-s} v_s enters the end rows and the fluxes.
@@ -178,7 +179,7 @@ int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef
                         int maxit, int* iters, int ngroups, cudaStream_t s);
 int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, long long vstride,
                           double h, double kappa, double2 sig_ik, int ngroups, cudaStream_t s);
-int swr_march_smem_bytes(int T, int G);
+int swr_march_smem_bytes(int T, int G, int stage_slots = 0);
 
 // Interface algebra launchers (swr_krylov.cu)
 int swr_launch_toeplitz(int N, int nt, const double2* cols, const double2* x, const double2* add,

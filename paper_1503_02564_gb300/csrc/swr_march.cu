@@ -36,6 +36,21 @@ namespace cg = cooperative_groups;
 __device__ __forceinline__ void prefetch_l2(const void* ptr) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
 }
+// 16-byte asynchronous global -> shared copy (bypassing L1) and its group control
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Assembly of A_j - B_j (P1 elements, generalised mass by exact quadrature of the
@@ -462,8 +477,8 @@ int swr_launch_factor_steps(FactorSet& fs, int N, const int* d_n, const int* d_g
 // Shared memory (per CTA): separator values usep, PCR ping-pong dA/dB
 // ([T+G] each) and, per chunk, the first/last interior u and y ([T] each).
 // ---------------------------------------------------------------------------
-int swr_march_smem_bytes(int T, int G) {
-    return (int)sizeof(double2) * (3 * (T + G) + 4 * T + 2 * G);
+int swr_march_smem_bytes(int T, int G, int stage_slots) {
+    return (int)sizeof(double2) * (3 * (T + G) + 4 * T + 2 * G + stage_slots * T);
 }
 
 template <int L>
@@ -537,6 +552,55 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
     const double2* sbinv = a.sep + (size_t)(j * 3 + 2) * (P + 1);
     const double2* pcr = a.pcr + (size_t)j * levels * 2 * (P + 1);
     const bool stepped = a.fstride != 0;
+    // Streamed per-step factors are staged one step ahead in shared memory by
+    // asynchronous copies, each thread copying exactly the entries it reads
+    // (element-major slots, slot k of thread tid at stg[k * T + tid]):
+    //   stage 1: separator data (E_l, E_r, 1/delta, PCR coefficients);
+    //   stage 2: also the chunk factors (q, c) and the spikes (a, b).
+    // Every phase refills its buffer for step t+1 right after its last read at
+    // step t, and waits (cp.async.wait_group 2) before its first read: the
+    // groups are committed in the fixed order (q,c) | separator | (a,b).
+    const int stage = a.stage;
+    const int npc = 2 * levels + 3;
+    double2* stg = hsum + 2 * G;
+    auto issue_fa = [&](const double2* Fs) {   // Fs == nullptr: commit an empty group
+        if (stage >= 2 && Fs && valid && Lp > 0) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) {
+                    cp_async16(stg + (npc + i * 2 + 0) * T + tid, Fs + (i * 4 + 0) * P);
+                    cp_async16(stg + (npc + i * 2 + 1) * T + tid, Fs + (i * 4 + 1) * P);
+                }
+        }
+        cp_async_commit();
+    };
+    auto issue_fd = [&](const double2* Fs) {
+        if (stage >= 2 && Fs && valid && Lp > 0) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) {
+                    cp_async16(stg + (npc + 2 * L + i * 2 + 0) * T + tid, Fs + (i * 4 + 2) * P);
+                    cp_async16(stg + (npc + 2 * L + i * 2 + 1) * T + tid, Fs + (i * 4 + 3) * P);
+                }
+        }
+        cp_async_commit();
+    };
+    auto issue_pc = [&](bool on, long long sofs, long long pofs) {
+        if (stage >= 1 && on && valid) {
+            cp_async16(stg + 0 * T + tid, sE_l + sofs + p);
+            cp_async16(stg + 1 * T + tid, sE_r + sofs + p);
+            cp_async16(stg + 2 * T + tid, sbinv + sofs + p);
+            for (int k = 0; k < 2 * levels; ++k)
+                cp_async16(stg + (3 + k) * T + tid, pcr + pofs + (size_t)k * (P + 1) + p);
+        }
+        cp_async_commit();
+    };
+    // chunk factor (i, k) and separator datum k of the current step
+    auto FAC = [&](int i, int k) -> double2 {
+        if (stage >= 2)
+            return stg[(npc + (k < 2 ? i * 2 + k : 2 * L + i * 2 + k - 2)) * T + tid];
+        return F[(i * 4 + k) * P];
+    };
 
     double2 u[L], y[L];
 #pragma unroll
@@ -553,11 +617,16 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
     if (hl) hist_l[0] = zero_u0 ? zero : a.u0[goff + sp];
     if (hr) hist_r[0] = zero_u0 ? zero : a.u0[goff + sp];
     const int hs_l = (C == 1) ? 2 * g : 0, hs_r = hs_l + 1;
+    if (stage > 0) {   // step 1's factors
+        issue_fa(F);
+        issue_pc(true, 0, 0);
+        issue_fd(F);
+    }
     SYNC();
 
     double2 lin = zero, rin = zero;
     for (int t = 1; t <= nt; ++t) {
-        if (stepped && valid && t < nt) {
+        if (stage == 0 && stepped && valid && t < nt) {
             // the next step's factors stream from HBM: request them into L2 now
             if (Lp > 0) {
 #pragma unroll
@@ -572,6 +641,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
             for (int k = 0; k < 2 * levels; ++k) prefetch_l2(pcr + a.pstride + (size_t)k * (P + 1) + p);
         }
         // ---- phase A: chunk right-hand sides and local LU solves -------------
+        if (stage >= 2) cp_async_wait<2>();
         if (valid && Lp > 0) {
             const double2 uL = *SEP(usep, p), uR = *SEP(usep, p + 1);
             double2 zprev = zero, cprev = zero, uf = zero, ul = zero;
@@ -589,7 +659,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     const double2 z = (i == 0) ? f : cfms(cprev, zprev, f);
                     y[i] = z;
                     zprev = z;
-                    cprev = F[(i * 4 + 1) * P];
+                    cprev = FAC(i, 1);
                     if (i == 0) uf = u[i];
                     ul = csel(i == Lp - 1, u[i], ul);
                 }
@@ -598,9 +668,9 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
 #pragma unroll
             for (int i = L - 1; i >= 0; --i) {
                 if (i < Lp) {
-                    const double2 qi = F[(i * 4 + 0) * P];
+                    const double2 qi = FAC(i, 0);
                     double2 yi = cmul(qi, y[i]);
-                    if (i != Lp - 1) yi = cfms(F[(i * 4 + 1) * P], ynext, yi);
+                    if (i != Lp - 1) yi = cfms(FAC(i, 1), ynext, yi);
                     else yl = yi;
                     y[i] = yi;
                     ynext = yi;
@@ -611,6 +681,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
             *CHK(yfst, p) = y[0];
             *CHK(ylst, p) = yl;
         }
+        if (stage > 0) issue_fa(t < nt ? F + a.fstride : nullptr);
         if (a.s02) {
             // history sums of the ends this CTA holds, one warp per end
             const int lane = tid & 31, w = tid >> 5, nw = T >> 5;
@@ -638,6 +709,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         }
         SYNC();
         // ---- phase B: reduced right-hand side at my separator ------------------
+        if (stage >= 1) cp_async_wait<2>();
         if (valid) {
             double2 d = zero;
             if (realsep) {
@@ -669,8 +741,10 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     if (a.s02) f = cfma(hsum[hs_r], a.c2_ik, f);
                 }
                 d = f;
-                if (!le) d = cfms(sE_l[p], *CHK(ylst, p - 1), d);
-                if (!re) d = cfms(sE_r[p], *CHK(yfst, p), d);
+                const double2 El = (stage >= 1) ? stg[0 * T + tid] : sE_l[p];
+                const double2 Er = (stage >= 1) ? stg[1 * T + tid] : sE_r[p];
+                if (!le) d = cfms(El, *CHK(ylst, p - 1), d);
+                if (!re) d = cfms(Er, *CHK(yfst, p), d);
             }
             *SEP(dA, p) = d;
         }
@@ -681,12 +755,14 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         for (int k = 0; k < levels; ++k) {
             const int st = 1 << k;
             if (valid) {
-                const double2* al = pcr + (size_t)(k * 2 + 0) * (P + 1);
-                const double2* ga = pcr + (size_t)(k * 2 + 1) * (P + 1);
+                const double2 alp = (stage >= 1) ? stg[(3 + 2 * k) * T + tid]
+                                                 : pcr[(size_t)(k * 2 + 0) * (P + 1) + p];
+                const double2 gap = (stage >= 1) ? stg[(4 + 2 * k) * T + tid]
+                                                 : pcr[(size_t)(k * 2 + 1) * (P + 1) + p];
                 double2 dd = *SEP(src, p);
-                if (p - st >= 0) dd = cfma(al[p], *SEP(src, p - st), dd);
-                if (p + st <= P) dd = cfma(ga[p], *SEP(src, p + st), dd);
-                if (k == levels - 1) dd = cmul(dd, sbinv[p]);
+                if (p - st >= 0) dd = cfma(alp, *SEP(src, p - st), dd);
+                if (p + st <= P) dd = cfma(gap, *SEP(src, p + st), dd);
+                if (k == levels - 1) dd = cmul(dd, (stage >= 1) ? stg[2 * T + tid] : sbinv[p]);
                 *SEP(dst, p) = dd;
             }
             SYNC();
@@ -694,18 +770,21 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
             src = dst;
             dst = tmp;
         }
+        if (stage > 0) issue_pc(t < nt, a.sstride, a.pstride);
         // ---- phase D: spike correction, CN update, fluxes ---------------------
+        if (stage >= 2) cp_async_wait<2>();
         if (valid && Lp > 0) {
             const double2 vL = *SEP(src, p), vR = *SEP(src, p + 1);
 #pragma unroll
             for (int i = 0; i < L; ++i) {
                 if (i < Lp) {
-                    double2 v = cfms(F[(i * 4 + 2) * P], vL, y[i]);
-                    v = cfms(F[(i * 4 + 3) * P], vR, v);
+                    double2 v = cfms(FAC(i, 2), vL, y[i]);
+                    v = cfms(FAC(i, 3), vR, v);
                     u[i] = make_double2(fma(2.0, v.x, -u[i].x), fma(2.0, v.y, -u[i].y));
                 }
             }
         }
+        if (stage > 0) issue_fd(t < nt ? F + a.fstride : nullptr);
         if (realsep) {
             const double2 v = *SEP(src, p);
             double2* us = SEP(usep, p);
@@ -737,6 +816,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         pcr += a.pstride;
         SYNC();
     }
+    if (stage > 0) cp_async_wait_all();   // no copy in flight past the loop
     // ---- final state ----------------------------------------------------------
     bool bad = false;
     if (valid) {
@@ -1144,7 +1224,8 @@ int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, lon
 
 template <int L>
 static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s) {
-    const int smem = swr_march_smem_bytes(a.T, a.G);
+    const int slots = a.stage == 2 ? 2 * a.levels + 3 + 4 * L : (a.stage == 1 ? 2 * a.levels + 3 : 0);
+    const int smem = swr_march_smem_bytes(a.T, a.G, slots);
     auto kern = k_march_static<L>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
@@ -1173,6 +1254,16 @@ int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t
     a.fstride = fs.fstride;
     a.sstride = fs.sstride;
     a.pstride = fs.pstride;
+    // streamed factors: stage them in shared memory when the slots fit (200 KB budget)
+    a.stage = 0;
+    if (fs.nsteps > 1) {
+        const int npc = 2 * fs.levels + 3;
+        const int budget = 200 * 1024;
+        if (swr_march_smem_bytes(a.T, a.G, npc + 4 * fs.L) <= budget)
+            a.stage = 2;
+        else if (swr_march_smem_bytes(a.T, a.G, npc) <= budget)
+            a.stage = 1;
+    }
     a.P = fs.P;
     a.levels = fs.levels;
     a.sub_P = fs.sub_P;

@@ -85,6 +85,29 @@ def test_tdep_apply_R_matches_oracle(case, streamed):
     plan.destroy()
 
 
+@pytest.mark.parametrize("chunk", [4, 8, 16])
+def test_tdep_streamed_long_subdomains_match_oracle(chunk):
+    """Streamed per-step factors on long subdomains (thread-block clusters): the
+    factors are staged in shared memory in full, or only the separator part when
+    the chunk factors do not fit (chunk 8 and 16 here), and the result is the same."""
+    wl = W.config4(nsub=4, nx=60001, nt=12)
+    os.environ["SWR_CHUNK_L"] = str(chunk)
+    try:
+        plan = gpu_plan(wl, True)
+    finally:
+        os.environ.pop("SWR_CHUNK_L", None)
+    g = W.random_interface(wl.nblk, wl.nt, 33)
+    gi = torch.tensor(g.ravel(), dtype=torch.complex128, device="cuda")
+    go = torch.zeros_like(gi)
+    plan.apply_R(gi, go)
+    d = torch.zeros_like(gi)
+    plan.get_interface(d, None)
+    plan.destroy()
+    P = problem(wl)
+    assert rel(go.cpu().numpy(), O.apply_R(P, g)) < TOL_MARCH
+    assert rel(d.cpu().numpy(), O.build_d(P)) < TOL_MARCH
+
+
 @pytest.mark.parametrize("streamed", [True, False])
 def test_tdep_with_constant_potential_equals_static_path(streamed):
     """Fed V(t,x) = V(x) for every t, both V(t,x) marches must give what the

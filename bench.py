@@ -20,6 +20,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -32,9 +33,9 @@ FLOPS_PER_POINT_STEP_TDEP = 56     # plus the per-step factorisation (one comple
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flop x GHz (max SM clock)
 
 # DRAM bytes (read + write) per march launch, mean over the timed step's march launches, from
-# the ncu launch lists summarised in profiles/launch_list_scaling.md and
-# profiles/launch_list_timedep.md; valid only for the march sources they were taken from
-# (sha256 prefix of swr_march.cu + swr_internal.cuh), null otherwise.
+# the ncu launch lists of the two workloads kept with the profiles; valid only for the march
+# sources they were taken from (sha256 prefix of swr_march.cu + swr_internal.cuh), null
+# otherwise.
 MARCH_TRAFFIC = {"sources": "456be31e0d81e772",
                  "scaling": 22309600.0, "timedep": 6631845878.0}
 
@@ -120,7 +121,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"swr_clocks_rank{index}.csv")
 
     def start(self):
         try:

@@ -22,7 +22,7 @@ module writes the paper's algorithms out step by step on top of them with NumPy:
   must reproduce;
 * brute-force dense L on tiny grids.
 
-Readings of points the paper leaves open (all listed in the design doc):
+Readings of points the paper leaves open:
   Robin S-bar v = sigma v with complex sigma; generalised mass by exact P1
   quadrature; equal partitions give the first E mod N subdomains one extra
   element; stopping on the absolute Euclidean norm of the true residual; the

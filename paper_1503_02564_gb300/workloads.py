@@ -7,7 +7,7 @@ Every generator uses ``numpy.random.default_rng(20150309 + config_id)``.
 The paper's own experiments (Section 6) use analytic potentials and initial
 data on (-21, 21) with dx = 1e-5; these workloads have the same kind of inputs
 (smooth real potentials, Gaussian packets or a soliton, Neumann ends, equal
-subdomains) at the sizes of the benchmark configurations listed in the design doc.
+subdomains) at the sizes of the five benchmark workloads below.
 """
 from __future__ import annotations
 

@@ -692,3 +692,68 @@ def mono_interface(P: Problem):
         g[blk_r(j)] = dnl + sbar
         g[blk_l(j + 1)] = dnr + sbar
     return g, m.uT
+
+
+# --------------------------------------------------------------------------
+# Gradient of a final-time misfit (discrete adjoint of the monodomain scheme)
+# --------------------------------------------------------------------------
+def _mass_apply(md, mo, x):
+    """M x for the P1 mass matrix given as (diag, offdiag)."""
+    y = md * x
+    y[:-1] += mo * x[1:]
+    y[1:] += mo * x[:-1]
+    return y
+
+
+def misfit(P: Problem, uT, u_target):
+    """J = (u(T) - u_target)^H M (u(T) - u_target), the M-weighted misfit."""
+    md, mo, _, _, _, _ = p1_matrices(P.nx, P.h, None)
+    e = np.asarray(uT, np.complex128) - np.asarray(u_target, np.complex128)
+    return float(np.real(np.vdot(e, _mass_apply(md, mo, e))))
+
+
+def potential_form(x, y, h):
+    """Re( x^H (dM_W / dW_k) y ) for every node k: the derivative of the P1
+    generalised mass matrix (exact quadrature of the P1 interpolant of W,
+    Eq. AvML) with respect to the nodal value W_k.  Element [a, b] contributes
+    h/12 (3 x_a* y_a + x_a* y_b + x_b* y_a + x_b* y_b) to k = a and
+    h/12 (x_a* y_a + x_a* y_b + x_b* y_a + 3 x_b* y_b) to k = b."""
+    s = np.conj(x) * y
+    c = np.conj(x[:-1]) * y[1:] + np.conj(x[1:]) * y[:-1]
+    g = np.zeros(len(x), np.complex128)
+    g[:-1] += h / 12.0 * (3.0 * s[:-1] + c + s[1:])
+    g[1:] += h / 12.0 * (s[:-1] + c + 3.0 * s[1:])
+    return np.real(g)
+
+
+def adjoint_gradient(P: Problem, u_target):
+    """dJ/dV for J = (u_N - u_target)^H M (u_N - u_target), u_N the monodomain
+    Crank-Nicolson solution at T (Eq. CNS_L with the P1 matrices of Eq. AvML,
+    Neumann ends; converged SWR reproduces it), V static and real.
+
+    Discrete adjoint of the scheme A v_n = B u_{n-1}, u_n = 2 v_n - u_{n-1}
+    with A = (2i/dt) M - S + M_V and B = (2i/dt) M: with dJ = Re(lam_n^H du_n),
+    lam_N = 2 M (u_N - u_target) and, for n = N..1,
+        A^H mu_n = lam_n,                      (A^H = conj(A): A is symmetric)
+        dJ/dV   += -2 Re(mu_n^H (dM_V/dV) v_n),
+        lam_{n-1} = 2 B^H mu_n - lam_n.
+    Every v_n comes from the forward march.  Returns (J, dJ/dV)."""
+    if P.vkind != V_STATIC:
+        raise NotImplementedError("adjoint gradient: static V only")
+    n, h, dt, nt = P.nx, P.h, P.dt, P.nt
+    m = mono_march(P, sel=np.arange(n))
+    vs = m.vsel                                   # row t = v_t (row 0 = u0)
+    md, mo, sd, so, wd, wo = p1_matrices(n, h, P.V)
+    I2 = 2j / dt
+    dg = I2 * md - sd + wd
+    lo = I2 * mo - so + wo
+    e = m.uT - np.asarray(u_target, np.complex128)
+    Me = _mass_apply(md, mo, e)
+    J = float(np.real(np.vdot(e, Me)))
+    lam = 2.0 * Me
+    grad = np.zeros(n)
+    for t in range(nt, 0, -1):
+        mu = thomas(np.conj(lo), np.conj(dg), np.conj(lo), lam)
+        grad += -2.0 * potential_form(mu, vs[t], h)
+        lam = 2.0 * np.conj(I2) * _mass_apply(md, mo, mu) - lam
+    return J, grad

@@ -400,3 +400,44 @@ def test_planted_flux_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(O, "s_tilde", orig)
     _, uTm = O.mono_interface(P)
     assert rel(r.uT, uTm) > 1e-6
+
+
+# --------------------------------------------------------------------------
+# Gradient of the final-time misfit (discrete adjoint of the monodomain scheme)
+# --------------------------------------------------------------------------
+def _adjoint_case():
+    wl = W.config1(nx=61, nt=25, nsub=3)
+    rng = np.random.default_rng(11)
+    tgt = wl.u0 * np.exp(0.3j) + 0.1 * rng.standard_normal(wl.nx)
+    return wl, tgt, rng
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """dJ/dV by the adjoint against central differences of J computed by the
+    forward monodomain march alone, in six seeded directions."""
+    wl, tgt, rng = _adjoint_case()
+    J, g = O.adjoint_gradient(problem(wl), tgt)
+
+    def J_of(V):
+        wv = W.config1(nx=61, nt=25, nsub=3)
+        wv.V = V
+        Pv = problem(wv)
+        return O.misfit(Pv, O.mono_march(Pv).uT, tgt)
+
+    assert abs(J - J_of(wl.V)) <= 1e-14 * J
+    for _ in range(6):
+        d = rng.standard_normal(wl.nx)
+        eps = 1e-4
+        fd = (J_of(wl.V + eps * d) - J_of(wl.V - eps * d)) / (2 * eps)
+        assert abs(fd - g @ d) <= 1e-7 * abs(fd)
+
+
+def test_adjoint_gradient_vanishes_for_a_conserved_norm():
+    """With u_target = 0, J = ||u(T)||_M^2 = ||u_0||_M^2 for every real V (the
+    discrete CN scheme conserves the M-norm exactly), so dJ/dV = 0."""
+    wl, tgt, _ = _adjoint_case()
+    J0, g0 = O.adjoint_gradient(problem(wl), np.zeros(wl.nx))
+    _, g = O.adjoint_gradient(problem(wl), tgt)
+    assert np.max(np.abs(g0)) <= 1e-12 * np.max(np.abs(g))
+    md, mo, *_ = O.p1_matrices(wl.nx, (wl.b0 - wl.a0) / (wl.nx - 1), None)
+    assert abs(J0 - np.real(np.vdot(wl.u0, O._mass_apply(md, mo, wl.u0)))) <= 1e-13 * J0

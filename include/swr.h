@@ -190,8 +190,31 @@ swr_status swr_get_interface(swr_plan_t p, double *d, double *cols);
  * x, y: cplx[(2N-2) * nt], distinct buffers. */
 swr_status swr_apply_precond(swr_plan_t p, const double *y, double *x);
 
-/* Gradient of J = ||u(T) - u_target||^2_M with respect to the nodal potential
- * by an adjoint march.  Not provided by this build: returns SWR_ERR_UNSUPPORTED. */
+/* Final-time misfit J = (u_T - u_target)^H M (u_T - u_target), M the P1 mass
+ * matrix of the whole grid (not a passage of the paper: the objective of the
+ * gradient below).  uT, u_target: cplx[nx] (device); ubar: cplx[nx] (device,
+ * may be NULL) receives the M-weighted cotangent 2 (u_T - u_target), i.e.
+ * dJ = Re(ubar^H M du_T); *J (host) receives J.  Synchronises the stream. */
+swr_status swr_misfit(swr_plan_t p, const double *uT, const double *u_target, double *ubar,
+                      double *J);
+
+/* Gradient dJ/dV(x) of a final-time objective J through the converged SWR
+ * solution (no counterpart in the paper, which has no adjoint).  Needs a plan
+ * with a static potential, Robin transmission and the GMRES solver, after a
+ * successful swr_solve (SWR_ERR_STATE otherwise; SWR_ERR_UNSUPPORTED for other
+ * plans).
+ *   dJ_duT:     cplx[nx] (device), the M-weighted cotangent ubar of J at u(T):
+ *               dJ = Re(ubar^H M du_T) (swr_misfit returns it for the misfit);
+ *   dJ_dV:      double[nx] (device), overwritten with dJ/dV_k for the nodal V;
+ *   ckpt_every: checkpoint interval K in time steps (<= 0: 50).
+ * Method: the discrete adjoint of the Crank-Nicolson march, conjugated and
+ * scaled, is the same march run from (dt/2i) conj(ubar); it is solved by SWR on
+ * the plan's own interface problem (same Toeplitz columns and preconditioner),
+ * then forward segments of K steps are recomputed from checkpoints of u and the
+ * adjoint march over the mirrored steps accumulates
+ *   dJ/dV_k = -2 Re sum_n (v^adj_{N-n+1})^T (dM_V/dV_k) v_n.
+ * Device memory: (ceil(nt/K) + K + 5) nx complex plus two interface vectors.
+ * Synchronises the stream. */
 swr_status swr_adjoint(swr_plan_t p, const double *dJ_duT, double *dJ_dV,
                        int32_t ckpt_every);
 

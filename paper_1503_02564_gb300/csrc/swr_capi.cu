@@ -50,6 +50,14 @@ struct swr_plan_s {
     double2 c2{}, c2_ik{};         // S_0^2: c2 and c2 / (i kappa)
     double* d_beta = nullptr;      // S_0^2: beta_0..beta_nt
     double2* d_s02hist = nullptr;  // S_0^2: end traces of every system of a launch
+    double2* d_gconv = nullptr;    // interface vector of the last successful swr_solve
+    bool solved = false;
+    // adjoint work, allocated by the first swr_adjoint (checkpoint interval adj_K)
+    int adj_K = 0;
+    double2 *d_ckpt = nullptr, *d_slab = nullptr, *d_ya = nullptr, *d_yb = nullptr;
+    double2 *d_dy = nullptr, *d_gy = nullptr;
+    double *d_gint = nullptr, *d_gl = nullptr, *d_gr = nullptr, *d_part = nullptr;
+    MarchSys* d_sys_seg = nullptr;
     std::vector<int> off, n, goff, loff, tc;
     int *d_n = nullptr, *d_goff = nullptr, *d_loff = nullptr, *d_tc = nullptr;
     double2 *d_dg = nullptr, *d_od = nullptr;       // A - B for V (static) or V0
@@ -195,7 +203,7 @@ inline int chunks_for(int nmax, int L) { return (nmax - 1 + L) / (L + 1); }
 
 // march kernel kinds: constant matrix; V(t,x) refactorised per step inside the
 // march; nonlinear; V(t,x) with per-step factorisations streamed from HBM
-enum { MK_STATIC = 0, MK_TDEP = 1, MK_NL = 2, MK_TSTAT = 3 };
+enum { MK_STATIC = 0, MK_TDEP = 1, MK_NL = 2, MK_TSTAT = 3, MK_ADJ = 4 };
 
 // Threads per CTA and CTA groups for a shape whose L, C, G are set; tps = P + 1.
 inline MarchCfg shape_of(MarchCfg c, int tps, int nsys) {
@@ -211,8 +219,18 @@ inline MarchCfg shape_of(MarchCfg c, int tps, int nsys) {
 
 // Largest CTA the march kernel of this kind and chunk length is compiled for.
 inline int march_tmax(int kind, int L) {
-    return (L == 16 || kind == MK_TDEP || kind == MK_NL) ? 256 : 384;
+    return (L == 16 || kind == MK_TDEP || kind == MK_NL || kind == MK_ADJ) ? 256 : 384;
 }
+
+// Extra arguments of the segment marches of the adjoint gradient (MK_ADJ).
+struct SegArgs {
+    int mode = 0;             // 0 march, 1 record v, 2 accumulate the potential form
+    int t0 = 0;               // first step of the segment within the flux blocks
+    long long gstride = 0;    // flux block stride (0: the launch's own step count)
+    double2* vrec = nullptr;
+    const double2* vfwd = nullptr;
+    double *gint = nullptr, *gl = nullptr, *gr = nullptr;
+};
 
 MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
     MarchCfg c;
@@ -231,8 +249,9 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
     int L = 4;
     if (kind == MK_TDEP) {
         L = 4;   // per-step refactorisation keeps LU, spikes and state in registers
-    } else if (kind == MK_NL) {
-        // state, right-hand side, iterate and solve per node in registers: L <= 8
+    } else if (kind == MK_NL || kind == MK_ADJ) {
+        // state, right-hand side, iterate and solve (or the adjoint sums) per node
+        // in registers: L <= 8
         L = ((long long)(chunks_for(p->nmax, 8) + 1) * nsys >= want) ? 8 : 4;
     } else if (p->forceL) {
         L = p->forceL;
@@ -281,7 +300,7 @@ inline double2 cmul_h(double2 a, double2 b) {
 // (the autotuner's probes).  Returns 0 or a launcher error code.
 int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
                const MarchSys* d_sys, int nsys, const double2* gin, double2* gout, double2* uT,
-               double2* trace, const double2* u0, int nt_run) {
+               double2* trace, const double2* u0, int nt_run, const SegArgs& seg = SegArgs()) {
     if (cfg.C > 16) return -2;
     const FactorSet& fs = zero_potential ? p->fs0L[lidx(cfg.L)] : p->fsL[lidx(cfg.L)];
     if (fs.L != cfg.L) return -3;
@@ -303,6 +322,15 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     a.two_sigma = p->two_sigma;
     a.inv_ik = p->inv_ik;
     a.status = p->d_status;
+    a.t0 = seg.t0;
+    a.gstride = seg.gstride > 0 ? seg.gstride : nt_run;
+    a.nxrec = p->nx;
+    a.vrec = seg.vrec;
+    a.vfwd = seg.vfwd;
+    a.gint = seg.gint;
+    a.gl = seg.gl;
+    a.gr = seg.gr;
+    a.h12 = p->h / 12.0;
     if (p->d.tc == SWR_TC_S02) {
         a.s02 = 1;
         a.beta = p->d_beta;
@@ -317,7 +345,7 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     if (kind == MK_NL)
         return swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
                                    p->d.nl_maxit, nullptr, cfg.ngroups, p->s);
-    return swr_launch_march(fs, a, cfg.ngroups, p->s);
+    return swr_launch_march(fs, a, cfg.ngroups, p->s, seg.mode);
 }
 
 inline int march_kind(swr_plan_t p, bool zero_potential) {
@@ -374,7 +402,7 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
     const MarchCfg guess = march_config(p, nsys, kind);
     std::vector<int> Ls;
     if (kind == MK_TDEP) Ls = {4};
-    else if (kind == MK_NL) Ls = {8, 4};
+    else if (kind == MK_NL || kind == MK_ADJ) Ls = {8, 4};
     else if (p->forceL) Ls = {p->forceL};
     else Ls = {16, 8, 4};
     std::vector<MarchCfg> cands;
@@ -643,14 +671,15 @@ swr_status apply_M(swr_plan_t p, const double2* y, double2* x) {
 
 // Restarted right-preconditioned GMRES(m) on A g = d (Saad, Alg. 6.9 with
 // classical Gram-Schmidt applied twice).  Stops on the true residual.
-swr_status gmres(swr_plan_t p, double2* g, bool g_init, swr_info* info) {
+// GMRES(m) on (I - L) g = b (b = d for the forward problem), stopping on the
+// true residual ||b - (I - L) g||_2 < tol.
+swr_status gmres(swr_plan_t p, const double2* b, double tol, double2* g, bool g_init,
+                 swr_info* info) {
     swr_status st = ensure_workspace(p);
     if (st) return st;
     Workspace& w = p->ws;
     const long long n = w.n;
     const int m = w.m, ldh = m + 1;
-    const double tol = p->d.tol_abs;
-    const double2* b = p->d_iface;   // d
     const bool pc = has_precond(p);
     if (!g_init) CK(cudaMemsetAsync(g, 0, sizeof(double2) * n, p->s));
     // r = b - A g
@@ -835,7 +864,10 @@ void swr_destroy(swr_plan_t p) {
         swr_factor_free(p->fsL[k]);
         swr_factor_free(p->fs0L[k]);
     }
-    cudaFree(p->d_beta); cudaFree(p->d_s02hist);
+    cudaFree(p->d_beta); cudaFree(p->d_s02hist); cudaFree(p->d_gconv);
+    cudaFree(p->d_ckpt); cudaFree(p->d_slab); cudaFree(p->d_ya); cudaFree(p->d_yb);
+    cudaFree(p->d_dy); cudaFree(p->d_gy); cudaFree(p->d_gint); cudaFree(p->d_gl);
+    cudaFree(p->d_gr); cudaFree(p->d_part); cudaFree(p->d_sys_seg);
     cudaFree(p->d_u0); cudaFree(p->d_V); cudaFree(p->d_Vbar); cudaFree(p->d_iface); cudaFree(p->d_iface0);
     cudaFree(p->d_lag0); cudaFree(p->d_lag0_0); cudaFree(p->d_hist); cudaFree(p->d_gtmp);
     cudaFree(p->d_gtmp2); cudaFree(p->d_trace);
@@ -999,6 +1031,7 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
         if (!st)
             st = dalloc(&p->d_s02hist, (size_t)std::max(p->nsys_build, p->N) * 2 * (p->nt + 1));
     }
+    if (!st) st = dalloc(&p->d_gconv, nb);
     if (!st) st = upload_systems(&p->d_sys_R, apply_systems(p->N, 0));
     if (!st) st = upload_systems(&p->d_sys_final, apply_systems(p->N, SYS_WRITE_UT | SYS_TRACE));
     if (!st) {
@@ -1141,10 +1174,13 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     if (p->d.vkind == SWR_V_NONLINEAR)
         st = nl_fixed_point(p, g, init, &loc);
     else if (p->d.solver == SWR_SOLVER_GMRES)
-        st = gmres(p, g, init, &loc);
+        st = gmres(p, p->d_iface, p->d.tol_abs, g, init, &loc);
     else
         st = fixed_point(p, g, init, p->d.solver == SWR_SOLVER_CLASSICAL, &loc);
     if (st != SWR_OK && st != SWR_ERR_NOT_CONVERGED) return st;
+    p->solved = false;
+    CK(cudaMemcpyAsync(p->d_gconv, g, sizeof(double2) * (size_t)p->nblk * p->nt,
+                       cudaMemcpyDeviceToDevice, s));
     CK(cudaEventRecord(p->ev[2], s));
     // final march (last step of Algorithms 1-3)
     double2* uT = uT_ ? reinterpret_cast<double2*>(uT_) : nullptr;
@@ -1173,6 +1209,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     long long sweeps = 1 + (p->d.solver == SWR_SOLVER_CLASSICAL ? loc.iterations : 0);
     loc.march_point_steps = sweeps * nodes * (long long)p->nt;
     if (info) *info = loc;
+    p->solved = (st == SWR_OK);
     return st;
 }
 
@@ -1239,9 +1276,124 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats* out, int32_t reset) {
     return SWR_OK;
 }
 
-swr_status swr_adjoint(swr_plan_t p, const double*, double*, int32_t) {
-    if (!p) return SWR_ERR_ARG;
-    return SWR_ERR_UNSUPPORTED;
+swr_status swr_misfit(swr_plan_t p, const double* uT_, const double* target_, double* ubar_,
+                      double* J) {
+    if (!p || !uT_ || !target_ || !J) return SWR_ERR_ARG;
+    if (!p->d_part && dalloc(&p->d_part, 160)) return SWR_ERR_NOMEM;
+    LK(swr_launch_misfit(reinterpret_cast<const double2*>(uT_),
+                         reinterpret_cast<const double2*>(target_), p->nx, p->h,
+                         reinterpret_cast<double2*>(ubar_), p->d_part, p->d_part + 150, p->s));
+    CK(cudaMemcpyAsync(J, p->d_part + 150, sizeof(double), cudaMemcpyDeviceToHost, p->s));
+    CK(cudaStreamSynchronize(p->s));
+    return SWR_OK;
+}
+
+// Gradient of J(V) through the converged SWR solution (which is the monodomain
+// Crank-Nicolson solution u_N).  With the M-weighted cotangent ubar (dJ =
+// Re(ubar^H M du_N)), the discrete adjoint of u_n = 2 A^{-1} B u_{n-1} - u_{n-1}
+// (A = (2i/dt) M - S + M_V complex symmetric, B = (2i/dt) M) conjugated and
+// scaled, z_n = B^{-1} conj(lambda_n), obeys the same map backwards:
+//     z_N = (dt / 2i) conj(ubar),   z_{n-1} = 2 A^{-1} B z_n - z_n,
+// so the adjoint is an SWR solve of the same interface problem (same L, same
+// preconditioner) from the initial state z_N, marched as y_m = z_{N-m}, and
+//     dJ/dV_k = -2 Re sum_n (v^y_{N-n+1})^T (dM_V/dV_k) v_n,
+// v^y_m, v_n the midpoint values of the two marches.  The forward v_n are
+// recomputed segment by segment from checkpoints of u every K steps (the
+// segment is recorded, then the adjoint march over the mirrored steps reads it).
+swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t ckpt_every) {
+    if (!p || !ubar_ || !dJdV_) return SWR_ERR_ARG;
+    if (!p->built || !p->solved) return SWR_ERR_STATE;
+    if (p->d.vkind != SWR_V_STATIC || p->d.tc != SWR_TC_ROBIN ||
+        p->d.solver != SWR_SOLVER_GMRES)
+        return SWR_ERR_UNSUPPORTED;
+    cudaStream_t s = p->s;
+    const int nt = p->nt, nx = p->nx, N = p->N;
+    const size_t nb = (size_t)p->nblk * nt;
+    const int K = std::max(1, std::min(ckpt_every > 0 ? ckpt_every : 50, nt));
+    const int C = (nt + K - 1) / K;
+    swr_status st = SWR_OK;
+    if (p->adj_K != K) {
+        cudaFree(p->d_ckpt);
+        cudaFree(p->d_slab);
+        p->d_ckpt = p->d_slab = nullptr;
+        p->adj_K = 0;
+        if ((st = dalloc(&p->d_ckpt, (size_t)C * nx))) return st;
+        if ((st = dalloc(&p->d_slab, (size_t)K * nx))) return st;
+        p->adj_K = K;
+    }
+    if (!p->d_ya) {
+        if ((st = dalloc(&p->d_ya, nx)) || (st = dalloc(&p->d_yb, nx)) ||
+            (st = dalloc(&p->d_dy, nb)) || (st = dalloc(&p->d_gy, nb)) ||
+            (st = dalloc(&p->d_gint, nx)) || (st = dalloc(&p->d_gl, nx)) ||
+            (st = dalloc(&p->d_gr, nx)) ||
+            (st = upload_systems(&p->d_sys_seg, apply_systems(N, SYS_WRITE_UT))))
+            return st;
+    }
+    CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
+    // launch shape of the segment marches (chunk length <= 8 for the gradient sums)
+    if (p->autotune) {
+        if ((st = tune_march(p, MK_ADJ, false, p->d_sys_R, N, p->d_dy, p->d_V, p->d_dg, p->d_od)))
+            return st;
+    }
+    const MarchCfg cfg = march_config(p, N, MK_ADJ);
+    if (p->fsL[lidx(cfg.L)].L != cfg.L &&
+        (st = factor_for(p, p->fsL[lidx(cfg.L)], cfg.L, p->d_V, p->d_dg, p->d_od)))
+        return st;
+    auto seg = [&](int mode, const double2* gin, int t0, int nrun, const double2* u0,
+                   double2* uT) -> swr_status {
+        SegArgs sa;
+        sa.mode = mode;
+        sa.t0 = t0;
+        sa.gstride = nt;
+        sa.vrec = p->d_slab;
+        sa.vfwd = p->d_slab;
+        sa.gint = p->d_gint;
+        sa.gl = p->d_gl;
+        sa.gr = p->d_gr;
+        const long long work = (long long)nx * nrun;
+        const int pi = prof_begin(p, 0, work);
+        const int rc = launch_cfg(p, cfg, MK_ADJ, false, p->d_sys_seg, N, gin, nullptr, uT,
+                                  nullptr, u0, nrun, sa);
+        prof_end(p, pi);
+        if (rc) return launch_fail("adjoint segment march", __LINE__);
+        return SWR_OK;
+    };
+    // 1. forward checkpoints: ckpt[c] = u after c K steps
+    CK(cudaMemcpyAsync(p->d_ckpt, p->d_u0, sizeof(double2) * nx, cudaMemcpyDeviceToDevice, s));
+    for (int c = 1; c < C; ++c)
+        if ((st = seg(0, p->d_gconv, (c - 1) * K, K, p->d_ckpt + (size_t)(c - 1) * nx,
+                      p->d_ckpt + (size_t)c * nx)))
+            return st;
+    // 2. adjoint initial state and its interface problem: d_y = R_y 0, (I - L) g_y = d_y
+    LK(swr_launch_adj_seed(reinterpret_cast<const double2*>(ubar_), 0.5 * p->d.dt, nx, p->d_ya, s));
+    CK(cudaMemsetAsync(p->d_dy, 0, sizeof(double2) * nb, s));
+    if ((st = run_march(p, false, p->d_sys_build, N, nullptr, p->d_dy, nullptr, nullptr, p->d_ya,
+                        p->work_R)))
+        return st;
+    double dn = 0.0, dny = 0.0;
+    if ((st = norm2(p, p->d_iface, (long long)nb, &dn)) || (st = norm2(p, p->d_dy, (long long)nb, &dny)))
+        return st;
+    // the forward solve's accuracy relative to its right-hand side
+    const double tol = (dn > 0.0) ? p->d.tol_abs * dny / dn : p->d.tol_abs;
+    swr_info loc{};
+    st = gmres(p, p->d_dy, tol, p->d_gy, false, &loc);
+    if (st != SWR_OK) return st;
+    // 3. segments from the last to the first: record the forward v, then march the
+    //    adjoint over the mirrored steps and accumulate the potential form
+    CK(cudaMemsetAsync(p->d_gint, 0, sizeof(double) * nx, s));
+    CK(cudaMemsetAsync(p->d_gl, 0, sizeof(double) * nx, s));
+    CK(cudaMemsetAsync(p->d_gr, 0, sizeof(double) * nx, s));
+    double2* ycur = p->d_ya;
+    double2* ynext = p->d_yb;
+    for (int c = C - 1; c >= 0; --c) {
+        const int t0 = c * K, Kc = std::min(K, nt - t0);
+        if ((st = seg(1, p->d_gconv, t0, Kc, p->d_ckpt + (size_t)c * nx, nullptr))) return st;
+        if ((st = seg(2, p->d_gy, nt - t0 - Kc, Kc, ycur, ynext))) return st;
+        std::swap(ycur, ynext);
+    }
+    LK(swr_launch_grad_combine(p->d_gint, p->d_gl, p->d_gr, nx, dJdV_, s));
+    CK(cudaStreamSynchronize(s));
+    return read_status(p);
 }
 
 }  // extern "C"

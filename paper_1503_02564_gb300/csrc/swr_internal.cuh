@@ -140,6 +140,23 @@ struct MarchArgs {
     double2* trace;       // [nsys][2][nt]
     long long fstride, sstride, pstride;   // per-step factor strides (0: constant matrix)
     int stage;            // staging of streamed factors in shared memory (0, 1, 2)
+    // A launch may march a segment of the time axis: its step t is step t0 + t of the
+    // flux blocks, whose stride is gstride (the whole problem's nt).
+    int t0;
+    long long gstride;
+    // Adjoint support (segment marches of the gradient):
+    //   record mode: v of every step into vrec[(t-1) * nxrec + global node];
+    //   gradient mode: with x = this march's v and y = vfwd[(nt - t) * nxrec + node],
+    //   accumulate Re x^T (dM_W/dW_k) y per node k into gint (interior nodes of a
+    //   chunk), gl (a separator, from the element on its right) and gr (a separator,
+    //   from the element on its left); h12 = h / 12.
+    long long nxrec;
+    double2* vrec;
+    const double2* vfwd;
+    double* gint;
+    double* gl;
+    double* gr;
+    double h12;
     // S_0^2 transmission condition (Section 2.2): S-bar v_n = c2 sum_{s<=n} beta_{n-s} v_s.
     // The current-step term sits in the matrix (sigma0 = c2 beta_0) and in two_sigma;
     // the history b_n = c2 sum_{s<n} beta_{n-s} v_s enters the end rows and the fluxes.
@@ -174,7 +191,8 @@ int swr_launch_factor_steps(FactorSet& fs, int N, const int* d_n, const int* d_g
 void swr_factor_free(FactorSet& fs);
 int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
                       const double2* od, int* status, cudaStream_t s);
-int swr_launch_march(const FactorSet& fs, MarchArgs a, int nsys_groups, cudaStream_t s);
+int swr_launch_march(const FactorSet& fs, MarchArgs a, int nsys_groups, cudaStream_t s,
+                     int mode = 0);
 int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef, double tol,
                         int maxit, int* iters, int ngroups, cudaStream_t s);
 int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, long long vstride,
@@ -203,3 +221,9 @@ size_t swr_causal_scratch_bytes(int N);
 int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s);
 int swr_launch_jump(const double2* trace, const MarchSys* sys, int N, int nt, double* out,
                     cudaStream_t s);
+int swr_launch_misfit(const double2* u, const double2* tgt, long long n, double h, double2* ubar,
+                      double* part, double* out, cudaStream_t s);
+int swr_launch_adj_seed(const double2* ubar, double half_dt, long long n, double2* y,
+                        cudaStream_t s);
+int swr_launch_grad_combine(const double* gint, const double* gl, const double* gr, long long n,
+                            double* out, cudaStream_t s);

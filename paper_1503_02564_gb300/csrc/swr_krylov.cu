@@ -514,3 +514,81 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, c
     swr_count_launch(1);
     return 0;
 }
+
+// ---------------------------------------------------------------------------
+// Final-time misfit and adjoint helpers.
+// J = (u - u_target)^H M (u - u_target), M the P1 mass matrix on the whole grid
+// (h/6 tridiag(1, 4, 1), h/3 on the two end rows); ubar = 2 (u - u_target), the
+// M-weighted cotangent: dJ = Re(ubar^H M du).  Partial sums per block are added
+// in a fixed order by one block: the result is reproducible.
+// ---------------------------------------------------------------------------
+__global__ void k_misfit_partial(const double2* __restrict__ u, const double2* __restrict__ tgt,
+                                 long long n, double h, double2* __restrict__ ubar,
+                                 double* __restrict__ part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const double2 e = csub(u[k], tgt[k]);
+        double2 me = cscale(e, (k == 0 || k == n - 1) ? h / 3.0 : 2.0 * h / 3.0);
+        if (k > 0) me = cadd(me, cscale(csub(u[k - 1], tgt[k - 1]), h / 6.0));
+        if (k < n - 1) me = cadd(me, cscale(csub(u[k + 1], tgt[k + 1]), h / 6.0));
+        acc += e.x * me.x + e.y * me.y;                 // Re(conj(e) (M e))
+        if (ubar) ubar[k] = cscale(e, 2.0);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double acc = 0.0;
+        for (int b = 0; b < nb; ++b) acc += part[b];
+        *out = acc;
+    }
+}
+
+int swr_launch_misfit(const double2* u, const double2* tgt, long long n, double h, double2* ubar,
+                      double* part, double* out, cudaStream_t s) {
+    const int nbk = 128;   // part holds nbk + 1 doubles
+    k_misfit_partial<<<nbk, 256, 0, s>>>(u, tgt, n, h, ubar, part);
+    k_sum_partials<<<1, 32, 0, s>>>(part, nbk, out);
+    swr_count_launch(2);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Initial state of the adjoint march: y_0 = (dt / 2i) conj(ubar).
+__global__ void k_adj_seed(const double2* __restrict__ ubar, double half_dt, long long n,
+                           double2* __restrict__ y) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double2 b = ubar[k];
+    y[k] = make_double2(-half_dt * b.y, -half_dt * b.x);   // -i (dt/2) (b.x - i b.y)
+}
+
+// dJ/dV_k = -2 (interior + left-element + right-element parts of the potential form).
+__global__ void k_grad_combine(const double* __restrict__ gint, const double* __restrict__ gl,
+                               const double* __restrict__ gr, long long n, double* __restrict__ out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    out[k] = -2.0 * (gint[k] + gl[k] + gr[k]);
+}
+
+int swr_launch_adj_seed(const double2* ubar, double half_dt, long long n, double2* y,
+                        cudaStream_t s) {
+    k_adj_seed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ubar, half_dt, n, y);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int swr_launch_grad_combine(const double* gint, const double* gl, const double* gr, long long n,
+                            double* out, cudaStream_t s) {
+    k_grad_combine<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(gint, gl, gr, n, out);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}

@@ -481,8 +481,10 @@ int swr_march_smem_bytes(int T, int G, int stage_slots) {
     return (int)sizeof(double2) * (3 * (T + G) + 4 * T + 2 * G + stage_slots * T);
 }
 
-template <int L>
-__global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const MarchArgs a) {
+// MODE 0: march; 1: also record v of every step; 2: also accumulate the adjoint
+// potential form against recorded forward values (see MarchArgs).
+template <int L, int MODE>
+__global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march_static(const MarchArgs a) {
     extern __shared__ double2 sm[];
     const int T = a.T, G = a.G, P = a.P, C = a.C, nt = a.nt, levels = a.levels;
     const int S = T + G;
@@ -624,6 +626,12 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
     }
     SYNC();
 
+    // gradient mode: per-thread sums of the potential form (interior nodes of the
+    // chunk, and the one-sided parts of its two separators)
+    double ga_int[MODE == 2 ? L : 1], ga_l = 0.0, ga_r = 0.0;
+#pragma unroll
+    for (int i = 0; i < (MODE == 2 ? L : 1); ++i) ga_int[i] = 0.0;
+
     double2 lin = zero, rin = zero;
     for (int t = 1; t <= nt; ++t) {
         if (stage == 0 && stepped && valid && t < nt) {
@@ -728,7 +736,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     if (sy.flags & SYS_IMP_L)
                         lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                     else
-                        lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
+                        lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * a.gstride + a.t0 + t - 1] : zero;
                     f = cfms(lin, a.inv_ik, f);
                     if (a.s02) f = cfma(hsum[hs_l], a.c2_ik, f);
                 }
@@ -736,7 +744,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                     if (sy.flags & SYS_IMP_R)
                         rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                     else
-                        rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
+                        rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * a.gstride + a.t0 + t - 1] : zero;
                     f = cfms(rin, a.inv_ik, f);
                     if (a.s02) f = cfma(hsum[hs_r], a.c2_ik, f);
                 }
@@ -773,6 +781,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         if (stage > 0) issue_pc(t < nt, a.sstride, a.pstride);
         // ---- phase D: spike correction, CN update, fluxes ---------------------
         if (stage >= 2) cp_async_wait<2>();
+        double2 vv[MODE == 2 ? L : 1];
         if (valid && Lp > 0) {
             const double2 vL = *SEP(src, p), vR = *SEP(src, p + 1);
 #pragma unroll
@@ -780,13 +789,46 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                 if (i < Lp) {
                     double2 v = cfms(FAC(i, 2), vL, y[i]);
                     v = cfms(FAC(i, 3), vR, v);
+                    if constexpr (MODE == 1)
+                        a.vrec[(size_t)(t - 1) * a.nxrec + goff + sp + 1 + i] = v;
+                    if constexpr (MODE == 2) vv[i] = v;
                     u[i] = make_double2(fma(2.0, v.x, -u[i].x), fma(2.0, v.y, -u[i].y));
+                }
+            }
+        }
+        if constexpr (MODE == 2) {
+            // elements e = 0..Lp from separator p (node sp) to separator p+1 (node
+            // sp + Lp + 1); x = this march's v, y = the recorded forward v of the
+            // mirrored step
+            if (valid && p < Pj) {
+                const double2* yrow = a.vfwd + (size_t)(nt - t) * a.nxrec + goff + sp;
+                const double2 xL = *SEP(src, p), xR = *SEP(src, p + 1);
+                const double h12 = a.h12;
+#pragma unroll
+                for (int e = 0; e <= L; ++e) {
+                    if (e <= Lp) {
+                        const double2 xa = (e == 0) ? xL : vv[e > 0 ? e - 1 : 0];
+                        const double2 xb = (e < L) ? csel(e < Lp, vv[e < L ? e : 0], xR) : xR;
+                        const double2 ya = yrow[e], yb = yrow[e + 1];
+                        const double sa = xa.x * ya.x - xa.y * ya.y;
+                        const double sb = xb.x * yb.x - xb.y * yb.y;
+                        const double c = (xa.x * yb.x - xa.y * yb.y) + (xb.x * ya.x - xb.y * ya.y);
+                        const double toa = h12 * (3.0 * sa + c + sb);
+                        const double tob = h12 * (sa + c + 3.0 * sb);
+                        if (e == 0) ga_l += toa;
+                        else ga_int[e > 0 ? e - 1 : 0] += toa;
+                        if (e < Lp) ga_int[e < L ? e : 0] += tob;
+                        else ga_r += tob;
+                    }
                 }
             }
         }
         if (stage > 0) issue_fd(t < nt ? F + a.fstride : nullptr);
         if (realsep) {
             const double2 v = *SEP(src, p);
+            if constexpr (MODE == 1) {   // an interface node is recorded by its left subdomain
+                if (!(p == 0 && (tcf & 1))) a.vrec[(size_t)(t - 1) * a.nxrec + goff + sp] = v;
+            }
             double2* us = SEP(usep, p);
             const double2 uo = *us;
             *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
@@ -795,7 +837,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                 if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
                     double2 o = csub(cmul(a.two_sigma, v), lin);
                     if (a.s02) o = cfma(a.two_c2, hsum[hs_l], o);
-                    a.gout[(size_t)sy.out_a * nt + t - 1] = o;
+                    a.gout[(size_t)sy.out_a * a.gstride + a.t0 + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
@@ -804,7 +846,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
                 if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
                     double2 o = csub(cmul(a.two_sigma, v), rin);
                     if (a.s02) o = cfma(a.two_c2, hsum[hs_r], o);
-                    a.gout[(size_t)sy.out_b * nt + t - 1] = o;
+                    a.gout[(size_t)sy.out_b * a.gstride + a.t0 + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
@@ -817,6 +859,16 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_static(const M
         SYNC();
     }
     if (stage > 0) cp_async_wait_all();   // no copy in flight past the loop
+    if constexpr (MODE == 2) {
+        // add this segment's sums; every entry has exactly one writer per launch
+        if (valid && p < Pj) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.gint[goff + sp + 1 + i] += ga_int[i];
+            a.gl[goff + sp] += ga_l;
+            a.gr[goff + sp + Lp + 1] += ga_r;
+        }
+    }
     // ---- final state ----------------------------------------------------------
     bool bad = false;
     if (valid) {
@@ -1223,10 +1275,14 @@ int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, lon
 }
 
 template <int L>
-static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s) {
+static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s, int mode) {
     const int slots = a.stage == 2 ? 2 * a.levels + 3 + 4 * L : (a.stage == 1 ? 2 * a.levels + 3 : 0);
     const int smem = swr_march_smem_bytes(a.T, a.G, slots);
-    auto kern = k_march_static<L>;
+    void (*kern)(const MarchArgs) = k_march_static<L, 0>;
+    if constexpr (L <= 8) {   // record and gradient modes exist for L <= 8
+        if (mode == 1) kern = k_march_static<L, 1>;
+        if (mode == 2) kern = k_march_static<L, 2>;
+    }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return -1;
@@ -1249,7 +1305,7 @@ static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, kern, a) == cudaSuccess ? 0 : -1;
 }
 
-int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t s) {
+int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t s, int mode) {
     if (fs.nsteps > 1 && fs.nsteps < a.nt) return -2;
     a.fstride = fs.fstride;
     a.sstride = fs.sstride;
@@ -1272,10 +1328,11 @@ int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t
     a.fac = fs.fac;
     a.sep = fs.sep;
     a.pcr = fs.pcr;
+    if (mode != 0 && (fs.L == 16 || fs.nsteps > 1 || a.s02)) return -2;   // adjoint modes: L <= 8, V(x), Robin
     switch (fs.L) {
-        case 4: return launch_march_t<4>(a, ngroups, s);
-        case 8: return launch_march_t<8>(a, ngroups, s);
-        case 16: return launch_march_t<16>(a, ngroups, s);
+        case 4: return launch_march_t<4>(a, ngroups, s, mode);
+        case 8: return launch_march_t<8>(a, ngroups, s, mode);
+        case 16: return launch_march_t<16>(a, ngroups, s, 0);
         default: return -2;
     }
 }

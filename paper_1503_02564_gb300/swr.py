@@ -91,6 +91,7 @@ def lib():
         L.swr_get_interface.argtypes = [vp, dp, dp]
         L.swr_apply_precond.argtypes = [vp, dp, dp]
         L.swr_adjoint.argtypes = [vp, dp, dp, ctypes.c_int32]
+        L.swr_misfit.argtypes = [vp, dp, dp, dp, ctypes.POINTER(ctypes.c_double)]
         L.swr_get_stats.argtypes = [vp, ctypes.POINTER(swr_stats), ctypes.c_int32]
         L.swr_causal_solve_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                dp, dp, dp, vp]
@@ -102,7 +103,7 @@ def lib():
         L.swr_status_string.restype = ctypes.c_char_p
         for f in ("swr_plan", "swr_build_interface", "swr_solve", "swr_apply_R",
                   "swr_apply_interface", "swr_get_interface", "swr_apply_precond", "swr_adjoint",
-                  "swr_get_stats", "swr_causal_solve_noalloc"):
+                  "swr_get_stats", "swr_causal_solve_noalloc", "swr_misfit"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -215,6 +216,21 @@ class Plan:
                                        _ptr(x, torch.complex128, self.n_interface, "x")),
                "swr_apply_precond")
 
+    def misfit(self, uT, u_target, ubar=None):
+        """J = (uT - u_target)^H M (uT - u_target); ubar (optional) receives 2 (uT - u_target)."""
+        J = ctypes.c_double()
+        _check(lib().swr_misfit(self.handle, _ptr(uT, torch.complex128, self.nx, "uT"),
+                                _ptr(u_target, torch.complex128, self.nx, "u_target"),
+                                _ptr(ubar, torch.complex128, self.nx, "ubar"), ctypes.byref(J)),
+               "swr_misfit")
+        return J.value
+
+    def adjoint(self, ubar, grad, ckpt_every=50):
+        """grad <- dJ/dV for the M-weighted cotangent ubar of J at u(T) (after solve())."""
+        _check(lib().swr_adjoint(self.handle, _ptr(ubar, torch.complex128, self.nx, "ubar"),
+                                 _ptr(grad, torch.float64, self.nx, "grad"), int(ckpt_every)),
+               "swr_adjoint")
+
     def get_stats(self, reset=False):
         st = swr_stats()
         _check(lib().swr_get_stats(self.handle, ctypes.byref(st), int(bool(reset))), "swr_get_stats")
@@ -230,3 +246,28 @@ class Plan:
             self.destroy()
         except Exception:
             pass
+
+
+class SWRMisfit(torch.autograd.Function):
+    """J(V) = ||u(T) - u_target||_M^2 with u the converged SWR solution for the
+    static potential V (a CUDA float64 tensor of nx nodal values); the backward
+    pass is swr_adjoint.  plan: a Plan with a static potential, Robin
+    transmission and GMRES; u0, u_target: complex128 CUDA tensors."""
+
+    @staticmethod
+    def forward(ctx, V, plan, u0, u_target, ckpt_every=50):
+        plan.build_interface(V, u0)
+        uT = torch.empty(plan.nx, dtype=torch.complex128, device=V.device)
+        plan.solve(None, False, uT)
+        ubar = torch.empty_like(uT)
+        J = plan.misfit(uT, u_target, ubar)
+        ctx.plan, ctx.ckpt_every = plan, ckpt_every
+        ctx.save_for_backward(ubar)
+        return torch.tensor(J, dtype=torch.float64, device=V.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (ubar,) = ctx.saved_tensors
+        grad = torch.empty(ctx.plan.nx, dtype=torch.float64, device=ubar.device)
+        ctx.plan.adjoint(ubar, grad, ctx.ckpt_every)
+        return grad * gJ, None, None, None, None

@@ -30,7 +30,7 @@ def test_header_declares_the_boundary():
     names = _declared()
     for f in ("swr_plan", "swr_build_interface", "swr_solve", "swr_adjoint", "swr_destroy",
               "swr_status_string", "swr_apply_R", "swr_apply_interface", "swr_get_interface",
-              "swr_apply_precond"):
+              "swr_apply_precond", "swr_misfit"):
         assert f in names, f
 
 

@@ -57,10 +57,12 @@ def parse():
     ap.add_argument("--impl", default="swr", choices=["swr", "reference"])
     ap.add_argument("--nsub", default=",".join(str(n) for n in NSUBS))
     ap.add_argument("--precond", default="causal", choices=["causal", "none"])
-    ap.add_argument("--workload", default="scaling", choices=["scaling", "timedep"],
+    ap.add_argument("--workload", default="scaling", choices=["scaling", "timedep", "adjoint"],
                     help="scaling: the N in {16,64,256,500} static-potential step (default); "
                          "timedep: the time-dependent potential case (60001 nodes, 1000 steps, "
-                         "N = 64, GMRES preconditioned by the mean-potential operator)")
+                         "N = 64, GMRES preconditioned by the mean-potential operator); "
+                         "adjoint: the scaling step plus the misfit gradient dJ/dV by "
+                         "swr_adjoint (checkpoints every 50 steps)")
     ap.add_argument("--tc", default="robin", choices=["robin", "s02"],
                     help="transmission condition of the scaling workload: Robin "
                          "p = sqrt(5) e^{-i pi/4} (default) or the order-2 potential "
@@ -185,6 +187,23 @@ def cpu_oracle_sample(wl_full, nsub_sample):
     return ps / dt, dt, ps
 
 
+def cpu_oracle_adjoint_sample(wl_full, nt_sample):
+    """Time the oracle's discrete adjoint (monodomain forward march keeping every
+    v_n, then the adjoint solves) on the workload's grid for nt_sample steps.
+    Returns (point-steps/s, seconds, point-steps) with 2 x nodes x steps."""
+    import numpy as np
+    import oracle as O
+    from paper_1503_02564_gb300 import workloads as W
+    P = O.Problem(wl_full.a0, wl_full.b0, wl_full.nx, wl_full.dt, nt_sample,
+                  wl_full.off.astype(np.int64), wl_full.u0, wl_full.V, vkind=wl_full.vkind,
+                  tc=wl_full.tc, sigma=wl_full.sigma)
+    t0 = time.perf_counter()
+    O.adjoint_gradient(P, W.misfit_target(wl_full))
+    dt = time.perf_counter() - t0
+    ps = 2 * P.nx * nt_sample
+    return ps / dt, dt, ps
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle timed on the host cores."""
     rank, world, local = dist_env()
@@ -237,6 +256,7 @@ def main():
     nsubs = tuple(int(x) for x in args.nsub.split(","))
     precond = swr.SWR_PC_CAUSAL if args.precond == "causal" else swr.SWR_PC_NONE
     timedep = args.workload == "timedep"
+    adjoint = args.workload == "adjoint"
     if timedep:
         nsubs = (64,)
 
@@ -260,6 +280,12 @@ def main():
         uT = torch.zeros(wl.nx, dtype=torch.complex128, device=dev)
         cases.append(dict(N=N, wl=wl, plan=plan, V=V, u0=u0, g=g, uT=uT,
                           ps=march_point_steps(wl)))
+        if adjoint:
+            cases[-1].update(
+                tgt=torch.tensor(W.misfit_target(wl), dtype=torch.complex128, device=dev),
+                ubar=torch.empty_like(uT),
+                grad=torch.empty(wl.nx, dtype=torch.float64, device=dev),
+                ev=(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)))
     ps_step = sum(c["ps"] for c in cases)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
@@ -268,6 +294,11 @@ def main():
         for c in cases:
             c["plan"].build_interface(c["V"], c["u0"])
             infos.append(c["plan"].solve(c["g"], False, c["uT"]))
+            if adjoint:
+                c["ev"][0].record()
+                c["J"] = c["plan"].misfit(c["uT"], c["tgt"], c["ubar"])
+                c["plan"].adjoint(c["ubar"], c["grad"], 50)
+                c["ev"][1].record()
         return infos
 
     for _ in range(args.warmup):
@@ -343,8 +374,14 @@ def main():
         for c in cases:
             hosts.append(dict(V=c["V"].cpu().pin_memory(), u0=c["u0"].cpu().pin_memory(),
                               uT=torch.empty_like(c["uT"], device="cpu").pin_memory()))
+            if adjoint:
+                hosts[-1].update(tgt=c["tgt"].cpu().pin_memory(),
+                                 grad=torch.empty_like(c["grad"], device="cpu").pin_memory())
         h2d = sum(h["V"].numel() * 8 + h["u0"].numel() * 16 for h in hosts)
         d2h = sum(h["uT"].numel() * 16 for h in hosts)
+        if adjoint:
+            h2d += sum(h["tgt"].numel() * 16 for h in hosts)
+            d2h += sum(h["grad"].numel() * 8 + 8 for h in hosts)
         torch.cuda.synchronize()
         e_ms = 0.0
         for _ in range(args.steps):
@@ -357,6 +394,11 @@ def main():
                 c["plan"].build_interface(c["V"], c["u0"])
                 c["plan"].solve(c["g"], False, c["uT"])
                 h["uT"].copy_(c["uT"], non_blocking=True)
+                if adjoint:
+                    c["tgt"].copy_(h["tgt"], non_blocking=True)
+                    c["plan"].misfit(c["uT"], c["tgt"], c["ubar"])
+                    c["plan"].adjoint(c["ubar"], c["grad"], 50)
+                    h["grad"].copy_(c["grad"], non_blocking=True)
             ev1.record()
             ev1.synchronize()
             e_ms += ev0.elapsed_time(ev1)
@@ -365,7 +407,13 @@ def main():
                "ms_per_step": e_ms / args.steps}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and adjoint:
+        v, s, ps = cpu_oracle_adjoint_sample(cases[0]["wl"], 100)
+        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle discrete adjoint of the monodomain scheme on the "
+                         f"{cases[0]['wl'].nx}-node grid, first 100 steps (forward and adjoint "
+                         f"marches, {ps:.3g} point-steps, {s:.1f} s)"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         if timedep:
             wl_cpu = cases[0]["wl"]
         else:
@@ -383,13 +431,19 @@ def main():
                           "residual": info["residual"], "build_ms": info["t_build_ms"],
                           "solve_ms": info["t_solve_ms"], "final_ms": info["t_final_ms"],
                           "interface_jump": info["interface_jump"]})
+            if adjoint:
+                per_n[-1].update(J=c["J"], adjoint_ms=c["ev"][0].elapsed_time(c["ev"][1]),
+                                 grad_norm=float(c["grad"].norm()))
         line = {
             "metric": "SWR subdomain CN point-steps/s (solve time to 1e-10 interface residual "
                       "reported as ms_per_step)",
             "value": value, "unit": "point-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name_timedep(cases[0]["wl"].nt) if timedep else workload_name(nsubs, args.tc, cases[0]["wl"].nt),
+            "config": {"workload": workload_name_timedep(cases[0]["wl"].nt) if timedep else
+                       (workload_name(nsubs, args.tc, cases[0]["wl"].nt)
+                        + ("; then J = ||u(T) - u_target||_M^2 and dJ/dV(x) by swr_adjoint, "
+                           "checkpoints every 50 steps" if adjoint else "")),
                        "point_steps_per_step": ps_step,
                        "precond": "mean_potential" if timedep else args.precond, "l2": "flushed by a 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

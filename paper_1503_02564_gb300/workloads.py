@@ -142,3 +142,11 @@ def random_interface(nblk: int, nt: int, seed: int = 7) -> np.ndarray:
     """A seeded random interface vector (the paper's 'random g^0', Section 6)."""
     rng = np.random.default_rng(SEED_BASE + 100 + seed)
     return (rng.standard_normal((nblk, nt)) + 1j * rng.standard_normal((nblk, nt)))
+
+
+def misfit_target(wl: Workload, seed: int = 9) -> np.ndarray:
+    """A seeded final-time target for the misfit ||u(T) - u_target||_M^2: the
+    initial data with a phase shift plus 5 % complex noise."""
+    rng = np.random.default_rng(SEED_BASE + 200 + seed)
+    noise = rng.standard_normal(wl.nx) + 1j * rng.standard_normal(wl.nx)
+    return wl.u0 * np.exp(0.4j) + 0.05 * noise

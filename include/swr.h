@@ -145,6 +145,21 @@ typedef struct swr_plan_s *swr_plan_t;
  * failure. */
 swr_status swr_plan(const swr_desc *d, swr_plan_t *out, void *stream);
 
+/* A batch of independent problem instances in one plan (no counterpart in the
+ * paper, which solves one problem at a time).  descs[0..count-1] each give an
+ * instance's grid (nx, a0, b0), step count nt and partition (nsub, node_off);
+ * all other fields, the grid step h = (b0 - a0)/(nx - 1) (to 1e-12 relative)
+ * and dt must agree (SWR_ERR_ARG otherwise), and vkind must be SWR_V_STATIC
+ * (SWR_ERR_UNSUPPORTED otherwise).  Every launch of the plan (marches,
+ * Toeplitz applies, GMRES vector kernels) covers all instances at once; the
+ * causal substitution runs as few cooperative launches as hold whole instances.
+ * The plan's arrays are the instances' arrays concatenated in order: V, u0, uT
+ * (sum of nx), interface vectors (sum of (2 nsub - 2) nt, instance by
+ * instance, blocks as for one instance) and first columns (sum of 4 nsub nt).
+ * GMRES runs on the concatenated (block-diagonal) system, so its stopping test
+ * bounds every instance's residual.  swr_adjoint is not available for batches. */
+swr_status swr_plan_batch(const swr_desc *descs, int32_t count, swr_plan_t *out, void *stream);
+
 /* Assemble and factor the subdomain systems A_j - B_j (Eq. AvML) for potential
  * V and build the interface problem (Section 4.1):
  *   SWR_V_STATIC:    d = R 0 and the first columns of X^{j,1..4} (Props. 3-4),

@@ -44,7 +44,19 @@ struct Workspace {
 struct swr_plan_s {
     swr_desc d{};
     cudaStream_t s = nullptr;
+    // N, nx, nblk: totals over the plan's instances; nt: the longest instance
     int N = 0, nx = 0, nt = 0, nblk = 0, nmax = 0, ntot = 0, nsm = 152;
+    // instances (a single problem, or a batch of independent problems with equal h
+    // and dt): interface vectors and Toeplitz columns concatenated
+    int ninst = 1;
+    bool batched = false;          // more than one instance: kernels take the tables
+    std::vector<InstInfo> inst;
+    std::vector<int> inst_nx, inst_xoff;
+    long long nb = 0, ncols = 0;   // interface vector length, first-column length
+    int nif = 0;                   // interfaces
+    std::vector<std::pair<int, int>> causal_groups;   // (first interface, count) per launch
+    InstInfo* d_inst = nullptr;
+    int *d_blk_inst = nullptr, *d_if_inst = nullptr;
     double h = 0.0;
     double2 inv_ik{}, sigma0{}, two_sigma{};
     double2 c2{}, c2_ik{};         // S_0^2: c2 and c2 / (i kappa)
@@ -533,44 +545,59 @@ swr_status assemble(swr_plan_t p, const double* V, double2* dg, double2* od) {
     return SWR_OK;
 }
 
-std::vector<MarchSys> build_systems(int N, int nblk, bool with_d) {
-    // blocks in the interface buffer: d occupies [0, nblk), cols occupy nblk + 4j + (p-1)
+// March systems of every instance.  Flux offsets are absolute (complex entries):
+// an instance's interface blocks (2N-2 of nt) start at its foff, block 2k = r_k,
+// 2k+1 = l_{k+1}; its first columns start at nb + coff in the build buffer
+// (d followed by the columns), slot 4j + p - 1 = X^{j,p}.
+std::vector<MarchSys> build_systems(const swr_plan_s* p, bool with_d) {
     std::vector<MarchSys> v;
-    if (with_d) {
-        for (int j = 0; j < N; ++j) {
-            MarchSys s{j, 0, -1, -1, -1, -1};
-            if (j > 0) s.out_a = 2 * (j - 1);       // r_{j-1}
-            if (j < N - 1) s.out_b = 2 * (j + 1) - 1;  // l_{j+1}
+    const long long nb = p->nb;
+    if (with_d) {   // d = R 0: one march per subdomain, all instances first
+        for (const InstInfo& I : p->inst)
+            for (int j = 0; j < I.N; ++j) {
+                MarchSys s{I.sub0 + j, 0, I.nt, -1, -1, -1, -1};
+                if (j > 0) s.out_a = (int)(I.foff + (long long)(2 * (j - 1)) * I.nt);      // r_{j-1}
+                if (j < I.N - 1) s.out_b = (int)(I.foff + (long long)(2 * (j + 1) - 1) * I.nt);  // l_{j+1}
+                v.push_back(s);
+            }
+    }
+    for (const InstInfo& I : p->inst) {   // l impulse: X^{j,1} (r_{j-1}), X^{j,3} (l_{j+1})
+        const long long c = nb + I.coff;
+        for (int j = 1; j < I.N; ++j) {
+            MarchSys s{I.sub0 + j, SYS_ZERO_U0 | SYS_IMP_L, I.nt, -1, -1,
+                       (int)(c + (long long)(4 * j + 0) * I.nt), -1};
+            if (j < I.N - 1) s.out_b = (int)(c + (long long)(4 * j + 2) * I.nt);
             v.push_back(s);
         }
     }
-    for (int j = 1; j < N; ++j) {                // l impulse: X^{j,1} (r_{j-1}), X^{j,3} (l_{j+1})
-        MarchSys s{j, SYS_ZERO_U0 | SYS_IMP_L, -1, -1, nblk + 4 * j + 0, -1};
-        if (j < N - 1) s.out_b = nblk + 4 * j + 2;
-        v.push_back(s);
-    }
-    for (int j = 0; j < N - 1; ++j) {            // r impulse: X^{j,2} (r_{j-1}), X^{j,4} (l_{j+1})
-        MarchSys s{j, SYS_ZERO_U0 | SYS_IMP_R, -1, -1, -1, nblk + 4 * j + 3};
-        if (j > 0) s.out_a = nblk + 4 * j + 1;
-        v.push_back(s);
+    for (const InstInfo& I : p->inst) {   // r impulse: X^{j,2} (r_{j-1}), X^{j,4} (l_{j+1})
+        const long long c = nb + I.coff;
+        for (int j = 0; j < I.N - 1; ++j) {
+            MarchSys s{I.sub0 + j, SYS_ZERO_U0 | SYS_IMP_R, I.nt, -1, -1, -1,
+                       (int)(c + (long long)(4 * j + 3) * I.nt)};
+            if (j > 0) s.out_a = (int)(c + (long long)(4 * j + 1) * I.nt);
+            v.push_back(s);
+        }
     }
     return v;
 }
 
-std::vector<MarchSys> apply_systems(int N, int extra_flags) {
+// One system per subdomain (global order) reading and writing interface vectors.
+std::vector<MarchSys> apply_systems(const swr_plan_s* p, int extra_flags) {
     std::vector<MarchSys> v;
-    for (int j = 0; j < N; ++j) {
-        MarchSys s{j, extra_flags, -1, -1, -1, -1};
-        if (j > 0) {
-            s.in_l = 2 * j - 1;
-            s.out_a = 2 * (j - 1);
+    for (const InstInfo& I : p->inst)
+        for (int j = 0; j < I.N; ++j) {
+            MarchSys s{I.sub0 + j, extra_flags, I.nt, -1, -1, -1, -1};
+            if (j > 0) {
+                s.in_l = (int)(I.foff + (long long)(2 * j - 1) * I.nt);
+                s.out_a = (int)(I.foff + (long long)(2 * (j - 1)) * I.nt);
+            }
+            if (j < I.N - 1) {
+                s.in_r = (int)(I.foff + (long long)(2 * j) * I.nt);
+                s.out_b = (int)(I.foff + (long long)(2 * (j + 1) - 1) * I.nt);
+            }
+            v.push_back(s);
         }
-        if (j < N - 1) {
-            s.in_r = 2 * j;
-            s.out_b = 2 * (j + 1) - 1;
-        }
-        v.push_back(s);
-    }
     return v;
 }
 
@@ -585,7 +612,7 @@ swr_status upload_systems(MarchSys** dst, const std::vector<MarchSys>& v) {
 
 swr_status ensure_workspace(swr_plan_t p) {
     Workspace& w = p->ws;
-    const long long n = (long long)p->nblk * p->nt;
+    const long long n = p->nb;
     const int m = p->d.restart;
     if (w.V && w.m == m && w.n == n) return SWR_OK;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
@@ -611,6 +638,35 @@ swr_status ensure_workspace(swr_plan_t p) {
 }
 
 // ||v||_2 (device -> host)
+// Interface algebra over all instances of the plan (tables only for a batch).
+int p_toeplitz(swr_plan_t p, const double2* cols, const double2* x, const double2* add,
+               double2* y, int mode) {
+    return swr_launch_toeplitz(p->N, p->nt, cols, x, add, y, mode, p->s,
+                               p->batched ? p->d_inst : nullptr, p->d_blk_inst, p->nblk, p->nt);
+}
+int p_lag0(swr_plan_t p, const double2* cols, double2* lag0) {
+    return swr_launch_lag0_setup(p->N, p->nt, cols, lag0, p->s,
+                                 p->batched ? p->d_inst : nullptr, p->d_if_inst, p->nif);
+}
+int p_jump(swr_plan_t p) {
+    return swr_launch_jump(p->d_trace, p->d_sys_final, p->N, p->nt, p->d_scal, p->s,
+                           p->batched ? p->d_inst : nullptr, p->d_if_inst, p->nif);
+}
+int p_causal(swr_plan_t p, const double2* cols, const double2* lag0, const double2* y,
+             double2* x) {
+    if (!p->batched)
+        return swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps, p->d_hist,
+                                 p->d_status, p->s);
+    // whole instances per cooperative launch, as many as fit at once
+    for (const auto& g : p->causal_groups) {
+        const int rc = swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps,
+                                         p->d_hist, p->d_status, p->s, p->d_inst, p->d_if_inst,
+                                         g.first, g.second, p->nif);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
 swr_status norm2(swr_plan_t p, const double2* v, long long n, double* out) {
     Workspace& w = p->ws;
     LK(swr_launch_dots(v, 0, 1, v, n, w.partial, 512, w.h, p->s));
@@ -624,11 +680,10 @@ swr_status norm2(swr_plan_t p, const double2* v, long long n, double* out) {
 
 // y = A x for the interface system (I - L) g = d.
 swr_status apply_A(swr_plan_t p, const double2* x, double2* y) {
-    const long long n = (long long)p->nblk * p->nt;
+    const long long n = p->nb;
     if (p->d.vkind == SWR_V_STATIC) {
         const int pi = prof_begin(p, 1, 0);
-        const int rc = swr_launch_toeplitz(p->N, p->nt, p->d_iface + (size_t)p->nblk * p->nt, x,
-                                           nullptr, y, 0, p->s);
+        const int rc = p_toeplitz(p, p->d_iface + p->nb, x, nullptr, y, 0);
         prof_end(p, pi);
         return rc ? SWR_ERR_UNSUPPORTED : SWR_OK;
     }
@@ -651,18 +706,17 @@ swr_status apply_M(swr_plan_t p, const double2* y, double2* x) {
     const double2* cols;
     const double2* lag0;
     if (p->d.precond == SWR_PC_CAUSAL && p->d.vkind == SWR_V_STATIC) {
-        cols = p->d_iface + (size_t)p->nblk * p->nt;
+        cols = p->d_iface + (size_t)p->nb;
         lag0 = p->d_lag0;
     } else if ((p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) &&
                p->have_L0) {
-        cols = p->d_iface0 + (size_t)p->nblk * p->nt;
+        cols = p->d_iface0 + (size_t)p->nb;
         lag0 = p->d_lag0_0;
     } else {
         return SWR_ERR_STATE;
     }
     const int pi = prof_begin(p, 2, 0);
-    int rc = swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps, p->d_hist,
-                               p->d_status, p->s);
+    int rc = p_causal(p, cols, lag0, y, x);
     prof_end(p, pi);
     if (rc == -2) return SWR_ERR_UNSUPPORTED;
     if (rc) return launch_fail("causal substitution", __LINE__);
@@ -774,8 +828,7 @@ swr_status fixed_point(swr_plan_t p, double2* g, bool g_init, bool classical, sw
                                 p->work_R)))
                 return st;
         } else {
-            if (swr_launch_toeplitz(p->N, p->nt, p->d_iface + (size_t)p->nblk * p->nt, g,
-                                    p->d_iface, w.z, 1, p->s))
+            if (p_toeplitz(p, p->d_iface + p->nb, g, p->d_iface, w.z, 1))
                 return SWR_ERR_UNSUPPORTED;
         }
         CK(cudaMemcpyAsync(w.r, w.z, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
@@ -865,6 +918,7 @@ void swr_destroy(swr_plan_t p) {
         swr_factor_free(p->fs0L[k]);
     }
     cudaFree(p->d_beta); cudaFree(p->d_s02hist); cudaFree(p->d_gconv);
+    cudaFree(p->d_inst); cudaFree(p->d_blk_inst); cudaFree(p->d_if_inst);
     cudaFree(p->d_ckpt); cudaFree(p->d_slab); cudaFree(p->d_ya); cudaFree(p->d_yb);
     cudaFree(p->d_dy); cudaFree(p->d_gy); cudaFree(p->d_gint); cudaFree(p->d_gl);
     cudaFree(p->d_gr); cudaFree(p->d_part); cudaFree(p->d_sys_seg);
@@ -884,12 +938,17 @@ void swr_destroy(swr_plan_t p) {
     delete p;
 }
 
-swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
+// Validate and set up one plan over count problem instances (count = 1: swr_plan).
+static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, void* stream) {
     if (!out) return SWR_ERR_ARG;
     *out = nullptr;
-    if (!d) return SWR_ERR_ARG;
-    if (d->nx < 3 || d->nt < 1 || !(d->dt > 0.0) || d->nsub < 2 || !(d->b0 > d->a0))
-        return SWR_ERR_ARG;
+    if (!ds || count < 1) return SWR_ERR_ARG;
+    const swr_desc* d = &ds[0];
+    for (int i = 0; i < count; ++i) {
+        const swr_desc& e = ds[i];
+        if (e.nx < 3 || e.nt < 1 || !(e.dt > 0.0) || e.nsub < 2 || !(e.b0 > e.a0))
+            return SWR_ERR_ARG;
+    }
     if (d->vkind < 0 || d->vkind > 2 || d->tc < SWR_TC_ROBIN || d->tc > SWR_TC_S02)
         return SWR_ERR_ARG;
     if (d->solver < 0 || d->solver > 2 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
@@ -897,6 +956,20 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     if (d->vkind == SWR_V_TIME && d->solver == SWR_SOLVER_FIXED_POINT) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_TIME && (long long)(d->nt + 1) * d->nx > (1LL << 31)) return SWR_ERR_ARG;
     if (d->precond == SWR_PC_CAUSAL && d->vkind != SWR_V_STATIC) return SWR_ERR_ARG;
+    const double h0 = (d->b0 - d->a0) / (d->nx - 1);
+    if (count > 1) {
+        // a batch shares everything but the grid extent, the step count and the partition
+        if (d->vkind != SWR_V_STATIC) return SWR_ERR_UNSUPPORTED;
+        for (int i = 1; i < count; ++i) {
+            const swr_desc& e = ds[i];
+            const double hi = (e.b0 - e.a0) / (e.nx - 1);
+            if (std::fabs(hi - h0) > 1e-12 * h0 || e.dt != d->dt || e.vkind != d->vkind ||
+                e.tc != d->tc || e.tc_re != d->tc_re || e.tc_im != d->tc_im ||
+                e.solver != d->solver || e.restart != d->restart || e.maxit != d->maxit ||
+                e.tol_abs != d->tol_abs || e.precond != d->precond || e.pc_sweeps != d->pc_sweeps)
+                return SWR_ERR_ARG;
+        }
+    }
     swr_plan_t p = new (std::nothrow) swr_plan_s();
     if (!p) return SWR_ERR_NOMEM;
     p->d = *d;
@@ -910,36 +983,69 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     if (p->d.nl_coef == 0.0) p->d.nl_coef = 1.0;
     p->causal_sweeps = (d->pc_sweeps >= 0) ? std::min(d->pc_sweeps, 16) : 0;
     p->s = (cudaStream_t)stream;
-    p->N = d->nsub;
-    p->nx = d->nx;
-    p->nt = d->nt;
-    p->nblk = 2 * p->N - 2;
-    p->h = (d->b0 - d->a0) / (d->nx - 1);
-    // partition
-    p->off.resize(p->N + 1);
-    if (d->node_off) {
-        for (int j = 0; j <= p->N; ++j) p->off[j] = d->node_off[j];
-    } else {
-        const int E = d->nx - 1, base = E / p->N, extra = E % p->N;
-        p->off[0] = 0;
-        for (int j = 0; j < p->N; ++j) p->off[j + 1] = p->off[j] + base + (j < extra ? 1 : 0);
+    p->ninst = count;
+    p->batched = count > 1;
+    p->h = h0;
+    // instances: partitions, subdomain tables, interface and column offsets
+    int ntot = 0, nmax = 0, xoff = 0, sub = 0, ifc = 0, blk = 0, ntmax = 0;
+    long long foff = 0, coff = 0;
+    for (int i = 0; i < count; ++i) {
+        const swr_desc& e = ds[i];
+        const int Ni = e.nsub;
+        std::vector<int> off(Ni + 1);
+        if (e.node_off) {
+            for (int j = 0; j <= Ni; ++j) off[j] = e.node_off[j];
+        } else {
+            const int E = e.nx - 1, base = E / Ni, extra = E % Ni;
+            off[0] = 0;
+            for (int j = 0; j < Ni; ++j) off[j + 1] = off[j] + base + (j < extra ? 1 : 0);
+        }
+        bool ok = off[0] == 0 && off[Ni] == e.nx - 1;
+        for (int j = 0; j < Ni && ok; ++j) ok = (off[j + 1] - off[j] >= 2);
+        if (!ok) {
+            delete p;
+            return SWR_ERR_ARG;
+        }
+        if (count == 1) p->off = off;
+        for (int j = 0; j < Ni; ++j) {
+            const int nj = off[j + 1] - off[j] + 1;
+            p->n.push_back(nj);
+            p->goff.push_back(xoff + off[j]);
+            p->loff.push_back(ntot);
+            p->tc.push_back((j > 0 ? 1 : 0) | (j < Ni - 1 ? 2 : 0));
+            ntot += nj;
+            nmax = std::max(nmax, nj);
+        }
+        InstInfo I{};
+        I.N = Ni;
+        I.nt = e.nt;
+        I.sub0 = sub;
+        I.if0 = ifc;
+        I.blk0 = blk;
+        I.foff = foff;
+        I.coff = coff;
+        p->inst.push_back(I);
+        p->inst_nx.push_back(e.nx);
+        p->inst_xoff.push_back(xoff);
+        sub += Ni;
+        ifc += Ni - 1;
+        blk += 2 * Ni - 2;
+        foff += (long long)(2 * Ni - 2) * e.nt;
+        coff += (long long)4 * Ni * e.nt;
+        xoff += e.nx;
+        ntmax = std::max(ntmax, e.nt);
     }
-    bool ok = p->off[0] == 0 && p->off[p->N] == d->nx - 1;
-    for (int j = 0; j < p->N && ok; ++j) ok = (p->off[j + 1] - p->off[j] >= 2);
-    if (!ok) {
+    if (foff + coff >= (1LL << 31)) {   // march systems address fluxes with 32-bit offsets
         delete p;
         return SWR_ERR_ARG;
     }
-    int ntot = 0, nmax = 0;
-    for (int j = 0; j < p->N; ++j) {
-        const int nj = p->off[j + 1] - p->off[j] + 1;
-        p->n.push_back(nj);
-        p->goff.push_back(p->off[j]);
-        p->loff.push_back(ntot);
-        p->tc.push_back((j > 0 ? 1 : 0) | (j < p->N - 1 ? 2 : 0));
-        ntot += nj;
-        nmax = std::max(nmax, nj);
-    }
+    p->N = sub;
+    p->nx = xoff;
+    p->nt = ntmax;
+    p->nblk = blk;
+    p->nif = ifc;
+    p->nb = foff;
+    p->ncols = coff;
     p->ntot = ntot;
     p->nmax = nmax;
     const double kappa = 2.0 / d->dt * (p->h / 6.0);
@@ -969,7 +1075,7 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
         p->autotune = atoi(e) != 0;
     }
     swr_status st = SWR_OK;
-    const size_t nb = (size_t)p->nblk * p->nt;
+    const size_t nb = (size_t)p->nb;
     if (!st) st = dalloc(&p->d_n, p->N);
     if (!st) st = dalloc(&p->d_goff, p->N);
     if (!st) st = dalloc(&p->d_loff, p->N);
@@ -977,7 +1083,7 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     if (!st) st = dalloc(&p->d_dg, ntot);
     if (!st) st = dalloc(&p->d_od, ntot);
     if (!st) st = dalloc(&p->d_u0, p->nx);
-    if (!st) st = dalloc(&p->d_iface, nb + (size_t)4 * p->N * p->nt);
+    if (!st) st = dalloc(&p->d_iface, nb + (size_t)p->ncols);
     if (!st) st = dalloc(&p->d_lag0, 4 * p->N);
     if (!st) st = dalloc(reinterpret_cast<char**>(&p->d_hist), swr_causal_scratch_bytes(p->N));
     if (!st) st = dalloc(&p->d_gtmp, nb);
@@ -993,7 +1099,7 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
         st = dalloc(&p->d_Vbar, p->nx);
         if (!st) st = dalloc(&p->d_dg0, ntot);
         if (!st) st = dalloc(&p->d_od0, ntot);
-        if (!st) st = dalloc(&p->d_iface0, nb + (size_t)4 * p->N * p->nt);
+        if (!st) st = dalloc(&p->d_iface0, nb + (size_t)p->ncols);
         if (!st) st = dalloc(&p->d_lag0_0, 4 * p->N);
     }
     if (!st) {
@@ -1005,14 +1111,15 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
             st = SWR_ERR_CUDA;
     }
     if (!st) {
-        auto vb = build_systems(p->N, p->nblk, true);
+        auto vb = build_systems(p, true);
         p->nsys_build = (int)vb.size();
         for (size_t k = 0; k < vb.size(); ++k) {
-            const long long w = (long long)p->n[vb[k].sub] * p->nt;
+            const long long w = (long long)p->n[vb[k].sub] * vb[k].nt;
             p->work_build += w;
             if ((int)k >= p->N) p->work_build_imp += w;
         }
-        for (int j = 0; j < p->N; ++j) p->work_R += (long long)p->n[j] * p->nt;
+        for (const InstInfo& I : p->inst)
+            for (int j = 0; j < I.N; ++j) p->work_R += (long long)p->n[I.sub0 + j] * I.nt;
         st = upload_systems(&p->d_sys_build, vb);
     }
     if (!st && d->tc == SWR_TC_S02) {
@@ -1032,8 +1139,41 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
             st = dalloc(&p->d_s02hist, (size_t)std::max(p->nsys_build, p->N) * 2 * (p->nt + 1));
     }
     if (!st) st = dalloc(&p->d_gconv, nb);
-    if (!st) st = upload_systems(&p->d_sys_R, apply_systems(p->N, 0));
-    if (!st) st = upload_systems(&p->d_sys_final, apply_systems(p->N, SYS_WRITE_UT | SYS_TRACE));
+    if (!st && p->batched) {
+        // instance tables of the interface kernels, and the instance groups that one
+        // cooperative launch of the causal substitution can hold
+        std::vector<int> bi(p->nblk), ii(p->nif);
+        for (int i = 0; i < p->ninst; ++i) {
+            const InstInfo& I = p->inst[i];
+            for (int b = 0; b < 2 * I.N - 2; ++b) bi[I.blk0 + b] = i;
+            for (int k = 0; k < I.N - 1; ++k) ii[I.if0 + k] = i;
+        }
+        st = dalloc(&p->d_inst, p->ninst);
+        if (!st) st = dalloc(&p->d_blk_inst, p->nblk);
+        if (!st) st = dalloc(&p->d_if_inst, p->nif);
+        if (!st && (cudaMemcpy(p->d_inst, p->inst.data(), sizeof(InstInfo) * p->ninst,
+                               cudaMemcpyHostToDevice) ||
+                    cudaMemcpy(p->d_blk_inst, bi.data(), sizeof(int) * p->nblk,
+                               cudaMemcpyHostToDevice) ||
+                    cudaMemcpy(p->d_if_inst, ii.data(), sizeof(int) * p->nif,
+                               cudaMemcpyHostToDevice)))
+            st = SWR_ERR_CUDA;
+        const int cap = swr_causal_capacity(p->nt);
+        int k0 = 0, cnt = 0;
+        for (int i = 0; i < p->ninst && !st; ++i) {
+            const int ni = p->inst[i].N - 1;
+            if (ni > cap) st = SWR_ERR_UNSUPPORTED;
+            if (cnt + ni > cap) {
+                p->causal_groups.push_back({k0, cnt});
+                k0 += cnt;
+                cnt = 0;
+            }
+            cnt += ni;
+        }
+        if (cnt > 0) p->causal_groups.push_back({k0, cnt});
+    }
+    if (!st) st = upload_systems(&p->d_sys_R, apply_systems(p, 0));
+    if (!st) st = upload_systems(&p->d_sys_final, apply_systems(p, SYS_WRITE_UT | SYS_TRACE));
     if (!st) {
         for (auto& e : p->ev)
             if (cudaEventCreate(&e) != cudaSuccess) st = SWR_ERR_CUDA;
@@ -1048,10 +1188,18 @@ swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
     return SWR_OK;
 }
 
+swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
+    return plan_create(d, 1, out, stream);
+}
+
+swr_status swr_plan_batch(const swr_desc* descs, int32_t count, swr_plan_t* out, void* stream) {
+    return plan_create(descs, count, out, stream);
+}
+
 swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) {
     if (!p || !V || !u0) return SWR_ERR_ARG;
     cudaStream_t s = p->s;
-    const size_t nb = (size_t)p->nblk * p->nt;
+    const size_t nb = (size_t)p->nb;
     const size_t nV = (p->d.vkind == SWR_V_TIME) ? (size_t)(p->nt + 1) * p->nx : p->nx;
     CK(cudaEventRecord(p->ev[0], s));
     CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
@@ -1097,7 +1245,7 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
                 return st;
         }
         // the probes wrote into d_iface; the build below starts the clock again
-        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
+        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)p->ncols), s));
         CK(cudaEventRecord(p->ev[0], s));
     }
     if (p->d.vkind == SWR_V_TIME) {
@@ -1110,7 +1258,7 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
         else
             st = factor_for(p, p->fsL[lidx(Lt)], Lt, p->d_V, p->d_dg, p->d_od);
         if (st) return st;
-        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
+        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)p->ncols), s));
         // d = R 0 (Section 4.1; valid for V(t,x)): the first N systems of the build list
         st = run_march(p, false, p->d_sys_build, p->N, nullptr, p->d_iface, nullptr, nullptr,
                        p->d_u0, p->work_R);
@@ -1125,13 +1273,13 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
         if ((st = factor_for(p, p->fsL[lidx(Lb)], Lb, p->d_V, p->d_dg, p->d_od))) return st;
         if (La != Lb && (st = factor_for(p, p->fsL[lidx(La)], La, p->d_V, p->d_dg, p->d_od)))
             return st;
-        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
+        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)p->ncols), s));
         // Algorithm 3, step 1: d and the first columns, 3 marches per interior subdomain
         st = run_march(p, false, p->d_sys_build, p->nsys_build, nullptr, p->d_iface, nullptr,
                        nullptr, p->d_u0, p->work_build);
         if (st) return st;
         const double2* cols = p->d_iface + nb;
-        LK(swr_launch_lag0_setup(p->N, p->nt, cols, p->d_lag0, s));
+        LK(p_lag0(p, cols, p->d_lag0));
     }
     if (p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) {
         const double* Vp = nullptr;                       // V = 0 (Section 5)
@@ -1143,12 +1291,12 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
         if ((st = assemble(p, Vp, p->d_dg0, p->d_od0))) return st;
         const int L0 = march_config(p, p->nsys_build - p->N).L;
         if ((st = factor_for(p, p->fs0L[lidx(L0)], L0, Vp, p->d_dg0, p->d_od0))) return st;
-        CK(cudaMemsetAsync(p->d_iface0, 0, sizeof(double2) * (nb + (size_t)4 * p->N * p->nt), s));
+        CK(cudaMemsetAsync(p->d_iface0, 0, sizeof(double2) * (nb + (size_t)p->ncols), s));
         // impulse marches only (the first N systems of the build list are the d marches)
         st = run_march(p, true, p->d_sys_build + p->N, p->nsys_build - p->N, nullptr,
                        p->d_iface0, nullptr, nullptr, p->d_u0, p->work_build_imp);
         if (st) return st;
-        LK(swr_launch_lag0_setup(p->N, p->nt, p->d_iface0 + nb, p->d_lag0_0, s));
+        LK(p_lag0(p, p->d_iface0 + nb, p->d_lag0_0));
         p->have_L0 = true;
     }
     CK(cudaEventRecord(p->ev[1], s));
@@ -1179,7 +1327,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
         st = fixed_point(p, g, init, p->d.solver == SWR_SOLVER_CLASSICAL, &loc);
     if (st != SWR_OK && st != SWR_ERR_NOT_CONVERGED) return st;
     p->solved = false;
-    CK(cudaMemcpyAsync(p->d_gconv, g, sizeof(double2) * (size_t)p->nblk * p->nt,
+    CK(cudaMemcpyAsync(p->d_gconv, g, sizeof(double2) * (size_t)p->nb,
                        cudaMemcpyDeviceToDevice, s));
     CK(cudaEventRecord(p->ev[2], s));
     // final march (last step of Algorithms 1-3)
@@ -1187,7 +1335,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     swr_status st2 = run_march(p, false, p->d_sys_final, p->N, g, p->d_gtmp, uT, p->d_trace,
                                p->d_u0, p->work_R);
     if (st2) return st2;
-    LK(swr_launch_jump(p->d_trace, p->d_sys_final, p->N, p->nt, p->d_scal, s));
+    LK(p_jump(p));
     CK(cudaEventRecord(p->ev[3], s));
     double jump = 0.0;
     CK(cudaMemcpyAsync(&jump, p->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1201,13 +1349,8 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     loc.t_build_ms = p->t_build_ms;
     loc.t_solve_ms = a;
     loc.t_final_ms = b;
-    long long marches = p->N;   // final march
-    if (p->d.solver == SWR_SOLVER_CLASSICAL) marches += (long long)loc.iterations * p->N;
-    loc.march_point_steps = marches * 0;   // filled below from node counts
-    long long nodes = 0;
-    for (int j = 0; j < p->N; ++j) nodes += p->n[j];
     long long sweeps = 1 + (p->d.solver == SWR_SOLVER_CLASSICAL ? loc.iterations : 0);
-    loc.march_point_steps = sweeps * nodes * (long long)p->nt;
+    loc.march_point_steps = sweeps * p->work_R;   // nodes x steps of one pass over all instances
     if (info) *info = loc;
     p->solved = (st == SWR_OK);
     return st;
@@ -1216,7 +1359,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
 swr_status swr_apply_R(swr_plan_t p, const double* g_in, double* g_out) {
     if (!p || !g_in || !g_out || g_in == g_out) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
-    CK(cudaMemsetAsync(g_out, 0, sizeof(double2) * (size_t)p->nblk * p->nt, p->s));
+    CK(cudaMemsetAsync(g_out, 0, sizeof(double2) * (size_t)p->nb, p->s));
     swr_status st = run_march(p, false, p->d_sys_R, p->N, reinterpret_cast<const double2*>(g_in),
                               reinterpret_cast<double2*>(g_out), nullptr, nullptr, p->d_u0,
                               p->work_R);
@@ -1228,9 +1371,8 @@ swr_status swr_apply_interface(swr_plan_t p, const double* x, double* y) {
     if (!p || !x || !y || x == y) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     if (p->d.vkind != SWR_V_STATIC) return SWR_ERR_UNSUPPORTED;
-    if (swr_launch_toeplitz(p->N, p->nt, p->d_iface + (size_t)p->nblk * p->nt,
-                            reinterpret_cast<const double2*>(x), nullptr,
-                            reinterpret_cast<double2*>(y), 0, p->s))
+    if (p_toeplitz(p, p->d_iface + p->nb, reinterpret_cast<const double2*>(x), nullptr,
+                   reinterpret_cast<double2*>(y), 0))
         return SWR_ERR_UNSUPPORTED;
     CK(cudaStreamSynchronize(p->s));
     return SWR_OK;
@@ -1239,10 +1381,10 @@ swr_status swr_apply_interface(swr_plan_t p, const double* x, double* y) {
 swr_status swr_get_interface(swr_plan_t p, double* d, double* cols) {
     if (!p) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
-    const size_t nb = (size_t)p->nblk * p->nt;
+    const size_t nb = (size_t)p->nb;
     if (d) CK(cudaMemcpyAsync(d, p->d_iface, sizeof(double2) * nb, cudaMemcpyDeviceToDevice, p->s));
     if (cols)
-        CK(cudaMemcpyAsync(cols, p->d_iface + nb, sizeof(double2) * 4 * p->N * p->nt,
+        CK(cudaMemcpyAsync(cols, p->d_iface + nb, sizeof(double2) * p->ncols,
                            cudaMemcpyDeviceToDevice, p->s));
     CK(cudaStreamSynchronize(p->s));
     return SWR_OK;
@@ -1304,7 +1446,7 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
     if (!p || !ubar_ || !dJdV_) return SWR_ERR_ARG;
     if (!p->built || !p->solved) return SWR_ERR_STATE;
     if (p->d.vkind != SWR_V_STATIC || p->d.tc != SWR_TC_ROBIN ||
-        p->d.solver != SWR_SOLVER_GMRES)
+        p->d.solver != SWR_SOLVER_GMRES || p->batched)
         return SWR_ERR_UNSUPPORTED;
     cudaStream_t s = p->s;
     const int nt = p->nt, nx = p->nx, N = p->N;
@@ -1326,7 +1468,7 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
             (st = dalloc(&p->d_dy, nb)) || (st = dalloc(&p->d_gy, nb)) ||
             (st = dalloc(&p->d_gint, nx)) || (st = dalloc(&p->d_gl, nx)) ||
             (st = dalloc(&p->d_gr, nx)) ||
-            (st = upload_systems(&p->d_sys_seg, apply_systems(N, SYS_WRITE_UT))))
+            (st = upload_systems(&p->d_sys_seg, apply_systems(p, SYS_WRITE_UT))))
             return st;
     }
     CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));

@@ -93,8 +93,9 @@ enum : int {
 struct MarchSys {
     int sub;             // subdomain index
     int flags;           // SYS_*
-    int in_l, in_r;      // block index in gin holding l_j / r_j (or -1)
-    int out_a, out_b;    // block index in gout for -l + 2 S v(a) / -r + 2 S v(b) (or -1)
+    int nt;              // time steps of this system (its problem instance)
+    int in_l, in_r;      // offset (complex entries) in gin of l_j / r_j at step 1 (or -1)
+    int out_a, out_b;    // offset in gout of -l + 2 S v(a) / -r + 2 S v(b) at step 1 (or -1)
 };
 
 // Chunked (partitioned) factorisation of the subdomain matrices for one chunk
@@ -170,6 +171,21 @@ struct MarchArgs {
     int* status;
 };
 
+// One problem instance of a batched plan.  The instances' subdomains, interface
+// blocks and Toeplitz first columns are concatenated; the interface kernels take
+// an InstInfo table plus a block -> instance (or interface -> instance) map, or
+// NULL for a single instance described by their (N, nt) arguments.
+struct InstInfo {
+    int N;            // subdomains
+    int nt;           // time steps
+    int sub0;         // first subdomain (global index)
+    int if0;          // first interface (global index; its interfaces are k = 0..N-2)
+    int blk0;         // first interface block (global index; 2N-2 blocks)
+    int pad;
+    long long foff;   // offset (complex entries) of its interface vector (blocks of nt)
+    long long coff;   // offset of its first columns (4N slots of nt)
+};
+
 // Process-wide count of kernels launched by this library (swr_capi.cu).
 void swr_count_launch(int n);
 
@@ -201,7 +217,8 @@ int swr_march_smem_bytes(int T, int G, int stage_slots = 0);
 
 // Interface algebra launchers (swr_krylov.cu)
 int swr_launch_toeplitz(int N, int nt, const double2* cols, const double2* x, const double2* add,
-                        double2* y, int mode, cudaStream_t s);
+                        double2* y, int mode, cudaStream_t s, const InstInfo* inst = nullptr,
+                        const int* blk_inst = nullptr, int nblk_total = 0, int ntmax = 0);
 int swr_launch_dots(const double2* V, long long ldv, int nvec, const double2* w, long long n,
                     double2* partial, int nblocks, double2* out, cudaStream_t s);
 int swr_launch_gemv_sub(const double2* V, long long ldv, int nvec, const double2* h, double2* w,
@@ -216,11 +233,16 @@ int swr_launch_lsq(const double2* H, int ldh, const double2* sv, int k, double2*
                    cudaStream_t s);
 int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0,
                       const double2* y, double2* x, int sweeps, void* scratch, int* status,
-                      cudaStream_t s);
+                      cudaStream_t s, const InstInfo* inst = nullptr, const int* if_inst = nullptr,
+                      int k0 = 0, int nif_group = 0, int nif_total = 0);
+int swr_causal_capacity(int nt);
 size_t swr_causal_scratch_bytes(int N);
-int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s);
+int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s,
+                          const InstInfo* inst = nullptr, const int* if_inst = nullptr,
+                          int nif_total = 0);
 int swr_launch_jump(const double2* trace, const MarchSys* sys, int N, int nt, double* out,
-                    cudaStream_t s);
+                    cudaStream_t s, const InstInfo* inst = nullptr, const int* if_inst = nullptr,
+                    int nif_total = 0);
 int swr_launch_misfit(const double2* u, const double2* tgt, long long n, double h, double2* ubar,
                       double* part, double* out, cudaStream_t s);
 int swr_launch_adj_seed(const double2* ubar, double half_dt, long long n, double2* y,

@@ -48,9 +48,20 @@ __device__ __forceinline__ void block_sources(int o, int N, int& c1, int& i1, in
 // ---------------------------------------------------------------------------
 __global__ void k_toeplitz(int N, int nt, const double2* __restrict__ cols,
                            const double2* __restrict__ x, const double2* __restrict__ add,
-                           double2* __restrict__ y, int mode) {
+                           double2* __restrict__ y, int mode, const InstInfo* __restrict__ inst,
+                           const int* __restrict__ blk_inst) {
     extern __shared__ double2 sh[];
-    const int o = blockIdx.x;
+    int o = blockIdx.x;
+    if (inst) {   // batched plan: this block's instance
+        const InstInfo I = inst[blk_inst[blockIdx.x]];
+        N = I.N;
+        nt = I.nt;
+        o = blockIdx.x - I.blk0;
+        cols += I.coff;
+        x += I.foff;
+        y += I.foff;
+        if (add) add += I.foff;
+    }
     int c1, i1, c2, i2;
     block_sources(o, N, c1, i1, c2, i2);
     double2* C1 = sh;
@@ -93,13 +104,15 @@ __global__ void k_toeplitz(int N, int nt, const double2* __restrict__ cols,
 }
 
 int swr_launch_toeplitz(int N, int nt, const double2* cols, const double2* x, const double2* add,
-                        double2* y, int mode, cudaStream_t s) {
-    const int smem = 4 * nt * (int)sizeof(double2);
+                        double2* y, int mode, cudaStream_t s, const InstInfo* inst,
+                        const int* blk_inst, int nblk_total, int ntmax) {
+    const int smem = 4 * (inst ? ntmax : nt) * (int)sizeof(double2);
     if (smem > 227 * 1024) return -2;
     if (cudaFuncSetAttribute(k_toeplitz, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return -1;
-    k_toeplitz<<<2 * N - 2, 256, smem, s>>>(N, nt, cols, x, add, y, mode);
+    k_toeplitz<<<inst ? nblk_total : 2 * N - 2, 256, smem, s>>>(N, nt, cols, x, add, y, mode, inst,
+                                                                 blk_inst);
     swr_count_launch(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -290,12 +303,21 @@ int swr_launch_lsq(const double2* H, int ldh, const double2* sv, int k, double2*
 // (trace buffer [sys][2][nt], systems 0..N-1 are the subdomains in order).
 // ---------------------------------------------------------------------------
 __global__ void k_jump(const double2* __restrict__ trace, int N, int nt,
-                       unsigned long long* out) {
+                       unsigned long long* out, const InstInfo* __restrict__ inst,
+                       const int* __restrict__ if_inst, int nif_total) {
+    // trace rows have stride nt (the longest instance); interface k lies between
+    // subdomains j and j+1 of its instance
     double m = 0.0;
-    const long long tot = (long long)(N - 1) * nt;
+    const long long tot = (long long)(inst ? nif_total : N - 1) * nt;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
          q += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(q / nt), n = (int)(q % nt);
+        int j = (int)(q / nt);
+        const int n = (int)(q % nt);
+        if (inst) {
+            const InstInfo I = inst[if_inst[j]];
+            if (n >= I.nt) continue;
+            j = I.sub0 + (j - I.if0);
+        }
         const double2 a = trace[((size_t)j * 2 + 1) * nt + n];
         const double2 b = trace[((size_t)(j + 1) * 2 + 0) * nt + n];
         m = fmax(m, hypot(a.x - b.x, a.y - b.y));
@@ -304,9 +326,10 @@ __global__ void k_jump(const double2* __restrict__ trace, int N, int nt,
 }
 
 int swr_launch_jump(const double2* trace, const MarchSys*, int N, int nt, double* out,
-                    cudaStream_t s) {
+                    cudaStream_t s, const InstInfo* inst, const int* if_inst, int nif_total) {
     cudaMemsetAsync(out, 0, sizeof(double), s);
-    k_jump<<<64, 256, 0, s>>>(trace, N, nt, reinterpret_cast<unsigned long long*>(out));
+    k_jump<<<64, 256, 0, s>>>(trace, N, nt, reinterpret_cast<unsigned long long*>(out), inst,
+                              if_inst, nif_total);
     swr_count_launch(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -326,22 +349,32 @@ int swr_launch_jump(const double2* trace, const MarchSys*, int N, int nt, double
 //                 lag-0 solves, step by step, one thread per interface.
 // ---------------------------------------------------------------------------
 __global__ void k_lag0_setup(int N, int nt, const double2* __restrict__ cols,
-                             double2* __restrict__ lag0) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N - 1) return;
+                             double2* __restrict__ lag0, const InstInfo* __restrict__ inst,
+                             const int* __restrict__ if_inst, int nif_total) {
+    const int kg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kg >= (inst ? nif_total : N - 1)) return;
+    int k = kg;
+    if (inst) {
+        const InstInfo I = inst[if_inst[kg]];
+        nt = I.nt;
+        k = kg - I.if0;
+        cols += I.coff;
+    }
     const double2 a = cols[(size_t)(4 * (k + 1) + 0) * nt];   // X^{k+1,1}[0]: r_k <- l_{k+1}
     const double2 b = cols[(size_t)(4 * k + 3) * nt];         // X^{k,4}[0]:   l_{k+1} <- r_k
     // D = [[1, -a], [-b, 1]],  D^{-1} = [[1, a], [b, 1]] / (1 - a b)
     const double2 det = csub(make_double2(1.0, 0.0), cmul(a, b));
     const double2 r = crcp(det);
-    lag0[k * 4 + 0] = r;
-    lag0[k * 4 + 1] = cmul(a, r);
-    lag0[k * 4 + 2] = cmul(b, r);
-    lag0[k * 4 + 3] = r;
+    lag0[kg * 4 + 0] = r;
+    lag0[kg * 4 + 1] = cmul(a, r);
+    lag0[kg * 4 + 2] = cmul(b, r);
+    lag0[kg * 4 + 3] = r;
 }
 
-int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s) {
-    k_lag0_setup<<<(N + 127) / 128, 128, 0, s>>>(N, nt, cols, lag0);
+int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s,
+                          const InstInfo* inst, const int* if_inst, int nif_total) {
+    const int nif = inst ? nif_total : N - 1;
+    k_lag0_setup<<<(nif + 127) / 128, 128, 0, s>>>(N, nt, cols, lag0, inst, if_inst, nif_total);
     swr_count_launch(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -369,14 +402,15 @@ __device__ __forceinline__ void store_release(int* p, int v) {
     r.store(v, cuda::memory_order_release);
 }
 
-// Wait until the neighbours of interface k have reached `target`; returns false
-// (after raising the abort flag) on timeout or when another CTA aborted.
-__device__ bool wait_neighbours(int k, int nif, int target, const int* progress, int* abortf,
-                                int* status) {
+// Wait until the neighbours of interface k (global index; hl, hr: they exist in
+// its instance) have reached `target`; returns false (after raising the abort
+// flag) on timeout or when another CTA aborted.
+__device__ bool wait_neighbours(int k, bool hl, bool hr, int target, const int* progress,
+                                int* abortf, int* status) {
     long long polls = 0;
     for (int side = 0; side < 2; ++side) {
         const int nb = (side == 0) ? k - 1 : k + 1;
-        if (nb < 0 || nb >= nif) continue;
+        if ((side == 0 && !hl) || (side == 1 && !hr)) continue;
         while (load_acquire(progress + nb) < target) {
             if (load_acquire(abortf) != 0) return false;
             if (++polls > kWaitPolls) {
@@ -399,11 +433,26 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                                                      const double2* __restrict__ y,
                                                      double2* __restrict__ x,
                                                      double2* __restrict__ xsw, int* progress,
-                                                     int* abortf, int* status) {
+                                                     int* abortf, int* status,
+                                                     const InstInfo* __restrict__ inst,
+                                                     const int* __restrict__ if_inst, int k0,
+                                                     int nif_all) {
     __shared__ double2 hp[2][4];     // partial histories, by parity of the step they serve
     __shared__ int s_go;
-    const int nif = N - 1;
-    const int k = blockIdx.x;
+    // global interface kg (progress, sweep values, lag-0 blocks); local k within its
+    // instance (blocks, columns)
+    const int kg = k0 + blockIdx.x;
+    int k = kg;
+    if (inst) {
+        const InstInfo I = inst[if_inst[kg]];
+        N = I.N;
+        nt = I.nt;
+        k = kg - I.if0;
+        cols += I.coff;
+        y += I.foff;
+        x += I.foff;
+    }
+    const bool has_l = (k >= 1), has_r = (k + 1 <= N - 2);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double2 zero = make_double2(0.0, 0.0);
     // source e of interface k:
@@ -434,17 +483,17 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
     const bool solver = (threadIdx.x == 0);
     if (solver) {
         for (int e = 0; e < 4; ++e) source(e, hs[e], cs[e], xs[e]);
-        D00 = lag0[k * 4 + 0];
-        D01 = lag0[k * 4 + 1];
-        D10 = lag0[k * 4 + 2];
-        D11 = lag0[k * 4 + 3];
+        D00 = lag0[kg * 4 + 0];
+        D01 = lag0[kg * 4 + 1];
+        D10 = lag0[kg * 4 + 2];
+        D11 = lag0[kg * 4 + 3];
         cB0 = hs[1] ? cs[1][0] : zero;
         cD0 = hs[3] ? cs[3][0] : zero;
         for (int e = 0; e < 4; ++e) c1[e] = (hs[e] && nt > 1) ? cs[e][1] : zero;
     }
     __syncthreads();
     for (int n = 0; n < nt; ++n) {
-        if (solver) s_go = wait_neighbours(k, nif, n * S1, progress, abortf, status) ? 1 : 0;
+        if (solver) s_go = wait_neighbours(kg, has_l, has_r, n * S1, progress, abortf, status) ? 1 : 0;
         __syncthreads();                                       // B1: values < n visible
         if (!s_go) break;
         if (solver) {
@@ -460,20 +509,20 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             double2 z2 = cfma(D11, r2, cmul(D10, r1));
             for (int sw = 1; sw <= sweeps; ++sw) {
                 // publish sweep sw-1 of this step, then use the neighbours' sweep sw-1
-                double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif;
-                out[2 * k] = z1;
-                out[2 * k + 1] = z2;
-                store_release(progress + k, n * S1 + sw);
-                if (!wait_neighbours(k, nif, n * S1 + sw, progress, abortf, status)) break;
-                const double2 xr = (k + 1 <= N - 2) ? out[2 * (k + 1)] : zero;   // r_{k+1}
-                const double2 xl = (k >= 1) ? out[2 * (k - 1) + 1] : zero;      // l_k
+                double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif_all;
+                out[2 * kg] = z1;
+                out[2 * kg + 1] = z2;
+                store_release(progress + kg, n * S1 + sw);
+                if (!wait_neighbours(kg, has_l, has_r, n * S1 + sw, progress, abortf, status)) break;
+                const double2 xr = has_r ? out[2 * (kg + 1)] : zero;       // r_{k+1}
+                const double2 xl = has_l ? out[2 * (kg - 1) + 1] : zero;   // l_k
                 const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
                 z1 = cfma(D01, e2, cmul(D00, e1));
                 z2 = cfma(D11, e2, cmul(D10, e1));
             }
             x[(size_t)(2 * k) * nt + n] = z1;
             x[(size_t)(2 * k + 1) * nt + n] = z2;
-            store_release(progress + k, (n + 1) * S1);         // orders the x writes above
+            store_release(progress + kg, (n + 1) * S1);        // orders the x writes above
         } else if (w >= 1) {
             // step n+1's history from values s <= n-1 (lags >= 2)
             double2 acc = zero;
@@ -488,27 +537,45 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
 
 size_t swr_causal_scratch_bytes(int N) {
     // xsw: 2 x 2(N-1) complex sweep values, then N-1 progress counters and the abort flag
+    // (a batched plan passes N = its total interface count + 1)
     return sizeof(double2) * (size_t)4 * (N - 1) + sizeof(int) * (size_t)N;
 }
 
-int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, const double2* y,
-                      double2* x, int sweeps, void* scratch, int* status, cudaStream_t s) {
-    const int nif = N - 1;
-    double2* xsw = static_cast<double2*>(scratch);
-    int* progress = reinterpret_cast<int*>(xsw + (size_t)4 * nif);
-    int* abortf = progress + nif;
+// Interfaces one cooperative launch can hold (all CTAs resident at once).
+int swr_causal_capacity(int) {
     int dev = 0, nsm = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_causal_wave, 160, 0) != cudaSuccess)
+        return 0;
+    return nsm * per;
+}
+
+// Single instance (inst == NULL): interfaces 0..N-2.  Batched plan: interfaces
+// k0 .. k0+nif_group-1 of the nif_total, whole instances only (a wave never
+// waits on an interface outside its instance).
+int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, const double2* y,
+                      double2* x, int sweeps, void* scratch, int* status, cudaStream_t s,
+                      const InstInfo* inst, const int* if_inst, int k0, int nif_group,
+                      int nif_total) {
+    const int nif = inst ? nif_total : N - 1;
+    const int ncta = inst ? nif_group : N - 1;
+    if (!inst) k0 = 0;
+    if (ncta <= 0) return 0;
+    double2* xsw = static_cast<double2*>(scratch);
+    int* progress = reinterpret_cast<int*>(xsw + (size_t)4 * nif);
+    int* abortf = progress + nif;
+    const int cap = swr_causal_capacity(nt);
+    if (cap <= 0) return -1;
+    if (ncta > cap) return -2;           // all CTAs must be resident at once
+    // this launch's progress counters and the abort flag start at zero
+    if (cudaMemsetAsync(progress + k0, 0, sizeof(int) * (size_t)ncta, s) != cudaSuccess ||
+        cudaMemsetAsync(abortf, 0, sizeof(int), s) != cudaSuccess)
         return -1;
-    if (nif > nsm * per) return -2;      // all CTAs must be resident at once
-    // progress counters and the abort flag start at zero on every call
-    if (cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)N, s) != cudaSuccess) return -1;
     void* args[] = {(void*)&N, (void*)&nt, (void*)&sweeps, (void*)&cols, (void*)&lag0,
                     (void*)&y, (void*)&x, (void*)&xsw, (void*)&progress, (void*)&abortf,
-                    (void*)&status};
-    if (cudaLaunchCooperativeKernel((const void*)k_causal_wave, dim3(nif), dim3(160), args, 0, s) !=
+                    (void*)&status, (void*)&inst, (void*)&if_inst, (void*)&k0, (void*)&nif};
+    if (cudaLaunchCooperativeKernel((const void*)k_causal_wave, dim3(ncta), dim3(160), args, 0, s) !=
         cudaSuccess)
         return -1;
     swr_count_launch(1);

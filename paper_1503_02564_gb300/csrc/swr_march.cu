@@ -533,7 +533,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     };
 
     const double2 zero = make_double2(0.0, 0.0);
-    MarchSys sy = {0, 0, -1, -1, -1, -1};
+    MarchSys sy = {0, 0, 0, -1, -1, -1, -1};
     int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0;
     if (valid) {
         sy = a.sys[sidx];
@@ -546,6 +546,20 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     }
     const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
     const bool realsep = valid && (p <= Pj);          // separators beyond Pj are padding
+    // Systems of a launch may have different step counts (a batch of problem
+    // instances): the CTA runs to the longest of its systems (a cluster holds one
+    // system), and a system past its own count neither reads fluxes, nor writes
+    // outputs, nor advances its state.
+    int ntc = 0;
+    if (C == 1) {
+        for (int gg = 0; gg < G; ++gg) {
+            const int si = blockIdx.x * G + gg;
+            if (si < a.nsys) ntc = max(ntc, a.sys[si].nt);
+        }
+    } else {
+        ntc = a.sys[blockIdx.x / C].nt;
+    }
+    ntc = min(ntc, nt);
     // factor pointers; with per-step factorisations they advance by one step's
     // stride per time step (the strides are zero for a constant matrix)
     const double2* F = a.fac + (size_t)j * L * 4 * P + (p < P ? p : 0);
@@ -633,7 +647,8 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     for (int i = 0; i < (MODE == 2 ? L : 1); ++i) ga_int[i] = 0.0;
 
     double2 lin = zero, rin = zero;
-    for (int t = 1; t <= nt; ++t) {
+    for (int t = 1; t <= ntc; ++t) {
+        const bool live = t <= sy.nt;
         if (stage == 0 && stepped && valid && t < nt) {
             // the next step's factors stream from HBM: request them into L2 now
             if (Lp > 0) {
@@ -736,7 +751,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     if (sy.flags & SYS_IMP_L)
                         lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                     else
-                        lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * a.gstride + a.t0 + t - 1] : zero;
+                        lin = (live && sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l + a.t0 + t - 1] : zero;
                     f = cfms(lin, a.inv_ik, f);
                     if (a.s02) f = cfma(hsum[hs_l], a.c2_ik, f);
                 }
@@ -744,7 +759,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     if (sy.flags & SYS_IMP_R)
                         rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                     else
-                        rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * a.gstride + a.t0 + t - 1] : zero;
+                        rin = (live && sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r + a.t0 + t - 1] : zero;
                     f = cfms(rin, a.inv_ik, f);
                     if (a.s02) f = cfma(hsum[hs_r], a.c2_ik, f);
                 }
@@ -790,9 +805,9 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     double2 v = cfms(FAC(i, 2), vL, y[i]);
                     v = cfms(FAC(i, 3), vR, v);
                     if constexpr (MODE == 1)
-                        a.vrec[(size_t)(t - 1) * a.nxrec + goff + sp + 1 + i] = v;
+                        if (live) a.vrec[(size_t)(t - 1) * a.nxrec + goff + sp + 1 + i] = v;
                     if constexpr (MODE == 2) vv[i] = v;
-                    u[i] = make_double2(fma(2.0, v.x, -u[i].x), fma(2.0, v.y, -u[i].y));
+                    if (live) u[i] = make_double2(fma(2.0, v.x, -u[i].x), fma(2.0, v.y, -u[i].y));
                 }
             }
         }
@@ -800,7 +815,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             // elements e = 0..Lp from separator p (node sp) to separator p+1 (node
             // sp + Lp + 1); x = this march's v, y = the recorded forward v of the
             // mirrored step
-            if (valid && p < Pj) {
+            if (valid && live && p < Pj) {
                 const double2* yrow = a.vfwd + (size_t)(nt - t) * a.nxrec + goff + sp;
                 const double2 xL = *SEP(src, p), xR = *SEP(src, p + 1);
                 const double h12 = a.h12;
@@ -824,7 +839,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             }
         }
         if (stage > 0) issue_fd(t < nt ? F + a.fstride : nullptr);
-        if (realsep) {
+        if (realsep && live) {
             const double2 v = *SEP(src, p);
             if constexpr (MODE == 1) {   // an interface node is recorded by its left subdomain
                 if (!(p == 0 && (tcf & 1))) a.vrec[(size_t)(t - 1) * a.nxrec + goff + sp] = v;
@@ -837,7 +852,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                 if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
                     double2 o = csub(cmul(a.two_sigma, v), lin);
                     if (a.s02) o = cfma(a.two_c2, hsum[hs_l], o);
-                    a.gout[(size_t)sy.out_a * a.gstride + a.t0 + t - 1] = o;
+                    a.gout[(size_t)sy.out_a + a.t0 + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
@@ -846,7 +861,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                 if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
                     double2 o = csub(cmul(a.two_sigma, v), rin);
                     if (a.s02) o = cfma(a.two_c2, hsum[hs_r], o);
-                    a.gout[(size_t)sy.out_b * a.gstride + a.t0 + t - 1] = o;
+                    a.gout[(size_t)sy.out_b + a.t0 + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
@@ -884,7 +899,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             const double2 us = *SEP(usep, p);
             bad |= !cfinite(us);
             // the interface node belongs to the left subdomain
-            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || j == 0)) a.uT[goff + sp] = us;
+            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || !(tcf & 1))) a.uT[goff + sp] = us;
         }
     }
     if (bad) atomicOr(a.status, ST_NONFINITE);
@@ -991,7 +1006,7 @@ __global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
             cl.sync();
     };
     const double2 zero = make_double2(0.0, 0.0);
-    MarchSys sy = {0, 0, -1, -1, -1, -1};
+    MarchSys sy = {0, 0, 0, -1, -1, -1, -1};
     int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0, n = 0;
     if (valid) {
         sy = a.sys[sidx];
@@ -1117,14 +1132,14 @@ __global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
                     if (sy.flags & SYS_IMP_L)
                         lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                     else
-                        lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
+                        lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l + t - 1] : zero;
                     f = cfms(lin, a.inv_ik, f);
                 }
                 if (re && (tcf & 2)) {
                     if (sy.flags & SYS_IMP_R)
                         rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                     else
-                        rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
+                        rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r + t - 1] : zero;
                     f = cfms(rin, a.inv_ik, f);
                 }
                 dg = tdep_diag(V0, V1, gs, sp, n, tcf, h, kappa, ta.sig_ik);
@@ -1196,12 +1211,12 @@ __global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
             *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
             if (p == 0) {
                 if ((tcf & 1) && sy.out_a >= 0 && a.gout)
-                    a.gout[(size_t)sy.out_a * nt + t - 1] = csub(cmul(a.two_sigma, v), lin);
+                    a.gout[(size_t)sy.out_a + t - 1] = csub(cmul(a.two_sigma, v), lin);
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
             if (p == Pj) {
                 if ((tcf & 2) && sy.out_b >= 0 && a.gout)
-                    a.gout[(size_t)sy.out_b * nt + t - 1] = csub(cmul(a.two_sigma, v), rin);
+                    a.gout[(size_t)sy.out_b + t - 1] = csub(cmul(a.two_sigma, v), rin);
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
         }
@@ -1220,7 +1235,7 @@ __global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
         if (realsep) {
             const double2 us = *SEP(usep, p);
             bad |= !cfinite(us);
-            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || j == 0)) a.uT[goff + sp] = us;
+            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || !(tcf & 1))) a.uT[goff + sp] = us;
         }
     }
     if (bad) atomicOr(a.status, ST_NONFINITE);

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
             cl.sync();
     };
     const double2 zero = make_double2(0.0, 0.0);
-    MarchSys sy = {0, 0, -1, -1, -1, -1};
+    MarchSys sy = {0, 0, 0, -1, -1, -1, -1};
     int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0;
     if (valid) {
         sy = a.sys[sidx];
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 if (sy.flags & SYS_IMP_L)
                     lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                 else
-                    lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l * nt + t - 1] : zero;
+                    lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l + t - 1] : zero;
                 fs = cfms(lin, a.inv_ik, fs);
                 if (a.s02) fs = cfma(hsum[hs_l], a.c2_ik, fs);
             }
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 if (sy.flags & SYS_IMP_R)
                     rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
                 else
-                    rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r * nt + t - 1] : zero;
+                    rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r + t - 1] : zero;
                 fs = cfms(rin, a.inv_ik, fs);
                 if (a.s02) fs = cfma(hsum[hs_r], a.c2_ik, fs);
             }
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
                     double2 o = csub(cmul(a.two_sigma, v), lin);
                     if (a.s02) o = cfma(a.two_c2, hsum[hs_l], o);
-                    a.gout[(size_t)sy.out_a * nt + t - 1] = o;
+                    a.gout[(size_t)sy.out_a + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
                     double2 o = csub(cmul(a.two_sigma, v), rin);
                     if (a.s02) o = cfma(a.two_c2, hsum[hs_r], o);
-                    a.gout[(size_t)sy.out_b * nt + t - 1] = o;
+                    a.gout[(size_t)sy.out_b + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
         if (realsep) {
             const double2 us = *SEP(usep, p);
             bad |= !cfinite(us);
-            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || j == 0)) a.uT[goff + sp] = us;
+            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || !(tcf & 1))) a.uT[goff + sp] = us;
         }
         if (p == 0 && na.iters) atomicMax(na.iters + sidx, itmax);
     }

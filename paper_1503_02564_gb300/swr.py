@@ -84,6 +84,8 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         vp, dp = ctypes.c_void_p, ctypes.c_void_p
         L.swr_plan.argtypes = [ctypes.POINTER(swr_desc), ctypes.POINTER(vp), vp]
+        L.swr_plan_batch.argtypes = [ctypes.POINTER(swr_desc), ctypes.c_int32,
+                                     ctypes.POINTER(vp), vp]
         L.swr_build_interface.argtypes = [vp, dp, dp]
         L.swr_solve.argtypes = [vp, dp, ctypes.c_int32, dp, ctypes.POINTER(swr_info)]
         L.swr_apply_R.argtypes = [vp, dp, dp]
@@ -101,7 +103,7 @@ def lib():
         L.swr_kernel_launch_count.restype = ctypes.c_int64
         L.swr_status_string.argtypes = [ctypes.c_int]
         L.swr_status_string.restype = ctypes.c_char_p
-        for f in ("swr_plan", "swr_build_interface", "swr_solve", "swr_apply_R",
+        for f in ("swr_plan", "swr_plan_batch", "swr_build_interface", "swr_solve", "swr_apply_R",
                   "swr_apply_interface", "swr_get_interface", "swr_apply_precond", "swr_adjoint",
                   "swr_get_stats", "swr_causal_solve_noalloc", "swr_misfit"):
             getattr(L, f).restype = ctypes.c_int
@@ -180,6 +182,10 @@ class Plan:
     def n_interface(self):
         return self.nblk * self.nt
 
+    @property
+    def n_cols(self):
+        return 4 * self.nsub * self.nt
+
     def build_interface(self, V, u0):
         nV = self.nx if self.vkind != SWR_V_TIME else (self.nt + 1) * self.nx
         _check(lib().swr_build_interface(self.handle, _ptr(V, torch.float64, nV, "V"),
@@ -208,7 +214,7 @@ class Plan:
 
     def get_interface(self, d=None, cols=None):
         _check(lib().swr_get_interface(self.handle, _ptr(d, torch.complex128, self.n_interface, "d"),
-                                       _ptr(cols, torch.complex128, 4 * self.nsub * self.nt, "cols")),
+                                       _ptr(cols, torch.complex128, self.n_cols, "cols")),
                "swr_get_interface")
 
     def apply_precond(self, y, x):
@@ -271,3 +277,56 @@ class SWRMisfit(torch.autograd.Function):
         grad = torch.empty(ctx.plan.nx, dtype=torch.float64, device=ubar.device)
         ctx.plan.adjoint(ubar, grad, ctx.ckpt_every)
         return grad * gJ, None, None, None, None
+
+
+class BatchPlan(Plan):
+    """swr_plan_batch: independent instances in one plan.  `instances` is a list of
+    dicts with the per-instance fields nx, a0, b0, nt, nsub and optionally
+    node_off; the keyword arguments are shared.  Arrays (V, u0, uT, interface
+    vectors, first columns) are the instances' arrays concatenated in order;
+    `inst_nx`, `inst_nb` and `inst_ncols` give the per-instance lengths."""
+
+    def __init__(self, instances, *, dt, tc=SWR_TC_ROBIN, p=0j, solver=SWR_SOLVER_GMRES,
+                 restart=30, maxit=2000, tol_abs=1e-10, precond=SWR_PC_NONE, pc_sweeps=-1,
+                 stream=None):
+        count = len(instances)
+        descs = (swr_desc * count)()
+        self._offs = []
+        for i, ins in enumerate(instances):
+            d = descs[i]
+            d.nx, d.a0, d.b0, d.nt, d.dt, d.nsub = (int(ins["nx"]), float(ins["a0"]),
+                                                    float(ins["b0"]), int(ins["nt"]), dt,
+                                                    int(ins["nsub"]))
+            if ins.get("node_off") is not None:
+                arr = (ctypes.c_int32 * (d.nsub + 1))(*[int(v) for v in ins["node_off"]])
+                self._offs.append(arr)
+                d.node_off = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32))
+            d.vkind, d.tc = SWR_V_STATIC, tc
+            d.tc_re, d.tc_im = complex(p).real, complex(p).imag
+            d.solver, d.restart, d.maxit, d.tol_abs, d.precond = (solver, restart, maxit,
+                                                                  tol_abs, precond)
+            d.nl_maxit, d.nl_tol, d.nl_coef, d.pc_sweeps = 50, 1e-13, 1.0, pc_sweeps
+        self.descs = descs
+        self.inst_nx = [int(i["nx"]) for i in instances]
+        self.inst_nb = [(2 * int(i["nsub"]) - 2) * int(i["nt"]) for i in instances]
+        self.inst_ncols = [4 * int(i["nsub"]) * int(i["nt"]) for i in instances]
+        self.nx = sum(self.inst_nx)
+        self.nt = max(int(i["nt"]) for i in instances)
+        self.nsub = sum(int(i["nsub"]) for i in instances)
+        self.nblk = 2 * self.nsub - 2 * count
+        self.vkind = SWR_V_STATIC
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(lib().swr_plan_batch(descs, count, ctypes.byref(h),
+                                    ctypes.c_void_p(stream.cuda_stream)), "swr_plan_batch")
+        self.handle = h
+
+    @property
+    def n_interface(self):
+        return sum(self.inst_nb)
+
+    @property
+    def n_cols(self):
+        return sum(self.inst_ncols)

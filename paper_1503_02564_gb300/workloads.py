@@ -102,6 +102,39 @@ def config2(nsub=16, nx=200001, nt=500, dt=1e-3) -> Workload:
                     equal_offsets(nx, nsub), V, u0)
 
 
+def config3(count=128, nsub_range=(4, 64), size_range=(200, 2000), total_range=(2000, 40000),
+            nt_range=(100, 400), h=1e-3, dt=1e-3):
+    """Batch of independent SWR instances.  Each: N ~ U{nsub_range} subdomains
+    whose sizes (nodes, shared ends included) are ~ U{size_range}, redrawn until
+    the instance's node count lies in total_range; nt ~ U{nt_range}; grid step h
+    on a domain centred at 0; V = sum of 4 Gaussian bumps (amplitudes U(-10, 10),
+    widths U(0.5, 3), centres inside the domain); u0 one Gaussian packet (width
+    U(0.5, 2), wavenumber U(-10, 10)).  Returns a list of Workloads."""
+    rng = np.random.default_rng(SEED_BASE + 3)
+    out = []
+    for i in range(count):
+        while True:
+            N = int(rng.integers(nsub_range[0], nsub_range[1] + 1))
+            elems = rng.integers(size_range[0] - 1, size_range[1], size=N)   # nodes - 1
+            nx = int(elems.sum()) + 1
+            if total_range[0] <= nx <= total_range[1]:
+                break
+        nt = int(rng.integers(nt_range[0], nt_range[1] + 1))
+        half = 0.5 * (nx - 1) * h
+        a0, b0 = -half, half
+        x = a0 + h * np.arange(nx)
+        amp = rng.uniform(-10.0, 10.0, size=4)
+        w = rng.uniform(0.5, 3.0, size=4)
+        c = rng.uniform(a0, b0, size=4)
+        V = np.zeros(nx)
+        for k in range(4):
+            V += amp[k] * np.exp(-(x - c[k]) ** 2 / (2.0 * w[k] ** 2))
+        u0 = gaussian_packets(x, rng, 1, (0.5 * a0, 0.5 * b0), (0.5, 2.0), (-10.0, 10.0))
+        off = np.concatenate([[0], np.cumsum(elems)]).astype(np.int32)
+        out.append(Workload("config3_batch_%d" % i, a0, b0, nx, dt, nt, off, V, u0))
+    return out
+
+
 def config4(nsub=64, nx=60001, nt=1000, dt=1e-3) -> Workload:
     """Time-dependent V(t,x) = -x^2/4 (1 + 0.5 sin 4t) - 10 exp(-(x - 5 sin t)^2)
     on (-30, 30); u0 = exp(-(x-x0)^2/2 + i k0 x), x0 ~ U(-10,10), k0 ~ U(-5,5).

@@ -362,6 +362,8 @@ def run_batch(args):
                                "iterations_min_max": [min(its), max(its)],
                                "max_rel_diff_uT": dev_max},
         "batched_iterations": info["iterations"], "batched_residual": info["residual"],
+        "batched_phases_ms": {"build": info["t_build_ms"], "solve": info["t_solve_ms"],
+                              "final": info["t_final_ms"]},
         "cpu_baseline": cpu,
         "e2e": {"value": ps / (t_e / args.steps * 1e-3), "unit": "point-steps/s",
                 "h2d_bytes_per_step": V.numel() * 8 + u0.numel() * 16,

@@ -80,8 +80,18 @@ struct swr_plan_s {
     // V(t,x): factor every step's matrix once per build and stream the factors
     // (SWR_TDEP_PRECOMP=0, or too little free memory: refactorise inside the march)
     int tdep_pre = -1;             // -1: not decided yet
-    // launch shapes chosen by the autotuner: {kind, nsys, L, C, G, T, ngroups}
-    std::vector<std::array<int, 7>> tuned;
+    // launch shapes chosen by the autotuner: {kind, nsys, L, C, G, T, ngroups, ragged}
+    std::vector<std::array<int, 8>> tuned;
+    // host copies of the uploaded system lists (device pointer, systems), and the
+    // ragged packings built for them: key (list, count, L, T) -> device tables
+    std::vector<std::pair<const MarchSys*, std::vector<MarchSys>>> host_sys;
+    struct Packing {
+        const MarchSys* sys;
+        int nsys, L, T, nctas, gmax;
+        int* d_start;
+        int2* d_rag;
+    };
+    std::vector<Packing> packings;
     double2* d_u0 = nullptr;
     double* d_V = nullptr;
     double* d_Vbar = nullptr;      // potential of the preconditioner operator (MEAN_POTENTIAL)
@@ -209,6 +219,7 @@ swr_status read_status(swr_plan_t p) {
 // (or too few systems for the SMs) is spread over a thread-block cluster.
 struct MarchCfg {
     int L = 8, C = 1, G = 1, T = 32, ngroups = 1;
+    int ragged = 0;   // C == 1 only: systems packed by size (G, ngroups from the packing)
 };
 
 inline int chunks_for(int nmax, int L) { return (nmax - 1 + L) / (L + 1); }
@@ -253,6 +264,7 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
             c.G = t[4];
             c.T = t[5];
             c.ngroups = t[6];
+            c.ragged = t[7];
             return c;
         }
     const int nsm = p->nsm;
@@ -299,13 +311,79 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
             c.C = std::max(c.C, C);
         }
     }
-    return shape_of(c, tps, nsys);
+    c = shape_of(c, tps, nsys);
+    if (p->batched && kind == MK_STATIC && c.C == 1) {
+        // uneven subdomains of several instances: pack by size instead of padding
+        c.ragged = 1;
+        c.T = std::min(TMAX, std::max(128, ((tps + 31) / 32) * 32));
+    }
+    return c;
 }
 
 inline int lidx(int L) { return L == 4 ? 0 : (L == 8 ? 1 : 2); }
 
 inline double2 cmul_h(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Ragged packing of a system list for chunk length L and T threads per CTA:
+// systems sorted by step count, then by thread count P_j + 1 (largest first),
+// fill CTAs in order, a new CTA starting when the next system does not fit.  A
+// CTA then holds systems of (nearly) equal length, and the longest CTAs come
+// first in the grid, which the hardware schedules first.  Returns the cached
+// packing, or nullptr when a system needs more than T threads or the list is
+// not known on the host.
+const swr_plan_s::Packing* ragged_packing(swr_plan_t p, const MarchSys* d_sys, int nsys, int L,
+                                          int T) {
+    for (const auto& k : p->packings)
+        if (k.sys == d_sys && k.nsys == nsys && k.L == L && k.T == T) return &k;
+    const MarchSys* hs = nullptr;
+    for (const auto& e : p->host_sys) {
+        const MarchSys* b = e.first;
+        if (d_sys >= b && d_sys + nsys <= b + e.second.size()) {
+            hs = e.second.data() + (d_sys - b);
+            break;
+        }
+    }
+    if (!hs) return nullptr;
+    std::vector<int> need(nsys), order(nsys);
+    for (int q = 0; q < nsys; ++q) {
+        need[q] = chunks_for(p->n[hs[q].sub], L) + 1;
+        if (need[q] > T) return nullptr;
+        order[q] = q;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (hs[a].nt != hs[b].nt) return hs[a].nt > hs[b].nt;
+        return need[a] > need[b];
+    });
+    std::vector<int> start{0};
+    std::vector<int2> rag;
+    int used = 0, gmax = 0, cnt = 0;
+    for (int q : order) {
+        if (used + need[q] > T) {
+            start.push_back((int)rag.size());
+            gmax = std::max(gmax, cnt);
+            used = cnt = 0;
+        }
+        rag.push_back(make_int2(q, used));
+        used += need[q];
+        ++cnt;
+    }
+    gmax = std::max(gmax, cnt);
+    start.push_back((int)rag.size());
+    swr_plan_s::Packing k{d_sys, nsys, L, T, (int)start.size() - 1, gmax, nullptr, nullptr};
+    if (dalloc(&k.d_start, start.size()) || dalloc(&k.d_rag, rag.size())) {
+        cudaFree(k.d_start);
+        return nullptr;
+    }
+    if (cudaMemcpy(k.d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(k.d_rag, rag.data(), sizeof(int2) * rag.size(), cudaMemcpyHostToDevice)) {
+        cudaFree(k.d_start);
+        cudaFree(k.d_rag);
+        return nullptr;
+    }
+    p->packings.push_back(k);
+    return &p->packings.back();
 }
 
 // Launch one march with an explicit shape; nt_run < nt runs only the first steps
@@ -321,6 +399,16 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     a.C = cfg.C;
     a.G = cfg.G;
     a.T = cfg.T;
+    int ngroups = cfg.ngroups;
+    if (cfg.ragged) {
+        if (cfg.C != 1 || kind != MK_STATIC || fs.nsteps > 1) return -2;
+        const swr_plan_s::Packing* pk = ragged_packing(p, d_sys, nsys, cfg.L, cfg.T);
+        if (!pk) return -2;
+        a.rag_start = pk->d_start;
+        a.rag = pk->d_rag;
+        a.G = pk->gmax;
+        ngroups = pk->nctas;
+    }
     a.nsys = nsys;
     a.sys = d_sys;
     a.sub_n = p->d_n;
@@ -357,7 +445,7 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     if (kind == MK_NL)
         return swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
                                    p->d.nl_maxit, nullptr, cfg.ngroups, p->s);
-    return swr_launch_march(fs, a, cfg.ngroups, p->s, seg.mode);
+    return swr_launch_march(fs, a, ngroups, p->s, seg.mode);
 }
 
 inline int march_kind(swr_plan_t p, bool zero_potential) {
@@ -437,6 +525,20 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
                 cands.push_back(shape_of(c, tps, nsys));
             }
         }
+        // batched plans of uneven subdomains: ragged packings by size, for the CTA
+        // sizes that hold the largest system
+        if (p->batched && kind == MK_STATIC && tps <= TMAX) {
+            const int Ts[8] = {64, 96, 128, 160, 192, 256, 320, 384};
+            for (int T : Ts) {
+                if (T < tps || T > TMAX) continue;
+                MarchCfg r;
+                r.L = L;
+                r.C = 1;
+                r.T = T;
+                r.ragged = 1;
+                cands.push_back(r);
+            }
+        }
         // clusters: each CTA keeps at least one full warp of separators and
         // none is left without separators
         const int Cmin = std::max(2, (tps + TMAX - 1) / TMAX);
@@ -472,7 +574,8 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
         const MarchCfg& c = cands[k];
         bool dup = false;
         for (size_t q = 0; q < k && !dup; ++q)
-            dup = cands[q].L == c.L && cands[q].C == c.C && cands[q].G == c.G;
+            dup = cands[q].L == c.L && cands[q].C == c.C && cands[q].G == c.G &&
+                  cands[q].ragged == c.ragged && (!c.ragged || cands[q].T == c.T);
         if (dup) continue;
         if (launch_cfg(p, c, kind, zero_potential, d_sys, nsys, nullptr, gout, nullptr, nullptr,
                        p->d_u0, ntp) != 0) {
@@ -502,8 +605,8 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
         }
         if (const char* e = getenv("SWR_DEBUG"))
             if (atoi(e) >= 2)
-                fprintf(stderr, "swr autotune probe kind %d nsys %d: L %d C %d G %d T %d %.3f ms\n",
-                        kind, nsys, c.L, c.C, c.G, c.T, ms);
+                fprintf(stderr, "swr autotune probe kind %d nsys %d: L %d C %d G %d T %d%s %.3f ms\n",
+                        kind, nsys, c.L, c.C, c.G, c.T, c.ragged ? " ragged" : "", ms);
         if (best_ms < 0.f || ms < best_ms) {
             best_ms = ms;
             best = c;
@@ -512,9 +615,10 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (getenv("SWR_DEBUG"))
-        fprintf(stderr, "swr autotune kind %d nsys %d: L %d C %d G %d T %d (%.3f ms / %d steps)\n",
-                kind, nsys, best.L, best.C, best.G, best.T, best_ms, ntp);
-    p->tuned.push_back({kind, nsys, best.L, best.C, best.G, best.T, best.ngroups});
+        fprintf(stderr, "swr autotune kind %d nsys %d: L %d C %d G %d T %d%s (%.3f ms / %d steps)\n",
+                kind, nsys, best.L, best.C, best.G, best.T, best.ragged ? " ragged" : "", best_ms,
+                ntp);
+    p->tuned.push_back({kind, nsys, best.L, best.C, best.G, best.T, best.ngroups, best.ragged});
     if (kind == MK_TSTAT)   // probe-sized per-step sets of the losing chunk lengths
         for (int L : Ls)
             if (L != best.L) swr_factor_free(p->fsL[lidx(L)]);
@@ -601,12 +705,14 @@ std::vector<MarchSys> apply_systems(const swr_plan_s* p, int extra_flags) {
     return v;
 }
 
-swr_status upload_systems(MarchSys** dst, const std::vector<MarchSys>& v) {
+swr_status upload_systems(MarchSys** dst, const std::vector<MarchSys>& v,
+                          swr_plan_s* p = nullptr) {
     cudaFree(*dst);
     *dst = nullptr;
     swr_status st = dalloc(dst, v.size());
     if (st) return st;
     CK(cudaMemcpy(*dst, v.data(), sizeof(MarchSys) * v.size(), cudaMemcpyHostToDevice));
+    if (p) p->host_sys.push_back({*dst, v});
     return SWR_OK;
 }
 
@@ -919,6 +1025,10 @@ void swr_destroy(swr_plan_t p) {
     }
     cudaFree(p->d_beta); cudaFree(p->d_s02hist); cudaFree(p->d_gconv);
     cudaFree(p->d_inst); cudaFree(p->d_blk_inst); cudaFree(p->d_if_inst);
+    for (auto& k : p->packings) {
+        cudaFree(k.d_start);
+        cudaFree(k.d_rag);
+    }
     cudaFree(p->d_ckpt); cudaFree(p->d_slab); cudaFree(p->d_ya); cudaFree(p->d_yb);
     cudaFree(p->d_dy); cudaFree(p->d_gy); cudaFree(p->d_gint); cudaFree(p->d_gl);
     cudaFree(p->d_gr); cudaFree(p->d_part); cudaFree(p->d_sys_seg);
@@ -1120,7 +1230,7 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
         }
         for (const InstInfo& I : p->inst)
             for (int j = 0; j < I.N; ++j) p->work_R += (long long)p->n[I.sub0 + j] * I.nt;
-        st = upload_systems(&p->d_sys_build, vb);
+        st = upload_systems(&p->d_sys_build, vb, p);
     }
     if (!st && d->tc == SWR_TC_S02) {
         // beta_s = (-1)^s alpha_s, alpha_{2k} = alpha_{2k+1} = prod_{i<=k} (2i-1)/(2i):
@@ -1172,8 +1282,8 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
         }
         if (cnt > 0) p->causal_groups.push_back({k0, cnt});
     }
-    if (!st) st = upload_systems(&p->d_sys_R, apply_systems(p, 0));
-    if (!st) st = upload_systems(&p->d_sys_final, apply_systems(p, SYS_WRITE_UT | SYS_TRACE));
+    if (!st) st = upload_systems(&p->d_sys_R, apply_systems(p, 0), p);
+    if (!st) st = upload_systems(&p->d_sys_final, apply_systems(p, SYS_WRITE_UT | SYS_TRACE), p);
     if (!st) {
         for (auto& e : p->ev)
             if (cudaEventCreate(&e) != cudaSuccess) st = SWR_ERR_CUDA;

@@ -141,6 +141,11 @@ struct MarchArgs {
     double2* trace;       // [nsys][2][nt]
     long long fstride, sstride, pstride;   // per-step factor strides (0: constant matrix)
     int stage;            // staging of streamed factors in shared memory (0, 1, 2)
+    // Ragged packing (C == 1): CTA b holds the systems rag[rag_start[b] .. rag_start[b+1])
+    // as (system index, first thread) pairs, each with exactly P_j + 1 threads and no
+    // padding; NULL: G systems of P + 1 threads per CTA.
+    const int* rag_start;
+    const int2* rag;
     // A launch may march a segment of the time axis: its step t is step t0 + t of the
     // flux blocks, whose stride is gstride (the whole problem's nt).
     int t0;

@@ -500,7 +500,25 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     const int rank = (C > 1) ? (int)cl.block_rank() : 0;
     const int tid = threadIdx.x;
     int g, p, sidx;
-    if (C == 1) {
+    // ragged packing: this CTA's systems and the first thread of each
+    const bool ragged = (C == 1) && a.rag;
+    int re0 = 0, rne = 0, rbase = 0;
+    if (ragged) {
+        re0 = a.rag_start[blockIdx.x];
+        rne = a.rag_start[blockIdx.x + 1] - re0;
+        g = -1;
+        p = -1;
+        sidx = a.nsys;
+        for (int q = 0; q < rne; ++q) {
+            const int2 en = a.rag[re0 + q];
+            if (tid >= en.y) {
+                g = q;
+                sidx = en.x;
+                rbase = en.y;
+            }
+        }
+        if (g >= 0) p = tid - rbase;
+    } else if (C == 1) {
         g = tid / (P + 1);
         p = tid - g * (P + 1);
         sidx = blockIdx.x * G + g;
@@ -511,15 +529,19 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
         sidx = blockIdx.x / C;
         if (p > P) p = -1;
     }
-    const bool valid = (p >= 0) && (sidx < a.nsys);
+    bool valid = (p >= 0) && (sidx < a.nsys);
+    if (ragged && valid && p > a.sub_P[a.sys[sidx].sub]) valid = false;   // the next system's
+    const int rcbase = rbase - (g > 0 ? g : 0);   // ragged chunk slots: sum of P_j before
 
     auto SEP = [&](double2* arr, int ps) -> double2* {
+        if (ragged) return arr + rbase + ps;
         if (C == 1) return arr + g * (P + 1) + ps;
         const int home = ps / T;
         double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
         return base + (ps - home * T);
     };
     auto CHK = [&](double2* arr, int pc) -> double2* {
+        if (ragged) return arr + rcbase + pc;
         if (C == 1) return arr + g * P + pc;
         const int home = pc / T;
         double2* base = (home == rank) ? arr : cl.map_shared_rank(arr, home);
@@ -551,7 +573,9 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     // system), and a system past its own count neither reads fluxes, nor writes
     // outputs, nor advances its state.
     int ntc = 0;
-    if (C == 1) {
+    if (ragged) {
+        for (int q = 0; q < rne; ++q) ntc = max(ntc, a.sys[a.rag[re0 + q].x].nt);
+    } else if (C == 1) {
         for (int gg = 0; gg < G; ++gg) {
             const int si = blockIdx.x * G + gg;
             if (si < a.nsys) ntc = max(ntc, a.sys[si].nt);
@@ -709,8 +733,9 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             // history sums of the ends this CTA holds, one warp per end
             const int lane = tid & 31, w = tid >> 5, nw = T >> 5;
             if (C == 1) {
-                for (int e = w; e < 2 * G; e += nw) {
-                    const int gs = blockIdx.x * G + (e >> 1), side = e & 1;
+                for (int e = w; e < 2 * (ragged ? rne : G); e += nw) {
+                    const int gs = ragged ? a.rag[re0 + (e >> 1)].x : blockIdx.x * G + (e >> 1);
+                    const int side = e & 1;
                     if (gs < a.nsys && (a.sub_tc[a.sys[gs].sub] & (1 << side))) {
                         const double2 hsv = s02_history(
                             a.beta, a.hist + ((size_t)gs * 2 + side) * (nt + 1), t, lane);
@@ -784,7 +809,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                                                  : pcr[(size_t)(k * 2 + 1) * (P + 1) + p];
                 double2 dd = *SEP(src, p);
                 if (p - st >= 0) dd = cfma(alp, *SEP(src, p - st), dd);
-                if (p + st <= P) dd = cfma(gap, *SEP(src, p + st), dd);
+                if (p + st <= (ragged ? Pj : P)) dd = cfma(gap, *SEP(src, p + st), dd);
                 if (k == levels - 1) dd = cmul(dd, (stage >= 1) ? stg[2 * T + tid] : sbinv[p]);
                 *SEP(dst, p) = dd;
             }

@@ -44,12 +44,20 @@ def small_batch(count=5, tc=W.TC_ROBIN, **kw):
     return wls
 
 
-def batch_plan(wls, **kw):
+def batch_plan(wls, autotune=True, **kw):
+    """autotune=False: the modelled launch shapes, which pack the uneven systems
+    of a batch by size (ragged packing) instead of padding them."""
+    import os
     from paper_1503_02564_gb300 import swr
     insts = [dict(nx=w.nx, a0=w.a0, b0=w.b0, nt=w.nt, nsub=w.nsub, node_off=w.off) for w in wls]
     kw.setdefault("p", wls[0].sigma)
     kw.setdefault("tc", wls[0].tc)
-    plan = swr.BatchPlan(insts, dt=wls[0].dt, **kw)
+    if not autotune:
+        os.environ["SWR_AUTOTUNE"] = "0"
+    try:
+        plan = swr.BatchPlan(insts, dt=wls[0].dt, **kw)
+    finally:
+        os.environ.pop("SWR_AUTOTUNE", None)
     V = torch.tensor(np.concatenate([w.V for w in wls]), dtype=torch.float64, device="cuda")
     u0 = torch.tensor(np.concatenate([w.u0 for w in wls]), dtype=torch.complex128, device="cuda")
     plan.build_interface(V, u0)
@@ -64,10 +72,11 @@ def split(arr, lengths):
     return out
 
 
+@pytest.mark.parametrize("autotune", [True, False])
 @pytest.mark.parametrize("tc", [W.TC_ROBIN, W.TC_S02])
-def test_batch_build_matches_oracle_per_instance(tc):
+def test_batch_build_matches_oracle_per_instance(tc, autotune):
     wls = small_batch(tc=tc)
-    plan = batch_plan(wls)
+    plan = batch_plan(wls, autotune)
     d = torch.zeros(plan.n_interface, dtype=torch.complex128, device="cuda")
     cols = torch.zeros(plan.n_cols, dtype=torch.complex128, device="cuda")
     plan.get_interface(d, cols)
@@ -80,9 +89,10 @@ def test_batch_build_matches_oracle_per_instance(tc):
         assert rel(ci, O.build_columns(P)) < TOL_MARCH
 
 
-def test_batch_apply_R_matches_oracle_per_instance():
+@pytest.mark.parametrize("autotune", [True, False])
+def test_batch_apply_R_matches_oracle_per_instance(autotune):
     wls = small_batch(count=6)
-    plan = batch_plan(wls)
+    plan = batch_plan(wls, autotune)
     gs = [W.random_interface(w.nblk, w.nt, 50 + i) for i, w in enumerate(wls)]
     gi = torch.tensor(np.concatenate([g.ravel() for g in gs]), dtype=torch.complex128,
                       device="cuda")
@@ -93,11 +103,12 @@ def test_batch_apply_R_matches_oracle_per_instance():
         assert rel(o, O.apply_R(problem(w), g)) < TOL_MARCH
 
 
+@pytest.mark.parametrize("autotune", [True, False])
 @pytest.mark.parametrize("tc", [W.TC_ROBIN, W.TC_S02])
-def test_batch_solve_reproduces_each_monodomain_solution(tc):
+def test_batch_solve_reproduces_each_monodomain_solution(tc, autotune):
     from paper_1503_02564_gb300 import swr
     wls = small_batch(tc=tc)
-    plan = batch_plan(wls, precond=swr.SWR_PC_CAUSAL, restart=100, tol_abs=1e-12)
+    plan = batch_plan(wls, autotune, precond=swr.SWR_PC_CAUSAL, restart=100, tol_abs=1e-12)
     g = torch.zeros(plan.n_interface, dtype=torch.complex128, device="cuda")
     uT = torch.zeros(plan.nx, dtype=torch.complex128, device="cuda")
     info = plan.solve(g, False, uT)

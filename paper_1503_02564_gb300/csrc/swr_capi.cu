@@ -92,6 +92,19 @@ struct swr_plan_s {
         int2* d_rag;
     };
     std::vector<Packing> packings;
+    // The build after the first is captured into a CUDA graph (assembly,
+    // factorisations, marches, lag-0 setup) and later builds replay it
+    // (SWR_GRAPH=0 disables).  Launches inside the graph are timed by their own
+    // events, read back after the replay.
+    bool use_graph = true, capturing = false, graph_pending = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long graph_kernels = 0;
+    static const int NGPROF = 64;
+    int gcount = 0;
+    int gkind[NGPROF] = {};
+    long long gwork[NGPROF] = {};
+    cudaEvent_t gev[2 * NGPROF] = {};
     double2* d_u0 = nullptr;
     double* d_V = nullptr;
     double* d_Vbar = nullptr;      // potential of the preconditioner operator (MEAN_POTENTIAL)
@@ -166,27 +179,47 @@ swr_status dalloc(T** p, size_t count) {
 }
 
 // Resolve the pending launch timings (call only after the stream is synchronised).
+void prof_add(swr_plan_t p, int kind, long long work, float ms) {
+    if (kind == 0) {
+        p->stats.march_launches += 1;
+        p->stats.march_point_steps += work;
+        p->stats.march_ms += ms;
+    } else if (kind == 1) {
+        p->stats.toeplitz_launches += 1;
+        p->stats.toeplitz_ms += ms;
+    } else {
+        p->stats.precond_calls += 1;
+        p->stats.precond_ms += ms;
+    }
+}
+
 void prof_flush(swr_plan_t p) {
     for (int i = 0; i < p->pcount; ++i) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, p->pev[2 * i], p->pev[2 * i + 1]);
-        if (p->pkind[i] == 0) {
-            p->stats.march_launches += 1;
-            p->stats.march_point_steps += p->pwork[i];
-            p->stats.march_ms += ms;
-        } else if (p->pkind[i] == 1) {
-            p->stats.toeplitz_launches += 1;
-            p->stats.toeplitz_ms += ms;
-        } else {
-            p->stats.precond_calls += 1;
-            p->stats.precond_ms += ms;
-        }
+        prof_add(p, p->pkind[i], p->pwork[i], ms);
     }
     p->pcount = 0;
+    if (p->graph_pending) {   // launches of the last graph replay
+        for (int i = 0; i < p->gcount; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->gev[2 * i], p->gev[2 * i + 1]);
+            prof_add(p, p->gkind[i], p->gwork[i], ms);
+        }
+        p->graph_pending = false;
+    }
 }
 
 // Bracket a launch with events; when the ring is full, synchronise and resolve.
 int prof_begin(swr_plan_t p, int kind, long long work) {
+    if (p->capturing) {   // a launch inside the build graph: its own events
+        if (p->gcount == swr_plan_s::NGPROF) return -1;
+        const int i = p->gcount++;
+        p->gkind[i] = kind;
+        p->gwork[i] = work;
+        cudaEventRecord(p->gev[2 * i], p->s);
+        return 1000000 + i;
+    }
     if (p->pcount == swr_plan_s::NPROF) {
         cudaStreamSynchronize(p->s);
         prof_flush(p);
@@ -197,7 +230,13 @@ int prof_begin(swr_plan_t p, int kind, long long work) {
     cudaEventRecord(p->pev[2 * i], p->s);
     return i;
 }
-void prof_end(swr_plan_t p, int i) { cudaEventRecord(p->pev[2 * i + 1], p->s); }
+void prof_end(swr_plan_t p, int i) {
+    if (i < 0) return;
+    if (i >= 1000000)
+        cudaEventRecord(p->gev[2 * (i - 1000000) + 1], p->s);
+    else
+        cudaEventRecord(p->pev[2 * i + 1], p->s);
+}
 
 swr_status read_status(swr_plan_t p) {
     int st = 0;
@@ -1025,6 +1064,10 @@ void swr_destroy(swr_plan_t p) {
     }
     cudaFree(p->d_beta); cudaFree(p->d_s02hist); cudaFree(p->d_gconv);
     cudaFree(p->d_inst); cudaFree(p->d_blk_inst); cudaFree(p->d_if_inst);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto& e : p->gev)
+        if (e) cudaEventDestroy(e);
     for (auto& k : p->packings) {
         cudaFree(k.d_start);
         cudaFree(k.d_rag);
@@ -1306,58 +1349,15 @@ swr_status swr_plan_batch(const swr_desc* descs, int32_t count, swr_plan_t* out,
     return plan_create(descs, count, out, stream);
 }
 
-swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) {
-    if (!p || !V || !u0) return SWR_ERR_ARG;
+// Everything a build does after the inputs are in place and the first build's
+// tuning is done: assembly, factorisations, the d / first-column marches and
+// the preconditioner's operator.  Stream work only (no host synchronisation),
+// so that it can be captured into a CUDA graph.
+static swr_status build_body(swr_plan_t p, bool do_assemble) {
     cudaStream_t s = p->s;
     const size_t nb = (size_t)p->nb;
-    const size_t nV = (p->d.vkind == SWR_V_TIME) ? (size_t)(p->nt + 1) * p->nx : p->nx;
-    CK(cudaEventRecord(p->ev[0], s));
-    CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
-    CK(cudaMemcpyAsync(p->d_V, V, sizeof(double) * nV, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(p->d_u0, u0, sizeof(double2) * p->nx, cudaMemcpyDeviceToDevice, s));
-    swr_status st = assemble(p, p->d_V, p->d_dg, p->d_od);
-    if (st) return st;
-    if (p->d.vkind == SWR_V_TIME && p->tdep_pre < 0) {
-        // per-step factorisations need nt copies of the factors (about 110 bytes
-        // per node and step); take them while they use at most half the free memory
-        bool on = p->nt >= 2;
-        if (const char* e = getenv("SWR_TDEP_PRECOMP")) on = on && atoi(e) != 0;
-        // the refactorising march has no S_0^2 history terms
-        if (p->d.tc == SWR_TC_S02) on = p->nt >= 2;
-        if (on) {
-            size_t fr = 0, tot = 0;
-            CK(cudaMemGetInfo(&fr, &tot));
-            const size_t need =
-                (size_t)p->nt * swr_factor_step_bytes(p->N, 4, chunks_for(p->nmax, 4));
-            on = need <= fr / 2;
-        }
-        p->tdep_pre = on ? 1 : 0;
-    }
-    if (p->autotune && !p->built) {
-        // first build: measure the launch shapes of every march this plan makes
-        const int k = march_kind(p, false);
-        if ((st = tune_march(p, k, false, p->d_sys_R, p->N, p->d_iface, p->d_V, p->d_dg, p->d_od)))
-            return st;
-        if (k == MK_STATIC &&
-            (st = tune_march(p, k, false, p->d_sys_build, p->nsys_build, p->d_iface, p->d_V,
-                             p->d_dg, p->d_od)))
-            return st;
-        if (p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) {
-            const double* Vp = nullptr;
-            if (p->d.precond == SWR_PC_MEAN_POTENTIAL) {
-                LK(swr_launch_row_mean(p->d_V, p->d.vkind == SWR_V_TIME ? p->nt + 1 : 1, p->nx,
-                                       p->d_Vbar, s));
-                Vp = p->d_Vbar;
-            }
-            if ((st = assemble(p, Vp, p->d_dg0, p->d_od0))) return st;
-            if ((st = tune_march(p, MK_STATIC, true, p->d_sys_build + p->N, p->nsys_build - p->N,
-                                 p->d_iface, Vp, p->d_dg0, p->d_od0)))
-                return st;
-        }
-        // the probes wrote into d_iface; the build below starts the clock again
-        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)p->ncols), s));
-        CK(cudaEventRecord(p->ev[0], s));
-    }
+    swr_status st = SWR_OK;
+    if (do_assemble && (st = assemble(p, p->d_V, p->d_dg, p->d_od))) return st;
     if (p->d.vkind == SWR_V_TIME) {
         // chunk tables for the per-step refactorising march (the factors of the
         // t = 0 matrix computed alongside are not used)
@@ -1408,6 +1408,111 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
         if (st) return st;
         LK(p_lag0(p, p->d_iface0 + nb, p->d_lag0_0));
         p->have_L0 = true;
+    }
+    return SWR_OK;
+}
+
+swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) {
+    if (!p || !V || !u0) return SWR_ERR_ARG;
+    cudaStream_t s = p->s;
+    const size_t nb = (size_t)p->nb;
+    const size_t nV = (p->d.vkind == SWR_V_TIME) ? (size_t)(p->nt + 1) * p->nx : p->nx;
+    CK(cudaEventRecord(p->ev[0], s));
+    CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
+    CK(cudaMemcpyAsync(p->d_V, V, sizeof(double) * nV, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(p->d_u0, u0, sizeof(double2) * p->nx, cudaMemcpyDeviceToDevice, s));
+    swr_status st = SWR_OK;
+    if (const char* e = getenv("SWR_GRAPH")) p->use_graph = p->use_graph && atoi(e) != 0;
+    const bool direct = !p->built || !p->use_graph;
+    if (direct && (st = assemble(p, p->d_V, p->d_dg, p->d_od))) return st;
+    if (p->d.vkind == SWR_V_TIME && p->tdep_pre < 0) {
+        // per-step factorisations need nt copies of the factors (about 110 bytes
+        // per node and step); take them while they use at most half the free memory
+        bool on = p->nt >= 2;
+        if (const char* e = getenv("SWR_TDEP_PRECOMP")) on = on && atoi(e) != 0;
+        // the refactorising march has no S_0^2 history terms
+        if (p->d.tc == SWR_TC_S02) on = p->nt >= 2;
+        if (on) {
+            size_t fr = 0, tot = 0;
+            CK(cudaMemGetInfo(&fr, &tot));
+            const size_t need =
+                (size_t)p->nt * swr_factor_step_bytes(p->N, 4, chunks_for(p->nmax, 4));
+            on = need <= fr / 2;
+        }
+        p->tdep_pre = on ? 1 : 0;
+    }
+    if (p->autotune && !p->built) {
+        // first build: measure the launch shapes of every march this plan makes
+        const int k = march_kind(p, false);
+        if ((st = tune_march(p, k, false, p->d_sys_R, p->N, p->d_iface, p->d_V, p->d_dg, p->d_od)))
+            return st;
+        if (k == MK_STATIC &&
+            (st = tune_march(p, k, false, p->d_sys_build, p->nsys_build, p->d_iface, p->d_V,
+                             p->d_dg, p->d_od)))
+            return st;
+        if (p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) {
+            const double* Vp = nullptr;
+            if (p->d.precond == SWR_PC_MEAN_POTENTIAL) {
+                LK(swr_launch_row_mean(p->d_V, p->d.vkind == SWR_V_TIME ? p->nt + 1 : 1, p->nx,
+                                       p->d_Vbar, s));
+                Vp = p->d_Vbar;
+            }
+            if ((st = assemble(p, Vp, p->d_dg0, p->d_od0))) return st;
+            if ((st = tune_march(p, MK_STATIC, true, p->d_sys_build + p->N, p->nsys_build - p->N,
+                                 p->d_iface, Vp, p->d_dg0, p->d_od0)))
+                return st;
+        }
+        // the probes wrote into d_iface; the build below starts the clock again
+        CK(cudaMemsetAsync(p->d_iface, 0, sizeof(double2) * (nb + (size_t)p->ncols), s));
+        CK(cudaEventRecord(p->ev[0], s));
+    }
+    if (!p->built || !p->use_graph) {
+        st = build_body(p, false);
+        if (st) return st;
+    } else if (p->gexec) {
+        // replay the captured build
+        CK(cudaGraphLaunch(p->gexec, s));
+        g_launches += p->graph_kernels;
+        p->graph_pending = true;
+    } else {
+        // second build: capture it, then launch the graph (later builds replay it)
+        for (auto& e : p->gev)
+            if (!e && cudaEventCreate(&e) != cudaSuccess) p->use_graph = false;
+        bool ok = p->use_graph;
+        const long long k0 = g_launches.load();
+        if (ok) ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            p->capturing = true;
+            p->gcount = 0;
+            st = build_body(p, true);
+            p->capturing = false;
+            cudaGraph_t gr = nullptr;
+            const bool ended = cudaStreamEndCapture(s, &gr) == cudaSuccess && gr;
+            if (st || !ended) {
+                if (gr) cudaGraphDestroy(gr);
+                cudaGetLastError();
+                ok = false;
+            } else if (cudaGraphInstantiate(&p->gexec, gr, 0) != cudaSuccess) {
+                cudaGraphDestroy(gr);
+                cudaGetLastError();
+                p->gexec = nullptr;
+                ok = false;
+            } else {
+                p->graph = gr;
+                p->graph_kernels = g_launches.load() - k0;
+            }
+        }
+        g_launches -= g_launches.load() - k0;   // captured launches ran nowhere yet
+        if (ok) {
+            CK(cudaGraphLaunch(p->gexec, s));
+            g_launches += p->graph_kernels;
+            p->graph_pending = true;
+        } else {
+            // capture is not available here: build directly from now on
+            p->use_graph = false;
+            p->gcount = 0;
+            if ((st = build_body(p, true))) return st;
+        }
     }
     CK(cudaEventRecord(p->ev[1], s));
     st = read_status(p);

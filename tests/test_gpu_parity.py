@@ -253,3 +253,35 @@ def test_solve_with_null_outputs(vkind):
     plan.destroy()
     assert info["status"] in (swr.SWR_OK, swr.SWR_ERR_NOT_CONVERGED)
     assert np.isfinite(info["residual"])
+
+
+@pytest.mark.parametrize("case", ["config2_N16_small", "two_long"])
+def test_repeated_builds_replay_the_captured_build(case):
+    """The second build is captured into a CUDA graph and later builds replay it:
+    d and the first columns are bitwise those of a direct build, a replay reads
+    the new V, and every build counts the same kernel launches."""
+    from paper_1503_02564_gb300 import swr
+    wl = CASES[case]()
+    plan = gpu_plan(wl)                      # first build (direct, tuned)
+    d1, c1 = gpu_interface(plan)
+    V = torch.tensor(wl.V, dtype=torch.float64, device="cuda")
+    u0 = torch.tensor(wl.u0, dtype=torch.complex128, device="cuda")
+    counts = []
+    for _ in range(3):                       # capture, then two replays
+        k0 = swr.swr_kernel_launch_count()
+        plan.build_interface(V, u0)
+        counts.append(swr.swr_kernel_launch_count() - k0)
+        d, c = gpu_interface(plan)
+        assert np.array_equal(d, d1) and np.array_equal(c, c1)
+    assert counts[0] == counts[1] == counts[2] > 0
+    V2 = torch.tensor(wl.V * 0.5, dtype=torch.float64, device="cuda")
+    plan.build_interface(V2, u0)             # replay with a different potential
+    d3, _ = gpu_interface(plan)
+    plan.destroy()
+    wl2 = CASES[case]()
+    wl2.V = wl.V * 0.5
+    fresh = gpu_plan(wl2)
+    d4, _ = gpu_interface(fresh)
+    fresh.destroy()
+    assert np.array_equal(d3, d4)
+    assert rel(d3, O.build_d(problem(wl2))) < TOL_MARCH

@@ -757,3 +757,73 @@ def adjoint_gradient(P: Problem, u_target):
         grad += -2.0 * potential_form(mu, vs[t], h)
         lam = 2.0 * np.conj(I2) * _mass_apply(md, mo, mu) - lam
     return J, grad
+
+
+def _potential_form_matrix(v, h):
+    """The real-linear map w -> r(w), r_k = Re( sum_ab v_a (dM_W/dW_k)_ab w_b )
+    (the P1 rule of Eq. AvML, no conjugation), as a sparse real matrix acting
+    on [Re w; Im w].  Element [a, b]: dM/dW_a = h/12 (3,1;1,1), dM/dW_b =
+    h/12 (1,1;1,3)."""
+    import scipy.sparse as sp
+    n = len(v)
+    rows, cols, vals = [], [], []
+
+    def add(k, a, b, wgt):          # r_k += wgt Re(v_a w_b)
+        # Re(v_a w_b) = v_a.re w_b.re - v_a.im w_b.im
+        rows.extend([k, k]); cols.extend([b, n + b])
+        vals.extend([wgt * v[a].real, -wgt * v[a].imag])
+
+    c = h / 12.0
+    for e in range(n - 1):
+        a, b = e, e + 1
+        for (ia, ib, wa, wb) in ((a, a, 3.0, 1.0), (a, b, 1.0, 1.0), (b, a, 1.0, 1.0),
+                                 (b, b, 1.0, 3.0)):
+            add(a, ia, ib, c * wa)
+            add(b, ia, ib, c * wb)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, 2 * n))
+
+
+def adjoint_gradient_nl(P: Problem, u_target):
+    """dJ/dV0 for J = (u_N - u_target)^H M (u_N - u_target), u_N the monodomain
+    solution of the nonlinear scheme (Eq. CNS_NL / AvMNL with f(v) = c|v|^2 and
+    the static V0, Neumann ends), each step solved to convergence:
+        F(v_n) = A0 v_n + M_{c|v_n|^2} v_n - B u_{n-1} = 0,  u_n = 2 v_n - u_{n-1},
+    A0 = (2i/dt) M - S + M_V0, B = (2i/dt) M.  The linearisation in v is real-
+    linear, T(x) = At x + K(x) with At = A0 + M_{c|v|^2} and
+    K(x) = M_{2c Re(conj(v) x)} v, whose adjoint for Re(y^H x) is
+    T*(y) = conj(At) y + 2c v . Re(v^H (dM/dW_k) y).  With lam_N = 2 M (u_N - u_t):
+        T_n* mu_n = 2 lam_n  (solved exactly as a real 2n x 2n sparse system),
+        dJ/dV0 += -Re(mu_n^H (dM/dV0) v_n),
+        lam_{n-1} = B^H mu_n - lam_n.
+    Returns (J, dJ/dV0)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    if P.vkind != V_NONLINEAR:
+        raise NotImplementedError("adjoint_gradient_nl: nonlinear problems only")
+    n, h, dt, nt, coef = P.nx, P.h, P.dt, P.nt, P.nl_coef
+    m = mono_march(P, sel=np.arange(n))
+    vs = m.vsel
+    md, mo, sd, so, wd, wo = p1_matrices(n, h, P.V)
+    I2 = 2j / dt
+    dg0 = I2 * md - sd + wd
+    lo0 = I2 * mo - so + wo
+    e = m.uT - np.asarray(u_target, np.complex128)
+    Me = _mass_apply(md, mo, e)
+    J = float(np.real(np.vdot(e, Me)))
+    lam = 2.0 * Me
+    grad = np.zeros(n)
+    for t in range(nt, 0, -1):
+        v = vs[t]
+        _, _, _, _, wdv, wov = p1_matrices(n, h, coef * np.abs(v) ** 2)
+        Ct = sp.diags([np.conj(lo0 + wov), np.conj(dg0 + wdv), np.conj(lo0 + wov)], [-1, 0, 1],
+                      format="csr")                                  # conj(At)
+        Creal = sp.bmat([[Ct.real, -Ct.imag], [Ct.imag, Ct.real]], format="csr")
+        # 2c v . Re(v^H dM_k y) = 2c v . R(conj(v)) y
+        R = _potential_form_matrix(np.conj(v), h)
+        Kreal = sp.vstack([sp.diags(2 * coef * v.real) @ R, sp.diags(2 * coef * v.imag) @ R])
+        rhs = 2.0 * lam
+        x = spla.spsolve((Creal + Kreal).tocsc(), np.concatenate([rhs.real, rhs.imag]))
+        mu = x[:n] + 1j * x[n:]
+        grad += -potential_form(mu, v, h)
+        lam = np.conj(I2) * _mass_apply(md, mo, mu) - lam
+    return J, grad

@@ -441,3 +441,41 @@ def test_adjoint_gradient_vanishes_for_a_conserved_norm():
     assert np.max(np.abs(g0)) <= 1e-12 * np.max(np.abs(g))
     md, mo, *_ = O.p1_matrices(wl.nx, (wl.b0 - wl.a0) / (wl.nx - 1), None)
     assert abs(J0 - np.real(np.vdot(wl.u0, O._mass_apply(md, mo, wl.u0)))) <= 1e-13 * J0
+
+
+def _adjoint_nl_case():
+    wl = W.config5(nsub=3, nx=81, nt=20)
+    rng = np.random.default_rng(12)
+    tgt = wl.u0 * np.exp(0.3j) + 0.05 * (rng.standard_normal(wl.nx)
+                                         + 1j * rng.standard_normal(wl.nx))
+    return wl, tgt, rng
+
+
+def test_nonlinear_adjoint_gradient_matches_central_differences():
+    """The nonlinear scheme's discrete adjoint (real-linear linearisation of
+    |v|^2 v) against central differences of J from the forward march alone."""
+    wl, tgt, rng = _adjoint_nl_case()
+    J, g = O.adjoint_gradient_nl(problem(wl, nl_tol=1e-15, nl_maxit=200), tgt)
+
+    def J_of(V):
+        wv = W.config5(nsub=3, nx=81, nt=20)
+        wv.V = V
+        Pv = problem(wv, nl_tol=1e-15, nl_maxit=200)
+        return O.misfit(Pv, O.mono_march(Pv).uT, tgt)
+
+    assert abs(J - J_of(wl.V)) <= 1e-14 * J
+    for _ in range(6):
+        d = rng.standard_normal(wl.nx)
+        eps = 1e-4
+        fd = (J_of(wl.V + eps * d) - J_of(wl.V - eps * d)) / (2 * eps)
+        assert abs(fd - g @ d) <= 1e-7 * abs(fd)
+
+
+def test_nonlinear_adjoint_gradient_vanishes_for_a_conserved_norm():
+    """The nonlinear scheme conserves the M-norm at convergence of each step, so
+    J = ||u(T)||_M^2 does not depend on V0."""
+    wl, tgt, _ = _adjoint_nl_case()
+    P = problem(wl, nl_tol=1e-15, nl_maxit=200)
+    _, g0 = O.adjoint_gradient_nl(P, np.zeros(wl.nx))
+    _, g = O.adjoint_gradient_nl(P, tgt)
+    assert np.max(np.abs(g0)) <= 1e-12 * np.max(np.abs(g))

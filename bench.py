@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 NSUBS = (16, 64, 256, 500)
 FLOPS_PER_POINT_STEP = 36          # Thomas with stored factors, per node and time step
 FLOPS_PER_POINT_STEP_TDEP = 56     # plus the per-step factorisation (one complex reciprocal)
+# nonlinear march, per node and inner fixed-point iteration: the linear solve with stored
+# factors (36) plus the generalised-mass term b_f(zeta) (30) and the convergence test (10)
+FLOPS_PER_POINT_ITER_NL = 76
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flop x GHz (max SM clock)
 
 # DRAM bytes (read + write) per march launch, mean over the timed step's march launches, from
@@ -58,14 +61,16 @@ def parse():
     ap.add_argument("--nsub", default=",".join(str(n) for n in NSUBS))
     ap.add_argument("--precond", default="causal", choices=["causal", "none"])
     ap.add_argument("--workload", default="scaling",
-                    choices=["scaling", "timedep", "adjoint", "batch"],
+                    choices=["scaling", "timedep", "adjoint", "batch", "nonlinear"],
                     help="scaling: the N in {16,64,256,500} static-potential step (default); "
                          "timedep: the time-dependent potential case (60001 nodes, 1000 steps, "
                          "N = 64, GMRES preconditioned by the mean-potential operator); "
                          "adjoint: the scaling step plus the misfit gradient dJ/dV by "
                          "swr_adjoint (checkpoints every 50 steps); batch: 128 independent "
                          "instances (uneven partitions, 100-400 steps) in one batched plan, "
-                         "reported beside one plan per instance")
+                         "reported beside one plan per instance; nonlinear: |u|^2 + V0 "
+                         "(20001 nodes, 1000 steps, N = 32), preconditioned fixed point, then "
+                         "the misfit gradient dJ/dV0 by swr_adjoint (checkpoints every 50)")
     ap.add_argument("--tc", default="robin", choices=["robin", "s02"],
                     help="transmission condition of the scaling workload: Robin "
                          "p = sqrt(5) e^{-i pi/4} (default) or the order-2 potential "
@@ -101,6 +106,15 @@ def workload_name_timedep(nt=1000):
             "V=-x^2/4(1+0.5 sin 4t)-10exp(-(x-5 sin t)^2), seeded packet, Robin "
             "p=sqrt(5)e^{-i pi/4}, d = R0 + GMRES(60) on g - Rg + d preconditioned by the "
             "mean-potential interface operator to 1e-10 + final march")
+
+
+def workload_name_nonlinear(nt=1000):
+    return ("swr_nonlinear: x in (-20,20), 20001 P1 nodes, T=%g dt=5e-4 (%d steps), N=32, "
+            "V=|u|^2+V0, V0=-sum of 6 seeded Gaussian wells (depth 2-10), u0=sech(x)e^{2ix}, "
+            "Robin p=sqrt(5)e^{-i pi/4}, inner fixed point to 1e-13 per step, outer fixed point "
+            "preconditioned by the V0 interface operator to 1e-10 + final march; then "
+            "J = ||u(T) - u_target||_M^2 and dJ/dV0 by swr_adjoint (monodomain discrete "
+            "adjoint, checkpoints every 50 steps)" % (nt * 5e-4, nt))
 
 
 def march_point_steps(wl):
@@ -202,6 +216,25 @@ def cpu_oracle_adjoint_sample(wl_full, nt_sample):
                   tc=wl_full.tc, sigma=wl_full.sigma)
     t0 = time.perf_counter()
     O.adjoint_gradient(P, W.misfit_target(wl_full))
+    dt = time.perf_counter() - t0
+    ps = 2 * P.nx * nt_sample
+    return ps / dt, dt, ps
+
+
+def cpu_oracle_adjoint_nl_sample(wl_full, nt_sample):
+    """Time the oracle's discrete adjoint of the nonlinear monodomain scheme
+    (forward march with the inner fixed points, then the exact linearised
+    adjoint solves) on the workload's grid for nt_sample steps.  Returns
+    (point-steps/s, seconds, point-steps) with 2 x nodes x steps."""
+    import numpy as np
+    import oracle as O
+    from paper_1503_02564_gb300 import workloads as W
+    P = O.Problem(wl_full.a0, wl_full.b0, wl_full.nx, wl_full.dt, nt_sample,
+                  wl_full.off.astype(np.int64), wl_full.u0, wl_full.V, vkind=wl_full.vkind,
+                  tc=wl_full.tc, sigma=wl_full.sigma, nl_coef=wl_full.nl_coef, nl_tol=1e-13,
+                  nl_maxit=50)
+    t0 = time.perf_counter()
+    O.adjoint_gradient_nl(P, W.misfit_target(wl_full))
     dt = time.perf_counter() - t0
     ps = 2 * P.nx * nt_sample
     return ps / dt, dt, ps
@@ -397,13 +430,22 @@ def main():
     nsubs = tuple(int(x) for x in args.nsub.split(","))
     precond = swr.SWR_PC_CAUSAL if args.precond == "causal" else swr.SWR_PC_NONE
     timedep = args.workload == "timedep"
-    adjoint = args.workload == "adjoint"
+    nonlin = args.workload == "nonlinear"
+    adjoint = args.workload in ("adjoint", "nonlinear")
     if timedep:
         nsubs = (64,)
+    if nonlin:
+        nsubs = (32,)
 
     cases = []
     for N in nsubs:
-        if timedep:
+        if nonlin:
+            wl = W.config5(nsub=N, nt=args.nt) if args.nt > 0 else W.config5(nsub=N)
+            plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
+                            node_off=wl.off, p=wl.sigma, vkind=swr.SWR_V_NONLINEAR,
+                            solver=swr.SWR_SOLVER_FIXED_POINT, maxit=200, tol_abs=1e-10,
+                            precond=swr.SWR_PC_MEAN_POTENTIAL, nl_tol=1e-13, nl_maxit=50)
+        elif timedep:
             wl = W.config4(nsub=N, nt=args.nt) if args.nt > 0 else W.config4(nsub=N)
             plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
                             node_off=wl.off, p=wl.sigma, vkind=swr.SWR_V_TIME, restart=60,
@@ -494,12 +536,20 @@ def main():
     streamed = variant == swr.MARCH_TDEP_STREAMED
     fpp = FLOPS_PER_POINT_STEP_TDEP if variant == swr.MARCH_TDEP_REFACTOR else FLOPS_PER_POINT_STEP
     m_kernel = "k_march_tdep" if variant == swr.MARCH_TDEP_REFACTOR else "k_march_static"
+    nl_pit = sum(s["march_point_iterations"] for s in st)
+    nl_ms = sum(s["nl_march_ms"] for s in st)
+    nl_launch = sum(s["nl_march_launches"] for s in st)
     # algorithmic bytes per point-step: u read + written (32 B) plus, streamed,
     # the factors of that node and step
     bpp = 32.0
     if streamed:
         bpp += st[0]["march_factor_bytes_per_step"] / float(cases[0]["wl"].nx)
     achieved = fpp * m_ps / (m_ms * 1e-3) / 1e9 if m_ms > 0 else 0.0
+    if nonlin:
+        # the nonlinear marches (forward SWR sweeps and the adjoint's monodomain marches)
+        # dominate: their flops per node and inner iteration over their own device time
+        m_kernel = "k_march_nl"
+        achieved = FLOPS_PER_POINT_ITER_NL * nl_pit / (nl_ms * 1e-3) / 1e9 if nl_ms > 0 else 0.0
     # whole-step throughput from the library's own count of marched point-steps
     # (equal to the analytic count for the scaling step; GMRES-dependent otherwise)
     ps_step = m_ps / args.steps
@@ -548,7 +598,14 @@ def main():
                "ms_per_step": e_ms / args.steps}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and adjoint:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and nonlin:
+        v, s, ps = cpu_oracle_adjoint_nl_sample(cases[0]["wl"], 40)
+        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle discrete adjoint of the nonlinear monodomain scheme on the "
+                         f"{cases[0]['wl'].nx}-node grid, first 40 steps (forward march with "
+                         f"inner fixed points, exact linearised adjoint solves; {ps:.3g} "
+                         f"point-steps, {s:.1f} s)"}
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline and adjoint:
         v, s, ps = cpu_oracle_adjoint_sample(cases[0]["wl"], 100)
         cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle discrete adjoint of the monodomain scheme on the "
@@ -582,11 +639,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name_timedep(cases[0]["wl"].nt) if timedep else
+                       workload_name_nonlinear(cases[0]["wl"].nt) if nonlin else
                        (workload_name(nsubs, args.tc, cases[0]["wl"].nt)
                         + ("; then J = ||u(T) - u_target||_M^2 and dJ/dV(x) by swr_adjoint, "
                            "checkpoints every 50 steps" if adjoint else "")),
                        "point_steps_per_step": ps_step,
-                       "precond": "mean_potential" if timedep else args.precond, "l2": "flushed by a 256 MB write before each step",
+                       "precond": "mean_potential" if (timedep or nonlin) else args.precond,
+                       "l2": "flushed by a 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"kernel": m_kernel, "bound": "alu",
                          "achieved": achieved,
@@ -594,6 +653,9 @@ def main():
                          "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
                          "launches": m_launch, "avg_launch_ms": m_ms / max(m_launch, 1),
                          "flops_per_point_step": fpp,
+                         **({"flops_per_point_iteration": FLOPS_PER_POINT_ITER_NL,
+                             "point_iterations": nl_pit, "nl_launches": nl_launch,
+                             "nl_ms": nl_ms} if nonlin else {}),
                          "peak_basis": "nominal FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
                          "march_share_of_step": m_ms / t_ms if t_ms > 0 else None},
             "hbm_roof": {"point_steps_per_s": hbm * 1e9 / bpp,

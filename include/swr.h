@@ -135,6 +135,10 @@ typedef struct swr_stats {
                                  * (-1 before the first build)                          */
     int64_t march_factor_bytes_per_step; /* variant 3: factor bytes one R march reads
                                  * per time step (all subdomains); 0 otherwise           */
+    int64_t march_point_iterations; /* nonlinear marches (swr_adjoint's included): nodes
+                                 * x inner fixed-point iterations, summed over steps     */
+    int64_t nl_march_launches;  /* of the march launches above, the nonlinear ones      */
+    double nl_march_ms;         /* and their summed device time                         */
 } swr_stats;
 
 typedef struct swr_plan_s *swr_plan_t;
@@ -214,20 +218,29 @@ swr_status swr_misfit(swr_plan_t p, const double *uT, const double *u_target, do
                       double *J);
 
 /* Gradient dJ/dV(x) of a final-time objective J through the converged SWR
- * solution (no counterpart in the paper, which has no adjoint).  Needs a plan
- * with a static potential, Robin transmission and the GMRES solver, after a
- * successful swr_solve (SWR_ERR_STATE otherwise; SWR_ERR_UNSUPPORTED for other
- * plans).
+ * solution (no counterpart in the paper, which has no adjoint).  Needs, after a
+ * successful swr_solve (SWR_ERR_STATE otherwise), a single-instance plan with
+ *   SWR_V_STATIC, Robin transmission and the GMRES solver: dJ/dV;
+ *   SWR_V_NONLINEAR (any transmission condition and solver):     dJ/dV0;
+ * SWR_ERR_UNSUPPORTED for other plans.
  *   dJ_duT:     cplx[nx] (device), the M-weighted cotangent ubar of J at u(T):
  *               dJ = Re(ubar^H M du_T) (swr_misfit returns it for the misfit);
  *   dJ_dV:      double[nx] (device), overwritten with dJ/dV_k for the nodal V;
  *   ckpt_every: checkpoint interval K in time steps (<= 0: 50).
- * Method: the discrete adjoint of the Crank-Nicolson march, conjugated and
- * scaled, is the same march run from (dt/2i) conj(ubar); it is solved by SWR on
- * the plan's own interface problem (same Toeplitz columns and preconditioner),
- * then forward segments of K steps are recomputed from checkpoints of u and the
- * adjoint march over the mirrored steps accumulates
+ * Method (static V): the discrete adjoint of the Crank-Nicolson march,
+ * conjugated and scaled, is the same march run from (dt/2i) conj(ubar); it is
+ * solved by SWR on the plan's own interface problem (same Toeplitz columns and
+ * preconditioner), then forward segments of K steps are recomputed from
+ * checkpoints of u and the adjoint march over the mirrored steps accumulates
  *   dJ/dV_k = -2 Re sum_n (v^adj_{N-n+1})^T (dM_V/dV_k) v_n.
+ * Method (nonlinear, Eq. CNS_NL with f = c|v|^2): the discrete adjoint of the
+ * monodomain scheme, which the converged SWR solution reproduces.  Each adjoint
+ * step solves the step's derivative, A0 w + M_{c|v|^2} w + 2c conj(v) .
+ * Re(v^T (dM_W/dW_k) w) = (2i/dt) M z, by the march's inner fixed point about the
+ * recorded forward v_n (relative test nl_tol, cap nl_maxit: SWR_ERR_NOT_CONVERGED
+ * when reached), z <- 2 w - z, and dJ/dV0_k = -2 Re sum_n w_n^T (dM_V/dV_k) v_n.
+ * The whole grid is one system on a thread-block cluster (at most 16 CTAs of 256
+ * threads: nx <= 20476, or 36856 with 8-node chunks; SWR_ERR_UNSUPPORTED above).
  * Device memory: (ceil(nt/K) + K + 5) nx complex plus two interface vectors.
  * Synchronises the stream. */
 swr_status swr_adjoint(swr_plan_t p, const double *dJ_duT, double *dJ_dV,

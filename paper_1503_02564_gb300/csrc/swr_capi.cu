@@ -70,6 +70,11 @@ struct swr_plan_s {
     double2 *d_dy = nullptr, *d_gy = nullptr;
     double *d_gint = nullptr, *d_gl = nullptr, *d_gr = nullptr, *d_part = nullptr;
     MarchSys* d_sys_seg = nullptr;
+    // nonlinear adjoint: the whole grid as one system with Neumann ends
+    int* d_mono = nullptr;                          // {n, goff, loff, tc} of that system
+    double2 *d_mdg = nullptr, *d_mod = nullptr;     // its A - B for V0
+    FactorSet fsM;
+    MarchSys* d_sys_mono = nullptr;
     std::vector<int> off, n, goff, loff, tc;
     int *d_n = nullptr, *d_goff = nullptr, *d_loff = nullptr, *d_tc = nullptr;
     double2 *d_dg = nullptr, *d_od = nullptr;       // A - B for V (static) or V0
@@ -120,6 +125,7 @@ struct swr_plan_s {
     int nsys_build = 0;
     long long work_build = 0, work_build_imp = 0, work_R = 0;   // point-steps per launch
     int* d_status = nullptr;
+    unsigned long long* d_pit = nullptr;   // nonlinear marches: nodes x inner iterations
     double* d_scal = nullptr;      // [0] jump
     Workspace ws;
     int causal_sweeps = 0;
@@ -180,10 +186,14 @@ swr_status dalloc(T** p, size_t count) {
 
 // Resolve the pending launch timings (call only after the stream is synchronised).
 void prof_add(swr_plan_t p, int kind, long long work, float ms) {
-    if (kind == 0) {
+    if (kind == 0 || kind == 3) {   // 3: a nonlinear march, also counted on its own
         p->stats.march_launches += 1;
         p->stats.march_point_steps += work;
         p->stats.march_ms += ms;
+        if (kind == 3) {
+            p->stats.nl_march_launches += 1;
+            p->stats.nl_march_ms += ms;
+        }
     } else if (kind == 1) {
         p->stats.toeplitz_launches += 1;
         p->stats.toeplitz_ms += ms;
@@ -483,7 +493,7 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
                                      cmul_h(p->sigma0, p->inv_ik), cfg.ngroups, p->s);
     if (kind == MK_NL)
         return swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
-                                   p->d.nl_maxit, nullptr, cfg.ngroups, p->s);
+                                   p->d.nl_maxit, nullptr, cfg.ngroups, p->s, 0, p->d_pit);
     return swr_launch_march(fs, a, ngroups, p->s, seg.mode);
 }
 
@@ -499,7 +509,7 @@ swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, i
                      const double2* u0, long long work) {
     const int kind = march_kind(p, zero_potential);
     const MarchCfg cfg = march_config(p, nsys, kind);
-    const int pi = prof_begin(p, 0, work);
+    const int pi = prof_begin(p, kind == MK_NL ? 3 : 0, work);
     const int rc = launch_cfg(p, cfg, kind, zero_potential, d_sys, nsys, gin, gout, uT, trace, u0,
                               p->nt);
     prof_end(p, pi);
@@ -1033,6 +1043,102 @@ swr_status nl_fixed_point(swr_plan_t p, double2* g, bool g_init, swr_info* info)
 // ===========================================================================
 // Entry points
 // ===========================================================================
+// ---------------------------------------------------------------------------
+// Nonlinear adjoint (Eq. CNS_NL / AvMNL with f(v) = c|v|^2, static V0).  Every
+// step of the forward scheme solves F(v_n) = A0 v_n + M_{c|v_n|^2} v_n -
+// B u_{n-1} = 0, u_n = 2 v_n - u_{n-1} (A0 = (2i/dt) M - S + M_V0, B = (2i/dt)
+// M).  With dJ = Re(lambda_N^H du_N), lambda_N = M ubar, the adjoint of one step
+// solves T_n^* mu_n = 2 lambda_n, lambda_{n-1} = B^H mu_n - lambda_n, where T_n
+// is the real-linear derivative of F at v_n.  Conjugated and scaled,
+// z_n = B^{-1} conj(lambda_n) and omega_n = conj(mu_n) / 2:
+//     At omega + 2c conj(v_n) . Re(v_n^T (dM_W/dW_k) omega) = B z_n,
+//     z_{n-1} = 2 omega_n - z_n,        z_N = (dt / 2i) conj(ubar),
+// (At = A0 + M_{c|v_n|^2}), the same march as the forward one with the inner
+// fixed point linearised about the recorded v_n, and
+//     dJ/dV0_k = -2 Re sum_n omega_n^T (dM_V/dV_k) v_n.
+// The adjoint step is not a subdomain problem with a fixed interface operator
+// (its matrix changes with v_n), so the gradient is taken of the monodomain
+// scheme, which the converged SWR solution reproduces: the whole grid is one
+// system spread over a thread-block cluster.
+// ---------------------------------------------------------------------------
+
+// Tables and factorisation of the one-system grid (first call only).
+swr_status mono_setup(swr_plan_t p) {
+    if (p->d_mono) return SWR_OK;
+    const int nx = p->nx;
+    const int L = chunks_for(nx, 4) + 1 <= 16 * 256 ? 4 : 8;
+    if (chunks_for(nx, L) + 1 > 16 * 256) return SWR_ERR_UNSUPPORTED;
+    swr_status st = SWR_OK;
+    const int tab[4] = {nx, 0, 0, 0};
+    MarchSys sys{};
+    sys.sub = 0;
+    sys.flags = SYS_WRITE_UT;
+    sys.nt = p->nt;
+    sys.in_l = sys.in_r = sys.out_a = sys.out_b = -1;
+    if ((st = dalloc(&p->d_mono, 4)) || (st = dalloc(&p->d_mdg, nx)) ||
+        (st = dalloc(&p->d_mod, nx)) || (st = dalloc(&p->d_sys_mono, 1)))
+        return st;
+    CK(cudaMemcpyAsync(p->d_mono, tab, sizeof(tab), cudaMemcpyHostToDevice, p->s));
+    CK(cudaMemcpyAsync(p->d_sys_mono, &sys, sizeof(sys), cudaMemcpyHostToDevice, p->s));
+    swr_launch_assemble_static(p->d_V, 1, p->d_mono, p->d_mono + 1, p->d_mono + 2, p->d_mono + 3,
+                               nx, p->h, p->d.dt, p->sigma0, p->inv_ik, p->d_mdg, p->d_mod, p->s);
+    CK(cudaGetLastError());
+    if (swr_factor_alloc(p->fsM, 1, L, chunks_for(nx, L), p->s) != 0) return SWR_ERR_NOMEM;
+    if (swr_launch_factor(p->fsM, 1, p->d_mono, p->d_mono + 2, p->d_mdg, p->d_mod, p->d_status,
+                          p->s) != 0) {
+        cudaGetLastError();
+        return SWR_ERR_CUDA;
+    }
+    CK(cudaStreamSynchronize(p->s));
+    return SWR_OK;
+}
+
+// One march of the nonlinear scheme over the one-system grid for nrun steps:
+// mode 0 from u0 to uT, 1 also records v_n of every step into the slab, 2 the
+// adjoint march reading it (see above).
+swr_status mono_nl_march(swr_plan_t p, int mode, const double2* u0, double2* uT, int nrun) {
+    const FactorSet& fs = p->fsM;
+    const int tps = fs.P + 1;
+    MarchCfg c;
+    c.L = fs.L;
+    c.G = 1;
+    c.C = std::max((tps + 255) / 256, std::min(16, tps / 64));
+    c.C = std::max(1, std::min(c.C, std::max(1, p->nsm / 2)));
+    c = shape_of(c, tps, 1);
+    if (c.C > 16 || c.T > 256) return SWR_ERR_UNSUPPORTED;
+    MarchArgs a{};
+    a.nt = nrun;
+    a.C = c.C;
+    a.G = 1;
+    a.T = c.T;
+    a.nsys = 1;
+    a.sys = p->d_sys_mono;
+    a.sub_n = p->d_mono;
+    a.sub_goff = p->d_mono + 1;
+    a.sub_tc = p->d_mono + 3;
+    a.u0 = u0;
+    a.uT = uT;
+    a.two_sigma = p->two_sigma;
+    a.inv_ik = p->inv_ik;
+    a.status = p->d_status;
+    a.gstride = nrun;
+    a.nxrec = p->nx;
+    a.vrec = p->d_slab;
+    a.vfwd = p->d_slab;
+    a.gint = p->d_gint;
+    a.gl = p->d_gl;
+    a.gr = p->d_gr;
+    a.h12 = p->h / 12.0;
+    const double kappa = 2.0 / p->d.dt * (p->h / 6.0);
+    const int pi = prof_begin(p, 3, (long long)p->nx * nrun);
+    const int rc = swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
+                                       p->d.nl_maxit, nullptr, 1, p->s, mode, p->d_pit);
+    prof_end(p, pi);
+    if (rc == -2) return SWR_ERR_UNSUPPORTED;
+    if (rc) return launch_fail("nonlinear adjoint march", __LINE__);
+    return SWR_OK;
+}
+
 extern "C" {
 
 const char* swr_status_string(swr_status s) {
@@ -1075,11 +1181,13 @@ void swr_destroy(swr_plan_t p) {
     cudaFree(p->d_ckpt); cudaFree(p->d_slab); cudaFree(p->d_ya); cudaFree(p->d_yb);
     cudaFree(p->d_dy); cudaFree(p->d_gy); cudaFree(p->d_gint); cudaFree(p->d_gl);
     cudaFree(p->d_gr); cudaFree(p->d_part); cudaFree(p->d_sys_seg);
+    cudaFree(p->d_mono); cudaFree(p->d_mdg); cudaFree(p->d_mod); cudaFree(p->d_sys_mono);
+    swr_factor_free(p->fsM);
     cudaFree(p->d_u0); cudaFree(p->d_V); cudaFree(p->d_Vbar); cudaFree(p->d_iface); cudaFree(p->d_iface0);
     cudaFree(p->d_lag0); cudaFree(p->d_lag0_0); cudaFree(p->d_hist); cudaFree(p->d_gtmp);
     cudaFree(p->d_gtmp2); cudaFree(p->d_trace);
     cudaFree(p->d_sys_build); cudaFree(p->d_sys_R); cudaFree(p->d_sys_final);
-    cudaFree(p->d_status); cudaFree(p->d_scal);
+    cudaFree(p->d_status); cudaFree(p->d_scal); cudaFree(p->d_pit);
     Workspace& w = p->ws;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
     cudaFree(w.sn); cudaFree(w.sv); cudaFree(w.y); cudaFree(w.h); cudaFree(w.partial);
@@ -1244,6 +1352,7 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     if (!st) st = dalloc(&p->d_trace, (size_t)p->N * 2 * p->nt);
     if (!st) st = dalloc(&p->d_status, 1);
     if (!st) st = dalloc(&p->d_scal, 4);
+    if (!st) st = dalloc(&p->d_pit, 1);
     if (!st) {
         const size_t nV = (d->vkind == SWR_V_TIME) ? (size_t)(p->nt + 1) * p->nx : p->nx;
         st = dalloc(&p->d_V, nV);
@@ -1260,7 +1369,8 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
             cudaMemcpy(p->d_goff, p->goff.data(), sizeof(int) * p->N, cudaMemcpyHostToDevice) ||
             cudaMemcpy(p->d_loff, p->loff.data(), sizeof(int) * p->N, cudaMemcpyHostToDevice) ||
             cudaMemcpy(p->d_tc, p->tc.data(), sizeof(int) * p->N, cudaMemcpyHostToDevice) ||
-            cudaMemset(p->d_status, 0, sizeof(int)))
+            cudaMemset(p->d_status, 0, sizeof(int)) ||
+            cudaMemset(p->d_pit, 0, sizeof(unsigned long long)))
             st = SWR_ERR_CUDA;
     }
     if (!st) {
@@ -1628,8 +1738,15 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats* out, int32_t reset) {
             out->march_factor_bytes_per_step =
                 (int64_t)sizeof(double2) * (fs.fstride + fs.sstride + fs.pstride);
         }
+        unsigned long long pit = 0;
+        CK(cudaMemcpy(&pit, p->d_pit, sizeof(pit), cudaMemcpyDeviceToHost));
+        out->march_point_iterations = (int64_t)pit;
     }
-    if (reset) p->stats = swr_stats{};
+    if (reset) {
+        p->stats = swr_stats{};
+        CK(cudaMemsetAsync(p->d_pit, 0, sizeof(unsigned long long), p->s));
+        CK(cudaStreamSynchronize(p->s));
+    }
     return SWR_OK;
 }
 
@@ -1660,8 +1777,11 @@ swr_status swr_misfit(swr_plan_t p, const double* uT_, const double* target_, do
 swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t ckpt_every) {
     if (!p || !ubar_ || !dJdV_) return SWR_ERR_ARG;
     if (!p->built || !p->solved) return SWR_ERR_STATE;
-    if (p->d.vkind != SWR_V_STATIC || p->d.tc != SWR_TC_ROBIN ||
-        p->d.solver != SWR_SOLVER_GMRES || p->batched)
+    // the nonlinear gradient is taken of the monodomain scheme (any transmission
+    // condition and solver); the linear one runs the adjoint interface solve
+    const bool nl = (p->d.vkind == SWR_V_NONLINEAR);
+    if (p->batched || (!nl && (p->d.vkind != SWR_V_STATIC || p->d.tc != SWR_TC_ROBIN ||
+                               p->d.solver != SWR_SOLVER_GMRES)))
         return SWR_ERR_UNSUPPORTED;
     cudaStream_t s = p->s;
     const int nt = p->nt, nx = p->nx, N = p->N;
@@ -1687,6 +1807,31 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
             return st;
     }
     CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
+    if (nl) {
+        if ((st = mono_setup(p))) return st;
+        CK(cudaMemcpyAsync(p->d_ckpt, p->d_u0, sizeof(double2) * nx, cudaMemcpyDeviceToDevice, s));
+        for (int c = 1; c < C; ++c)
+            if ((st = mono_nl_march(p, 0, p->d_ckpt + (size_t)(c - 1) * nx,
+                                    p->d_ckpt + (size_t)c * nx, K)))
+                return st;
+        LK(swr_launch_adj_seed(reinterpret_cast<const double2*>(ubar_), 0.5 * p->d.dt, nx,
+                               p->d_ya, s));
+        CK(cudaMemsetAsync(p->d_gint, 0, sizeof(double) * nx, s));
+        CK(cudaMemsetAsync(p->d_gl, 0, sizeof(double) * nx, s));
+        CK(cudaMemsetAsync(p->d_gr, 0, sizeof(double) * nx, s));
+        double2* ycur = p->d_ya;
+        double2* ynext = p->d_yb;
+        for (int c = C - 1; c >= 0; --c) {
+            const int Kc = std::min(K, nt - c * K);
+            if ((st = mono_nl_march(p, 1, p->d_ckpt + (size_t)c * nx, nullptr, Kc)) ||
+                (st = mono_nl_march(p, 2, ycur, ynext, Kc)))
+                return st;
+            std::swap(ycur, ynext);
+        }
+        LK(swr_launch_grad_combine(p->d_gint, p->d_gl, p->d_gr, nx, dJdV_, s));
+        CK(cudaStreamSynchronize(s));
+        return read_status(p);
+    }
     // launch shape of the segment marches (chunk length <= 8 for the gradient sums)
     if (p->autotune) {
         if ((st = tune_march(p, MK_ADJ, false, p->d_sys_R, N, p->d_dy, p->d_V, p->d_dg, p->d_od)))

@@ -215,7 +215,8 @@ int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, c
 int swr_launch_march(const FactorSet& fs, MarchArgs a, int nsys_groups, cudaStream_t s,
                      int mode = 0);
 int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef, double tol,
-                        int maxit, int* iters, int ngroups, cudaStream_t s);
+                        int maxit, int* iters, int ngroups, cudaStream_t s, int mode = 0,
+                        unsigned long long* pit = nullptr);
 int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, long long vstride,
                           double h, double kappa, double2 sig_ik, int ngroups, cudaStream_t s);
 int swr_march_smem_bytes(int T, int G, int stage_slots = 0);

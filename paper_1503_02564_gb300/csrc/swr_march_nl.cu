@@ -22,6 +22,7 @@ struct NlArgs {
     double tol;       // inner tolerance
     int maxit;        // inner cap
     int* iters;       // optional: max inner iterations over steps, per system
+    unsigned long long* pit;   // optional: += nodes x inner iterations, summed over steps
 };
 
 // sum of the P1 element weights times zeta around a node: s such that
@@ -46,6 +47,19 @@ __device__ __forceinline__ double2 sub_bf(double2 rhs, double2 s, double cw) {
     return make_double2(fma(-cw, s.y, rhs.x), fma(cw, s.x, rhs.y));
 }
 __device__ __forceinline__ double nrm2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double rmul(double2 a, double2 b) { return a.x * b.x - a.y * b.y; }
+// Adjoint of the nonlinear step: the real-linear part of the linearised |v|^2 v,
+// 2c conj(v_k) Re(v^T (dM_W/dW_k) w) / (h/12), from the element(s) at node k
+// (values at k-1, k, k+1 of the forward v and of the iterate w).
+__device__ __forceinline__ double2 lin_term(bool hasl, bool hasr, double2 vl, double2 v0,
+                                            double2 vr, double2 wl, double2 w0, double2 wr,
+                                            double coef) {
+    double r = 0.0;
+    if (hasl) r += rmul(vl, wl) + rmul(vl, w0) + rmul(v0, wl) + 3.0 * rmul(v0, w0);
+    if (hasr) r += 3.0 * rmul(v0, w0) + rmul(v0, wr) + rmul(vr, w0) + rmul(vr, wr);
+    const double s = 2.0 * coef * r;
+    return make_double2(s * v0.x, -s * v0.y);
+}
 __device__ __forceinline__ unsigned long long dbits(double v) {
     return (unsigned long long)__double_as_longlong(v);
 }
@@ -55,7 +69,14 @@ int swr_march_nl_smem_bytes(int T, int G) {
            (int)sizeof(unsigned long long) * (4 * G + 4);
 }
 
-template <int L>
+// MODE 0: march; 1: also record v of every step (a.vrec); 2: adjoint of the
+// nonlinear step (see swr_adjoint): the inner fixed point solves
+//     (A - B) w + M_{c|v|^2} w + 2c conj(v) . Re(v^T dM w) = (2i/dt) M rho
+// with v the recorded forward midpoint value of the mirrored step (a.vfwd), and
+// the potential form of w against v is accumulated as in the constant-matrix march.
+// The adjoint is linear in its data, so its inner test is relative:
+// max |dw| <= tol max |w| (the march tests max |dzeta| <= tol max(1, max |zeta|)).
+template <int L, int MODE>
 __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
     const MarchArgs& a = na.m;
     extern __shared__ double2 sm[];
@@ -75,6 +96,12 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
     unsigned long long* red = reinterpret_cast<unsigned long long*>(ylst + T);
     unsigned long long* cnt = red + 4 * G;
     double2* hsum = reinterpret_cast<double2*>(cnt + 4);   // [2G] S_0^2 history sums
+    // MODE 2: forward values of this step: chunk nodes [L][T] (element-major),
+    // separators (SEP layout) and the chunk ends (CHK layout) for the neighbours
+    double2* vfc = hsum + 2 * G;
+    double2* vfsep = vfc + L * T;
+    double2* vffst = vfsep + (T + G);
+    double2* vflst = vffst + T;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (C > 1) ? (int)cl.block_rank() : 0;
     const int tid = threadIdx.x;
@@ -170,7 +197,11 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
 
     double2 lin = zero, rin = zero, fs = zero;
     int itmax = 0;
+    unsigned long long itsum = 0;   // inner iterations summed over the steps
     bool nl_fail = false;
+    double ga_int[MODE == 2 ? L : 1], ga_l = 0.0, ga_r = 0.0;   // MODE 2 sums
+#pragma unroll
+    for (int i = 0; i < (MODE == 2 ? L : 1); ++i) ga_int[i] = 0.0;
     for (int t = 1; t <= nt; ++t) {
         // ---- step-constant right-hand side (2i/dt) M u_{n-1} - fluxes, scaled ----
         if (valid && Lp > 0) {
@@ -218,6 +249,17 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                     if (lane == 0) hsum[1] = hsv;
                 }
             }
+        }
+        if constexpr (MODE == 2) {   // forward values of the mirrored step
+            const double2* vrow = a.vfwd + (size_t)(nt - t) * a.nxrec + goff + sp;
+            if (valid && Lp > 0) {
+#pragma unroll
+                for (int i = 0; i < L; ++i)
+                    if (i < Lp) vfc[i * T + tid] = vrow[1 + i];
+                *CHK(vffst, p) = vrow[1];
+                *CHK(vflst, p) = vrow[Lp];
+            }
+            if (realsep) *SEP(vfsep, p) = vrow[0];
         }
         // reduction slot 0 serves the first inner iteration of this step
         for (int q = tid; q < 2 * G; q += blockDim.x) red[q] = 0ull;
@@ -274,6 +316,13 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 const double2 zL = *SEP(zsep, p), zR = *SEP(zsep, p + 1);
                 double Wprev = coef * nrm2(zL);
                 double W0 = coef * nrm2(z[0]);
+                double2 vL = zero, vR = zero;
+                if constexpr (MODE == 2) {   // W from the forward values
+                    vL = *SEP(vfsep, p);
+                    vR = *SEP(vfsep, p + 1);
+                    Wprev = coef * nrm2(vL);
+                    W0 = coef * nrm2(vfc[tid]);
+                }
                 double2 zprev = zero, cprev = zero;
 #pragma unroll
                 for (int i = 0; i < L; ++i) {
@@ -284,8 +333,21 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                             zr_ = (i == Lp - 1) ? zR : z[i + 1];
                         else
                             zr_ = zR;
-                        const double Wr = coef * nrm2(zr_);
-                        const double2 rhs = sub_bf(f[i], bf_sum(true, true, zl_, z[i], zr_, Wprev, W0, Wr), cw);
+                        double Wr;
+                        double2 sx;
+                        if constexpr (MODE == 2) {
+                            const double2 vl = (i == 0) ? vL : vfc[(i > 0 ? i - 1 : 0) * T + tid];
+                            const double2 v0 = vfc[i * T + tid];
+                            const double2 vr = (i + 1 < L && i != Lp - 1)
+                                                   ? vfc[(i + 1 < L ? i + 1 : 0) * T + tid] : vR;
+                            Wr = coef * nrm2(vr);
+                            sx = cadd(bf_sum(true, true, zl_, z[i], zr_, Wprev, W0, Wr),
+                                      lin_term(true, true, vl, v0, vr, zl_, z[i], zr_, coef));
+                        } else {
+                            Wr = coef * nrm2(zr_);
+                            sx = bf_sum(true, true, zl_, z[i], zr_, Wprev, W0, Wr);
+                        }
+                        const double2 rhs = sub_bf(f[i], sx, cw);
                         const double2 zz = (i == 0) ? rhs : cfms(cprev, zprev, rhs);
                         y[i] = zz;
                         zprev = zz;
@@ -317,8 +379,18 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                     const double2 zs = *SEP(zsep, p);
                     const double2 zl_ = hasl ? *CHK(zlst, p - 1) : zero;
                     const double2 zr_ = hasr ? *CHK(zfst, p) : zero;
-                    const double2 sb = bf_sum(hasl, hasr, zl_, zs, zr_, coef * nrm2(zl_),
-                                              coef * nrm2(zs), coef * nrm2(zr_));
+                    double2 sb;
+                    if constexpr (MODE == 2) {
+                        const double2 vs = *SEP(vfsep, p);
+                        const double2 vl = hasl ? *CHK(vflst, p - 1) : zero;
+                        const double2 vr = hasr ? *CHK(vffst, p) : zero;
+                        sb = cadd(bf_sum(hasl, hasr, zl_, zs, zr_, coef * nrm2(vl), coef * nrm2(vs),
+                                         coef * nrm2(vr)),
+                                  lin_term(hasl, hasr, vl, vs, vr, zl_, zs, zr_, coef));
+                    } else {
+                        sb = bf_sum(hasl, hasr, zl_, zs, zr_, coef * nrm2(zl_), coef * nrm2(zs),
+                                    coef * nrm2(zr_));
+                    }
                     d = sub_bf(fs, sb, cw);
                     if (hasl) d = cfms(sE_l[p], *CHK(ylst, p - 1), d);
                     if (hasr) d = cfms(sE_r[p], *CHK(yfst, p), d);
@@ -377,7 +449,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
             if (C > 1) {
                 const double dm = __longlong_as_double((long long)RED_ALL(slot, 0));
                 const double zm = __longlong_as_double((long long)RED_ALL(slot, 1));
-                conv_all = (dm <= na.tol * na.tol * fmax(1.0, zm));
+                conv_all = (dm <= na.tol * na.tol * (MODE == 2 ? zm : fmax(1.0, zm)));
             }
             if (active) {
                 const double dm = __longlong_as_double((long long)RED_ALL(slot, 0));
@@ -386,7 +458,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
                 for (int i = 0; i < L; ++i)
                     if (i < Lp) z[i] = y[i];
                 if (realsep) *SEP(zsep, p) = zsn;
-                if (dm <= na.tol * na.tol * fmax(1.0, zm)) {
+                if (dm <= na.tol * na.tol * (MODE == 2 ? zm : fmax(1.0, zm))) {
                     active = false;
                     used = it + 1;
                 } else if (C == 1 && p == 0) {
@@ -407,6 +479,43 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
         }
         if (active) nl_fail = true;      // cap reached without convergence
         if (valid && used > itmax) itmax = used;
+        itsum += (unsigned long long)used;
+        if constexpr (MODE == 1) {   // record v_n (an interface node by its left subdomain)
+            double2* row = a.vrec + (size_t)(t - 1) * a.nxrec + goff + sp;
+            if (valid && Lp > 0) {
+#pragma unroll
+                for (int i = 0; i < L; ++i)
+                    if (i < Lp) row[1 + i] = z[i];
+            }
+            if (realsep && !(p == 0 && (tcf & 1))) row[0] = *SEP(zsep, p);
+        }
+        if constexpr (MODE == 2) {
+            // potential form of w (this march) against the forward v, elements from
+            // separator p to separator p+1 (as in the constant-matrix march)
+            if (valid && p < Pj) {
+                const double2 xL = *SEP(zsep, p), xR = *SEP(zsep, p + 1);
+                const double2 yL = *SEP(vfsep, p), yR = *SEP(vfsep, p + 1);
+                const double h12 = a.h12;
+#pragma unroll
+                for (int e = 0; e <= L; ++e) {
+                    if (e <= Lp) {
+                        const int im = e > 0 ? e - 1 : 0, ic = e < L ? e : 0;
+                        const double2 xa = (e == 0) ? xL : z[im];
+                        const double2 ya = (e == 0) ? yL : vfc[im * T + tid];
+                        const double2 xb = (e < L) ? csel(e < Lp, z[ic], xR) : xR;
+                        const double2 yb = (e < L && e < Lp) ? vfc[ic * T + tid] : yR;
+                        const double sa = rmul(xa, ya), sb = rmul(xb, yb);
+                        const double c = rmul(xa, yb) + rmul(xb, ya);
+                        const double toa = h12 * (3.0 * sa + c + sb);
+                        const double tob = h12 * (sa + c + 3.0 * sb);
+                        if (e == 0) ga_l += toa;
+                        else ga_int[im] += toa;
+                        if (e < Lp) ga_int[ic] += tob;
+                        else ga_r += tob;
+                    }
+                }
+            }
+        }
         // ---- v_n = zeta: CN update and fluxes ---------------------------------
 #pragma unroll
         for (int i = 0; i < L; ++i)
@@ -437,6 +546,15 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
         }
         SYNC();
     }
+    if constexpr (MODE == 2) {   // add this segment's sums (one writer per entry)
+        if (valid && p < Pj) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.gint[goff + sp + 1 + i] += ga_int[i];
+            a.gl[goff + sp] += ga_l;
+            a.gr[goff + sp + Lp + 1] += ga_r;
+        }
+    }
     bool bad = false;
     if (valid) {
 #pragma unroll
@@ -453,6 +571,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
             if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || !(tcf & 1))) a.uT[goff + sp] = us;
         }
         if (p == 0 && na.iters) atomicMax(na.iters + sidx, itmax);
+        if (p == 0 && na.pit) atomicAdd(na.pit, itsum * (unsigned long long)a.sub_n[j]);
     }
     if (bad) atomicOr(a.status, ST_NONFINITE);
     if (nl_fail) atomicOr(a.status, ST_NL_NOCONV);
@@ -460,9 +579,13 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
 }
 
 template <int L>
-static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s) {
-    const int smem = swr_march_nl_smem_bytes(na.m.T, na.m.G);
-    auto kern = k_march_nl<L>;
+static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s, int mode) {
+    int smem = swr_march_nl_smem_bytes(na.m.T, na.m.G);
+    if (mode == 2)   // forward values of the step: [L][T], separators, chunk ends
+        smem += (int)sizeof(double2) * (L * na.m.T + (na.m.T + na.m.G) + 2 * na.m.T);
+    void (*kern)(const NlArgs) = k_march_nl<L, 0>;
+    if (mode == 1) kern = k_march_nl<L, 1>;
+    if (mode == 2) kern = k_march_nl<L, 2>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return -1;
@@ -486,7 +609,9 @@ static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s) {
 }
 
 int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef, double tol,
-                        int maxit, int* iters, int ngroups, cudaStream_t s) {
+                        int maxit, int* iters, int ngroups, cudaStream_t s, int mode,
+                        unsigned long long* pit) {
+    if (mode != 0 && a.s02) return -2;   // the adjoint modes: Robin or Neumann ends
     a.P = fs.P;
     a.levels = fs.levels;
     a.sub_P = fs.sub_P;
@@ -495,10 +620,10 @@ int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef
     a.fac = fs.fac;
     a.sep = fs.sep;
     a.pcr = fs.pcr;
-    NlArgs na{a, cw, coef, tol, maxit, iters};
+    NlArgs na{a, cw, coef, tol, maxit, iters, pit};
     switch (fs.L) {
-        case 4: return launch_nl_t<4>(na, ngroups, s);
-        case 8: return launch_nl_t<8>(na, ngroups, s);
+        case 4: return launch_nl_t<4>(na, ngroups, s, mode);
+        case 8: return launch_nl_t<8>(na, ngroups, s, mode);
         default: return -2;
     }
 }

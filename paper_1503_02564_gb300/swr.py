@@ -60,6 +60,8 @@ class swr_stats(ctypes.Structure):
         ("toeplitz_ms", ctypes.c_double), ("precond_calls", ctypes.c_int64),
         ("precond_ms", ctypes.c_double), ("march_variant", ctypes.c_int32),
         ("march_factor_bytes_per_step", ctypes.c_int64),
+        ("march_point_iterations", ctypes.c_int64),
+        ("nl_march_launches", ctypes.c_int64), ("nl_march_ms", ctypes.c_double),
     ]
 
     def as_dict(self):

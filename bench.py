@@ -626,6 +626,9 @@ def main():
         per_n = []
         for c, info in zip(cases, infos_last):
             per_n.append({"N": c["N"], "iterations": info["iterations"],
+                          "causal_sweeps": st[len(per_n)]["causal_sweeps"],
+                          "superposed": st[len(per_n)]["superposed"],
+                          "toeplitz_fft_length": st[len(per_n)]["toeplitz_fft_length"],
                           "residual": info["residual"], "build_ms": info["t_build_ms"],
                           "solve_ms": info["t_solve_ms"], "final_ms": info["t_final_ms"],
                           "interface_jump": info["interface_jump"]})

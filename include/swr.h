@@ -102,7 +102,9 @@ typedef struct swr_desc {
     int32_t pc_sweeps;          /* block-Jacobi sweeps resolving the same-step coupling  */
                                 /* of neighbouring interfaces in the causal substitution */
                                 /* (CAUSAL / ZERO_POTENTIAL preconditioners), 0..16;    */
-                                /* < 0: chosen by the library                           */
+                                /* < 0: chosen by the library (CAUSAL, static V: 1 when */
+                                /* the lag-0 corner entries X^{j,2}[0], X^{j,3}[0] of   */
+                                /* the first build exceed 1e-5 in modulus, else 0)      */
 } swr_desc;
 
 typedef struct swr_info {
@@ -139,6 +141,13 @@ typedef struct swr_stats {
                                  * x inner fixed-point iterations, summed over steps     */
     int64_t nl_march_launches;  /* of the march launches above, the nonlinear ones      */
     double nl_march_ms;         /* and their summed device time                         */
+    int32_t superposed;         /* 1: swr_solve forms u(T) by superposition of the build
+                                 * marches' recorded states (static V, Robin, enough free
+                                 * memory, SWR_SUPERPOSE not 0) instead of a final march  */
+    int32_t toeplitz_fft_length; /* transform length M of the FFT Toeplitz applies (the
+                                 * power of two >= 2 nt - 1, for 16 <= nt and M <= 4096,
+                                 * SWR_TOEPLITZ_FFT not 0); 0: direct causal sums        */
+    int32_t causal_sweeps;      /* block-Jacobi sweeps of the causal substitution in use */
 } swr_stats;
 
 typedef struct swr_plan_s *swr_plan_t;
@@ -177,8 +186,15 @@ swr_status swr_plan_batch(const swr_desc *descs, int32_t count, swr_plan_t *out,
  * Errors: SWR_ERR_SINGULAR (a pivot of A - B vanished), SWR_ERR_ARG, SWR_ERR_CUDA. */
 swr_status swr_build_interface(swr_plan_t p, const double *V, const double *u0);
 
-/* Solve the interface problem with the plan's solver, then run the final march
- * (last step of Algorithms 1-3).
+/* Solve the interface problem with the plan's solver, then form u(T) (last step
+ * of Algorithms 1-3).  By default a final march of every subdomain with the
+ * converged fluxes.  Static V with Robin transmission (p != 0): the march is
+ * linear and time invariant, so swr_build_interface records the full states of
+ * its impulse-driven marches (2 nt n_j complex per subdomain, when that takes at
+ * most a quarter of the free device memory and SWR_SUPERPOSE is not 0) and u(T)
+ * is their superposition weighted by the converged fluxes plus the zero-flux
+ * march's final state; info->interface_jump then comes from the final residual
+ * (v_j(b_j) - v_{j+1}(a_{j+1}) = ((R g - g)[l_{j+1}] - (R g - g)[r_j]) / 2p).
  * g:    cplx[(2N-2) * nt]; on entry the initial guess g0 (ignored if
  *       g_is_initial == 0, then g0 = 0), on exit the converged interface vector.
  *       May be NULL (then g0 = 0 and the result is not returned).

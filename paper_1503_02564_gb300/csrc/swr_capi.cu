@@ -125,10 +125,22 @@ struct swr_plan_s {
     int nsys_build = 0;
     long long work_build = 0, work_build_imp = 0, work_R = 0;   // point-steps per launch
     int* d_status = nullptr;
+    // Toeplitz applies through the FFT (SWR_TOEPLITZ_FFT=0: direct causal sums):
+    // transform length fftM (0: direct), twiddles, spectra of the two column sets
+    int fftM = 0;
+    double2* d_W = nullptr;
+    double2 *d_spec = nullptr, *d_spec0 = nullptr;
+    // static V, Robin: u(T) by superposition of the build marches' recorded states
+    // instead of a final march (SWR_SUPERPOSE=0, or too little free memory: final march)
+    bool superpose = false;
+    double2* d_urec = nullptr;
+    std::vector<long long> rec_base;   // per subdomain: Phi_l (nt x n_j), Phi_r, U_d (n_j)
+    long long* d_rec_base = nullptr;
     unsigned long long* d_pit = nullptr;   // nonlinear marches: nodes x inner iterations
     double* d_scal = nullptr;      // [0] jump
     Workspace ws;
     int causal_sweeps = 0;
+    bool auto_sweeps = false;      // pc_sweeps < 0: chosen from the lag-0 corners at the first build
     bool built = false;
     bool have_L0 = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -468,6 +480,7 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     a.gout = gout;
     a.uT = uT;
     a.trace = trace;
+    a.urec = (!zero_potential && p->superpose) ? p->d_urec : nullptr;
     a.two_sigma = p->two_sigma;
     a.inv_ik = p->inv_ik;
     a.status = p->d_status;
@@ -705,10 +718,16 @@ swr_status assemble(swr_plan_t p, const double* V, double2* dg, double2* od) {
 std::vector<MarchSys> build_systems(const swr_plan_s* p, bool with_d) {
     std::vector<MarchSys> v;
     const long long nb = p->nb;
+    // superposed u(T): every impulse march records its states, the d march its final state
+    const bool rec = p->superpose;
+    auto slot = [&](int sub, int which, int nt) -> long long {   // 0: Phi_l, 1: Phi_r, 2: U_d
+        return rec ? p->rec_base[sub] + (long long)which * nt * p->n[sub] : 0;
+    };
     if (with_d) {   // d = R 0: one march per subdomain, all instances first
         for (const InstInfo& I : p->inst)
             for (int j = 0; j < I.N; ++j) {
-                MarchSys s{I.sub0 + j, 0, I.nt, -1, -1, -1, -1};
+                MarchSys s{I.sub0 + j, rec ? SYS_REC_LAST : 0, I.nt, -1, -1, -1, -1,
+                           slot(I.sub0 + j, 2, I.nt)};
                 if (j > 0) s.out_a = (int)(I.foff + (long long)(2 * (j - 1)) * I.nt);      // r_{j-1}
                 if (j < I.N - 1) s.out_b = (int)(I.foff + (long long)(2 * (j + 1) - 1) * I.nt);  // l_{j+1}
                 v.push_back(s);
@@ -717,8 +736,8 @@ std::vector<MarchSys> build_systems(const swr_plan_s* p, bool with_d) {
     for (const InstInfo& I : p->inst) {   // l impulse: X^{j,1} (r_{j-1}), X^{j,3} (l_{j+1})
         const long long c = nb + I.coff;
         for (int j = 1; j < I.N; ++j) {
-            MarchSys s{I.sub0 + j, SYS_ZERO_U0 | SYS_IMP_L, I.nt, -1, -1,
-                       (int)(c + (long long)(4 * j + 0) * I.nt), -1};
+            MarchSys s{I.sub0 + j, SYS_ZERO_U0 | SYS_IMP_L | (rec ? SYS_REC_U : 0), I.nt, -1, -1,
+                       (int)(c + (long long)(4 * j + 0) * I.nt), -1, slot(I.sub0 + j, 0, I.nt)};
             if (j < I.N - 1) s.out_b = (int)(c + (long long)(4 * j + 2) * I.nt);
             v.push_back(s);
         }
@@ -726,8 +745,8 @@ std::vector<MarchSys> build_systems(const swr_plan_s* p, bool with_d) {
     for (const InstInfo& I : p->inst) {   // r impulse: X^{j,2} (r_{j-1}), X^{j,4} (l_{j+1})
         const long long c = nb + I.coff;
         for (int j = 0; j < I.N - 1; ++j) {
-            MarchSys s{I.sub0 + j, SYS_ZERO_U0 | SYS_IMP_R, I.nt, -1, -1, -1,
-                       (int)(c + (long long)(4 * j + 3) * I.nt)};
+            MarchSys s{I.sub0 + j, SYS_ZERO_U0 | SYS_IMP_R | (rec ? SYS_REC_U : 0), I.nt, -1, -1,
+                       -1, (int)(c + (long long)(4 * j + 3) * I.nt), slot(I.sub0 + j, 1, I.nt)};
             if (j > 0) s.out_a = (int)(c + (long long)(4 * j + 1) * I.nt);
             v.push_back(s);
         }
@@ -796,6 +815,14 @@ swr_status ensure_workspace(swr_plan_t p) {
 // Interface algebra over all instances of the plan (tables only for a batch).
 int p_toeplitz(swr_plan_t p, const double2* cols, const double2* x, const double2* add,
                double2* y, int mode) {
+    if (p->fftM) {
+        const double2* spec = (cols == p->d_iface + p->nb) ? p->d_spec
+                            : (cols == p->d_iface0 + p->nb) ? p->d_spec0 : nullptr;
+        if (spec)
+            return swr_launch_toeplitz_fft(p->N, p->nt, spec, x, add, y, mode, p->fftM, p->d_W,
+                                           p->s, p->batched ? p->d_inst : nullptr,
+                                           p->d_blk_inst, p->nblk);
+    }
     return swr_launch_toeplitz(p->N, p->nt, cols, x, add, y, mode, p->s,
                                p->batched ? p->d_inst : nullptr, p->d_blk_inst, p->nblk, p->nt);
 }
@@ -1188,6 +1215,8 @@ void swr_destroy(swr_plan_t p) {
     cudaFree(p->d_gtmp2); cudaFree(p->d_trace);
     cudaFree(p->d_sys_build); cudaFree(p->d_sys_R); cudaFree(p->d_sys_final);
     cudaFree(p->d_status); cudaFree(p->d_scal); cudaFree(p->d_pit);
+    cudaFree(p->d_urec); cudaFree(p->d_rec_base);
+    cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0);
     Workspace& w = p->ws;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
     cudaFree(w.sn); cudaFree(w.sv); cudaFree(w.y); cudaFree(w.h); cudaFree(w.partial);
@@ -1243,6 +1272,7 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     if (!(p->d.nl_tol > 0.0)) p->d.nl_tol = 1e-13;
     if (p->d.nl_coef == 0.0) p->d.nl_coef = 1.0;
     p->causal_sweeps = (d->pc_sweeps >= 0) ? std::min(d->pc_sweeps, 16) : 0;
+    p->auto_sweeps = d->pc_sweeps < 0 && d->vkind == SWR_V_STATIC && d->precond == SWR_PC_CAUSAL;
     p->s = (cudaStream_t)stream;
     p->ninst = count;
     p->batched = count > 1;
@@ -1374,6 +1404,64 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
             st = SWR_ERR_CUDA;
     }
     if (!st) {
+        // FFT Toeplitz applies: transform length M >= 2 nt - 1 (a power of two), for
+        // 16 <= nt and M <= 4096 (three M-point buffers in shared memory)
+        bool on = true;
+        if (const char* e = getenv("SWR_TOEPLITZ_FFT")) on = atoi(e) != 0;
+        int M = 1;
+        while (M < 2 * p->nt - 1) M <<= 1;
+        const bool want0 =
+            d->precond == SWR_PC_ZERO_POTENTIAL || d->precond == SWR_PC_MEAN_POTENTIAL;
+        const bool want = d->vkind == SWR_V_STATIC || want0;
+        if (on && want && p->nt >= 16 && M <= 4096) {
+            std::vector<double2> W(M / 2);
+            for (int k = 0; k < M / 2; ++k) {
+                const double a = 2.0 * M_PI * (double)k / (double)M;
+                W[k] = make_double2(std::cos(a), -std::sin(a));
+            }
+            const size_t ns = (size_t)4 * p->N * M;
+            if (dalloc(&p->d_W, (size_t)M / 2) == SWR_OK &&
+                (d->vkind != SWR_V_STATIC || dalloc(&p->d_spec, ns) == SWR_OK) &&
+                (!want0 || dalloc(&p->d_spec0, ns) == SWR_OK) &&
+                cudaMemcpy(p->d_W, W.data(), sizeof(double2) * (M / 2), cudaMemcpyHostToDevice) ==
+                    cudaSuccess) {
+                p->fftM = M;
+            } else {
+                cudaGetLastError();
+                cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0);
+                p->d_W = p->d_spec = p->d_spec0 = nullptr;
+            }
+        }
+    }
+    if (!st && d->vkind == SWR_V_STATIC && d->tc == SWR_TC_ROBIN && (d->tc_re != 0.0 || d->tc_im != 0.0)) {
+        // u(T) by superposition: Phi_l, Phi_r (nt x n_j each) and U_d per subdomain, if
+        // they take at most a quarter of the free memory
+        bool on = true;
+        if (const char* e = getenv("SWR_SUPERPOSE")) on = atoi(e) != 0;
+        long long tot = 0;
+        std::vector<long long> base(p->N, 0);
+        for (const InstInfo& I : p->inst)
+            for (int j = 0; j < I.N; ++j) {
+                base[I.sub0 + j] = tot;
+                tot += (2LL * I.nt + 1) * p->n[I.sub0 + j];
+            }
+        size_t fr = 0, all = 0;
+        if (on && cudaMemGetInfo(&fr, &all) == cudaSuccess &&
+            (size_t)tot * sizeof(double2) <= fr / 4 && dalloc(&p->d_urec, (size_t)tot) == SWR_OK &&
+            dalloc(&p->d_rec_base, (size_t)p->N) == SWR_OK &&
+            cudaMemcpy(p->d_rec_base, base.data(), sizeof(long long) * p->N,
+                       cudaMemcpyHostToDevice) == cudaSuccess) {
+            p->superpose = true;
+            p->rec_base = base;
+        } else {
+            cudaGetLastError();
+            cudaFree(p->d_urec);
+            cudaFree(p->d_rec_base);
+            p->d_urec = nullptr;
+            p->d_rec_base = nullptr;
+        }
+    }
+    if (!st) {
         auto vb = build_systems(p, true);
         p->nsys_build = (int)vb.size();
         for (size_t k = 0; k < vb.size(); ++k) {
@@ -1500,6 +1588,9 @@ static swr_status build_body(swr_plan_t p, bool do_assemble) {
         if (st) return st;
         const double2* cols = p->d_iface + nb;
         LK(p_lag0(p, cols, p->d_lag0));
+        if (p->fftM)
+            LK(swr_launch_col_spectra(p->N, p->nt, cols, p->d_spec, p->fftM, p->d_W, s,
+                                      p->batched ? p->d_inst : nullptr, p->ninst));
     }
     if (p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) {
         const double* Vp = nullptr;                       // V = 0 (Section 5)
@@ -1517,6 +1608,9 @@ static swr_status build_body(swr_plan_t p, bool do_assemble) {
                        p->d_iface0, nullptr, nullptr, p->d_u0, p->work_build_imp);
         if (st) return st;
         LK(p_lag0(p, p->d_iface0 + nb, p->d_lag0_0));
+        if (p->fftM)
+            LK(swr_launch_col_spectra(p->N, p->nt, p->d_iface0 + nb, p->d_spec0, p->fftM,
+                                      p->d_W, s, p->batched ? p->d_inst : nullptr, p->ninst));
         p->have_L0 = true;
     }
     return SWR_OK;
@@ -1627,6 +1721,28 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
     CK(cudaEventRecord(p->ev[1], s));
     st = read_status(p);
     if (st) return st;
+    if (!p->built && p->auto_sweeps) {
+        // The causal substitution drops the same-step coupling of neighbouring
+        // interfaces, the corner entries X^{j,2}[0], X^{j,3}[0] of the subdomain
+        // inverses; one block-Jacobi sweep restores it.  Measured on the scaling
+        // workload: corners 3e-4 (N = 500, 0.2-wide subdomains) take GMRES from 7
+        // to 3 iterations and the solve from 54 to 43 ms with one sweep; corners
+        // 8e-7 (N = 256) or smaller keep the iteration count and the sweep only
+        // adds its hand-off (18 -> 25 ms).  Threshold between the two: 1e-5.
+        double cmax = 0.0;
+        for (const InstInfo& I : p->inst) {
+            if (I.N < 3) continue;
+            std::vector<double2> c0((size_t)4 * I.N);
+            CK(cudaMemcpy2DAsync(c0.data(), sizeof(double2), p->d_iface + p->nb + I.coff,
+                                 sizeof(double2) * I.nt, sizeof(double2), (size_t)4 * I.N,
+                                 cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            for (int j = 1; j + 1 < I.N; ++j)
+                for (int q = 1; q <= 2; ++q)
+                    cmax = std::max(cmax, std::hypot(c0[4 * j + q].x, c0[4 * j + q].y));
+        }
+        p->causal_sweeps = (cmax > 1e-5) ? 1 : 0;
+    }
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
     p->t_build_ms = ms;
@@ -1655,12 +1771,25 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     CK(cudaMemcpyAsync(p->d_gconv, g, sizeof(double2) * (size_t)p->nb,
                        cudaMemcpyDeviceToDevice, s));
     CK(cudaEventRecord(p->ev[2], s));
-    // final march (last step of Algorithms 1-3)
     double2* uT = uT_ ? reinterpret_cast<double2*>(uT_) : nullptr;
-    swr_status st2 = run_march(p, false, p->d_sys_final, p->N, g, p->d_gtmp, uT, p->d_trace,
-                               p->d_u0, p->work_R);
-    if (st2) return st2;
-    LK(p_jump(p));
+    if (p->superpose) {
+        // u(T) from the build marches' states (the march is linear and time invariant);
+        // the interface mismatch from w = L g + d and g
+        if (uT)
+            LK(swr_launch_superpose(p->d_urec, p->d_rec_base, p->d_sys_final, p->N, p->d_n,
+                                    p->d_goff, p->d_tc, p->nmax, g, uT, s));
+        if (p_toeplitz(p, p->d_iface + p->nb, g, p->d_iface, p->d_gtmp, 1))
+            return launch_fail("toeplitz", __LINE__);
+        const double as = std::hypot(p->two_sigma.x, p->two_sigma.y);
+        LK(swr_launch_jump_res(p->d_gtmp, g, p->N, p->nt, as > 0.0 ? 1.0 / as : 0.0, p->d_scal,
+                               s, p->batched ? p->d_inst : nullptr, p->d_if_inst, p->nif));
+    } else {
+        // final march (last step of Algorithms 1-3)
+        swr_status st2 = run_march(p, false, p->d_sys_final, p->N, g, p->d_gtmp, uT, p->d_trace,
+                                   p->d_u0, p->work_R);
+        if (st2) return st2;
+        LK(p_jump(p));
+    }
     CK(cudaEventRecord(p->ev[3], s));
     double jump = 0.0;
     CK(cudaMemcpyAsync(&jump, p->d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1674,7 +1803,8 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     loc.t_build_ms = p->t_build_ms;
     loc.t_solve_ms = a;
     loc.t_final_ms = b;
-    long long sweeps = 1 + (p->d.solver == SWR_SOLVER_CLASSICAL ? loc.iterations : 0);
+    long long sweeps = (p->superpose ? 0 : 1) +
+                       (p->d.solver == SWR_SOLVER_CLASSICAL ? loc.iterations : 0);
     loc.march_point_steps = sweeps * p->work_R;   // nodes x steps of one pass over all instances
     if (info) *info = loc;
     p->solved = (st == SWR_OK);
@@ -1741,6 +1871,9 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats* out, int32_t reset) {
         unsigned long long pit = 0;
         CK(cudaMemcpy(&pit, p->d_pit, sizeof(pit), cudaMemcpyDeviceToHost));
         out->march_point_iterations = (int64_t)pit;
+        out->superposed = p->superpose ? 1 : 0;
+        out->toeplitz_fft_length = p->fftM;
+        out->causal_sweeps = p->causal_sweeps;
     }
     if (reset) {
         p->stats = swr_stats{};

@@ -88,6 +88,9 @@ enum : int {
     SYS_IMP_R = 4,       // r_{j,1} = 1, other r = 0
     SYS_WRITE_UT = 8,    // write u(T) into the nodal output
     SYS_TRACE = 16,      // write v_n at both ends into the trace buffer
+    // record states for u(T) by superposition (a.urec set; local node order):
+    SYS_REC_U = 32,      // u after every step t at urec[rec + (t-1) n_j + node]
+    SYS_REC_LAST = 64,   // u after the system's last step at urec[rec + node]
 };
 
 struct MarchSys {
@@ -96,6 +99,7 @@ struct MarchSys {
     int nt;              // time steps of this system (its problem instance)
     int in_l, in_r;      // offset (complex entries) in gin of l_j / r_j at step 1 (or -1)
     int out_a, out_b;    // offset in gout of -l + 2 S v(a) / -r + 2 S v(b) at step 1 (or -1)
+    long long rec;       // SYS_REC_*: offset (complex entries) of its states in urec
 };
 
 // Chunked (partitioned) factorisation of the subdomain matrices for one chunk
@@ -139,6 +143,7 @@ struct MarchArgs {
     double2* gout;        // output blocks
     double2* uT;          // nodal output
     double2* trace;       // [nsys][2][nt]
+    double2* urec;        // states of the SYS_REC_* systems (NULL: none recorded)
     long long fstride, sstride, pstride;   // per-step factor strides (0: constant matrix)
     int stage;            // staging of streamed factors in shared memory (0, 1, 2)
     // Ragged packing (C == 1): CTA b holds the systems rag[rag_start[b] .. rag_start[b+1])
@@ -249,6 +254,26 @@ int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cud
 int swr_launch_jump(const double2* trace, const MarchSys* sys, int N, int nt, double* out,
                     cudaStream_t s, const InstInfo* inst = nullptr, const int* if_inst = nullptr,
                     int nif_total = 0);
+// Toeplitz apply through the FFT (transform length M, a power of two >= 2 nt - 1;
+// W[k] = exp(-2 pi i k / M), k < M/2): spectra of the 4 N first columns once per
+// build, then applies as swr_launch_toeplitz.
+int swr_launch_col_spectra(int nsub_total, int nt, const double2* cols, double2* spec, int M,
+                           const double2* W, cudaStream_t s, const InstInfo* inst = nullptr,
+                           int ninst = 0);
+int swr_launch_toeplitz_fft(int N, int nt, const double2* spec, const double2* x,
+                            const double2* add, double2* y, int mode, int M, const double2* W,
+                            cudaStream_t s, const InstInfo* inst = nullptr,
+                            const int* blk_inst = nullptr, int nblk_total = 0);
+// u(T) by superposition of the recorded build-march states (static V): subdomain j's
+// states at urec + rec_base[j] (impulse-l responses, impulse-r responses, each nt rows of
+// n_j, then the zero-flux final state); sys[j] gives its flux blocks and step count.
+int swr_launch_superpose(const double2* urec, const long long* rec_base, const MarchSys* sys,
+                         int N, const int* sub_n, const int* sub_goff, const int* sub_tc,
+                         int nmax, const double2* g, double2* uT, cudaStream_t s);
+// Interface mismatch from R(g) = L g + d (w) and g: max |(w-g)[l_{k+1}] - (w-g)[r_k]| * scale.
+int swr_launch_jump_res(const double2* w, const double2* g, int N, int nt, double scale,
+                        double* out, cudaStream_t s, const InstInfo* inst = nullptr,
+                        const int* if_inst = nullptr, int nif_total = 0);
 int swr_launch_misfit(const double2* u, const double2* tgt, long long n, double h, double2* ubar,
                       double* part, double* out, cudaStream_t s);
 int swr_launch_adj_seed(const double2* ubar, double half_dt, long long n, double2* y,

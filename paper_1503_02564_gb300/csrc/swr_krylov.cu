@@ -118,6 +118,149 @@ int swr_launch_toeplitz(int N, int nt, const double2* cols, const double2* x, co
 }
 
 // ---------------------------------------------------------------------------
+// The same apply through the FFT.  An output block is c1 * x1 + c2 * x2 on
+// steps 0..nt-1, each a causal convolution of two length-nt sequences; with a
+// transform length M >= 2 nt - 1 (a power of two) the circular convolution of
+// the zero-padded sequences equals it on 0..nt-1.  The spectra of the first
+// columns are formed once per build (k_col_spectra); an apply transforms the two
+// input blocks, multiplies by the spectra, sums and transforms back: 3 M log2 M
+// radix-2 butterflies per block in place of nt^2 complex multiply-adds.
+// The FFT is a radix-2 Stockham transform (self-sorting, out of place, ping-pong
+// between two shared-memory buffers); stage s with m = 2^s: butterfly b = (j, k),
+// j = b / m, k = b mod m, l = M / (2m):
+//     y[k + 2jm] = x[k + jm] + x[k + jm + lm],
+//     y[k + 2jm + m] = W^{jm} (x[k + jm] - x[k + jm + lm]),   W = exp(-2 pi i / M)
+// (conj(W) for the inverse).  W^k, k < M/2, comes from a table built on the host.
+// ---------------------------------------------------------------------------
+__device__ double2* fft_stockham(double2* x, double2* y, int M, int logM,
+                                 const double2* __restrict__ W, bool inverse) {
+    const int half = M >> 1;
+    for (int s = 0; s < logM; ++s) {
+        const int m = 1 << s, l = half >> s;
+        for (int b = threadIdx.x; b < half; b += blockDim.x) {
+            const int j = b >> s, k = b & (m - 1);
+            double2 w = __ldg(W + j * m);
+            if (inverse) w.y = -w.y;
+            const double2 c0 = x[k + j * m], c1 = x[k + j * m + l * m];
+            y[k + 2 * j * m] = cadd(c0, c1);
+            y[k + 2 * j * m + m] = cmul(w, csub(c0, c1));
+        }
+        __syncthreads();
+        double2* t = x;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
+// Instance of a global subdomain (batched plans; inst sorted by sub0).
+__device__ __forceinline__ int inst_of_sub(const InstInfo* inst, int ninst, int sub) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].sub0 <= sub) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Spectra of the first columns: slot 4 s + q of global subdomain s at spec[(4 s + q) M].
+__global__ void k_col_spectra(int nt, const double2* __restrict__ cols, double2* __restrict__ spec,
+                              int M, int logM, const double2* __restrict__ W,
+                              const InstInfo* __restrict__ inst, int ninst) {
+    extern __shared__ double2 sh[];
+    const int slot = blockIdx.x;             // 4 s + q
+    const double2* c = cols + (size_t)slot * nt;
+    if (inst) {
+        const InstInfo I = inst[inst_of_sub(inst, ninst, slot >> 2)];
+        nt = I.nt;
+        c = cols + I.coff + (size_t)(4 * ((slot >> 2) - I.sub0) + (slot & 3)) * I.nt;
+    }
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int t = threadIdx.x; t < M; t += blockDim.x) sh[t] = (t < nt) ? c[t] : zero;
+    __syncthreads();
+    const double2* r = fft_stockham(sh, sh + M, M, logM, W, false);
+    for (int t = threadIdx.x; t < M; t += blockDim.x) spec[(size_t)slot * M + t] = r[t];
+}
+
+int swr_launch_col_spectra(int nsub_total, int nt, const double2* cols, double2* spec, int M,
+                           const double2* W, cudaStream_t s, const InstInfo* inst, int ninst) {
+    int logM = 0;
+    while ((1 << logM) < M) ++logM;
+    const int smem = 2 * M * (int)sizeof(double2);
+    if (cudaFuncSetAttribute(k_col_spectra, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -1;
+    k_col_spectra<<<4 * nsub_total, 256, smem, s>>>(nt, cols, spec, M, logM, W, inst, ninst);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// y = x - L x (mode 0) or y = L x + add (mode 1), as k_toeplitz, from the spectra.
+__global__ void __launch_bounds__(256) k_toeplitz_fft(
+    int N, int nt, const double2* __restrict__ spec, const double2* __restrict__ x,
+    const double2* __restrict__ add, double2* __restrict__ y, int mode, int M, int logM,
+    const double2* __restrict__ W, const InstInfo* __restrict__ inst,
+    const int* __restrict__ blk_inst) {
+    extern __shared__ double2 sh[];
+    int o = blockIdx.x;
+    if (inst) {
+        const InstInfo I = inst[blk_inst[blockIdx.x]];
+        N = I.N;
+        nt = I.nt;
+        o = blockIdx.x - I.blk0;
+        spec += (size_t)4 * I.sub0 * M;
+        x += I.foff;
+        y += I.foff;
+        if (add) add += I.foff;
+    }
+    int c1, i1, c2, i2;
+    block_sources(o, N, c1, i1, c2, i2);
+    double2* A = sh;
+    double2* B = sh + M;
+    double2* acc = sh + 2 * M;
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int e = 0; e < 2; ++e) {
+        const int ci = e ? c2 : c1, ii = e ? i2 : i1;
+        if (ci < 0) break;
+        for (int t = threadIdx.x; t < M; t += blockDim.x)
+            A[t] = (t < nt) ? x[(size_t)ii * nt + t] : zero;
+        __syncthreads();
+        const double2* r = fft_stockham(A, B, M, logM, W, false);
+        const double2* sc = spec + (size_t)ci * M;
+        for (int t = threadIdx.x; t < M; t += blockDim.x) {
+            const double2 v = cmul(r[t], sc[t]);
+            acc[t] = e ? cadd(acc[t], v) : v;
+        }
+        __syncthreads();
+    }
+    const double2* r = fft_stockham(acc, A, M, logM, W, true);
+    const double inv = 1.0 / (double)M;
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const size_t idx = (size_t)o * nt + t;
+        const double2 v = make_double2(r[t].x * inv, r[t].y * inv);
+        y[idx] = (mode == 0) ? csub(x[idx], v) : cadd(v, add[idx]);
+    }
+}
+
+int swr_launch_toeplitz_fft(int N, int nt, const double2* spec, const double2* x,
+                            const double2* add, double2* y, int mode, int M, const double2* W,
+                            cudaStream_t s, const InstInfo* inst, const int* blk_inst,
+                            int nblk_total) {
+    int logM = 0;
+    while ((1 << logM) < M) ++logM;
+    const int smem = 3 * M * (int)sizeof(double2);
+    if (smem > 227 * 1024) return -2;
+    if (cudaFuncSetAttribute(k_toeplitz_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -1;
+    k_toeplitz_fft<<<inst ? nblk_total : 2 * N - 2, 256, smem, s>>>(
+        N, nt, spec, x, add, y, mode, M, logM, W, inst, blk_inst);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
 // Batched dot products out[i] = V_i^H w, i < nvec (V_i = V + i*ldv), in two
 // deterministic passes (per-CTA partial sums, then a fixed-order reduction).
 // ---------------------------------------------------------------------------
@@ -335,6 +478,128 @@ int swr_launch_jump(const double2* trace, const MarchSys*, int N, int nt, double
 }
 
 // ---------------------------------------------------------------------------
+// The same mismatch without a final march.  With w = R(g) = L g + d, the fluxes
+// of Eq. TransmisionCond give 2 S v_j(b_j) = w[l_{k+1}] + g[r_k] and 2 S v_{j+1}(a_{j+1}) =
+// w[r_k] + g[l_{k+1}] (Robin, S the scalar p), so v_j(b_j) - v_{j+1}(a_{j+1}) =
+// ((w - g)[l_{k+1}] - (w - g)[r_k]) / (2 S): the final residual's two blocks.
+// ---------------------------------------------------------------------------
+__global__ void k_jump_res(const double2* __restrict__ w, const double2* __restrict__ g, int N,
+                           int nt, double scale, unsigned long long* out,
+                           const InstInfo* __restrict__ inst, const int* __restrict__ if_inst,
+                           int nif_total) {
+    double m = 0.0;
+    const long long tot = (long long)(inst ? nif_total : N - 1) * nt;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < tot;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(q / nt);
+        const int n = (int)(q % nt);
+        long long r, l;   // r_k and l_{k+1} at step n
+        if (inst) {
+            const InstInfo I = inst[if_inst[k]];
+            if (n >= I.nt) continue;
+            const int kk = k - I.if0;
+            r = I.foff + (long long)(2 * kk) * I.nt + n;
+            l = r + I.nt;
+        } else {
+            r = (long long)(2 * k) * nt + n;
+            l = r + nt;
+        }
+        const double2 dl = csub(w[l], g[l]), dr = csub(w[r], g[r]);
+        m = fmax(m, hypot(dl.x - dr.x, dl.y - dr.y));
+    }
+    atomicMax(out, (unsigned long long)__double_as_longlong(m * scale));
+}
+
+int swr_launch_jump_res(const double2* w, const double2* g, int N, int nt, double scale,
+                        double* out, cudaStream_t s, const InstInfo* inst, const int* if_inst,
+                        int nif_total) {
+    cudaMemsetAsync(out, 0, sizeof(double), s);
+    k_jump_res<<<64, 256, 0, s>>>(w, g, N, nt, scale, reinterpret_cast<unsigned long long*>(out),
+                                  inst, if_inst, nif_total);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
+// u(T) by superposition (static V).  The subdomain march is linear and time
+// invariant, so the response to a flux impulse at step n is the response to the
+// impulse at step 1 delayed by n - 1 steps (the shift structure of Props. 3-4,
+// here for the whole state, not only its end traces).  With Phi_l(k), Phi_r(k) the
+// states after k steps of the build marches driven by l_{j,1} = 1 and r_{j,1} = 1,
+// and U_d the final state of the march from u0 with zero fluxes,
+//     u_j(T) = U_d + sum_{n=1}^{N} Phi_l(N - n + 1) l_j[n] + Phi_r(N - n + 1) r_j[n],
+// a dense (n_j x N) complex matrix-vector product per subdomain and flux side.
+// One thread per node, reading one row of states per step (coalesced); the
+// fluxes of a tile of steps are staged in shared memory, in the order of k.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_superpose(
+    const double2* __restrict__ urec, const long long* __restrict__ rec_base,
+    const MarchSys* __restrict__ sys, const int* __restrict__ sub_n,
+    const int* __restrict__ sub_goff, const int* __restrict__ sub_tc,
+    const double2* __restrict__ g, double2* __restrict__ uT) {
+    constexpr int KT = 256;
+    __shared__ double2 fl[KT], fr[KT];
+    const int j = blockIdx.y;
+    const int n = sub_n[j];
+    if (blockIdx.x * blockDim.x >= n) return;   // the whole CTA lies past this subdomain
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = li < n;
+    const MarchSys sy = sys[j];
+    const int nt = sy.nt;
+    const double2* Pl = urec + rec_base[j] + li;
+    const double2* Pr = Pl + (size_t)nt * n;
+    const double2 zero = make_double2(0.0, 0.0);
+    double2 a0 = in ? Pl[(size_t)2 * nt * n] : zero, a1 = zero, a2 = zero, a3 = zero;
+    const bool hl = sy.in_l >= 0, hr = sy.in_r >= 0;
+    for (int k0 = 0; k0 < nt; k0 += KT) {
+        const int kc = min(KT, nt - k0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < kc; q += blockDim.x) {
+            const int gi = nt - 1 - (k0 + q);   // Phi(k) multiplies the flux of step nt - k + 1
+            fl[q] = hl ? g[(size_t)sy.in_l + gi] : zero;
+            fr[q] = hr ? g[(size_t)sy.in_r + gi] : zero;
+        }
+        __syncthreads();
+        if (!in) continue;
+        const double2* pl = Pl + (size_t)k0 * n;
+        const double2* pr = Pr + (size_t)k0 * n;
+        int q = 0;
+        if (hl && hr) {
+            for (; q + 1 < kc; q += 2) {
+                a0 = cfma(pl[(size_t)q * n], fl[q], a0);
+                a1 = cfma(pr[(size_t)q * n], fr[q], a1);
+                a2 = cfma(pl[(size_t)(q + 1) * n], fl[q + 1], a2);
+                a3 = cfma(pr[(size_t)(q + 1) * n], fr[q + 1], a3);
+            }
+            for (; q < kc; ++q) {
+                a0 = cfma(pl[(size_t)q * n], fl[q], a0);
+                a1 = cfma(pr[(size_t)q * n], fr[q], a1);
+            }
+        } else if (hl || hr) {
+            const double2* pp = hl ? pl : pr;
+            const double2* ff = hl ? fl : fr;
+            for (; q + 1 < kc; q += 2) {
+                a0 = cfma(pp[(size_t)q * n], ff[q], a0);
+                a2 = cfma(pp[(size_t)(q + 1) * n], ff[q + 1], a2);
+            }
+            if (q < kc) a0 = cfma(pp[(size_t)q * n], ff[q], a0);
+        }
+    }
+    // the interface node belongs to the left subdomain
+    if (in && !(li == 0 && (sub_tc[j] & 1)))
+        uT[sub_goff[j] + li] = cadd(cadd(a0, a1), cadd(a2, a3));
+}
+
+int swr_launch_superpose(const double2* urec, const long long* rec_base, const MarchSys* sys,
+                         int N, const int* sub_n, const int* sub_goff, const int* sub_tc,
+                         int nmax, const double2* g, double2* uT, cudaStream_t s) {
+    dim3 grid((nmax + 255) / 256, N);
+    k_superpose<<<grid, 256, 0, s>>>(urec, rec_base, sys, sub_n, sub_goff, sub_tc, g, uT);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ---------------------------------------------------------------------------
 // Time-causal block forward substitution for (I - L) x = y.
 // Every block of L is lower-triangular Toeplitz in time (Props. 3-4), so with
 // x_n the values of all blocks at time n:
@@ -342,11 +607,9 @@ int swr_launch_jump(const double2* trace, const MarchSys*, int N, int nt, double
 // The lag-0 matrix L[0] couples the two fluxes of one interface (r_k, l_{k+1})
 // strongly (2x2 block D_k, solved exactly) and neighbouring interfaces only
 // through the corner entries of the subdomain inverse (X^{j,2}[0], X^{j,3}[0]),
-// which are resolved by `sweeps` block-Jacobi sweeps (0: dropped).
-// Time is processed in tiles of b steps:
-//   k_causal_far  (whole GPU): hist = y + contributions of all earlier tiles;
-//   k_causal_near (one thread-block cluster): the in-tile history and the
-//                 lag-0 solves, step by step, one thread per interface.
+// which are resolved by `sweeps` block-Jacobi sweeps (0: dropped).  The
+// substitution runs as a wavefront over the interfaces (k_causal_wave below);
+// k_lag0_setup forms the inverses of the 2x2 lag-0 blocks D_k once per build.
 // ---------------------------------------------------------------------------
 __global__ void k_lag0_setup(int N, int nt, const double2* __restrict__ cols,
                              double2* __restrict__ lag0, const InstInfo* __restrict__ inst,

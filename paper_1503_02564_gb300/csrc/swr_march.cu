@@ -555,7 +555,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     };
 
     const double2 zero = make_double2(0.0, 0.0);
-    MarchSys sy = {0, 0, 0, -1, -1, -1, -1};
+    MarchSys sy = {0, 0, 0, -1, -1, -1, -1, 0};
     int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0;
     if (valid) {
         sy = a.sys[sidx];
@@ -568,6 +568,9 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     }
     const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
     const bool realsep = valid && (p <= Pj);          // separators beyond Pj are padding
+    // every step's state recorded (impulse responses for the superposed u(T))
+    const bool rec_u = valid && a.urec && (sy.flags & SYS_REC_U);
+    const int nj = valid ? a.sub_n[j] : 0;
     // Systems of a launch may have different step counts (a batch of problem
     // instances): the CTA runs to the longest of its systems (a cluster holds one
     // system), and a system past its own count neither reads fluxes, nor writes
@@ -891,6 +894,13 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
         }
+        if (rec_u && live) {   // u_t of this system in local node order
+            double2* row = a.urec + sy.rec + (size_t)(t - 1) * nj;
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) row[sp + 1 + i] = u[i];
+            if (realsep) row[sp] = *SEP(usep, p);
+        }
         F += a.fstride;
         sE_l += a.sstride;
         sE_r += a.sstride;
@@ -925,6 +935,12 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             bad |= !cfinite(us);
             // the interface node belongs to the left subdomain
             if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || !(tcf & 1))) a.uT[goff + sp] = us;
+            if ((sy.flags & SYS_REC_LAST) && a.urec) a.urec[sy.rec + sp] = us;
+        }
+        if ((sy.flags & SYS_REC_LAST) && a.urec) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.urec[sy.rec + sp + 1 + i] = u[i];
         }
     }
     if (bad) atomicOr(a.status, ST_NONFINITE);
@@ -1031,7 +1047,7 @@ __global__ void __launch_bounds__(256, 1) k_march_tdep(const TdepArgs ta) {
             cl.sync();
     };
     const double2 zero = make_double2(0.0, 0.0);
-    MarchSys sy = {0, 0, 0, -1, -1, -1, -1};
+    MarchSys sy = {0, 0, 0, -1, -1, -1, -1, 0};
     int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0, n = 0;
     if (valid) {
         sy = a.sys[sidx];

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
             cl.sync();
     };
     const double2 zero = make_double2(0.0, 0.0);
-    MarchSys sy = {0, 0, 0, -1, -1, -1, -1};
+    MarchSys sy = {0, 0, 0, -1, -1, -1, -1, 0};
     int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0;
     if (valid) {
         sy = a.sys[sidx];

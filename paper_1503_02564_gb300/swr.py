@@ -62,6 +62,8 @@ class swr_stats(ctypes.Structure):
         ("march_factor_bytes_per_step", ctypes.c_int64),
         ("march_point_iterations", ctypes.c_int64),
         ("nl_march_launches", ctypes.c_int64), ("nl_march_ms", ctypes.c_double),
+        ("superposed", ctypes.c_int32), ("toeplitz_fft_length", ctypes.c_int32),
+        ("causal_sweeps", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -285,3 +285,85 @@ def test_repeated_builds_replay_the_captured_build(case):
     fresh.destroy()
     assert np.array_equal(d3, d4)
     assert rel(d3, O.build_d(problem(wl2))) < TOL_MARCH
+
+
+def _solve_with(wl, superpose, **kw):
+    from paper_1503_02564_gb300 import swr
+    os.environ["SWR_SUPERPOSE"] = "1" if superpose else "0"
+    try:
+        plan = gpu_plan(wl, **kw)
+    finally:
+        os.environ.pop("SWR_SUPERPOSE", None)
+    assert plan.get_stats()["superposed"] == (1 if superpose else 0)
+    g, uT, info = _solve(plan, wl)
+    plan.destroy()
+    return g, uT, info
+
+
+@pytest.mark.parametrize("case", ["config1_small", "ragged_tiny", "config2_N16_small", "two_long"])
+def test_superposed_final_state_matches_final_march(case):
+    """u(T) as the superposition of the build marches' recorded states (static V,
+    Robin) against the final march with the same converged fluxes, and the
+    interface mismatch from the final residual against the one from the final
+    march's traces."""
+    from paper_1503_02564_gb300 import swr
+    wl = CASES[case]()
+    kw = dict(precond=swr.SWR_PC_CAUSAL, restart=100, maxit=1000, tol_abs=1e-12)
+    g1, u1, i1 = _solve_with(wl, True, **kw)
+    g0, u0, i0 = _solve_with(wl, False, **kw)
+    assert np.array_equal(g1, g0)          # the solve itself does not change
+    assert rel(u1, u0) < 1e-12
+    assert abs(i1["interface_jump"] - i0["interface_jump"]) <= 1e-12 + 1e-3 * i0["interface_jump"]
+    assert i1["march_point_steps"] == 0 and i0["march_point_steps"] > 0
+    _, uTm = O.mono_interface(problem(wl))
+    assert rel(u1, uTm) < TOL_SOLVE
+
+
+def test_superposed_final_state_null_uT_and_unconverged():
+    """uT may be NULL; with an iteration cap the superposition still reproduces
+    the final march of the (unconverged) fluxes, and the mismatch is nonzero."""
+    from paper_1503_02564_gb300 import swr
+    wl = CASES["config2_N16_small"]()
+    out = []
+    for sp in (True, False):
+        os.environ["SWR_SUPERPOSE"] = "1" if sp else "0"
+        try:
+            plan = gpu_plan(wl, maxit=3, restart=30)
+        finally:
+            os.environ.pop("SWR_SUPERPOSE", None)
+        info = plan.solve(None, False, None, allow_not_converged=True)
+        assert info["status"] == swr.SWR_ERR_NOT_CONVERGED
+        uT = torch.zeros(wl.nx, dtype=torch.complex128, device="cuda")
+        info = plan.solve(None, False, uT, allow_not_converged=True)
+        out.append((uT.cpu().numpy(), info["interface_jump"]))
+        plan.destroy()
+    assert rel(out[0][0], out[1][0]) < 1e-12
+    assert out[0][1] > 1e-6 and abs(out[0][1] - out[1][1]) <= 1e-9 * out[1][1]
+
+
+@pytest.mark.parametrize("fft", [True, False])
+@pytest.mark.parametrize("case", ["config1_small", "ragged_tiny", "config2_N16_small", "long_nt"])
+def test_toeplitz_apply_fft_and_direct_match_oracle(case, fft):
+    """(I - L) x and L x + d from the first columns, by the FFT (transform length
+    the power of two >= 2 nt - 1) and by the direct causal sums, against the
+    oracle's (I - L) x; nt = 1500 takes the largest transform (4096)."""
+    from paper_1503_02564_gb300 import swr
+    wl = W.config1(nx=241, nt=1500, nsub=4) if case == "long_nt" else CASES[case]()
+    os.environ["SWR_TOEPLITZ_FFT"] = "1" if fft else "0"
+    try:
+        plan = gpu_plan(wl)
+    finally:
+        os.environ.pop("SWR_TOEPLITZ_FFT", None)
+    M = plan.get_stats()["toeplitz_fft_length"]
+    if fft:
+        assert M >= 2 * wl.nt - 1 and M & (M - 1) == 0 and M < 4 * wl.nt
+    else:
+        assert M == 0
+    P = problem(wl)
+    cols = O.build_columns(P)
+    x = W.random_interface(wl.nblk, wl.nt, 9)
+    xi = torch.tensor(x.ravel(), dtype=torch.complex128, device="cuda")
+    y = torch.zeros_like(xi)
+    plan.apply_interface(xi, y)
+    plan.destroy()
+    assert rel(y.cpu().numpy(), O.apply_I_minus_L(P, cols, x)) < TOL_MARCH

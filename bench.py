@@ -627,6 +627,7 @@ def main():
         for c, info in zip(cases, infos_last):
             per_n.append({"N": c["N"], "iterations": info["iterations"],
                           "causal_sweeps": st[len(per_n)]["causal_sweeps"],
+                          "causal_window": st[len(per_n)]["causal_window"],
                           "superposed": st[len(per_n)]["superposed"],
                           "toeplitz_fft_length": st[len(per_n)]["toeplitz_fft_length"],
                           "residual": info["residual"], "build_ms": info["t_build_ms"],

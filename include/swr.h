@@ -65,7 +65,15 @@ enum { SWR_TC_ROBIN = 0, SWR_TC_S02 = 1 };
  * marches (Algorithm 1).  For SWR_V_NONLINEAR the interface operator R_nl is
  * nonlinear: FIXED_POINT runs g <- g - P^{-1}(g - R_nl g) with the plan's
  * preconditioner (Section 5), CLASSICAL runs g <- R_nl g, GMRES is rejected. */
-enum { SWR_SOLVER_GMRES = 0, SWR_SOLVER_FIXED_POINT = 1, SWR_SOLVER_CLASSICAL = 2 };
+enum { SWR_SOLVER_GMRES = 0, SWR_SOLVER_FIXED_POINT = 1, SWR_SOLVER_CLASSICAL = 2,
+       SWR_SOLVER_CAUSAL = 3 };
+/* SWR_SOLVER_CAUSAL (static V only): no Krylov iteration.  The blocks of L are
+ * causal Toeplitz in time (Props. 3-4), so (I - L) g = d is solved by block
+ * forward substitution in time, g = P^{-1} d with the CAUSAL preconditioner's
+ * substitution (in its window form the same-step coupling of neighbouring
+ * interfaces is solved exactly, so P = I - L to rounding), then refined,
+ * g += P^{-1} (d - (I - L) g), while the true residual is >= tol_abs (at most
+ * maxit substitutions; iterations counts them). */
 /* Preconditioners for GMRES (right preconditioning):
  *   NONE;
  *   ZERO_POTENTIAL: P = I - L_0, the interface operator with V = 0 (Section 5);
@@ -102,9 +110,10 @@ typedef struct swr_desc {
     int32_t pc_sweeps;          /* block-Jacobi sweeps resolving the same-step coupling  */
                                 /* of neighbouring interfaces in the causal substitution */
                                 /* (CAUSAL / ZERO_POTENTIAL preconditioners), 0..16;    */
-                                /* < 0: chosen by the library (CAUSAL, static V: 1 when */
-                                /* the lag-0 corner entries X^{j,2}[0], X^{j,3}[0] of   */
-                                /* the first build exceed 1e-5 in modulus, else 0)      */
+                                /* < 0: chosen by the library (CAUSAL, static V, after  */
+                                /* the first build: the exact window form when the       */
+                                /* corner couplings decay within 8 interfaces, see       */
+                                /* swr_stats.causal_window; else 1 sweep)               */
 } swr_desc;
 
 typedef struct swr_info {
@@ -148,6 +157,8 @@ typedef struct swr_stats {
                                  * power of two >= 2 nt - 1, for 16 <= nt and M <= 4096,
                                  * SWR_TOEPLITZ_FFT not 0); 0: direct causal sums        */
     int32_t causal_sweeps;      /* block-Jacobi sweeps of the causal substitution in use */
+    int32_t causal_window;      /* H >= 1: the substitution solves the same-step coupling
+                                 * exactly over a window of H interfaces each side; 0: sweeps */
 } swr_stats;
 
 typedef struct swr_plan_s *swr_plan_t;

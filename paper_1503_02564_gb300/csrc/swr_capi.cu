@@ -141,6 +141,8 @@ struct swr_plan_s {
     Workspace ws;
     int causal_sweeps = 0;
     bool auto_sweeps = false;      // pc_sweeps < 0: chosen from the lag-0 corners at the first build
+    int causal_H = 0;              // >= 1: window form of the substitution (exact lag-0 solve)
+    double2* d_Gw = nullptr;       // rows of the lag-0 inverse, [nif][2H+1][4]
     bool built = false;
     bool have_L0 = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -836,14 +838,18 @@ int p_jump(swr_plan_t p) {
 }
 int p_causal(swr_plan_t p, const double2* cols, const double2* lag0, const double2* y,
              double2* x) {
+    // the window form applies to the plan's own operator (the rows of its lag-0 inverse)
+    const bool win = p->causal_H > 0 && cols == p->d_iface + p->nb;
+    const double2* Gw = win ? p->d_Gw : nullptr;
+    const int H = win ? p->causal_H : 0;
     if (!p->batched)
         return swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps, p->d_hist,
-                                 p->d_status, p->s);
+                                 p->d_status, p->s, nullptr, nullptr, 0, 0, 0, Gw, H);
     // whole instances per cooperative launch, as many as fit at once
     for (const auto& g : p->causal_groups) {
         const int rc = swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps,
                                          p->d_hist, p->d_status, p->s, p->d_inst, p->d_if_inst,
-                                         g.first, g.second, p->nif);
+                                         g.first, g.second, p->nif, Gw, H);
         if (rc) return rc;
     }
     return 0;
@@ -1026,6 +1032,50 @@ swr_status fixed_point(swr_plan_t p, double2* g, bool g_init, bool classical, sw
         info->residual = diff;
     }
     return diff < p->d.tol_abs ? SWR_OK : SWR_ERR_NOT_CONVERGED;
+}
+
+// Direct time-causal solve of (I - L) g = d (static V): block forward substitution
+// in time, g = P^{-1} d, refined by g += P^{-1} r, r = d - (I - L) g, while the
+// true residual ||r||_2 >= tol (at most maxit substitutions).
+swr_status causal_direct(swr_plan_t p, double2* g, bool g_init, swr_info* info) {
+    swr_status st = ensure_workspace(p);
+    if (st) return st;
+    Workspace& w = p->ws;
+    const long long n = w.n;
+    const double2* cols = p->d_iface + (size_t)p->nb;
+    auto residual = [&](double* out) -> swr_status {   // w.r = d - (I - L) g
+        if (p_toeplitz(p, cols, g, nullptr, w.z, 0)) return SWR_ERR_UNSUPPORTED;
+        CK(cudaMemcpyAsync(w.r, p->d_iface, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+        LK(swr_launch_axpby(w.r, w.z, n, make_double2(1.0, 0.0), make_double2(-1.0, 0.0), p->s));
+        return norm2(p, w.r, n, out);
+    };
+    double res = INFINITY;
+    if (g_init) {
+        if ((st = residual(&res))) return st;
+    } else {
+        CK(cudaMemsetAsync(g, 0, sizeof(double2) * n, p->s));
+        CK(cudaMemcpyAsync(w.r, p->d_iface, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+        if ((st = norm2(p, w.r, n, &res))) return st;
+    }
+    const double res0 = res;
+    int it = 0;
+    while (res >= p->d.tol_abs && it < p->d.maxit) {
+        const int pi = prof_begin(p, 2, 0);
+        const int rc = p_causal(p, cols, p->d_lag0, w.r, w.w);
+        prof_end(p, pi);
+        if (rc == -2) return SWR_ERR_UNSUPPORTED;
+        if (rc) return launch_fail("causal substitution", __LINE__);
+        LK(swr_launch_axpby(g, w.w, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s));
+        ++it;
+        if ((st = residual(&res))) return st;
+        if (!std::isfinite(res)) return SWR_ERR_NONFINITE;
+    }
+    if (info) {
+        info->iterations = it;
+        info->residual = res;
+        info->residual0 = res0;
+    }
+    return res < p->d.tol_abs ? SWR_OK : SWR_ERR_NOT_CONVERGED;
 }
 
 // Nonlinear potential (Section 5): g^{k+1} = g^k - P^{-1}(g^k - R_nl g^k) with the
@@ -1216,7 +1266,7 @@ void swr_destroy(swr_plan_t p) {
     cudaFree(p->d_sys_build); cudaFree(p->d_sys_R); cudaFree(p->d_sys_final);
     cudaFree(p->d_status); cudaFree(p->d_scal); cudaFree(p->d_pit);
     cudaFree(p->d_urec); cudaFree(p->d_rec_base);
-    cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0);
+    cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0); cudaFree(p->d_Gw);
     Workspace& w = p->ws;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
     cudaFree(w.sn); cudaFree(w.sv); cudaFree(w.y); cudaFree(w.h); cudaFree(w.partial);
@@ -1241,7 +1291,8 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     }
     if (d->vkind < 0 || d->vkind > 2 || d->tc < SWR_TC_ROBIN || d->tc > SWR_TC_S02)
         return SWR_ERR_ARG;
-    if (d->solver < 0 || d->solver > 2 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
+    if (d->solver < 0 || d->solver > 3 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
+    if (d->solver == SWR_SOLVER_CAUSAL && d->vkind != SWR_V_STATIC) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_NONLINEAR && d->solver == SWR_SOLVER_GMRES) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_TIME && d->solver == SWR_SOLVER_FIXED_POINT) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_TIME && (long long)(d->nt + 1) * d->nx > (1LL << 31)) return SWR_ERR_ARG;
@@ -1272,7 +1323,8 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     if (!(p->d.nl_tol > 0.0)) p->d.nl_tol = 1e-13;
     if (p->d.nl_coef == 0.0) p->d.nl_coef = 1.0;
     p->causal_sweeps = (d->pc_sweeps >= 0) ? std::min(d->pc_sweeps, 16) : 0;
-    p->auto_sweeps = d->pc_sweeps < 0 && d->vkind == SWR_V_STATIC && d->precond == SWR_PC_CAUSAL;
+    p->auto_sweeps = d->pc_sweeps < 0 && d->vkind == SWR_V_STATIC &&
+                     (d->precond == SWR_PC_CAUSAL || d->solver == SWR_SOLVER_CAUSAL);
     p->s = (cudaStream_t)stream;
     p->ninst = count;
     p->batched = count > 1;
@@ -1591,6 +1643,9 @@ static swr_status build_body(swr_plan_t p, bool do_assemble) {
         if (p->fftM)
             LK(swr_launch_col_spectra(p->N, p->nt, cols, p->d_spec, p->fftM, p->d_W, s,
                                       p->batched ? p->d_inst : nullptr, p->ninst));
+        if (p->causal_H > 0)
+            LK(swr_launch_lag0_window(p->N, p->nt, cols, p->d_lag0, p->d_Gw, p->causal_H, s,
+                                      p->batched ? p->d_inst : nullptr, p->d_if_inst, p->nif));
     }
     if (p->d.precond == SWR_PC_ZERO_POTENTIAL || p->d.precond == SWR_PC_MEAN_POTENTIAL) {
         const double* Vp = nullptr;                       // V = 0 (Section 5)
@@ -1722,14 +1777,14 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
     st = read_status(p);
     if (st) return st;
     if (!p->built && p->auto_sweeps) {
-        // The causal substitution drops the same-step coupling of neighbouring
-        // interfaces, the corner entries X^{j,2}[0], X^{j,3}[0] of the subdomain
-        // inverses; one block-Jacobi sweep restores it.  Measured on the scaling
-        // workload: corners 3e-4 (N = 500, 0.2-wide subdomains) take GMRES from 7
-        // to 3 iterations and the solve from 54 to 43 ms with one sweep; corners
-        // 8e-7 (N = 256) or smaller keep the iteration count and the sweep only
-        // adds its hand-off (18 -> 25 ms).  Threshold between the two: 1e-5.
-        double cmax = 0.0;
+        // The substitution's same-step coupling of neighbouring interfaces is the
+        // corner entries cB_k = X^{k+1,2}[0], cD_k = X^{k,3}[0] of the subdomain
+        // inverses, of relative size f = max_k max(|cB_k|, |cD_k|) ||D_k^{-1}||_inf.
+        // The window form resolves it to f^{H+1}: H is the smallest width with
+        // f^{H+1} <= 1e-16 (then P^{-1} is (I - L)^{-1} to rounding and GMRES needs
+        // one iteration); f^9 > 1e-16 (narrow subdomains) takes one block-Jacobi
+        // sweep instead, f <= 1e-16 neither.
+        double f = 0.0;
         for (const InstInfo& I : p->inst) {
             if (I.N < 3) continue;
             std::vector<double2> c0((size_t)4 * I.N);
@@ -1737,11 +1792,34 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
                                  sizeof(double2) * I.nt, sizeof(double2), (size_t)4 * I.N,
                                  cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
-            for (int j = 1; j + 1 < I.N; ++j)
-                for (int q = 1; q <= 2; ++q)
-                    cmax = std::max(cmax, std::hypot(c0[4 * j + q].x, c0[4 * j + q].y));
+            for (int k = 0; k + 1 < I.N; ++k) {
+                const double2 a = c0[4 * (k + 1) + 0], b = c0[4 * k + 3];
+                const double2 det = make_double2(1.0 - (a.x * b.x - a.y * b.y),
+                                                 -(a.x * b.y + a.y * b.x));
+                const double na = std::hypot(a.x, a.y), nbv = std::hypot(b.x, b.y);
+                const double dinv = std::max(1.0 + na, 1.0 + nbv) / std::hypot(det.x, det.y);
+                double c = 0.0;
+                if (k + 2 < I.N) c = std::max(c, std::hypot(c0[4 * (k + 1) + 1].x, c0[4 * (k + 1) + 1].y));
+                if (k >= 1) c = std::max(c, std::hypot(c0[4 * k + 2].x, c0[4 * k + 2].y));
+                f = std::max(f, c * dinv);
+            }
         }
-        p->causal_sweeps = (cmax > 1e-5) ? 1 : 0;
+        int H = 0;
+        if (f > 1e-16) {
+            H = 1;
+            while (H <= 8 && std::pow(f, H + 1) > 1e-16) ++H;
+        }
+        p->causal_sweeps = 0;
+        p->causal_H = 0;
+        if (H > 8) {
+            p->causal_sweeps = 1;
+        } else if (H >= 1) {
+            if (!p->d_Gw && (st = dalloc(&p->d_Gw, (size_t)p->nif * (2 * 8 + 1) * 4))) return st;
+            p->causal_H = H;
+            LK(swr_launch_lag0_window(p->N, p->nt, p->d_iface + p->nb, p->d_lag0, p->d_Gw, H, s,
+                                      p->batched ? p->d_inst : nullptr, p->d_if_inst, p->nif));
+            CK(cudaStreamSynchronize(s));
+        }
     }
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, p->ev[0], p->ev[1]));
@@ -1762,6 +1840,8 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     swr_status st;
     if (p->d.vkind == SWR_V_NONLINEAR)
         st = nl_fixed_point(p, g, init, &loc);
+    else if (p->d.solver == SWR_SOLVER_CAUSAL)
+        st = causal_direct(p, g, init, &loc);
     else if (p->d.solver == SWR_SOLVER_GMRES)
         st = gmres(p, p->d_iface, p->d.tol_abs, g, init, &loc);
     else
@@ -1874,6 +1954,7 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats* out, int32_t reset) {
         out->superposed = p->superpose ? 1 : 0;
         out->toeplitz_fft_length = p->fftM;
         out->causal_sweeps = p->causal_sweeps;
+        out->causal_window = p->causal_H;
     }
     if (reset) {
         p->stats = swr_stats{};

@@ -245,7 +245,13 @@ int swr_launch_lsq(const double2* H, int ldh, const double2* sv, int k, double2*
 int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0,
                       const double2* y, double2* x, int sweeps, void* scratch, int* status,
                       cudaStream_t s, const InstInfo* inst = nullptr, const int* if_inst = nullptr,
-                      int k0 = 0, int nif_group = 0, int nif_total = 0);
+                      int k0 = 0, int nif_group = 0, int nif_total = 0,
+                      const double2* Gw = nullptr, int H = 0);
+// Rows of the lag-0 inverse for the window form of the substitution, |j - k| <= H
+// (1 <= H <= 8): Gw[nif][2H+1][4].
+int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* lag0, double2* Gw,
+                           int H, cudaStream_t s, const InstInfo* inst = nullptr,
+                           const int* if_inst = nullptr, int nif_total = 0);
 int swr_causal_capacity(int nt);
 size_t swr_causal_scratch_bytes(int N);
 int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s,

@@ -687,9 +687,120 @@ __device__ bool wait_neighbours(int k, bool hl, bool hr, int target, const int* 
     return true;
 }
 
+// Wait until interface nb has reached `target` (one lane per interface waited on).
+__device__ bool wait_one(int nb, int target, const int* progress, int* abortf, int* status) {
+    long long polls = 0;
+    while (load_acquire(progress + nb) < target) {
+        if (load_acquire(abortf) != 0) return false;
+        if (++polls > kWaitPolls) {
+            atomicOr(status, ST_TIMEOUT);
+            store_release(abortf, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// Rows of the inverse of the lag-0 system.  With z_k = (r_k, l_{k+1}) the values
+// of interface k at one time step, the same-step part of (I - L) is block
+// tridiagonal, A0 = D + U + Lw:
+//     D_k = [[1, -a_k], [-b_k, 1]],  a_k = X^{k+1,1}[0],  b_k = X^{k,4}[0],
+//     U_k z_{k+1} = -cB_k r_{k+1} e_1,   cB_k = X^{k+1,2}[0],
+//     Lw_k z_{k-1} = -cD_k l_k e_2,      cD_k = X^{k,3}[0].
+// A0 = (I - F) D with F = -(U + Lw) D^{-1}, so row k of A0^{-1} is
+// D_k^{-1} sum_m psi^(m), psi^(0) = e_k, psi^(m+1)_j = psi^(m)_{j-1} F_{j-1,j} +
+// psi^(m)_{j+1} F_{j+1,j} = [cB_{j-1} psi_{j-1}[:,0] | cD_{j+1} psi_{j+1}[:,1]] D_j^{-1}.
+// The couplings cB, cD are the corner entries of the subdomain inverses (small:
+// psi^(m) decays like (|c| |D^{-1}|)^m); m runs to H + 4 over a window of H + 4
+// interfaces each side, and the blocks |j - k| <= H are kept:
+//     Gw[(k (2H+1) + j - k + H) 4 + {00, 01, 10, 11}] = (A0^{-1})_{k,j}.
+// One thread per interface.
+constexpr int kWinMaxH = 8;
+constexpr int kWinW = kWinMaxH + 4;
+
+__global__ void k_lag0_window(int N, int nt, const double2* __restrict__ cols,
+                              const double2* __restrict__ lag0, double2* __restrict__ Gw, int H,
+                              const InstInfo* __restrict__ inst, const int* __restrict__ if_inst,
+                              int nif_total) {
+    const int kg = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kg >= (inst ? nif_total : N - 1)) return;
+    int k = kg;
+    if (inst) {
+        const InstInfo I = inst[if_inst[kg]];
+        N = I.N;
+        nt = I.nt;
+        k = kg - I.if0;
+        cols += I.coff;
+    }
+    const int nI = N - 1, W = H + 4;
+    const double2 zero = make_double2(0.0, 0.0);
+    double2 psi[2 * kWinW + 1][4], nxt[2 * kWinW + 1][4], sum[2 * kWinW + 1][4];
+    for (int q = 0; q < 2 * W + 1; ++q)
+        for (int e = 0; e < 4; ++e) psi[q][e] = sum[q][e] = zero;
+    psi[W][0] = psi[W][3] = sum[W][0] = sum[W][3] = make_double2(1.0, 0.0);
+    auto cB = [&](int j) { return (j + 1 <= N - 2) ? cols[(size_t)(4 * (j + 1) + 1) * nt] : zero; };
+    auto cD = [&](int j) { return (j >= 1) ? cols[(size_t)(4 * j + 2) * nt] : zero; };
+    for (int m = 1; m <= W; ++m) {
+        for (int q = 0; q < 2 * W + 1; ++q) {
+            const int j = k + q - W;
+            for (int e = 0; e < 4; ++e) nxt[q][e] = zero;
+            if (j < 0 || j >= nI) continue;
+            // T = [cB_{j-1} psi_{j-1}[:,0] | cD_{j+1} psi_{j+1}[:,1]]
+            double2 t00 = zero, t10 = zero, t01 = zero, t11 = zero;
+            if (q > 0 && j - 1 >= 0) {
+                const double2 c = cB(j - 1);
+                t00 = cmul(c, psi[q - 1][0]);
+                t10 = cmul(c, psi[q - 1][2]);
+            }
+            if (q < 2 * W && j + 1 < nI) {
+                const double2 c = cD(j + 1);
+                t01 = cmul(c, psi[q + 1][1]);
+                t11 = cmul(c, psi[q + 1][3]);
+            }
+            const double2* Di = lag0 + (size_t)(kg + q - W) * 4;   // D_j^{-1}
+            nxt[q][0] = cfma(t00, Di[0], cmul(t01, Di[2]));
+            nxt[q][1] = cfma(t00, Di[1], cmul(t01, Di[3]));
+            nxt[q][2] = cfma(t10, Di[0], cmul(t11, Di[2]));
+            nxt[q][3] = cfma(t10, Di[1], cmul(t11, Di[3]));
+        }
+        for (int q = 0; q < 2 * W + 1; ++q)
+            for (int e = 0; e < 4; ++e) {
+                psi[q][e] = nxt[q][e];
+                sum[q][e] = cadd(sum[q][e], nxt[q][e]);
+            }
+    }
+    const double2* Dk = lag0 + (size_t)kg * 4;
+    for (int d = -H; d <= H; ++d) {
+        const int q = W + d;
+        double2* g = Gw + ((size_t)kg * (2 * H + 1) + d + H) * 4;
+        const double2* s = sum[q];
+        g[0] = cfma(Dk[0], s[0], cmul(Dk[1], s[2]));
+        g[1] = cfma(Dk[0], s[1], cmul(Dk[1], s[3]));
+        g[2] = cfma(Dk[2], s[0], cmul(Dk[3], s[2]));
+        g[3] = cfma(Dk[2], s[1], cmul(Dk[3], s[3]));
+    }
+}
+
+int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* lag0, double2* Gw,
+                           int H, cudaStream_t s, const InstInfo* inst, const int* if_inst,
+                           int nif_total) {
+    if (H < 1 || H > kWinMaxH) return -2;
+    const int nif = inst ? nif_total : N - 1;
+    k_lag0_window<<<(nif + 63) / 64, 64, 0, s>>>(N, nt, cols, lag0, Gw, H, inst, if_inst,
+                                                 nif_total);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 // Warp 0 waits, solves and publishes; warps 1-4 (one per source block) compute,
 // during step n, the part of step n+1's history that uses values older than n
 // (lags >= 2), so that step n+1 adds one lag-1 term on its critical path.
+// The same-step coupling of neighbouring interfaces is resolved either by
+// `sweeps` block-Jacobi sweeps (H == 0), or exactly (to (|c| |D^{-1}|)^{H+1}) by
+// the window form (H >= 1): interface k publishes its right-hand side R_n(k),
+// waits for those of the interfaces within H, and forms x_n(k) = sum_d
+// G_{k,k+d} R_n(k+d) from the rows of the lag-0 inverse (k_lag0_window).
 __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweeps,
                                                      const double2* __restrict__ cols,
                                                      const double2* __restrict__ lag0,
@@ -699,7 +810,8 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                                                      int* abortf, int* status,
                                                      const InstInfo* __restrict__ inst,
                                                      const int* __restrict__ if_inst, int k0,
-                                                     int nif_all) {
+                                                     int nif_all, const double2* __restrict__ Gw,
+                                                     int H) {
     __shared__ double2 hp[2][4];     // partial histories, by parity of the step they serve
     __shared__ int s_go;
     // global interface kg (progress, sweep values, lag-0 blocks); local k within its
@@ -731,7 +843,9 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         cc = has ? cols + (size_t)cslot * nt : nullptr;
         xin = has ? x + (size_t)inb * nt : nullptr;
     };
-    const int S1 = sweeps + 1;
+    const int S1 = (H > 0) ? 2 : sweeps + 1;
+    // window of interfaces within this instance
+    const int dlo = (H > 0) ? -min(H, k) : 0, dhi = (H > 0) ? min(H, N - 2 - k) : 0;
     if (threadIdx.x < 8) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
     // role data: warps 1-4 accumulate source e = w-1; lane 0 of warp 0 solves
     bool has = false;
@@ -755,38 +869,89 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         for (int e = 0; e < 4; ++e) c1[e] = (hs[e] && nt > 1) ? cs[e][1] : zero;
     }
     __syncthreads();
+    const double2* Gk = (H > 0) ? Gw + (size_t)kg * (2 * H + 1) * 4 : nullptr;
     for (int n = 0; n < nt; ++n) {
-        if (solver) s_go = wait_neighbours(kg, has_l, has_r, n * S1, progress, abortf, status) ? 1 : 0;
+        if (w == 0) {
+            // lanes 0 and 1 wait for the left and right neighbours' values < n
+            bool ok = true;
+            if (lane < 2 && (lane == 0 ? has_l : has_r))
+                ok = wait_one(kg + (lane == 0 ? -1 : 1), n * S1, progress, abortf, status);
+            ok = __all_sync(0xffffffffu, ok);
+            if (lane == 0) s_go = ok ? 1 : 0;
+        }
         __syncthreads();                                       // B1: values < n visible
         if (!s_go) break;
-        if (solver) {
+        if (w == 0) {
             // history of step n: partial (lags >= 2, computed during step n-1) + lag 1
-            double2 h[4];
-            for (int e = 0; e < 4; ++e) {
-                h[e] = hp[n & 1][e];
-                if (n >= 1 && hs[e]) h[e] = cfma(c1[e], xs[e][n - 1], h[e]);
+            double2 r1 = zero, r2 = zero;
+            if (solver) {
+                double2 h[4];
+                for (int e = 0; e < 4; ++e) {
+                    h[e] = hp[n & 1][e];
+                    if (n >= 1 && hs[e]) h[e] = cfma(c1[e], xs[e][n - 1], h[e]);
+                }
+                r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(h[0], h[1]));
+                r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(h[2], h[3]));
             }
-            const double2 r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(h[0], h[1]));
-            const double2 r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(h[2], h[3]));
-            double2 z1 = cfma(D01, r2, cmul(D00, r1));
-            double2 z2 = cfma(D11, r2, cmul(D10, r1));
-            for (int sw = 1; sw <= sweeps; ++sw) {
-                // publish sweep sw-1 of this step, then use the neighbours' sweep sw-1
-                double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif_all;
-                out[2 * kg] = z1;
-                out[2 * kg + 1] = z2;
-                store_release(progress + kg, n * S1 + sw);
-                if (!wait_neighbours(kg, has_l, has_r, n * S1 + sw, progress, abortf, status)) break;
-                const double2 xr = has_r ? out[2 * (kg + 1)] : zero;       // r_{k+1}
-                const double2 xl = has_l ? out[2 * (kg - 1) + 1] : zero;   // l_k
-                const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
-                z1 = cfma(D01, e2, cmul(D00, e1));
-                z2 = cfma(D11, e2, cmul(D10, e1));
+            double2 z1 = zero, z2 = zero;
+            if (H > 0) {
+                // publish R_n(k); lane H + d waits for interface k + d and forms its
+                // term G_{k,k+d} R_n(k+d); the warp sums the terms
+                double2* out = xsw + (size_t)(n & 1) * 2 * nif_all;
+                if (solver) {
+                    out[2 * kg] = r1;
+                    out[2 * kg + 1] = r2;
+                    store_release(progress + kg, n * 2 + 1);
+                }
+                r1.x = __shfl_sync(0xffffffffu, r1.x, 0);
+                r1.y = __shfl_sync(0xffffffffu, r1.y, 0);
+                r2.x = __shfl_sync(0xffffffffu, r2.x, 0);
+                r2.y = __shfl_sync(0xffffffffu, r2.y, 0);
+                const int d = lane - H;
+                bool ok = true;
+                double2 t1 = zero, t2 = zero;
+                if (d >= dlo && d <= dhi) {
+                    double2 q1 = r1, q2 = r2;
+                    if (d != 0) {
+                        ok = wait_one(kg + d, n * 2 + 1, progress, abortf, status);
+                        if (ok) {
+                            q1 = out[2 * (kg + d)];
+                            q2 = out[2 * (kg + d) + 1];
+                        }
+                    }
+                    if (ok) {
+                        const double2* g = Gk + (d + H) * 4;
+                        t1 = cfma(g[0], q1, cmul(g[1], q2));
+                        t2 = cfma(g[2], q1, cmul(g[3], q2));
+                    }
+                }
+                (void)__all_sync(0xffffffffu, ok);     // a failed wait has raised the abort flag
+                z1 = warp_sum(t1);
+                z2 = warp_sum(t2);
+            } else if (solver) {
+                z1 = cfma(D01, r2, cmul(D00, r1));
+                z2 = cfma(D11, r2, cmul(D10, r1));
+                for (int sw = 1; sw <= sweeps; ++sw) {
+                    // publish sweep sw-1 of this step, then use the neighbours' sweep sw-1
+                    double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif_all;
+                    out[2 * kg] = z1;
+                    out[2 * kg + 1] = z2;
+                    store_release(progress + kg, n * S1 + sw);
+                    if (!wait_neighbours(kg, has_l, has_r, n * S1 + sw, progress, abortf, status))
+                        break;
+                    const double2 xr = has_r ? out[2 * (kg + 1)] : zero;       // r_{k+1}
+                    const double2 xl = has_l ? out[2 * (kg - 1) + 1] : zero;   // l_k
+                    const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
+                    z1 = cfma(D01, e2, cmul(D00, e1));
+                    z2 = cfma(D11, e2, cmul(D10, e1));
+                }
             }
-            x[(size_t)(2 * k) * nt + n] = z1;
-            x[(size_t)(2 * k + 1) * nt + n] = z2;
-            store_release(progress + kg, (n + 1) * S1);        // orders the x writes above
-        } else if (w >= 1) {
+            if (solver) {
+                x[(size_t)(2 * k) * nt + n] = z1;
+                x[(size_t)(2 * k + 1) * nt + n] = z2;
+                store_release(progress + kg, (n + 1) * S1);    // orders the x writes above
+            }
+        } else {
             // step n+1's history from values s <= n-1 (lags >= 2)
             double2 acc = zero;
             if (has && n + 1 < nt)
@@ -820,7 +985,8 @@ int swr_causal_capacity(int) {
 int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, const double2* y,
                       double2* x, int sweeps, void* scratch, int* status, cudaStream_t s,
                       const InstInfo* inst, const int* if_inst, int k0, int nif_group,
-                      int nif_total) {
+                      int nif_total, const double2* Gw, int H) {
+    if (H < 0 || H > kWinMaxH || (H > 0 && !Gw)) return -2;
     const int nif = inst ? nif_total : N - 1;
     const int ncta = inst ? nif_group : N - 1;
     if (!inst) k0 = 0;
@@ -837,7 +1003,8 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, c
         return -1;
     void* args[] = {(void*)&N, (void*)&nt, (void*)&sweeps, (void*)&cols, (void*)&lag0,
                     (void*)&y, (void*)&x, (void*)&xsw, (void*)&progress, (void*)&abortf,
-                    (void*)&status, (void*)&inst, (void*)&if_inst, (void*)&k0, (void*)&nif};
+                    (void*)&status, (void*)&inst, (void*)&if_inst, (void*)&k0, (void*)&nif,
+                    (void*)&Gw, (void*)&H};
     if (cudaLaunchCooperativeKernel((const void*)k_causal_wave, dim3(ncta), dim3(160), args, 0, s) !=
         cudaSuccess)
         return -1;

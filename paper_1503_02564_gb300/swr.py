@@ -21,7 +21,7 @@ SWR_ERR_NONFINITE, SWR_ERR_TIMEOUT, SWR_ERR_NOMEM, SWR_ERR_CUDA = 4, 5, 6, 7
 SWR_ERR_STATE, SWR_ERR_UNSUPPORTED = 8, 9
 SWR_V_STATIC, SWR_V_TIME, SWR_V_NONLINEAR = 0, 1, 2
 SWR_TC_ROBIN, SWR_TC_S02 = 0, 1
-SWR_SOLVER_GMRES, SWR_SOLVER_FIXED_POINT, SWR_SOLVER_CLASSICAL = 0, 1, 2
+SWR_SOLVER_GMRES, SWR_SOLVER_FIXED_POINT, SWR_SOLVER_CLASSICAL, SWR_SOLVER_CAUSAL = 0, 1, 2, 3
 SWR_PC_NONE, SWR_PC_ZERO_POTENTIAL, SWR_PC_CAUSAL, SWR_PC_MEAN_POTENTIAL = 0, 1, 2, 3
 # swr_stats.march_variant
 MARCH_CONSTANT, MARCH_TDEP_REFACTOR, MARCH_NONLINEAR, MARCH_TDEP_STREAMED = 0, 1, 2, 3
@@ -63,7 +63,7 @@ class swr_stats(ctypes.Structure):
         ("march_point_iterations", ctypes.c_int64),
         ("nl_march_launches", ctypes.c_int64), ("nl_march_ms", ctypes.c_double),
         ("superposed", ctypes.c_int32), ("toeplitz_fft_length", ctypes.c_int32),
-        ("causal_sweeps", ctypes.c_int32),
+        ("causal_sweeps", ctypes.c_int32), ("causal_window", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -367,3 +367,87 @@ def test_toeplitz_apply_fft_and_direct_match_oracle(case, fft):
     plan.apply_interface(xi, y)
     plan.destroy()
     assert rel(y.cpu().numpy(), O.apply_I_minus_L(P, cols, x)) < TOL_MARCH
+
+
+def narrow(nsub=500, nx=20001, nt=40):
+    """0.2-wide subdomains (40 intervals at h = 0.005, dt = 1e-3): the same-step
+    coupling of neighbouring interfaces (lag-0 corner entries ~3e-4) matters."""
+    return W.config2(nsub=nsub, nx=nx, nt=nt)
+
+
+@pytest.mark.parametrize("pc_sweeps", [-1, 0, 1])
+def test_causal_window_makes_the_preconditioner_exact(pc_sweeps):
+    """pc_sweeps < 0 on narrow subdomains picks the window form (causal_window >= 1):
+    P^{-1} is (I - L)^{-1} to rounding, so right-preconditioned GMRES converges in
+    one iteration; 0 or 1 sweeps converge to the same solution in more."""
+    from paper_1503_02564_gb300 import swr
+    wl = narrow()
+    plan = gpu_plan(wl, precond=swr.SWR_PC_CAUSAL, restart=30, tol_abs=1e-11,
+                    pc_sweeps=pc_sweeps)
+    st = plan.get_stats()
+    g, uT, info = _solve(plan, wl)
+    plan.destroy()
+    if pc_sweeps < 0:
+        assert st["causal_window"] >= 1 and st["causal_sweeps"] == 0, st
+        assert info["iterations"] == 1, info
+    else:
+        assert st["causal_window"] == 0 and st["causal_sweeps"] == pc_sweeps
+        assert info["iterations"] > 1, info
+    gs, uTm = _narrow_mono(wl)
+    assert info["residual"] < 1e-11
+    assert rel(uT, uTm) < TOL_SOLVE
+    assert rel(g, gs) < TOL_SOLVE
+
+
+_NARROW = {}
+
+
+def _narrow_mono(wl):
+    if "m" not in _NARROW:
+        _NARROW["m"] = O.mono_interface(problem(wl))
+    return _NARROW["m"]
+
+
+def test_causal_window_precondition_is_near_identity():
+    """(I - L) P^{-1} y = y to ~1e-13 with the window form (the same check with
+    no same-step coupling resolved stays at the size of the dropped corners)."""
+    from paper_1503_02564_gb300 import swr
+    wl = narrow(nt=24)
+    P = problem(wl)
+    cols = O.build_columns(P)
+    y = W.random_interface(wl.nblk, wl.nt, 12)
+    yi = torch.tensor(y.ravel(), dtype=torch.complex128, device="cuda")
+    errs = []
+    for sw in (-1, 0):
+        plan = gpu_plan(wl, precond=swr.SWR_PC_CAUSAL, pc_sweeps=sw)
+        x = torch.zeros_like(yi)
+        plan.apply_precond(yi, x)
+        plan.destroy()
+        errs.append(rel(O.apply_I_minus_L(P, cols, x.cpu().numpy()), y))
+    assert errs[0] < 1e-12, errs
+    assert errs[1] > 1e-8, errs
+
+
+@pytest.mark.parametrize("case", ["config1_small", "ragged_tiny", "config2_N16_small", "narrow"])
+def test_direct_causal_solver_reproduces_monodomain(case):
+    """SWR_SOLVER_CAUSAL: (I - L) g = d by block forward substitution in time, no
+    Krylov iteration; one or two substitutions reach the tolerance."""
+    from paper_1503_02564_gb300 import swr
+    wl = narrow() if case == "narrow" else CASES[case]()
+    plan = gpu_plan(wl, solver=swr.SWR_SOLVER_CAUSAL, maxit=20, tol_abs=1e-11)
+    g, uT, info = _solve(plan, wl)
+    plan.destroy()
+    assert info["status"] == swr.SWR_OK, info
+    assert info["iterations"] <= 2, info
+    gs, uTm = _narrow_mono(wl) if case == "narrow" else O.mono_interface(problem(wl))
+    assert rel(uT, uTm) < TOL_SOLVE
+    assert rel(g, gs) < TOL_SOLVE
+
+
+def test_direct_causal_solver_rejects_time_dependent_potential():
+    from paper_1503_02564_gb300 import swr
+    wl = W.config4(nsub=4, nx=801, nt=20)
+    with pytest.raises(swr.SWRError) as e:
+        swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
+                 node_off=wl.off, vkind=swr.SWR_V_TIME, solver=swr.SWR_SOLVER_CAUSAL)
+    assert e.value.status == swr.SWR_ERR_ARG

@@ -26,6 +26,7 @@ struct Workspace {
     long long n = 0;
     int m = 0;
     double2* V = nullptr;       // (m+1) x n Krylov basis
+    double2* Z = nullptr;       // m x n preconditioned basis vectors P^{-1} v_j (preconditioned runs)
     double2* w = nullptr;       // n
     double2* z = nullptr;       // n
     double2* r = nullptr;       // n
@@ -793,7 +794,7 @@ swr_status ensure_workspace(swr_plan_t p) {
     if (w.V && w.m == m && w.n == n) return SWR_OK;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
     cudaFree(w.sn); cudaFree(w.sv); cudaFree(w.y); cudaFree(w.h); cudaFree(w.partial);
-    cudaFree(w.res);
+    cudaFree(w.res); cudaFree(w.Z);
     w = Workspace();
     w.n = n;
     w.m = m;
@@ -923,6 +924,9 @@ swr_status gmres(swr_plan_t p, const double2* b, double tol, double2* g, bool g_
     const long long n = w.n;
     const int m = w.m, ldh = m + 1;
     const bool pc = has_precond(p);
+    // the preconditioned basis is kept, so the update g += P^{-1} V y = Z y costs no
+    // further substitution
+    if (pc && !w.Z && (st = dalloc(&w.Z, (size_t)m * n))) return st;
     if (!g_init) CK(cudaMemsetAsync(g, 0, sizeof(double2) * n, p->s));
     // r = b - A g
     if (g_init) {
@@ -950,8 +954,9 @@ swr_status gmres(swr_plan_t p, const double2* b, double tol, double2* g, bool g_
             double2* vj = w.V + (size_t)j * n;
             const double2* av = vj;
             if (pc) {
-                if ((st = apply_M(p, vj, w.z))) return st;
-                av = w.z;
+                double2* zj = w.Z + (size_t)j * n;
+                if ((st = apply_M(p, vj, zj))) return st;
+                av = zj;
             }
             if ((st = apply_A(p, av, w.w))) return st;
             double2* Hc = w.H + (size_t)j * ldh;
@@ -975,16 +980,9 @@ swr_status gmres(swr_plan_t p, const double2* b, double tol, double2* g, bool g_
             if (!std::isfinite(est)) return SWR_ERR_NONFINITE;
             if (est < tol) break;
         }
-        // g += M^{-1} V_k y
+        // g += P^{-1} V_k y = Z_k y
         LK(swr_launch_lsq(w.H, ldh, w.sv, k, w.y, p->s));
-        CK(cudaMemsetAsync(w.w, 0, sizeof(double2) * n, p->s));
-        LK(swr_launch_gemv_sub(w.V, n, k, w.y, w.w, n, 1.0, p->s));
-        if (pc) {
-            if ((st = apply_M(p, w.w, w.z))) return st;
-            LK(swr_launch_axpby(g, w.z, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s));
-        } else {
-            LK(swr_launch_axpby(g, w.w, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s));
-        }
+        LK(swr_launch_gemv_sub(pc ? w.Z : w.V, n, k, w.y, g, n, 1.0, p->s));
         // true residual
         if ((st = apply_A(p, g, w.r))) return st;
         LK(swr_launch_axpby(w.r, b, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s));

@@ -54,7 +54,7 @@ def lib():
             ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
             dp, ctypes.c_long, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
-            ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp, ip, ctypes.c_int, ip, dp]
+            ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp, dp, ip, ctypes.c_int, ip, dp, dp, dp]
         L.or_thomas.restype = ctypes.c_int
         L.or_thomas.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
         L.or_p1_matrices.restype = None
@@ -123,6 +123,13 @@ def beta_coefficients(n):
     return a * np.where(np.arange(n + 1) % 2 == 0, 1.0, -1.0)
 
 
+def gamma_coefficients(n):
+    """gamma_0..gamma_n of Section 2.2: (1, 2, 2, 2, ...)."""
+    g = np.full(n + 1, 2.0)
+    g[0] = 1.0
+    return g
+
+
 def s02_c2(dt):
     """c_2 = e^{-i pi/4} sqrt(2/dt) (S_0^2, Section 2.2)."""
     return np.exp(-1j * math.pi / 4) * math.sqrt(2.0 / dt)
@@ -143,7 +150,9 @@ def partition_equal(nx, nsub):
 # --------------------------------------------------------------------------
 # Problem description
 # --------------------------------------------------------------------------
-TC_ROBIN, TC_S02 = 0, 1
+TC_ROBIN, TC_S02, TC_S03, TC_S04, TC_S12, TC_S14 = 0, 1, 2, 3, 4, 5
+TC_NAMES = {TC_ROBIN: "Robin", TC_S02: "S_0^2", TC_S03: "S_0^3", TC_S04: "S_0^4",
+            TC_S12: "S_1^2", TC_S14: "S_1^4"}
 V_STATIC, V_TIME, V_NONLINEAR = 0, 1, 2
 
 
@@ -218,9 +227,10 @@ class MarchResult:
 
 def march(n, h, dt, nt, V, u0, *, vkind=V_STATIC, tc=TC_ROBIN, sigma=0.0, tc_left=False,
           tc_right=False, l=None, r=None, nl_coef=1.0, nl_maxit=50, nl_tol=1e-13,
-          sel=None) -> MarchResult:
+          sel=None, wl=None, wr=None) -> MarchResult:
     """One Crank-Nicolson march on n nodes (Eq. AvML / AvMNL); see or_march in
-    swr_oracle.c for the exact statement."""
+    swr_oracle.c for the exact statement.  tc >= TC_S03: the ends' S-bar are given
+    by their weight matrices wl, wr ((nt+1) x (nt+1), S-bar v_n = sum_s w[n, s] v_s)."""
     V = np.ascontiguousarray(V, dtype=np.float64)
     vstride = V.shape[1] if V.ndim == 2 else 0
     u0 = np.ascontiguousarray(u0, dtype=np.complex128)
@@ -239,10 +249,16 @@ def march(n, h, dt, nt, V, u0, *, vkind=V_STATIC, tc=TC_ROBIN, sigma=0.0, tc_lef
     else:
         vsel = None
     sig = complex(sigma)
-    st = lib().or_march(n, h, dt, nt, vkind, _p(V), vstride, nl_coef, nl_maxit, nl_tol, tc,
+    ctc = tc if tc <= TC_S02 else 2          # the C march: 0 Robin, 1 S_0^2, 2 weights
+    wlc = None if (wl is None or not tc_left) else np.ascontiguousarray(wl, np.complex128)
+    wrc = None if (wr is None or not tc_right) else np.ascontiguousarray(wr, np.complex128)
+    if ctc == 2 and ((tc_left and wlc is None) or (tc_right and wrc is None)):
+        raise ValueError("weights needed at every end with a transmission condition")
+    st = lib().or_march(n, h, dt, nt, vkind, _p(V), vstride, nl_coef, nl_maxit, nl_tol, ctc,
                         sig.real, sig.imag, c2.real, c2.imag, _p(beta), int(tc_left),
                         int(tc_right), _p(u0), _p(lc), _p(rc), _p(va), _p(vb), _p(uT),
-                        _ip(its), 0 if sel is None else len(sel), _ip(sel), _p(vsel))
+                        _ip(its), 0 if sel is None else len(sel), _ip(sel), _p(vsel),
+                        _p(wlc), _p(wrc))
     if st == -1000000:
         raise RuntimeError("nonlinear fixed point did not converge")
     if st != 0:
@@ -250,27 +266,95 @@ def march(n, h, dt, nt, V, u0, *, vkind=V_STATIC, tc=TC_ROBIN, sigma=0.0, tc_lef
     return MarchResult(va, vb, uT, its, vsel)
 
 
+def tc_weights(P: Problem, j, side, V=None):
+    """Weights w[n, s], 0 <= s <= n <= nt, of the discrete transmission operator at one
+    end of subdomain j (side 0: a_j, side 1: b_j), S-bar v_n = sum_s w[n, s] v_s, written
+    out from the discrete operators of Section 2.2 for V = V(x):
+      S_0^2: c2 beta_{n-s},  c2 = e^{-i pi/4} sqrt(2/dt);
+      S_0^3: S_0^2 - e^{i pi/4} sqrt(dt/2) (W_n / 2) alpha_{n-s};
+      S_0^4: S_0^3 - i (d_n W_n / 4) (dt/2) gamma_{n-s};
+      S_1^2: c2 e^{i Wc_n} beta_{n-s} e^{-i Wc_s};
+      S_1^4: S_1^2 - i sgn(d_n W_n) (sqrt|d_n W_n| / 2) e^{i Wc_n} (dt/2) gamma_{n-s}
+                     (sqrt|d_n W_s| / 2) e^{-i Wc_s}.
+    Readings: W_n is the potential at the end node (W_n = (V_n + V_{n-1})/2 = V there);
+    d_n W its outward normal derivative at the end, the central difference on the whole
+    grid (the end is an interior node of the whole grid), sign + at b_j and - at a_j;
+    Wc_n = (Vc_n + Vc_{n-1})/2 with Vc_n = int_0^{t_n} V ds = t_n V, and Wc_0 = 0 (Vc_{-1}
+    is not defined); sgn(0) = 0."""
+    if P.vkind != V_STATIC:
+        raise NotImplementedError("S_0^3, S_0^4, S_1^2, S_1^4: V = V(x) only")
+    V = P.V if V is None else V
+    nt, dt, h = P.nt, P.dt, P.h
+    g = int(P.off[j + side])
+    Wb = float(V[g])
+    dn = (float(V[g + 1]) - float(V[g - 1])) / (2.0 * h) * (1.0 if side == 1 else -1.0)
+    al, be, ga = alpha_coefficients(nt), beta_coefficients(nt), gamma_coefficients(nt)
+    c2 = s02_c2(dt)
+    c3 = np.exp(1j * math.pi / 4) * math.sqrt(dt / 2.0)
+    Wc = np.array([0.0] + [(n - 0.5) * dt * Wb for n in range(1, nt + 1)])
+    w = np.zeros((nt + 1, nt + 1), np.complex128)
+    for n in range(nt + 1):
+        for s_ in range(n + 1):
+            m = n - s_
+            if P.tc in (TC_S03, TC_S04):
+                x = c2 * be[m] - c3 * (Wb / 2.0) * al[m]
+                if P.tc == TC_S04:
+                    x += -1j * (dn / 4.0) * (dt / 2.0) * ga[m]
+            elif P.tc in (TC_S12, TC_S14):
+                ph = np.exp(1j * Wc[n]) * np.exp(-1j * Wc[s_])
+                x = c2 * ph * be[m]
+                if P.tc == TC_S14:
+                    r = math.sqrt(abs(dn)) / 2.0
+                    x += -1j * np.sign(dn) * r * ph * (dt / 2.0) * ga[m] * r
+            else:
+                raise ValueError("tc_weights: S_0^3, S_0^4, S_1^2 or S_1^4")
+            w[n, s_] = x
+    return w
+
+
 def sub_march(P: Problem, j, u0_local, l=None, r=None, V=None) -> MarchResult:
     """March of subdomain j (0-based) with fluxes l, r (Eq. AvML with
     Eq. TransmissionCondlocal); outer ends keep the Neumann condition."""
     a, b = int(P.off[j]), int(P.off[j + 1])
+    wl = wr = None
+    if P.tc >= TC_S03:
+        wl = tc_weights(P, j, 0, V) if j > 0 else None
+        wr = tc_weights(P, j, 1, V) if j < P.nsub - 1 else None
     return march(b - a + 1, P.h, P.dt, P.nt, P.local_V(j, V), u0_local, vkind=P.vkind,
                  tc=P.tc, sigma=P.sigma, tc_left=(j > 0), tc_right=(j < P.nsub - 1),
-                 l=l, r=r, nl_coef=P.nl_coef, nl_maxit=P.nl_maxit, nl_tol=P.nl_tol)
+                 l=l, r=r, nl_coef=P.nl_coef, nl_maxit=P.nl_maxit, nl_tol=P.nl_tol,
+                 wl=wl, wr=wr)
 
 
-def s_tilde(P: Problem, vtrace):
+def s_tilde(P: Problem, vtrace, j=None, side=None, V=None):
     """Fully discrete S-tilde applied to a boundary trace v_0..v_nt; returns
     entries for n = 1..nt (Eq. TransmissionCond_disc).  Robin: sigma v_n.
-    S_0^2: c_2 sum_{s=0}^{n} beta_{n-s} v_s."""
+    S_0^2: c_2 sum_{s=0}^{n} beta_{n-s} v_s.  S_0^3, S_0^4, S_1^2, S_1^4: the weights
+    of tc_weights at end `side` of subdomain j."""
     if P.tc == TC_ROBIN:
         return P.sigma * vtrace[1:]
+    if P.tc >= TC_S03:
+        return (tc_weights(P, j, side, V) @ np.asarray(vtrace, np.complex128))[1:]
     beta = P.beta()
     nt = P.nt
     out = np.zeros(nt, np.complex128)
     for n in range(1, nt + 1):
         out[n - 1] = P.c2() * np.dot(beta[n::-1][: n + 1], vtrace[: n + 1])
     return out
+
+
+def s_flux(P: Problem, vtrace, j, side, V=None):
+    """The operator the flux update of Eq. TransmisionCond applies to the trace of
+    subdomain j at its end `side`: l_{j+1} = -r_j + (S_j + S_{j+1}) v_j(b_j) and
+    r_{j-1} = -l_j + (S_j + S_{j-1}) v_j(a_j), the sum of the two subdomains'
+    operators at the interface.  Reading: the paper prints 2 S-bar, which is this sum
+    whenever the two sides' operators agree (Robin, S_0^2, S_0^3, S_1^2); for S_0^4 and
+    S_1^4 the d_n W terms of the two sides have opposite signs and cancel in the sum,
+    which is what makes converged SWR reproduce the monodomain solution."""
+    nb, nside = (j + 1, 0) if side == 1 else (j - 1, 1)
+    if P.tc >= TC_S03:
+        return s_tilde(P, vtrace, j, side, V) + s_tilde(P, vtrace, nb, nside, V)
+    return 2.0 * s_tilde(P, vtrace)
 
 
 def apply_R(P: Problem, g, *, zero_u0=False, V=None):
@@ -288,9 +372,9 @@ def apply_R(P: Problem, g, *, zero_u0=False, V=None):
         rj = g[blk_r(j)] if j < N - 1 else None
         m = sub_march(P, j, u0, lj, rj, V=V)
         if j > 0:
-            out[blk_r(j - 1)] = -lj + 2.0 * s_tilde(P, m.va)
+            out[blk_r(j - 1)] = -lj + s_flux(P, m.va, j, 0, V)
         if j < N - 1:
-            out[blk_l(j + 1)] = -rj + 2.0 * s_tilde(P, m.vb)
+            out[blk_l(j + 1)] = -rj + s_flux(P, m.vb, j, 1, V)
     return out
 
 
@@ -327,12 +411,12 @@ def build_columns(P: Problem, mode="zero_u0", d=None, V=None):
             pa = 0 if which == "l" else 1     # X^{j,1} / X^{j,2}: output r_{j-1}
             pb = 2 if which == "l" else 3     # X^{j,3} / X^{j,4}: output l_{j+1}
             if j > 0:
-                col = -lj + 2.0 * s_tilde(P, m.va)
+                col = -lj + s_flux(P, m.va, j, 0, V)
                 if mode == "minus_d":
                     col = col - d[blk_r(j - 1)]
                 cols[j, pa] = col
             if j < N - 1:
-                col = -rj + 2.0 * s_tilde(P, m.vb)
+                col = -rj + s_flux(P, m.vb, j, 1, V)
                 if mode == "minus_d":
                     col = col - d[blk_l(j + 1)]
                 cols[j, pb] = col
@@ -688,9 +772,8 @@ def mono_interface(P: Problem):
         dnr = (I2 * (h / 3 * (u0_ - v0) + h / 6 * (up - vp)) + (v0 - vp) / h
                - (h / 12 * (3 * W0 + Wp) * v0 + h / 12 * (W0 + Wp) * vp))
         vtrace = vs[:, 3 * q + 1]
-        sbar = s_tilde(P, vtrace)
-        g[blk_r(j)] = dnl + sbar
-        g[blk_l(j + 1)] = dnr + sbar
+        g[blk_r(j)] = dnl + s_tilde(P, vtrace, j, 1)
+        g[blk_l(j + 1)] = dnr + s_tilde(P, vtrace, j + 1, 0)
     return g, m.uT
 
 

@@ -105,6 +105,10 @@ int or_thomas(int n, const cplx *lo, const cplx *dg, const cplx *up, cplx *x,
  *   tc == 1, S_0^2:   S-bar v_n = c2 sum_{s=0}^{n} beta_{n-s} v_s
  *                     -> sigma0 = c2 beta_0, b_n = c2 sum_{s=0}^{n-1} beta_{n-s} v_s
  *                        at that end (sign from the proof of Prop. 1), v_0 = u_0.
+ *   tc == 2, any S-bar linear in the trace: S-bar v_n = sum_{s=0}^{n} w[n][s] v_s
+ *                     with w given per end (wl, wr: (nt+1) x (nt+1), row n holds
+ *                     s = 0..n) -> the end's matrix entry at step n is w[n][n] and
+ *                     b_n = sum_{s<n} w[n][s] v_s (S_0^3, S_0^4, S_1^2, S_1^4).
  *
  * Potential (vkind):
  *   0  static V(x): V has n entries;
@@ -120,7 +124,8 @@ int or_thomas(int n, const cplx *lo, const cplx *dg, const cplx *up, cplx *x,
  *      or after nl_maxit iterations.
  *
  * Inputs (interleaved complex): u0 (n), l and r (nt each; entry n_step-1 is the
- * flux of step n_step; NULL means zero), beta (nt+1, used when tc == 1).
+ * flux of step n_step; NULL means zero), beta (nt+1, used when tc == 1), wl and
+ * wr (used when tc == 2, NULL at an end without a transmission condition).
  * Outputs: va, vb (nt+1 each; entry t is v_t at the left / right end, entry 0
  * is u_0 there), uT (n, u at the final time), nl_iters (nt, inner counts;
  * optional), vsel (optional: (nt+1) x nsel values of v_t at the nodes sel[]).
@@ -132,8 +137,11 @@ int or_march(int n, double h, double dt, int nt, int vkind, const double *V,
              double sig_re, double sig_im, double c2_re, double c2_im,
              const double *beta, int tc_left, int tc_right, const double *u0_,
              const double *l_, const double *r_, double *va_, double *vb_,
-             double *uT_, int *nl_iters, int nsel, const int *sel, double *vsel_)
+             double *uT_, int *nl_iters, int nsel, const int *sel, double *vsel_,
+             const double *wl_, const double *wr_)
 {
+    const cplx *wl = (const cplx *)wl_, *wr = (const cplx *)wr_;
+    const long nw = nt + 1;
     const cplx I2dt = 2.0 * I / dt;
     const cplx sigma = sig_re + I * sig_im;
     const cplx c2 = c2_re + I * c2_im;
@@ -175,8 +183,8 @@ int or_march(int n, double h, double dt, int nt, int vkind, const double *V,
         /* Matrix A_n - B_n (complex symmetric tridiagonal). */
         for (i = 0; i < n; ++i) dg[i] = I2dt * md[i] - sd[i] + wd[i];
         for (i = 0; i < n - 1; ++i) lo[i] = I2dt * mo[i] - so[i] + wo[i];
-        if (tc_left) dg[0] -= sigma0;
-        if (tc_right) dg[n - 1] -= sigma0;
+        if (tc_left) dg[0] -= (tc == 2) ? wl[(long)t * nw + t] : sigma0;
+        if (tc_right) dg[n - 1] -= (tc == 2) ? wr[(long)t * nw + t] : sigma0;
 
         /* (2i/dt) M u_{n-1} */
         for (i = 0; i < n; ++i) {
@@ -197,6 +205,19 @@ int or_march(int n, double h, double dt, int nt, int vkind, const double *V,
                 cplx acc = 0.0;
                 for (s = 0; s < t; ++s) acc += beta[t - s] * vb[s];
                 rhs0[n - 1] += c2 * acc;
+            }
+        }
+        if (tc == 2) {
+            int s;
+            if (tc_left) {
+                cplx acc = 0.0;
+                for (s = 0; s < t; ++s) acc += wl[(long)t * nw + s] * va[s];
+                rhs0[0] += acc;
+            }
+            if (tc_right) {
+                cplx acc = 0.0;
+                for (s = 0; s < t; ++s) acc += wr[(long)t * nw + s] * vb[s];
+                rhs0[n - 1] += acc;
             }
         }
         if (tc_left && l) rhs0[0] -= l[t - 1];

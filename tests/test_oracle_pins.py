@@ -262,6 +262,73 @@ def test_beta_is_taylor_series_of_sqrt_ratio():
     assert np.allclose(coef.real, beta, atol=1e-11)
 
 
+def test_alpha_sum_is_the_half_order_integral():
+    """sqrt(dt/2) sum_{s<=n} alpha_{n-s} f(t_s) is the discrete half-order integral
+    I_t^{1/2} of S_0^3 (Section 2.2; generating function sqrt((1+z)/(1-z)), the
+    trapezoidal convolution quadrature).  For f = 1, I_t^{1/2} 1 = 2 sqrt(t / pi); the
+    error at t = 1 falls with dt."""
+    errs = []
+    for nt in (100, 400, 1600):
+        dt = 1.0 / nt
+        a = O.alpha_coefficients(nt)
+        approx = math.sqrt(dt / 2.0) * a.sum()
+        errs.append(abs(approx - 2.0 / math.sqrt(math.pi)))
+    assert errs[0] < 2e-2 and errs[1] < errs[0] / 1.8 and errs[2] < errs[1] / 1.8, errs
+
+
+def test_gamma_sum_is_the_trapezoidal_integral():
+    """(dt/2) sum_{s<=n} gamma_{n-s} f(t_s) with gamma = (1, 2, 2, ...) integrates the
+    linear f(t) = t exactly: t_n^2 / 2 (S_0^4's I_t, Section 2.2)."""
+    nt, dt = 37, 0.013
+    g = O.gamma_coefficients(nt)
+    for n in range(nt + 1):
+        ts = dt * np.arange(n + 1)
+        val = (dt / 2.0) * np.dot(g[n::-1][: n + 1], ts)
+        assert abs(val - (n * dt) ** 2 / 2.0) <= 1e-14 * max(1.0, (n * dt) ** 2)
+
+
+@pytest.mark.parametrize("tc", [O.TC_S03, O.TC_S04, O.TC_S12, O.TC_S14])
+def test_higher_order_tcs_reduce_to_s02_without_potential(tc):
+    """With V = 0 every potential and gauge TC of Section 2.2 is S_0^2 (W = d_n W = 0,
+    the gauge phase is 1)."""
+    wl = W.config1(nx=61, nt=20, nsub=3)
+    wl.V = np.zeros(wl.nx)
+    P2 = problem(wl, tc=O.TC_S02)
+    P = problem(wl, tc=tc)
+    tr = W.random_interface(1, wl.nt + 1, 4)[0]
+    ref = O.s_tilde(P2, tr)
+    for j, side in ((0, 1), (1, 0), (1, 1), (2, 0)):
+        assert np.abs(O.s_tilde(P, tr, j, side) - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("pair", [(O.TC_S03, O.TC_S04), (O.TC_S12, O.TC_S14)])
+def test_order4_terms_vanish_for_a_flat_potential(pair):
+    """The order-4 terms carry d_n W: a constant potential makes S_0^4 = S_0^3 and
+    S_1^4 = S_1^2, and the two sides of an interface agree."""
+    wl = W.config1(nx=61, nt=20, nsub=3)
+    wl.V = np.full(wl.nx, -3.5)
+    tr = W.random_interface(1, wl.nt + 1, 5)[0]
+    Pa, Pb = problem(wl, tc=pair[0]), problem(wl, tc=pair[1])
+    for j, side in ((0, 1), (1, 0), (1, 1), (2, 0)):
+        a, b = O.s_tilde(Pa, tr, j, side), O.s_tilde(Pb, tr, j, side)
+        assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
+    assert np.abs(O.s_tilde(Pb, tr, 0, 1) - O.s_tilde(Pb, tr, 1, 0)).max() <= \
+        1e-14 * np.abs(O.s_tilde(Pb, tr, 0, 1)).max()
+
+
+def test_order4_sides_differ_and_their_sum_is_order3():
+    """With a sloped potential the two sides of an interface carry opposite d_n W, so
+    S_0^4 differs between them while their sum (the flux update's operator) is
+    2 S_0^3."""
+    wl = W.config1(nx=61, nt=20, nsub=3)
+    tr = W.random_interface(1, wl.nt + 1, 6)[0]
+    P3, P4 = problem(wl, tc=O.TC_S03), problem(wl, tc=O.TC_S04)
+    left, right = O.s_tilde(P4, tr, 0, 1), O.s_tilde(P4, tr, 1, 0)
+    assert np.abs(left - right).max() > 1e-6 * np.abs(left).max()
+    assert np.abs(O.s_flux(P4, tr, 0, 1) - 2.0 * O.s_tilde(P3, tr, 0, 1)).max() <= \
+        1e-13 * np.abs(left).max()
+
+
 # --------------------------------------------------------------------------
 # Interface problem structure (Props. 1-4) by brute force
 # --------------------------------------------------------------------------
@@ -273,7 +340,7 @@ def _tiny(kind="static", tc=O.TC_ROBIN, nsub=3, nx=31, nt=8):
     return problem(wl, tc=tc)
 
 
-@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
+@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02, O.TC_S03, O.TC_S04, O.TC_S12, O.TC_S14])
 def test_bruteforce_L_is_causal_toeplitz(tc):
     P = _tiny(tc=tc)
     Ld, d = O.dense_L(P)
@@ -330,7 +397,7 @@ def test_columns_minus_d_equals_zero_u0():
 # --------------------------------------------------------------------------
 # Converged SWR equals the monodomain solution
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
+@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02, O.TC_S03, O.TC_S04, O.TC_S12, O.TC_S14])
 def test_swr_new_algorithm_reproduces_monodomain(tc):
     wl = W.config1(nx=241, nt=30, nsub=4)
     P = problem(wl, tc=tc)

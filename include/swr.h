@@ -59,7 +59,18 @@ enum { SWR_V_STATIC = 0, SWR_V_TIME = 1, SWR_V_NONLINEAR = 2 };
  * history sum the end rows and the emitted fluxes.  S_0^2 with V(t,x) needs the
  * streamed per-step factors (swr_build_interface returns SWR_ERR_UNSUPPORTED
  * when they do not fit in half of the free device memory). */
-enum { SWR_TC_ROBIN = 0, SWR_TC_S02 = 1 };
+enum { SWR_TC_ROBIN = 0, SWR_TC_S02 = 1, SWR_TC_S03 = 2, SWR_TC_S04 = 3, SWR_TC_S12 = 4,
+       SWR_TC_S14 = 5 };
+/* SWR_TC_S03, S04 (potential strategy, orders 3 and 4) and S12, S14 (gauge change
+ * strategy, orders 2 and 4), Section 2.2, for SWR_V_STATIC only, with the NONE or
+ * CAUSAL preconditioner.  At an end with node potential W and outward derivative
+ * d_nW (central difference on the whole grid), with c2 = e^{-i pi/4} sqrt(2/dt):
+ *   S03: S-bar v_n = sum_s [c2 beta_{n-s} - e^{i pi/4} sqrt(dt/2) (W/2) alpha_{n-s}] v_s
+ *   S04: S03 - i (d_nW / 4) (dt/2) sum_s gamma_{n-s} v_s,  gamma = (1, 2, 2, ...)
+ *   S12: c2 e^{i Wc_n} sum_s beta_{n-s} e^{-i Wc_s} v_s,  Wc_n = (n - 1/2) dt W, Wc_0 = 0
+ *   S14: S12 - i (d_nW / 4) (dt/2) e^{i Wc_n} sum_s gamma_{n-s} e^{-i Wc_s} v_s.
+ * The flux update applies the sum of the two subdomains' operators at an interface
+ * (2 S-bar when they agree; for S04/S14 the d_nW terms cancel in the sum). */
 /* Interface solvers: GMRES (Algorithms 2-3), fixed point on (I - L) g = d
  * (Algorithm 3 with the fixed point), classical iteration g <- R g with full
  * marches (Algorithm 1).  For SWR_V_NONLINEAR the interface operator R_nl is

@@ -144,6 +144,8 @@ struct swr_plan_s {
     bool auto_sweeps = false;      // pc_sweeps < 0: chosen from the lag-0 corners at the first build
     int causal_H = 0;              // >= 1: window form of the substitution (exact lag-0 solve)
     double2* d_Gw = nullptr;       // rows of the lag-0 inverse, [nif][2H+1][4]
+    // S_0^3, S_0^4, S_1^2, S_1^4: per-end kernels (own, flux update) and s = 0 factors
+    double2 *d_kap = nullptr, *d_kout = nullptr, *d_rho = nullptr;
     bool built = false;
     bool have_L0 = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -496,7 +498,13 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     a.gl = seg.gl;
     a.gr = seg.gr;
     a.h12 = p->h / 12.0;
-    if (p->d.tc == SWR_TC_S02) {
+    if (p->d.tc >= SWR_TC_S03 && !zero_potential) {
+        a.kap = p->d_kap;
+        a.kout = p->d_kout;
+        a.rho = p->d_rho;
+        a.kstride = p->nt + 1;
+    }
+    if (p->d.tc >= SWR_TC_S02) {
         a.s02 = 1;
         a.beta = p->d_beta;
         a.hist = p->d_s02hist;
@@ -708,8 +716,16 @@ swr_status factor_steps_for(swr_plan_t p, FactorSet& fs, int L, int nsteps) {
 }
 
 swr_status assemble(swr_plan_t p, const double* V, double2* dg, double2* od) {
+    // the higher-order conditions: the ends' kernels from this V first (their lag-0
+    // entries are the boundary matrix entries)
+    const bool gen = p->d_kap && dg == p->d_dg;
+    if (gen)
+        LK(swr_launch_tc_kernels(p->d.tc, V, p->N, p->d_n, p->d_goff, p->d_tc, p->nt + 1, p->h,
+                                 p->d.dt, p->d_beta, p->c2, p->d_kap, p->d_kout, p->d_rho,
+                                 p->s));
     swr_launch_assemble_static(V, p->N, p->d_n, p->d_goff, p->d_loff, p->d_tc, p->nmax, p->h,
-                               p->d.dt, p->sigma0, p->inv_ik, dg, od, p->s);
+                               p->d.dt, p->sigma0, p->inv_ik, dg, od, p->s,
+                               gen ? p->d_kap : nullptr, p->nt + 1);
     CK(cudaGetLastError());
     return SWR_OK;
 }
@@ -1265,6 +1281,7 @@ void swr_destroy(swr_plan_t p) {
     cudaFree(p->d_status); cudaFree(p->d_scal); cudaFree(p->d_pit);
     cudaFree(p->d_urec); cudaFree(p->d_rec_base);
     cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0); cudaFree(p->d_Gw);
+    cudaFree(p->d_kap); cudaFree(p->d_kout); cudaFree(p->d_rho);
     Workspace& w = p->ws;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
     cudaFree(w.sn); cudaFree(w.sv); cudaFree(w.y); cudaFree(w.h); cudaFree(w.partial);
@@ -1287,8 +1304,13 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
         if (e.nx < 3 || e.nt < 1 || !(e.dt > 0.0) || e.nsub < 2 || !(e.b0 > e.a0))
             return SWR_ERR_ARG;
     }
-    if (d->vkind < 0 || d->vkind > 2 || d->tc < SWR_TC_ROBIN || d->tc > SWR_TC_S02)
+    if (d->vkind < 0 || d->vkind > 2 || d->tc < SWR_TC_ROBIN || d->tc > SWR_TC_S14)
         return SWR_ERR_ARG;
+    // the higher-order conditions: V(x) only (their kernels are time invariant there)
+    if (d->tc >= SWR_TC_S03 &&
+        (d->vkind != SWR_V_STATIC || d->precond == SWR_PC_ZERO_POTENTIAL ||
+         d->precond == SWR_PC_MEAN_POTENTIAL))
+        return SWR_ERR_UNSUPPORTED;
     if (d->solver < 0 || d->solver > 3 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
     if (d->solver == SWR_SOLVER_CAUSAL && d->vkind != SWR_V_STATIC) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_NONLINEAR && d->solver == SWR_SOLVER_GMRES) return SWR_ERR_ARG;
@@ -1391,7 +1413,7 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     p->nmax = nmax;
     const double kappa = 2.0 / d->dt * (p->h / 6.0);
     p->inv_ik = make_double2(0.0, -1.0 / kappa);   // 1/(i kappa)
-    if (d->tc == SWR_TC_S02) {
+    if (d->tc >= SWR_TC_S02) {
         // S_0^2 (Section 2.2): S-bar v_n = c2 sum_{s<=n} beta_{n-s} v_s with
         // c2 = e^{-i pi/4} sqrt(2/dt); the s = n term, c2 beta_0 = c2, is the
         // boundary matrix entry sigma0
@@ -1523,7 +1545,14 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
             for (int j = 0; j < I.N; ++j) p->work_R += (long long)p->n[I.sub0 + j] * I.nt;
         st = upload_systems(&p->d_sys_build, vb, p);
     }
-    if (!st && d->tc == SWR_TC_S02) {
+    if (!st && d->tc >= SWR_TC_S03) {
+        // per-end kernels of the higher-order conditions (formed from V at every build)
+        const size_t ne = (size_t)2 * p->N;
+        st = dalloc(&p->d_kap, ne * (p->nt + 1));
+        if (!st) st = dalloc(&p->d_kout, ne * (p->nt + 1));
+        if (!st) st = dalloc(&p->d_rho, ne);
+    }
+    if (!st && d->tc >= SWR_TC_S02) {
         // beta_s = (-1)^s alpha_s, alpha_{2k} = alpha_{2k+1} = prod_{i<=k} (2i-1)/(2i):
         // the coefficients of sqrt((1-z)/(1+z)) (Section 2.2)
         std::vector<double> beta(p->nt + 1);

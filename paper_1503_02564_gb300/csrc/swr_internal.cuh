@@ -67,6 +67,33 @@ __device__ __forceinline__ double2 s02_history(const double* __restrict__ beta,
     return acc;
 }
 
+// The same for a transmission operator with a complex kernel per end (S_0^3, S_0^4,
+// S_1^2, S_1^4 for V(x)): o1 = sum_{s<t} k1[t-s] hist[s] (the end's own operator, for
+// its boundary row) and o2 = sum_{s<t} k2[t-s] hist[s] (the flux update's operator).
+__device__ __forceinline__ void conv_history2(const double2* __restrict__ k1,
+                                              const double2* __restrict__ k2,
+                                              const double2* hist, int t, int lane,
+                                              double2& o1, double2& o2) {
+    double2 a1 = make_double2(0.0, 0.0), a2 = a1;
+    for (int s = lane; s < t; s += 32) {
+        const double2 v = hist[s];
+        const double2 c1 = k1[t - s], c2 = k2[t - s];
+        a1.x = fma(c1.x, v.x, fma(-c1.y, v.y, a1.x));
+        a1.y = fma(c1.x, v.y, fma(c1.y, v.x, a1.y));
+        a2.x = fma(c2.x, v.x, fma(-c2.y, v.y, a2.x));
+        a2.y = fma(c2.x, v.y, fma(c2.y, v.x, a2.y));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a1.x += __shfl_xor_sync(0xffffffffu, a1.x, off);
+        a1.y += __shfl_xor_sync(0xffffffffu, a1.y, off);
+        a2.x += __shfl_xor_sync(0xffffffffu, a2.x, off);
+        a2.y += __shfl_xor_sync(0xffffffffu, a2.y, off);
+    }
+    o1 = a1;
+    o2 = a2;
+}
+
 // ---------------------------------------------------------------------------
 // device status word bits
 // ---------------------------------------------------------------------------
@@ -144,6 +171,16 @@ struct MarchArgs {
     double2* uT;          // nodal output
     double2* trace;       // [nsys][2][nt]
     double2* urec;        // states of the SYS_REC_* systems (NULL: none recorded)
+    // Transmission operators with a kernel per end (S_0^3, S_0^4, S_1^2, S_1^4; NULL:
+    // Robin or S_0^2 from the scalars below).  End e = 2 sub + side:
+    //   kap[e kstride + m]:  the end's own operator, S-bar v_n = sum_s kap[n-s] h_s
+    //                        (kap[0] is its boundary matrix entry);
+    //   kout[e kstride + m]: the flux update's operator (the two sides' sum);
+    //   rho[e]: h_0 = rho v_0 (the gauge strategy's phase at s = 0), h_s = v_s.
+    const double2* kap;
+    const double2* kout;
+    const double2* rho;
+    int kstride;
     long long fstride, sstride, pstride;   // per-step factor strides (0: constant matrix)
     int stage;            // staging of streamed factors in shared memory (0, 1, 2)
     // Ragged packing (C == 1): CTA b holds the systems rag[rag_start[b] .. rag_start[b+1])
@@ -203,7 +240,12 @@ void swr_count_launch(int n);
 int swr_launch_assemble_static(const double* V, int N, const int* d_n, const int* d_goff,
                                const int* d_loff, const int* d_tc, int ntot, double h, double dt,
                                double2 sigma0, double2 inv_ik, double2* dg, double2* od,
-                               cudaStream_t s);
+                               cudaStream_t s, const double2* kap = nullptr, int kstride = 0);
+// Per-end kernels of S_0^3, S_0^4, S_1^2, S_1^4 (tc = SWR_TC_*) from V(x): kap (the end's
+// own operator), kout (the flux update's: both sides' sum) for m < kstride, rho (s = 0).
+int swr_launch_tc_kernels(int tc, const double* V, int N, const int* d_n, const int* d_goff,
+                          const int* d_tc, int kstride, double h, double dt, const double* beta,
+                          double2 c2, double2* kap, double2* kout, double2* rho, cudaStream_t s);
 int swr_launch_row_mean(const double* V, int nrows, long long nx, double* out, cudaStream_t s);
 int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t s, int nsteps = 1,
                      long long ldd = 0);

@@ -62,7 +62,8 @@ __global__ void k_assemble_static(const double* __restrict__ V, long long vstrid
                                   const int* __restrict__ loff_, const int* __restrict__ tc_,
                                   double h, double dt, double2 sigma0, double2 inv_ik,
                                   double2* __restrict__ dg, double2* __restrict__ od,
-                                  long long ldd) {
+                                  long long ldd, const double2* __restrict__ kap = nullptr,
+                                  int kstride = 0) {
     const int j = blockIdx.y;
     const int n = n_[j];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -91,7 +92,9 @@ __global__ void k_assemble_static(const double* __restrict__ V, long long vstrid
         wd += h / 12.0 * (3.0 * W0 + Wp);
     }
     double2 D = make_double2(-sd + wd, 2.0 / dt * md);
-    if ((i == 0 && (tc & 1)) || (i == n - 1 && (tc & 2))) D = csub(D, sigma0);
+    // the end's boundary entry: sigma0, or the lag-0 entry of its own kernel
+    if (i == 0 && (tc & 1)) D = csub(D, kap ? kap[(size_t)(2 * j + 0) * kstride] : sigma0);
+    if (i == n - 1 && (tc & 2)) D = csub(D, kap ? kap[(size_t)(2 * j + 1) * kstride] : sigma0);
     dg[lo] = cmul(D, inv_ik);
     if (i < n - 1) {
         const double Wp = W(g + 1);
@@ -100,6 +103,77 @@ __global__ void k_assemble_static(const double* __restrict__ V, long long vstrid
     } else {
         od[lo] = make_double2(0.0, 0.0);
     }
+}
+
+// Kernels of the higher-order transmission operators for V(x) (Section 2.2).  End
+// e = 2 j + side of subdomain j sits on node g with potential W = V[g] and outward
+// derivative d_nW = +-(V[g+1] - V[g-1]) / 2h (+ at the right end).  For V(x) every
+// operator is a convolution of the end trace, S-bar v_n = sum_s k[n-s] h_s, with
+// h_s = v_s (s >= 1) and h_0 = rho v_0:
+//   S_0^3: k_m = c2 beta_m - e^{i pi/4} sqrt(dt/2) (W/2) alpha_m,            rho = 1;
+//   S_0^4: S_0^3's k_m - i (d_nW/4) (dt/2) gamma_m,                          rho = 1;
+//   S_1^2: k_m = c2 beta_m e^{i m dt W}, since e^{i Wc_n} e^{-i Wc_s} = e^{i (n-s) dt W}
+//          for s >= 1 (Wc_n = (n - 1/2) dt W) and e^{i n dt W} e^{-i dt W/2} for s = 0
+//          (Wc_0 = 0):                                                      rho = e^{-i dt W/2};
+//   S_1^4: k_m = [c2 beta_m - i (d_nW/4) (dt/2) gamma_m] e^{i m dt W}: sgn(d_nW) times the
+//          product of the two sqrt(|d_nW|)/2 factors is d_nW/4;              rho as S_1^2.
+// alpha_m = |beta_m|, gamma = (1, 2, 2, ...).  kout is the flux update's operator, the
+// sum of this end's kernel and the neighbour's at the same node (same W, opposite
+// d_nW).  One thread per (end, m).
+__device__ __forceinline__ double2 tc_kernel_entry(int tc, int m, double b, double W, double dn,
+                                                   double dt, double2 c2) {
+    const double al = fabs(b), ga = (m == 0) ? 1.0 : 2.0;
+    double2 k = make_double2(c2.x * b, c2.y * b);
+    if (tc == 2 || tc == 3) {   // S_0^3, S_0^4
+        const double r = sqrt(0.5 * dt) * 0.5 * W * al;   // e^{i pi/4} = (1 + i) / sqrt(2)
+        k.x -= r * 0.70710678118654752440;
+        k.y -= r * 0.70710678118654752440;
+        if (tc == 3) k.y -= 0.25 * dn * 0.5 * dt * ga;   // - i (d_nW/4)(dt/2) gamma
+        return k;
+    }
+    if (tc == 5) k.y -= 0.25 * dn * 0.5 * dt * ga;      // S_1^4
+    double sn, cs;
+    sincos((double)m * dt * W, &sn, &cs);
+    return make_double2(k.x * cs - k.y * sn, k.x * sn + k.y * cs);
+}
+
+__global__ void k_tc_kernels(int tc, const double* __restrict__ V, int N,
+                             const int* __restrict__ n_, const int* __restrict__ goff_,
+                             const int* __restrict__ tc_, int kstride, double h, double dt,
+                             const double* __restrict__ beta, double2 c2,
+                             double2* __restrict__ kap, double2* __restrict__ kout,
+                             double2* __restrict__ rho) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.y;
+    const int j = e >> 1, side = e & 1;
+    if (m >= kstride || j >= N || !(tc_[j] & (1 << side))) return;
+    const int g = goff_[j] + (side ? n_[j] - 1 : 0);    // an interior node of the whole grid
+    const double W = V[g];
+    const double dn = (V[g + 1] - V[g - 1]) / (2.0 * h) * (side ? 1.0 : -1.0);
+    const double2 k1 = tc_kernel_entry(tc, m, beta[m], W, dn, dt, c2);
+    const double2 k2 = tc_kernel_entry(tc, m, beta[m], W, -dn, dt, c2);
+    kap[(size_t)e * kstride + m] = k1;
+    kout[(size_t)e * kstride + m] = make_double2(k1.x + k2.x, k1.y + k2.y);
+    if (m == 0) {
+        if (tc >= 4) {
+            double sn, cs;
+            sincos(-0.5 * dt * W, &sn, &cs);
+            rho[e] = make_double2(cs, sn);
+        } else {
+            rho[e] = make_double2(1.0, 0.0);
+        }
+    }
+}
+
+int swr_launch_tc_kernels(int tc, const double* V, int N, const int* d_n, const int* d_goff,
+                          const int* d_tc, int kstride, double h, double dt, const double* beta,
+                          double2 c2, double2* kap, double2* kout, double2* rho, cudaStream_t s) {
+    if (tc < 2 || tc > 5) return -2;
+    dim3 grid((kstride + 255) / 256, 2 * N);
+    k_tc_kernels<<<grid, 256, 0, s>>>(tc, V, N, d_n, d_goff, d_tc, kstride, h, dt, beta, c2, kap,
+                                      kout, rho);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 // Vbar(x) = mean over the nrows rows of V (time average of a tabulated V(t,x)).
@@ -121,10 +195,10 @@ int swr_launch_row_mean(const double* V, int nrows, long long nx, double* out, c
 int swr_launch_assemble_static(const double* V, int N, const int* d_n, const int* d_goff,
                                const int* d_loff, const int* d_tc, int nmax, double h, double dt,
                                double2 sigma0, double2 inv_ik, double2* dg, double2* od,
-                               cudaStream_t s) {
+                               cudaStream_t s, const double2* kap, int kstride) {
     dim3 grid((nmax + 255) / 256, N);
     k_assemble_static<<<grid, 256, 0, s>>>(V, 0, d_n, d_goff, d_loff, d_tc, h, dt, sigma0, inv_ik,
-                                           dg, od, 0);
+                                           dg, od, 0, kap, kstride);
     swr_count_launch(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -478,12 +552,14 @@ int swr_launch_factor_steps(FactorSet& fs, int N, const int* d_n, const int* d_g
 // ([T+G] each) and, per chunk, the first/last interior u and y ([T] each).
 // ---------------------------------------------------------------------------
 int swr_march_smem_bytes(int T, int G, int stage_slots) {
-    return (int)sizeof(double2) * (3 * (T + G) + 4 * T + 2 * G + stage_slots * T);
+    return (int)sizeof(double2) * (3 * (T + G) + 4 * T + 4 * G + stage_slots * T);
 }
 
 // MODE 0: march; 1: also record v of every step; 2: also accumulate the adjoint
 // potential form against recorded forward values (see MarchArgs).
-template <int L, int MODE>
+// GEN: the ends carry per-end kernels (a.kap, a.kout, a.rho: S_0^3, S_0^4, S_1^2, S_1^4),
+// a separate instantiation so that Robin and S_0^2 marches keep their registers.
+template <int L, int MODE, bool GEN = false>
 __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march_static(const MarchArgs a) {
     extern __shared__ double2 sm[];
     const int T = a.T, G = a.G, P = a.P, C = a.C, nt = a.nt, levels = a.levels;
@@ -496,6 +572,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     double2* yfst = ulst + T;
     double2* ylst = yfst + T;
     double2* hsum = ylst + T;        // [2G] S_0^2 history sums of this step (C > 1: [2])
+    double2* hsum2 = hsum + 2 * G;   // [2G] flux-update history sums (per-end kernels)
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (C > 1) ? (int)cl.block_rank() : 0;
     const int tid = threadIdx.x;
@@ -605,7 +682,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     // groups are committed in the fixed order (q,c) | separator | (a,b).
     const int stage = a.stage;
     const int npc = 2 * levels + 3;
-    double2* stg = hsum + 2 * G;
+    double2* stg = hsum + 4 * G;
     auto issue_fa = [&](const double2* Fs) {   // Fs == nullptr: commit an empty group
         if (stage >= 2 && Fs && valid && Lp > 0) {
 #pragma unroll
@@ -657,8 +734,10 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     const bool hr = a.s02 && realsep && p == Pj && (tcf & 2);
     double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * (nt + 1) : nullptr;
     double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * (nt + 1) : nullptr;
-    if (hl) hist_l[0] = zero_u0 ? zero : a.u0[goff + sp];
-    if (hr) hist_r[0] = zero_u0 ? zero : a.u0[goff + sp];
+    // per-end kernels: h_0 = rho v_0; the flux weight on v_n is kout[0]
+    constexpr bool gen = GEN;
+    if (hl) hist_l[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 0], a.u0[goff + sp]) : a.u0[goff + sp]);
+    if (hr) hist_r[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 1], a.u0[goff + sp]) : a.u0[goff + sp]);
     const int hs_l = (C == 1) ? 2 * g : 0, hs_r = hs_l + 1;
     if (stage > 0) {   // step 1's factors
         issue_fa(F);
@@ -740,21 +819,52 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     const int gs = ragged ? a.rag[re0 + (e >> 1)].x : blockIdx.x * G + (e >> 1);
                     const int side = e & 1;
                     if (gs < a.nsys && (a.sub_tc[a.sys[gs].sub] & (1 << side))) {
-                        const double2 hsv = s02_history(
-                            a.beta, a.hist + ((size_t)gs * 2 + side) * (nt + 1), t, lane);
-                        if (lane == 0) hsum[e] = hsv;
+                        const double2* hh = a.hist + ((size_t)gs * 2 + side) * (nt + 1);
+                        if (gen) {
+                            const size_t ke = (size_t)(2 * a.sys[gs].sub + side) * a.kstride;
+                            double2 o1, o2;
+                            conv_history2(a.kap + ke, a.kout + ke, hh, t, lane, o1, o2);
+                            if (lane == 0) {
+                                hsum[e] = o1;
+                                hsum2[e] = o2;
+                            }
+                        } else {
+                            const double2 hsv = s02_history(a.beta, hh, t, lane);
+                            if (lane == 0) hsum[e] = hsv;
+                        }
                     }
                 }
             } else {
                 const int Pe = a.sub_P[a.sys[sidx].sub];
                 const int tce = a.sub_tc[a.sys[sidx].sub];
+                const int se = a.sys[sidx].sub;
                 if (w == 0 && rank == 0 && (tce & 1)) {
-                    const double2 hsv = s02_history(a.beta, hist_l, t, lane);
-                    if (lane == 0) hsum[0] = hsv;
+                    if (gen) {
+                        const size_t ke = (size_t)(2 * se + 0) * a.kstride;
+                        double2 o1, o2;
+                        conv_history2(a.kap + ke, a.kout + ke, hist_l, t, lane, o1, o2);
+                        if (lane == 0) {
+                            hsum[0] = o1;
+                            hsum2[0] = o2;
+                        }
+                    } else {
+                        const double2 hsv = s02_history(a.beta, hist_l, t, lane);
+                        if (lane == 0) hsum[0] = hsv;
+                    }
                 }
                 if (w == (nw > 1 ? 1 : 0) && rank == Pe / T && (tce & 2)) {
-                    const double2 hsv = s02_history(a.beta, hist_r, t, lane);
-                    if (lane == 0) hsum[1] = hsv;
+                    if (gen) {
+                        const size_t ke = (size_t)(2 * se + 1) * a.kstride;
+                        double2 o1, o2;
+                        conv_history2(a.kap + ke, a.kout + ke, hist_r, t, lane, o1, o2);
+                        if (lane == 0) {
+                            hsum[1] = o1;
+                            hsum2[1] = o2;
+                        }
+                    } else {
+                        const double2 hsv = s02_history(a.beta, hist_r, t, lane);
+                        if (lane == 0) hsum[1] = hsv;
+                    }
                 }
             }
         }
@@ -781,7 +891,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     else
                         lin = (live && sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l + a.t0 + t - 1] : zero;
                     f = cfms(lin, a.inv_ik, f);
-                    if (a.s02) f = cfma(hsum[hs_l], a.c2_ik, f);
+                    if (a.s02) f = cfma(hsum[hs_l], gen ? a.inv_ik : a.c2_ik, f);
                 }
                 if (re && (tcf & 2)) {
                     if (sy.flags & SYS_IMP_R)
@@ -789,7 +899,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     else
                         rin = (live && sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r + a.t0 + t - 1] : zero;
                     f = cfms(rin, a.inv_ik, f);
-                    if (a.s02) f = cfma(hsum[hs_r], a.c2_ik, f);
+                    if (a.s02) f = cfma(hsum[hs_r], gen ? a.inv_ik : a.c2_ik, f);
                 }
                 d = f;
                 const double2 El = (stage >= 1) ? stg[0 * T + tid] : sE_l[p];
@@ -878,8 +988,10 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             if (p == 0) {
                 if (hl) hist_l[t] = v;
                 if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
-                    double2 o = csub(cmul(a.two_sigma, v), lin);
-                    if (a.s02) o = cfma(a.two_c2, hsum[hs_l], o);
+                    const double2 ts = gen ? a.kout[(size_t)(2 * j + 0) * a.kstride] : a.two_sigma;
+                    double2 o = csub(cmul(ts, v), lin);
+                    if (gen) o = cadd(o, hsum2[hs_l]);
+                    else if (a.s02) o = cfma(a.two_c2, hsum[hs_l], o);
                     a.gout[(size_t)sy.out_a + a.t0 + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
@@ -887,8 +999,10 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             if (p == Pj) {
                 if (hr) hist_r[t] = v;
                 if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
-                    double2 o = csub(cmul(a.two_sigma, v), rin);
-                    if (a.s02) o = cfma(a.two_c2, hsum[hs_r], o);
+                    const double2 ts = gen ? a.kout[(size_t)(2 * j + 1) * a.kstride] : a.two_sigma;
+                    double2 o = csub(cmul(ts, v), rin);
+                    if (gen) o = cadd(o, hsum2[hs_r]);
+                    else if (a.s02) o = cfma(a.two_c2, hsum[hs_r], o);
                     a.gout[(size_t)sy.out_b + a.t0 + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
@@ -1334,11 +1448,12 @@ template <int L>
 static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s, int mode) {
     const int slots = a.stage == 2 ? 2 * a.levels + 3 + 4 * L : (a.stage == 1 ? 2 * a.levels + 3 : 0);
     const int smem = swr_march_smem_bytes(a.T, a.G, slots);
-    void (*kern)(const MarchArgs) = k_march_static<L, 0>;
+    void (*kern)(const MarchArgs) = a.kap ? k_march_static<L, 0, true> : k_march_static<L, 0>;
     if constexpr (L <= 8) {   // record and gradient modes exist for L <= 8
         if (mode == 1) kern = k_march_static<L, 1>;
         if (mode == 2) kern = k_march_static<L, 2>;
     }
+    if (mode != 0 && a.kap) return -2;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return -1;

@@ -612,6 +612,7 @@ int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef
                         int maxit, int* iters, int ngroups, cudaStream_t s, int mode,
                         unsigned long long* pit) {
     if (mode != 0 && a.s02) return -2;   // the adjoint modes: Robin or Neumann ends
+    if (a.kap) return -2;                // higher-order conditions: V(x) only
     a.P = fs.P;
     a.levels = fs.levels;
     a.sub_P = fs.sub_P;

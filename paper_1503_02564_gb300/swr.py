@@ -20,7 +20,7 @@ SWR_OK, SWR_ERR_ARG, SWR_ERR_SINGULAR, SWR_ERR_NOT_CONVERGED = 0, 1, 2, 3
 SWR_ERR_NONFINITE, SWR_ERR_TIMEOUT, SWR_ERR_NOMEM, SWR_ERR_CUDA = 4, 5, 6, 7
 SWR_ERR_STATE, SWR_ERR_UNSUPPORTED = 8, 9
 SWR_V_STATIC, SWR_V_TIME, SWR_V_NONLINEAR = 0, 1, 2
-SWR_TC_ROBIN, SWR_TC_S02 = 0, 1
+SWR_TC_ROBIN, SWR_TC_S02, SWR_TC_S03, SWR_TC_S04, SWR_TC_S12, SWR_TC_S14 = 0, 1, 2, 3, 4, 5
 SWR_SOLVER_GMRES, SWR_SOLVER_FIXED_POINT, SWR_SOLVER_CLASSICAL, SWR_SOLVER_CAUSAL = 0, 1, 2, 3
 SWR_PC_NONE, SWR_PC_ZERO_POTENTIAL, SWR_PC_CAUSAL, SWR_PC_MEAN_POTENTIAL = 0, 1, 2, 3
 # swr_stats.march_variant

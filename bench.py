@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--nsub", default=",".join(str(n) for n in NSUBS))
     ap.add_argument("--precond", default="causal", choices=["causal", "none"])
     ap.add_argument("--workload", default="scaling",
-                    choices=["scaling", "timedep", "adjoint", "batch", "nonlinear"],
+                    choices=["scaling", "timedep", "adjoint", "batch", "nonlinear", "tcs"],
                     help="scaling: the N in {16,64,256,500} static-potential step (default); "
                          "timedep: the time-dependent potential case (60001 nodes, 1000 steps, "
                          "N = 64, GMRES preconditioned by the mean-potential operator); "
@@ -70,7 +70,10 @@ def parse():
                          "instances (uneven partitions, 100-400 steps) in one batched plan, "
                          "reported beside one plan per instance; nonlinear: |u|^2 + V0 "
                          "(20001 nodes, 1000 steps, N = 32), preconditioned fixed point, then "
-                         "the misfit gradient dJ/dV0 by swr_adjoint (checkpoints every 50)")
+                         "the misfit gradient dJ/dV0 by swr_adjoint (checkpoints every 50); "
+                         "tcs: the comparison of transmission conditions and interface solvers "
+                         "in the setting of the paper's Section 6 (V=-x^2 on (-21,21), dx=1e-5, "
+                         "N in {2,500}, random g0)")
     ap.add_argument("--tc", default="robin", choices=["robin", "s02"],
                     help="transmission condition of the scaling workload: Robin "
                          "p = sqrt(5) e^{-i pi/4} (default) or the order-2 potential "
@@ -81,6 +84,10 @@ def parse():
     ap.add_argument("--nt", type=int, default=0,
                     help="override the workload's number of time steps (smaller cases for "
                          "profiling; 0: the workload's own)")
+    ap.add_argument("--tcs-nx", type=int, default=84001,
+                    help="nodes of the tcs workload on (-21, 21): 84001 is dx = 5e-4; the "
+                         "paper's dx = 1e-5 (4200001 nodes) needs 2.1M-node subdomains at N = 2, "
+                         "beyond the 69632-node subdomain limit of the march")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -410,12 +417,87 @@ def run_batch(args):
         c["plan"].destroy()
 
 
+def run_tcs(args):
+    """Transmission conditions x interface solvers in the setting of the paper's
+    comparison (Section 6): V = -x^2 on (-21, 21), dx = 5e-4 by default (the paper's
+    1e-5 needs subdomains beyond the march's size limit at N = 2), dt = 1e-3,
+    T = 0.5, N in {2, 500}, random initial interface vector, no preconditioner (the
+    new algorithm); per entry the build, the solve to ||residual||_2 < 1e-10 (the fixed
+    point: ||g^{k+1} - g^k||_2 < 1e-10) and its iterations.  Robin takes the paper's
+    parameters per N and solver (S-bar v = -i p v).  One step is the whole table."""
+    import numpy as np
+    import torch
+    from paper_1503_02564_gb300 import swr
+    from paper_1503_02564_gb300 import workloads as W
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    os.environ["SWR_SUPERPOSE"] = "0"     # 4.2M nodes: keep u(T) from the final march
+    conds = [("S_0^2", swr.SWR_TC_S02), ("S_0^3", swr.SWR_TC_S03), ("S_0^4", swr.SWR_TC_S04),
+             ("S_1^2", swr.SWR_TC_S12), ("S_1^4", swr.SWR_TC_S14), ("Robin", swr.SWR_TC_ROBIN)]
+    solvers = [("fixed point", swr.SWR_SOLVER_FIXED_POINT), ("gmres", swr.SWR_SOLVER_GMRES),
+               ("bicgstab", swr.SWR_SOLVER_BICGSTAB)]
+    robin_p = {(2, "fixed point"): 44.0, (2, "gmres"): 5.0, (2, "bicgstab"): 5.0,
+               (500, "fixed point"): 45.0, (500, "gmres"): 19.0, (500, "bicgstab"): 6.0}
+    nt = args.nt if args.nt > 0 else 500
+    table, ps_total, t_total = [], 0, 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for N in (2, 500):
+        wl = W.tc_comparison(nsub=N, nx=args.tcs_nx, nt=nt)
+        V = torch.tensor(wl.V, dtype=torch.float64, device=dev)
+        u0 = torch.tensor(wl.u0, dtype=torch.complex128, device=dev)
+        g0 = torch.tensor(W.random_interface(wl.nblk, wl.nt, 1).ravel(), dtype=torch.complex128,
+                          device=dev)
+        for cname, tc in conds:
+            for sname, solver in solvers:
+                p = -1j * robin_p[(N, sname)] if tc == swr.SWR_TC_ROBIN else 0j
+                plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
+                                node_off=wl.off, tc=tc, p=p, solver=solver, restart=200,
+                                maxit=2000, tol_abs=1e-10)
+                g = g0.clone()
+                torch.cuda.synchronize()
+                ev0.record()
+                plan.build_interface(V, u0)
+                info = plan.solve(g, True, None, allow_not_converged=True)
+                ev1.record()
+                ev1.synchronize()
+                ms = ev0.elapsed_time(ev1)
+                st = plan.get_stats(reset=True)
+                plan.destroy()
+                ps_total += st["march_point_steps"]
+                t_total += ms
+                table.append({"N": N, "tc": cname, "solver": sname,
+                              "robin_p": robin_p[(N, sname)] if tc == swr.SWR_TC_ROBIN else None,
+                              "iterations": info["iterations"],
+                              "converged": info["status"] == swr.SWR_OK,
+                              "residual": info["residual"], "solve_ms": info["t_solve_ms"],
+                              "build_ms": info["t_build_ms"], "total_ms": ms})
+    line = {
+        "metric": "SWR subdomain CN point-steps/s (solve time to 1e-10 interface residual "
+                  "reported as ms_per_step)",
+        "value": ps_total / (t_total * 1e-3), "unit": "point-steps/s", "n_gpus": world,
+        "steps": 1, "warmup": 0, "ms_per_step": t_total, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "swr_tc_comparison: x in (-21,21), dx=%g (%d P1 nodes), "
+                               "T=%g dt=1e-3, V=-x^2, u0=exp(-(x+10)^2+20i(x+10)), N in {2,500}, "
+                               "random g0; S_0^2..S_1^4 and Robin x fixed point / GMRES(200) / "
+                               "BiCGStab, no preconditioner, to 1e-10"
+                               % (42.0 / (args.tcs_nx - 1), args.tcs_nx, nt * 1e-3),
+                   "parallelism": "single GPU"},
+        "table": table,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "tcs":
+        return run_tcs(args)
     import numpy as np
     import torch
     from paper_1503_02564_gb300 import swr

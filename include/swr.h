@@ -77,7 +77,11 @@ enum { SWR_TC_ROBIN = 0, SWR_TC_S02 = 1, SWR_TC_S03 = 2, SWR_TC_S04 = 3, SWR_TC_
  * nonlinear: FIXED_POINT runs g <- g - P^{-1}(g - R_nl g) with the plan's
  * preconditioner (Section 5), CLASSICAL runs g <- R_nl g, GMRES is rejected. */
 enum { SWR_SOLVER_GMRES = 0, SWR_SOLVER_FIXED_POINT = 1, SWR_SOLVER_CLASSICAL = 2,
-       SWR_SOLVER_CAUSAL = 3 };
+       SWR_SOLVER_CAUSAL = 3, SWR_SOLVER_BICGSTAB = 4 };
+/* SWR_SOLVER_BICGSTAB (V(x), V(t,x)): right-preconditioned BiCGStab on (I - L) g = d,
+ * the alternative Krylov method of Section 6 (Tables 6-7), same preconditioners and
+ * true-residual stopping test as GMRES; iterations counts BiCGStab steps (two operator
+ * applications each). */
 /* SWR_SOLVER_CAUSAL (static V only): no Krylov iteration.  The blocks of L are
  * causal Toeplitz in time (Props. 3-4), so (I - L) g = d is solved by block
  * forward substitution in time, g = P^{-1} d with the CAUSAL preconditioner's

@@ -38,6 +38,7 @@ struct Workspace {
     double2* h = nullptr;       // m+1 scratch for gemv coefficients
     double2* partial = nullptr; // (m+1) x nblocks
     double* res = nullptr;      // residual estimate
+    double2* bcg = nullptr;     // 7 x n BiCGStab vectors (first BiCGStab solve)
 };
 
 }  // namespace
@@ -810,7 +811,7 @@ swr_status ensure_workspace(swr_plan_t p) {
     if (w.V && w.m == m && w.n == n) return SWR_OK;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
     cudaFree(w.sn); cudaFree(w.sv); cudaFree(w.y); cudaFree(w.h); cudaFree(w.partial);
-    cudaFree(w.res); cudaFree(w.Z);
+    cudaFree(w.res); cudaFree(w.Z); cudaFree(w.bcg);
     w = Workspace();
     w.n = n;
     w.m = m;
@@ -1012,6 +1013,110 @@ swr_status gmres(swr_plan_t p, const double2* b, double tol, double2* g, bool g_
     }
     if (!std::isfinite(beta)) return SWR_ERR_NONFINITE;
     return beta < tol ? SWR_OK : SWR_ERR_NOT_CONVERGED;
+}
+
+// Right-preconditioned BiCGStab (van der Vorst 1992) on (I - L) g = b, the
+// alternative Krylov method of Section 6 (Tables 6-7), with the plan's
+// preconditioner as for GMRES; complex inner products <x, y> = x^H y, shadow residual
+// r^ = r_0.  Each iteration: two operator applications and two preconditioner
+// applications; stops on the true residual ||b - (I - L) g||_2 < tol, recomputed
+// when the recurrence's residual passes the test.
+swr_status bicgstab(swr_plan_t p, const double2* b, double tol, double2* g, bool g_init,
+                    swr_info* info) {
+    swr_status st = ensure_workspace(p);
+    if (st) return st;
+    Workspace& w = p->ws;
+    const long long n = w.n;
+    const bool pc = has_precond(p);
+    if (!w.bcg && (st = dalloc(&w.bcg, (size_t)7 * n))) return st;
+    double2 *r = w.bcg, *rh = r + n, *pv = rh + n, *v = pv + n, *ph = v + n, *sv = ph + n,
+            *t = sv + n;
+    double2* sh = w.z;                                 // P^{-1} s
+    auto dot = [&](const double2* x, const double2* y, double2* out) -> swr_status {
+        LK(swr_launch_dots(x, 0, 1, y, n, w.partial, 512, w.h, p->s));
+        CK(cudaMemcpyAsync(out, w.h, sizeof(double2), cudaMemcpyDeviceToHost, p->s));
+        CK(cudaStreamSynchronize(p->s));
+        return SWR_OK;
+    };
+    auto cdiv = [](double2 a, double2 c) {
+        const double den = c.x * c.x + c.y * c.y;
+        return make_double2((a.x * c.x + a.y * c.y) / den, (a.y * c.x - a.x * c.y) / den);
+    };
+    auto precond = [&](const double2* x, double2* y) -> swr_status {
+        if (pc) return apply_M(p, x, y);
+        CK(cudaMemcpyAsync(y, x, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+        return SWR_OK;
+    };
+    auto true_residual = [&](double* out) -> swr_status {   // r = b - A g
+        if ((st = apply_A(p, g, r))) return st;
+        LK(swr_launch_axpby(r, b, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s));
+        return norm2(p, r, n, out);
+    };
+    double res = 0.0;
+    if (g_init) {
+        if ((st = true_residual(&res))) return st;
+    } else {
+        CK(cudaMemsetAsync(g, 0, sizeof(double2) * n, p->s));
+        CK(cudaMemcpyAsync(r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+        if ((st = norm2(p, r, n, &res))) return st;
+    }
+    if (info) info->residual0 = res;
+    CK(cudaMemcpyAsync(rh, r, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+    CK(cudaMemsetAsync(pv, 0, sizeof(double2) * n, p->s));
+    CK(cudaMemsetAsync(v, 0, sizeof(double2) * n, p->s));
+    double2 rho_prev = make_double2(1.0, 0.0), alpha = rho_prev, omega = rho_prev;
+    int it = 0;
+    const double2 one = make_double2(1.0, 0.0);
+    while (res >= tol && it < p->d.maxit) {
+        if (!std::isfinite(res)) return SWR_ERR_NONFINITE;
+        double2 rho;
+        if ((st = dot(rh, r, &rho))) return st;
+        if (rho.x == 0.0 && rho.y == 0.0) break;          // breakdown: restart below
+        const double2 beta = cmul_h(cdiv(rho, rho_prev), cdiv(alpha, omega));
+        // p = r + beta (p - omega v)
+        LK(swr_launch_axpby(pv, v, n, one, make_double2(-omega.x, -omega.y), p->s));
+        LK(swr_launch_axpby(pv, r, n, beta, one, p->s));
+        if ((st = precond(pv, ph))) return st;
+        if ((st = apply_A(p, ph, v))) return st;
+        double2 rv;
+        if ((st = dot(rh, v, &rv))) return st;
+        alpha = cdiv(rho, rv);
+        // s = r - alpha v
+        CK(cudaMemcpyAsync(sv, r, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+        LK(swr_launch_axpby(sv, v, n, one, make_double2(-alpha.x, -alpha.y), p->s));
+        double sn = 0.0;
+        if ((st = norm2(p, sv, n, &sn))) return st;
+        ++it;
+        if (sn < tol) {
+            LK(swr_launch_axpby(g, ph, n, one, alpha, p->s));
+            if ((st = true_residual(&res))) return st;
+            if (res < tol) break;
+            CK(cudaMemcpyAsync(rh, r, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+            rho_prev = alpha = omega = one;
+            CK(cudaMemsetAsync(pv, 0, sizeof(double2) * n, p->s));
+            CK(cudaMemsetAsync(v, 0, sizeof(double2) * n, p->s));
+            continue;
+        }
+        if ((st = precond(sv, sh))) return st;
+        if ((st = apply_A(p, sh, t))) return st;
+        double2 ts, tt;
+        if ((st = dot(t, sv, &ts)) || (st = dot(t, t, &tt))) return st;
+        omega = cdiv(ts, tt);
+        // g += alpha p^ + omega s^,  r = s - omega t
+        LK(swr_launch_axpby(g, ph, n, one, alpha, p->s));
+        LK(swr_launch_axpby(g, sh, n, one, omega, p->s));
+        CK(cudaMemcpyAsync(r, sv, sizeof(double2) * n, cudaMemcpyDeviceToDevice, p->s));
+        LK(swr_launch_axpby(r, t, n, one, make_double2(-omega.x, -omega.y), p->s));
+        if ((st = norm2(p, r, n, &res))) return st;
+        rho_prev = rho;
+        if (res < tol && (st = true_residual(&res))) return st;
+    }
+    if (info) {
+        info->iterations = it;
+        info->residual = res;
+    }
+    if (!std::isfinite(res)) return SWR_ERR_NONFINITE;
+    return res < tol ? SWR_OK : SWR_ERR_NOT_CONVERGED;
 }
 
 // Fixed point g <- L g + d (Algorithm 3 with the fixed point) or g <- R g
@@ -1311,7 +1416,8 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
         (d->vkind != SWR_V_STATIC || d->precond == SWR_PC_ZERO_POTENTIAL ||
          d->precond == SWR_PC_MEAN_POTENTIAL))
         return SWR_ERR_UNSUPPORTED;
-    if (d->solver < 0 || d->solver > 3 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
+    if (d->solver < 0 || d->solver > 4 || d->precond < 0 || d->precond > 3) return SWR_ERR_ARG;
+    if (d->solver == SWR_SOLVER_BICGSTAB && d->vkind == SWR_V_NONLINEAR) return SWR_ERR_ARG;
     if (d->solver == SWR_SOLVER_CAUSAL && d->vkind != SWR_V_STATIC) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_NONLINEAR && d->solver == SWR_SOLVER_GMRES) return SWR_ERR_ARG;
     if (d->vkind == SWR_V_TIME && d->solver == SWR_SOLVER_FIXED_POINT) return SWR_ERR_ARG;
@@ -1869,6 +1975,8 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
         st = nl_fixed_point(p, g, init, &loc);
     else if (p->d.solver == SWR_SOLVER_CAUSAL)
         st = causal_direct(p, g, init, &loc);
+    else if (p->d.solver == SWR_SOLVER_BICGSTAB)
+        st = bicgstab(p, p->d_iface, p->d.tol_abs, g, init, &loc);
     else if (p->d.solver == SWR_SOLVER_GMRES)
         st = gmres(p, p->d_iface, p->d.tol_abs, g, init, &loc);
     else

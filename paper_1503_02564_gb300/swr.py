@@ -22,6 +22,7 @@ SWR_ERR_STATE, SWR_ERR_UNSUPPORTED = 8, 9
 SWR_V_STATIC, SWR_V_TIME, SWR_V_NONLINEAR = 0, 1, 2
 SWR_TC_ROBIN, SWR_TC_S02, SWR_TC_S03, SWR_TC_S04, SWR_TC_S12, SWR_TC_S14 = 0, 1, 2, 3, 4, 5
 SWR_SOLVER_GMRES, SWR_SOLVER_FIXED_POINT, SWR_SOLVER_CLASSICAL, SWR_SOLVER_CAUSAL = 0, 1, 2, 3
+SWR_SOLVER_BICGSTAB = 4
 SWR_PC_NONE, SWR_PC_ZERO_POTENTIAL, SWR_PC_CAUSAL, SWR_PC_MEAN_POTENTIAL = 0, 1, 2, 3
 # swr_stats.march_variant
 MARCH_CONSTANT, MARCH_TDEP_REFACTOR, MARCH_NONLINEAR, MARCH_TDEP_STREAMED = 0, 1, 2, 3

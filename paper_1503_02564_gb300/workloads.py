@@ -171,6 +171,18 @@ def config5(nsub=32, nx=20001, nt=1000, dt=5e-4) -> Workload:
     return wl
 
 
+def tc_comparison(nsub=2, nx=4200001, nt=500, dt=1e-3) -> Workload:
+    """The setting of the paper's comparison of transmission conditions (Section 6):
+    (a0, b0) = (-21, 21), dx = 1e-5 (4200001 nodes), T = 0.5 with dt = 1e-3,
+    V(x) = -x^2, u0 = exp(-(x+10)^2 + 20 i (x+10)), N equal subdomains."""
+    a0, b0 = -21.0, 21.0
+    x = np.linspace(a0, b0, nx)
+    V = -x * x
+    u0 = np.exp(-(x + 10.0) ** 2 + 20j * (x + 10.0))
+    return Workload("tc_comparison_N%d" % nsub, a0, b0, nx, dt, nt, equal_offsets(nx, nsub),
+                    V, u0.astype(np.complex128))
+
+
 def random_interface(nblk: int, nt: int, seed: int = 7) -> np.ndarray:
     """A seeded random interface vector (the paper's 'random g^0', Section 6)."""
     rng = np.random.default_rng(SEED_BASE + 100 + seed)

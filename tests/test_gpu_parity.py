@@ -451,3 +451,38 @@ def test_direct_causal_solver_rejects_time_dependent_potential():
         swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
                  node_off=wl.off, vkind=swr.SWR_V_TIME, solver=swr.SWR_SOLVER_CAUSAL)
     assert e.value.status == swr.SWR_ERR_ARG
+
+
+@pytest.mark.parametrize("precond", [0, 2])
+@pytest.mark.parametrize("case", ["config1_small", "ragged_tiny", "config2_N16_small"])
+def test_bicgstab_reproduces_monodomain(case, precond):
+    """Right-preconditioned BiCGStab on (I - L) g = d (the alternative Krylov method of
+    Section 6) reaches the monodomain solution."""
+    from paper_1503_02564_gb300 import swr
+    wl = CASES[case]()
+    plan = gpu_plan(wl, solver=swr.SWR_SOLVER_BICGSTAB, maxit=2000, tol_abs=1e-12,
+                    precond=swr.SWR_PC_CAUSAL if precond == 2 else swr.SWR_PC_NONE)
+    g, uT, info = _solve(plan, wl)
+    plan.destroy()
+    assert info["status"] == swr.SWR_OK, info
+    gs, uTm = O.mono_interface(problem(wl))
+    assert rel(uT, uTm) < TOL_SOLVE
+    assert rel(g, gs) < TOL_SOLVE
+
+
+def test_bicgstab_time_dependent_matches_gmres():
+    """V(t,x): matrix-free BiCGStab preconditioned by the mean-potential operator
+    reaches the GMRES solution (and the monodomain one)."""
+    from paper_1503_02564_gb300 import swr
+    wl = W.config4(nsub=8, nx=2001, nt=40)
+    out = []
+    for solver in (swr.SWR_SOLVER_GMRES, swr.SWR_SOLVER_BICGSTAB):
+        plan = gpu_plan(wl, solver=solver, restart=60, maxit=400, tol_abs=1e-11,
+                        precond=swr.SWR_PC_MEAN_POTENTIAL)
+        g, uT, info = _solve(plan, wl)
+        plan.destroy()
+        assert info["status"] == swr.SWR_OK, info
+        out.append(uT)
+    assert rel(out[1], out[0]) < TOL_SOLVE
+    _, uTm = O.mono_interface(problem(wl))
+    assert rel(out[1], uTm) < TOL_SOLVE

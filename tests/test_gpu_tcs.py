@@ -102,7 +102,7 @@ def test_apply_R_matches_oracle(tc, case):
     assert rel(go.cpu().numpy(), O.apply_R(problem(wl, tc), g)) < TOL_MARCH
 
 
-@pytest.mark.parametrize("solver", ["gmres", "causal", "classical"])
+@pytest.mark.parametrize("solver", ["gmres", "bicgstab", "causal", "classical"])
 @pytest.mark.parametrize("tc", TCS)
 def test_converged_swr_is_the_monodomain_solution(tc, solver):
     from paper_1503_02564_gb300 import swr
@@ -110,6 +110,8 @@ def test_converged_swr_is_the_monodomain_solution(tc, solver):
     kw = dict(restart=100, maxit=2000, tol_abs=1e-12, precond=swr.SWR_PC_CAUSAL)
     if solver == "causal":
         kw["solver"] = swr.SWR_SOLVER_CAUSAL
+    if solver == "bicgstab":
+        kw["solver"] = swr.SWR_SOLVER_BICGSTAB
     if solver == "classical":
         kw = dict(solver=swr.SWR_SOLVER_CLASSICAL, maxit=2000, tol_abs=1e-11)
     plan = gpu_plan(wl, tc, **kw)

@@ -127,6 +127,11 @@ struct swr_plan_s {
     int nsys_build = 0;
     long long work_build = 0, work_build_imp = 0, work_R = 0;   // point-steps per launch
     int* d_status = nullptr;
+    // subdomains too long for one cluster of the constant-matrix march: every march of
+    // the plan runs on the whole grid (k_march_long), its state in d_long
+    bool long_march = false;
+    void* d_long = nullptr;
+    size_t long_bytes = 0;
     // Toeplitz applies through the FFT (SWR_TOEPLITZ_FFT=0: direct causal sums):
     // transform length fftM (0: direct), twiddles, spectra of the two column sets
     int fftM = 0;
@@ -324,6 +329,11 @@ struct SegArgs {
 
 MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
     MarchCfg c;
+    if (p->long_march && kind == MK_STATIC) {   // the grid-wide march, 16-node chunks
+        c.L = 16;
+        c.T = 256;
+        return c;
+    }
     for (const auto& t : p->tuned)
         if (t[0] == kind && t[1] == nsys) {
             c.L = t[2];
@@ -513,6 +523,10 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
         a.two_c2 = make_double2(2.0 * p->c2.x, 2.0 * p->c2.y);
     }
     const double kappa = 2.0 / p->d.dt * (p->h / 6.0);
+    if (p->long_march && kind == MK_STATIC) {
+        if (seg.mode != 0 || cfg.L != 16) return -2;
+        return swr_launch_march_long(fs, a, p->d_long, p->long_bytes, p->nsm, p->s);
+    }
     if (kind == MK_TDEP)
         return swr_launch_march_tdep(fs, a, p->d_V, p->nx, p->h, kappa,
                                      cmul_h(p->sigma0, p->inv_ik), cfg.ngroups, p->s);
@@ -570,7 +584,7 @@ swr_status factor_steps_for(swr_plan_t p, FactorSet& fs, int L, int nsteps);
 
 swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSys* d_sys,
                       int nsys, double2* gout, const double* V, double2* dg, double2* od) {
-    if (!p->autotune || nsys <= 0) return SWR_OK;
+    if (!p->autotune || nsys <= 0 || (p->long_march && kind == MK_STATIC)) return SWR_OK;
     for (const auto& t : p->tuned)
         if (t[0] == kind && t[1] == nsys) return SWR_OK;
     const MarchCfg guess = march_config(p, nsys, kind);
@@ -1386,7 +1400,7 @@ void swr_destroy(swr_plan_t p) {
     cudaFree(p->d_status); cudaFree(p->d_scal); cudaFree(p->d_pit);
     cudaFree(p->d_urec); cudaFree(p->d_rec_base);
     cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0); cudaFree(p->d_Gw);
-    cudaFree(p->d_kap); cudaFree(p->d_kout); cudaFree(p->d_rho);
+    cudaFree(p->d_kap); cudaFree(p->d_kout); cudaFree(p->d_rho); cudaFree(p->d_long);
     Workspace& w = p->ws;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
     cudaFree(w.sn); cudaFree(w.sv); cudaFree(w.y); cudaFree(w.h); cudaFree(w.partial);
@@ -1650,6 +1664,20 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
         for (const InstInfo& I : p->inst)
             for (int j = 0; j < I.N; ++j) p->work_R += (long long)p->n[I.sub0 + j] * I.nt;
         st = upload_systems(&p->d_sys_build, vb, p);
+    }
+    bool force_long = false;   // SWR_LONG_MARCH=1: the grid-wide march for any V(x) plan
+    if (const char* e = getenv("SWR_LONG_MARCH")) force_long = atoi(e) != 0;
+    if (!st && (force_long || chunks_for(p->nmax, 16) + 1 > 16 * march_tmax(MK_STATIC, 16))) {
+        // a subdomain longer than one cluster can hold (16 CTAs x 256 chunks of 16 nodes):
+        // the grid-wide march, V(x) and single instances only
+        if (d->vkind != SWR_V_STATIC || p->batched) {
+            st = SWR_ERR_UNSUPPORTED;
+        } else {
+            p->long_march = true;
+            p->long_bytes = swr_long_scratch_bytes(std::max(p->nsys_build, p->N), 16,
+                                                   chunks_for(p->nmax, 16));
+            st = dalloc(reinterpret_cast<char**>(&p->d_long), p->long_bytes);
+        }
     }
     if (!st && d->tc >= SWR_TC_S03) {
         // per-end kernels of the higher-order conditions (formed from V at every build)
@@ -2129,7 +2157,8 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
     // the nonlinear gradient is taken of the monodomain scheme (any transmission
     // condition and solver); the linear one runs the adjoint interface solve
     const bool nl = (p->d.vkind == SWR_V_NONLINEAR);
-    if (p->batched || (!nl && (p->d.vkind != SWR_V_STATIC || p->d.tc != SWR_TC_ROBIN ||
+    if (p->batched || p->long_march ||
+        (!nl && (p->d.vkind != SWR_V_STATIC || p->d.tc != SWR_TC_ROBIN ||
                                p->d.solver != SWR_SOLVER_GMRES)))
         return SWR_ERR_UNSUPPORTED;
     cudaStream_t s = p->s;

@@ -289,6 +289,11 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0,
                       cudaStream_t s, const InstInfo* inst = nullptr, const int* if_inst = nullptr,
                       int k0 = 0, int nif_group = 0, int nif_total = 0,
                       const double2* Gw = nullptr, int H = 0);
+// Long subdomains (beyond one cluster): the whole grid marches every system of the list
+// (L = 16 factors), state in the scratch of swr_long_scratch_bytes(nsys, 16, P).
+size_t swr_long_scratch_bytes(int nsys, int L, int P);
+int swr_launch_march_long(const FactorSet& fs, MarchArgs a, void* scratch, size_t scratch_bytes,
+                          int nsm, cudaStream_t s);
 // Rows of the lag-0 inverse for the window form of the substitution, |j - k| <= H
 // (1 <= H <= 8): Gw[nif][2H+1][4].
 int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* lag0, double2* Gw,

@@ -180,8 +180,12 @@ typedef struct swr_plan_s *swr_plan_t;
 
 /* Validate d, copy the partition and allocate the plan on the current device.
  * stream: cudaStream_t (as void*) on which all later work of this plan runs.
- * Errors: SWR_ERR_ARG (bad field), SWR_ERR_NOMEM, SWR_ERR_CUDA.  *out is NULL on
- * failure. */
+ * Subdomains up to 69632 nodes are marched by thread-block clusters; a V(x) plan
+ * with a longer subdomain is marched by the whole grid (one cooperative launch, the
+ * state in device memory; SWR_LONG_MARCH=1 forces it); V(t,x), nonlinear and batched
+ * plans with such a subdomain return SWR_ERR_UNSUPPORTED.
+ * Errors: SWR_ERR_ARG (bad field), SWR_ERR_UNSUPPORTED, SWR_ERR_NOMEM, SWR_ERR_CUDA.
+ * *out is NULL on failure. */
 swr_status swr_plan(const swr_desc *d, swr_plan_t *out, void *stream);
 
 /* A batch of independent problem instances in one plan (no counterpart in the

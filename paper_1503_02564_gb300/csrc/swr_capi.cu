@@ -641,7 +641,7 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
     // factors for every candidate chunk length (per-step kinds: the probed steps)
     // streamed per-step factors: probe enough steps that their factors overflow
     // L2 (129 MB), as in the real march, instead of probing an L2-resident set
-    int ntp = std::min(p->nt, 16);
+    int ntp = std::min(p->nt, 48);
     if (kind == MK_TSTAT) {
         const size_t step = swr_factor_step_bytes(p->N, 4, chunks_for(p->nmax, 4));
         const size_t want = ((size_t)256 << 20) / std::max<size_t>(step, 1) + 1;

@@ -565,24 +565,24 @@ __global__ void __launch_bounds__(256) k_superpose(
         const double2* pr = Pr + (size_t)k0 * n;
         int q = 0;
         if (hl && hr) {
-            for (; q + 1 < kc; q += 2) {
-                a0 = cfma(pl[(size_t)q * n], fl[q], a0);
-                a1 = cfma(pr[(size_t)q * n], fr[q], a1);
-                a2 = cfma(pl[(size_t)(q + 1) * n], fl[q + 1], a2);
-                a3 = cfma(pr[(size_t)(q + 1) * n], fr[q + 1], a3);
+            for (; q + 1 < kc; q += 2) {   // each state is read once: streaming loads
+                a0 = cfma(__ldcs(pl + (size_t)q * n), fl[q], a0);
+                a1 = cfma(__ldcs(pr + (size_t)q * n), fr[q], a1);
+                a2 = cfma(__ldcs(pl + (size_t)(q + 1) * n), fl[q + 1], a2);
+                a3 = cfma(__ldcs(pr + (size_t)(q + 1) * n), fr[q + 1], a3);
             }
             for (; q < kc; ++q) {
-                a0 = cfma(pl[(size_t)q * n], fl[q], a0);
-                a1 = cfma(pr[(size_t)q * n], fr[q], a1);
+                a0 = cfma(__ldcs(pl + (size_t)q * n), fl[q], a0);
+                a1 = cfma(__ldcs(pr + (size_t)q * n), fr[q], a1);
             }
         } else if (hl || hr) {
             const double2* pp = hl ? pl : pr;
             const double2* ff = hl ? fl : fr;
             for (; q + 1 < kc; q += 2) {
-                a0 = cfma(pp[(size_t)q * n], ff[q], a0);
-                a2 = cfma(pp[(size_t)(q + 1) * n], ff[q + 1], a2);
+                a0 = cfma(__ldcs(pp + (size_t)q * n), ff[q], a0);
+                a2 = cfma(__ldcs(pp + (size_t)(q + 1) * n), ff[q + 1], a2);
             }
-            if (q < kc) a0 = cfma(pp[(size_t)q * n], ff[q], a0);
+            if (q < kc) a0 = cfma(__ldcs(pp + (size_t)q * n), ff[q], a0);
         }
     }
     // the interface node belongs to the left subdomain

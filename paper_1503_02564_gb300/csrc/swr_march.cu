@@ -1009,11 +1009,13 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             }
         }
         if (rec_u && live) {   // u_t of this system in local node order
+            // streaming stores: the recorded states are read once, by the superposition,
+            // and must not evict the factors the march rereads every step from L2
             double2* row = a.urec + sy.rec + (size_t)(t - 1) * nj;
 #pragma unroll
             for (int i = 0; i < L; ++i)
-                if (i < Lp) row[sp + 1 + i] = u[i];
-            if (realsep) row[sp] = *SEP(usep, p);
+                if (i < Lp) __stcs(row + sp + 1 + i, u[i]);
+            if (realsep) __stcs(row + sp, *SEP(usep, p));
         }
         F += a.fstride;
         sE_l += a.sstride;

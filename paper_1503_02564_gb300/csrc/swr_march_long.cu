@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(256) k_march_long(const MarchArgs a, const Lon
                     const double2 uo = ST(sc.ust, s, i, p);
                     const double2 un = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
                     ST(sc.ust, s, i, p) = un;
-                    if (rec) row[sp + 1 + i] = un;
+                    if (rec) __stcs(row + sp + 1 + i, un);
                 }
             }
         }

@@ -1625,7 +1625,8 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
             }
         }
     }
-    if (!st && d->vkind == SWR_V_STATIC && d->tc == SWR_TC_ROBIN && (d->tc_re != 0.0 || d->tc_im != 0.0)) {
+    if (!st && d->vkind == SWR_V_STATIC &&
+        (d->tc == SWR_TC_ROBIN ? (d->tc_re != 0.0 || d->tc_im != 0.0) : p->nt < 4260)) {
         // u(T) by superposition: Phi_l, Phi_r (nt x n_j each) and U_d per subdomain, if
         // they take at most a quarter of the free memory
         bool on = true;
@@ -2023,9 +2024,16 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
                                     p->d_goff, p->d_tc, p->nmax, g, uT, s));
         if (p_toeplitz(p, p->d_iface + p->nb, g, p->d_iface, p->d_gtmp, 1))
             return launch_fail("toeplitz", __LINE__);
-        const double as = std::hypot(p->two_sigma.x, p->two_sigma.y);
-        LK(swr_launch_jump_res(p->d_gtmp, g, p->N, p->nt, as > 0.0 ? 1.0 / as : 0.0, p->d_scal,
-                               s, p->batched ? p->d_inst : nullptr, p->d_if_inst, p->nif));
+        if (p->d.tc == SWR_TC_ROBIN) {
+            const double as = std::hypot(p->two_sigma.x, p->two_sigma.y);
+            LK(swr_launch_jump_res(p->d_gtmp, g, p->N, p->nt, as > 0.0 ? 1.0 / as : 0.0,
+                                   p->d_scal, s, p->batched ? p->d_inst : nullptr, p->d_if_inst,
+                                   p->nif));
+        } else {   // the mismatch trace through the flux update's convolution
+            LK(swr_launch_jump_conv(p->d_gtmp, g, p->N, p->nt, p->d_kout, p->nt + 1, p->c2,
+                                    p->d_beta, p->d_scal, s, p->batched ? p->d_inst : nullptr,
+                                    p->d_if_inst, p->nif));
+        }
     } else {
         // final march (last step of Algorithms 1-3)
         swr_status st2 = run_march(p, false, p->d_sys_final, p->N, g, p->d_gtmp, uT, p->d_trace,

@@ -317,6 +317,12 @@ int swr_launch_toeplitz_fft(int N, int nt, const double2* spec, const double2* x
                             const double2* add, double2* y, int mode, int M, const double2* W,
                             cudaStream_t s, const InstInfo* inst = nullptr,
                             const int* blk_inst = nullptr, int nblk_total = 0);
+// The same for convolution operators (S_0^2: kout NULL, K = 2 c2 beta; the higher-order
+// ones: the flux kernels kout); nt <= 4259 (trace, kernel and data in shared memory).
+int swr_launch_jump_conv(const double2* w, const double2* g, int N, int nt, const double2* kout,
+                         int kstride, double2 c2, const double* beta, double* out,
+                         cudaStream_t s, const InstInfo* inst = nullptr,
+                         const int* if_inst = nullptr, int nif_total = 0);
 // u(T) by superposition of the recorded build-march states (static V): subdomain j's
 // states at urec + rec_base[j] (impulse-l responses, impulse-r responses, each nt rows of
 // n_j, then the zero-flux final state); sys[j] gives its flux blocks and step count.

@@ -510,6 +510,97 @@ __global__ void k_jump_res(const double2* __restrict__ w, const double2* __restr
     atomicMax(out, (unsigned long long)__double_as_longlong(m * scale));
 }
 
+// The same for a convolution transmission operator (S_0^2 and the higher-order ones):
+// the flux update's operator K = S-bar_j + S-bar_{j+1} acts on the mismatch trace dv
+// (dv_0 = 0: both sides start from u0), K dv = (w - g)[l_{k+1}] - (w - g)[r_k], a lower-
+// triangular Toeplitz system solved by forward substitution: one CTA per interface, dv
+// in shared memory, the history sum of every step split over the threads (fixed-order
+// reduction).  kout: the interface's kernel (the right end of subdomain j = k), or NULL
+// with c2, beta for S_0^2 (K = 2 c2 beta).
+__global__ void __launch_bounds__(256) k_jump_conv(
+    const double2* __restrict__ w, const double2* __restrict__ g, int N, int nt,
+    const double2* __restrict__ kout, int kstride, double2 c2, const double* __restrict__ beta,
+    unsigned long long* out, const InstInfo* __restrict__ inst, const int* __restrict__ if_inst,
+    int nif_total) {
+    extern __shared__ double2 dv[];               // [nt + 1] trace, then kernel, right-hand side
+    __shared__ double2 part[8];
+    const int k = blockIdx.x;
+    long long r0;
+    int ntk = nt, sub;
+    if (inst) {
+        const InstInfo I = inst[if_inst[k]];
+        const int kk = k - I.if0;
+        ntk = I.nt;
+        r0 = I.foff + (long long)(2 * kk) * I.nt;
+        sub = I.sub0 + kk;
+    } else {
+        r0 = (long long)(2 * k) * nt;
+        sub = k;
+    }
+    const long long l0 = r0 + ntk;
+    const double2* K = kout ? kout + (size_t)(2 * sub + 1) * kstride : nullptr;
+    auto kern = [&](int m) -> double2 {
+        if (K) return K[m];
+        return make_double2(2.0 * c2.x * beta[m], 2.0 * c2.y * beta[m]);
+    };
+    double2* kk = dv + (nt + 1);                  // the kernel and the right-hand sides, staged
+    double2* rr = kk + (nt + 1);
+    for (int q = threadIdx.x; q <= ntk; q += blockDim.x) {
+        kk[q] = kern(q);
+        if (q >= 1) {
+            const double2 dl = csub(w[l0 + q - 1], g[l0 + q - 1]);
+            const double2 dr = csub(w[r0 + q - 1], g[r0 + q - 1]);
+            rr[q] = csub(dl, dr);
+        }
+    }
+    const double2 k0 = kern(0);
+    const double den = k0.x * k0.x + k0.y * k0.y;
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    double m = 0.0;
+    if (threadIdx.x == 0) dv[0] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int n = 1; n <= ntk; ++n) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int s = 1 + threadIdx.x; s < n; s += blockDim.x) acc = cfma(kk[n - s], dv[s], acc);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (lane == 0) part[wi] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double2 tot = make_double2(0.0, 0.0);
+            for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot = cadd(tot, part[q]);
+            const double2 rhs = csub(rr[n], tot);
+            const double2 v = make_double2((rhs.x * k0.x + rhs.y * k0.y) / den,
+                                           (rhs.y * k0.x - rhs.x * k0.y) / den);
+            dv[n] = v;
+            m = fmax(m, hypot(v.x, v.y));
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+int swr_launch_jump_conv(const double2* w, const double2* g, int N, int nt, const double2* kout,
+                         int kstride, double2 c2, const double* beta, double* out, cudaStream_t s,
+                         const InstInfo* inst, const int* if_inst, int nif_total) {
+    const int nif = inst ? nif_total : N - 1;
+    cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (nif <= 0) return 0;
+    const int smem = 3 * (nt + 1) * (int)sizeof(double2);
+    if (smem > 200 * 1024) return -2;
+    if (cudaFuncSetAttribute(k_jump_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
+        return -1;
+    k_jump_conv<<<nif, 256, smem, s>>>(w, g, N, nt, kout, kstride, c2, beta,
+                                       reinterpret_cast<unsigned long long*>(out), inst, if_inst,
+                                       nif_total);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int swr_launch_jump_res(const double2* w, const double2* g, int N, int nt, double scale,
                         double* out, cudaStream_t s, const InstInfo* inst, const int* if_inst,
                         int nif_total) {

@@ -290,6 +290,8 @@ def test_repeated_builds_replay_the_captured_build(case):
 def _solve_with(wl, superpose, **kw):
     from paper_1503_02564_gb300 import swr
     os.environ["SWR_SUPERPOSE"] = "1" if superpose else "0"
+    if "tc" in kw:
+        wl.tc = kw["tc"]
     try:
         plan = gpu_plan(wl, **kw)
     finally:
@@ -300,15 +302,16 @@ def _solve_with(wl, superpose, **kw):
     return g, uT, info
 
 
+@pytest.mark.parametrize("tc", [0, 1, 3, 5])
 @pytest.mark.parametrize("case", ["config1_small", "ragged_tiny", "config2_N16_small", "two_long"])
-def test_superposed_final_state_matches_final_march(case):
+def test_superposed_final_state_matches_final_march(case, tc):
     """u(T) as the superposition of the build marches' recorded states (static V,
     Robin) against the final march with the same converged fluxes, and the
     interface mismatch from the final residual against the one from the final
     march's traces."""
     from paper_1503_02564_gb300 import swr
     wl = CASES[case]()
-    kw = dict(precond=swr.SWR_PC_CAUSAL, restart=100, maxit=1000, tol_abs=1e-12)
+    kw = dict(precond=swr.SWR_PC_CAUSAL, restart=100, maxit=1000, tol_abs=1e-12, tc=tc)
     g1, u1, i1 = _solve_with(wl, True, **kw)
     g0, u0, i0 = _solve_with(wl, False, **kw)
     assert np.array_equal(g1, g0)          # the solve itself does not change

@@ -96,9 +96,13 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
     unsigned long long* red = reinterpret_cast<unsigned long long*>(ylst + T);
     unsigned long long* cnt = red + 4 * G;
     double2* hsum = reinterpret_cast<double2*>(cnt + 4);   // [2G] S_0^2 history sums
+    // the previous step's converged iterate (chunk nodes [L][T], separators SEP layout),
+    // for the extrapolated start of the inner fixed point
+    double2* zpc = hsum + 2 * G;
+    double2* zps = zpc + L * T;
     // MODE 2: forward values of this step: chunk nodes [L][T] (element-major),
     // separators (SEP layout) and the chunk ends (CHK layout) for the neighbours
-    double2* vfc = hsum + 2 * G;
+    double2* vfc = zps + (T + G);
     double2* vfsep = vfc + L * T;
     double2* vffst = vfsep + (T + G);
     double2* vflst = vffst + T;
@@ -294,6 +298,27 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
             }
         }
         // ---- inner fixed point (Eq. AvMNL) ------------------------------------
+        // start: zeta^0 = 2 v_{n-1} - v_{n-2} (the paper starts from v_{n-1}; both reach the
+        // same fixed point to the inner tolerance, the extrapolation in fewer iterations);
+        // step 1 starts from v_0 = u_0.  Each thread updates its own nodes and separator;
+        // neighbours read the separators only after the first barrier below.
+        if (valid && Lp > 0) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    const double2 vp = zpc[i * T + tid];
+                    zpc[i * T + tid] = z[i];
+                    if (t >= 2) z[i] = make_double2(fma(2.0, z[i].x, -vp.x), fma(2.0, z[i].y, -vp.y));
+                }
+            }
+        }
+        if (realsep) {
+            double2* zs = SEP(zsep, p);
+            double2* zq = SEP(zps, p);
+            const double2 vn = *zs, vp = *zq;
+            *zq = vn;
+            if (t >= 2) *zs = make_double2(fma(2.0, vn.x, -vp.x), fma(2.0, vn.y, -vp.y));
+        }
         bool active = valid;
         int used = na.maxit;
         for (int it = 0; it < na.maxit; ++it) {
@@ -580,7 +605,8 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
 
 template <int L>
 static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s, int mode) {
-    int smem = swr_march_nl_smem_bytes(na.m.T, na.m.G);
+    int smem = swr_march_nl_smem_bytes(na.m.T, na.m.G) +
+               (int)sizeof(double2) * (L * na.m.T + na.m.T + na.m.G);   // previous iterate
     if (mode == 2)   // forward values of the step: [L][T], separators, chunk ends
         smem += (int)sizeof(double2) * (L * na.m.T + (na.m.T + na.m.G) + 2 * na.m.T);
     void (*kern)(const NlArgs) = k_march_nl<L, 0>;

@@ -7,7 +7,8 @@ steps (dt = 1e-3), seeded Gaussian-well potential and Gaussian packets, Robin
 transmission p = sqrt(5) exp(-i pi/4).  Each solve is swr_build_interface
 (assembly, factorisation, d and the Toeplitz columns by marches) followed by
 swr_solve (right-preconditioned GMRES(30) on (I - L) g = d to an absolute
-residual of 1e-10, then the final march).
+residual of 1e-10, then u(T) by superposition of the impulse responses' states
+recorded during the build).
 
 Reported: point-steps/s of all marches in the step (whole job), the solve time
 per step, the roofline of the march kernel (FP64-ALU bound), the CPU oracle's
@@ -100,11 +101,28 @@ def dist_env():
     return rank, world, local
 
 
+def replicas_max_ms(t_ms, dev=None):
+    """Replicas (torchrun, one rank per GPU, each solving its own copy): the
+    job's time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_ms
+    t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step, steps, world, t_ms):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return units_per_rank_step * steps * world / (t_ms * 1e-3)
+
+
 def workload_name(nsubs, tc="robin", nt=500):
     tcs = ("S_0^2 c2=e^{-i pi/4}sqrt(2/dt)" if tc == "s02" else "Robin p=sqrt(5)e^{-i pi/4}")
     return ("swr_scaling: x in (-50,50), 200001 P1 nodes, T=%g dt=1e-3 (%d steps), "
             "N in {%s}, V=-5*sum of 8 seeded Gaussians, u0=4 seeded packets, "
-            "%s, build interface + GMRES(30) to 1e-10 + final march"
+            "%s, build interface + GMRES(30) to 1e-10 + u(T) by superposition"
             % (nt * 1e-3, nt, ",".join(str(n) for n in nsubs), tcs))
 
 
@@ -125,8 +143,10 @@ def workload_name_nonlinear(nt=1000):
 
 
 def march_point_steps(wl):
-    """Point-steps of the marches in one solve: per subdomain the d march, the
-    impulse marches (one per existing neighbour) and the final march."""
+    """Point-steps of the marches of one solve with a final march: per subdomain
+    the d march, the impulse marches (one per existing neighbour) and the final
+    march.  The reported value uses the library's own count of the marches that
+    ran (no final march when u(T) is superposed)."""
     off = wl.off
     N = wl.nsub
     tot = 0
@@ -596,12 +616,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    t_ms = sum(per_step_ms)
-    if world > 1:
-        t = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = ps_step * args.steps * world / (t_ms * 1e-3)
+    t_ms = replicas_max_ms(sum(per_step_ms), dev)
 
     # march kernel statistics inside the timed region (events around each launch)
     st = [c["plan"].get_stats(reset=True) for c in cases]
@@ -635,7 +650,7 @@ def main():
     # whole-step throughput from the library's own count of marched point-steps
     # (equal to the analytic count for the scaling step; GMRES-dependent otherwise)
     ps_step = m_ps / args.steps
-    value = ps_step * args.steps * world / (t_ms * 1e-3)
+    value = whole_job_rate(ps_step, args.steps, world, t_ms)
     hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
     march_pss = m_ps / (m_ms * 1e-3) if m_ms > 0 else 0.0
@@ -675,7 +690,8 @@ def main():
             ev1.record()
             ev1.synchronize()
             e_ms += ev0.elapsed_time(ev1)
-        e2e = {"value": ps_step * args.steps * world / (e_ms * 1e-3), "unit": "point-steps/s",
+        e_ms = replicas_max_ms(e_ms, dev)
+        e2e = {"value": whole_job_rate(ps_step, args.steps, world, e_ms), "unit": "point-steps/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e_ms / args.steps}
 

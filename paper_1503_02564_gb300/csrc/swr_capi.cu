@@ -81,7 +81,7 @@ struct swr_plan_s {
     int *d_n = nullptr, *d_goff = nullptr, *d_loff = nullptr, *d_tc = nullptr;
     double2 *d_dg = nullptr, *d_od = nullptr;       // A - B for V (static) or V0
     double2 *d_dg0 = nullptr, *d_od0 = nullptr;     // A - B for V = 0
-    FactorSet fsL[3], fs0L[3];     // chunked factorisations for L = 4, 8, 16 (V and V = 0)
+    FactorSet fsL[4], fs0L[4];     // chunked factorisations for L = 4, 8, 16, 12 (V and V = 0)
     int forceL = 0;                // SWR_CHUNK_L override (0: chosen per launch)
     bool autotune = true;          // SWR_AUTOTUNE=0 disables the measured launch-shape choice
     // V(t,x): factor every step's matrix once per build and stream the factors
@@ -397,7 +397,7 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
     return c;
 }
 
-inline int lidx(int L) { return L == 4 ? 0 : (L == 8 ? 1 : 2); }
+inline int lidx(int L) { return L == 4 ? 0 : (L == 8 ? 1 : (L == 16 ? 2 : 3)); }
 
 inline double2 cmul_h(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -592,7 +592,7 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
     if (kind == MK_TDEP) Ls = {4};
     else if (kind == MK_NL || kind == MK_ADJ) Ls = {8, 4};
     else if (p->forceL) Ls = {p->forceL};
-    else Ls = {16, 8, 4};
+    else Ls = {16, 12, 8, 4};   // 12: six systems of ~780 nodes in one 384-thread CTA
     std::vector<MarchCfg> cands;
     cands.push_back(guess);
     for (int L : Ls) {
@@ -1374,7 +1374,7 @@ void swr_destroy(swr_plan_t p) {
     cudaStreamSynchronize(p->s);
     cudaFree(p->d_n); cudaFree(p->d_goff); cudaFree(p->d_loff); cudaFree(p->d_tc);
     cudaFree(p->d_dg); cudaFree(p->d_od); cudaFree(p->d_dg0); cudaFree(p->d_od0);
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         swr_factor_free(p->fsL[k]);
         swr_factor_free(p->fs0L[k]);
     }
@@ -1550,9 +1550,9 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (p->nsm <= 0) p->nsm = 152;
-    if (const char* e = getenv("SWR_CHUNK_L")) {   // tuning override: 4, 8 or 16
+    if (const char* e = getenv("SWR_CHUNK_L")) {   // tuning override: 4, 8, 12 or 16
         const int v = atoi(e);
-        if (v == 4 || v == 8 || v == 16) p->forceL = v;
+        if (v == 4 || v == 8 || v == 12 || v == 16) p->forceL = v;
     }
     if (const char* e = getenv("SWR_AUTOTUNE")) {   // 0: keep the modelled launch shapes
         p->autotune = atoi(e) != 0;

@@ -889,9 +889,20 @@ int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* la
 // (lags >= 2), so that step n+1 adds one lag-1 term on its critical path.
 // The same-step coupling of neighbouring interfaces is resolved either by
 // `sweeps` block-Jacobi sweeps (H == 0), or exactly (to (|c| |D^{-1}|)^{H+1}) by
-// the window form (H >= 1): interface k publishes its right-hand side R_n(k),
-// waits for those of the interfaces within H, and forms x_n(k) = sum_d
-// G_{k,k+d} R_n(k+d) from the rows of the lag-0 inverse (k_lag0_window).
+// the window form (H >= 1), x_n(k) = sum_d G_{k,k+d} R_n(k+d) with the rows of
+// the lag-0 inverse (k_lag0_window) and R_n(i) the right-hand side of interface i
+// at step n: y_n(i) plus its history.
+//
+// Window form, one hand-off per step: interface i publishes, with x_{n-1}(i), the
+// part of R_n(i) that does not involve step n-1 (y_n(i) and the lags >= 2), as
+// P_n(i); progress(i) = n + 1 then says that x_{n-1}(i) and P_n(i) are visible.
+// At step n lane H+1+d waits for interface k+d (|d| <= H+1), and lane H+1+d
+// (|d| <= H) forms R_n(k+d) = P_n(k+d) + the lag-1 terms from x_{n-1} of
+// interfaces k+d-1, k+d, k+d+1, then its term G_{k,k+d} R_n(k+d).
+// P_n lives in a two-slot ring: interface k overwrites slot (n+1)&1 at the end of
+// step n, after it has seen every interface within H+1 finish step n-1, and
+// those within H were the only readers of P_{n-1}(k).
+template <bool WIN>
 __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweeps,
                                                      const double2* __restrict__ cols,
                                                      const double2* __restrict__ lag0,
@@ -921,136 +932,182 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
     const bool has_l = (k >= 1), has_r = (k + 1 <= N - 2);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double2 zero = make_double2(0.0, 0.0);
-    // source e of interface k:
-    //  e=0: r_k     <- X^{k+1,1} l_{k+1} (block 2k+1)   e=1: r_k <- X^{k+1,2} r_{k+1} (block 2k+2)
-    //  e=2: l_{k+1} <- X^{k,4}   r_k     (block 2k)     e=3: l_{k+1} <- X^{k,3} l_k (block 2k-1)
-    auto source = [&](int e, bool& has, const double2*& cc, const double2*& xin) {
+    // source e of interface i:
+    //  e=0: r_i     <- X^{i+1,1} l_{i+1} (block 2i+1)   e=1: r_i <- X^{i+1,2} r_{i+1} (block 2i+2)
+    //  e=2: l_{i+1} <- X^{i,4}   r_i     (block 2i)     e=3: l_{i+1} <- X^{i,3} l_i (block 2i-1)
+    auto source = [&](int i, int e, bool& has, const double2*& cc, const double2*& xin) {
         int cslot = 0, inb = 0;
         has = true;
-        if (e == 0) { cslot = 4 * (k + 1) + 0; inb = 2 * k + 1; }
-        if (e == 1) { has = (k + 1 <= N - 2); cslot = 4 * (k + 1) + 1; inb = 2 * k + 2; }
-        if (e == 2) { cslot = 4 * k + 3; inb = 2 * k; }
-        if (e == 3) { has = (k >= 1); cslot = 4 * k + 2; inb = 2 * k - 1; }
+        if (e == 0) { cslot = 4 * (i + 1) + 0; inb = 2 * i + 1; }
+        if (e == 1) { has = (i + 1 <= N - 2); cslot = 4 * (i + 1) + 1; inb = 2 * i + 2; }
+        if (e == 2) { cslot = 4 * i + 3; inb = 2 * i; }
+        if (e == 3) { has = (i >= 1); cslot = 4 * i + 2; inb = 2 * i - 1; }
         cc = has ? cols + (size_t)cslot * nt : nullptr;
         xin = has ? x + (size_t)inb * nt : nullptr;
     };
-    const int S1 = (H > 0) ? 2 : sweeps + 1;
-    // window of interfaces within this instance
-    const int dlo = (H > 0) ? -min(H, k) : 0, dhi = (H > 0) ? min(H, N - 2 - k) : 0;
     if (threadIdx.x < 8) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
-    // role data: warps 1-4 accumulate source e = w-1; lane 0 of warp 0 solves
+    // role data: warps 1-4 accumulate source e = w-1 of this interface
     bool has = false;
     const double2* cc = nullptr;
     const double2* xin = nullptr;
-    if (w >= 1) source(w - 1, has, cc, xin);
-    bool hs[4] = {false, false, false, false};
-    const double2* cs[4] = {nullptr, nullptr, nullptr, nullptr};
-    const double2* xs[4] = {nullptr, nullptr, nullptr, nullptr};
-    double2 D00 = zero, D01 = zero, D10 = zero, D11 = zero, cB0 = zero, cD0 = zero;
-    double2 c1[4] = {zero, zero, zero, zero};
-    const bool solver = (threadIdx.x == 0);
-    if (solver) {
-        for (int e = 0; e < 4; ++e) source(e, hs[e], cs[e], xs[e]);
-        D00 = lag0[kg * 4 + 0];
-        D01 = lag0[kg * 4 + 1];
-        D10 = lag0[kg * 4 + 2];
-        D11 = lag0[kg * 4 + 3];
-        cB0 = hs[1] ? cs[1][0] : zero;
-        cD0 = hs[3] ? cs[3][0] : zero;
-        for (int e = 0; e < 4; ++e) c1[e] = (hs[e] && nt > 1) ? cs[e][1] : zero;
-    }
-    __syncthreads();
-    const double2* Gk = (H > 0) ? Gw + (size_t)kg * (2 * H + 1) * 4 : nullptr;
-    for (int n = 0; n < nt; ++n) {
-        if (w == 0) {
-            // lanes 0 and 1 wait for the left and right neighbours' values < n
-            bool ok = true;
-            if (lane < 2 && (lane == 0 ? has_l : has_r))
-                ok = wait_one(kg + (lane == 0 ? -1 : 1), n * S1, progress, abortf, status);
-            ok = __all_sync(0xffffffffu, ok);
-            if (lane == 0) s_go = ok ? 1 : 0;
-        }
-        __syncthreads();                                       // B1: values < n visible
-        if (!s_go) break;
-        if (w == 0) {
-            // history of step n: partial (lags >= 2, computed during step n-1) + lag 1
-            double2 r1 = zero, r2 = zero;
-            if (solver) {
-                double2 h[4];
-                for (int e = 0; e < 4; ++e) {
-                    h[e] = hp[n & 1][e];
-                    if (n >= 1 && hs[e]) h[e] = cfma(c1[e], xs[e][n - 1], h[e]);
-                }
-                r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(h[0], h[1]));
-                r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(h[2], h[3]));
+    if (w >= 1) source(k, w - 1, has, cc, xin);
+    // history warps: step n+1's terms from values s <= n-1 (lags >= 2)
+    auto history = [&](int n) {
+        double2 acc = zero;
+        if (has && n + 1 < nt)
+            for (int s = lane; s < n; s += 32) acc = cfma(__ldg(cc + n + 1 - s), xin[s], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) hp[(n + 1) & 1][w - 1] = acc;
+    };
+
+    if constexpr (WIN) {
+        // ---- window form (H >= 1) ---------------------------------------------
+        const int d = lane - (H + 1);
+        const int i = k + d;                                   // this lane's interface
+        const bool inwin = (d >= -H && d <= H && i >= 0 && i <= N - 2);
+        const bool waits = (d != 0 && d >= -H - 1 && d <= H + 1 && i >= 0 && i <= N - 2);
+        // lane data for R_n(i): the lag-1 coefficients and source rows of its four
+        // sources (the order of `source`; a missing source keeps a zero coefficient)
+        const double2 *xs0 = x, *xs1 = x, *xs2 = x, *xs3 = x;
+        double2 c10 = zero, c11 = zero, c12 = zero, c13 = zero;
+        double2 g0 = zero, g1 = zero, g2 = zero, g3 = zero;
+        const bool h1 = inwin && (i + 1 <= N - 2), h3 = inwin && (i >= 1);
+        if (w == 0 && inwin) {
+            xs0 = x + (size_t)(2 * i + 1) * nt;
+            xs2 = x + (size_t)(2 * i) * nt;
+            if (h1) xs1 = x + (size_t)(2 * i + 2) * nt;
+            if (h3) xs3 = x + (size_t)(2 * i - 1) * nt;
+            if (nt > 1) {
+                c10 = cols[(size_t)(4 * (i + 1) + 0) * nt + 1];
+                c12 = cols[(size_t)(4 * i + 3) * nt + 1];
+                if (h1) c11 = cols[(size_t)(4 * (i + 1) + 1) * nt + 1];
+                if (h3) c13 = cols[(size_t)(4 * i + 2) * nt + 1];
             }
-            double2 z1 = zero, z2 = zero;
-            if (H > 0) {
-                // publish R_n(k); lane H + d waits for interface k + d and forms its
-                // term G_{k,k+d} R_n(k+d); the warp sums the terms
-                double2* out = xsw + (size_t)(n & 1) * 2 * nif_all;
-                if (solver) {
-                    out[2 * kg] = r1;
-                    out[2 * kg + 1] = r2;
-                    store_release(progress + kg, n * 2 + 1);
-                }
-                r1.x = __shfl_sync(0xffffffffu, r1.x, 0);
-                r1.y = __shfl_sync(0xffffffffu, r1.y, 0);
-                r2.x = __shfl_sync(0xffffffffu, r2.x, 0);
-                r2.y = __shfl_sync(0xffffffffu, r2.y, 0);
-                const int d = lane - H;
+            const double2* g = Gw + ((size_t)kg * (2 * H + 1) + d + H) * 4;
+            g0 = g[0];
+            g1 = g[1];
+            g2 = g[2];
+            g3 = g[3];
+        }
+        // P_0(k) = y_0(k): no history at step 0
+        if (threadIdx.x == 0) {
+            xsw[2 * kg] = y[(size_t)(2 * k) * nt];
+            xsw[2 * kg + 1] = y[(size_t)(2 * k + 1) * nt];
+            store_release(progress + kg, 1);
+        }
+        __syncthreads();
+        for (int n = 0; n < nt; ++n) {
+            if (w == 0) {
                 bool ok = true;
+                if (waits) ok = wait_one(kg + d, n + 1, progress, abortf, status);
+                ok = __all_sync(0xffffffffu, ok);
+                if (lane == 0) s_go = ok ? 1 : 0;
+            }
+            __syncthreads();                                   // B1: x_{<n}, P_n visible
+            if (!s_go) break;
+            if (w == 0) {
                 double2 t1 = zero, t2 = zero;
-                if (d >= dlo && d <= dhi) {
-                    double2 q1 = r1, q2 = r2;
-                    if (d != 0) {
-                        ok = wait_one(kg + d, n * 2 + 1, progress, abortf, status);
-                        if (ok) {
-                            q1 = out[2 * (kg + d)];
-                            q2 = out[2 * (kg + d) + 1];
-                        }
+                if (inwin) {
+                    const double2* P = xsw + (size_t)(n & 1) * 2 * nif_all + 2 * (kg + d);
+                    double2 r1 = P[0], r2 = P[1];
+                    if (n >= 1) {
+                        r1 = cfma(c10, xs0[n - 1], r1);
+                        if (h1) r1 = cfma(c11, xs1[n - 1], r1);
+                        r2 = cfma(c12, xs2[n - 1], r2);
+                        if (h3) r2 = cfma(c13, xs3[n - 1], r2);
                     }
-                    if (ok) {
-                        const double2* g = Gk + (d + H) * 4;
-                        t1 = cfma(g[0], q1, cmul(g[1], q2));
-                        t2 = cfma(g[2], q1, cmul(g[3], q2));
-                    }
+                    t1 = cfma(g0, r1, cmul(g1, r2));
+                    t2 = cfma(g2, r1, cmul(g3, r2));
                 }
-                (void)__all_sync(0xffffffffu, ok);     // a failed wait has raised the abort flag
-                z1 = warp_sum(t1);
-                z2 = warp_sum(t2);
-            } else if (solver) {
-                z1 = cfma(D01, r2, cmul(D00, r1));
-                z2 = cfma(D11, r2, cmul(D10, r1));
-                for (int sw = 1; sw <= sweeps; ++sw) {
-                    // publish sweep sw-1 of this step, then use the neighbours' sweep sw-1
-                    double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif_all;
-                    out[2 * kg] = z1;
-                    out[2 * kg + 1] = z2;
-                    store_release(progress + kg, n * S1 + sw);
-                    if (!wait_neighbours(kg, has_l, has_r, n * S1 + sw, progress, abortf, status))
-                        break;
-                    const double2 xr = has_r ? out[2 * (kg + 1)] : zero;       // r_{k+1}
-                    const double2 xl = has_l ? out[2 * (kg - 1) + 1] : zero;   // l_k
-                    const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
-                    z1 = cfma(D01, e2, cmul(D00, e1));
-                    z2 = cfma(D11, e2, cmul(D10, e1));
+                const double2 z1 = warp_sum(t1), z2 = warp_sum(t2);
+                if (lane == 0) {
+                    x[(size_t)(2 * k) * nt + n] = z1;
+                    x[(size_t)(2 * k + 1) * nt + n] = z2;
                 }
+            } else {
+                history(n);
             }
-            if (solver) {
-                x[(size_t)(2 * k) * nt + n] = z1;
-                x[(size_t)(2 * k + 1) * nt + n] = z2;
-                store_release(progress + kg, (n + 1) * S1);    // orders the x writes above
+            __syncthreads();                                   // B2: x_n, hp of n+1 done
+            if (threadIdx.x == 0) {
+                if (n + 1 < nt) {
+                    const double2* h = hp[(n + 1) & 1];
+                    double2* P = xsw + (size_t)((n + 1) & 1) * 2 * nif_all + 2 * kg;
+                    P[0] = cadd(y[(size_t)(2 * k) * nt + n + 1], cadd(h[0], h[1]));
+                    P[1] = cadd(y[(size_t)(2 * k + 1) * nt + n + 1], cadd(h[2], h[3]));
+                }
+                store_release(progress + kg, n + 2);           // orders x_n and P_{n+1}
             }
-        } else {
-            // step n+1's history from values s <= n-1 (lags >= 2)
-            double2 acc = zero;
-            if (has && n + 1 < nt)
-                for (int s = lane; s < n; s += 32) acc = cfma(__ldg(cc + n + 1 - s), xin[s], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) hp[(n + 1) & 1][w - 1] = acc;
         }
-        __syncthreads();                                       // B2
+    } else {
+        // ---- sweep form (H == 0) -------------------------------------------------
+        const int S1 = sweeps + 1;
+        bool hs[4] = {false, false, false, false};
+        const double2* cs[4] = {nullptr, nullptr, nullptr, nullptr};
+        const double2* xs[4] = {nullptr, nullptr, nullptr, nullptr};
+        double2 D00 = zero, D01 = zero, D10 = zero, D11 = zero, cB0 = zero, cD0 = zero;
+        double2 c1[4] = {zero, zero, zero, zero};
+        const bool solver = (threadIdx.x == 0);
+        if (solver) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) source(k, e, hs[e], cs[e], xs[e]);
+            D00 = lag0[kg * 4 + 0];
+            D01 = lag0[kg * 4 + 1];
+            D10 = lag0[kg * 4 + 2];
+            D11 = lag0[kg * 4 + 3];
+            cB0 = hs[1] ? cs[1][0] : zero;
+            cD0 = hs[3] ? cs[3][0] : zero;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) c1[e] = (hs[e] && nt > 1) ? cs[e][1] : zero;
+        }
+        __syncthreads();
+        for (int n = 0; n < nt; ++n) {
+            if (w == 0) {
+                // lanes 0 and 1 wait for the left and right neighbours' values < n
+                bool ok = true;
+                if (lane < 2 && (lane == 0 ? has_l : has_r))
+                    ok = wait_one(kg + (lane == 0 ? -1 : 1), n * S1, progress, abortf, status);
+                ok = __all_sync(0xffffffffu, ok);
+                if (lane == 0) s_go = ok ? 1 : 0;
+            }
+            __syncthreads();                                   // B1: values < n visible
+            if (!s_go) break;
+            if (w == 0) {
+                if (solver) {
+                    // history of step n: partial (lags >= 2, computed during step n-1) + lag 1
+                    double2 h[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        h[e] = hp[n & 1][e];
+                        if (n >= 1 && hs[e]) h[e] = cfma(c1[e], xs[e][n - 1], h[e]);
+                    }
+                    const double2 r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(h[0], h[1]));
+                    const double2 r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(h[2], h[3]));
+                    double2 z1 = cfma(D01, r2, cmul(D00, r1));
+                    double2 z2 = cfma(D11, r2, cmul(D10, r1));
+                    for (int sw = 1; sw <= sweeps; ++sw) {
+                        // publish sweep sw-1 of this step, then use the neighbours' sweep sw-1
+                        double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif_all;
+                        out[2 * kg] = z1;
+                        out[2 * kg + 1] = z2;
+                        store_release(progress + kg, n * S1 + sw);
+                        if (!wait_neighbours(kg, has_l, has_r, n * S1 + sw, progress, abortf,
+                                             status))
+                            break;
+                        const double2 xr = has_r ? out[2 * (kg + 1)] : zero;       // r_{k+1}
+                        const double2 xl = has_l ? out[2 * (kg - 1) + 1] : zero;   // l_k
+                        const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
+                        z1 = cfma(D01, e2, cmul(D00, e1));
+                        z2 = cfma(D11, e2, cmul(D10, e1));
+                    }
+                    x[(size_t)(2 * k) * nt + n] = z1;
+                    x[(size_t)(2 * k + 1) * nt + n] = z2;
+                    store_release(progress + kg, (n + 1) * S1);    // orders the x writes above
+                }
+            } else {
+                history(n);
+            }
+            __syncthreads();                                   // B2
+        }
     }
 }
 
@@ -1065,9 +1122,14 @@ int swr_causal_capacity(int) {
     int dev = 0, nsm = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_causal_wave, 160, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_causal_wave<false>, 160, 0) !=
+            cudaSuccess)
         return 0;
-    return nsm * per;
+    int perw = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perw, k_causal_wave<true>, 160, 0) !=
+        cudaSuccess)
+        return 0;
+    return nsm * std::min(per, perw);
 }
 
 // Single instance (inst == NULL): interfaces 0..N-2.  Batched plan: interfaces
@@ -1096,8 +1158,8 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, c
                     (void*)&y, (void*)&x, (void*)&xsw, (void*)&progress, (void*)&abortf,
                     (void*)&status, (void*)&inst, (void*)&if_inst, (void*)&k0, (void*)&nif,
                     (void*)&Gw, (void*)&H};
-    if (cudaLaunchCooperativeKernel((const void*)k_causal_wave, dim3(ncta), dim3(160), args, 0, s) !=
-        cudaSuccess)
+    const void* fn = (H > 0) ? (const void*)k_causal_wave<true> : (const void*)k_causal_wave<false>;
+    if (cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(160), args, 0, s) != cudaSuccess)
         return -1;
     swr_count_launch(1);
     return 0;

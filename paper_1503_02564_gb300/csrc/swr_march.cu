@@ -500,6 +500,11 @@ static int launch_factor_batch(FactorSet& fs, int N, const int* d_n, const int* 
                                                     fs.sep_pos, fs.clen, fac, fs.tips, status, ldd,
                                                     fs.fstride);
             break;
+        case 12:
+            k_factor_chunks<12><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
+                                                     fs.sep_pos, fs.clen, fac, fs.tips, status,
+                                                     ldd, fs.fstride);
+            break;
         case 16:
             k_factor_chunks<16><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
                                                      fs.sep_pos, fs.clen, fac, fs.tips, status,
@@ -1501,10 +1506,11 @@ int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t
     a.fac = fs.fac;
     a.sep = fs.sep;
     a.pcr = fs.pcr;
-    if (mode != 0 && (fs.L == 16 || fs.nsteps > 1 || a.s02)) return -2;   // adjoint modes: L <= 8, V(x), Robin
+    if (mode != 0 && (fs.L > 8 || fs.nsteps > 1 || a.s02)) return -2;   // adjoint modes: L <= 8, V(x), Robin
     switch (fs.L) {
         case 4: return launch_march_t<4>(a, ngroups, s, mode);
         case 8: return launch_march_t<8>(a, ngroups, s, mode);
+        case 12: return launch_march_t<12>(a, ngroups, s, 0);
         case 16: return launch_march_t<16>(a, ngroups, s, 0);
         default: return -2;
     }

@@ -83,7 +83,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("chunk", [4, 8, 16])
+@pytest.mark.parametrize("chunk", [4, 8, 12, 16])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_build_interface_matches_oracle(case, chunk):
     wl = CASES[case]()

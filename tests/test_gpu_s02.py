@@ -82,7 +82,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("chunk", [4, 8, 16])
+@pytest.mark.parametrize("chunk", [4, 8, 12, 16])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_s02_build_interface_matches_oracle(case, chunk):
     """d = R 0 and the Toeplitz first columns with S_0^2 ends, every chunk

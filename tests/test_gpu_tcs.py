@@ -68,7 +68,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("chunk", [4, 16])
+@pytest.mark.parametrize("chunk", [4, 12, 16])
 @pytest.mark.parametrize("case", sorted(CASES))
 @pytest.mark.parametrize("tc", TCS)
 def test_build_interface_matches_oracle(tc, case, chunk):

@@ -85,7 +85,7 @@ def test_tdep_apply_R_matches_oracle(case, streamed):
     plan.destroy()
 
 
-@pytest.mark.parametrize("chunk", [4, 8, 16])
+@pytest.mark.parametrize("chunk", [4, 8, 12, 16])
 def test_tdep_streamed_long_subdomains_match_oracle(chunk):
     """Streamed per-step factors on long subdomains (thread-block clusters): the
     factors are staged in shared memory in full, or only the separator part when

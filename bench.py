@@ -40,8 +40,8 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flop x GHz (max
 # the ncu launch lists of the two workloads kept with the profiles; valid only for the march
 # sources they were taken from (sha256 prefix of swr_march.cu + swr_internal.cuh), null
 # otherwise.
-MARCH_TRAFFIC = {"sources": "cc7fdd7bfeaeb248",
-                 "scaling": 3119987712.0, "timedep": 6636864821.0}
+MARCH_TRAFFIC = {"sources": "d744ed0b72cab1ec",
+                 "scaling": 3119406144.0, "timedep": 6636864821.0}
 
 
 def march_sources_hash():

@@ -157,6 +157,22 @@ def march_point_steps(wl):
     return tot
 
 
+def host_info():
+    """The host the CPU oracle is timed on: logical CPUs and the CPU model."""
+    import platform
+    model = platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model, "threads_used": 1}
+
+
 def march_point_steps_d(wl):
     """Point-steps of one d march of every subdomain."""
     return sum(int(wl.off[j + 1] - wl.off[j] + 1) * wl.nt for j in range(wl.nsub))
@@ -302,7 +318,7 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(NSUBS, args.tc),
                    "sample": "oracle d-marches of subdomains 0..24 of N=500 per step"},
-        "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "host": host_info(),
                          "sample": "25 of 500 subdomain marches (401 nodes x 500 steps each)"},
         "e2e": {"value": value, "unit": "point-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -400,7 +416,7 @@ def run_batch(args):
             v1, s1, p1 = cpu_oracle_sample(w, w.nsub)
             secs += s1
             pss += p1
-        cpu = {"value": pss / secs, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": pss / secs, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"oracle d-marches of every subdomain of the first 8 instances "
                          f"({pss:.3g} point-steps, {secs:.1f} s)"}
     line = {
@@ -707,14 +723,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and nonlin:
         v, s, ps = cpu_oracle_adjoint_nl_sample(cases[0]["wl"], 40)
-        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"oracle discrete adjoint of the nonlinear monodomain scheme on the "
                          f"{cases[0]['wl'].nx}-node grid, first 40 steps (forward march with "
                          f"inner fixed points, exact linearised adjoint solves; {ps:.3g} "
                          f"point-steps, {s:.1f} s)"}
     elif rank == 0 and world == 1 and not args.no_cpu_baseline and adjoint:
         v, s, ps = cpu_oracle_adjoint_sample(cases[0]["wl"], 100)
-        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"oracle discrete adjoint of the monodomain scheme on the "
                          f"{cases[0]['wl'].nx}-node grid, first 100 steps (forward and adjoint "
                          f"marches, {ps:.3g} point-steps, {s:.1f} s)"}
@@ -725,7 +741,7 @@ def main():
             wl_cpu = cases[-1]["wl"] if cases[-1]["N"] == 500 else W.config2(nsub=500)
         v, s, ps = cpu_oracle_sample(wl_cpu, wl_cpu.nsub, min_seconds=10.0)
         npass = int(round(ps / march_point_steps_d(wl_cpu)))
-        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "host": host_info(),
                "sample": f"oracle d-marches of all {wl_cpu.nsub} subdomains of the "
                          f"{'time-dependent' if timedep else 'N=500 scaling'} workload, "
                          f"{npass} passes ({ps:.3g} point-steps, {s:.1f} s)"}

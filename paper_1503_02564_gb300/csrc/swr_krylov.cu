@@ -43,9 +43,11 @@ __device__ __forceinline__ void block_sources(int o, int N, int& c1, int& i1, in
 // ---------------------------------------------------------------------------
 // y = x - L x (mode 0)  or  y = L x + add (mode 1, the fixed point of Alg. 3).
 // One CTA per output block; the two first columns and the two input blocks
-// are staged in shared memory; thread q computes the causal sums for times q
-// and nt-1-q (equal work per thread).
+// are staged in shared memory (SMEM; read from L2 when they do not fit, nt >
+// 3632); thread q computes the causal sums for times q and nt-1-q (equal work
+// per thread).
 // ---------------------------------------------------------------------------
+template <bool SMEM>
 __global__ void k_toeplitz(int N, int nt, const double2* __restrict__ cols,
                            const double2* __restrict__ x, const double2* __restrict__ add,
                            double2* __restrict__ y, int mode, const InstInfo* __restrict__ inst,
@@ -64,19 +66,31 @@ __global__ void k_toeplitz(int N, int nt, const double2* __restrict__ cols,
     }
     int c1, i1, c2, i2;
     block_sources(o, N, c1, i1, c2, i2);
-    double2* C1 = sh;
-    double2* X1 = sh + nt;
-    double2* C2 = sh + 2 * nt;
-    double2* X2 = sh + 3 * nt;
     const double2 zero = make_double2(0.0, 0.0);
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        C1[t] = cols[(size_t)c1 * nt + t];
-        X1[t] = x[(size_t)i1 * nt + t];
-        C2[t] = (c2 >= 0) ? cols[(size_t)c2 * nt + t] : zero;
-        X2[t] = (c2 >= 0) ? x[(size_t)i2 * nt + t] : zero;
-    }
-    __syncthreads();
     const bool two = (c2 >= 0);
+    const double2 *C1, *X1, *C2, *X2;
+    if constexpr (SMEM) {
+        double2* c1s = sh;
+        double2* x1s = sh + nt;
+        double2* c2s = sh + 2 * nt;
+        double2* x2s = sh + 3 * nt;
+        for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+            c1s[t] = cols[(size_t)c1 * nt + t];
+            x1s[t] = x[(size_t)i1 * nt + t];
+            c2s[t] = two ? cols[(size_t)c2 * nt + t] : zero;
+            x2s[t] = two ? x[(size_t)i2 * nt + t] : zero;
+        }
+        __syncthreads();
+        C1 = c1s;
+        X1 = x1s;
+        C2 = c2s;
+        X2 = x2s;
+    } else {
+        C1 = cols + (size_t)c1 * nt;
+        X1 = x + (size_t)i1 * nt;
+        C2 = two ? cols + (size_t)c2 * nt : C1;   // read only when two
+        X2 = two ? x + (size_t)i2 * nt : X1;
+    }
     for (int q = threadIdx.x; q < (nt + 1) / 2; q += blockDim.x) {
         for (int e = 0; e < 2; ++e) {
             const int n = (e == 0) ? q : nt - 1 - q;
@@ -106,13 +120,17 @@ __global__ void k_toeplitz(int N, int nt, const double2* __restrict__ cols,
 int swr_launch_toeplitz(int N, int nt, const double2* cols, const double2* x, const double2* add,
                         double2* y, int mode, cudaStream_t s, const InstInfo* inst,
                         const int* blk_inst, int nblk_total, int ntmax) {
-    const int smem = 4 * (inst ? ntmax : nt) * (int)sizeof(double2);
-    if (smem > 227 * 1024) return -2;
-    if (cudaFuncSetAttribute(k_toeplitz, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess)
-        return -1;
-    k_toeplitz<<<inst ? nblk_total : 2 * N - 2, 256, smem, s>>>(N, nt, cols, x, add, y, mode, inst,
-                                                                 blk_inst);
+    const int nblk = inst ? nblk_total : 2 * N - 2;
+    const long long smem = 4LL * (inst ? ntmax : nt) * (long long)sizeof(double2);
+    if (smem > 227 * 1024) {
+        k_toeplitz<false><<<nblk, 256, 0, s>>>(N, nt, cols, x, add, y, mode, inst, blk_inst);
+    } else {
+        if (cudaFuncSetAttribute(k_toeplitz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return -1;
+        k_toeplitz<true><<<nblk, 256, (int)smem, s>>>(N, nt, cols, x, add, y, mode, inst,
+                                                      blk_inst);
+    }
     swr_count_launch(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -489,3 +489,42 @@ def test_bicgstab_time_dependent_matches_gmres():
     assert rel(out[1], out[0]) < TOL_SOLVE
     _, uTm = O.mono_interface(problem(wl))
     assert rel(out[1], uTm) < TOL_SOLVE
+
+
+@pytest.mark.parametrize("nt,want_M", [(15, 0), (16, 32), (2048, 4096), (2049, 0)])
+def test_toeplitz_fft_eligibility_edges(nt, want_M):
+    """The library's own choice at the edges of the FFT apply (16 <= nt <= 2048, transform
+    the power of two >= 2 nt - 1): the transform length it reports, and (I - L) x against
+    the oracle on either side of each edge."""
+    wl = W.config1(nx=121, nt=nt, nsub=3)
+    plan = gpu_plan(wl)
+    assert plan.get_stats()["toeplitz_fft_length"] == want_M
+    P = problem(wl)
+    cols = O.build_columns(P)
+    x = W.random_interface(wl.nblk, wl.nt, 19)
+    xi = torch.tensor(x.ravel(), dtype=torch.complex128, device="cuda")
+    y = torch.zeros_like(xi)
+    plan.apply_interface(xi, y)
+    plan.destroy()
+    assert rel(y.cpu().numpy(), O.apply_I_minus_L(P, cols, x)) < TOL_MARCH
+
+
+@pytest.mark.parametrize("nt,superposed", [(4259, 1), (4260, 0)])
+def test_s02_superposition_limit(nt, superposed):
+    """S_0^2 ends: u(T) is superposed, and the interface mismatch found by the Toeplitz
+    forward substitution with the trace, kernel and data in shared memory, up to
+    nt = 4259; beyond it the final march takes over.  Both against the monodomain
+    solution."""
+    from paper_1503_02564_gb300 import swr
+    wl = W.config1(nx=121, nt=nt, nsub=3)
+    wl.tc = swr.SWR_TC_S02
+    plan = gpu_plan(wl, tc=swr.SWR_TC_S02, precond=swr.SWR_PC_CAUSAL, restart=50, maxit=500,
+                    tol_abs=1e-11)
+    assert plan.get_stats()["superposed"] == superposed
+    g, uT, info = _solve(plan, wl)
+    plan.destroy()
+    assert info["residual"] < 1e-11
+    gs, uTm = O.mono_interface(problem(wl))
+    assert rel(uT, uTm) < TOL_SOLVE
+    assert rel(g, gs) < TOL_SOLVE
+    assert info["interface_jump"] < 1e-9

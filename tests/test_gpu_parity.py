@@ -528,3 +528,32 @@ def test_s02_superposition_limit(nt, superposed):
     assert rel(uT, uTm) < TOL_SOLVE
     assert rel(g, gs) < TOL_SOLVE
     assert info["interface_jump"] < 1e-9
+
+
+@pytest.mark.parametrize("where", ["V", "u0"])
+def test_device_status_reports_bad_inputs(where):
+    """The kernels' status word, read by the host after the build: a NaN in the potential
+    makes a pivot non-finite in the chunk factorisation (SWR_ERR_SINGULAR); a NaN in the
+    initial state reaches the marched state (SWR_ERR_NONFINITE).  Neither traps; the plan
+    is destroyed normally and a fresh plan on the same device then solves correctly."""
+    from paper_1503_02564_gb300 import swr
+    wl = CASES["config1_small"]()
+    V = np.array(wl.V, dtype=np.float64)
+    u0 = np.array(wl.u0, dtype=np.complex128)
+    if where == "V":
+        V[wl.nx // 3] = np.nan
+        want = swr.SWR_ERR_SINGULAR
+    else:
+        u0[wl.nx // 2] = complex(np.nan, 0.0)
+        want = swr.SWR_ERR_NONFINITE
+    plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
+                    node_off=wl.off, p=wl.sigma, vkind=wl.vkind)
+    with pytest.raises(swr.SWRError) as e:
+        plan.build_interface(torch.tensor(V, device="cuda"), torch.tensor(u0, device="cuda"))
+    assert e.value.status == want
+    plan.destroy()
+    plan = gpu_plan(wl)
+    g, uT, info = _solve(plan, wl)
+    plan.destroy()
+    _, uTm = O.mono_interface(problem(wl))
+    assert rel(uT, uTm) < TOL_SOLVE

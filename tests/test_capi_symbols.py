@@ -133,3 +133,16 @@ def test_batch_validation_refuses_mismatched_instances(libswr):
     h = ctypes.c_void_p()
     d = _desc()
     assert libswr.swr_plan_batch(ctypes.byref(d), 0, ctypes.byref(h), None) == S.SWR_ERR_ARG
+
+
+def test_binding_has_no_cpu_path(monkeypatch, tmp_path):
+    """The binding refuses host tensors (the compute path is the CUDA library only) and
+    raises when the library has not been built, instead of falling back to anything."""
+    import torch
+    from paper_1503_02564_gb300 import swr
+    with pytest.raises(TypeError):
+        swr._ptr(torch.zeros(4, dtype=torch.float64), torch.float64, 4, "V")
+    monkeypatch.setattr(swr, "_lib", None)
+    monkeypatch.setattr(swr, "LIB_PATH", str(tmp_path / "libswr.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        swr.lib()

@@ -12,7 +12,7 @@ recorded during the build).
 
 Reported: point-steps/s of all marches in the step (whole job), the solve time
 per step, the roofline of the march kernel (FP64-ALU bound), the CPU oracle's
-march throughput on the machine's host, and an end-to-end figure with host buffers.
+march throughput on the host CPU, and an end-to-end figure with host buffers.
 Multi-GPU runs (torchrun) are replicas: every rank solves its own copy.
 """
 import argparse

@@ -46,7 +46,7 @@ typedef enum swr_status {
     SWR_ERR_NOMEM = 6,          /* device allocation failed                              */
     SWR_ERR_CUDA = 7,           /* other CUDA runtime error                              */
     SWR_ERR_STATE = 8,          /* call order violated (e.g. solve before build)         */
-    SWR_ERR_UNSUPPORTED = 9     /* combination not provided by this build                */
+    SWR_ERR_UNSUPPORTED = 9     /* combination not supported by the library              */
 } swr_status;
 
 /* Potential kinds (Eq. Schequ: V(t,x) or f(u)). */

@@ -1362,7 +1362,8 @@ const char* swr_status_string(swr_status s) {
         case SWR_ERR_NOMEM: return "SWR_ERR_NOMEM: device allocation failed";
         case SWR_ERR_CUDA: return "SWR_ERR_CUDA: CUDA runtime error";
         case SWR_ERR_STATE: return "SWR_ERR_STATE: call order violated";
-        case SWR_ERR_UNSUPPORTED: return "SWR_ERR_UNSUPPORTED: not provided by this build";
+        case SWR_ERR_UNSUPPORTED:
+            return "SWR_ERR_UNSUPPORTED: combination not supported by the library";
     }
     return "unknown swr_status";
 }

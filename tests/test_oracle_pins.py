@@ -546,3 +546,49 @@ def test_nonlinear_adjoint_gradient_vanishes_for_a_conserved_norm():
     _, g0 = O.adjoint_gradient_nl(P, np.zeros(wl.nx))
     _, g = O.adjoint_gradient_nl(P, tgt)
     assert np.max(np.abs(g0)) <= 1e-12 * np.max(np.abs(g))
+
+
+def _paper_fixed_point_counts():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "fixed_point_counts_N2.txt")
+    out = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            name, count = line.split()
+            out[name] = int(count)
+    return out
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("tc", [O.TC_S02, O.TC_S03, O.TC_S04, O.TC_S12, O.TC_S14])
+def test_fixed_point_counts_match_the_paper(tc):
+    """The transmission operators themselves, not only the converged solution (which any
+    invertible operator reproduces): the oracle's fixed-point iteration count on the
+    paper's N = 2 comparison problem against the count the paper prints (Table 6).  The
+    grid is dx = 5e-4 instead of the paper's 1e-5 (a minute of CPU time instead of an
+    hour); the count hardly depends on it, so the pin allows one iteration either way.
+    The interface sits at x = 0, where V = -x^2 and its derivative vanish, so this pins the
+    S_0^2 core of every condition (c2, the beta coefficients, the flux exchange); their
+    W terms are pinned by the weight tests above."""
+    want = _paper_fixed_point_counts()[O.TC_NAMES[tc]]
+    wl = W.tc_comparison(nsub=2, nx=84001, nt=500)
+    P = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0, wl.V,
+                  vkind=wl.vkind, tc=tc, sigma=0j)
+    g0 = W.random_interface(wl.nblk, wl.nt, 1)
+    res = O.fixed_point(lambda g: O.apply_R(P, g), g0, tol=1e-10, maxit=20)
+    assert abs(res.iterations - want) <= 1, (O.TC_NAMES[tc], res.iterations, want)
+
+
+@pytest.mark.slow
+def test_fixed_point_count_pin_catches_a_planted_mistake(monkeypatch):
+    """The count pin has teeth: with c2 conjugated (e^{+i pi/4} instead of e^{-i pi/4}) the
+    same iteration does not converge within 10 iterations (the paper's count is 6)."""
+    good = O.s02_c2
+    monkeypatch.setattr(O, "s02_c2", lambda dt: np.conj(good(dt)))
+    wl = W.tc_comparison(nsub=2, nx=84001, nt=500)
+    P = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0, wl.V,
+                  vkind=wl.vkind, tc=O.TC_S03, sigma=0j)
+    g0 = W.random_interface(wl.nblk, wl.nt, 1)
+    res = O.fixed_point(lambda g: O.apply_R(P, g), g0, tol=1e-10, maxit=10)
+    assert res.iterations >= 10 and not res.converged

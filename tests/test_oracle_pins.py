@@ -651,3 +651,47 @@ def test_nonlinear_classical_count_matches_the_paper():
     res = O.fixed_point(lambda g: O.apply_R(P, g), np.zeros((P.nblk, nt), np.complex128),
                         tol=1e-10, maxit=want[N] + 5)
     assert res.converged and abs(res.iterations - want[N]) <= 1, (res.iterations, want[N])
+
+
+def _paper_preconditioned_counts():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "preconditioned_counts_N10.txt")
+    out = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            name, count = line.split()
+            out[name] = int(count)
+    return out
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("problem", ["5tx", "nls"])
+def test_preconditioned_counts_match_the_paper(problem):
+    """The preconditioner of Section 5 (P = I - L_0 from the zero-potential operator, P^{-1}
+    by inner GMRES from zero as in Eq. Pxg) inside the preconditioned fixed point: its
+    iteration count on the paper's N = 10 problems against the counts printed (17 for
+    V = 5tx, 11 for V = |u|^2), on grids of dx = 5e-3 and 2e-3, to one iteration."""
+    want = _paper_preconditioned_counts()[problem]
+    a0, b0, dt, nt, N = -21.0, 21.0, 1e-3, 500, 10
+    if problem == "5tx":
+        nx = 8401
+        x = np.linspace(a0, b0, nx)
+        t = np.arange(nt + 1) * dt
+        V = 5.0 * t[:, None] * x[None, :]
+        u0 = np.exp(-(x + 10.0) ** 2 + 20j * (x + 10.0))
+        kind = O.V_TIME
+    else:
+        nx = 21001
+        x = np.linspace(a0, b0, nx)
+        V = np.zeros(nx)
+        u0 = 2.0 / np.cosh(math.sqrt(2.0) * (x + 10.0)) * np.exp(20j * (x + 10.0))
+        kind = O.V_NONLINEAR
+    P = O.Problem(a0, b0, nx, dt, nt, W.equal_offsets(nx, N).astype(np.int64),
+                  u0.astype(np.complex128), V, vkind=kind, tc=O.TC_S02, sigma=0j, nl_coef=1.0)
+    P0 = O.zero_potential_problem(P)
+    Minv = O.make_precond_inner(P0, O.build_columns(P0, "zero_u0"))
+    step = lambda g: g - np.asarray(Minv((g - O.apply_R(P, g)).ravel())).reshape(g.shape)
+    res = O.fixed_point(step, np.zeros((P.nblk, nt), np.complex128), tol=1e-10,
+                        maxit=want + 5)
+    assert res.converged and abs(res.iterations - want) <= 1, (problem, res.iterations, want)

@@ -695,3 +695,27 @@ def test_preconditioned_counts_match_the_paper(problem):
     res = O.fixed_point(step, np.zeros((P.nblk, nt), np.complex128), tol=1e-10,
                         maxit=want + 5)
     assert res.converged and abs(res.iterations - want) <= 1, (problem, res.iterations, want)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("tc", [O.TC_S02, O.TC_S14])
+def test_gmres_counts_match_the_paper(tc):
+    """The oracle's GMRES (Saad's, restart 200, absolute true-residual test) on the paper's
+    N = 2 comparison problem, the interface operator built from the Toeplitz first columns
+    (the new algorithm): its iteration count against the paper's GMRES column (5), at
+    dx = 5e-4, to one iteration."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "gmres_counts_N2.txt")
+    want = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            name, count = line.split()
+            want[name] = int(count)
+    wl = W.tc_comparison(nsub=2, nx=84001, nt=500)
+    P = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0, wl.V,
+                  vkind=wl.vkind, tc=tc, sigma=0j)
+    res = O.solve_new(P, solver="gmres", tol=1e-10, restart=200, maxit=50,
+                      g0=W.random_interface(wl.nblk, wl.nt, 1))
+    w = want[O.TC_NAMES[tc]]
+    assert abs(res.iterations - w) <= 1, (O.TC_NAMES[tc], res.iterations, w)

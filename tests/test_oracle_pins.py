@@ -719,3 +719,27 @@ def test_gmres_counts_match_the_paper(tc):
                       g0=W.random_interface(wl.nblk, wl.nt, 1))
     w = want[O.TC_NAMES[tc]]
     assert abs(res.iterations - w) <= 1, (O.TC_NAMES[tc], res.iterations, w)
+
+
+@pytest.mark.slow
+def test_robin_nonlinear_preconditioned_count_matches_the_paper():
+    """The Robin condition itself (S-bar v = -i p v, p real, the paper's convention): the
+    preconditioned algorithm on the paper's |u|^2 problem, N = 10, p = 20, against the
+    count the paper prints (11), at dx = 2e-3, to one iteration (the oracle also gives the
+    paper's 12 for p = 5)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "robin_nl_counts.txt")
+    want = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            p, n, count = line.split()
+            want[(float(p), int(n))] = int(count)
+    a0, b0, dt, nt, N, nx, p = -21.0, 21.0, 1e-3, 500, 10, 21001, 20.0
+    x = np.linspace(a0, b0, nx)
+    u0 = 2.0 / np.cosh(math.sqrt(2.0) * (x + 10.0)) * np.exp(20j * (x + 10.0))
+    P = O.Problem(a0, b0, nx, dt, nt, W.equal_offsets(nx, N).astype(np.int64),
+                  u0.astype(np.complex128), np.zeros(nx), vkind=O.V_NONLINEAR, tc=O.TC_ROBIN,
+                  sigma=-1j * p, nl_coef=1.0)
+    res = O.solve_nonlinear(P, precond=True, tol=1e-10, maxit=want[(p, N)] + 5)
+    assert abs(res.iterations - want[(p, N)]) <= 1, (res.iterations, want[(p, N)])

@@ -61,6 +61,12 @@ def lib():
         L.or_p1_matrices.argtypes = [ctypes.c_int, ctypes.c_double, dp] + [dp] * 6
         L.or_causal_conv.restype = None
         L.or_causal_conv.argtypes = [ctypes.c_int, dp, dp, dp]
+        vp = ctypes.c_void_p
+        L.or_march_ext.restype = ctypes.c_int
+        L.or_march_ext.argtypes = [
+            ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, dp, ctypes.c_int,
+            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
+            ctypes.c_int, ctypes.c_int, dp, dp, dp, vp, vp, vp, dp, dp]
         _LIB = L
     return _LIB
 
@@ -266,6 +272,37 @@ def march(n, h, dt, nt, V, u0, *, vkind=V_STATIC, tc=TC_ROBIN, sigma=0.0, tc_lef
     return MarchResult(va, vb, uT, its, vsel)
 
 
+def march_ext(n, h, dt, nt, V, u0, *, tc=TC_ROBIN, sigma=0.0, tc_left=False,
+              tc_right=False, l=None, r=None, wl=None, wr=None) -> MarchResult:
+    """The static-V march of ``march`` carried in extended precision (C long double:
+    64-bit significand on x86-64, binary128 on AArch64); see or_march_ext.  The
+    inputs are the binary64 values that define the problem; the end traces va, vb
+    and u(T) come back as np.clongdouble.  Used to tell rounding from error where a
+    binary64 result cancels."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    assert V.ndim == 1
+    u0 = np.ascontiguousarray(u0, dtype=np.complex128)
+    lc = None if l is None else np.ascontiguousarray(l, dtype=np.complex128)
+    rc = None if r is None else np.ascontiguousarray(r, dtype=np.complex128)
+    beta = beta_coefficients(nt)
+    c2 = s02_c2(dt)
+    va = np.zeros(nt + 1, np.clongdouble)
+    vb = np.zeros(nt + 1, np.clongdouble)
+    uT = np.zeros(n, np.clongdouble)
+    sig = complex(sigma)
+    ctc = tc if tc <= TC_S02 else 2
+    wlc = None if (wl is None or not tc_left) else np.ascontiguousarray(wl, np.complex128)
+    wrc = None if (wr is None or not tc_right) else np.ascontiguousarray(wr, np.complex128)
+    if ctc == 2 and ((tc_left and wlc is None) or (tc_right and wrc is None)):
+        raise ValueError("weights needed at every end with a transmission condition")
+    st = lib().or_march_ext(n, h, dt, nt, _p(V), ctc, sig.real, sig.imag, c2.real, c2.imag,
+                            _p(beta), int(tc_left), int(tc_right), _p(u0), _p(lc), _p(rc),
+                            va.ctypes.data, vb.ctypes.data, uT.ctypes.data, _p(wlc), _p(wrc))
+    if st != 0:
+        raise ZeroDivisionError(f"zero pivot at row {-st - 1}")
+    return MarchResult(va, vb, uT, np.zeros(nt, np.int32))
+
+
 def tc_weights(P: Problem, j, side, V=None):
     """Weights w[n, s], 0 <= s <= n <= nt, of the discrete transmission operator at one
     end of subdomain j (side 0: a_j, side 1: b_j), S-bar v_n = sum_s w[n, s] v_s, written
@@ -421,6 +458,92 @@ def build_columns(P: Problem, mode="zero_u0", d=None, V=None):
                     col = col - d[blk_l(j + 1)]
                 cols[j, pb] = col
     return cols
+
+
+def _s_flux_ext(P: Problem, vtrace, j, side):
+    """s_flux in extended precision: the operator's binary64 coefficients (sigma, c2,
+    beta, the weights of tc_weights) applied to an np.clongdouble trace in
+    np.clongdouble arithmetic; entries n = 1..nt.  Also returns the magnitude of the
+    summands of every entry, sum_s |K[n, s]| |v_s| (K the operator's weights)."""
+    v = np.asarray(vtrace, np.clongdouble)
+    av = np.abs(v)
+    nt = P.nt
+    out = np.zeros(nt, np.clongdouble)
+    mag = np.zeros(nt, np.longdouble)
+    if P.tc == TC_ROBIN:
+        k = 2 * np.clongdouble(P.sigma)
+        return k * v[1:], np.abs(k) * av[1:]
+    if P.tc == TC_S02:
+        beta = P.beta().astype(np.longdouble)
+        c2 = 2 * np.clongdouble(P.c2())
+        for n in range(1, nt + 1):
+            acc = np.clongdouble(0)
+            for s_ in range(n + 1):
+                acc += beta[n - s_] * v[s_]
+                mag[n - 1] += abs(beta[n - s_]) * av[s_]
+            out[n - 1] = c2 * acc
+        return out, np.abs(c2) * mag
+    nb, nside = (j + 1, 0) if side == 1 else (j - 1, 1)
+    w = (tc_weights(P, j, side).astype(np.clongdouble)
+         + tc_weights(P, nb, nside).astype(np.clongdouble))
+    for n in range(1, nt + 1):
+        acc = np.clongdouble(0)
+        for s_ in range(n + 1):
+            acc += w[n, s_] * v[s_]
+            mag[n - 1] += abs(w[n, s_]) * av[s_]
+        out[n - 1] = acc
+    return out, mag
+
+
+def build_ext(P: Problem):
+    """d = R 0 and the first columns (zero-u0 form) of ``build_d`` / ``build_columns``
+    for a static potential, every march and flux in extended precision (march_ext).
+    Returns (d, cols, d_mag, cols_mag): d and cols as np.clongdouble arrays shaped like
+    theirs, and for every entry the magnitude of the summands that form it,
+    |input flux| + sum_s |K[n, s]| |v_s|, which bounds what rounding of the trace v can
+    do to an entry whose summands cancel (an almost transparent condition)."""
+    if P.vkind != V_STATIC:
+        raise NotImplementedError("build_ext: static V only")
+    N, nt = P.nsub, P.nt
+    d = np.zeros((P.nblk, nt), np.clongdouble)
+    cols = np.zeros((N, 4, nt), np.clongdouble)
+    dmag = np.zeros((P.nblk, nt), np.longdouble)
+    cmag = np.zeros((N, 4, nt), np.longdouble)
+    e1 = np.zeros(nt, np.complex128)
+    e1[0] = 1.0
+    zero = np.zeros(nt, np.complex128)
+    for j in range(N):
+        a, b = int(P.off[j]), int(P.off[j + 1])
+        wl = tc_weights(P, j, 0) if (P.tc >= TC_S03 and j > 0) else None
+        wr = tc_weights(P, j, 1) if (P.tc >= TC_S03 and j < N - 1) else None
+
+        def run(u0, lj, rj):
+            return march_ext(b - a + 1, P.h, P.dt, nt, P.local_V(j), u0, tc=P.tc,
+                             sigma=P.sigma, tc_left=(j > 0), tc_right=(j < N - 1),
+                             l=lj, r=rj, wl=wl, wr=wr)
+        m = run(P.u0[a:b + 1], zero if j > 0 else None, zero if j < N - 1 else None)
+        if j > 0:
+            d[blk_r(j - 1)], dmag[blk_r(j - 1)] = _s_flux_ext(P, m.va, j, 0)
+        if j < N - 1:
+            d[blk_l(j + 1)], dmag[blk_l(j + 1)] = _s_flux_ext(P, m.vb, j, 1)
+        z0 = np.zeros(b - a + 1, np.complex128)
+        for which in ("l", "r"):
+            if (which == "l" and j == 0) or (which == "r" and j == N - 1):
+                continue
+            lj = (e1 if which == "l" else zero) if j > 0 else None
+            rj = (e1 if which == "r" else zero) if j < N - 1 else None
+            m = run(z0, lj, rj)
+            pa = 0 if which == "l" else 1
+            pb = 2 if which == "l" else 3
+            if j > 0:
+                f, mg = _s_flux_ext(P, m.va, j, 0)
+                cols[j, pa] = f - np.asarray(lj, np.clongdouble)
+                cmag[j, pa] = mg + np.abs(np.asarray(lj, np.clongdouble))
+            if j < N - 1:
+                f, mg = _s_flux_ext(P, m.vb, j, 1)
+                cols[j, pb] = f - np.asarray(rj, np.clongdouble)
+                cmag[j, pb] = mg + np.abs(np.asarray(rj, np.clongdouble))
+    return d, cols, dmag, cmag
 
 
 def causal_conv(c, x):

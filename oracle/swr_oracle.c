@@ -287,3 +287,141 @@ void or_causal_conv(int nt, const double *c_, const double *x_, double *y_)
         y[t] = acc;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* The same march in extended precision (static V, linear ends).            */
+/* ------------------------------------------------------------------------ */
+/*
+ * or_march_ext repeats or_march for a static potential (vkind 0) with every
+ * intermediate quantity in C `long double` (x86-64: the 64-bit-significand
+ * extended format, unit roundoff 5.4e-20; AArch64: IEEE binary128, 9.6e-35).
+ * The inputs are the same binary64 values as for or_march (they define the
+ * problem); the matrices of Eq. AvML, the Thomas solves, the S_0^2 history
+ * b_n and the CN update are carried in long double, and the end traces and
+ * u(T) are returned in long double.  It exists to decide, where a result
+ * cancels (the flux 2 S-tilde v - l of an almost transparent condition), how
+ * much of a difference between two binary64 computations is rounding of
+ * either, and it is kept as literal as or_march: one Thomas solve per step.
+ *
+ * Arguments as for or_march (tc 0 Robin, 1 S_0^2, 2 weights wl / wr), except:
+ * no potential kind, no nonlinear arguments, no selected nodes; va, vb (nt+1)
+ * and uT (n) are arrays of `long double complex`.
+ * Returns 0, or -(i+1) when pivot i of a step is exactly zero.
+ */
+typedef long double complex cplxl;
+
+static int or_thomas_ext(int n, const cplxl *lo, const cplxl *dg, cplxl *x, cplxl *work)
+{
+    int i;
+    cplxl piv = dg[0];
+    if (piv == 0.0L) return -1;
+    work[0] = (n > 1) ? lo[0] / piv : 0.0L;
+    x[0] = x[0] / piv;
+    for (i = 1; i < n; ++i) {
+        piv = dg[i] - lo[i - 1] * work[i - 1];
+        if (piv == 0.0L) return -(i + 1);
+        work[i] = (i < n - 1) ? lo[i] / piv : 0.0L;
+        x[i] = (x[i] - lo[i - 1] * x[i - 1]) / piv;
+    }
+    for (i = n - 2; i >= 0; --i) x[i] = x[i] - work[i] * x[i + 1];
+    return 0;
+}
+
+int or_march_ext(int n, double h_, double dt_, int nt, const double *V, int tc,
+                 double sig_re, double sig_im, double c2_re, double c2_im,
+                 const double *beta, int tc_left, int tc_right, const double *u0_,
+                 const double *l_, const double *r_, long double *va_, long double *vb_,
+                 long double *uT_, const double *wl_, const double *wr_)
+{
+    const cplx *u0 = (const cplx *)u0_, *l = (const cplx *)l_, *r = (const cplx *)r_;
+    const cplx *wl = (const cplx *)wl_, *wr = (const cplx *)wr_;
+    cplxl *va = (cplxl *)va_, *vb = (cplxl *)vb_, *uT = (cplxl *)uT_;
+    const long nw = nt + 1;
+    const long double h = h_, dt = dt_;
+    const cplxl I2dt = 2.0L * I / dt;
+    const cplxl sigma = (long double)sig_re + I * (long double)sig_im;
+    const cplxl c2 = (long double)c2_re + I * (long double)c2_im;
+    const cplxl sigma0 = (tc == 0) ? sigma : c2 * (long double)beta[0];
+    long double *md = calloc(n, sizeof(long double)), *mo = calloc(n, sizeof(long double));
+    long double *sd = calloc(n, sizeof(long double)), *so = calloc(n, sizeof(long double));
+    long double *wd = calloc(n, sizeof(long double)), *wo = calloc(n, sizeof(long double));
+    cplxl *u = malloc(sizeof(cplxl) * n), *v = malloc(sizeof(cplxl) * n);
+    cplxl *dg = malloc(sizeof(cplxl) * n), *lo = malloc(sizeof(cplxl) * n);
+    cplxl *work = malloc(sizeof(cplxl) * n);
+    int status = 0, i, t, e, s;
+
+    /* P1 matrices of Eq. AvML, element by element (as or_p1_matrices). */
+    for (e = 0; e < n - 1; ++e) {
+        const long double We = V[e], Wf = V[e + 1];
+        md[e] += h / 3.0L;
+        md[e + 1] += h / 3.0L;
+        mo[e] += h / 6.0L;
+        sd[e] += 1.0L / h;
+        sd[e + 1] += 1.0L / h;
+        so[e] += -1.0L / h;
+        wd[e] += h / 12.0L * (3.0L * We + Wf);
+        wd[e + 1] += h / 12.0L * (We + 3.0L * Wf);
+        wo[e] += h / 12.0L * (We + Wf);
+    }
+    for (i = 0; i < n; ++i) u[i] = (long double)creal(u0[i]) + I * (long double)cimag(u0[i]);
+    va[0] = u[0];
+    vb[0] = u[n - 1];
+
+    for (t = 1; t <= nt && status == 0; ++t) {
+        for (i = 0; i < n; ++i) dg[i] = I2dt * md[i] - sd[i] + wd[i];
+        for (i = 0; i < n - 1; ++i) lo[i] = I2dt * mo[i] - so[i] + wo[i];
+        if (tc_left)
+            dg[0] -= (tc == 2) ? (long double)creal(wl[(long)t * nw + t])
+                                     + I * (long double)cimag(wl[(long)t * nw + t])
+                               : sigma0;
+        if (tc_right)
+            dg[n - 1] -= (tc == 2) ? (long double)creal(wr[(long)t * nw + t])
+                                         + I * (long double)cimag(wr[(long)t * nw + t])
+                                   : sigma0;
+        /* (2i/dt) M u_{n-1} */
+        for (i = 0; i < n; ++i) {
+            cplxl acc = md[i] * u[i];
+            if (i > 0) acc += mo[i - 1] * u[i - 1];
+            if (i < n - 1) acc += mo[i] * u[i + 1];
+            v[i] = I2dt * acc;
+        }
+        /* + b_n (history of the end trace), - Q^T (l_n, r_n)^T */
+        if (tc == 1 && tc_left) {
+            cplxl acc = 0.0L;
+            for (s = 0; s < t; ++s) acc += (long double)beta[t - s] * va[s];
+            v[0] += c2 * acc;
+        }
+        if (tc == 1 && tc_right) {
+            cplxl acc = 0.0L;
+            for (s = 0; s < t; ++s) acc += (long double)beta[t - s] * vb[s];
+            v[n - 1] += c2 * acc;
+        }
+        if (tc == 2 && tc_left) {
+            cplxl acc = 0.0L;
+            for (s = 0; s < t; ++s)
+                acc += ((long double)creal(wl[(long)t * nw + s])
+                        + I * (long double)cimag(wl[(long)t * nw + s])) * va[s];
+            v[0] += acc;
+        }
+        if (tc == 2 && tc_right) {
+            cplxl acc = 0.0L;
+            for (s = 0; s < t; ++s)
+                acc += ((long double)creal(wr[(long)t * nw + s])
+                        + I * (long double)cimag(wr[(long)t * nw + s])) * vb[s];
+            v[n - 1] += acc;
+        }
+        if (tc_left && l)
+            v[0] -= (long double)creal(l[t - 1]) + I * (long double)cimag(l[t - 1]);
+        if (tc_right && r)
+            v[n - 1] -= (long double)creal(r[t - 1]) + I * (long double)cimag(r[t - 1]);
+
+        status = or_thomas_ext(n, lo, dg, v, work);
+        for (i = 0; i < n; ++i) u[i] = 2.0L * v[i] - u[i];
+        va[t] = v[0];
+        vb[t] = v[n - 1];
+    }
+    for (i = 0; i < n; ++i) uT[i] = u[i];
+    free(md); free(mo); free(sd); free(so); free(wd); free(wo);
+    free(u); free(v); free(dg); free(lo); free(work);
+    return status;
+}

@@ -115,15 +115,32 @@ def test_long_subdomains_refused_where_not_built():
     assert e.value.status == swr.SWR_ERR_UNSUPPORTED
 
 
+def rel_to_summands(a, ref, mag):
+    """|| a - ref || / || mag ||: the error of an output relative to the magnitude of the
+    summands that form it (mag = |input flux| + sum_s |K| |v_s|, from the extended
+    reference).  Where the flux of an almost transparent condition cancels (the S_0^2
+    family on fine grids: |mag| / |ref| ~ 4e4 at h = 7.7e-4), rounding of the marched
+    trace v at the level cond(A) * eps ~ 1e-13 moves the output by that much relative
+    to its summands, whoever computes it; this is the measure in which a march output is
+    accurate."""
+    a = np.asarray(a, np.clongdouble).ravel()
+    ref = np.asarray(ref, np.clongdouble).ravel()
+    e = np.linalg.norm((a - ref).astype(np.complex128))
+    return float(e / np.linalg.norm(np.asarray(mag, np.float64).ravel()))
+
+
 @pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02, O.TC_S14])
 @pytest.mark.parametrize("nx,nsub", [(20001, 2), (4001, 16), (130001, 2)])
 def test_forced_grid_march_matches_cluster_march(nx, nsub, tc, monkeypatch):
     """SWR_LONG_MARCH=1 runs the grid-wide march where the cluster march also applies:
     the two agree to rounding (bitwise when both take 16-node chunks: the arithmetic per
-    node is the same), and both match the oracle.  At h = 7.7e-4 (130001 nodes on
-    (-50, 50)) both marches' S_0^2 and S_1^4 columns differ from the oracle by ~4e-10
-    alike: the flux 2 c2 sum beta_{n-s} v_s cancels by ~1e2, amplifying the march's
-    ~5e-12 rounding at cond(A) ~ 3 dt / h^2 ~ 5e3; so 2e-9 there, 1e-10 elsewhere."""
+    node is the same), and both match the oracle's extended-precision build
+    (oracle.build_ext, every march and flux in long double) to 1e-10 relative to the
+    summands of each output.  At h = 7.7e-4 (130001 nodes on (-50, 50)) the S_0^2 and
+    S_1^4 columns are ~5e-5 formed from summands of size ~1 (the condition is almost
+    transparent), so the binary64 oracle itself sits ~3e-10 from the extended reference
+    in plain relative terms and ~1e-14 relative to the summands; the plain relative error
+    of d (no such cancellation) is held to 1e-10 as well."""
     wl = W.config2(nsub=nsub, nx=nx, nt=12)
     out = []
     for force in ("0", "1"):
@@ -135,11 +152,15 @@ def test_forced_grid_march_matches_cluster_march(nx, nsub, tc, monkeypatch):
         plan.destroy()
         out.append((d.cpu().numpy(), cols.cpu().numpy()))
     P = problem(wl, tc)
-    dref, cref = O.build_d(P), O.build_columns(P).ravel()
-    print("d: cluster %.2e grid %.2e  cols: cluster %.2e grid %.2e  grid-cluster %.2e %.2e" % (
-        rel(out[0][0], dref), rel(out[1][0], dref), rel(out[0][1], cref), rel(out[1][1], cref),
-        rel(out[1][0], out[0][0]), rel(out[1][1], out[0][1])))
+    dx, cx, dmag, cmag = O.build_ext(P)
+    print("d: cluster %.2e grid %.2e  cols: cluster %.2e grid %.2e (plain %.2e %.2e)"
+          "  grid-cluster %.2e %.2e" % (
+              rel_to_summands(out[0][0], dx, dmag), rel_to_summands(out[1][0], dx, dmag),
+              rel_to_summands(out[0][1], cx, cmag), rel_to_summands(out[1][1], cx, cmag),
+              rel(out[0][1], cx.astype(np.complex128)), rel(out[1][1], cx.astype(np.complex128)),
+              rel(out[1][0], out[0][0]), rel(out[1][1], out[0][1])))
     assert rel(out[1][0], out[0][0]) < 1e-11 and rel(out[1][1], out[0][1]) < 1e-11
-    tol = 2e-9 if (nx > 100000 and tc != O.TC_ROBIN) else 1e-10
     for dd, cc in out:
-        assert rel(dd, dref) < 1e-10 and rel(cc, cref) < tol
+        assert rel(dd, dx.astype(np.complex128)) < TOL_MARCH
+        assert rel_to_summands(dd, dx, dmag) < TOL_MARCH
+        assert rel_to_summands(cc, cx, cmag) < TOL_MARCH

@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--nsub", default=",".join(str(n) for n in NSUBS))
     ap.add_argument("--precond", default="causal", choices=["causal", "none"])
     ap.add_argument("--workload", default="scaling",
-                    choices=["scaling", "timedep", "adjoint", "batch", "nonlinear", "tcs"],
+                    choices=["scaling", "timedep", "adjoint", "batch", "nonlinear", "tcs",
+                             "fp64peak"],
                     help="scaling: the N in {16,64,256,500} static-potential step (default); "
                          "timedep: the time-dependent potential case (60001 nodes, 1000 steps, "
                          "N = 64, GMRES preconditioned by the mean-potential operator); "
@@ -74,7 +75,8 @@ def parse():
                          "the misfit gradient dJ/dV0 by swr_adjoint (checkpoints every 50); "
                          "tcs: the comparison of transmission conditions and interface solvers "
                          "in the setting of the paper's Section 6 (V=-x^2 on (-21,21), dx=1e-5, "
-                         "N in {2,500}, random g0)")
+                         "N in {2,500}, random g0); fp64peak: the FP64 throughput probes "
+                         "(DFMA and DMMA m8n8k4), each timed for >= 1 s with clocks sampled")
     ap.add_argument("--tc", default="robin", choices=["robin", "s02"],
                     help="transmission condition of the scaling workload: Robin "
                          "p = sqrt(5) e^{-i pi/4} (default) or the order-2 potential "
@@ -290,6 +292,51 @@ def cpu_oracle_adjoint_nl_sample(wl_full, nt_sample):
     dt = time.perf_counter() - t0
     ps = 2 * P.nx * nt_sample
     return ps / dt, dt, ps
+
+
+def fp64_probe(kind, seconds, dev, sampler=None):
+    """Run the library's FP64 throughput probe (kind 0: DFMA, 1: DMMA m8n8k4) for about
+    `seconds` of device time after a calibration launch; returns (GFLOP/s, ms, clocks)."""
+    import torch
+    from paper_1503_02564_gb300 import swr
+    blocks, threads = 152 * 4, 256
+    sink = torch.empty(blocks * threads, dtype=torch.float64, device=dev)
+    iters = 2000
+    swr.swr_fp64_peak(kind, iters, blocks, threads, sink)            # warm-up
+    flops, ms = swr.swr_fp64_peak(kind, iters, blocks, threads, sink)
+    iters = max(iters, int(iters * seconds * 1e3 / max(ms, 1e-3)))
+    if sampler is not None:
+        sampler.start()
+    flops, ms = swr.swr_fp64_peak(kind, iters, blocks, threads, sink)
+    clocks = sampler.stop() if sampler is not None else None
+    if not torch.isfinite(sink).all():
+        raise RuntimeError("FP64 probe produced non-finite values")
+    return flops / (ms * 1e-3) / 1e9, ms, clocks
+
+
+def run_fp64peak(args):
+    """FP64 DFMA and DMMA throughput on this GPU, each timed for >= 1 s with the SM
+    clock sampled during the launch (time x median MHz reported beside each)."""
+    import torch
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    out = {}
+    for kind, name in ((0, "dfma"), (1, "dmma_m8n8k4")):
+        gf, ms, clocks = fp64_probe(kind, 1.5, dev, ClockSampler(local))
+        out[name] = {"gflops": gf, "ms": ms, "clocks": clocks,
+                     "ms_x_median_mhz": ms * clocks["sm_mhz"] if clocks else None,
+                     "gflops_per_ghz": gf / (clocks["sm_mhz"] * 1e-3) if clocks else None}
+    line = {"metric": "FP64 throughput (DFMA vector pipe and DMMA m8n8k4 tensor path)",
+            "value": out["dfma"]["gflops"], "unit": "GFLOP/s", "n_gpus": 1, "steps": 1,
+            "warmup": 1, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fp64peak: 608 CTAs x 256 threads, >= 1 s per probe",
+                       "dfma": "8 independent fma chains per thread",
+                       "dmma": "4 independent m8n8k4 accumulator tiles per warp"},
+            "probes": out,
+            "nominal_dfma_gflops_at_max_clock": FP64_PEAK_GFLOPS}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -543,6 +590,8 @@ def main():
         return run_batch(args)
     if args.workload == "tcs":
         return run_tcs(args)
+    if args.workload == "fp64peak":
+        return run_fp64peak(args)
     import numpy as np
     import torch
     from paper_1503_02564_gb300 import swr

@@ -319,7 +319,10 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats *out, int32_t reset);
  *           synchronises it at the end to report a bounded-wait timeout.
  * The first call on a device looks up the device address of the library array
  * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  All calls share the one array: calls that overlap on the
+ * any stream capture.  The lookup is repeated only when the device's context has
+ * changed (e.g. after cudaDeviceReset).  Every call copies the status word to the
+ * host and synchronises the stream before it returns.  All calls share the one
+ * array: calls that overlap on the
  * GPU (other streams, other threads) race and give wrong results.  Each call
  * clears the array's progress counters and status word; the other entries are
  * written before they are read.
@@ -330,6 +333,34 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats *out, int32_t reset);
 swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t sweeps,
                                     const double *cols, const double *y, double *x,
                                     void *stream);
+
+/* FP64 throughput probe: the denominator of the marches' roofline (no counterpart
+ * in the paper; the march is FP64-bound on this part and its peak rate is measured,
+ * not taken from a datasheet).  One timed launch of `blocks` CTAs of `threads`
+ * threads (32..256, a multiple of 32) on stream (cudaStream_t as void*):
+ *   kind 0: DFMA, each thread `iters` rounds of 8 independent fused multiply-add
+ *           chains (2 flops each);
+ *   kind 1: DMMA, each warp `iters` rounds of 4 independent
+ *           mma.sync.aligned.m8n8k4 f64 products (512 flops each).
+ * sink: double[blocks * threads] (device) receives the chains' values; *flops
+ * (host) the flops executed; *ms (host) the launch's device time from CUDA events
+ * on the stream.  Synchronises the stream.
+ * Errors: SWR_ERR_ARG (kind, sizes, NULL pointers), SWR_ERR_CUDA. */
+swr_status swr_fp64_peak(int32_t kind, int64_t iters, int32_t blocks, int32_t threads,
+                         double *sink, double *flops, float *ms, void *stream);
+
+/* TEST HOOK of the bounded device waits (no counterpart in the paper; off by
+ * default, for failure-detection tests).  The causal substitution (CAUSAL
+ * preconditioner, SWR_SOLVER_CAUSAL, swr_causal_solve_noalloc) hands values between
+ * the CTAs of one cooperative launch through progress counters, and every wait on a
+ * counter gives up after a bounded number of polls (about 1-2 s), raising
+ * SWR_ERR_TIMEOUT.  On the current device this sets
+ *   max_polls: the poll limit of those waits (<= 0: the default);
+ *   withhold:  an interface (global index) whose CTA never publishes its progress,
+ *              so that its neighbours' waits run out (< 0: none, the default).
+ * Affects launches enqueued after the call; restore with (0, -1).
+ * Errors: SWR_ERR_CUDA. */
+swr_status swr_test_wait_hook(int64_t max_polls, int32_t withhold);
 
 /* Number of CUDA kernels this library has launched in this process, over all
  * plans (a monotonically increasing counter; host-only, no device work). */

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libswr.so")
 SOURCES = ["swr_march.cu", "swr_march_nl.cu", "swr_march_long.cu", "swr_krylov.cu",
-           "swr_capi.cu", "swr_noalloc.cu"]
+           "swr_capi.cu", "swr_noalloc.cu", "swr_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -1370,6 +1370,10 @@ const char* swr_status_string(swr_status s) {
 
 int64_t swr_kernel_launch_count(void) { return (int64_t)g_launches.load(); }
 
+swr_status swr_test_wait_hook(int64_t max_polls, int32_t withhold) {
+    return swr_set_wait_hook((long long)max_polls, (int)withhold) == 0 ? SWR_OK : SWR_ERR_CUDA;
+}
+
 void swr_destroy(swr_plan_t p) {
     if (!p) return;
     cudaStreamSynchronize(p->s);
@@ -2101,10 +2105,11 @@ swr_status swr_apply_precond(swr_plan_t p, const double* y, double* x) {
     if (!p || !y || !x || x == y) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     if (!has_precond(p)) return SWR_ERR_STATE;
+    // the status word reports this call's device errors (a bounded wait that gave up)
+    CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), p->s));
     swr_status st = apply_M(p, reinterpret_cast<const double2*>(y), reinterpret_cast<double2*>(x));
     if (st) return st;
-    CK(cudaStreamSynchronize(p->s));
-    return SWR_OK;
+    return read_status(p);
 }
 
 swr_status swr_get_stats(swr_plan_t p, swr_stats* out, int32_t reset) {

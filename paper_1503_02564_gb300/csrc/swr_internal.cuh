@@ -300,6 +300,10 @@ int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* la
                            int H, cudaStream_t s, const InstInfo* inst = nullptr,
                            const int* if_inst = nullptr, int nif_total = 0);
 int swr_causal_capacity(int nt);
+// Test hook of the substitution's bounded waits on the current device: poll limit
+// (<= 0: the default, about 1-2 s) and an interface whose progress is never
+// published (< 0: none).  Returns 0 or -1 (CUDA error).
+int swr_set_wait_hook(long long max_polls, int withhold);
 size_t swr_causal_scratch_bytes(int N);
 int swr_launch_lag0_setup(int N, int nt, const double2* cols, double2* lag0, cudaStream_t s,
                           const InstInfo* inst = nullptr, const int* if_inst = nullptr,

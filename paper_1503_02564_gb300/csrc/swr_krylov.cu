@@ -765,6 +765,13 @@ namespace {
 constexpr long long kWaitPolls = 4000000;    // about 1-2 s with the back-off below
 }
 
+// Test hook of the bounded waits (swr_test_wait_hook; defaults: the poll limit above,
+// no interface withheld).  With d_wait_withhold = k >= 0, interface k's CTA never
+// publishes its progress, so its neighbours' waits run out after d_wait_poll_limit
+// polls and every CTA leaves through the abort flag with ST_TIMEOUT raised.
+__device__ long long d_wait_poll_limit = kWaitPolls;
+__device__ int d_wait_withhold = -1;
+
 __device__ __forceinline__ int load_acquire(const int* p) {
     cuda::atomic_ref<const int, cuda::thread_scope_device> r(*p);
     return r.load(cuda::memory_order_acquire);
@@ -778,14 +785,14 @@ __device__ __forceinline__ void store_release(int* p, int v) {
 // its instance) have reached `target`; returns false (after raising the abort
 // flag) on timeout or when another CTA aborted.
 __device__ bool wait_neighbours(int k, bool hl, bool hr, int target, const int* progress,
-                                int* abortf, int* status) {
+                                int* abortf, int* status, long long lim) {
     long long polls = 0;
     for (int side = 0; side < 2; ++side) {
         const int nb = (side == 0) ? k - 1 : k + 1;
         if ((side == 0 && !hl) || (side == 1 && !hr)) continue;
         while (load_acquire(progress + nb) < target) {
             if (load_acquire(abortf) != 0) return false;
-            if (++polls > kWaitPolls) {
+            if (++polls > lim) {
                 atomicOr(status, ST_TIMEOUT);
                 store_release(abortf, 1);
                 return false;
@@ -797,11 +804,12 @@ __device__ bool wait_neighbours(int k, bool hl, bool hr, int target, const int* 
 }
 
 // Wait until interface nb has reached `target` (one lane per interface waited on).
-__device__ bool wait_one(int nb, int target, const int* progress, int* abortf, int* status) {
+__device__ bool wait_one(int nb, int target, const int* progress, int* abortf, int* status,
+                         long long lim) {
     long long polls = 0;
     while (load_acquire(progress + nb) < target) {
         if (load_acquire(abortf) != 0) return false;
-        if (++polls > kWaitPolls) {
+        if (++polls > lim) {
             atomicOr(status, ST_TIMEOUT);
             store_release(abortf, 1);
             return false;
@@ -937,6 +945,8 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
     // global interface kg (progress, sweep values, lag-0 blocks); local k within its
     // instance (blocks, columns)
     const int kg = k0 + blockIdx.x;
+    const long long lim = d_wait_poll_limit;
+    const bool publish = (kg != d_wait_withhold);     // false only under the test hook
     int k = kg;
     if (inst) {
         const InstInfo I = inst[if_inst[kg]];
@@ -1011,13 +1021,13 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         if (threadIdx.x == 0) {
             xsw[2 * kg] = y[(size_t)(2 * k) * nt];
             xsw[2 * kg + 1] = y[(size_t)(2 * k + 1) * nt];
-            store_release(progress + kg, 1);
+            if (publish) store_release(progress + kg, 1);
         }
         __syncthreads();
         for (int n = 0; n < nt; ++n) {
             if (w == 0) {
                 bool ok = true;
-                if (waits) ok = wait_one(kg + d, n + 1, progress, abortf, status);
+                if (waits) ok = wait_one(kg + d, n + 1, progress, abortf, status, lim);
                 ok = __all_sync(0xffffffffu, ok);
                 if (lane == 0) s_go = ok ? 1 : 0;
             }
@@ -1053,7 +1063,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                     P[0] = cadd(y[(size_t)(2 * k) * nt + n + 1], cadd(h[0], h[1]));
                     P[1] = cadd(y[(size_t)(2 * k + 1) * nt + n + 1], cadd(h[2], h[3]));
                 }
-                store_release(progress + kg, n + 2);           // orders x_n and P_{n+1}
+                if (publish) store_release(progress + kg, n + 2);   // orders x_n and P_{n+1}
             }
         }
     } else {
@@ -1083,7 +1093,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                 // lanes 0 and 1 wait for the left and right neighbours' values < n
                 bool ok = true;
                 if (lane < 2 && (lane == 0 ? has_l : has_r))
-                    ok = wait_one(kg + (lane == 0 ? -1 : 1), n * S1, progress, abortf, status);
+                    ok = wait_one(kg + (lane == 0 ? -1 : 1), n * S1, progress, abortf, status, lim);
                 ok = __all_sync(0xffffffffu, ok);
                 if (lane == 0) s_go = ok ? 1 : 0;
             }
@@ -1107,9 +1117,9 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                         double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif_all;
                         out[2 * kg] = z1;
                         out[2 * kg + 1] = z2;
-                        store_release(progress + kg, n * S1 + sw);
+                        if (publish) store_release(progress + kg, n * S1 + sw);
                         if (!wait_neighbours(kg, has_l, has_r, n * S1 + sw, progress, abortf,
-                                             status))
+                                             status, lim))
                             break;
                         const double2 xr = has_r ? out[2 * (kg + 1)] : zero;       // r_{k+1}
                         const double2 xl = has_l ? out[2 * (kg - 1) + 1] : zero;   // l_k
@@ -1119,7 +1129,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                     }
                     x[(size_t)(2 * k) * nt + n] = z1;
                     x[(size_t)(2 * k + 1) * nt + n] = z2;
-                    store_release(progress + kg, (n + 1) * S1);    // orders the x writes above
+                    if (publish) store_release(progress + kg, (n + 1) * S1);   // orders x above
                 }
             } else {
                 history(n);
@@ -1127,6 +1137,15 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             __syncthreads();                                   // B2
         }
     }
+}
+
+int swr_set_wait_hook(long long max_polls, int withhold) {
+    const long long lim = max_polls > 0 ? max_polls : kWaitPolls;
+    const int wh = withhold >= 0 ? withhold : -1;
+    if (cudaMemcpyToSymbol(d_wait_poll_limit, &lim, sizeof(lim)) != cudaSuccess ||
+        cudaMemcpyToSymbol(d_wait_withhold, &wh, sizeof(wh)) != cudaSuccess)
+        return -1;
+    return 0;
 }
 
 size_t swr_causal_scratch_bytes(int N) {

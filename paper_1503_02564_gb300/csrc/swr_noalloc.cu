@@ -13,7 +13,11 @@
 // library holds it (about 135 KB) until the process exits.  Host code must not
 // hand the array's name to a kernel: on the host it is only a stand-in symbol.
 // Its device address is looked up with cudaGetSymbolAddress once per device,
-// with that device current, the first time the entry point runs there.
+// with that device current, the first time the entry point runs there, and again
+// only if the device's context has changed since (after a cudaDeviceReset the
+// array lives at a new address in the new context).
+#include <cuda.h>   // CUcontext / CUresult types of cuCtxGetId (found at run time)
+
 #include <mutex>
 
 #include "swr_internal.cuh"
@@ -29,6 +33,30 @@ constexpr size_t kCausalElems = (kCausalBytes + sizeof(double2) - 1) / sizeof(do
 
 std::mutex g_setup_mutex;
 double2* g_scratch_addr[kNoallocMaxDevices] = {};
+unsigned long long g_scratch_ctx[kNoallocMaxDevices] = {};
+
+// Unique id of the current context (cuCtxGetId, looked up through the runtime so
+// that the library needs no link to the driver library); 0 when unavailable, in
+// which case the address is looked up on every call.
+unsigned long long current_context_id() {
+    typedef CUresult (*ctx_id_fn)(CUcontext, unsigned long long*);
+    static ctx_id_fn fn = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        cudaGetLastError();
+        fn = reinterpret_cast<ctx_id_fn>(f);
+        looked_up = true;
+    }
+    unsigned long long id = 0;
+    if (!fn || fn(nullptr, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -48,13 +76,16 @@ extern "C" swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t
     double2* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_addr[dev]) {
+        const unsigned long long ctx = current_context_id();
+        if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
             void* addr = nullptr;
             if (cudaGetSymbolAddress(&addr, g_noalloc_scratch) != cudaSuccess || !addr) {
                 cudaGetLastError();
+                g_scratch_addr[dev] = nullptr;
                 return SWR_ERR_CUDA;
             }
             g_scratch_addr[dev] = static_cast<double2*>(addr);
+            g_scratch_ctx[dev] = current_context_id();   // the lookup made one current
         }
         scratch = g_scratch_addr[dev];
     }

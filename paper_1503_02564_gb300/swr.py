@@ -102,6 +102,10 @@ def lib():
         L.swr_get_stats.argtypes = [vp, ctypes.POINTER(swr_stats), ctypes.c_int32]
         L.swr_causal_solve_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                dp, dp, dp, vp]
+        L.swr_fp64_peak.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                    ctypes.c_int32, dp, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_float), vp]
+        L.swr_test_wait_hook.argtypes = [ctypes.c_int64, ctypes.c_int32]
         L.swr_destroy.argtypes = [vp]
         L.swr_destroy.restype = None
         L.swr_kernel_launch_count.argtypes = []
@@ -110,7 +114,8 @@ def lib():
         L.swr_status_string.restype = ctypes.c_char_p
         for f in ("swr_plan", "swr_plan_batch", "swr_build_interface", "swr_solve", "swr_apply_R",
                   "swr_apply_interface", "swr_get_interface", "swr_apply_precond", "swr_adjoint",
-                  "swr_get_stats", "swr_causal_solve_noalloc", "swr_misfit"):
+                  "swr_get_stats", "swr_causal_solve_noalloc", "swr_misfit", "swr_fp64_peak",
+                  "swr_test_wait_hook"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -152,6 +157,25 @@ def swr_causal_solve_noalloc(nsub, nt, sweeps, cols, y, x, stream=None):
         int(nsub), int(nt), int(sweeps), _ptr(cols, torch.complex128, 4 * nsub * nt, "cols"),
         _ptr(y, torch.complex128, n, "y"), _ptr(x, torch.complex128, n, "x"),
         ctypes.c_void_p(stream.cuda_stream))
+
+
+def swr_test_wait_hook(max_polls=0, withhold=-1):
+    """Test hook of the substitution's bounded waits on the current device (see
+    include/swr.h); (0, -1) restores the defaults."""
+    _check(lib().swr_test_wait_hook(int(max_polls), int(withhold)), "swr_test_wait_hook")
+
+
+def swr_fp64_peak(kind, iters, blocks, threads, sink, stream=None):
+    """One timed FP64 probe launch (kind 0: DFMA, 1: DMMA m8n8k4); returns
+    (flops, ms).  sink: float64 CUDA tensor of blocks * threads entries."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    flops, ms = ctypes.c_double(), ctypes.c_float()
+    _check(lib().swr_fp64_peak(int(kind), int(iters), int(blocks), int(threads),
+                               _ptr(sink, torch.float64, blocks * threads, "sink"),
+                               ctypes.byref(flops), ctypes.byref(ms),
+                               ctypes.c_void_p(stream.cuda_stream)), "swr_fp64_peak")
+    return flops.value, float(ms.value)
 
 
 class Plan:

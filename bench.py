@@ -660,6 +660,11 @@ def main():
                 c["ev"][1].record()
         return infos
 
+    # the roofline's denominator: this GPU's FP64 DFMA rate, measured now (about 1.5 s)
+    peak_gf, peak_ms, peak_clk = fp64_probe(0, 1.5, dev, ClockSampler(local))
+    peak_basis = ("measured FP64 DFMA rate of this GPU (swr_fp64_peak, %.0f ms, median SM "
+                  "%s MHz)" % (peak_ms, peak_clk["sm_mhz"] if peak_clk else "?"))
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -826,14 +831,15 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"kernel": m_kernel, "bound": "alu",
                          "achieved": achieved,
-                         "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                         "peak": peak_gf, "unit": "GFLOP/s",
+                         "frac": achieved / peak_gf, "traffic": traffic,
                          "launches": m_launch, "avg_launch_ms": m_ms / max(m_launch, 1),
                          "flops_per_point_step": fpp,
                          **({"flops_per_point_iteration": FLOPS_PER_POINT_ITER_NL,
                              "point_iterations": nl_pit, "nl_launches": nl_launch,
                              "nl_ms": nl_ms} if nonlin else {}),
-                         "peak_basis": "nominal FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+                         "peak_basis": peak_basis,
+                         "frac_of_nominal": achieved / FP64_PEAK_GFLOPS,
                          "march_share_of_step": m_ms / t_ms if t_ms > 0 else None},
             "hbm_roof": {"point_steps_per_s": hbm * 1e9 / bpp,
                          "march_point_steps_per_s": march_pss,

@@ -171,6 +171,20 @@ def config5(nsub=32, nx=20001, nt=1000, dt=5e-4) -> Workload:
     return wl
 
 
+def config5_target_potential(wl: Workload, seed: int = 9) -> np.ndarray:
+    """The perturbed potential whose final state is the misfit target of the nonlinear
+    workload: V0 with every well depth d_k multiplied by (1 + 0.05 xi_k), xi ~ N(0, 1)
+    seeded.  (The target state itself is u(T) of the nonlinear problem with this
+    potential; whoever needs it marches it.)"""
+    rng = np.random.default_rng(SEED_BASE + 300 + seed)
+    dep, c, w = wl.meta["V0_params"]
+    dep = dep * (1.0 + 0.05 * rng.standard_normal(len(dep)))
+    V = np.zeros(wl.nx)
+    for k in range(len(dep)):
+        V -= dep[k] * np.exp(-(wl.x - c[k]) ** 2 / (2.0 * w[k] ** 2))
+    return V
+
+
 def tc_comparison(nsub=2, nx=4200001, nt=500, dt=1e-3) -> Workload:
     """The setting of the paper's comparison of transmission conditions (Section 6):
     (a0, b0) = (-21, 21), dx = 1e-5 (4200001 nodes), T = 0.5 with dt = 1e-3,

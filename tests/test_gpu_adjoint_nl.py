@@ -110,7 +110,8 @@ def test_nonlinear_adjoint_against_central_differences():
 
 def test_nonlinear_adjoint_full_size_against_oracle_and_differences():
     """Full-size nonlinear workload (20001 nodes, 1000 steps, N = 32, checkpoints
-    every 50 steps).  (1) The gradient against the oracle's, stored by
+    every 50 steps), the misfit target being u(T) for the seeded perturbed potential
+    (computed by the oracle).  (1) The gradient against the oracle's, stored by
     tests/golden/make_nl_gradient.py (1e-9 relative).  (2) Central differences
     of the GPU forward SWR solve in 16 seeded directions d, fourth order,
     (8 (J(+e) - J(-e)) - (J(+2e) - J(-2e))) / (12 e) with e = 1e-3, to 1e-6
@@ -123,8 +124,8 @@ def test_nonlinear_adjoint_full_size_against_oracle_and_differences():
     import os
     from paper_1503_02564_gb300 import swr
     wl = W.config5()
-    tgt = W.misfit_target(wl)
     gold = np.load(os.path.join(os.path.dirname(__file__), "golden", "nl_gradient_config5.npz"))
+    tgt = gold["u_target"]     # the oracle's u(T) for the seeded perturbed potential
 
     def run(V, K):
         plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,

@@ -92,6 +92,11 @@ def parse():
                          "paper's dx = 1e-5 (4200001 nodes) needs 2.1M-node subdomains at N = 2, "
                          "beyond the 69632-node subdomain limit of the march")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="scaling workload: skip the sub-records of the other workloads "
+                         "(plain, batch, time-dependent, nonlinear + gradient)")
+    ap.add_argument("--sub-steps", type=int, default=2)
+    ap.add_argument("--sub-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -159,7 +164,7 @@ def march_point_steps(wl):
     return tot
 
 
-def host_info():
+def host_info(threads_used=1):
     """The host the CPU oracle is timed on: logical CPUs and the CPU model."""
     import platform
     model = platform.machine()
@@ -172,7 +177,7 @@ def host_info():
                     break
     except OSError:
         pass
-    return {"nproc": os.cpu_count(), "cpu": model, "threads_used": 1}
+    return {"nproc": os.cpu_count(), "cpu": model, "threads_used": threads_used}
 
 
 def march_point_steps_d(wl):
@@ -258,6 +263,37 @@ def cpu_oracle_sample(wl_full, nsub_sample, min_seconds=0.0, max_passes=20):
     return ps / dt, dt, ps
 
 
+def cpu_oracle_marches(wl_full, threads, min_seconds=0.0, max_passes=50):
+    """The oracle's subdomain d-marches (R applied to zero fluxes) of every subdomain of
+    the workload, one march per task on `threads` host threads (the oracle's C march
+    releases the interpreter lock), passes repeated until min_seconds have elapsed.
+    Returns (point-steps/s, seconds, point-steps)."""
+    import concurrent.futures
+    import numpy as np
+    import oracle as O
+    P = O.Problem(wl_full.a0, wl_full.b0, wl_full.nx, wl_full.dt, wl_full.nt,
+                  wl_full.off.astype(np.int64), wl_full.u0, wl_full.V, vkind=wl_full.vkind,
+                  tc=wl_full.tc, sigma=wl_full.sigma)
+    N = P.nsub
+
+    def one(j):
+        a, b = int(P.off[j]), int(P.off[j + 1])
+        l = np.zeros(P.nt, np.complex128) if j > 0 else None
+        r = np.zeros(P.nt, np.complex128) if j < N - 1 else None
+        O.sub_march(P, j, P.u0[a:b + 1], l, r)
+        return (b - a + 1) * P.nt
+
+    ps = 0
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        t0 = time.perf_counter()
+        for _ in range(max_passes):
+            ps += sum(ex.map(one, range(N)))
+            if time.perf_counter() - t0 >= min_seconds:
+                break
+        dt = time.perf_counter() - t0
+    return ps / dt, dt, ps
+
+
 def cpu_oracle_adjoint_sample(wl_full, nt_sample):
     """Time the oracle's discrete adjoint (monodomain forward march keeping every
     v_n, then the adjoint solves) on the workload's grid for nt_sample steps.
@@ -322,7 +358,7 @@ def run_fp64peak(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     out = {}
-    for kind, name in ((0, "dfma"), (1, "dmma_m8n8k4")):
+    for kind, name in ((0, "dfma"), (1, "dmma_m8n8k4"), (2, "dfma_and_dmma_together")):
         gf, ms, clocks = fp64_probe(kind, 1.5, dev, ClockSampler(local))
         out[name] = {"gflops": gf, "ms": ms, "clocks": clocks,
                      "ms_x_median_mhz": ms * clocks["sm_mhz"] if clocks else None,
@@ -373,9 +409,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, peak=None):
     """128 independent instances of the batch workload: one batched plan (every
-    launch covers all instances) against one plan per instance, same solver."""
+    launch covers all instances) against one plan per instance, same solver.
+    Returns the JSON record."""
     import numpy as np
     import torch
     from paper_1503_02564_gb300 import swr
@@ -383,6 +420,10 @@ def run_batch(args):
     rank, world, local = dist_env()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if peak is None:
+        pg, pms, pclk = fp64_probe(0, 1.5, dev, ClockSampler(local))
+        peak = (pg, "measured FP64 DFMA rate of this GPU (swr_fp64_peak, %.0f ms, median SM "
+                    "%s MHz)" % (pms, pclk["sm_mhz"] if pclk else "?"))
     wls = W.config3()
     shared = dict(p=wls[0].sigma, restart=30, maxit=2000, tol_abs=1e-10,
                   precond=swr.SWR_PC_CAUSAL)
@@ -458,14 +499,24 @@ def run_batch(args):
     t_e, _ = timed(e2e_step)
     cpu = None
     if not args.no_cpu_baseline:
-        v, secs, pss = 0.0, 0.0, 0
-        for w in wls[:8]:
-            v1, s1, p1 = cpu_oracle_sample(w, w.nsub)
-            secs += s1
-            pss += p1
-        cpu = {"value": pss / secs, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "host": host_info(),
-               "sample": f"oracle d-marches of every subdomain of the first 8 instances "
-                         f"({pss:.3g} point-steps, {secs:.1f} s)"}
+        ncores = os.cpu_count() or 1
+        runs = {}
+        for thr in (ncores, 1):
+            secs, pss = 0.0, 0
+            for w in wls[:8]:
+                _, s1, p1 = cpu_oracle_marches(w, thr)
+                secs += s1
+                pss += p1
+            runs[thr] = (pss / secs, secs, pss)
+        v, secs, pss = runs[ncores]
+        cpu = {"value": v, "unit": "point-steps/s", "cores": ncores, "kind": "oracle",
+               "host": host_info(ncores),
+               "sample": f"oracle d-marches of every subdomain of the first 8 instances, one "
+                         f"march per task on {ncores} threads ({pss:.3g} point-steps, "
+                         f"{secs:.1f} s)",
+               "one_core": {"value": runs[1][0], "cores": 1,
+                            "sample": f"the same on one thread ({runs[1][2]:.3g} point-steps, "
+                                      f"{runs[1][1]:.1f} s)"}}
     line = {
         "metric": "SWR subdomain CN point-steps/s (solve time to 1e-10 interface residual "
                   "reported as ms_per_step)",
@@ -483,12 +534,12 @@ def run_batch(args):
                    "point_steps_per_step": ps, "l2": "flushed by a 256 MB write before each step",
                    "parallelism": "single GPU"},
         "roofline": {"kernel": "k_march_static", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                     "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                     "peak": peak[0], "unit": "GFLOP/s",
+                     "frac": achieved / peak[0], "traffic": None,
                      "launches": st["march_launches"],
                      "avg_launch_ms": st["march_ms"] / max(st["march_launches"], 1),
                      "flops_per_point_step": FLOPS_PER_POINT_STEP,
-                     "peak_basis": "nominal FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz"},
+                     "peak_basis": peak[1], "frac_of_nominal": achieved / FP64_PEAK_GFLOPS},
         "per_instance_plans": {"ms_per_step": t_s / args.steps,
                                "speedup_of_batched": t_s / t_b,
                                "iterations_min_max": [min(its), max(its)],
@@ -502,11 +553,207 @@ def run_batch(args):
                 "d2h_bytes_per_step": uT.numel() * 16, "ms_per_step": t_e / args.steps},
         "gpu_launches": launches, "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     plan.destroy()
     for c in singles:
         c["plan"].destroy()
+    return line
+
+
+def oracle_solve_split(P, threads, solver="gmres", restart=30, maxit=2000):
+    """The oracle's whole new-algorithm solve (Algorithm 3) split into its parts, the
+    marches of each part run one per task on `threads` host threads: build (d and the
+    first columns), Krylov (GMRES(restart) on (I - L) g = d to 1e-10, or the fixed point
+    g <- L g + d), final march.  Returns a dict of seconds, iterations, point-steps."""
+    import concurrent.futures
+    import numpy as np
+    import oracle as O
+    N, nt = P.nsub, P.nt
+    e1 = np.zeros(nt, np.complex128)
+    e1[0] = 1.0
+    zero = np.zeros(nt, np.complex128)
+
+    def flux(j, m, lj, rj, out, which):
+        if j > 0:
+            out[("a", j, which)] = (-lj if lj is not None else 0) + O.s_flux(P, m.va, j, 0)
+        if j < N - 1:
+            out[("b", j, which)] = (-rj if rj is not None else 0) + O.s_flux(P, m.vb, j, 1)
+
+    def build_task(job):
+        j, which = job
+        a, b = int(P.off[j]), int(P.off[j + 1])
+        u0 = P.u0[a:b + 1] if which == "d" else np.zeros(b - a + 1, np.complex128)
+        lj = ((e1 if which == "l" else zero) if j > 0 else None)
+        rj = ((e1 if which == "r" else zero) if j < N - 1 else None)
+        m = O.sub_march(P, j, u0, lj, rj)
+        out = {}
+        flux(j, m, lj, rj, out, which)
+        return out, (b - a + 1) * nt
+
+    jobs = [(j, w) for j in range(N) for w in ("d", "l", "r")
+            if not ((w == "l" and j == 0) or (w == "r" and j == N - 1))]
+    ps = 0
+    with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+        t0 = time.perf_counter()
+        res = {}
+        for out, n in ex.map(build_task, jobs):
+            res.update(out)
+            ps += n
+        d = np.zeros((P.nblk, nt), np.complex128)
+        cols = np.zeros((N, 4, nt), np.complex128)
+        for j in range(N):
+            if j > 0:
+                d[O.blk_r(j - 1)] = res[("a", j, "d")]
+                cols[j, 0] = res[("a", j, "l")]
+                if j < N - 1:
+                    cols[j, 1] = res[("a", j, "r")]
+            if j < N - 1:
+                d[O.blk_l(j + 1)] = res[("b", j, "d")]
+                cols[j, 3] = res[("b", j, "r")]
+                if j > 0:
+                    cols[j, 2] = res[("b", j, "l")]
+        t1 = time.perf_counter()
+        if solver == "gmres":
+            r = O.gmres(lambda v: O.apply_I_minus_L(P, cols, v), d, None, m=restart,
+                        tol=1e-10, maxit=maxit)
+        else:
+            r = O.fixed_point(lambda v: O.apply_L(P, cols, v) + d, np.zeros_like(d), tol=1e-10,
+                              maxit=maxit)
+        g = np.asarray(r.x).reshape(d.shape)
+        t2 = time.perf_counter()
+
+        def final_task(j):
+            a, b = int(P.off[j]), int(P.off[j + 1])
+            O.sub_march(P, j, P.u0[a:b + 1], g[O.blk_l(j)] if j > 0 else None,
+                        g[O.blk_r(j)] if j < N - 1 else None)
+            return (b - a + 1) * nt
+        ps += sum(ex.map(final_task, range(N)))
+        t3 = time.perf_counter()
+    return {"build_s": t1 - t0, "krylov_s": t2 - t1, "final_s": t3 - t2, "total_s": t3 - t0,
+            "iterations": int(r.iterations), "converged": bool(r.converged),
+            "point_steps": ps, "threads": threads}
+
+
+def run_plain(args, dev, local, peak):
+    """The plain workload (1001 nodes on (-12, 12), 200 steps, N = 4, V = -x^2/4): the
+    new algorithm (Algorithm 3: d and L built by marches, GMRES(30) on (I - L) g = d to
+    1e-10, u(T)) against the classical algorithm (Algorithm 1: g <- R g with full
+    marches until ||g^{k+1} - g^k|| < 1e-10), for the configuration's Robin condition
+    S-bar v = sqrt(5) e^{-i pi/4} v and for the paper's S_0^2.  Timed per solve on the
+    plan's stream; the record's value is the new algorithm's (Robin, GMRES with the
+    causal preconditioner) point-steps/s."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1503_02564_gb300 import swr
+    from paper_1503_02564_gb300 import workloads as W
+    wl = W.config1()
+    V = torch.tensor(wl.V, dtype=torch.float64, device=dev)
+    u0 = torch.tensor(wl.u0, dtype=torch.complex128, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    CLASSICAL_CAP = 100
+
+    def plan_for(tc, solver, precond, maxit=2000):
+        return swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
+                        node_off=wl.off, p=wl.sigma, tc=tc, solver=solver, precond=precond,
+                        restart=30, maxit=maxit, tol_abs=1e-10)
+
+    def timed(plan, host=None):
+        g = torch.zeros(plan.n_interface, dtype=torch.complex128, device=dev)
+        uT = torch.zeros(wl.nx, dtype=torch.complex128, device=dev)
+        ms, info = [], None
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record()
+            if host is not None:
+                V.copy_(host[0], non_blocking=True)
+                u0.copy_(host[1], non_blocking=True)
+            plan.build_interface(V, u0)
+            info = plan.solve(g, False, uT, allow_not_converged=True)
+            if host is not None:
+                host[2].copy_(uT, non_blocking=True)
+            ev1.record()
+            ev1.synchronize()
+            if k >= args.warmup:
+                ms.append(ev0.elapsed_time(ev1))
+        return sum(ms) / len(ms), info, uT.cpu().numpy()
+
+    P = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0, wl.V,
+                  sigma=wl.sigma)
+    _, u_mono = O.mono_interface(P)
+    rows = []
+    head = None
+    for tcname, tc in (("Robin p=sqrt(5)e^{-i pi/4}", swr.SWR_TC_ROBIN),
+                       ("S_0^2", swr.SWR_TC_S02)):
+        for alg, solver, precond, cap in (
+                ("new (Alg. 3), GMRES(30) + causal preconditioner", swr.SWR_SOLVER_GMRES,
+                 swr.SWR_PC_CAUSAL, 2000),
+                ("new (Alg. 3), GMRES(30)", swr.SWR_SOLVER_GMRES, swr.SWR_PC_NONE, 2000),
+                ("classical (Alg. 1)", swr.SWR_SOLVER_CLASSICAL, swr.SWR_PC_NONE,
+                 CLASSICAL_CAP)):
+            plan = plan_for(tc, solver, precond, cap)
+            plan.get_stats(reset=True)
+            ms, info, uT = timed(plan)
+            st = plan.get_stats(reset=True)
+            row = {"tc": tcname, "algorithm": alg, "ms": ms, "iterations": info["iterations"],
+                   "converged": info["status"] == swr.SWR_OK,
+                   "residual0": info["residual0"], "residual": info["residual"],
+                   "rel_err_uT_vs_monodomain": float(np.linalg.norm(uT - u_mono) /
+                                                     np.linalg.norm(u_mono)),
+                   "march_point_steps": st["march_point_steps"] / (args.warmup + args.steps),
+                   "march_ms": st["march_ms"] / (args.warmup + args.steps)}
+            if solver == swr.SWR_SOLVER_CLASSICAL and not row["converged"]:
+                row["note"] = ("diverges: ||g^{k+1} - g^k|| went from %.3g to %.3g in %d "
+                               "iterations (cap)" % (info["residual0"], info["residual"],
+                                                     info["iterations"]))
+            rows.append(row)
+            if head is None:
+                head = (plan, ms, st)
+            else:
+                plan.destroy()
+    plan, ms, st = head
+    ps = st["march_point_steps"] / (args.warmup + args.steps)
+    achieved = FLOPS_PER_POINT_STEP * st["march_point_steps"] / (st["march_ms"] * 1e-3) / 1e9
+    hV, hu0 = V.cpu().pin_memory(), u0.cpu().pin_memory()
+    huT = torch.empty(wl.nx, dtype=torch.complex128).pin_memory()
+    e_ms, _, _ = timed(plan, (hV, hu0, huT))
+    plan.destroy()
+    cpu = None
+    if not args.no_cpu_baseline:
+        ncores = os.cpu_count() or 1
+        Ps = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0, wl.V,
+                       sigma=wl.sigma, tc=O.TC_S02)
+        sp_all = oracle_solve_split(Ps, ncores)
+        sp_one = oracle_solve_split(Ps, 1)
+        cpu = {"value": sp_all["point_steps"] / sp_all["total_s"], "unit": "point-steps/s",
+               "cores": ncores, "kind": "oracle", "host": host_info(ncores),
+               "sample": "the oracle's whole new-algorithm solve of this workload with S_0^2 "
+                         "(build marches, GMRES(30) to 1e-10, final march), marches one per "
+                         "task on %d threads: %d GMRES iterations, %.2f s" % (
+                             ncores, sp_all["iterations"], sp_all["total_s"]),
+               "split_all_cores": sp_all, "split_one_core": sp_one}
+    return {
+        "metric": "SWR subdomain CN point-steps/s (solve time to 1e-10 interface residual "
+                  "reported as ms_per_step)",
+        "value": ps / (ms * 1e-3), "unit": "point-steps/s", "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "f64",
+        "config": {"workload": "swr_plain: x in (-12,12), 1001 P1 nodes, T=0.2 dt=1e-3 (200 "
+                               "steps), N=4 equal, V=-x^2/4, u0=exp(-x^2/2+5ix) with +-1e-3 "
+                               "seeded phase noise, Robin p=sqrt(5)e^{-i pi/4}; new algorithm "
+                               "(GMRES(30), causal preconditioner) vs classical, to 1e-10",
+                   "l2": "flushed by a 256 MB write before each solve"},
+        "algorithms": rows,
+        "roofline": {"kernel": "k_march_static", "bound": "alu", "achieved": achieved,
+                     "peak": peak[0], "unit": "GFLOP/s", "frac": achieved / peak[0],
+                     "traffic": None, "peak_basis": peak[1],
+                     "flops_per_point_step": FLOPS_PER_POINT_STEP,
+                     "note": "4 systems of 251 nodes: latency-bound, one CTA per system"},
+        "e2e": {"value": ps / (e_ms * 1e-3), "unit": "point-steps/s",
+                "h2d_bytes_per_step": wl.nx * 8 + wl.nx * 16,
+                "d2h_bytes_per_step": wl.nx * 16, "ms_per_step": e_ms},
+        "cpu_baseline": cpu,
+    }
 
 
 def run_tcs(args):
@@ -587,15 +834,15 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
-        return run_batch(args)
+        line = run_batch(args)
+        if dist_env()[0] == 0:
+            print(json.dumps(line), flush=True)
+        return
     if args.workload == "tcs":
         return run_tcs(args)
     if args.workload == "fp64peak":
         return run_fp64peak(args)
-    import numpy as np
     import torch
-    from paper_1503_02564_gb300 import swr
-    from paper_1503_02564_gb300 import workloads as W
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -603,11 +850,55 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    nsubs = tuple(int(x) for x in args.nsub.split(","))
+    # the roofline's denominator: this GPU's FP64 DFMA rate, measured now (about 1.5 s)
+    peak_gf, peak_ms, peak_clk = fp64_probe(0, 1.5, dev, ClockSampler(local))
+    peak = (peak_gf, "measured FP64 DFMA rate of this GPU (swr_fp64_peak, %.0f ms, median SM "
+                     "%s MHz)" % (peak_ms, peak_clk["sm_mhz"] if peak_clk else "?"))
+    line = run_workload(args, args.workload, rank, world, local, dev, peak)
+    if (rank == 0 and world == 1 and args.workload == "scaling" and not args.no_sub
+            and args.nt == 0):
+        # the other workloads of the method, fewer steps each, beside the headline
+        import copy
+        subs = {}
+        for name in ("plain", "batch", "timedep", "nonlinear"):
+            t0 = time.perf_counter()
+            try:
+                sa = copy.copy(args)
+                sa.steps, sa.warmup = args.sub_steps, args.sub_warmup
+                if name == "plain":
+                    subs[name] = run_plain(sa, dev, local, peak)
+                elif name == "batch":
+                    subs[name] = run_batch(sa, peak)
+                else:
+                    sa.workload, sa.nsub, sa.precond = name, "", "causal"
+                    subs[name] = run_workload(sa, name, rank, world, local, dev, peak)
+            except Exception as e:   # a failed sub-record must not hide the headline
+                subs[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+            subs[name]["wall_s"] = time.perf_counter() - t0
+        line["sub"] = subs
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_workload(args, workload, rank, world, local, dev, peak):
+    """One timed workload (scaling / timedep / adjoint / nonlinear): W warm-up steps,
+    K timed steps with the L2 flushed before each, CUDA events on the plans' stream,
+    max over ranks; the march roofline from the library's per-launch events, an
+    end-to-end figure from pinned host buffers, and the CPU oracle's rate.  Returns the
+    JSON record (rank 0) or None."""
+    import numpy as np
+    import torch
+    from paper_1503_02564_gb300 import swr
+    from paper_1503_02564_gb300 import workloads as W
+
+    peak_gf, peak_basis = peak
+    nsubs = tuple(int(x) for x in args.nsub.split(",")) if args.nsub else NSUBS
     precond = swr.SWR_PC_CAUSAL if args.precond == "causal" else swr.SWR_PC_NONE
-    timedep = args.workload == "timedep"
-    nonlin = args.workload == "nonlinear"
-    adjoint = args.workload in ("adjoint", "nonlinear")
+    timedep = workload == "timedep"
+    nonlin = workload == "nonlinear"
+    adjoint = workload in ("adjoint", "nonlinear")
     if timedep:
         nsubs = (64,)
     if nonlin:
@@ -640,8 +931,17 @@ def main():
         cases.append(dict(N=N, wl=wl, plan=plan, V=V, u0=u0, g=g, uT=uT,
                           ps=march_point_steps(wl)))
         if adjoint:
+            if nonlin:
+                # the misfit target: u(T) for the seeded perturbed potential (untimed)
+                plan.build_interface(torch.tensor(W.config5_target_potential(wl),
+                                                  dtype=torch.float64, device=dev), u0)
+                tgt_t = torch.zeros(wl.nx, dtype=torch.complex128, device=dev)
+                plan.solve(None, False, tgt_t)
+                tgt_np = tgt_t.cpu().numpy()
+            else:
+                tgt_np = W.misfit_target(wl)
             cases[-1].update(
-                tgt=torch.tensor(W.misfit_target(wl), dtype=torch.complex128, device=dev),
+                tgt=torch.tensor(tgt_np, dtype=torch.complex128, device=dev),
                 ubar=torch.empty_like(uT),
                 grad=torch.empty(wl.nx, dtype=torch.float64, device=dev),
                 ev=(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)))
@@ -659,11 +959,6 @@ def main():
                 c["plan"].adjoint(c["ubar"], c["grad"], 50)
                 c["ev"][1].record()
         return infos
-
-    # the roofline's denominator: this GPU's FP64 DFMA rate, measured now (about 1.5 s)
-    peak_gf, peak_ms, peak_clk = fp64_probe(0, 1.5, dev, ClockSampler(local))
-    peak_basis = ("measured FP64 DFMA rate of this GPU (swr_fp64_peak, %.0f ms, median SM "
-                  "%s MHz)" % (peak_ms, peak_clk["sm_mhz"] if peak_clk else "?"))
 
     for _ in range(args.warmup):
         step()
@@ -793,13 +1088,20 @@ def main():
             wl_cpu = cases[0]["wl"]
         else:
             wl_cpu = cases[-1]["wl"] if cases[-1]["N"] == 500 else W.config2(nsub=500)
-        v, s, ps = cpu_oracle_sample(wl_cpu, wl_cpu.nsub, min_seconds=10.0)
-        npass = int(round(ps / march_point_steps_d(wl_cpu)))
-        cpu = {"value": v, "unit": "point-steps/s", "cores": 1, "kind": "oracle", "host": host_info(),
-               "sample": f"oracle d-marches of all {wl_cpu.nsub} subdomains of the "
-                         f"{'time-dependent' if timedep else 'N=500 scaling'} workload, "
-                         f"{npass} passes ({ps:.3g} point-steps, {s:.1f} s)"}
+        ncores = os.cpu_count() or 1
+        v, s, ps = cpu_oracle_marches(wl_cpu, ncores, min_seconds=8.0)
+        v1, s1, ps1 = cpu_oracle_marches(wl_cpu, 1, min_seconds=6.0)
+        what = "time-dependent" if timedep else "N=500 scaling"
+        cpu = {"value": v, "unit": "point-steps/s", "cores": ncores, "kind": "oracle",
+               "host": host_info(ncores),
+               "sample": f"oracle d-marches of the {what} workload's {wl_cpu.nsub} subdomains, "
+                         f"one march per task on {ncores} threads ({ps:.3g} point-steps, "
+                         f"{s:.1f} s)",
+               "one_core": {"value": v1, "cores": 1,
+                            "sample": f"the same marches on one thread ({ps1:.3g} "
+                                      f"point-steps, {s1:.1f} s)"}}
 
+    line = None
     if rank == 0:
         per_n = []
         for c, info in zip(cases, infos_last):
@@ -854,11 +1156,9 @@ def main():
                       "precond_ms": sum(s["precond_ms"] for s in st),
                       "march_ms": m_ms},
         }
-        print(json.dumps(line), flush=True)
     for c in cases:
         c["plan"].destroy()
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    return line if rank == 0 else None
 
 
 if __name__ == "__main__":

@@ -341,7 +341,9 @@ swr_status swr_causal_solve_noalloc(int32_t nsub, int32_t nt, int32_t sweeps,
  *   kind 0: DFMA, each thread `iters` rounds of 8 independent fused multiply-add
  *           chains (2 flops each);
  *   kind 1: DMMA, each warp `iters` rounds of 4 independent
- *           mma.sync.aligned.m8n8k4 f64 products (512 flops each).
+ *           mma.sync.aligned.m8n8k4 f64 products (512 flops each);
+ *   kind 2: both in every round of every warp, equal flops (the 8 chains and one
+ *           m8n8k4 product: 512 flops each per warp).
  * sink: double[blocks * threads] (device) receives the chains' values; *flops
  * (host) the flops executed; *ms (host) the launch's device time from CUDA events
  * on the stream.  Synchronises the stream.

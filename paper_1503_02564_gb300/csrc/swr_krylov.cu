@@ -910,9 +910,11 @@ int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* la
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Warp 0 waits, solves and publishes; warps 1-4 (one per source block) compute,
-// during step n, the part of step n+1's history that uses values older than n
-// (lags >= 2), so that step n+1 adds one lag-1 term on its critical path.
+// Warp 0 waits, solves and publishes; warps 1-4 (one per source block) form the
+// history sums, lags >= 3, two steps ahead of warp 0 and without a per-step barrier:
+// they run as soon as warp 0 has seen step m's inputs (shared flag s_xready) and hand
+// their sums over in a three-slot ring with one ready flag per warp (s_hdone).  Warp 0
+// then adds only the lag-2 and lag-1 terms on its critical path.
 // The same-step coupling of neighbouring interfaces is resolved either by
 // `sweeps` block-Jacobi sweeps (H == 0), or exactly (to (|c| |D^{-1}|)^{H+1}) by
 // the window form (H >= 1), x_n(k) = sum_d G_{k,k+d} R_n(k+d) with the rows of
@@ -928,6 +930,23 @@ int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* la
 // P_n lives in a two-slot ring: interface k overwrites slot (n+1)&1 at the end of
 // step n, after it has seen every interface within H+1 finish step n-1, and
 // those within H were the only readers of P_{n-1}(k).
+namespace {
+constexpr long long kLocalPolls = 1LL << 24;   // bound of a wait between warps of one CTA
+}
+
+// Wait until *flag >= target (a shared flag written by another warp of this CTA), or
+// until *stop is set; false on stop or when the bound runs out.
+__device__ __forceinline__ bool cta_wait_ge(const volatile int* flag, int target,
+                                            const volatile int* stop) {
+    long long polls = 0;
+    while (*flag < target) {
+        if (*stop) return false;
+        if (++polls > kLocalPolls) return false;
+        __nanosleep(32);
+    }
+    return true;
+}
+
 template <bool WIN>
 __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweeps,
                                                      const double2* __restrict__ cols,
@@ -940,8 +959,10 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                                                      const int* __restrict__ if_inst, int k0,
                                                      int nif_all, const double2* __restrict__ Gw,
                                                      int H) {
-    __shared__ double2 hp[2][4];     // partial histories, by parity of the step they serve
-    __shared__ int s_go;
+    __shared__ double2 hp[3][4];        // lags >= 3 of step m (slot m % 3), one per source
+    __shared__ volatile int s_xready;   // warp 0 has seen the inputs of step s_xready
+    __shared__ volatile int s_hdone[4]; // history warp e has filled the slots of steps <= it
+    __shared__ volatile int s_stop;     // warp 0 left its loop early (timeout or abort)
     // global interface kg (progress, sweep values, lag-0 blocks); local k within its
     // instance (blocks, columns)
     const int kg = k0 + blockIdx.x;
@@ -973,19 +994,79 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         cc = has ? cols + (size_t)cslot * nt : nullptr;
         xin = has ? x + (size_t)inb * nt : nullptr;
     };
-    if (threadIdx.x < 8) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
-    // role data: warps 1-4 accumulate source e = w-1 of this interface
-    bool has = false;
-    const double2* cc = nullptr;
-    const double2* xin = nullptr;
-    if (w >= 1) source(k, w - 1, has, cc, xin);
-    // history warps: step n+1's terms from values s <= n-1 (lags >= 2)
-    auto history = [&](int n) {
-        double2 acc = zero;
-        if (has && n + 1 < nt)
-            for (int s = lane; s < n; s += 32) acc = cfma(__ldg(cc + n + 1 - s), xin[s], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) hp[(n + 1) & 1][w - 1] = acc;
+    if (threadIdx.x < 12) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
+    if (threadIdx.x < 4) s_hdone[threadIdx.x] = 2;   // steps 0..2 have no lag >= 3 term
+    if (threadIdx.x == 0) {
+        s_xready = -1;
+        s_stop = 0;
+    }
+    __syncthreads();
+
+    // ---- history warps: lags >= 3 of step m + 2 from the values s <= m - 1 ----------
+    if (w >= 1) {
+        const int e = w - 1;
+        bool has = false;
+        const double2* cc = nullptr;
+        const double2* xin = nullptr;
+        source(k, e, has, cc, xin);
+        for (int m = 1; m + 2 < nt; ++m) {
+            if (!cta_wait_ge(&s_xready, m, &s_stop)) break;
+            __threadfence();   // pairs with warp 0's fence before s_xready = m
+            double2 a0 = zero, a1 = zero;
+            if (has) {
+                // x of other CTAs through L2 (__ldcg): the flag above is CTA-scoped
+                int s = lane;
+                for (; s + 32 < m; s += 64) {
+                    a0 = cfma(__ldg(cc + m + 2 - s), __ldcg(xin + s), a0);
+                    a1 = cfma(__ldg(cc + m + 2 - s - 32), __ldcg(xin + s + 32), a1);
+                }
+                if (s < m) a0 = cfma(__ldg(cc + m + 2 - s), __ldcg(xin + s), a0);
+            }
+            const double2 acc = warp_sum(cadd(a0, a1));
+            if (lane == 0) {
+                hp[(m + 2) % 3][e] = acc;
+                __threadfence_block();
+                s_hdone[e] = m + 2;
+            }
+        }
+        return;
+    }
+
+    // ---- warp 0 ----------------------------------------------------------------------
+    // lag-2 data of this interface's four sources (lane 0 forms the published sums)
+    bool hs[4] = {false, false, false, false};
+    const double2* xs2[4] = {nullptr, nullptr, nullptr, nullptr};
+    double2 c2e[4] = {zero, zero, zero, zero};
+    if (lane == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const double2* cc;
+            source(k, e, hs[e], cc, xs2[e]);
+            if (hs[e] && nt > 2) c2e[e] = cc[2];
+        }
+    }
+    // history sums of step m for this interface, lags >= 2 (lane 0; waits on the warps)
+    auto hist_ge2 = [&](int m, double2& h0, double2& h1, double2& h2, double2& h3) -> bool {
+        bool ok = true;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ok = ok && cta_wait_ge(&s_hdone[e], m, &s_stop);
+        if (!ok) return false;
+        __threadfence_block();
+        double2 h[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = hp[m % 3][e];
+            if (m >= 2 && hs[e]) h[e] = cfma(c2e[e], __ldcg(xs2[e] + m - 2), h[e]);
+        }
+        h0 = h[0];
+        h1 = h[1];
+        h2 = h[2];
+        h3 = h[3];
+        return true;
+    };
+    auto fail_local = [&]() {   // a wait between this CTA's warps ran out: leave everywhere
+        atomicOr(status, ST_TIMEOUT);
+        store_release(abortf, 1);
     };
 
     if constexpr (WIN) {
@@ -996,13 +1077,13 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         const bool waits = (d != 0 && d >= -H - 1 && d <= H + 1 && i >= 0 && i <= N - 2);
         // lane data for R_n(i): the lag-1 coefficients and source rows of its four
         // sources (the order of `source`; a missing source keeps a zero coefficient)
-        const double2 *xs0 = x, *xs1 = x, *xs2 = x, *xs3 = x;
+        const double2 *xs0 = x, *xs1 = x, *xs2w = x, *xs3 = x;
         double2 c10 = zero, c11 = zero, c12 = zero, c13 = zero;
         double2 g0 = zero, g1 = zero, g2 = zero, g3 = zero;
         const bool h1 = inwin && (i + 1 <= N - 2), h3 = inwin && (i >= 1);
-        if (w == 0 && inwin) {
+        if (inwin) {
             xs0 = x + (size_t)(2 * i + 1) * nt;
-            xs2 = x + (size_t)(2 * i) * nt;
+            xs2w = x + (size_t)(2 * i) * nt;
             if (h1) xs1 = x + (size_t)(2 * i + 2) * nt;
             if (h3) xs3 = x + (size_t)(2 * i - 1) * nt;
             if (nt > 1) {
@@ -1018,96 +1099,102 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             g3 = g[3];
         }
         // P_0(k) = y_0(k): no history at step 0
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             xsw[2 * kg] = y[(size_t)(2 * k) * nt];
             xsw[2 * kg + 1] = y[(size_t)(2 * k + 1) * nt];
             if (publish) store_release(progress + kg, 1);
         }
-        __syncthreads();
+        __syncwarp();
         for (int n = 0; n < nt; ++n) {
-            if (w == 0) {
-                bool ok = true;
-                if (waits) ok = wait_one(kg + d, n + 1, progress, abortf, status, lim);
-                ok = __all_sync(0xffffffffu, ok);
-                if (lane == 0) s_go = ok ? 1 : 0;
+            bool ok = true;
+            if (waits) ok = wait_one(kg + d, n + 1, progress, abortf, status, lim);
+            ok = __all_sync(0xffffffffu, ok);                  // x_{<n}, P_n visible
+            if (!ok) break;
+            if (lane == 0) {
+                __threadfence();
+                s_xready = n;                                  // history warps may use x_{<n}
             }
-            __syncthreads();                                   // B1: x_{<n}, P_n visible
-            if (!s_go) break;
-            if (w == 0) {
-                double2 t1 = zero, t2 = zero;
-                if (inwin) {
-                    const double2* P = xsw + (size_t)(n & 1) * 2 * nif_all + 2 * (kg + d);
-                    double2 r1 = P[0], r2 = P[1];
-                    if (n >= 1) {
-                        r1 = cfma(c10, xs0[n - 1], r1);
-                        if (h1) r1 = cfma(c11, xs1[n - 1], r1);
-                        r2 = cfma(c12, xs2[n - 1], r2);
-                        if (h3) r2 = cfma(c13, xs3[n - 1], r2);
-                    }
-                    t1 = cfma(g0, r1, cmul(g1, r2));
-                    t2 = cfma(g2, r1, cmul(g3, r2));
-                }
-                const double2 z1 = warp_sum(t1), z2 = warp_sum(t2);
-                if (lane == 0) {
-                    x[(size_t)(2 * k) * nt + n] = z1;
-                    x[(size_t)(2 * k + 1) * nt + n] = z2;
-                }
-            } else {
-                history(n);
+            // the next right-hand side's data, off the critical path
+            double2 yn1a = zero, yn1b = zero;
+            if (lane == 0 && n + 1 < nt) {
+                yn1a = y[(size_t)(2 * k) * nt + n + 1];
+                yn1b = y[(size_t)(2 * k + 1) * nt + n + 1];
             }
-            __syncthreads();                                   // B2: x_n, hp of n+1 done
-            if (threadIdx.x == 0) {
+            double2 t1 = zero, t2 = zero;
+            if (inwin) {
+                const double2* P = xsw + (size_t)(n & 1) * 2 * nif_all + 2 * (kg + d);
+                double2 r1 = P[0], r2 = P[1];
+                if (n >= 1) {
+                    r1 = cfma(c10, xs0[n - 1], r1);
+                    if (h1) r1 = cfma(c11, xs1[n - 1], r1);
+                    r2 = cfma(c12, xs2w[n - 1], r2);
+                    if (h3) r2 = cfma(c13, xs3[n - 1], r2);
+                }
+                t1 = cfma(g0, r1, cmul(g1, r2));
+                t2 = cfma(g2, r1, cmul(g3, r2));
+            }
+            const double2 z1 = warp_sum(t1), z2 = warp_sum(t2);
+            int go = 1;
+            if (lane == 0) {
+                x[(size_t)(2 * k) * nt + n] = z1;
+                x[(size_t)(2 * k + 1) * nt + n] = z2;
                 if (n + 1 < nt) {
-                    const double2* h = hp[(n + 1) & 1];
-                    double2* P = xsw + (size_t)((n + 1) & 1) * 2 * nif_all + 2 * kg;
-                    P[0] = cadd(y[(size_t)(2 * k) * nt + n + 1], cadd(h[0], h[1]));
-                    P[1] = cadd(y[(size_t)(2 * k + 1) * nt + n + 1], cadd(h[2], h[3]));
+                    double2 q0, q1, q2, q3;
+                    if (hist_ge2(n + 1, q0, q1, q2, q3)) {
+                        double2* P = xsw + (size_t)((n + 1) & 1) * 2 * nif_all + 2 * kg;
+                        P[0] = cadd(yn1a, cadd(q0, q1));
+                        P[1] = cadd(yn1b, cadd(q2, q3));
+                    } else {
+                        go = 0;
+                        fail_local();
+                    }
                 }
-                if (publish) store_release(progress + kg, n + 2);   // orders x_n and P_{n+1}
+                if (go && publish) store_release(progress + kg, n + 2);   // x_n and P_{n+1}
             }
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) break;
         }
     } else {
         // ---- sweep form (H == 0) -------------------------------------------------
         const int S1 = sweeps + 1;
-        bool hs[4] = {false, false, false, false};
         const double2* cs[4] = {nullptr, nullptr, nullptr, nullptr};
         const double2* xs[4] = {nullptr, nullptr, nullptr, nullptr};
+        bool hsw[4] = {false, false, false, false};
         double2 D00 = zero, D01 = zero, D10 = zero, D11 = zero, cB0 = zero, cD0 = zero;
         double2 c1[4] = {zero, zero, zero, zero};
-        const bool solver = (threadIdx.x == 0);
+        const bool solver = (lane == 0);
         if (solver) {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) source(k, e, hs[e], cs[e], xs[e]);
+            for (int e = 0; e < 4; ++e) source(k, e, hsw[e], cs[e], xs[e]);
             D00 = lag0[kg * 4 + 0];
             D01 = lag0[kg * 4 + 1];
             D10 = lag0[kg * 4 + 2];
             D11 = lag0[kg * 4 + 3];
-            cB0 = hs[1] ? cs[1][0] : zero;
-            cD0 = hs[3] ? cs[3][0] : zero;
+            cB0 = hsw[1] ? cs[1][0] : zero;
+            cD0 = hsw[3] ? cs[3][0] : zero;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) c1[e] = (hs[e] && nt > 1) ? cs[e][1] : zero;
+            for (int e = 0; e < 4; ++e) c1[e] = (hsw[e] && nt > 1) ? cs[e][1] : zero;
         }
-        __syncthreads();
         for (int n = 0; n < nt; ++n) {
-            if (w == 0) {
-                // lanes 0 and 1 wait for the left and right neighbours' values < n
-                bool ok = true;
-                if (lane < 2 && (lane == 0 ? has_l : has_r))
-                    ok = wait_one(kg + (lane == 0 ? -1 : 1), n * S1, progress, abortf, status, lim);
-                ok = __all_sync(0xffffffffu, ok);
-                if (lane == 0) s_go = ok ? 1 : 0;
-            }
-            __syncthreads();                                   // B1: values < n visible
-            if (!s_go) break;
-            if (w == 0) {
-                if (solver) {
-                    // history of step n: partial (lags >= 2, computed during step n-1) + lag 1
-                    double2 h[4];
+            // lanes 0 and 1 wait for the left and right neighbours' values < n
+            bool ok = true;
+            if (lane < 2 && (lane == 0 ? has_l : has_r))
+                ok = wait_one(kg + (lane == 0 ? -1 : 1), n * S1, progress, abortf, status, lim);
+            ok = __all_sync(0xffffffffu, ok);                  // values < n visible
+            if (!ok) break;
+            int go = 1;
+            if (solver) {
+                __threadfence();
+                s_xready = n;
+                // history of step n: lags >= 2 (the warps' sums and lag 2) + lag 1
+                double2 h[4];
+                if (!hist_ge2(n, h[0], h[1], h[2], h[3])) {
+                    go = 0;
+                    fail_local();
+                } else {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        h[e] = hp[n & 1][e];
-                        if (n >= 1 && hs[e]) h[e] = cfma(c1[e], xs[e][n - 1], h[e]);
-                    }
+                    for (int e = 0; e < 4; ++e)
+                        if (n >= 1 && hsw[e]) h[e] = cfma(c1[e], xs[e][n - 1], h[e]);
                     const double2 r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(h[0], h[1]));
                     const double2 r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(h[2], h[3]));
                     double2 z1 = cfma(D01, r2, cmul(D00, r1));
@@ -1119,24 +1206,28 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                         out[2 * kg + 1] = z2;
                         if (publish) store_release(progress + kg, n * S1 + sw);
                         if (!wait_neighbours(kg, has_l, has_r, n * S1 + sw, progress, abortf,
-                                             status, lim))
+                                             status, lim)) {
+                            go = 0;
                             break;
+                        }
                         const double2 xr = has_r ? out[2 * (kg + 1)] : zero;       // r_{k+1}
                         const double2 xl = has_l ? out[2 * (kg - 1) + 1] : zero;   // l_k
                         const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
                         z1 = cfma(D01, e2, cmul(D00, e1));
                         z2 = cfma(D11, e2, cmul(D10, e1));
                     }
-                    x[(size_t)(2 * k) * nt + n] = z1;
-                    x[(size_t)(2 * k + 1) * nt + n] = z2;
-                    if (publish) store_release(progress + kg, (n + 1) * S1);   // orders x above
+                    if (go) {
+                        x[(size_t)(2 * k) * nt + n] = z1;
+                        x[(size_t)(2 * k + 1) * nt + n] = z2;
+                        if (publish) store_release(progress + kg, (n + 1) * S1);   // orders x
+                    }
                 }
-            } else {
-                history(n);
             }
-            __syncthreads();                                   // B2
+            go = __shfl_sync(0xffffffffu, go, 0);
+            if (!go) break;
         }
     }
+    if (lane == 0) s_stop = 1;   // releases history warps still waiting
 }
 
 int swr_set_wait_hook(long long max_polls, int withhold) {

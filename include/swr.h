@@ -131,6 +131,34 @@ typedef struct swr_desc {
                                 /* swr_stats.causal_window; else 1 sweep)               */
 } swr_desc;
 
+/* Execution choices of a plan (no counterpart in the paper: they change how the
+ * library runs the method, never what it computes beyond rounding).  Zero-filled
+ * means "library default" for every field; swr_tuning_defaults writes the defaults
+ * explicitly.  A plan takes its copy at creation (swr_plan_ex / swr_plan_batch_ex);
+ * swr_plan / swr_plan_batch use the defaults. */
+typedef struct swr_tuning {
+    int32_t chunk_L;            /* chunk length of the partitioned marches: 0 (default)  */
+                                /* chosen per launch; 4, 8, 12 or 16 fixed              */
+    int32_t autotune;           /* launch shapes: 0 (default) measured by probe marches  */
+                                /* at the first build; -1 the modelled shape            */
+    int32_t toeplitz_fft;       /* (I - L) x: 0 (default) FFT convolution for           */
+                                /* 16 <= nt <= 2048; -1 direct causal sums              */
+    int32_t superpose;          /* u(T), static V: 0 (default) by superposition of the   */
+                                /* recorded impulse responses when they fit; -1 final   */
+                                /* march                                                */
+    int32_t long_march;         /* 0 (default): the grid-wide march only for subdomains */
+                                /* longer than a cluster holds; 1 for every V(x) plan   */
+    int32_t graph;              /* builds after the first: 0 (default) replayed as a     */
+                                /* CUDA graph; -1 launched directly                     */
+    int32_t tdep_precomp;       /* V(t,x): 0 (default) every step's factors computed once */
+                                /* per build when they fit; -1 refactorised per step    */
+    int32_t two_level;          /* systems spread over a cluster: 0 (default) two-level  */
+                                /* separator solve (one cluster barrier per step) when   */
+                                /* a system has <= 993 separators; -1 cluster-wide PCR   */
+    int32_t debug;              /* 1: failing CUDA calls (2: also the launch-shape      */
+                                /* probes) reported on stderr; 0 (default) silent        */
+} swr_tuning;
+
 typedef struct swr_info {
     int32_t iterations;         /* outer iterations (GMRES steps or fixed-point sweeps) */
     int32_t restarts;
@@ -167,13 +195,15 @@ typedef struct swr_stats {
     double nl_march_ms;         /* and their summed device time                         */
     int32_t superposed;         /* 1: swr_solve forms u(T) by superposition of the build
                                  * marches' recorded states (static V, Robin, enough free
-                                 * memory, SWR_SUPERPOSE not 0) instead of a final march  */
+                                 * memory, tuning.superpose >= 0) instead of a final march */
     int32_t toeplitz_fft_length; /* transform length M of the FFT Toeplitz applies (the
                                  * power of two >= 2 nt - 1, for 16 <= nt and M <= 4096,
-                                 * SWR_TOEPLITZ_FFT not 0); 0: direct causal sums        */
+                                 * tuning.toeplitz_fft >= 0); 0: direct causal sums      */
     int32_t causal_sweeps;      /* block-Jacobi sweeps of the causal substitution in use */
     int32_t causal_window;      /* H >= 1: the substitution solves the same-step coupling
                                  * exactly over a window of H interfaces each side; 0: sweeps */
+    int64_t two_level_launches; /* march launches that took the two-level separator solve
+                                 * (a system spread over a cluster)                     */
 } swr_stats;
 
 typedef struct swr_plan_s *swr_plan_t;
@@ -182,11 +212,19 @@ typedef struct swr_plan_s *swr_plan_t;
  * stream: cudaStream_t (as void*) on which all later work of this plan runs.
  * Subdomains up to 69632 nodes are marched by thread-block clusters; a V(x) plan
  * with a longer subdomain is marched by the whole grid (one cooperative launch, the
- * state in device memory; SWR_LONG_MARCH=1 forces it); V(t,x), nonlinear and batched
+ * state in device memory; swr_tuning.long_march = 1 forces it); V(t,x), nonlinear and batched
  * plans with such a subdomain return SWR_ERR_UNSUPPORTED.
  * Errors: SWR_ERR_ARG (bad field), SWR_ERR_UNSUPPORTED, SWR_ERR_NOMEM, SWR_ERR_CUDA.
  * *out is NULL on failure. */
 swr_status swr_plan(const swr_desc *d, swr_plan_t *out, void *stream);
+
+/* swr_plan with explicit execution choices (tuning may be NULL: the defaults).
+ * Errors as swr_plan, and SWR_ERR_ARG for a tuning field out of range. */
+swr_status swr_plan_ex(const swr_desc *d, const swr_tuning *tuning, swr_plan_t *out,
+                       void *stream);
+
+/* Fill *t with the library defaults (host-only, no device work). */
+void swr_tuning_defaults(swr_tuning *t);
 
 /* A batch of independent problem instances in one plan (no counterpart in the
  * paper, which solves one problem at a time).  descs[0..count-1] each give an
@@ -202,6 +240,10 @@ swr_status swr_plan(const swr_desc *d, swr_plan_t *out, void *stream);
  * GMRES runs on the concatenated (block-diagonal) system, so its stopping test
  * bounds every instance's residual.  swr_adjoint is not available for batches. */
 swr_status swr_plan_batch(const swr_desc *descs, int32_t count, swr_plan_t *out, void *stream);
+
+/* swr_plan_batch with explicit execution choices (tuning may be NULL). */
+swr_status swr_plan_batch_ex(const swr_desc *descs, int32_t count, const swr_tuning *tuning,
+                             swr_plan_t *out, void *stream);
 
 /* Assemble and factor the subdomain systems A_j - B_j (Eq. AvML) for potential
  * V and build the interface problem (Section 4.1):
@@ -221,7 +263,7 @@ swr_status swr_build_interface(swr_plan_t p, const double *V, const double *u0);
  * converged fluxes.  Static V with Robin transmission (p != 0): the march is
  * linear and time invariant, so swr_build_interface records the full states of
  * its impulse-driven marches (2 nt n_j complex per subdomain, when that takes at
- * most a quarter of the free device memory and SWR_SUPERPOSE is not 0) and u(T)
+ * most a quarter of the free device memory and tuning.superpose >= 0) and u(T)
  * is their superposition weighted by the converged fluxes plus the zero-flux
  * march's final state; info->interface_jump then comes from the final residual
  * (v_j(b_j) - v_{j+1}(a_{j+1}) = ((R g - g)[l_{j+1}] - (R g - g)[r_j]) / 2p).

@@ -82,10 +82,11 @@ struct swr_plan_s {
     double2 *d_dg = nullptr, *d_od = nullptr;       // A - B for V (static) or V0
     double2 *d_dg0 = nullptr, *d_od0 = nullptr;     // A - B for V = 0
     FactorSet fsL[4], fs0L[4];     // chunked factorisations for L = 4, 8, 16, 12 (V and V = 0)
-    int forceL = 0;                // SWR_CHUNK_L override (0: chosen per launch)
-    bool autotune = true;          // SWR_AUTOTUNE=0 disables the measured launch-shape choice
+    swr_tuning tune{};             // execution choices (swr_plan_ex; zero: defaults)
+    int forceL = 0;                // tune.chunk_L (0: chosen per launch)
+    bool autotune = true;          // tune.autotune >= 0: measured launch shapes
     // V(t,x): factor every step's matrix once per build and stream the factors
-    // (SWR_TDEP_PRECOMP=0, or too little free memory: refactorise inside the march)
+    // (tune.tdep_precomp < 0, or too little free memory: refactorise inside the march)
     int tdep_pre = -1;             // -1: not decided yet
     // launch shapes chosen by the autotuner: {kind, nsys, L, C, G, T, ngroups, ragged}
     std::vector<std::array<int, 8>> tuned;
@@ -101,7 +102,7 @@ struct swr_plan_s {
     std::vector<Packing> packings;
     // The build after the first is captured into a CUDA graph (assembly,
     // factorisations, marches, lag-0 setup) and later builds replay it
-    // (SWR_GRAPH=0 disables).  Launches inside the graph are timed by their own
+    // (tune.graph < 0 disables).  Launches inside the graph are timed by their own
     // events, read back after the replay.
     bool use_graph = true, capturing = false, graph_pending = false;
     cudaGraph_t graph = nullptr;
@@ -132,13 +133,13 @@ struct swr_plan_s {
     bool long_march = false;
     void* d_long = nullptr;
     size_t long_bytes = 0;
-    // Toeplitz applies through the FFT (SWR_TOEPLITZ_FFT=0: direct causal sums):
+    // Toeplitz applies through the FFT (tune.toeplitz_fft < 0: direct causal sums):
     // transform length fftM (0: direct), twiddles, spectra of the two column sets
     int fftM = 0;
     double2* d_W = nullptr;
     double2 *d_spec = nullptr, *d_spec0 = nullptr;
     // static V, Robin: u(T) by superposition of the build marches' recorded states
-    // instead of a final march (SWR_SUPERPOSE=0, or too little free memory: final march)
+    // instead of a final march (tune.superpose < 0, or too little free memory: final march)
     bool superpose = false;
     double2* d_urec = nullptr;
     std::vector<long long> rec_base;   // per subdomain: Phi_l (nt x n_j), Phi_r, U_d (n_j)
@@ -154,6 +155,7 @@ struct swr_plan_s {
     double2 *d_kap = nullptr, *d_kout = nullptr, *d_rho = nullptr;
     bool built = false;
     bool have_L0 = false;
+    int two_level = 1;             // two-level separator solve for cluster-spread systems
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double t_build_ms = 0.0;
     // per-launch timing ring: kind 0 = march, 1 = Toeplitz apply, 2 = P^{-1}
@@ -167,12 +169,10 @@ struct swr_plan_s {
 
 namespace {
 
-// With SWR_DEBUG set in the environment, failing CUDA calls are reported on stderr.
-bool debug_on() {
-    static int on = -1;
-    if (on < 0) on = getenv("SWR_DEBUG") ? 1 : 0;
-    return on == 1;
-}
+// Failing CUDA calls are reported on stderr while a call into a plan created with
+// swr_tuning.debug >= 1 runs on this thread (set at the entry points).
+thread_local int t_debug = 0;
+bool debug_on() { return t_debug >= 1; }
 swr_status cuda_fail(cudaError_t e, const char* what, int line) {
     if (debug_on()) fprintf(stderr, "libswr: %s failed at line %d: %s\n", what, line, cudaGetErrorString(e));
     return SWR_ERR_CUDA;
@@ -500,6 +500,7 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     a.two_sigma = p->two_sigma;
     a.inv_ik = p->inv_ik;
     a.status = p->d_status;
+    a.two_level = p->two_level;
     a.t0 = seg.t0;
     a.gstride = seg.gstride > 0 ? seg.gstride : nt_run;
     a.nxrec = p->nx;
@@ -533,7 +534,10 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     if (kind == MK_NL)
         return swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
                                    p->d.nl_maxit, nullptr, cfg.ngroups, p->s, 0, p->d_pit);
-    return swr_launch_march(fs, a, ngroups, p->s, seg.mode);
+    const int rc = swr_launch_march(fs, a, ngroups, p->s, seg.mode);
+    if (rc == 0 && cfg.C > 1 && seg.mode == 0 && fs.nsteps == 1 && fs.tl_ok && p->two_level)
+        p->stats.two_level_launches += 1;
+    return rc;
 }
 
 inline int march_kind(swr_plan_t p, bool zero_potential) {
@@ -565,6 +569,10 @@ swr_status factor_for(swr_plan_t p, FactorSet& fs, int L, const double* V, doubl
         if (swr_factor_alloc(fs, p->N, L, chunks_for(p->nmax, L), p->s) != 0) return SWR_ERR_NOMEM;
     }
     if (swr_launch_factor(fs, p->N, p->d_n, p->d_loff, dg, od, p->d_status, p->s) != 0) {
+        cudaGetLastError();
+        return SWR_ERR_CUDA;
+    }
+    if (swr_launch_factor_tl(fs, p->N, p->d_loff, dg, od, p->d_status, p->s) == -1) {
         cudaGetLastError();
         return SWR_ERR_CUDA;
     }
@@ -691,8 +699,7 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
             cudaGetLastError();
             continue;
         }
-        if (const char* e = getenv("SWR_DEBUG"))
-            if (atoi(e) >= 2)
+        if (p->tune.debug >= 2)
                 fprintf(stderr, "swr autotune probe kind %d nsys %d: L %d C %d G %d T %d%s %.3f ms\n",
                         kind, nsys, c.L, c.C, c.G, c.T, c.ragged ? " ragged" : "", ms);
         if (best_ms < 0.f || ms < best_ms) {
@@ -702,7 +709,7 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (getenv("SWR_DEBUG"))
+    if (p->tune.debug >= 1)
         fprintf(stderr, "swr autotune kind %d nsys %d: L %d C %d G %d T %d%s (%.3f ms / %d steps)\n",
                 kind, nsys, best.L, best.C, best.G, best.T, best.ragged ? " ragged" : "", best_ms,
                 ntp);
@@ -1418,10 +1425,18 @@ void swr_destroy(swr_plan_t p) {
 }
 
 // Validate and set up one plan over count problem instances (count = 1: swr_plan).
-static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, void* stream) {
+static swr_status plan_create(const swr_desc* ds, int count, const swr_tuning* tuning,
+                              swr_plan_t* out, void* stream) {
     if (!out) return SWR_ERR_ARG;
     *out = nullptr;
     if (!ds || count < 1) return SWR_ERR_ARG;
+    if (tuning) {
+        const swr_tuning& u = *tuning;
+        if (!(u.chunk_L == 0 || u.chunk_L == 4 || u.chunk_L == 8 || u.chunk_L == 12 ||
+              u.chunk_L == 16) ||
+            u.debug < 0)
+            return SWR_ERR_ARG;
+    }
     const swr_desc* d = &ds[0];
     for (int i = 0; i < count; ++i) {
         const swr_desc& e = ds[i];
@@ -1459,6 +1474,8 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     swr_plan_t p = new (std::nothrow) swr_plan_s();
     if (!p) return SWR_ERR_NOMEM;
     p->d = *d;
+    if (tuning) p->tune = *tuning;
+    t_debug = p->tune.debug;
     p->d.node_off = nullptr;
     if (p->d.restart <= 0) p->d.restart = 30;
     if (p->d.restart > 200) p->d.restart = 200;   // Gram-Schmidt kernels take <= 256 vectors
@@ -1555,13 +1572,9 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (p->nsm <= 0) p->nsm = 152;
-    if (const char* e = getenv("SWR_CHUNK_L")) {   // tuning override: 4, 8, 12 or 16
-        const int v = atoi(e);
-        if (v == 4 || v == 8 || v == 12 || v == 16) p->forceL = v;
-    }
-    if (const char* e = getenv("SWR_AUTOTUNE")) {   // 0: keep the modelled launch shapes
-        p->autotune = atoi(e) != 0;
-    }
+    p->forceL = p->tune.chunk_L;                 // 0, 4, 8, 12 or 16 (validated)
+    p->autotune = p->tune.autotune >= 0;
+    p->two_level = p->tune.two_level >= 0 ? 1 : 0;
     swr_status st = SWR_OK;
     const size_t nb = (size_t)p->nb;
     if (!st) st = dalloc(&p->d_n, p->N);
@@ -1603,8 +1616,7 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
     if (!st) {
         // FFT Toeplitz applies: transform length M >= 2 nt - 1 (a power of two), for
         // 16 <= nt and M <= 4096 (three M-point buffers in shared memory)
-        bool on = true;
-        if (const char* e = getenv("SWR_TOEPLITZ_FFT")) on = atoi(e) != 0;
+        const bool on = p->tune.toeplitz_fft >= 0;
         int M = 1;
         while (M < 2 * p->nt - 1) M <<= 1;
         const bool want0 =
@@ -1634,8 +1646,7 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
         (d->tc == SWR_TC_ROBIN ? (d->tc_re != 0.0 || d->tc_im != 0.0) : p->nt < 4260)) {
         // u(T) by superposition: Phi_l, Phi_r (nt x n_j each) and U_d per subdomain, if
         // they take at most a quarter of the free memory
-        bool on = true;
-        if (const char* e = getenv("SWR_SUPERPOSE")) on = atoi(e) != 0;
+        const bool on = p->tune.superpose >= 0;
         long long tot = 0;
         std::vector<long long> base(p->N, 0);
         for (const InstInfo& I : p->inst)
@@ -1671,8 +1682,7 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
             for (int j = 0; j < I.N; ++j) p->work_R += (long long)p->n[I.sub0 + j] * I.nt;
         st = upload_systems(&p->d_sys_build, vb, p);
     }
-    bool force_long = false;   // SWR_LONG_MARCH=1: the grid-wide march for any V(x) plan
-    if (const char* e = getenv("SWR_LONG_MARCH")) force_long = atoi(e) != 0;
+    const bool force_long = p->tune.long_march >= 1;   // the grid-wide march for any V(x) plan
     if (!st && (force_long || chunks_for(p->nmax, 16) + 1 > 16 * march_tmax(MK_STATIC, 16))) {
         // a subdomain longer than one cluster can hold (16 CTAs x 256 chunks of 16 nodes):
         // the grid-wide march, V(x) and single instances only
@@ -1759,11 +1769,25 @@ static swr_status plan_create(const swr_desc* ds, int count, swr_plan_t* out, vo
 }
 
 swr_status swr_plan(const swr_desc* d, swr_plan_t* out, void* stream) {
-    return plan_create(d, 1, out, stream);
+    return plan_create(d, 1, nullptr, out, stream);
+}
+
+swr_status swr_plan_ex(const swr_desc* d, const swr_tuning* tuning, swr_plan_t* out,
+                       void* stream) {
+    return plan_create(d, 1, tuning, out, stream);
 }
 
 swr_status swr_plan_batch(const swr_desc* descs, int32_t count, swr_plan_t* out, void* stream) {
-    return plan_create(descs, count, out, stream);
+    return plan_create(descs, count, nullptr, out, stream);
+}
+
+swr_status swr_plan_batch_ex(const swr_desc* descs, int32_t count, const swr_tuning* tuning,
+                             swr_plan_t* out, void* stream) {
+    return plan_create(descs, count, tuning, out, stream);
+}
+
+void swr_tuning_defaults(swr_tuning* t) {
+    if (t) *t = swr_tuning{};
 }
 
 // Everything a build does after the inputs are in place and the first build's
@@ -1839,6 +1863,7 @@ static swr_status build_body(swr_plan_t p, bool do_assemble) {
 }
 
 swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p || !V || !u0) return SWR_ERR_ARG;
     cudaStream_t s = p->s;
     const size_t nb = (size_t)p->nb;
@@ -1848,14 +1873,14 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
     CK(cudaMemcpyAsync(p->d_V, V, sizeof(double) * nV, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemcpyAsync(p->d_u0, u0, sizeof(double2) * p->nx, cudaMemcpyDeviceToDevice, s));
     swr_status st = SWR_OK;
-    if (const char* e = getenv("SWR_GRAPH")) p->use_graph = p->use_graph && atoi(e) != 0;
+    if (p->tune.graph < 0) p->use_graph = false;
     const bool direct = !p->built || !p->use_graph;
     if (direct && (st = assemble(p, p->d_V, p->d_dg, p->d_od))) return st;
     if (p->d.vkind == SWR_V_TIME && p->tdep_pre < 0) {
         // per-step factorisations need nt copies of the factors (about 110 bytes
         // per node and step); take them while they use at most half the free memory
         bool on = p->nt >= 2;
-        if (const char* e = getenv("SWR_TDEP_PRECOMP")) on = on && atoi(e) != 0;
+        if (p->tune.tdep_precomp < 0) on = false;
         // the refactorising march has no S_0^2 history terms
         if (p->d.tc == SWR_TC_S02) on = p->nt >= 2;
         if (on) {
@@ -1996,6 +2021,7 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
 }
 
 swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_, swr_info* info) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     cudaStream_t s = p->s;
@@ -2068,6 +2094,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
 }
 
 swr_status swr_apply_R(swr_plan_t p, const double* g_in, double* g_out) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p || !g_in || !g_out || g_in == g_out) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     CK(cudaMemsetAsync(g_out, 0, sizeof(double2) * (size_t)p->nb, p->s));
@@ -2079,6 +2106,7 @@ swr_status swr_apply_R(swr_plan_t p, const double* g_in, double* g_out) {
 }
 
 swr_status swr_apply_interface(swr_plan_t p, const double* x, double* y) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p || !x || !y || x == y) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     if (p->d.vkind != SWR_V_STATIC) return SWR_ERR_UNSUPPORTED;
@@ -2090,6 +2118,7 @@ swr_status swr_apply_interface(swr_plan_t p, const double* x, double* y) {
 }
 
 swr_status swr_get_interface(swr_plan_t p, double* d, double* cols) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     const size_t nb = (size_t)p->nb;
@@ -2102,6 +2131,7 @@ swr_status swr_get_interface(swr_plan_t p, double* d, double* cols) {
 }
 
 swr_status swr_apply_precond(swr_plan_t p, const double* y, double* x) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p || !y || !x || x == y) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     if (!has_precond(p)) return SWR_ERR_STATE;
@@ -2113,6 +2143,7 @@ swr_status swr_apply_precond(swr_plan_t p, const double* y, double* x) {
 }
 
 swr_status swr_get_stats(swr_plan_t p, swr_stats* out, int32_t reset) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p) return SWR_ERR_ARG;
     CK(cudaStreamSynchronize(p->s));
     prof_flush(p);
@@ -2143,6 +2174,7 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats* out, int32_t reset) {
 
 swr_status swr_misfit(swr_plan_t p, const double* uT_, const double* target_, double* ubar_,
                       double* J) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p || !uT_ || !target_ || !J) return SWR_ERR_ARG;
     if (!p->d_part && dalloc(&p->d_part, 160)) return SWR_ERR_NOMEM;
     LK(swr_launch_misfit(reinterpret_cast<const double2*>(uT_),
@@ -2166,6 +2198,7 @@ swr_status swr_misfit(swr_plan_t p, const double* uT_, const double* target_, do
 // recomputed segment by segment from checkpoints of u every K steps (the
 // segment is recorded, then the adjoint march over the mirrored steps reads it).
 swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t ckpt_every) {
+    t_debug = p ? p->tune.debug : 0;
     if (!p || !ubar_ || !dJdV_) return SWR_ERR_ARG;
     if (!p->built || !p->solved) return SWR_ERR_STATE;
     // the nonlinear gradient is taken of the monodomain scheme (any transmission

@@ -151,7 +151,21 @@ struct FactorSet {
     double2* dgb = nullptr;        // [batch][ldd] assembled diagonal (nsteps > 1)
     double2* odb = nullptr;        // [batch][ldd] assembled coupling
     long long ldd = 0;
+    // Two-level separator solve for systems spread over a cluster (constant matrix,
+    // P < kTlMaxSep): separators in warp blocks of 32, lane 0 of every block (and the
+    // system's last separator) a super-separator, lanes 1..31 a super-chunk solved by
+    // PCR with warp shuffles; the super-separators form a tridiagonal reduced system
+    // of at most 32 unknowns, solved by one warp.  Layout, per subdomain:
+    //   tl_pcr  [N][5][2][P+1]  super-chunk PCR coefficients (alpha, gamma), zero off it
+    //   tl_aux  [N][3][P+1]     1/delta after the last level, spikes a (left), b (right)
+    //   tl_red  [N][13][32]     reduced system: 5 levels of (alpha, gamma), 1/delta,
+    //                           and the weights of y_last(q-1), y_first(q) in its RHS
+    double2* tl_pcr = nullptr;
+    double2* tl_aux = nullptr;
+    double2* tl_red = nullptr;
+    bool tl_ok = false;
 };
+constexpr int kTlMaxSep = 993;   // P + 1 <= 993: at most 32 super-separators
 
 struct MarchArgs {
     int nt, P, levels, C, G, T, nsys;
@@ -216,6 +230,11 @@ struct MarchArgs {
     double2 two_sigma;    // 2 p (Robin): 2 S-tilde v = 2 p v
     double2 inv_ik;       // 1/(i kappa), kappa = (2/dt)(h/6): the system is scaled by it
     int* status;
+    // two-level separator solve of cluster-spread systems (FactorSet.tl_*; NULL: off)
+    const double2* tl_pcr;
+    const double2* tl_aux;
+    const double2* tl_red;
+    int two_level;        // 0: keep the cluster-wide PCR even when the data exists
 };
 
 // One problem instance of a batched plan.  The instances' subdomains, interface
@@ -259,6 +278,10 @@ int swr_launch_factor_steps(FactorSet& fs, int N, const int* d_n, const int* d_g
 void swr_factor_free(FactorSet& fs);
 int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
                       const double2* od, int* status, cudaStream_t s);
+// The two-level separator data (FactorSet.tl_*) after swr_launch_factor, for a constant
+// matrix with P + 1 <= kTlMaxSep; allocates it.  0, -1 (CUDA error) or -2 (not applicable).
+int swr_launch_factor_tl(FactorSet& fs, int N, const int* d_loff, const double2* dg,
+                         const double2* od, int* status, cudaStream_t s);
 int swr_launch_march(const FactorSet& fs, MarchArgs a, int nsys_groups, cudaStream_t s,
                      int mode = 0);
 int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef, double tol,
@@ -267,6 +290,7 @@ int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef
 int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, long long vstride,
                           double h, double kappa, double2 sig_ik, int ngroups, cudaStream_t s);
 int swr_march_smem_bytes(int T, int G, int stage_slots = 0);
+int swr_march_tl_smem_bytes(int T);
 
 // Interface algebra launchers (swr_krylov.cu)
 int swr_launch_toeplitz(int N, int nt, const double2* cols, const double2* x, const double2* add,

@@ -912,9 +912,12 @@ int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* la
 
 // Warp 0 waits, solves and publishes; warps 1-4 (one per source block) form the
 // history sums, lags >= 3, two steps ahead of warp 0 and without a per-step barrier:
-// they run as soon as warp 0 has seen step m's inputs (shared flag s_xready) and hand
-// their sums over in a three-slot ring with one ready flag per warp (s_hdone).  Warp 0
-// then adds only the lag-2 and lag-1 terms on its critical path.
+// each runs as soon as its source's values are there (this interface's x: the shared
+// counter s_xown; a neighbour's: its progress counter) and hands its sum over in a
+// three-slot ring with one ready flag per warp (s_hdone), refilling a slot only after
+// warp 0 has consumed it (s_hused).  Warp 0 adds only the lag-2 and lag-1 terms on
+// its critical path, and no fence or block-wide barrier sits in its time loop besides
+// the release of its own progress counter.
 // The same-step coupling of neighbouring interfaces is resolved either by
 // `sweeps` block-Jacobi sweeps (H == 0), or exactly (to (|c| |D^{-1}|)^{H+1}) by
 // the window form (H >= 1), x_n(k) = sum_d G_{k,k+d} R_n(k+d) with the rows of
@@ -934,13 +937,21 @@ namespace {
 constexpr long long kLocalPolls = 1LL << 24;   // bound of a wait between warps of one CTA
 }
 
-// Wait until *flag >= target (a shared flag written by another warp of this CTA), or
-// until *stop is set; false on stop or when the bound runs out.
-__device__ __forceinline__ bool cta_wait_ge(const volatile int* flag, int target,
-                                            const volatile int* stop) {
+// Flags between the warps of one CTA (shared memory, CTA-scope release/acquire).
+__device__ __forceinline__ int cta_load_acquire(const int* p) {
+    cuda::atomic_ref<const int, cuda::thread_scope_block> r(*p);
+    return r.load(cuda::memory_order_acquire);
+}
+__device__ __forceinline__ void cta_store_release(int* p, int v) {
+    cuda::atomic_ref<int, cuda::thread_scope_block> r(*p);
+    r.store(v, cuda::memory_order_release);
+}
+// Wait until *flag >= target, or until *stop is set; false on stop or when the bound
+// runs out.
+__device__ __forceinline__ bool cta_wait_ge(const int* flag, int target, const int* stop) {
     long long polls = 0;
-    while (*flag < target) {
-        if (*stop) return false;
+    while (cta_load_acquire(flag) < target) {
+        if (cta_load_acquire(stop)) return false;
         if (++polls > kLocalPolls) return false;
         __nanosleep(32);
     }
@@ -959,10 +970,11 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                                                      const int* __restrict__ if_inst, int k0,
                                                      int nif_all, const double2* __restrict__ Gw,
                                                      int H) {
-    __shared__ double2 hp[3][4];        // lags >= 3 of step m (slot m % 3), one per source
-    __shared__ volatile int s_xready;   // warp 0 has seen the inputs of step s_xready
-    __shared__ volatile int s_hdone[4]; // history warp e has filled the slots of steps <= it
-    __shared__ volatile int s_stop;     // warp 0 left its loop early (timeout or abort)
+    __shared__ double2 hp[3][4];   // lags >= 3 of step m (slot m % 3), one per source
+    __shared__ int s_xown;         // x_0 .. x_{s_xown - 1} of this interface are written
+    __shared__ int s_hused;        // warp 0 has consumed the history sums of steps <= s_hused
+    __shared__ int s_hdone[4];     // history warp e has filled the slots of steps <= s_hdone[e]
+    __shared__ int s_stop;         // warp 0 left its loop early (timeout or abort)
     // global interface kg (progress, sweep values, lag-0 blocks); local k within its
     // instance (blocks, columns)
     const int kg = k0 + blockIdx.x;
@@ -997,24 +1009,40 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
     if (threadIdx.x < 12) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
     if (threadIdx.x < 4) s_hdone[threadIdx.x] = 2;   // steps 0..2 have no lag >= 3 term
     if (threadIdx.x == 0) {
-        s_xready = -1;
+        s_xown = 0;
+        s_hused = -1;
         s_stop = 0;
     }
     __syncthreads();
 
     // ---- history warps: lags >= 3 of step m + 2 from the values s <= m - 1 ----------
+    // Sources 0 and 2 are this interface's own blocks (written by warp 0: wait on
+    // s_xown); sources 1 and 3 are the neighbours' (wait on their progress counters,
+    // read through L2).  A slot is refilled only after warp 0 has consumed it.
     if (w >= 1) {
         const int e = w - 1;
         bool has = false;
         const double2* cc = nullptr;
         const double2* xin = nullptr;
         source(k, e, has, cc, xin);
+        const bool own = (e == 0 || e == 2);
+        const int nb = (e == 1) ? kg + 1 : kg - 1;
         for (int m = 1; m + 2 < nt; ++m) {
-            if (!cta_wait_ge(&s_xready, m, &s_stop)) break;
-            __threadfence();   // pairs with warp 0's fence before s_xready = m
+            bool ok = cta_wait_ge(&s_hused, m - 1, &s_stop);
+            if (ok && has) {
+                if (own) {
+                    ok = cta_wait_ge(&s_xown, m, &s_stop);
+                } else if (lane == 0) {
+                    // x_{<= m-1} of the neighbour: progress >= m + 1 (window form) or
+                    // >= m (sweeps + 1) (sweep form)
+                    ok = wait_one(nb, WIN ? m + 1 : m * (sweeps + 1), progress, abortf, status,
+                                  lim);
+                }
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
             double2 a0 = zero, a1 = zero;
             if (has) {
-                // x of other CTAs through L2 (__ldcg): the flag above is CTA-scoped
                 int s = lane;
                 for (; s + 32 < m; s += 64) {
                     a0 = cfma(__ldg(cc + m + 2 - s), __ldcg(xin + s), a0);
@@ -1025,8 +1053,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             const double2 acc = warp_sum(cadd(a0, a1));
             if (lane == 0) {
                 hp[(m + 2) % 3][e] = acc;
-                __threadfence_block();
-                s_hdone[e] = m + 2;
+                cta_store_release(&s_hdone[e], m + 2);
             }
         }
         return;
@@ -1051,7 +1078,6 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
 #pragma unroll
         for (int e = 0; e < 4; ++e) ok = ok && cta_wait_ge(&s_hdone[e], m, &s_stop);
         if (!ok) return false;
-        __threadfence_block();
         double2 h[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -1062,6 +1088,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         h1 = h[1];
         h2 = h[2];
         h3 = h[3];
+        cta_store_release(&s_hused, m);
         return true;
     };
     auto fail_local = [&]() {   // a wait between this CTA's warps ran out: leave everywhere
@@ -1110,10 +1137,6 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             if (waits) ok = wait_one(kg + d, n + 1, progress, abortf, status, lim);
             ok = __all_sync(0xffffffffu, ok);                  // x_{<n}, P_n visible
             if (!ok) break;
-            if (lane == 0) {
-                __threadfence();
-                s_xready = n;                                  // history warps may use x_{<n}
-            }
             // the next right-hand side's data, off the critical path
             double2 yn1a = zero, yn1b = zero;
             if (lane == 0 && n + 1 < nt) {
@@ -1138,6 +1161,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             if (lane == 0) {
                 x[(size_t)(2 * k) * nt + n] = z1;
                 x[(size_t)(2 * k + 1) * nt + n] = z2;
+                cta_store_release(&s_xown, n + 1);
                 if (n + 1 < nt) {
                     double2 q0, q1, q2, q3;
                     if (hist_ge2(n + 1, q0, q1, q2, q3)) {
@@ -1184,8 +1208,6 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             if (!ok) break;
             int go = 1;
             if (solver) {
-                __threadfence();
-                s_xready = n;
                 // history of step n: lags >= 2 (the warps' sums and lag 2) + lag 1
                 double2 h[4];
                 if (!hist_ge2(n, h[0], h[1], h[2], h[3])) {
@@ -1219,6 +1241,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                     if (go) {
                         x[(size_t)(2 * k) * nt + n] = z1;
                         x[(size_t)(2 * k + 1) * nt + n] = z2;
+                        cta_store_release(&s_xown, n + 1);
                         if (publish) store_release(progress + kg, (n + 1) * S1);   // orders x
                     }
                 }
@@ -1227,7 +1250,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             if (!go) break;
         }
     }
-    if (lane == 0) s_stop = 1;   // releases history warps still waiting
+    if (lane == 0) cta_store_release(&s_stop, 1);   // releases history warps still waiting
 }
 
 int swr_set_wait_hook(long long max_polls, int withhold) {

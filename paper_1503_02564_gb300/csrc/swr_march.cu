@@ -418,6 +418,194 @@ __global__ void k_reduce_pcr(int N, int P, int levels, const int* __restrict__ l
     if (bad) atomicOr(status, ST_SINGULAR);
 }
 
+// ---------------------------------------------------------------------------
+// Two-level separator solve (clusters).  One CTA of 1024 threads per subdomain,
+// thread p = separator p (P + 1 <= 993).  The separator rows are those of
+// k_reduce_pcr: lo x_{p-1} + dd x_p + up x_{p+1} = d_p.  Warp q holds separators
+// 32q .. 32q+31; its lane 0 (s_q = 32q) and the last separator Pj are
+// super-separators, the others (lanes 1..m_q, m_q = min(31, Pj - 1 - 32q)) form
+// super-chunk q.  With the super-separators known, a super-chunk is the tridiagonal
+// system A_q x = d - lo e_first x_{s_q} - up e_last x_{s_{q+1}}, solved as
+// x = yhat - a x_{s_q} - b x_{s_{q+1}} (yhat = A_q^{-1} d by PCR, spikes a, b);
+// substituting the neighbouring super-chunks' first/last rows into row s_q gives a
+// tridiagonal system in the super-separators:
+//   RL_q x_{s_{q-1}} + RD_q x_{s_q} + RU_q x_{s_{q+1}}
+//       = d_{s_q} - cL_q yhat_last(q-1) - cU_q yhat_first(q),
+//   RL = -lo a_{s-1} (lo when super-chunk q-1 is empty), RU = -up b_{s+1} (or up),
+//   RD = dd - lo b_{s-1} - up a_{s+1} (terms of empty super-chunks dropped),
+//   cL = lo, cU = up (0 for an empty super-chunk).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 shfl_up2(double2 v, int d) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 shfl_down2(double2 v, int d) {
+    return make_double2(__shfl_down_sync(0xffffffffu, v.x, d),
+                        __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+// PCR coefficients of a tridiagonal system held one row per lane (rows outside
+// [lo_lane, hi_lane] are absent): alpha/gamma of level k into co[(2k) cs], co[(2k+1) cs]
+// (when `store`), and the decoupled diagonal into dfin.  Spike right-hand sides e1, e2
+// are carried along.
+__device__ void warp_pcr_coeffs(double2 L, double2 D, double2 U, int lane, int lo_lane,
+                                int hi_lane, double2* co, size_t cs, bool store, double2& e1,
+                                double2& e2, double2& dfin) {
+    const double2 zero = make_double2(0.0, 0.0);
+    const bool in = lane >= lo_lane && lane <= hi_lane;
+    if (!in) {
+        L = zero;
+        U = zero;
+        D = make_double2(1.0, 0.0);
+        e1 = zero;
+        e2 = zero;
+    }
+    for (int k = 0; k < 5; ++k) {
+        const int st = 1 << k;
+        const double2 Lm = shfl_up2(L, st), Dm = shfl_up2(D, st), Um = shfl_up2(U, st);
+        const double2 Lp = shfl_down2(L, st), Dp = shfl_down2(D, st), Up = shfl_down2(U, st);
+        const double2 e1m = shfl_up2(e1, st), e1p = shfl_down2(e1, st);
+        const double2 e2m = shfl_up2(e2, st), e2p = shfl_down2(e2, st);
+        double2 a = zero, g = zero;
+        if (in && lane - st >= lo_lane) a = cmul(make_double2(-L.x, -L.y), crcp(Dm));
+        if (in && lane + st <= hi_lane) g = cmul(make_double2(-U.x, -U.y), crcp(Dp));
+        const double2 nL = cmul(a, Lm), nU = cmul(g, Up);
+        const double2 nD = cfma(g, Lp, cfma(a, Um, D));
+        e1 = cfma(g, e1p, cfma(a, e1m, e1));
+        e2 = cfma(g, e2p, cfma(a, e2m, e2));
+        if (store) {
+            co[(size_t)(2 * k) * cs] = a;
+            co[(size_t)(2 * k + 1) * cs] = g;
+        }
+        L = nL;
+        D = nD;
+        U = nU;
+    }
+    dfin = D;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_factor_two_level(
+    int N, int P, const int* __restrict__ loff_, const double2* __restrict__ dg,
+    const double2* __restrict__ od, const int* __restrict__ sub_P,
+    const int* __restrict__ sep_pos, const double2* __restrict__ tips,
+    double2* __restrict__ tl_pcr, double2* __restrict__ tl_aux, double2* __restrict__ tl_red,
+    int* status) {
+    // per super-separator q: its row (lo, dd, up); per super-chunk q: the spikes at its
+    // first member (af, bf) and last member (al, bl)
+    __shared__ double2 s_lo[33], s_dd[33], s_up[33], s_af[33], s_bf[33], s_al[33], s_bl[33];
+    const int j = blockIdx.x;
+    const int p = threadIdx.x, lane = p & 31, q = p >> 5;
+    const int Pj = sub_P[j];
+    const int S = P + 1;
+    const int Q = (Pj + 31) / 32;
+    const double2 zero = make_double2(0.0, 0.0), one = make_double2(1.0, 0.0);
+    const double2* T = tips + (size_t)j * P * 4;
+    const int base = loff_[j];
+    // separator rows (as k_reduce_pcr); padding beyond Pj: identity rows
+    double2 lo = zero, dd = one, up = zero;
+    if (p <= Pj) {
+        const int s = sep_pos[j * S + p];
+        dd = dg[base + s];
+        if (p > 0) {
+            const double2 EL = od[base + s - 1];
+            dd = cfms(EL, T[(p - 1) * 4 + 3], dd);
+            lo = cmul(make_double2(-EL.x, -EL.y), T[(p - 1) * 4 + 2]);
+        }
+        if (p < Pj) {
+            const double2 ER = od[base + s];
+            dd = cfms(ER, T[p * 4 + 0], dd);
+            up = cmul(make_double2(-ER.x, -ER.y), T[p * 4 + 1]);
+        }
+    }
+    // super-separator rows: s_q = 32 q (q < Q) and s_Q = Pj
+    if ((lane == 0 && q < Q) || p == Pj) {
+        const int qi = (p == Pj) ? Q : q;
+        s_lo[qi] = lo;
+        s_dd[qi] = dd;
+        s_up[qi] = up;
+    }
+    // super-chunk q: lanes 1..m
+    const int m = (32 * q < Pj) ? min(31, Pj - 1 - 32 * q) : 0;
+    double2 e1 = (lane == 1) ? lo : zero, e2 = (lane == m) ? up : zero, dfin;
+    const bool keep = p < S;
+    warp_pcr_coeffs(lo, dd, up, lane, 1, m, tl_pcr + (size_t)j * 10 * S + (keep ? p : 0),
+                    (size_t)S, keep, e1, e2, dfin);
+    const bool member = lane >= 1 && lane <= m;
+    bool bad = false;
+    double2 binv = one, sa = zero, sb = zero;
+    if (member) {
+        bad = !cfinite(dfin) || (dfin.x == 0.0 && dfin.y == 0.0);
+        binv = crcp(dfin);
+        sa = cmul(e1, binv);
+        sb = cmul(e2, binv);
+    }
+    if (keep) {
+        tl_aux[((size_t)j * 3 + 0) * S + p] = binv;
+        tl_aux[((size_t)j * 3 + 1) * S + p] = sa;
+        tl_aux[((size_t)j * 3 + 2) * S + p] = sb;
+    }
+    if (member && lane == 1) {
+        s_af[q] = sa;
+        s_bf[q] = sb;
+    }
+    if (member && lane == m) {
+        s_al[q] = sa;
+        s_bl[q] = sb;
+    }
+    __syncthreads();
+    // reduced system over the super-separators
+    if (q == 0) {
+        double2 RL = zero, RD = one, RU = zero, cL = zero, cU = zero;
+        if (lane <= Q) {
+            const int sq = (lane < Q) ? 32 * lane : Pj;
+            const int mprev = (lane >= 1) ? sq - 1 - 32 * (lane - 1) : 0;   // members of q-1
+            const int mcur = (lane < Q) ? min(31, Pj - 1 - sq) : 0;          // members of q
+            RD = s_dd[lane];
+            if (lane >= 1) {
+                if (mprev > 0) {
+                    RL = cmul(make_double2(-s_lo[lane].x, -s_lo[lane].y), s_al[lane - 1]);
+                    RD = cfms(s_lo[lane], s_bl[lane - 1], RD);
+                    cL = s_lo[lane];
+                } else {
+                    RL = s_lo[lane];
+                }
+            }
+            if (lane < Q) {
+                if (mcur > 0) {
+                    RU = cmul(make_double2(-s_up[lane].x, -s_up[lane].y), s_bf[lane]);
+                    RD = cfms(s_up[lane], s_af[lane], RD);
+                    cU = s_up[lane];
+                } else {
+                    RU = s_up[lane];
+                }
+            }
+        }
+        double2* R = tl_red + (size_t)j * 13 * 32;
+        double2 z1 = zero, z2 = zero, rfin;
+        warp_pcr_coeffs(RL, RD, RU, lane, 0, Q, R + lane, 32, true, z1, z2, rfin);
+        double2 rinv = one;
+        if (lane <= Q) {
+            bad |= !cfinite(rfin) || (rfin.x == 0.0 && rfin.y == 0.0);
+            rinv = crcp(rfin);
+        }
+        R[10 * 32 + lane] = rinv;
+        R[11 * 32 + lane] = cL;
+        R[12 * 32 + lane] = cU;
+    }
+    if (bad) atomicOr(status, ST_SINGULAR);
+}
+
+int swr_launch_factor_tl(FactorSet& fs, int N, const int* d_loff, const double2* dg,
+                         const double2* od, int* status, cudaStream_t s) {
+    fs.tl_ok = false;
+    if (fs.nsteps != 1 || fs.P + 1 > kTlMaxSep || !fs.tl_pcr) return -2;
+    k_factor_two_level<<<N, 1024, 0, s>>>(N, fs.P, d_loff, dg, od, fs.sub_P, fs.sep_pos,
+                                           fs.tips, fs.tl_pcr, fs.tl_aux, fs.tl_red, status);
+    swr_count_launch(1);
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    fs.tl_ok = true;
+    return 0;
+}
+
 static int ilog2ceil(int v) {
     int k = 0;
     while ((1 << k) < v) ++k;
@@ -460,6 +648,11 @@ int swr_factor_alloc(FactorSet& fs, int N, int L, int P, cudaStream_t, int nstep
     if (fs.nsteps > 1) {
         ok &= cudaMalloc(&fs.dgb, sizeof(double2) * (size_t)ldd * nb) == cudaSuccess;
         ok &= cudaMalloc(&fs.odb, sizeof(double2) * (size_t)ldd * nb) == cudaSuccess;
+    } else if (S <= (size_t)kTlMaxSep) {
+        // the two-level separator data of cluster-spread systems
+        ok &= cudaMalloc(&fs.tl_pcr, sizeof(double2) * (size_t)N * 10 * S) == cudaSuccess;
+        ok &= cudaMalloc(&fs.tl_aux, sizeof(double2) * (size_t)N * 3 * S) == cudaSuccess;
+        ok &= cudaMalloc(&fs.tl_red, sizeof(double2) * (size_t)N * 13 * 32) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();   // clear the allocation error
@@ -480,6 +673,9 @@ void swr_factor_free(FactorSet& fs) {
     cudaFree(fs.red);
     cudaFree(fs.dgb);
     cudaFree(fs.odb);
+    cudaFree(fs.tl_pcr);
+    cudaFree(fs.tl_aux);
+    cudaFree(fs.tl_red);
     fs = FactorSet();
 }
 
@@ -1070,6 +1266,356 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
 }
 
 // ---------------------------------------------------------------------------
+// The constant-matrix march of one system spread over a cluster of C CTAs with the
+// two-level separator solve (FactorSet.tl_*): one cluster barrier per time step
+// instead of one per PCR level.  Thread p = rank T + tid owns separator p and chunk p
+// as in k_march_static; T is a multiple of 32, so warp q of the system (separators
+// 32q .. 32q+31) lies in one CTA, and the first separator of every CTA is a
+// super-separator.  Per step:
+//   A  chunk right-hand sides and local solves (the right separator's u comes from
+//      the same warp or, for a super-separator, from this CTA's replica usup);
+//   B  separator right-hand sides; a super-separator forms the part of its row it
+//      owns, and lane 31 the part that its chunk contributes to the next warp's
+//      super-separator;
+//   C  super-chunk PCR in registers (warp shuffles), then each warp publishes its
+//      super-separator data and the first/last super-chunk values (double-buffered
+//      by step parity); one cluster barrier;
+//   D  warp 0 of every CTA gathers the reduced right-hand sides (distributed shared
+//      memory) and solves the reduced system by PCR, so every CTA holds all
+//      super-separator values (xsup) and their u (usup); one CTA barrier;
+//   E  super-chunk values x = yhat - a x_{s_q} - b x_{s_{q+1}};
+//   F  spike correction of the chunks, CN update, fluxes (as k_march_static).
+// MODE 0 only (no recorded v, no gradient), constant factors.
+// ---------------------------------------------------------------------------
+int swr_march_tl_smem_bytes(int T) {
+    const int W = T / 32;
+    return (int)sizeof(double2) * (6 * T + 2 * W * 5 + 2 * 33 + 8);
+}
+
+template <int L, bool GEN>
+__global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const MarchArgs a) {
+    extern __shared__ double2 sm[];
+    const int T = a.T, P = a.P, C = a.C, nt = a.nt;
+    const int W = T / 32;
+    double2* usep = sm;              // [T] u at my separators
+    double2* xv = usep + T;          // [T] separator values of this step
+    double2* ufst = xv + T;
+    double2* ulst = ufst + T;
+    double2* yfst = ulst + T;
+    double2* ylst = yfst + T;
+    double2* pub = ylst + T;         // [2][W][5] per warp: P0, P1, yhat_first, yhat_last, P4
+    double2* xsup = pub + 2 * W * 5; // [33] super-separator values (every CTA)
+    double2* usup = xsup + 33;       // [33] u at the super-separators (every CTA)
+    double2* hsum = usup + 33;       // [2] S_0^2 / own-operator history of the two ends
+    double2* hsum2 = hsum + 2;       // [2] flux-update history (per-end kernels)
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    const int p = rank * T + tid;
+    const int sidx = blockIdx.x / C;
+    const double2 zero = make_double2(0.0, 0.0);
+    const bool valid = (p <= P) && (sidx < a.nsys);
+    MarchSys sy = {0, 0, 0, -1, -1, -1, -1, 0};
+    int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0;
+    if (sidx < a.nsys) {
+        sy = a.sys[sidx];
+        j = sy.sub;
+        Pj = a.sub_P[j];
+        goff = a.sub_goff[j];
+        tcf = a.sub_tc[j];
+    }
+    if (valid) {
+        Lp = (p < P) ? a.clen[j * P + p] : 0;
+        sp = a.sep_pos[j * (P + 1) + p];
+    }
+    const int Q = (Pj + 31) / 32;
+    const int q = p >> 5;
+    const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
+    const bool realsep = valid && (p <= Pj);
+    const bool sup = realsep && (lane == 0 || p == Pj);          // a super-separator
+    const int qsup = (p == Pj) ? Q : q;                           // its index
+    const int m = (32 * q < Pj) ? min(31, Pj - 1 - 32 * q) : 0;   // members of super-chunk q
+    const bool member = realsep && lane >= 1 && lane <= m;
+    // super-separator index of separator p + 1 (or -1 if it is a super-chunk member)
+    const int rsup = (p + 1 == Pj) ? Q : (((p + 1) & 31) == 0 ? (p + 1) >> 5 : -1);
+    const bool rec_u = valid && a.urec && (sy.flags & SYS_REC_U);
+    const int nj = (sidx < a.nsys) ? a.sub_n[j] : 0;
+    const int ntc = min(sy.nt, nt);
+    const size_t S = P + 1;
+    const double2* F = a.fac + (size_t)j * L * 4 * P + (p < P ? p : 0);
+    const double2* sE_l = a.sep + (size_t)(j * 3 + 0) * S;
+    const double2* sE_r = a.sep + (size_t)(j * 3 + 1) * S;
+    const double2* tpc = a.tl_pcr + (size_t)j * 10 * S + (valid ? p : 0);
+    const double2* tax = a.tl_aux + (size_t)j * 3 * S + (valid ? p : 0);
+    const double2* tred = a.tl_red + (size_t)j * 13 * 32 + lane;
+    // the separator solve's coefficients are re-read every step (L1-resident), which
+    // keeps the chunk state in registers
+
+    double2 u[L], y[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        u[i] = (valid && i < Lp && !zero_u0) ? a.u0[goff + sp + 1 + i] : zero;
+        y[i] = zero;
+    }
+    usep[tid] = (realsep && !zero_u0) ? a.u0[goff + sp] : zero;
+    // replicas of the super-separators' u in every CTA (warp 0)
+    if (wl == 0 && lane <= Q && sidx < a.nsys) {
+        const int ps = (lane < Q) ? 32 * lane : Pj;
+        usup[lane] = zero_u0 ? zero : a.u0[goff + a.sep_pos[j * S + ps]];
+    }
+    const bool hl = a.s02 && realsep && p == 0 && (tcf & 1);
+    const bool hr = a.s02 && realsep && p == Pj && (tcf & 2);
+    double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * (nt + 1) : nullptr;
+    double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * (nt + 1) : nullptr;
+    constexpr bool gen = GEN;
+    if (hl) hist_l[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 0], a.u0[goff + sp]) : a.u0[goff + sp]);
+    if (hr) hist_r[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 1], a.u0[goff + sp]) : a.u0[goff + sp]);
+    // the warps that hold the two ends form their history sums
+    const bool wleft = a.s02 && (tcf & 1) && rank == 0 && wl == 0;
+    const bool wright = a.s02 && (tcf & 2) && rank == Pj / T && wl == (Pj % T) / 32;
+    cl.sync();
+
+    double2 lin = zero, rin = zero;
+    for (int t = 1; t <= ntc; ++t) {
+        const int slot = (t & 1) * W * 5;
+        // ---- A: chunk right-hand sides and local LU solves ---------------------
+        if (valid && Lp > 0) {
+            const double2 uL = usep[tid];
+            const double2 uR = (rsup >= 0) ? usup[rsup] : usep[tid + 1];
+            double2 zprev = zero, cprev = zero, uf = zero, ul = zero;
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    const double2 left = (i == 0) ? uL : u[i - 1];
+                    double2 right;
+                    if (i + 1 < L)
+                        right = (i == Lp - 1) ? uR : u[i + 1];
+                    else
+                        right = uR;
+                    double2 f = make_double2(fma(4.0, u[i].x, left.x + right.x),
+                                             fma(4.0, u[i].y, left.y + right.y));
+                    const double2 z = (i == 0) ? f : cfms(cprev, zprev, f);
+                    y[i] = z;
+                    zprev = z;
+                    cprev = F[(i * 4 + 1) * P];
+                    if (i == 0) uf = u[i];
+                    ul = csel(i == Lp - 1, u[i], ul);
+                }
+            }
+            double2 ynext = zero, yl = zero;
+#pragma unroll
+            for (int i = L - 1; i >= 0; --i) {
+                if (i < Lp) {
+                    const double2 qi = F[(i * 4 + 0) * P];
+                    double2 yi = cmul(qi, y[i]);
+                    if (i != Lp - 1) yi = cfms(F[(i * 4 + 1) * P], ynext, yi);
+                    else yl = yi;
+                    y[i] = yi;
+                    ynext = yi;
+                }
+            }
+            ufst[tid] = uf;
+            ulst[tid] = ul;
+            yfst[tid] = y[0];
+            ylst[tid] = yl;
+        }
+        // history sums of the ends (the warps holding them)
+        if (wleft || wright) {
+            double2* hh = wleft ? hist_l : hist_r;
+            const int side = wleft ? 0 : 1;
+            if (gen) {
+                const size_t ke = (size_t)(2 * j + side) * a.kstride;
+                double2 o1, o2;
+                conv_history2(a.kap + ke, a.kout + ke, hh, t, lane, o1, o2);
+                if (lane == 0) {
+                    hsum[side] = o1;
+                    hsum2[side] = o2;
+                }
+            } else {
+                const double2 hsv = s02_history(a.beta, hh, t, lane);
+                if (lane == 0) hsum[side] = hsv;
+            }
+        }
+        __syncwarp();
+        // ---- B: separator right-hand sides --------------------------------------
+        double2 d = zero;
+        if (realsep) {
+            const double2 us = usep[tid];
+            const bool le = (p == 0), re = (p == Pj);
+            // the chunk on the left is in this warp unless p is a warp's lane 0
+            const bool own_left = !le && lane != 0;
+            const double2 um = own_left ? ulst[tid - 1] : zero;
+            const double2 up = re ? zero : ufst[tid];
+            double2 f;
+            if (le)
+                f = make_double2(fma(2.0, us.x, up.x), fma(2.0, us.y, up.y));
+            else if (re)
+                f = make_double2(fma(2.0, us.x, um.x), fma(2.0, us.y, um.y));
+            else
+                f = make_double2(fma(4.0, us.x, um.x + up.x), fma(4.0, us.y, um.y + up.y));
+            if (le && (tcf & 1)) {
+                if (sy.flags & SYS_IMP_L)
+                    lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                else
+                    lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l + a.t0 + t - 1] : zero;
+                f = cfms(lin, a.inv_ik, f);
+                if (a.s02) f = cfma(hsum[0], gen ? a.inv_ik : a.c2_ik, f);
+            }
+            if (re && (tcf & 2)) {
+                if (sy.flags & SYS_IMP_R)
+                    rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                else
+                    rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r + a.t0 + t - 1] : zero;
+                f = cfms(rin, a.inv_ik, f);
+                if (a.s02) f = cfma(hsum[1], gen ? a.inv_ik : a.c2_ik, f);
+            }
+            d = f;
+            if (own_left) d = cfms(sE_l[p], ylst[tid - 1], d);
+            if (!re) d = cfms(sE_r[p], yfst[tid], d);
+        }
+        // lane 31: this chunk's part of the next super-separator's row
+        double2 p1 = zero;
+        if (valid && lane == 31 && p + 1 <= Pj)
+            p1 = cfms(sE_l[p + 1], ylst[tid], ulst[tid]);
+        // ---- C: super-chunk PCR in registers ----------------------------------
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int st = 1 << k;
+            const double2 dm = shfl_up2(d, st), dp = shfl_down2(d, st);
+            if (member) d = cfma(tpc[(2 * k + 1) * S], dp, cfma(tpc[(2 * k) * S], dm, d));
+        }
+        if (member) d = cmul(d, tax[0]);
+        {
+            double2* pb = pub + slot + wl * 5;
+            if (lane == 0 && realsep) pb[0] = d;                 // row s_q, own part
+            if (lane == 31) pb[1] = p1;
+            if (lane == 1 && member) pb[2] = d;                  // yhat of the first member
+            if (member && lane == m) pb[3] = d;                  // yhat of the last member
+            if (p == Pj && lane != 0 && valid) pb[4] = d;        // row Pj, complete
+        }
+        cl.sync();
+        // ---- D: reduced system (warp 0 of every CTA) -----------------------------
+        if (wl == 0 && sidx < a.nsys) {
+            double2 r = zero;
+            if (lane <= Q) {
+                auto pubof = [&](int qq) -> const double2* {   // warp qq's published data
+                    const int home = (32 * qq) / T;
+                    double2* base = (home == rank) ? pub : cl.map_shared_rank(pub, home);
+                    return base + slot + ((32 * qq) % T) / 32 * 5;
+                };
+                if (lane == Q && (Pj & 31) != 0) {
+                    r = pubof(Q - 1)[4];
+                } else {
+                    r = pubof(lane)[0];
+                    if (lane >= 1) r = cadd(r, pubof(lane - 1)[1]);
+                }
+                const double2 cL = tred[11 * 32], cU = tred[12 * 32];
+                if (lane >= 1 && (cL.x != 0.0 || cL.y != 0.0))
+                    r = cfms(cL, pubof(lane - 1)[3], r);
+                if (lane < Q && (cU.x != 0.0 || cU.y != 0.0))
+                    r = cfms(cU, pubof(lane)[2], r);
+            }
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const int st = 1 << k;
+                const double2 rm = shfl_up2(r, st), rp = shfl_down2(r, st);
+                if (lane <= Q) r = cfma(tred[(2 * k + 1) * 32], rp, cfma(tred[(2 * k) * 32], rm, r));
+            }
+            if (lane <= Q) {
+                r = cmul(r, tred[10 * 32]);
+                xsup[lane] = r;
+                const double2 uo = usup[lane];
+                usup[lane] = make_double2(fma(2.0, r.x, -uo.x), fma(2.0, r.y, -uo.y));
+            }
+        }
+        __syncthreads();
+        // ---- E: super-chunk values -----------------------------------------------
+        double2 v = zero;
+        if (member) {
+            v = cfms(tax[S], xsup[q], d);
+            v = cfms(tax[2 * S], xsup[q + 1], v);
+        } else if (sup) {
+            v = xsup[qsup];
+        }
+        xv[tid] = v;
+        __syncwarp();
+        // ---- F: spike correction, CN update, fluxes -------------------------------
+        if (valid && Lp > 0) {
+            const double2 vR = (rsup >= 0) ? xsup[rsup] : xv[tid + 1];
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    double2 vi = cfms(F[(i * 4 + 2) * P], v, y[i]);
+                    vi = cfms(F[(i * 4 + 3) * P], vR, vi);
+                    u[i] = make_double2(fma(2.0, vi.x, -u[i].x), fma(2.0, vi.y, -u[i].y));
+                }
+            }
+        }
+        if (realsep) {
+            const double2 uo = usep[tid];
+            usep[tid] = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
+            if (p == 0) {
+                if (hl) hist_l[t] = v;
+                if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
+                    const double2 ts = gen ? a.kout[(size_t)(2 * j + 0) * a.kstride] : a.two_sigma;
+                    double2 o = csub(cmul(ts, v), lin);
+                    if (gen) o = cadd(o, hsum2[0]);
+                    else if (a.s02) o = cfma(a.two_c2, hsum[0], o);
+                    a.gout[(size_t)sy.out_a + a.t0 + t - 1] = o;
+                }
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
+            }
+            if (p == Pj) {
+                if (hr) hist_r[t] = v;
+                if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
+                    const double2 ts = gen ? a.kout[(size_t)(2 * j + 1) * a.kstride] : a.two_sigma;
+                    double2 o = csub(cmul(ts, v), rin);
+                    if (gen) o = cadd(o, hsum2[1]);
+                    else if (a.s02) o = cfma(a.two_c2, hsum[1], o);
+                    a.gout[(size_t)sy.out_b + a.t0 + t - 1] = o;
+                }
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
+            }
+        }
+        if (rec_u) {   // u_t of this system in local node order (streaming stores)
+            double2* row = a.urec + sy.rec + (size_t)(t - 1) * nj;
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) __stcs(row + sp + 1 + i, u[i]);
+            if (realsep) __stcs(row + sp, usep[tid]);
+        }
+        __syncwarp();
+    }
+    // ---- final state ----------------------------------------------------------
+    bool bad = false;
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < Lp) bad |= !cfinite(u[i]);
+        if ((sy.flags & SYS_WRITE_UT) && a.uT) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.uT[goff + sp + 1 + i] = u[i];
+        }
+        if (realsep) {
+            const double2 us = usep[tid];
+            bad |= !cfinite(us);
+            // the interface node belongs to the left subdomain
+            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || !(tcf & 1))) a.uT[goff + sp] = us;
+            if ((sy.flags & SYS_REC_LAST) && a.urec) a.urec[sy.rec + sp] = us;
+        }
+        if ((sy.flags & SYS_REC_LAST) && a.urec) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.urec[sy.rec + sp + 1 + i] = u[i];
+        }
+    }
+    if (bad) atomicOr(a.status, ST_NONFINITE);
+    // keep this CTA's shared memory alive until every CTA of the cluster is done
+    cl.sync();
+}
+
+// ---------------------------------------------------------------------------
 // Time-dependent potential (Eq. CNS_L with W_n = (V_n + V_{n-1})/2): the matrix
 // A_{j,n} - B_j changes every step, so each step refactors in place.  Chunk
 // thread: assemble its rows from W_n, LU, local solve and both spikes; the
@@ -1454,8 +2000,14 @@ int swr_launch_march_tdep(const FactorSet& fs, MarchArgs a, const double* V, lon
 template <int L>
 static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s, int mode) {
     const int slots = a.stage == 2 ? 2 * a.levels + 3 + 4 * L : (a.stage == 1 ? 2 * a.levels + 3 : 0);
-    const int smem = swr_march_smem_bytes(a.T, a.G, slots);
+    int smem = swr_march_smem_bytes(a.T, a.G, slots);
     void (*kern)(const MarchArgs) = a.kap ? k_march_static<L, 0, true> : k_march_static<L, 0>;
+    // a system spread over a cluster: the two-level separator solve (one cluster
+    // barrier per step) when its data was factored
+    if (a.C > 1 && mode == 0 && a.stage == 0 && a.fstride == 0 && a.tl_pcr && (a.T & 31) == 0) {
+        kern = a.kap ? k_march_tl<L, true> : k_march_tl<L, false>;
+        smem = swr_march_tl_smem_bytes(a.T);
+    }
     if constexpr (L <= 8) {   // record and gradient modes exist for L <= 8
         if (mode == 1) kern = k_march_static<L, 1>;
         if (mode == 2) kern = k_march_static<L, 2>;
@@ -1506,6 +2058,10 @@ int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t
     a.fac = fs.fac;
     a.sep = fs.sep;
     a.pcr = fs.pcr;
+    a.tl_pcr = fs.tl_ok ? fs.tl_pcr : nullptr;
+    a.tl_aux = fs.tl_aux;
+    a.tl_red = fs.tl_red;
+    if (!a.two_level) a.tl_pcr = nullptr;
     if (mode != 0 && (fs.L > 8 || fs.nsteps > 1 || a.s02)) return -2;   // adjoint modes: L <= 8, V(x), Robin
     switch (fs.L) {
         case 4: return launch_march_t<4>(a, ngroups, s, mode);

@@ -41,6 +41,29 @@ class swr_desc(ctypes.Structure):
     ]
 
 
+class swr_tuning(ctypes.Structure):
+    """Execution choices of a plan (include/swr.h); zero-filled means the defaults."""
+    _fields_ = [
+        ("chunk_L", ctypes.c_int32), ("autotune", ctypes.c_int32),
+        ("toeplitz_fft", ctypes.c_int32), ("superpose", ctypes.c_int32),
+        ("long_march", ctypes.c_int32), ("graph", ctypes.c_int32),
+        ("tdep_precomp", ctypes.c_int32), ("two_level", ctypes.c_int32),
+        ("debug", ctypes.c_int32),
+    ]
+
+
+def make_tuning(tuning):
+    """A swr_tuning from a dict of field -> int (None: NULL, the library defaults)."""
+    if tuning is None:
+        return None
+    t = swr_tuning()
+    for k, v in tuning.items():
+        if k not in dict(swr_tuning._fields_):
+            raise KeyError(f"unknown tuning field {k}")
+        setattr(t, k, int(v))
+    return t
+
+
 class swr_info(ctypes.Structure):
     _fields_ = [
         ("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
@@ -65,6 +88,7 @@ class swr_stats(ctypes.Structure):
         ("nl_march_launches", ctypes.c_int64), ("nl_march_ms", ctypes.c_double),
         ("superposed", ctypes.c_int32), ("toeplitz_fft_length", ctypes.c_int32),
         ("causal_sweeps", ctypes.c_int32), ("causal_window", ctypes.c_int32),
+        ("two_level_launches", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -91,6 +115,12 @@ def lib():
         L.swr_plan.argtypes = [ctypes.POINTER(swr_desc), ctypes.POINTER(vp), vp]
         L.swr_plan_batch.argtypes = [ctypes.POINTER(swr_desc), ctypes.c_int32,
                                      ctypes.POINTER(vp), vp]
+        L.swr_plan_ex.argtypes = [ctypes.POINTER(swr_desc), ctypes.POINTER(swr_tuning),
+                                  ctypes.POINTER(vp), vp]
+        L.swr_plan_batch_ex.argtypes = [ctypes.POINTER(swr_desc), ctypes.c_int32,
+                                        ctypes.POINTER(swr_tuning), ctypes.POINTER(vp), vp]
+        L.swr_tuning_defaults.argtypes = [ctypes.POINTER(swr_tuning)]
+        L.swr_tuning_defaults.restype = None
         L.swr_build_interface.argtypes = [vp, dp, dp]
         L.swr_solve.argtypes = [vp, dp, ctypes.c_int32, dp, ctypes.POINTER(swr_info)]
         L.swr_apply_R.argtypes = [vp, dp, dp]
@@ -112,7 +142,8 @@ def lib():
         L.swr_kernel_launch_count.restype = ctypes.c_int64
         L.swr_status_string.argtypes = [ctypes.c_int]
         L.swr_status_string.restype = ctypes.c_char_p
-        for f in ("swr_plan", "swr_plan_batch", "swr_build_interface", "swr_solve", "swr_apply_R",
+        for f in ("swr_plan", "swr_plan_batch", "swr_plan_ex", "swr_plan_batch_ex",
+                  "swr_build_interface", "swr_solve", "swr_apply_R",
                   "swr_apply_interface", "swr_get_interface", "swr_apply_precond", "swr_adjoint",
                   "swr_get_stats", "swr_causal_solve_noalloc", "swr_misfit", "swr_fp64_peak",
                   "swr_test_wait_hook"):
@@ -184,7 +215,7 @@ class Plan:
     def __init__(self, *, nx, a0, b0, nt, dt, nsub, node_off=None, vkind=SWR_V_STATIC,
                  tc=SWR_TC_ROBIN, p=0j, solver=SWR_SOLVER_GMRES, restart=30, maxit=2000,
                  tol_abs=1e-10, precond=SWR_PC_NONE, nl_maxit=50, nl_tol=1e-13, nl_coef=1.0,
-                 pc_sweeps=-1, stream=None):
+                 pc_sweeps=-1, stream=None, tuning=None):
         d = swr_desc()
         d.nx, d.a0, d.b0, d.nt, d.dt, d.nsub = nx, a0, b0, nt, dt, nsub
         self._off = None
@@ -203,7 +234,9 @@ class Plan:
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = ctypes.c_void_p()
-        _check(lib().swr_plan(ctypes.byref(d), ctypes.byref(h), ctypes.c_void_p(stream.cuda_stream)),
+        tu = make_tuning(tuning)
+        _check(lib().swr_plan_ex(ctypes.byref(d), ctypes.byref(tu) if tu is not None else None,
+                                 ctypes.byref(h), ctypes.c_void_p(stream.cuda_stream)),
                "swr_plan")
         self.handle = h
 
@@ -317,7 +350,7 @@ class BatchPlan(Plan):
 
     def __init__(self, instances, *, dt, tc=SWR_TC_ROBIN, p=0j, solver=SWR_SOLVER_GMRES,
                  restart=30, maxit=2000, tol_abs=1e-10, precond=SWR_PC_NONE, pc_sweeps=-1,
-                 stream=None):
+                 stream=None, tuning=None):
         count = len(instances)
         descs = (swr_desc * count)()
         self._offs = []
@@ -348,8 +381,10 @@ class BatchPlan(Plan):
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = ctypes.c_void_p()
-        _check(lib().swr_plan_batch(descs, count, ctypes.byref(h),
-                                    ctypes.c_void_p(stream.cuda_stream)), "swr_plan_batch")
+        tu = make_tuning(tuning)
+        _check(lib().swr_plan_batch_ex(descs, count, ctypes.byref(tu) if tu is not None else None,
+                                       ctypes.byref(h), ctypes.c_void_p(stream.cuda_stream)),
+               "swr_plan_batch")
         self.handle = h
 
     @property

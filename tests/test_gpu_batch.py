@@ -52,12 +52,8 @@ def batch_plan(wls, autotune=True, **kw):
     insts = [dict(nx=w.nx, a0=w.a0, b0=w.b0, nt=w.nt, nsub=w.nsub, node_off=w.off) for w in wls]
     kw.setdefault("p", wls[0].sigma)
     kw.setdefault("tc", wls[0].tc)
-    if not autotune:
-        os.environ["SWR_AUTOTUNE"] = "0"
-    try:
-        plan = swr.BatchPlan(insts, dt=wls[0].dt, **kw)
-    finally:
-        os.environ.pop("SWR_AUTOTUNE", None)
+    plan = swr.BatchPlan(insts, dt=wls[0].dt, tuning=None if autotune else {"autotune": -1},
+                         **kw)
     V = torch.tensor(np.concatenate([w.V for w in wls]), dtype=torch.float64, device="cuda")
     u0 = torch.tensor(np.concatenate([w.u0 for w in wls]), dtype=torch.complex128, device="cuda")
     plan.build_interface(V, u0)

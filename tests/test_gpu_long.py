@@ -87,14 +87,14 @@ def test_long_build_and_R_match_oracle(case, tc):
     assert rel(go.cpu().numpy(), O.apply_R(P, g)) < TOL_MARCH
 
 
-@pytest.mark.parametrize("superpose", ["1", "0"])
+@pytest.mark.parametrize("superpose", [1, 0])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_long_solve_reproduces_monodomain(case, superpose, monkeypatch):
+def test_long_solve_reproduces_monodomain(case, superpose):
     from paper_1503_02564_gb300 import swr
-    monkeypatch.setenv("SWR_SUPERPOSE", superpose)
     wl = CASES[case]()
-    plan = gpu_plan(wl, O.TC_ROBIN, precond=swr.SWR_PC_CAUSAL, restart=60, tol_abs=1e-11)
-    assert plan.get_stats()["superposed"] == int(superpose)
+    plan = gpu_plan(wl, O.TC_ROBIN, precond=swr.SWR_PC_CAUSAL, restart=60, tol_abs=1e-11,
+                    tuning={"superpose": 0 if superpose else -1})
+    assert plan.get_stats()["superposed"] == superpose
     g = torch.zeros(plan.n_interface, dtype=torch.complex128, device="cuda")
     uT = torch.zeros(wl.nx, dtype=torch.complex128, device="cuda")
     info = plan.solve(g, False, uT)
@@ -131,8 +131,8 @@ def rel_to_summands(a, ref, mag):
 
 @pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02, O.TC_S14])
 @pytest.mark.parametrize("nx,nsub", [(20001, 2), (4001, 16), (130001, 2)])
-def test_forced_grid_march_matches_cluster_march(nx, nsub, tc, monkeypatch):
-    """SWR_LONG_MARCH=1 runs the grid-wide march where the cluster march also applies:
+def test_forced_grid_march_matches_cluster_march(nx, nsub, tc):
+    """tuning.long_march = 1 runs the grid-wide march where the cluster march also applies:
     the two agree to rounding (bitwise when both take 16-node chunks: the arithmetic per
     node is the same), and both match the oracle's extended-precision build
     (oracle.build_ext, every march and flux in long double) to 1e-10 relative to the
@@ -143,9 +143,8 @@ def test_forced_grid_march_matches_cluster_march(nx, nsub, tc, monkeypatch):
     of d (no such cancellation) is held to 1e-10 as well."""
     wl = W.config2(nsub=nsub, nx=nx, nt=12)
     out = []
-    for force in ("0", "1"):
-        monkeypatch.setenv("SWR_LONG_MARCH", force)
-        plan = gpu_plan(wl, tc)
+    for force in (0, 1):
+        plan = gpu_plan(wl, tc, tuning={"long_march": force})
         d = torch.zeros(plan.n_interface, dtype=torch.complex128, device="cuda")
         cols = torch.zeros(4 * plan.nsub * plan.nt, dtype=torch.complex128, device="cuda")
         plan.get_interface(d, cols)

@@ -7,7 +7,6 @@ IEEE binary64; the GPU contracts multiply-adds and reorders sums, the oracle
 does not, which with the condition numbers here (about 2 dt / h^2 <= 1e4)
 leaves three orders of magnitude of margin.
 """
-import os
 
 import numpy as np
 import pytest
@@ -42,18 +41,15 @@ def problem(wl):
                      vkind=wl.vkind, tc=wl.tc, sigma=wl.sigma, nl_coef=wl.nl_coef)
 
 
-def gpu_plan(wl, chunk=None, autotune=True, **kw):
+def gpu_plan(wl, chunk=None, autotune=True, tuning=None, **kw):
     from paper_1503_02564_gb300 import swr
+    tuning = dict(tuning or {})
     if chunk is not None:
-        os.environ["SWR_CHUNK_L"] = str(chunk)
+        tuning["chunk_L"] = chunk
     if not autotune:
-        os.environ["SWR_AUTOTUNE"] = "0"
-    try:
-        plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
-                        node_off=wl.off, p=wl.sigma, vkind=wl.vkind, **kw)
-    finally:
-        os.environ.pop("SWR_CHUNK_L", None)
-        os.environ.pop("SWR_AUTOTUNE", None)
+        tuning["autotune"] = -1
+    plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
+                    node_off=wl.off, p=wl.sigma, vkind=wl.vkind, tuning=tuning, **kw)
     V = torch.tensor(wl.V, dtype=torch.float64, device="cuda")
     u0 = torch.tensor(wl.u0, dtype=torch.complex128, device="cuda")
     plan.build_interface(V, u0)
@@ -109,7 +105,7 @@ def test_build_interface_matches_oracle(case, chunk):
 @pytest.mark.parametrize("case", ["config2_N16_small", "ragged_tiny", "two_long"])
 def test_autotuned_shapes_match_modelled_shapes(case):
     """The measured launch shapes (first build) and the modelled ones
-    (SWR_AUTOTUNE=0) partition the same systems differently; both give the
+    (tuning.autotune = -1) partition the same systems differently; both give the
     oracle's d and columns, and agree with each other to rounding, also after
     a second build on the tuned plan."""
     wl = CASES[case]()
@@ -289,13 +285,9 @@ def test_repeated_builds_replay_the_captured_build(case):
 
 def _solve_with(wl, superpose, **kw):
     from paper_1503_02564_gb300 import swr
-    os.environ["SWR_SUPERPOSE"] = "1" if superpose else "0"
     if "tc" in kw:
         wl.tc = kw["tc"]
-    try:
-        plan = gpu_plan(wl, **kw)
-    finally:
-        os.environ.pop("SWR_SUPERPOSE", None)
+    plan = gpu_plan(wl, tuning={"superpose": 0 if superpose else -1}, **kw)
     assert plan.get_stats()["superposed"] == (1 if superpose else 0)
     g, uT, info = _solve(plan, wl)
     plan.destroy()
@@ -329,11 +321,7 @@ def test_superposed_final_state_null_uT_and_unconverged():
     wl = CASES["config2_N16_small"]()
     out = []
     for sp in (True, False):
-        os.environ["SWR_SUPERPOSE"] = "1" if sp else "0"
-        try:
-            plan = gpu_plan(wl, maxit=3, restart=30)
-        finally:
-            os.environ.pop("SWR_SUPERPOSE", None)
+        plan = gpu_plan(wl, maxit=3, restart=30, tuning={"superpose": 0 if sp else -1})
         info = plan.solve(None, False, None, allow_not_converged=True)
         assert info["status"] == swr.SWR_ERR_NOT_CONVERGED
         uT = torch.zeros(wl.nx, dtype=torch.complex128, device="cuda")
@@ -352,11 +340,7 @@ def test_toeplitz_apply_fft_and_direct_match_oracle(case, fft):
     oracle's (I - L) x; nt = 1500 takes the largest transform (4096)."""
     from paper_1503_02564_gb300 import swr
     wl = W.config1(nx=241, nt=1500, nsub=4) if case == "long_nt" else CASES[case]()
-    os.environ["SWR_TOEPLITZ_FFT"] = "1" if fft else "0"
-    try:
-        plan = gpu_plan(wl)
-    finally:
-        os.environ.pop("SWR_TOEPLITZ_FFT", None)
+    plan = gpu_plan(wl, tuning={"toeplitz_fft": 0 if fft else -1})
     M = plan.get_stats()["toeplitz_fft_length"]
     if fft:
         assert M >= 2 * wl.nt - 1 and M & (M - 1) == 0 and M < 4 * wl.nt

@@ -4,7 +4,6 @@ sqrt(2/dt).  The march carries the history sums at the subdomain ends; the
 interface algebra (Toeplitz columns, causal preconditioner, GMRES) is the same
 as for Robin.  Tolerances as for Robin: 1e-10 per march output, 1e-9 for the
 converged solution."""
-import os
 
 import numpy as np
 import pytest
@@ -46,13 +45,9 @@ def problem(wl):
 
 def gpu_plan(wl, chunk=None, **kw):
     from paper_1503_02564_gb300 import swr
-    if chunk is not None:
-        os.environ["SWR_CHUNK_L"] = str(chunk)
-    try:
-        plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
-                        node_off=wl.off, tc=swr.SWR_TC_S02, vkind=wl.vkind, **kw)
-    finally:
-        os.environ.pop("SWR_CHUNK_L", None)
+    plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
+                    node_off=wl.off, tc=swr.SWR_TC_S02, vkind=wl.vkind,
+                    tuning=None if chunk is None else {"chunk_L": chunk}, **kw)
     V = torch.tensor(np.ascontiguousarray(wl.V).ravel(), dtype=torch.float64, device="cuda")
     u0 = torch.tensor(wl.u0, dtype=torch.complex128, device="cuda")
     plan.build_interface(V, u0)

@@ -4,7 +4,6 @@ convolution of the end trace with a kernel formed per end from the potential at 
 node and its normal derivative.  Against the oracle, which writes the operators out
 from their printed definitions as weight matrices: d, the Toeplitz first columns and
 R g per march output (1e-10), converged SWR against the monodomain solution (1e-9)."""
-import os
 
 import numpy as np
 import pytest
@@ -42,13 +41,9 @@ def problem(wl, tc):
 
 def gpu_plan(wl, tc, chunk=None, **kw):
     from paper_1503_02564_gb300 import swr
-    if chunk is not None:
-        os.environ["SWR_CHUNK_L"] = str(chunk)
-    try:
-        plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
-                        node_off=wl.off, tc=tc, **kw)
-    finally:
-        os.environ.pop("SWR_CHUNK_L", None)
+    plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
+                    node_off=wl.off, tc=tc, tuning=None if chunk is None else {"chunk_L": chunk},
+                    **kw)
     plan.build_interface(torch.tensor(wl.V, dtype=torch.float64, device="cuda"),
                          torch.tensor(wl.u0, dtype=torch.complex128, device="cuda"))
     return plan

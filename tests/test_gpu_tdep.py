@@ -2,7 +2,6 @@
 step's factors computed once per build and streamed, and the per-step
 refactorising march), matrix-free GMRES of Algorithm 2 preconditioned by
 P = I - L_0."""
-import os
 
 import numpy as np
 import pytest
@@ -37,19 +36,20 @@ def problem(wl):
                      vkind=wl.vkind, tc=wl.tc, sigma=wl.sigma, nl_coef=wl.nl_coef)
 
 
-def gpu_plan(wl, streamed=None, **kw):
-    """streamed: True / False selects the V(t,x) march variant (None: default)."""
+def gpu_plan(wl, streamed=None, chunk=None, **kw):
+    """streamed: True / False selects the V(t,x) march variant (None: default);
+    chunk: a fixed chunk length."""
     from paper_1503_02564_gb300 import swr
+    tuning = {}
+    if streamed is not None:
+        tuning["tdep_precomp"] = 0 if streamed else -1
+    if chunk is not None:
+        tuning["chunk_L"] = chunk
     plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
-                    node_off=wl.off, p=wl.sigma, vkind=wl.vkind, **kw)
+                    node_off=wl.off, p=wl.sigma, vkind=wl.vkind, tuning=tuning, **kw)
     V = torch.tensor(np.ascontiguousarray(wl.V).ravel(), dtype=torch.float64, device="cuda")
     u0 = torch.tensor(wl.u0, dtype=torch.complex128, device="cuda")
-    if streamed is not None:
-        os.environ["SWR_TDEP_PRECOMP"] = "1" if streamed else "0"
-    try:
-        plan.build_interface(V, u0)
-    finally:
-        os.environ.pop("SWR_TDEP_PRECOMP", None)
+    plan.build_interface(V, u0)
     if streamed is not None and wl.vkind == swr.SWR_V_TIME:
         want = swr.MARCH_TDEP_STREAMED if streamed else swr.MARCH_TDEP_REFACTOR
         assert plan.get_stats()["march_variant"] == want
@@ -91,11 +91,7 @@ def test_tdep_streamed_long_subdomains_match_oracle(chunk):
     factors are staged in shared memory in full, or only the separator part when
     the chunk factors do not fit (chunk 8 and 16 here), and the result is the same."""
     wl = W.config4(nsub=4, nx=60001, nt=12)
-    os.environ["SWR_CHUNK_L"] = str(chunk)
-    try:
-        plan = gpu_plan(wl, True)
-    finally:
-        os.environ.pop("SWR_CHUNK_L", None)
+    plan = gpu_plan(wl, True, chunk=chunk)
     g = W.random_interface(wl.nblk, wl.nt, 33)
     gi = torch.tensor(g.ravel(), dtype=torch.complex128, device="cuda")
     go = torch.zeros_like(gi)

@@ -47,6 +47,10 @@ def ragged(L):
     for n in sizes:
         off.append(off[-1] + n - 1)
     wl.off = np.array(off, dtype=np.int32)
+    # initial data of size one at every interface (the seeded packets sit in (-30, 30),
+    # and at an interface outside them d would be an exponentially small tail)
+    x = wl.x
+    wl.u0 = np.exp(2j * x) * (1.0 + 0.3 * np.sin(0.7 * x))
     return wl
 
 

@@ -91,6 +91,9 @@ def parse():
                     help="nodes of the tcs workload on (-21, 21): 84001 is dx = 5e-4; the "
                          "paper's dx = 1e-5 (4200001 nodes) needs 2.1M-node subdomains at N = 2, "
                          "beyond the 69632-node subdomain limit of the march")
+    ap.add_argument("--tune", default="",
+                    help="execution choices of the plans (swr_tuning fields), e.g. "
+                         "'autotune=-1,chunk_L=12' (profiling with a fixed launch shape)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true",
                     help="scaling workload: skip the sub-records of the other workloads "
@@ -99,6 +102,17 @@ def parse():
     ap.add_argument("--sub-warmup", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
+
+
+def tuning_of(args):
+    """The --tune option as a dict for swr.Plan(tuning=...) (None: library defaults)."""
+    if not getattr(args, "tune", ""):
+        return None
+    out = {}
+    for kv in args.tune.split(","):
+        k, v = kv.split("=")
+        out[k.strip()] = int(v)
+    return out
 
 
 def dist_env():
@@ -911,19 +925,22 @@ def run_workload(args, workload, rank, world, local, dev, peak):
             plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
                             node_off=wl.off, p=wl.sigma, vkind=swr.SWR_V_NONLINEAR,
                             solver=swr.SWR_SOLVER_FIXED_POINT, maxit=200, tol_abs=1e-10,
-                            precond=swr.SWR_PC_MEAN_POTENTIAL, nl_tol=1e-13, nl_maxit=50)
+                            precond=swr.SWR_PC_MEAN_POTENTIAL, nl_tol=1e-13, nl_maxit=50,
+                            tuning=tuning_of(args))
         elif timedep:
             wl = W.config4(nsub=N, nt=args.nt) if args.nt > 0 else W.config4(nsub=N)
             plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
                             node_off=wl.off, p=wl.sigma, vkind=swr.SWR_V_TIME, restart=60,
-                            maxit=400, tol_abs=1e-10, precond=swr.SWR_PC_MEAN_POTENTIAL)
+                            maxit=400, tol_abs=1e-10, precond=swr.SWR_PC_MEAN_POTENTIAL,
+                            tuning=tuning_of(args))
         else:
             wl = W.config2(nsub=N, nt=args.nt) if args.nt > 0 else W.config2(nsub=N)
             if args.tc == "s02":
                 wl.tc = swr.SWR_TC_S02
             plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=N,
                             node_off=wl.off, p=wl.sigma, tc=wl.tc, restart=30, maxit=2000,
-                            tol_abs=1e-10, precond=precond, pc_sweeps=args.pc_sweeps)
+                            tol_abs=1e-10, precond=precond, pc_sweeps=args.pc_sweeps,
+                            tuning=tuning_of(args))
         V = torch.tensor(np.ascontiguousarray(wl.V).ravel(), dtype=torch.float64, device=dev)
         u0 = torch.tensor(wl.u0, dtype=torch.complex128, device=dev)
         g = torch.zeros(plan.n_interface, dtype=torch.complex128, device=dev)

@@ -156,6 +156,7 @@ struct swr_plan_s {
     bool built = false;
     bool have_L0 = false;
     int two_level = 1;             // two-level separator solve for cluster-spread systems
+    double2* d_hseg = nullptr;     // S_0^2 adjoint: segment marches' end traces [2][N][2][nt+1]
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double t_build_ms = 0.0;
     // per-launch timing ring: kind 0 = march, 1 = Toeplitz apply, 2 = P^{-1}
@@ -322,6 +323,8 @@ struct SegArgs {
     int mode = 0;             // 0 march, 1 record v, 2 accumulate the potential form
     int t0 = 0;               // first step of the segment within the flux blocks
     long long gstride = 0;    // flux block stride (0: the launch's own step count)
+    double2* hist = nullptr;  // S_0^2: end traces over the whole time axis [N][2][nt+1]
+    int ht0 = 0;              // absolute step before the segment's first step
     double2* vrec = nullptr;
     const double2* vfwd = nullptr;
     double *gint = nullptr, *gl = nullptr, *gr = nullptr;
@@ -522,6 +525,11 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
         a.hist = p->d_s02hist;
         a.c2_ik = p->c2_ik;
         a.two_c2 = make_double2(2.0 * p->c2.x, 2.0 * p->c2.y);
+        if (seg.hist) {   // a segment of the adjoint's marches: traces over the whole axis
+            a.hist = seg.hist;
+            a.hstride = p->nt + 1;
+            a.ht0 = seg.ht0;
+        }
     }
     const double kappa = 2.0 / p->d.dt * (p->h / 6.0);
     if (p->long_march && kind == MK_STATIC) {
@@ -1400,7 +1408,7 @@ void swr_destroy(swr_plan_t p) {
         cudaFree(k.d_start);
         cudaFree(k.d_rag);
     }
-    cudaFree(p->d_ckpt); cudaFree(p->d_slab); cudaFree(p->d_ya); cudaFree(p->d_yb);
+    cudaFree(p->d_ckpt); cudaFree(p->d_slab); cudaFree(p->d_ya); cudaFree(p->d_yb); cudaFree(p->d_hseg);
     cudaFree(p->d_dy); cudaFree(p->d_gy); cudaFree(p->d_gint); cudaFree(p->d_gl);
     cudaFree(p->d_gr); cudaFree(p->d_part); cudaFree(p->d_sys_seg);
     cudaFree(p->d_mono); cudaFree(p->d_mdg); cudaFree(p->d_mod); cudaFree(p->d_sys_mono);
@@ -2205,8 +2213,7 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
     // condition and solver); the linear one runs the adjoint interface solve
     const bool nl = (p->d.vkind == SWR_V_NONLINEAR);
     if (p->batched || p->long_march ||
-        (!nl && (p->d.vkind != SWR_V_STATIC || p->d.tc != SWR_TC_ROBIN ||
-                               p->d.solver != SWR_SOLVER_GMRES)))
+        (!nl && (p->d.vkind != SWR_V_STATIC || p->d.tc > SWR_TC_S02)))
         return SWR_ERR_UNSUPPORTED;
     cudaStream_t s = p->s;
     const int nt = p->nt, nx = p->nx, N = p->N;
@@ -2222,6 +2229,11 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
         if ((st = dalloc(&p->d_ckpt, (size_t)C * nx))) return st;
         if ((st = dalloc(&p->d_slab, (size_t)K * nx))) return st;
         p->adj_K = K;
+    }
+    const bool s02 = (p->d.tc == SWR_TC_S02);
+    if (s02 && !p->d_hseg) {
+        // the segments' end traces over the whole time axis: forward, adjoint
+        if ((st = dalloc(&p->d_hseg, (size_t)2 * N * 2 * (nt + 1)))) return st;
     }
     if (!p->d_ya) {
         if ((st = dalloc(&p->d_ya, nx)) || (st = dalloc(&p->d_yb, nx)) ||
@@ -2272,6 +2284,10 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
         sa.mode = mode;
         sa.t0 = t0;
         sa.gstride = nt;
+        if (s02) {   // forward traces for modes 0 and 1, the adjoint's for mode 2
+            sa.hist = p->d_hseg + (mode == 2 ? (size_t)N * 2 * (nt + 1) : 0);
+            sa.ht0 = t0;
+        }
         sa.vrec = p->d_slab;
         sa.vfwd = p->d_slab;
         sa.gint = p->d_gint;

@@ -224,7 +224,10 @@ struct MarchArgs {
     // the history b_n = c2 sum_{s<n} beta_{n-s} v_s enters the end rows and the fluxes.
     int s02;
     const double* beta;   // [nt+1]
-    double2* hist;        // [nsys][2][nt+1] end traces v_0..v_nt (v_0 = u0 at the end)
+    double2* hist;        // [nsys][2][hstride] end traces v_0..v_nt (v_0 = u0 at the end)
+    int hstride;          // entries per trace (0: nt + 1)
+    int ht0;              // absolute step before this launch's step 1: a segment march
+                          // continues the traces that earlier segments wrote (0: v_0 = u0)
     double2 c2_ik;        // c2 / (i kappa)
     double2 two_c2;       // 2 c2
     double2 two_sigma;    // 2 p (Robin): 2 S-tilde v = 2 p v

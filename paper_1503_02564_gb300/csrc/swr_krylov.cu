@@ -784,39 +784,38 @@ __device__ __forceinline__ void store_release(int* p, int v) {
 // Wait until the neighbours of interface k (global index; hl, hr: they exist in
 // its instance) have reached `target`; returns false (after raising the abort
 // flag) on timeout or when another CTA aborted.
+// The polls: the first kSpinPolls re-read the counter at once (a hand-off usually
+// lands within a few L2 round trips), later ones back off; the abort flag, a second
+// L2 round trip, is looked at only every 32nd poll.
+constexpr int kSpinPolls = 32;
+
+__device__ __forceinline__ bool poll_until(const int* cnt, int target, int* abortf, int* status,
+                                           long long lim) {
+    long long polls = 0;
+    while (load_acquire(cnt) < target) {
+        ++polls;
+        if ((polls & 31) == 0 && load_acquire(abortf) != 0) return false;
+        if (polls > lim) {
+            atomicOr(status, ST_TIMEOUT);
+            store_release(abortf, 1);
+            return false;
+        }
+        if (polls > kSpinPolls) __nanosleep(64);
+    }
+    return true;
+}
+
 __device__ bool wait_neighbours(int k, bool hl, bool hr, int target, const int* progress,
                                 int* abortf, int* status, long long lim) {
-    long long polls = 0;
-    for (int side = 0; side < 2; ++side) {
-        const int nb = (side == 0) ? k - 1 : k + 1;
-        if ((side == 0 && !hl) || (side == 1 && !hr)) continue;
-        while (load_acquire(progress + nb) < target) {
-            if (load_acquire(abortf) != 0) return false;
-            if (++polls > lim) {
-                atomicOr(status, ST_TIMEOUT);
-                store_release(abortf, 1);
-                return false;
-            }
-            __nanosleep(64);
-        }
-    }
+    if (hl && !poll_until(progress + k - 1, target, abortf, status, lim)) return false;
+    if (hr && !poll_until(progress + k + 1, target, abortf, status, lim)) return false;
     return true;
 }
 
 // Wait until interface nb has reached `target` (one lane per interface waited on).
 __device__ bool wait_one(int nb, int target, const int* progress, int* abortf, int* status,
                          long long lim) {
-    long long polls = 0;
-    while (load_acquire(progress + nb) < target) {
-        if (load_acquire(abortf) != 0) return false;
-        if (++polls > lim) {
-            atomicOr(status, ST_TIMEOUT);
-            store_release(abortf, 1);
-            return false;
-        }
-        __nanosleep(64);
-    }
-    return true;
+    return poll_until(progress + nb, target, abortf, status, lim);
 }
 
 // Rows of the inverse of the lag-0 system.  With z_k = (r_k, l_{k+1}) the values
@@ -1073,7 +1072,9 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         }
     }
     // history sums of step m for this interface, lags >= 2 (lane 0; waits on the warps)
-    auto hist_ge2 = [&](int m, double2& h0, double2& h1, double2& h2, double2& h3) -> bool {
+    // xm2: x_{m-2} of the sources when the caller has loaded them (else NULL)
+    auto hist_ge2 = [&](int m, const double2* xm2, double2& h0, double2& h1, double2& h2,
+                        double2& h3) -> bool {
         bool ok = true;
 #pragma unroll
         for (int e = 0; e < 4; ++e) ok = ok && cta_wait_ge(&s_hdone[e], m, &s_stop);
@@ -1082,7 +1083,8 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             h[e] = hp[m % 3][e];
-            if (m >= 2 && hs[e]) h[e] = cfma(c2e[e], __ldcg(xs2[e] + m - 2), h[e]);
+            if (m >= 2 && hs[e])
+                h[e] = cfma(c2e[e], xm2 ? xm2[e] : __ldcg(xs2[e] + m - 2), h[e]);
         }
         h0 = h[0];
         h1 = h[1];
@@ -1137,11 +1139,17 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             if (waits) ok = wait_one(kg + d, n + 1, progress, abortf, status, lim);
             ok = __all_sync(0xffffffffu, ok);                  // x_{<n}, P_n visible
             if (!ok) break;
-            // the next right-hand side's data, off the critical path
-            double2 yn1a = zero, yn1b = zero;
+            // the next right-hand side's data and its lag-2 terms (x_{n-1} of the four
+            // sources), loaded now, off the critical path
+            double2 yn1a = zero, yn1b = zero, x2[4] = {zero, zero, zero, zero};
             if (lane == 0 && n + 1 < nt) {
                 yn1a = y[(size_t)(2 * k) * nt + n + 1];
                 yn1b = y[(size_t)(2 * k + 1) * nt + n + 1];
+                if (n >= 1) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (hs[e]) x2[e] = __ldcg(xs2[e] + n - 1);
+                }
             }
             double2 t1 = zero, t2 = zero;
             if (inwin) {
@@ -1164,7 +1172,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                 cta_store_release(&s_xown, n + 1);
                 if (n + 1 < nt) {
                     double2 q0, q1, q2, q3;
-                    if (hist_ge2(n + 1, q0, q1, q2, q3)) {
+                    if (hist_ge2(n + 1, x2, q0, q1, q2, q3)) {
                         double2* P = xsw + (size_t)((n + 1) & 1) * 2 * nif_all + 2 * kg;
                         P[0] = cadd(yn1a, cadd(q0, q1));
                         P[1] = cadd(yn1b, cadd(q2, q3));
@@ -1210,7 +1218,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             if (solver) {
                 // history of step n: lags >= 2 (the warps' sums and lag 2) + lag 1
                 double2 h[4];
-                if (!hist_ge2(n, h[0], h[1], h[2], h[3])) {
+                if (!hist_ge2(n, nullptr, h[0], h[1], h[2], h[3])) {
                     go = 0;
                     fail_local();
                 } else {

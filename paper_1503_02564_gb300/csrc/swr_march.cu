@@ -598,8 +598,9 @@ int swr_launch_factor_tl(FactorSet& fs, int N, const int* d_loff, const double2*
                          const double2* od, int* status, cudaStream_t s) {
     fs.tl_ok = false;
     if (fs.nsteps != 1 || fs.P + 1 > kTlMaxSep || !fs.tl_pcr) return -2;
-    k_factor_two_level<<<N, 1024, 0, s>>>(N, fs.P, d_loff, dg, od, fs.sub_P, fs.sep_pos,
-                                           fs.tips, fs.tl_pcr, fs.tl_aux, fs.tl_red, status);
+    const int threads = std::max(32, ((fs.P + 1 + 31) / 32) * 32);   // one per separator
+    k_factor_two_level<<<N, threads, 0, s>>>(N, fs.P, d_loff, dg, od, fs.sub_P, fs.sep_pos,
+                                              fs.tips, fs.tl_pcr, fs.tl_aux, fs.tl_red, status);
     swr_count_launch(1);
     if (cudaGetLastError() != cudaSuccess) return -1;
     fs.tl_ok = true;
@@ -933,12 +934,15 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     // S_0^2: the end traces start with v_0 = u_0 at the end
     const bool hl = a.s02 && realsep && p == 0 && (tcf & 1);
     const bool hr = a.s02 && realsep && p == Pj && (tcf & 2);
-    double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * (nt + 1) : nullptr;
-    double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * (nt + 1) : nullptr;
+    // end traces v_0..v_{nt} at absolute steps: a launch marching a segment of the time
+    // axis (steps ht0 + 1 ..) extends the traces the earlier segments left
+    const int hst = a.hstride > 0 ? a.hstride : nt + 1, ht0 = a.ht0;
+    double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * hst : nullptr;
+    double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * hst : nullptr;
     // per-end kernels: h_0 = rho v_0; the flux weight on v_n is kout[0]
     constexpr bool gen = GEN;
-    if (hl) hist_l[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 0], a.u0[goff + sp]) : a.u0[goff + sp]);
-    if (hr) hist_r[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 1], a.u0[goff + sp]) : a.u0[goff + sp]);
+    if (hl && ht0 == 0) hist_l[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 0], a.u0[goff + sp]) : a.u0[goff + sp]);
+    if (hr && ht0 == 0) hist_r[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 1], a.u0[goff + sp]) : a.u0[goff + sp]);
     const int hs_l = (C == 1) ? 2 * g : 0, hs_r = hs_l + 1;
     if (stage > 0) {   // step 1's factors
         issue_fa(F);
@@ -1020,17 +1024,17 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     const int gs = ragged ? a.rag[re0 + (e >> 1)].x : blockIdx.x * G + (e >> 1);
                     const int side = e & 1;
                     if (gs < a.nsys && (a.sub_tc[a.sys[gs].sub] & (1 << side))) {
-                        const double2* hh = a.hist + ((size_t)gs * 2 + side) * (nt + 1);
+                        const double2* hh = a.hist + ((size_t)gs * 2 + side) * hst;
                         if (gen) {
                             const size_t ke = (size_t)(2 * a.sys[gs].sub + side) * a.kstride;
                             double2 o1, o2;
-                            conv_history2(a.kap + ke, a.kout + ke, hh, t, lane, o1, o2);
+                            conv_history2(a.kap + ke, a.kout + ke, hh, ht0 + t, lane, o1, o2);
                             if (lane == 0) {
                                 hsum[e] = o1;
                                 hsum2[e] = o2;
                             }
                         } else {
-                            const double2 hsv = s02_history(a.beta, hh, t, lane);
+                            const double2 hsv = s02_history(a.beta, hh, ht0 + t, lane);
                             if (lane == 0) hsum[e] = hsv;
                         }
                     }
@@ -1043,13 +1047,13 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     if (gen) {
                         const size_t ke = (size_t)(2 * se + 0) * a.kstride;
                         double2 o1, o2;
-                        conv_history2(a.kap + ke, a.kout + ke, hist_l, t, lane, o1, o2);
+                        conv_history2(a.kap + ke, a.kout + ke, hist_l, ht0 + t, lane, o1, o2);
                         if (lane == 0) {
                             hsum[0] = o1;
                             hsum2[0] = o2;
                         }
                     } else {
-                        const double2 hsv = s02_history(a.beta, hist_l, t, lane);
+                        const double2 hsv = s02_history(a.beta, hist_l, ht0 + t, lane);
                         if (lane == 0) hsum[0] = hsv;
                     }
                 }
@@ -1057,13 +1061,13 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     if (gen) {
                         const size_t ke = (size_t)(2 * se + 1) * a.kstride;
                         double2 o1, o2;
-                        conv_history2(a.kap + ke, a.kout + ke, hist_r, t, lane, o1, o2);
+                        conv_history2(a.kap + ke, a.kout + ke, hist_r, ht0 + t, lane, o1, o2);
                         if (lane == 0) {
                             hsum[1] = o1;
                             hsum2[1] = o2;
                         }
                     } else {
-                        const double2 hsv = s02_history(a.beta, hist_r, t, lane);
+                        const double2 hsv = s02_history(a.beta, hist_r, ht0 + t, lane);
                         if (lane == 0) hsum[1] = hsv;
                     }
                 }
@@ -1187,7 +1191,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             const double2 uo = *us;
             *us = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
             if (p == 0) {
-                if (hl) hist_l[t] = v;
+                if (hl) hist_l[ht0 + t] = v;
                 if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
                     const double2 ts = gen ? a.kout[(size_t)(2 * j + 0) * a.kstride] : a.two_sigma;
                     double2 o = csub(cmul(ts, v), lin);
@@ -1198,7 +1202,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
             if (p == Pj) {
-                if (hr) hist_r[t] = v;
+                if (hr) hist_r[ht0 + t] = v;
                 if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
                     const double2 ts = gen ? a.kout[(size_t)(2 * j + 1) * a.kstride] : a.two_sigma;
                     double2 o = csub(cmul(ts, v), rin);
@@ -1365,11 +1369,14 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
     }
     const bool hl = a.s02 && realsep && p == 0 && (tcf & 1);
     const bool hr = a.s02 && realsep && p == Pj && (tcf & 2);
-    double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * (nt + 1) : nullptr;
-    double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * (nt + 1) : nullptr;
+    // end traces v_0..v_{nt} at absolute steps: a launch marching a segment of the time
+    // axis (steps ht0 + 1 ..) extends the traces the earlier segments left
+    const int hst = a.hstride > 0 ? a.hstride : nt + 1, ht0 = a.ht0;
+    double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * hst : nullptr;
+    double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * hst : nullptr;
     constexpr bool gen = GEN;
-    if (hl) hist_l[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 0], a.u0[goff + sp]) : a.u0[goff + sp]);
-    if (hr) hist_r[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 1], a.u0[goff + sp]) : a.u0[goff + sp]);
+    if (hl && ht0 == 0) hist_l[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 0], a.u0[goff + sp]) : a.u0[goff + sp]);
+    if (hr && ht0 == 0) hist_r[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 1], a.u0[goff + sp]) : a.u0[goff + sp]);
     // the warps that hold the two ends form their history sums
     const bool wleft = a.s02 && (tcf & 1) && rank == 0 && wl == 0;
     const bool wright = a.s02 && (tcf & 2) && rank == Pj / T && wl == (Pj % T) / 32;
@@ -1426,13 +1433,13 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
             if (gen) {
                 const size_t ke = (size_t)(2 * j + side) * a.kstride;
                 double2 o1, o2;
-                conv_history2(a.kap + ke, a.kout + ke, hh, t, lane, o1, o2);
+                conv_history2(a.kap + ke, a.kout + ke, hh, ht0 + t, lane, o1, o2);
                 if (lane == 0) {
                     hsum[side] = o1;
                     hsum2[side] = o2;
                 }
             } else {
-                const double2 hsv = s02_history(a.beta, hh, t, lane);
+                const double2 hsv = s02_history(a.beta, hh, ht0 + t, lane);
                 if (lane == 0) hsum[side] = hsv;
             }
         }
@@ -1555,7 +1562,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
             const double2 uo = usep[tid];
             usep[tid] = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
             if (p == 0) {
-                if (hl) hist_l[t] = v;
+                if (hl) hist_l[ht0 + t] = v;
                 if ((tcf & 1) && sy.out_a >= 0 && a.gout) {
                     const double2 ts = gen ? a.kout[(size_t)(2 * j + 0) * a.kstride] : a.two_sigma;
                     double2 o = csub(cmul(ts, v), lin);
@@ -1566,7 +1573,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
             }
             if (p == Pj) {
-                if (hr) hist_r[t] = v;
+                if (hr) hist_r[ht0 + t] = v;
                 if ((tcf & 2) && sy.out_b >= 0 && a.gout) {
                     const double2 ts = gen ? a.kout[(size_t)(2 * j + 1) * a.kstride] : a.two_sigma;
                     double2 o = csub(cmul(ts, v), rin);
@@ -2062,7 +2069,8 @@ int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t
     a.tl_aux = fs.tl_aux;
     a.tl_red = fs.tl_red;
     if (!a.two_level) a.tl_pcr = nullptr;
-    if (mode != 0 && (fs.L > 8 || fs.nsteps > 1 || a.s02)) return -2;   // adjoint modes: L <= 8, V(x), Robin
+    // adjoint modes: L <= 8, V(x), Robin or S_0^2 (not the per-end kernels)
+    if (mode != 0 && (fs.L > 8 || fs.nsteps > 1 || a.kap)) return -2;
     switch (fs.L) {
         case 4: return launch_march_t<4>(a, ngroups, s, mode);
         case 8: return launch_march_t<8>(a, ngroups, s, mode);

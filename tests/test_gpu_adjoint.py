@@ -2,7 +2,9 @@
 the converged SWR solution (swr_adjoint): against the oracle's discrete adjoint
 of the monodomain scheme, against central differences of the GPU forward solve
 (16 seeded directions, 1e-6 relative), invariance under the checkpoint interval,
-and the torch.autograd.Function wrapper."""
+and the torch.autograd.Function wrapper; with Robin and with S_0^2 transmission
+(the segment marches then carry the ends' trace histories across checkpoints;
+the gradient is the monodomain one whatever the condition)."""
 import numpy as np
 import pytest
 
@@ -46,11 +48,11 @@ CASES = {
 }
 
 
-def gpu_gradient(wl, tgt, K=16, V=None):
+def gpu_gradient(wl, tgt, K=16, V=None, tc=None):
     from paper_1503_02564_gb300 import swr
     plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
                     node_off=wl.off, p=wl.sigma, restart=100, maxit=1000, tol_abs=1e-13,
-                    precond=swr.SWR_PC_CAUSAL)
+                    precond=swr.SWR_PC_CAUSAL, tc=swr.SWR_TC_ROBIN if tc is None else tc)
     Vt = torch.tensor(wl.V if V is None else V, dtype=torch.float64, device="cuda")
     plan.build_interface(Vt, torch.tensor(wl.u0, dtype=torch.complex128, device="cuda"))
     uT = torch.empty(wl.nx, dtype=torch.complex128, device="cuda")
@@ -64,35 +66,38 @@ def gpu_gradient(wl, tgt, K=16, V=None):
     return J, grad.cpu().numpy()
 
 
+@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_adjoint_gradient_matches_oracle(case):
+def test_adjoint_gradient_matches_oracle(case, tc):
     wl = CASES[case]()
     tgt = target(wl)
-    J, g = gpu_gradient(wl, tgt)
+    J, g = gpu_gradient(wl, tgt, tc=tc)
     Jo, go = O.adjoint_gradient(problem(wl), tgt)
     assert abs(J - Jo) <= 1e-10 * Jo
     assert rel(g, go) < 1e-8
 
 
-def test_adjoint_checkpoint_interval_does_not_change_the_gradient():
+@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
+def test_adjoint_checkpoint_interval_does_not_change_the_gradient(tc):
     wl = CASES["config1_small"]()
     tgt = target(wl)
-    ref = gpu_gradient(wl, tgt, K=60)[1]
+    ref = gpu_gradient(wl, tgt, K=60, tc=tc)[1]
     for K in (1, 7, 16, 59):
-        assert rel(gpu_gradient(wl, tgt, K=K)[1], ref) < 1e-12, K
+        assert rel(gpu_gradient(wl, tgt, K=K, tc=tc)[1], ref) < 1e-12, K
 
 
-def test_adjoint_gradient_against_central_differences():
+@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
+def test_adjoint_gradient_against_central_differences(tc):
     """16 seeded directions, J from the GPU forward solve alone."""
     wl = CASES["config1_small"]()
     tgt = target(wl)
-    J, g = gpu_gradient(wl, tgt)
+    J, g = gpu_gradient(wl, tgt, tc=tc)
     rng = np.random.default_rng(16)
     eps = 1e-4
     for _ in range(16):
         d = rng.standard_normal(wl.nx)
-        jp = gpu_gradient(wl, tgt, K=None, V=wl.V + eps * d)[0]
-        jm = gpu_gradient(wl, tgt, K=None, V=wl.V - eps * d)[0]
+        jp = gpu_gradient(wl, tgt, K=None, V=wl.V + eps * d, tc=tc)[0]
+        jm = gpu_gradient(wl, tgt, K=None, V=wl.V - eps * d, tc=tc)[0]
         fd = (jp - jm) / (2 * eps)
         assert abs(fd - g @ d) <= 1e-6 * abs(fd)
 
@@ -134,8 +139,9 @@ def test_adjoint_requires_a_solved_supported_plan():
         plan.adjoint(ubar, grad)
     assert e.value.status == swr.SWR_ERR_STATE
     plan.destroy()
+    # the per-end-kernel conditions (S_0^3 and up) are not differentiated
     plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
-                    node_off=wl.off, tc=swr.SWR_TC_S02)
+                    node_off=wl.off, tc=swr.SWR_TC_S03)
     plan.build_interface(torch.tensor(wl.V, dtype=torch.float64, device="cuda"),
                          torch.tensor(wl.u0, dtype=torch.complex128, device="cuda"))
     plan.solve(None, False, None)

@@ -965,6 +965,44 @@ def adjoint_gradient(P: Problem, u_target):
     return J, grad
 
 
+def adjoint_gradient_tdep(P: Problem, u_target):
+    """dJ/dV(t_m, x_k) for a tabulated time-dependent potential (rows m = 0..nt),
+    J = (u_N - u_target)^H M (u_N - u_target), u_N the monodomain Crank-Nicolson
+    solution (Eq. CNS_L with W_n = (V_n + V_{n-1})/2, Neumann ends).
+
+    Discrete adjoint of A_n v_n = B u_{n-1}, u_n = 2 v_n - u_{n-1}, with
+    A_n = (2i/dt) M - S + M_{W_n} (complex symmetric, so A_n^H = conj(A_n)) and
+    B = (2i/dt) M: with lam_N = 2 M (u_N - u_target) and, for n = N..1,
+        conj(A_n) mu_n = lam_n,
+        G_n(k) = -2 Re(mu_n^H (dM_W/dW_k) v_n)       (= dJ/dW_n(k)),
+        lam_{n-1} = 2 B^H mu_n - lam_n;
+    since W_n = (V_n + V_{n-1})/2, dJ/dV_m = (G_m + G_{m+1}) / 2 (G_0 = G_{N+1} = 0).
+    Every v_n comes from the forward march.  Returns (J, dJ/dV) with dJ/dV of
+    shape (nt + 1, nx)."""
+    if P.vkind != V_TIME:
+        raise NotImplementedError("adjoint_gradient_tdep: time-dependent V only")
+    n, h, dt, nt = P.nx, P.h, P.dt, P.nt
+    m = mono_march(P, sel=np.arange(n))
+    vs = m.vsel                                   # row t = v_t (row 0 = u0)
+    md, mo, sd, so, _, _ = p1_matrices(n, h, None)
+    I2 = 2j / dt
+    e = m.uT - np.asarray(u_target, np.complex128)
+    Me = _mass_apply(md, mo, e)
+    J = float(np.real(np.vdot(e, Me)))
+    lam = 2.0 * Me
+    G = np.zeros((nt + 2, n))
+    for t in range(nt, 0, -1):
+        W = 0.5 * (P.V[t] + P.V[t - 1])
+        _, _, _, _, wd, wo = p1_matrices(n, h, W)
+        dg = I2 * md - sd + wd
+        lo = I2 * mo - so + wo
+        mu = thomas(np.conj(lo), np.conj(dg), np.conj(lo), lam)
+        G[t] = -2.0 * potential_form(mu, vs[t], h)
+        lam = 2.0 * np.conj(I2) * _mass_apply(md, mo, mu) - lam
+    grad = 0.5 * (G[0:nt + 1] + G[1:nt + 2])
+    return J, grad
+
+
 def _potential_form_matrix(v, h):
     """The real-linear map w -> r(w), r_k = Re( sum_ab v_a (dM_W/dW_k)_ab w_b )
     (the P1 rule of Eq. AvML, no conjugation), as a sparse real matrix acting

@@ -15,6 +15,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>   // header-only; the ranges cost nothing without a tool attached
+
 #include "swr_internal.cuh"
 
 static std::atomic<long long> g_launches{0};
@@ -174,6 +176,15 @@ namespace {
 // swr_tuning.debug >= 1 runs on this thread (set at the entry points).
 thread_local int t_debug = 0;
 bool debug_on() { return t_debug >= 1; }
+
+// Named host range around each phase of the method (build, interface solve, final
+// state, adjoint) for timeline tools (Nsight Systems and the like).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 swr_status cuda_fail(cudaError_t e, const char* what, int line) {
     if (debug_on()) fprintf(stderr, "libswr: %s failed at line %d: %s\n", what, line, cudaGetErrorString(e));
     return SWR_ERR_CUDA;
@@ -964,6 +975,7 @@ swr_status apply_M(swr_plan_t p, const double2* y, double2* x) {
 // true residual ||b - (I - L) g||_2 < tol.
 swr_status gmres(swr_plan_t p, const double2* b, double tol, double2* g, bool g_init,
                  swr_info* info) {
+    NvtxRange nvtx_range("swr: GMRES interface solve");
     swr_status st = ensure_workspace(p);
     if (st) return st;
     Workspace& w = p->ws;
@@ -1052,6 +1064,7 @@ swr_status gmres(swr_plan_t p, const double2* b, double tol, double2* g, bool g_
 // when the recurrence's residual passes the test.
 swr_status bicgstab(swr_plan_t p, const double2* b, double tol, double2* g, bool g_init,
                     swr_info* info) {
+    NvtxRange nvtx_range("swr: BiCGStab interface solve");
     swr_status st = ensure_workspace(p);
     if (st) return st;
     Workspace& w = p->ws;
@@ -1151,6 +1164,7 @@ swr_status bicgstab(swr_plan_t p, const double2* b, double tol, double2* g, bool
 // Fixed point g <- L g + d (Algorithm 3 with the fixed point) or g <- R g
 // (Algorithm 1), until ||g^{k+1} - g^k||_2 < tol.
 swr_status fixed_point(swr_plan_t p, double2* g, bool g_init, bool classical, swr_info* info) {
+    NvtxRange nvtx_range("swr: fixed-point interface iteration");
     swr_status st = ensure_workspace(p);
     if (st) return st;
     Workspace& w = p->ws;
@@ -1186,6 +1200,7 @@ swr_status fixed_point(swr_plan_t p, double2* g, bool g_init, bool classical, sw
 // in time, g = P^{-1} d, refined by g += P^{-1} r, r = d - (I - L) g, while the
 // true residual ||r||_2 >= tol (at most maxit substitutions).
 swr_status causal_direct(swr_plan_t p, double2* g, bool g_init, swr_info* info) {
+    NvtxRange nvtx_range("swr: causal interface solve");
     swr_status st = ensure_workspace(p);
     if (st) return st;
     Workspace& w = p->ws;
@@ -1435,6 +1450,7 @@ void swr_destroy(swr_plan_t p) {
 // Validate and set up one plan over count problem instances (count = 1: swr_plan).
 static swr_status plan_create(const swr_desc* ds, int count, const swr_tuning* tuning,
                               swr_plan_t* out, void* stream) {
+    NvtxRange nvtx_range("swr_plan");
     if (!out) return SWR_ERR_ARG;
     *out = nullptr;
     if (!ds || count < 1) return SWR_ERR_ARG;
@@ -1872,6 +1888,7 @@ static swr_status build_body(swr_plan_t p, bool do_assemble) {
 
 swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) {
     t_debug = p ? p->tune.debug : 0;
+    NvtxRange nvtx_range("swr_build_interface");
     if (!p || !V || !u0) return SWR_ERR_ARG;
     cudaStream_t s = p->s;
     const size_t nb = (size_t)p->nb;
@@ -2030,6 +2047,7 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
 
 swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_, swr_info* info) {
     t_debug = p ? p->tune.debug : 0;
+    NvtxRange nvtx_range("swr_solve");
     if (!p) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     cudaStream_t s = p->s;
@@ -2103,6 +2121,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
 
 swr_status swr_apply_R(swr_plan_t p, const double* g_in, double* g_out) {
     t_debug = p ? p->tune.debug : 0;
+    NvtxRange nvtx_range("swr_apply_R");
     if (!p || !g_in || !g_out || g_in == g_out) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     CK(cudaMemsetAsync(g_out, 0, sizeof(double2) * (size_t)p->nb, p->s));
@@ -2115,6 +2134,7 @@ swr_status swr_apply_R(swr_plan_t p, const double* g_in, double* g_out) {
 
 swr_status swr_apply_interface(swr_plan_t p, const double* x, double* y) {
     t_debug = p ? p->tune.debug : 0;
+    NvtxRange nvtx_range("swr_apply_interface");
     if (!p || !x || !y || x == y) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     if (p->d.vkind != SWR_V_STATIC) return SWR_ERR_UNSUPPORTED;
@@ -2140,6 +2160,7 @@ swr_status swr_get_interface(swr_plan_t p, double* d, double* cols) {
 
 swr_status swr_apply_precond(swr_plan_t p, const double* y, double* x) {
     t_debug = p ? p->tune.debug : 0;
+    NvtxRange nvtx_range("swr_apply_precond");
     if (!p || !y || !x || x == y) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
     if (!has_precond(p)) return SWR_ERR_STATE;
@@ -2207,6 +2228,7 @@ swr_status swr_misfit(swr_plan_t p, const double* uT_, const double* target_, do
 // segment is recorded, then the adjoint march over the mirrored steps reads it).
 swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t ckpt_every) {
     t_debug = p ? p->tune.debug : 0;
+    NvtxRange nvtx_range("swr_adjoint");
     if (!p || !ubar_ || !dJdV_) return SWR_ERR_ARG;
     if (!p->built || !p->solved) return SWR_ERR_STATE;
     // the nonlinear gradient is taken of the monodomain scheme (any transmission

@@ -800,3 +800,56 @@ def test_extended_reference_shows_the_cancelled_columns_are_rounding():
     assert cancel > 1e4
     assert e / np.linalg.norm(cx.astype(np.complex128).ravel()) > 1e-11
     assert e / np.linalg.norm(cmag.astype(np.float64).ravel()) < 1e-13
+
+
+def _adjoint_tdep_case():
+    wl = W.config4(nsub=2, nx=121, nt=16)
+    P = problem(wl)
+    rng = np.random.default_rng(11)
+    tgt = wl.u0 * np.exp(0.3j) + 0.05 * (rng.standard_normal(wl.nx)
+                                         + 1j * rng.standard_normal(wl.nx))
+    return P, tgt
+
+
+def test_time_dependent_adjoint_gradient_matches_central_differences():
+    """dJ/dV(t_m, x_k) of the time-dependent scheme against fourth-order central
+    differences of J computed by the forward march alone, in six seeded directions of
+    the whole (nt + 1) x nx table."""
+    P, tgt = _adjoint_tdep_case()
+    J, g = O.adjoint_gradient_tdep(P, tgt)
+    assert g.shape == P.V.shape
+
+    def J_of(V):
+        Q = O.Problem(P.a0, P.b0, P.nx, P.dt, P.nt, P.off, P.u0, V, vkind=P.vkind)
+        return O.misfit(Q, O.mono_march(Q).uT, tgt)
+    rng = np.random.default_rng(12)
+    eps = 1e-2      # fourth order: truncation ~eps^4, well above rounding (J ~ 1)
+    for _ in range(6):
+        d = rng.standard_normal(P.V.shape)
+        j1 = J_of(P.V + eps * d) - J_of(P.V - eps * d)
+        j2 = J_of(P.V + 2 * eps * d) - J_of(P.V - 2 * eps * d)
+        fd = (8.0 * j1 - j2) / (12.0 * eps)          # fourth order
+        assert abs(fd - np.sum(g * d)) <= 1e-8 * abs(fd)
+
+
+def test_time_dependent_adjoint_gradient_vanishes_for_a_conserved_norm():
+    """J = ||u(T)||_M^2 is conserved for every real V(t, x): its gradient is zero."""
+    P, tgt = _adjoint_tdep_case()
+    _, g = O.adjoint_gradient_tdep(P, tgt)
+    _, g0 = O.adjoint_gradient_tdep(P, np.zeros(P.nx, np.complex128))
+    assert np.max(np.abs(g0)) <= 1e-10 * np.max(np.abs(g))
+
+
+def test_time_dependent_adjoint_reduces_to_the_static_one():
+    """For a potential that does not change in time the rows of dJ/dV(t_m, .) sum to
+    the static gradient dJ/dV (every W_n is the same V)."""
+    wl = W.config1(nx=101, nt=12, nsub=2)
+    Ps = problem(wl)
+    rng = np.random.default_rng(13)
+    tgt = wl.u0 * np.exp(0.2j) + 0.05 * rng.standard_normal(wl.nx)
+    Js, gs = O.adjoint_gradient(Ps, tgt)
+    Pt = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0,
+                   np.tile(wl.V, (wl.nt + 1, 1)), vkind=O.V_TIME, sigma=wl.sigma)
+    Jt, gt = O.adjoint_gradient_tdep(Pt, tgt)
+    assert abs(Jt - Js) <= 1e-13 * Js
+    assert rel(gt.sum(axis=0), gs) < 1e-12

@@ -308,12 +308,15 @@ swr_status swr_misfit(swr_plan_t p, const double *uT, const double *u_target, do
 /* Gradient dJ/dV(x) of a final-time objective J through the converged SWR
  * solution (no counterpart in the paper, which has no adjoint).  Needs, after a
  * successful swr_solve (SWR_ERR_STATE otherwise), a single-instance plan with
- *   SWR_V_STATIC, Robin transmission and the GMRES solver: dJ/dV;
- *   SWR_V_NONLINEAR (any transmission condition and solver):     dJ/dV0;
+ *   SWR_V_STATIC, Robin or S_0^2 transmission, any solver:   dJ/dV;
+ *   SWR_V_TIME, Robin or S_0^2, every step's factors stored (swr_stats.march_variant
+ *               3) with chunks of at most 8 nodes:          dJ/dV(t_m, x), m = 0..nt;
+ *   SWR_V_NONLINEAR (any transmission condition and solver):  dJ/dV0;
  * SWR_ERR_UNSUPPORTED for other plans.
  *   dJ_duT:     cplx[nx] (device), the M-weighted cotangent ubar of J at u(T):
  *               dJ = Re(ubar^H M du_T) (swr_misfit returns it for the misfit);
  *   dJ_dV:      double[nx] (device), overwritten with dJ/dV_k for the nodal V;
+ *               SWR_V_TIME: double[(nt + 1) nx], row m = dJ/dV(t_m, .) (the layout of V);
  *   ckpt_every: checkpoint interval K in time steps (<= 0: 50).
  * Method (static V): the discrete adjoint of the Crank-Nicolson march,
  * conjugated and scaled, is the same march run from (dt/2i) conj(ubar); it is
@@ -321,6 +324,12 @@ swr_status swr_misfit(swr_plan_t p, const double *uT, const double *u_target, do
  * preconditioner), then forward segments of K steps are recomputed from
  * checkpoints of u and the adjoint march over the mirrored steps accumulates
  *   dJ/dV_k = -2 Re sum_n (v^adj_{N-n+1})^T (dM_V/dV_k) v_n.
+ * With S_0^2 the segment marches carry the ends' trace histories over the whole
+ * time axis.  Method (V(t,x)): the adjoint march takes the step matrices A_N, ...,
+ * A_1 in that order, so its SWR problem is the forward one with the time axis
+ * reversed, solved matrix-free (Algorithm 2) with the plan's time-invariant
+ * preconditioner; adjoint step n gives dJ/dW_n = -2 Re (v^adj)^T (dM_W/dW) v_n, which
+ * enters dJ/dV(t_n) and dJ/dV(t_{n-1}) with weight 1/2 each (W_n = (V_n + V_{n-1})/2).
  * Method (nonlinear, Eq. CNS_NL with f = c|v|^2): the discrete adjoint of the
  * monodomain scheme, which the converged SWR solution reproduces.  Each adjoint
  * step solves the step's derivative, A0 w + M_{c|v|^2} w + 2c conj(v) .

@@ -159,6 +159,12 @@ struct swr_plan_s {
     bool have_L0 = false;
     int two_level = 1;             // two-level separator solve for cluster-spread systems
     double2* d_hseg = nullptr;     // S_0^2 adjoint: segment marches' end traces [2][N][2][nt+1]
+    // the interface problem the matrix-free operator (V(t,x), Algorithm 2) applies:
+    // the forward one (the plan's u0 and d, factors in time order) unless the adjoint
+    // of a time-dependent plan has switched to its time-reversed problem
+    const double2* cur_u0 = nullptr;
+    const double2* cur_d = nullptr;
+    int cur_rev = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double t_build_ms = 0.0;
     // per-launch timing ring: kind 0 = march, 1 = Toeplitz apply, 2 = P^{-1}
@@ -336,12 +342,15 @@ struct SegArgs {
     long long gstride = 0;    // flux block stride (0: the launch's own step count)
     double2* hist = nullptr;  // S_0^2: end traces over the whole time axis [N][2][nt+1]
     int ht0 = 0;              // absolute step before the segment's first step
+    int fstep0 = 0;           // V(t,x): per-step factor set of the segment's first step
+    int frev = 0;             // walk the factor sets backwards (time-reversed march)
     double2* vrec = nullptr;
     const double2* vfwd = nullptr;
     double *gint = nullptr, *gl = nullptr, *gr = nullptr;
 };
 
-MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
+// fixL > 0: the modelled shape for that chunk length (no tuned entry)
+MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC, int fixL = 0) {
     MarchCfg c;
     if (p->long_march && kind == MK_STATIC) {   // the grid-wide march, 16-node chunks
         c.L = 16;
@@ -349,7 +358,7 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
         return c;
     }
     for (const auto& t : p->tuned)
-        if (t[0] == kind && t[1] == nsys) {
+        if (fixL == 0 && t[0] == kind && t[1] == nsys) {
             c.L = t[2];
             c.C = t[3];
             c.G = t[4];
@@ -362,7 +371,9 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC) {
     const long long want = (long long)nsm * 4 * 32;
     const int cand[3] = {16, 8, 4};
     int L = 4;
-    if (kind == MK_TDEP) {
+    if (fixL > 0) {
+        L = fixL;
+    } else if (kind == MK_TDEP) {
         L = 4;   // per-step refactorisation keeps LU, spikes and state in registers
     } else if (kind == MK_NL || kind == MK_ADJ) {
         // state, right-hand side, iterate and solve (or the adjoint sums) per node
@@ -515,6 +526,8 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     a.inv_ik = p->inv_ik;
     a.status = p->d_status;
     a.two_level = p->two_level;
+    a.fstep0 = seg.fstep0;
+    a.frev = seg.frev;
     a.t0 = seg.t0;
     a.gstride = seg.gstride > 0 ? seg.gstride : nt_run;
     a.nxrec = p->nx;
@@ -572,8 +585,13 @@ swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, i
     const int kind = march_kind(p, zero_potential);
     const MarchCfg cfg = march_config(p, nsys, kind);
     const int pi = prof_begin(p, kind == MK_NL ? 3 : 0, work);
+    SegArgs sa;
+    if (p->cur_rev && !zero_potential) {   // time-reversed problem: last step's factors first
+        sa.fstep0 = p->nt - 1;
+        sa.frev = 1;
+    }
     const int rc = launch_cfg(p, cfg, kind, zero_potential, d_sys, nsys, gin, gout, uT, trace, u0,
-                              p->nt);
+                              p->nt, sa);
     prof_end(p, pi);
     if (rc == -2) return SWR_ERR_UNSUPPORTED;
     if (rc == -3) return SWR_ERR_STATE;
@@ -934,10 +952,12 @@ swr_status apply_A(swr_plan_t p, const double2* x, double2* y) {
         return rc ? SWR_ERR_UNSUPPORTED : SWR_OK;
     }
     // matrix-free: y = x - R x + d   (Algorithm 2)
-    swr_status st = run_march(p, false, p->d_sys_R, p->N, x, y, nullptr, nullptr, p->d_u0, p->work_R);
+    const double2* u0 = p->cur_u0 ? p->cur_u0 : p->d_u0;
+    const double2* d = p->cur_d ? p->cur_d : p->d_iface;
+    swr_status st = run_march(p, false, p->d_sys_R, p->N, x, y, nullptr, nullptr, u0, p->work_R);
     if (st) return st;
     LK(swr_launch_axpby(y, x, n, make_double2(-1.0, 0.0), make_double2(1.0, 0.0), p->s));
-    LK(swr_launch_axpby(y, p->d_iface, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s));
+    LK(swr_launch_axpby(y, d, n, make_double2(1.0, 0.0), make_double2(1.0, 0.0), p->s));
     return SWR_OK;
 }
 
@@ -2234,11 +2254,14 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
     // the nonlinear gradient is taken of the monodomain scheme (any transmission
     // condition and solver); the linear one runs the adjoint interface solve
     const bool nl = (p->d.vkind == SWR_V_NONLINEAR);
-    if (p->batched || p->long_march ||
-        (!nl && (p->d.vkind != SWR_V_STATIC || p->d.tc > SWR_TC_S02)))
-        return SWR_ERR_UNSUPPORTED;
     cudaStream_t s = p->s;
     const int nt = p->nt, nx = p->nx, N = p->N;
+    const bool tdep = (p->d.vkind == SWR_V_TIME);
+    if (p->batched || p->long_march || (!nl && p->d.tc > SWR_TC_S02)) return SWR_ERR_UNSUPPORTED;
+    // V(t,x): the adjoint walks every step's factors backwards, so they must be stored
+    // (the streamed variant) with chunks short enough for the gradient march (L <= 8)
+    if (tdep && (march_kind(p, false) != MK_TSTAT || march_config(p, N, MK_TSTAT).L > 8))
+        return SWR_ERR_UNSUPPORTED;
     const size_t nb = (size_t)p->nblk * nt;
     const int K = std::max(1, std::min(ckpt_every > 0 ? ckpt_every : 50, nt));
     const int C = (nt + K - 1) / K;
@@ -2288,6 +2311,96 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
             std::swap(ycur, ynext);
         }
         LK(swr_launch_grad_combine(p->d_gint, p->d_gl, p->d_gr, nx, dJdV_, s));
+        CK(cudaStreamSynchronize(s));
+        return read_status(p);
+    }
+    if (tdep) {
+        // V(t,x): W_n changes every step, so the adjoint march (the forward map run
+        // backwards, z_{n-1} = 2 A_n^{-1} B z_n - z_n) takes the factors of A_N, ...,
+        // A_1 in that order: its SWR problem is the forward one with the time axis
+        // reversed, solved matrix-free like the forward one (Algorithm 2) with the same
+        // time-invariant preconditioner.  Each adjoint step's potential form is
+        // dJ/dW_n, which goes to the rows n and n-1 of dJ/dV (W_n = (V_n + V_{n-1})/2).
+        const MarchCfg cfg0 = march_config(p, N, MK_TSTAT);          // forward segments
+        const MarchCfg cfga = march_config(p, N, MK_ADJ, cfg0.L);    // record / gradient
+        auto segT = [&](const MarchCfg& cfg, int mode, const double2* gin, int t0, int nrun,
+                        int fstep0, const double2* u0, double2* uT,
+                        const double2* vfwd) -> swr_status {
+            SegArgs sa;
+            sa.mode = mode;
+            sa.t0 = t0;
+            sa.gstride = nt;
+            sa.vrec = p->d_slab;
+            sa.vfwd = vfwd;
+            sa.gint = p->d_gint;
+            sa.gl = p->d_gl;
+            sa.gr = p->d_gr;
+            sa.fstep0 = fstep0;
+            if (s02) {
+                sa.hist = p->d_hseg + (mode == 2 ? (size_t)N * 2 * (nt + 1) : 0);
+                sa.ht0 = t0;
+            }
+            const int pi = prof_begin(p, 0, (long long)nx * nrun);
+            const int rc = launch_cfg(p, cfg, MK_TSTAT, false, p->d_sys_seg, N, gin, nullptr, uT,
+                                      nullptr, u0, nrun, sa);
+            prof_end(p, pi);
+            if (rc == -2) return SWR_ERR_UNSUPPORTED;
+            if (rc) return launch_fail("adjoint segment march (time-dependent)", __LINE__);
+            return SWR_OK;
+        };
+        // 1. forward checkpoints
+        CK(cudaMemcpyAsync(p->d_ckpt, p->d_u0, sizeof(double2) * nx, cudaMemcpyDeviceToDevice, s));
+        for (int c = 1; c < C; ++c)
+            if ((st = segT(cfg0, 0, p->d_gconv, (c - 1) * K, K, (c - 1) * K,
+                           p->d_ckpt + (size_t)(c - 1) * nx, p->d_ckpt + (size_t)c * nx,
+                           nullptr)))
+                return st;
+        // 2. the adjoint's time-reversed interface problem: d_y = R_rev 0, then
+        //    (I - L_rev) g_y = d_y by the plan's GMRES, matrix-free
+        LK(swr_launch_adj_seed(reinterpret_cast<const double2*>(ubar_), 0.5 * p->d.dt, nx,
+                               p->d_ya, s));
+        CK(cudaMemsetAsync(p->d_dy, 0, sizeof(double2) * nb, s));
+        p->cur_rev = 1;
+        st = run_march(p, false, p->d_sys_build, N, nullptr, p->d_dy, nullptr, nullptr, p->d_ya,
+                       p->work_R);
+        double dn = 0.0, dny = 0.0;
+        if (!st) st = norm2(p, p->d_iface, (long long)nb, &dn);
+        if (!st) st = norm2(p, p->d_dy, (long long)nb, &dny);
+        if (!st) {
+            const double tol = (dn > 0.0) ? p->d.tol_abs * dny / dn : p->d.tol_abs;
+            p->cur_u0 = p->d_ya;
+            p->cur_d = p->d_dy;
+            swr_info loc{};
+            st = gmres(p, p->d_dy, tol, p->d_gy, false, &loc);
+        }
+        p->cur_rev = 0;
+        p->cur_u0 = nullptr;
+        p->cur_d = nullptr;
+        if (st != SWR_OK) return st;
+        // 3. segments from the last to the first: record the forward v of the segment,
+        //    then one launch per adjoint step (its potential form is that step's
+        //    dJ/dW_n), adding it into the rows of dJ/dV
+        CK(cudaMemsetAsync(p->d_gint, 0, sizeof(double) * nx, s));
+        CK(cudaMemsetAsync(p->d_gl, 0, sizeof(double) * nx, s));
+        CK(cudaMemsetAsync(p->d_gr, 0, sizeof(double) * nx, s));
+        CK(cudaMemsetAsync(dJdV_, 0, sizeof(double) * (size_t)(nt + 1) * nx, s));
+        double2* ycur = p->d_ya;
+        double2* ynext = p->d_yb;
+        for (int c = C - 1; c >= 0; --c) {
+            const int t0 = c * K, Kc = std::min(K, nt - t0);
+            if ((st = segT(cfga, 1, p->d_gconv, t0, Kc, t0, p->d_ckpt + (size_t)c * nx, nullptr,
+                           nullptr)))
+                return st;
+            for (int i = 0; i < Kc; ++i) {
+                const int n = t0 + Kc - i;           // forward step of this adjoint step
+                const int ta = nt - n;               // adjoint steps before it
+                if ((st = segT(cfga, 2, p->d_gy, ta, 1, n - 1, ycur, ynext,
+                               p->d_slab + (size_t)(Kc - 1 - i) * nx)))
+                    return st;
+                LK(swr_launch_grad_step_tdep(p->d_gint, p->d_gl, p->d_gr, nx, n, dJdV_, s));
+                std::swap(ycur, ynext);
+            }
+        }
         CK(cudaStreamSynchronize(s));
         return read_status(p);
     }

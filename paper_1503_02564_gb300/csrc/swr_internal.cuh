@@ -238,6 +238,10 @@ struct MarchArgs {
     const double2* tl_aux;
     const double2* tl_red;
     int two_level;        // 0: keep the cluster-wide PCR even when the data exists
+    // per-step factors (V(t,x)): index of the factor set of this launch's step 1, and
+    // frev != 0 to walk them backwards (the adjoint's time-reversed march)
+    int fstep0;
+    int frev;
 };
 
 // One problem instance of a batched plan.  The instances' subdomains, interface
@@ -370,3 +374,9 @@ int swr_launch_adj_seed(const double2* ubar, double half_dt, long long n, double
                         cudaStream_t s);
 int swr_launch_grad_combine(const double* gint, const double* gl, const double* gr, long long n,
                             double* out, cudaStream_t s);
+// Time-dependent potential: one adjoint step's potential-form sums (gint, gl, gr) give
+// dJ/dW_n = -2 (gint + gl + gr), which enters dJ/dV_n and dJ/dV_{n-1} with weight 1/2
+// each (W_n = (V_n + V_{n-1}) / 2); adds them to rows n and n-1 of out (nx each) and
+// clears the sums.
+int swr_launch_grad_step_tdep(double* gint, double* gl, double* gr, long long nx, int n,
+                              double* out, cudaStream_t s);

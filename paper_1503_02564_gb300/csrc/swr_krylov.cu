@@ -1388,6 +1388,27 @@ __global__ void k_grad_combine(const double* __restrict__ gint, const double* __
     out[k] = -2.0 * (gint[k] + gl[k] + gr[k]);
 }
 
+__global__ void k_grad_step_tdep(double* __restrict__ gint, double* __restrict__ gl,
+                                 double* __restrict__ gr, long long nx, int n,
+                                 double* __restrict__ out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nx) return;
+    const double half = -(gint[k] + gl[k] + gr[k]);   // (1/2) dJ/dW_n
+    out[(size_t)n * nx + k] += half;
+    out[(size_t)(n - 1) * nx + k] += half;
+    gint[k] = 0.0;
+    gl[k] = 0.0;
+    gr[k] = 0.0;
+}
+
+int swr_launch_grad_step_tdep(double* gint, double* gl, double* gr, long long nx, int n,
+                              double* out, cudaStream_t s) {
+    if (n < 1) return -2;
+    k_grad_step_tdep<<<(unsigned)((nx + 255) / 256), 256, 0, s>>>(gint, gl, gr, nx, n, out);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int swr_launch_adj_seed(const double2* ubar, double half_dt, long long n, double2* y,
                         cudaStream_t s) {
     k_adj_seed<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ubar, half_dt, n, y);

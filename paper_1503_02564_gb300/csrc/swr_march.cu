@@ -2043,7 +2043,11 @@ static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s, int mode) {
 }
 
 int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t s, int mode) {
-    if (fs.nsteps > 1 && fs.nsteps < a.nt) return -2;
+    if (fs.nsteps > 1) {
+        // the launch's steps must lie inside the per-step factor sets
+        const long long last = a.frev ? (long long)a.fstep0 - (a.nt - 1) : (long long)a.fstep0 + a.nt - 1;
+        if (a.fstep0 < 0 || a.fstep0 >= fs.nsteps || last < 0 || last >= fs.nsteps) return -2;
+    }
     a.fstride = fs.fstride;
     a.sstride = fs.sstride;
     a.pstride = fs.pstride;
@@ -2065,12 +2069,22 @@ int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t
     a.fac = fs.fac;
     a.sep = fs.sep;
     a.pcr = fs.pcr;
+    if (fs.nsteps > 1) {   // start at step fstep0's factors; walk backwards when frev
+        a.fac += (size_t)a.fstep0 * fs.fstride;
+        a.sep += (size_t)a.fstep0 * fs.sstride;
+        a.pcr += (size_t)a.fstep0 * fs.pstride;
+        if (a.frev) {
+            a.fstride = -a.fstride;
+            a.sstride = -a.sstride;
+            a.pstride = -a.pstride;
+        }
+    }
     a.tl_pcr = fs.tl_ok ? fs.tl_pcr : nullptr;
     a.tl_aux = fs.tl_aux;
     a.tl_red = fs.tl_red;
     if (!a.two_level) a.tl_pcr = nullptr;
-    // adjoint modes: L <= 8, V(x), Robin or S_0^2 (not the per-end kernels)
-    if (mode != 0 && (fs.L > 8 || fs.nsteps > 1 || a.kap)) return -2;
+    // adjoint modes: L <= 8, Robin or S_0^2 (not the per-end kernels)
+    if (mode != 0 && (fs.L > 8 || a.kap)) return -2;
     switch (fs.L) {
         case 4: return launch_march_t<4>(a, ngroups, s, mode);
         case 8: return launch_march_t<8>(a, ngroups, s, mode);

@@ -294,9 +294,12 @@ class Plan:
         return J.value
 
     def adjoint(self, ubar, grad, ckpt_every=50):
-        """grad <- dJ/dV for the M-weighted cotangent ubar of J at u(T) (after solve())."""
+        """grad <- dJ/dV for the M-weighted cotangent ubar of J at u(T) (after solve());
+        grad has nx entries, or (nt + 1) nx for a time-dependent potential (the layout
+        of V)."""
+        ng = (self.nt + 1) * self.nx if self.vkind == SWR_V_TIME else self.nx
         _check(lib().swr_adjoint(self.handle, _ptr(ubar, torch.complex128, self.nx, "ubar"),
-                                 _ptr(grad, torch.float64, self.nx, "grad"), int(ckpt_every)),
+                                 _ptr(grad, torch.float64, ng, "grad"), int(ckpt_every)),
                "swr_adjoint")
 
     def get_stats(self, reset=False):

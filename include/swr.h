@@ -358,7 +358,7 @@ swr_status swr_get_stats(swr_plan_t p, swr_stats *out, int32_t reset);
  * up front in their own pool, or latency-critical loops that cannot afford the
  * device-wide synchronisation cudaMalloc/cudaFree imply.  The caller provides
  * inputs and outputs; the substitution's working arrays live in a fixed
- * library-owned device array (about 135 KB, held on every GPU that loads the
+ * library-owned device array (about 260 KB, held on every GPU that loads the
  * library until the process exits).
  *   nsub:   N, 2 <= N <= 1024 (larger N: SWR_ERR_ARG; the array is sized for 1024)
  *   nt:     time steps, >= 1

@@ -567,7 +567,8 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
         return swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
                                    p->d.nl_maxit, nullptr, cfg.ngroups, p->s, 0, p->d_pit);
     const int rc = swr_launch_march(fs, a, ngroups, p->s, seg.mode);
-    if (rc == 0 && cfg.C > 1 && seg.mode == 0 && fs.nsteps == 1 && fs.tl_ok && p->two_level)
+    if (rc == 0 && (cfg.C > 1 || (cfg.G == 1 && !cfg.ragged)) && seg.mode == 0 &&
+        fs.nsteps == 1 && fs.tl_ok && p->two_level)
         p->stats.two_level_launches += 1;
     return rc;
 }

@@ -331,6 +331,9 @@ int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* la
                            int H, cudaStream_t s, const InstInfo* inst = nullptr,
                            const int* if_inst = nullptr, int nif_total = 0);
 int swr_causal_capacity(int nt);
+// Progress counters of the causal substitution sit kProgStride ints apart (one per
+// 128-byte line: every counter is polled by many CTAs and written by one).
+constexpr int kProgStride = 32;
 // Test hook of the substitution's bounded waits on the current device: poll limit
 // (<= 0: the default, about 1-2 s) and an interface whose progress is never
 // published (< 0: none).  Returns 0 or -1 (CUDA error).

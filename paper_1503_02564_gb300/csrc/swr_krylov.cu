@@ -789,10 +789,16 @@ __device__ __forceinline__ void store_release(int* p, int v) {
 // L2 round trip, is looked at only every 32nd poll.
 constexpr int kSpinPolls = 32;
 
+__device__ __forceinline__ int load_relaxed(const int* p) {
+    cuda::atomic_ref<const int, cuda::thread_scope_device> r(*p);
+    return r.load(cuda::memory_order_relaxed);
+}
+
+// Relaxed polls (no cache maintenance per poll), one acquire once the value is there.
 __device__ __forceinline__ bool poll_until(const int* cnt, int target, int* abortf, int* status,
                                            long long lim) {
     long long polls = 0;
-    while (load_acquire(cnt) < target) {
+    while (load_relaxed(cnt) < target) {
         ++polls;
         if ((polls & 31) == 0 && load_acquire(abortf) != 0) return false;
         if (polls > lim) {
@@ -802,20 +808,23 @@ __device__ __forceinline__ bool poll_until(const int* cnt, int target, int* abor
         }
         if (polls > kSpinPolls) __nanosleep(64);
     }
+    (void)load_acquire(cnt);   // orders the reads that follow after the publisher's writes
     return true;
 }
 
 __device__ bool wait_neighbours(int k, bool hl, bool hr, int target, const int* progress,
                                 int* abortf, int* status, long long lim) {
-    if (hl && !poll_until(progress + k - 1, target, abortf, status, lim)) return false;
-    if (hr && !poll_until(progress + k + 1, target, abortf, status, lim)) return false;
+    if (hl && !poll_until(progress + (size_t)(k - 1) * kProgStride, target, abortf, status, lim))
+        return false;
+    if (hr && !poll_until(progress + (size_t)(k + 1) * kProgStride, target, abortf, status, lim))
+        return false;
     return true;
 }
 
 // Wait until interface nb has reached `target` (one lane per interface waited on).
 __device__ bool wait_one(int nb, int target, const int* progress, int* abortf, int* status,
                          long long lim) {
-    return poll_until(progress + nb, target, abortf, status, lim);
+    return poll_until(progress + (size_t)nb * kProgStride, target, abortf, status, lim);
 }
 
 // Rows of the inverse of the lag-0 system.  With z_k = (r_k, l_{k+1}) the values
@@ -1131,7 +1140,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         if (lane == 0) {
             xsw[2 * kg] = y[(size_t)(2 * k) * nt];
             xsw[2 * kg + 1] = y[(size_t)(2 * k + 1) * nt];
-            if (publish) store_release(progress + kg, 1);
+            if (publish) store_release(progress + (size_t)kg * kProgStride, 1);
         }
         __syncwarp();
         for (int n = 0; n < nt; ++n) {
@@ -1181,7 +1190,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                         fail_local();
                     }
                 }
-                if (go && publish) store_release(progress + kg, n + 2);   // x_n and P_{n+1}
+                if (go && publish) store_release(progress + (size_t)kg * kProgStride, n + 2);   // x_n and P_{n+1}
             }
             go = __shfl_sync(0xffffffffu, go, 0);
             if (!go) break;
@@ -1234,7 +1243,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                         double2* out = xsw + (size_t)((sw - 1) & 1) * 2 * nif_all;
                         out[2 * kg] = z1;
                         out[2 * kg + 1] = z2;
-                        if (publish) store_release(progress + kg, n * S1 + sw);
+                        if (publish) store_release(progress + (size_t)kg * kProgStride, n * S1 + sw);
                         if (!wait_neighbours(kg, has_l, has_r, n * S1 + sw, progress, abortf,
                                              status, lim)) {
                             go = 0;
@@ -1250,7 +1259,7 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                         x[(size_t)(2 * k) * nt + n] = z1;
                         x[(size_t)(2 * k + 1) * nt + n] = z2;
                         cta_store_release(&s_xown, n + 1);
-                        if (publish) store_release(progress + kg, (n + 1) * S1);   // orders x
+                        if (publish) store_release(progress + (size_t)kg * kProgStride, (n + 1) * S1);   // orders x
                     }
                 }
             }
@@ -1271,9 +1280,9 @@ int swr_set_wait_hook(long long max_polls, int withhold) {
 }
 
 size_t swr_causal_scratch_bytes(int N) {
-    // xsw: 2 x 2(N-1) complex sweep values, then N-1 progress counters and the abort flag
-    // (a batched plan passes N = its total interface count + 1)
-    return sizeof(double2) * (size_t)4 * (N - 1) + sizeof(int) * (size_t)N;
+    // xsw: 2 x 2(N-1) complex sweep values, then N-1 progress counters and the abort
+    // flag, kProgStride ints apart (a batched plan passes N = its total interface count + 1)
+    return sizeof(double2) * (size_t)4 * (N - 1) + sizeof(int) * (size_t)N * kProgStride;
 }
 
 // Interfaces one cooperative launch can hold (all CTAs resident at once).
@@ -1305,12 +1314,13 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, c
     if (ncta <= 0) return 0;
     double2* xsw = static_cast<double2*>(scratch);
     int* progress = reinterpret_cast<int*>(xsw + (size_t)4 * nif);
-    int* abortf = progress + nif;
+    int* abortf = progress + (size_t)nif * kProgStride;
     const int cap = swr_causal_capacity(nt);
     if (cap <= 0) return -1;
     if (ncta > cap) return -2;           // all CTAs must be resident at once
     // this launch's progress counters and the abort flag start at zero
-    if (cudaMemsetAsync(progress + k0, 0, sizeof(int) * (size_t)ncta, s) != cudaSuccess ||
+    if (cudaMemsetAsync(progress + (size_t)k0 * kProgStride, 0,
+                        sizeof(int) * (size_t)ncta * kProgStride, s) != cudaSuccess ||
         cudaMemsetAsync(abortf, 0, sizeof(int), s) != cudaSuccess)
         return -1;
     void* args[] = {(void*)&N, (void*)&nt, (void*)&sweeps, (void*)&cols, (void*)&lag0,

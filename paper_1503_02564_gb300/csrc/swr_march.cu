@@ -1270,9 +1270,9 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
 }
 
 // ---------------------------------------------------------------------------
-// The constant-matrix march of one system spread over a cluster of C CTAs with the
-// two-level separator solve (FactorSet.tl_*): one cluster barrier per time step
-// instead of one per PCR level.  Thread p = rank T + tid owns separator p and chunk p
+// The constant-matrix march of one system spread over a cluster of C CTAs (or alone
+// in its CTA, C = 1) with the two-level separator solve (FactorSet.tl_*): one cluster
+// barrier per time step instead of one per PCR level.  Thread p = rank T + tid owns separator p and chunk p
 // as in k_march_static; T is a multiple of 32, so warp q of the system (separators
 // 32q .. 32q+31) lies in one CTA, and the first separator of every CTA is a
 // super-separator.  Per step:
@@ -2009,9 +2009,11 @@ static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s, int mode) {
     const int slots = a.stage == 2 ? 2 * a.levels + 3 + 4 * L : (a.stage == 1 ? 2 * a.levels + 3 : 0);
     int smem = swr_march_smem_bytes(a.T, a.G, slots);
     void (*kern)(const MarchArgs) = a.kap ? k_march_static<L, 0, true> : k_march_static<L, 0>;
-    // a system spread over a cluster: the two-level separator solve (one cluster
-    // barrier per step) when its data was factored
-    if (a.C > 1 && mode == 0 && a.stage == 0 && a.fstride == 0 && a.tl_pcr && (a.T & 31) == 0) {
+    // a system spread over a cluster, or alone in its CTA: the two-level separator
+    // solve (one cluster / CTA barrier per step) when its data was factored
+    const bool one_system = (a.C > 1) || (a.G == 1 && !a.rag);
+    if (one_system && mode == 0 && a.stage == 0 && a.fstride == 0 && a.tl_pcr &&
+        (a.T & 31) == 0) {
         kern = a.kap ? k_march_tl<L, true> : k_march_tl<L, false>;
         smem = swr_march_tl_smem_bytes(a.T);
     }

@@ -10,7 +10,7 @@
 // fixed-size array in the library's own device memory instead.
 //
 // The scratch is a file-scope __device__ array: every GPU that loads the
-// library holds it (about 135 KB) until the process exits.  Host code must not
+// library holds it (about 260 KB) until the process exits.  Host code must not
 // hand the array's name to a kernel: on the host it is only a stand-in symbol.
 // Its device address is looked up with cudaGetSymbolAddress once per device,
 // with that device current, the first time the entry point runs there, and again
@@ -27,8 +27,10 @@ namespace {
 constexpr int kNoallocMaxSub = 1024;     // largest supported number of subdomains N
 constexpr int kNoallocMaxDevices = 64;
 constexpr size_t kLag0Elems = (size_t)4 * kNoallocMaxSub;
-// causal substitution scratch for N = 1024: 4(N-1) complex sweep values + N ints
-constexpr size_t kCausalBytes = sizeof(double2) * 4 * (kNoallocMaxSub - 1) + sizeof(int) * kNoallocMaxSub;
+// causal substitution scratch for N = 1024: 4(N-1) complex sweep values, then N
+// progress counters and the abort flag kProgStride ints apart
+constexpr size_t kCausalBytes =
+    sizeof(double2) * 4 * (kNoallocMaxSub - 1) + sizeof(int) * kNoallocMaxSub * kProgStride;
 constexpr size_t kCausalElems = (kCausalBytes + sizeof(double2) - 1) / sizeof(double2);
 
 std::mutex g_setup_mutex;

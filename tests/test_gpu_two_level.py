@@ -90,6 +90,25 @@ def test_two_level_march_matches_oracle_and_cluster_pcr(chunk, tc):
     assert rel(d1, d0) < 1e-12 and rel(c1, c0) < 1e-12 and rel(r1, r0) < 1e-12
 
 
+@pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
+def test_two_level_one_system_per_cta(tc):
+    """About a hundred systems (the build of 34 subdomains): the modelled shape puts one
+    system in each CTA (no cluster), and the two-level solve runs there too (its
+    cluster is the CTA itself)."""
+    wl = W.config2(nsub=34, nx=34 * 700 + 1, nt=14)
+    x = wl.x
+    wl.u0 = np.exp(2j * x) * (1.0 + 0.3 * np.sin(0.7 * x))
+    d1, c1, r1, g, st1 = build(wl, tc, 12, 0)
+    d0, c0, r0, _, st0 = build(wl, tc, 12, -1)
+    assert st1["two_level_launches"] > 0 and st0["two_level_launches"] == 0
+    P = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0, wl.V,
+                  tc=tc, sigma=wl.sigma)
+    assert rel(d1, O.build_d(P)) < TOL_MARCH
+    assert rel(c1, O.build_columns(P)) < TOL_MARCH
+    assert rel(r1, O.apply_R(P, g)) < TOL_MARCH
+    assert rel(d1, d0) < 1e-12 and rel(c1, c0) < 1e-12 and rel(r1, r0) < 1e-12
+
+
 def test_two_level_solve_reproduces_monodomain():
     """A full solve (causal preconditioner, u(T) by superposition) on the ragged
     partition with the two-level marches."""

@@ -153,6 +153,7 @@ struct swr_plan_s {
     bool auto_sweeps = false;      // pc_sweeps < 0: chosen from the lag-0 corners at the first build
     int causal_H = 0;              // >= 1: window form of the substitution (exact lag-0 solve)
     double2* d_Gw = nullptr;       // rows of the lag-0 inverse, [nif][2H+1][4]
+    double2* d_Pwin = nullptr;     // window form: partial right-hand sides P_n, layout of y
     // S_0^3, S_0^4, S_1^2, S_1^4: per-end kernels (own, flux update) and s = 0 factors
     double2 *d_kap = nullptr, *d_kout = nullptr, *d_rho = nullptr;
     bool built = false;
@@ -919,14 +920,23 @@ int p_causal(swr_plan_t p, const double2* cols, const double2* lag0, const doubl
     const bool win = p->causal_H > 0 && cols == p->d_iface + p->nb;
     const double2* Gw = win ? p->d_Gw : nullptr;
     const int H = win ? p->causal_H : 0;
+    const int sweeps = win ? 0 : p->causal_sweeps;
     if (!p->batched)
-        return swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps, p->d_hist,
-                                 p->d_status, p->s, nullptr, nullptr, 0, 0, 0, Gw, H);
+        return swr_launch_causal(p->N, p->nt, cols, lag0, y, x, sweeps, p->d_hist, p->d_status,
+                                 p->s, nullptr, nullptr, 0, 0, 0, Gw, H, p->d_Pwin);
+    // the values are the hand-off (sweeps == 0): x and the window's partial right-hand
+    // sides start unset, once for all groups
+    if (sweeps == 0) {
+        const size_t bytes = sizeof(double2) * (size_t)p->nb;
+        if (cudaMemsetAsync(x, 0xff, bytes, p->s) != cudaSuccess ||
+            (H > 0 && cudaMemsetAsync(p->d_Pwin, 0xff, bytes, p->s) != cudaSuccess))
+            return -1;
+    }
     // whole instances per cooperative launch, as many as fit at once
     for (const auto& g : p->causal_groups) {
-        const int rc = swr_launch_causal(p->N, p->nt, cols, lag0, y, x, p->causal_sweeps,
-                                         p->d_hist, p->d_status, p->s, p->d_inst, p->d_if_inst,
-                                         g.first, g.second, p->nif, Gw, H);
+        const int rc = swr_launch_causal(p->N, p->nt, cols, lag0, y, x, sweeps, p->d_hist,
+                                         p->d_status, p->s, p->d_inst, p->d_if_inst, g.first,
+                                         g.second, p->nif, Gw, H, p->d_Pwin);
         if (rc) return rc;
     }
     return 0;
@@ -1455,7 +1465,7 @@ void swr_destroy(swr_plan_t p) {
     cudaFree(p->d_sys_build); cudaFree(p->d_sys_R); cudaFree(p->d_sys_final);
     cudaFree(p->d_status); cudaFree(p->d_scal); cudaFree(p->d_pit);
     cudaFree(p->d_urec); cudaFree(p->d_rec_base);
-    cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0); cudaFree(p->d_Gw);
+    cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0); cudaFree(p->d_Gw); cudaFree(p->d_Pwin);
     cudaFree(p->d_kap); cudaFree(p->d_kout); cudaFree(p->d_rho); cudaFree(p->d_long);
     Workspace& w = p->ws;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
@@ -2053,6 +2063,7 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
             p->causal_sweeps = 1;
         } else if (H >= 1) {
             if (!p->d_Gw && (st = dalloc(&p->d_Gw, (size_t)p->nif * (2 * 8 + 1) * 4))) return st;
+            if (!p->d_Pwin && (st = dalloc(&p->d_Pwin, (size_t)p->nb))) return st;
             p->causal_H = H;
             LK(swr_launch_lag0_window(p->N, p->nt, p->d_iface + p->nb, p->d_lag0, p->d_Gw, H, s,
                                       p->batched ? p->d_inst : nullptr, p->d_if_inst, p->nif));

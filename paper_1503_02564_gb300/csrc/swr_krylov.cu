@@ -918,31 +918,38 @@ int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* la
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-// Warp 0 waits, solves and publishes; warps 1-4 (one per source block) form the
-// history sums, lags >= 3, two steps ahead of warp 0 and without a per-step barrier:
-// each runs as soon as its source's values are there (this interface's x: the shared
-// counter s_xown; a neighbour's: its progress counter) and hands its sum over in a
-// three-slot ring with one ready flag per warp (s_hdone), refilling a slot only after
-// warp 0 has consumed it (s_hused).  Warp 0 adds only the lag-2 and lag-1 terms on
-// its critical path, and no fence or block-wide barrier sits in its time loop besides
-// the release of its own progress counter.
-// The same-step coupling of neighbouring interfaces is resolved either by
-// `sweeps` block-Jacobi sweeps (H == 0), or exactly (to (|c| |D^{-1}|)^{H+1}) by
-// the window form (H >= 1), x_n(k) = sum_d G_{k,k+d} R_n(k+d) with the rows of
-// the lag-0 inverse (k_lag0_window) and R_n(i) the right-hand side of interface i
-// at step n: y_n(i) plus its history.
+// Both forms below share the history sums.  Warp 0 solves and hands on; warps 1-4
+// (one per source block) form the history sums of the lags beyond what warp 0 adds
+// itself, a few steps ahead of warp 0 and without a per-step barrier: each runs as soon
+// as its source's values are there and hands its sum over in a ring with one ready flag
+// per warp (s_hdone), refilling a slot only after warp 0 has consumed it (s_hused).
 //
-// Window form, one hand-off per step: interface i publishes, with x_{n-1}(i), the
-// part of R_n(i) that does not involve step n-1 (y_n(i) and the lags >= 2), as
-// P_n(i); progress(i) = n + 1 then says that x_{n-1}(i) and P_n(i) are visible.
-// At step n lane H+1+d waits for interface k+d (|d| <= H+1), and lane H+1+d
-// (|d| <= H) forms R_n(k+d) = P_n(k+d) + the lag-1 terms from x_{n-1} of
-// interfaces k+d-1, k+d, k+d+1, then its term G_{k,k+d} R_n(k+d).
-// P_n lives in a two-slot ring: interface k overwrites slot (n+1)&1 at the end of
-// step n, after it has seen every interface within H+1 finish step n-1, and
-// those within H were the only readers of P_{n-1}(k).
+// k_causal_flag: the values are the hand-off.  Every value that another CTA reads
+// (x_n of an interface's two blocks and, in the window form, its partial right-hand
+// side P_n) is written once, into an array preset to an "unset" bit pattern (all ones:
+// a NaN that is never stored, a computed value with that pattern being stored as the
+// canonical quiet NaN).  Readers poll the value itself with relaxed gpu-scope loads
+// until it is set, so no flag, fence or acquire lies between one interface's step and
+// its neighbours' next.  Each 8-byte word is single-copy atomic: a word that reads as
+// set holds its final value.
+// The same-step coupling of neighbouring interfaces is resolved exactly (to
+// (|c| |D^{-1}|)^{H+1}) by the window form, x_n(k) = sum_d G_{k,k+d} R_n(k+d), with
+// the rows of the lag-0 inverse (k_lag0_window) and R_n(i) the right-hand side of
+// interface i at step n: P_n(i), i.e. y_n(i) and the lags >= 2, plus the lag-1 terms.
+// H = 0 drops the coupling (G_{k,k} = D_k^{-1}, the lag-0 inverses themselves) and
+// keeps P_n(k) in a register.
+// k_causal_sweeps: the coupling resolved by `sweeps` >= 1 block-Jacobi sweeps, with
+// progress counters (release / acquire) around the values exchanged per sweep.
 namespace {
 constexpr long long kLocalPolls = 1LL << 24;   // bound of a wait between warps of one CTA
+constexpr long long kUnsetBits = -1LL;          // bit pattern of a value not yet written
+constexpr int kLA = 3;                          // k_causal_flag: warp 0 adds lags 2..kLA
+constexpr int kHB = 8;                          // history loads per lane in flight together
+// inputs of one step of the window form: 4H + 4 blocks and 2(2H + 1) partial right-hand
+// sides, at most kMaxInLane per lane (eight slots)
+constexpr int kMaxIn = 4 * kWinMaxH + 4 + 2 * (2 * kWinMaxH + 1);
+constexpr int kMaxInLane = (kMaxIn + 7) / 8;
+constexpr int kCausalThreads = 192;             // warp 0, four history warps, one idle
 }
 
 // Flags between the warps of one CTA (shared memory, CTA-scope release/acquire).
@@ -966,24 +973,83 @@ __device__ __forceinline__ bool cta_wait_ge(const int* flag, int target, const i
     return true;
 }
 
-template <bool WIN>
-__global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweeps,
-                                                     const double2* __restrict__ cols,
-                                                     const double2* __restrict__ lag0,
-                                                     const double2* __restrict__ y,
-                                                     double2* __restrict__ x,
-                                                     double2* __restrict__ xsw, int* progress,
-                                                     int* abortf, int* status,
-                                                     const InstInfo* __restrict__ inst,
-                                                     const int* __restrict__ if_inst, int k0,
-                                                     int nif_all, const double2* __restrict__ Gw,
-                                                     int H) {
-    __shared__ double2 hp[3][4];   // lags >= 3 of step m (slot m % 3), one per source
-    __shared__ int s_xown;         // x_0 .. x_{s_xown - 1} of this interface are written
-    __shared__ int s_hused;        // warp 0 has consumed the history sums of steps <= s_hused
-    __shared__ int s_hdone[4];     // history warp e has filled the slots of steps <= s_hdone[e]
-    __shared__ int s_stop;         // warp 0 left its loop early (timeout or abort)
-    // global interface kg (progress, sweep values, lag-0 blocks); local k within its
+// Relaxed gpu-scope 16-byte load / store (two single-copy-atomic 8-byte words).
+__device__ __forceinline__ double2 ld_relaxed2(const double2* p) {
+    double a, b;
+    asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(a), "=d"(b) : "l"(p));
+    return make_double2(a, b);
+}
+__device__ __forceinline__ bool is_set(double2 v) {
+    return __double_as_longlong(v.x) != kUnsetBits && __double_as_longlong(v.y) != kUnsetBits;
+}
+__device__ __forceinline__ double never_unset(double v) {
+    return __double_as_longlong(v) == kUnsetBits ? __longlong_as_double(0x7ff8000000000000LL) : v;
+}
+__device__ __forceinline__ void st_relaxed2(double2* p, double2 v) {
+    asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(never_unset(v.x)),
+                 "d"(never_unset(v.y))
+                 : "memory");
+}
+__device__ __forceinline__ void st_relaxed1(double* p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(never_unset(v)) : "memory");
+}
+// One more round of a bounded poll: false (after raising the abort flag on timeout)
+// when the bound has run out or another CTA aborted.
+__device__ __forceinline__ bool poll_tick(long long& polls, int* abortf, int* status,
+                                          long long lim) {
+    ++polls;
+    if ((polls & 31) == 0 && load_relaxed(abortf) != 0) return false;
+    if (polls > lim) {
+        atomicOr(status, ST_TIMEOUT);
+        store_release(abortf, 1);
+        return false;
+    }
+    if (polls > kSpinPolls) __nanosleep(64);
+    return true;
+}
+
+// Source e of interface i (N, nt, cols and x of its instance):
+//  e=0: r_i     <- X^{i+1,1} l_{i+1} (block 2i+1)   e=1: r_i <- X^{i+1,2} r_{i+1} (block 2i+2)
+//  e=2: l_{i+1} <- X^{i,4}   r_i     (block 2i)     e=3: l_{i+1} <- X^{i,3} l_i (block 2i-1)
+// has: the source exists; cc: its Toeplitz column; xin: its block of x.
+__device__ __forceinline__ void causal_source(int N, int nt, const double2* cols, double2* x,
+                                              int i, int e, bool& has, const double2*& cc,
+                                              double2*& xin) {
+    int cslot = 0, inb = 0;
+    has = true;
+    if (e == 0) { cslot = 4 * (i + 1) + 0; inb = 2 * i + 1; }
+    if (e == 1) { has = (i + 1 <= N - 2); cslot = 4 * (i + 1) + 1; inb = 2 * i + 2; }
+    if (e == 2) { cslot = 4 * i + 3; inb = 2 * i; }
+    if (e == 3) { has = (i >= 1); cslot = 4 * i + 2; inb = 2 * i - 1; }
+    cc = has ? cols + (size_t)cslot * nt : nullptr;
+    xin = has ? x + (size_t)inb * nt : nullptr;
+}
+
+// One CTA of kCausalThreads per interface: warp 0 solves, warps 1, 2, 3 and 5 form the
+// history sums of sources 0..3 (warp 4, which would share warp 0's sub-partition, leaves at
+// once).  cols_smem: the dynamic shared memory holds the four Toeplitz columns (4 nt).
+template <bool FLAG>
+__global__ void __launch_bounds__(kCausalThreads, 4) k_causal_wave(
+    int N, int nt, int sweeps, const double2* __restrict__ cols, const double2* __restrict__ lag0,
+    const double2* __restrict__ y, double2* x, double2* xsw, double2* P, int* progress,
+    int* abortf, int* status, const InstInfo* __restrict__ inst, const int* __restrict__ if_inst,
+    int k0, int nif_all, const double2* __restrict__ Gw, int H, int cols_smem) {
+    // lookahead: warp 0 adds the lags 2..LA itself, the history warps the lags > LA
+    constexpr int LA = FLAG ? kLA : 2;
+    extern __shared__ double2 s_cols[];  // [4][nt] when cols_smem
+    __shared__ double2 hp[LA + 1][4];   // lags > LA of step t (slot t % (LA + 1)), per source
+    __shared__ int s_xown;              // x_0 .. x_{s_xown - 1} of this interface are written
+    __shared__ int s_hused;             // warp 0 has consumed the history sums of steps <= s_hused
+    __shared__ int s_hdone[4];          // history warp e has filled the slots of steps <= s_hdone[e]
+    __shared__ int s_stop;              // warp 0 left its loop (done, timeout or abort)
+    // warp 0 of the value-polling form: its inputs (type, offset, per-lane weights) and
+    // the step's recent values
+    __shared__ int s_itype[FLAG ? kMaxIn : 1];
+    __shared__ long long s_ioff[FLAG ? kMaxIn : 1];
+    __shared__ double2 s_wq[FLAG ? kMaxIn : 1][4];
+    __shared__ double2 s_xo[2], s_P[2], s_nb[2], s_l3[4], s_c23[2][4];
+    __shared__ int s_nbin[2];
+    // global interface kg (sweep values, progress, lag-0 blocks); local k within its
     // instance (blocks, columns)
     const int kg = k0 + blockIdx.x;
     const long long lim = d_wait_poll_limit;
@@ -997,224 +1063,419 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
         cols += I.coff;
         y += I.foff;
         x += I.foff;
+        if (P) P += I.foff;
     }
     const bool has_l = (k >= 1), has_r = (k + 1 <= N - 2);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double2 zero = make_double2(0.0, 0.0);
-    // source e of interface i:
-    //  e=0: r_i     <- X^{i+1,1} l_{i+1} (block 2i+1)   e=1: r_i <- X^{i+1,2} r_{i+1} (block 2i+2)
-    //  e=2: l_{i+1} <- X^{i,4}   r_i     (block 2i)     e=3: l_{i+1} <- X^{i,3} l_i (block 2i-1)
-    auto source = [&](int i, int e, bool& has, const double2*& cc, const double2*& xin) {
-        int cslot = 0, inb = 0;
-        has = true;
-        if (e == 0) { cslot = 4 * (i + 1) + 0; inb = 2 * i + 1; }
-        if (e == 1) { has = (i + 1 <= N - 2); cslot = 4 * (i + 1) + 1; inb = 2 * i + 2; }
-        if (e == 2) { cslot = 4 * i + 3; inb = 2 * i; }
-        if (e == 3) { has = (i >= 1); cslot = 4 * i + 2; inb = 2 * i - 1; }
-        cc = has ? cols + (size_t)cslot * nt : nullptr;
-        xin = has ? x + (size_t)inb * nt : nullptr;
-    };
-    if (threadIdx.x < 12) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
-    if (threadIdx.x < 4) s_hdone[threadIdx.x] = 2;   // steps 0..2 have no lag >= 3 term
+    if (threadIdx.x < 4 * (LA + 1)) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
+    if (threadIdx.x < 4) s_hdone[threadIdx.x] = LA;   // steps 0..LA have no lag > LA
     if (threadIdx.x == 0) {
         s_xown = 0;
-        s_hused = -1;
+        s_hused = 0;
         s_stop = 0;
     }
     __syncthreads();
 
-    // ---- history warps: lags >= 3 of step m + 2 from the values s <= m - 1 ----------
+    // ---- history warps: the lags > LA of step m + LA from the values s <= m - 1 -------
     // Sources 0 and 2 are this interface's own blocks (written by warp 0: wait on
-    // s_xown); sources 1 and 3 are the neighbours' (wait on their progress counters,
-    // read through L2).  A slot is refilled only after warp 0 has consumed it.
+    // s_xown); sources 1 and 3 are the neighbours'.  A slot is refilled only after warp 0
+    // has consumed the step it held (m - 1).
+    if (w == 4) return;
     if (w >= 1) {
-        const int e = w - 1;
+        const int e = (w == 5) ? 3 : w - 1;
         bool has = false;
         const double2* cc = nullptr;
-        const double2* xin = nullptr;
-        source(k, e, has, cc, xin);
+        double2* xin = nullptr;
+        causal_source(N, nt, cols, x, k, e, has, cc, xin);
+        if (cols_smem && has) {   // this source's column into shared memory
+            for (int j = lane; j < nt; j += 32) s_cols[(size_t)e * nt + j] = __ldg(cc + j);
+            __syncwarp();
+            cc = s_cols + (size_t)e * nt;
+        }
         const bool own = (e == 0 || e == 2);
         const int nb = (e == 1) ? kg + 1 : kg - 1;
-        for (int m = 1; m + 2 < nt; ++m) {
-            bool ok = cta_wait_ge(&s_hused, m - 1, &s_stop);
-            if (ok && has) {
-                if (own) {
-                    ok = cta_wait_ge(&s_xown, m, &s_stop);
-                } else if (lane == 0) {
-                    // x_{<= m-1} of the neighbour: progress >= m + 1 (window form) or
-                    // >= m (sweeps + 1) (sweep form)
-                    ok = wait_one(nb, WIN ? m + 1 : m * (sweeps + 1), progress, abortf, status,
-                                  lim);
-                }
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
+        for (int m = 1; m + LA < nt; ++m) {
+            bool ok = __all_sync(0xffffffffu, cta_wait_ge(&s_hused, m - 1, &s_stop));
             if (!ok) break;
             double2 a0 = zero, a1 = zero;
             if (has) {
-                int s = lane;
-                for (; s + 32 < m; s += 64) {
-                    a0 = cfma(__ldg(cc + m + 2 - s), __ldcg(xin + s), a0);
-                    a1 = cfma(__ldg(cc + m + 2 - s - 32), __ldcg(xin + s + 32), a1);
+                if (own) {
+                    ok = __all_sync(0xffffffffu, cta_wait_ge(&s_xown, m, &s_stop));
+                } else if (!FLAG) {
+                    // x_{<= m-1} of the neighbour: progress >= m (sweeps + 1)
+                    bool o = true;
+                    if (lane == 0) o = wait_one(nb, m * (sweeps + 1), progress, abortf, status, lim);
+                    ok = __shfl_sync(0xffffffffu, o, 0);
+                } else {
+                    // the neighbour's newest value first (its values are read as written)
+                    long long polls = 0;
+                    bool o = true;
+                    if (lane == 0)
+                        while (!is_set(ld_relaxed2(xin + m - 1)))
+                            if (!poll_tick(polls, abortf, status, lim)) {
+                                o = false;
+                                break;
+                            }
+                    ok = __shfl_sync(0xffffffffu, o, 0);
                 }
-                if (s < m) a0 = cfma(__ldg(cc + m + 2 - s), __ldcg(xin + s), a0);
+                if (!ok) break;
+                if (own || !FLAG) {
+                    for (int base = 0; base < m; base += 32 * kHB) {
+                        double2 u[kHB];
+#pragma unroll
+                        for (int b = 0; b < kHB; ++b) {
+                            const int s = base + 32 * b + lane;
+                            u[b] = (s < m) ? __ldcg(xin + s) : zero;
+                        }
+#pragma unroll
+                        for (int b = 0; b < kHB; ++b) {
+                            const int s = base + 32 * b + lane;
+                            if (s < m) {
+                                if (b & 1) a1 = cfma(cc[m + LA - s], u[b], a1);
+                                else a0 = cfma(cc[m + LA - s], u[b], a0);
+                            }
+                        }
+                    }
+                } else {
+                    // the whole sum with every value checked, repeated until all were set;
+                    // kHB loads per lane issued together (one L2 round trip per 32 kHB values)
+                    long long polls = 0;
+                    while (true) {
+                        bool all = true;
+                        a0 = a1 = zero;
+                        for (int base = 0; base < m; base += 32 * kHB) {
+                            double2 u[kHB];
+#pragma unroll
+                            for (int b = 0; b < kHB; ++b) {
+                                const int s = base + 32 * b + lane;
+                                u[b] = (s < m) ? ld_relaxed2(xin + s) : zero;
+                            }
+#pragma unroll
+                            for (int b = 0; b < kHB; ++b) {
+                                const int s = base + 32 * b + lane;
+                                if (s < m) {
+                                    all = all && is_set(u[b]);
+                                    if (b & 1) a1 = cfma(cc[m + LA - s], u[b], a1);
+                                    else a0 = cfma(cc[m + LA - s], u[b], a0);
+                                }
+                            }
+                        }
+                        if (__all_sync(0xffffffffu, all)) break;
+                        bool o = true;
+                        if (lane == 0) o = poll_tick(polls, abortf, status, lim);
+                        if (!__shfl_sync(0xffffffffu, o, 0)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (!ok) break;
+                }
             }
             const double2 acc = warp_sum(cadd(a0, a1));
             if (lane == 0) {
-                hp[(m + 2) % 3][e] = acc;
-                cta_store_release(&s_hdone[e], m + 2);
+                hp[(m + LA) % (LA + 1)][e] = acc;
+                cta_store_release(&s_hdone[e], m + LA);
             }
         }
         return;
     }
 
     // ---- warp 0 ----------------------------------------------------------------------
-    // lag-2 data of this interface's four sources (lane 0 forms the published sums)
-    bool hs[4] = {false, false, false, false};
-    const double2* xs2[4] = {nullptr, nullptr, nullptr, nullptr};
-    double2 c2e[4] = {zero, zero, zero, zero};
+    // Lane 0 forms the history of step t for this interface: the warps' lags > LA plus
+    // the lags lo..LA, s_cl[j - 2][e] x_{t-j} of source e, with x_{t-j} = s_xl[j - lo][e]
+    // (the caller keeps s_xl[0] = x_{n-2} at the top of step n).  Both tables in shared
+    // memory, filled by lane 0.
+    __shared__ double2 s_cl[LA - 1][4];
+    __shared__ double2 s_xl[LA - 1][4];
+    double2* xsrc[4] = {nullptr, nullptr, nullptr, nullptr};
     if (lane == 0) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
+            bool has;
             const double2* cc;
-            source(k, e, hs[e], cc, xs2[e]);
-            if (hs[e] && nt > 2) c2e[e] = cc[2];
+            causal_source(N, nt, cols, x, k, e, has, cc, xsrc[e]);
+            for (int j = 2; j <= LA; ++j)
+                s_cl[j - 2][e] = (has && nt > j) ? cc[j] : zero;
+            for (int j = 0; j < LA - 1; ++j) s_xl[j][e] = zero;
         }
     }
-    // history sums of step m for this interface, lags >= 2 (lane 0; waits on the warps)
-    // xm2: x_{m-2} of the sources when the caller has loaded them (else NULL)
-    auto hist_ge2 = [&](int m, const double2* xm2, double2& h0, double2& h1, double2& h2,
-                        double2& h3) -> bool {
+    __syncwarp();
+    auto hist = [&](int t, int lo, double2 (&h)[4]) -> bool {
         bool ok = true;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) ok = ok && cta_wait_ge(&s_hdone[e], m, &s_stop);
+        for (int e = 0; e < 4; ++e) ok = ok && cta_wait_ge(&s_hdone[e], t, &s_stop);
         if (!ok) return false;
-        double2 h[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            h[e] = hp[m % 3][e];
-            if (m >= 2 && hs[e])
-                h[e] = cfma(c2e[e], xm2 ? xm2[e] : __ldcg(xs2[e] + m - 2), h[e]);
+            h[e] = hp[t % (LA + 1)][e];
+#pragma unroll
+            for (int j = 2; j <= LA; ++j)
+                if (j >= lo && t >= j) h[e] = cfma(s_cl[j - 2][e], s_xl[j - lo][e], h[e]);
         }
-        h0 = h[0];
-        h1 = h[1];
-        h2 = h[2];
-        h3 = h[3];
-        cta_store_release(&s_hused, m);
+        cta_store_release(&s_hused, t);
         return true;
+    };
+    // lane 0: a new x_{n-1} of the sources enters the recent values
+    auto push_recent = [&](const double2 (&v)[4]) {
+#pragma unroll
+        for (int j = LA - 2; j >= 1; --j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) s_xl[j][e] = s_xl[j - 1][e];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s_xl[0][e] = v[e];
     };
     auto fail_local = [&]() {   // a wait between this CTA's warps ran out: leave everywhere
         atomicOr(status, ST_TIMEOUT);
         store_release(abortf, 1);
     };
 
-    if constexpr (WIN) {
-        // ---- window form (H >= 1) ---------------------------------------------
-        const int d = lane - (H + 1);
-        const int i = k + d;                                   // this lane's interface
-        const bool inwin = (d >= -H && d <= H && i >= 0 && i <= N - 2);
-        const bool waits = (d != 0 && d >= -H - 1 && d <= H + 1 && i >= 0 && i <= N - 2);
-        // lane data for R_n(i): the lag-1 coefficients and source rows of its four
-        // sources (the order of `source`; a missing source keeps a zero coefficient)
-        const double2 *xs0 = x, *xs1 = x, *xs2w = x, *xs3 = x;
-        double2 c10 = zero, c11 = zero, c12 = zero, c13 = zero;
-        double2 g0 = zero, g1 = zero, g2 = zero, g3 = zero;
-        const bool h1 = inwin && (i + 1 <= N - 2), h3 = inwin && (i >= 1);
-        if (inwin) {
-            xs0 = x + (size_t)(2 * i + 1) * nt;
-            xs2w = x + (size_t)(2 * i) * nt;
-            if (h1) xs1 = x + (size_t)(2 * i + 2) * nt;
-            if (h3) xs3 = x + (size_t)(2 * i - 1) * nt;
-            if (nt > 1) {
-                c10 = cols[(size_t)(4 * (i + 1) + 0) * nt + 1];
-                c12 = cols[(size_t)(4 * i + 3) * nt + 1];
-                if (h1) c11 = cols[(size_t)(4 * (i + 1) + 1) * nt + 1];
-                if (h3) c13 = cols[(size_t)(4 * i + 2) * nt + 1];
+    if constexpr (FLAG) {
+        // ---- the values are the hand-off (window H >= 0) --------------------------------
+        // x_n(k), two blocks (outputs o = 0: block 2k, o = 1: block 2k+1), is linear in the
+        // inputs of step n: x_{n-1} of the window's blocks b = 2(k-H)-1 .. 2(k+H)+2 and
+        // the partial right-hand sides P_n(k+d)[row], |d| <= H:
+        //   x_n(k)[o] = sum_inputs w_o u,   w_o = G_{k,k+d}[o][row] for P_n(k+d)[row], and
+        //   for a block b the sum of G_{k,i}[o][row] c1 over the sources (i, row, e) that
+        //   read b, c1 their lag-1 coefficient.
+        // On this part every FP64 warp instruction costs the same whatever the number of
+        // active lanes, so the arithmetic is spread over the lanes: q = lane >> 3 picks a
+        // real output (o = q >> 1, real or imaginary part q & 1), s = lane & 7 a slot that
+        // takes the inputs s, s + 8, ...; a three-level butterfly over the slots sums.
+        // P_{n+1}(k) (y_{n+1}, the history warps' lags > LA, lags 2..3) is formed the same
+        // way, row = q >> 1, one term per slot.
+        const int q = lane >> 3, sl = lane & 7, o = q >> 1, part = q & 1;
+        const int ilo = max(k - H, 0), ihi = min(k + H, N - 2);
+        const int blo = max(2 * (k - H) - 1, 0), bhi = min(2 * (k + H) + 2, 2 * N - 3);
+        const int nxin = bhi - blo + 1, nin = nxin + 2 * (ihi - ilo + 1);
+        auto G = [&](int i, int oo, int row) {   // (A0^{-1})_{k,i}[oo][row]
+            return Gw[((size_t)kg * (2 * H + 1) + (i - k) + H) * 4 + oo * 2 + row];
+        };
+        auto c1of = [&](int i, int e) {          // lag-1 coefficient of source e of i
+            bool has;
+            const double2* cc;
+            double2* xi;
+            causal_source(N, nt, cols, x, i, e, has, cc, xi);
+            return (has && nt > 1) ? cc[1] : zero;
+        };
+        for (int j = lane; j < nin; j += 32) {
+            double2 w0 = zero, w1 = zero;
+            int type;
+            long long off;
+            if (j < nxin) {
+                const int b = blo + j;
+                type = (b == 2 * k) ? 2 : (b == 2 * k + 1) ? 3 : 0;
+                off = (long long)b * nt;
+                // readers of block b: (i, row, e) = (b/2, 1, 2), (b/2 - 1, 0, 1) for even b;
+                // ((b-1)/2, 0, 0), ((b-1)/2 + 1, 1, 3) for odd b
+                const int i1 = (b & 1) ? (b - 1) / 2 : b / 2;
+                const int i2 = (b & 1) ? i1 + 1 : i1 - 1;
+                const int r1 = (b & 1) ? 0 : 1, r2 = 1 - r1;
+                const int e1 = (b & 1) ? 0 : 2, e2 = (b & 1) ? 3 : 1;
+                if (i1 >= ilo && i1 <= ihi) {
+                    const double2 c = c1of(i1, e1);
+                    w0 = cfma(G(i1, 0, r1), c, w0);
+                    w1 = cfma(G(i1, 1, r1), c, w1);
+                }
+                if (i2 >= ilo && i2 <= ihi) {
+                    const double2 c = c1of(i2, e2);
+                    w0 = cfma(G(i2, 0, r2), c, w0);
+                    w1 = cfma(G(i2, 1, r2), c, w1);
+                }
+            } else {
+                const int i = ilo + (j - nxin) / 2, row = (j - nxin) & 1;
+                type = (i == k) ? 4 + row : 1;
+                off = (long long)(2 * i + row) * nt;
+                w0 = G(i, 0, row);
+                w1 = G(i, 1, row);
             }
-            const double2* g = Gw + ((size_t)kg * (2 * H + 1) + d + H) * 4;
-            g0 = g[0];
-            g1 = g[1];
-            g2 = g[2];
-            g3 = g[3];
+            s_itype[j] = type;
+            s_ioff[j] = off;
+            // lane q's share: a1 b1 + a2 b2 with (b1, b2) = (re, im) of the input for a
+            // real part, (im, re) for an imaginary part
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const double2 ww = (qq >> 1) ? w1 : w0;
+                s_wq[j][qq] = make_double2(ww.x, (qq & 1) ? ww.y : -ww.y);
+            }
         }
-        // P_0(k) = y_0(k): no history at step 0
+        if (lane < 4) {
+            bool has;
+            const double2* cc;
+            double2* xi;
+            causal_source(N, nt, cols, x, k, lane, has, cc, xi);
+            s_c23[0][lane] = (has && nt > 2) ? cc[2] : zero;
+            s_c23[1][lane] = (has && nt > 3) ? cc[3] : zero;
+            s_l3[lane] = zero;
+        }
+        if (lane < 2) {
+            s_xo[lane] = zero;
+            s_nb[lane] = zero;
+            const double2 y0 = y[(size_t)(2 * k + lane) * nt];   // P_0(k) = y_0(k)
+            s_P[lane] = y0;
+            if (H > 0 && publish) st_relaxed2(P + (size_t)(2 * k + lane) * nt, y0);
+        }
         if (lane == 0) {
-            xsw[2 * kg] = y[(size_t)(2 * k) * nt];
-            xsw[2 * kg + 1] = y[(size_t)(2 * k + 1) * nt];
-            if (publish) store_release(progress + (size_t)kg * kProgStride, 1);
+            // inputs that are the neighbours' source blocks (lag 2 of P_{n+1})
+            s_nbin[0] = has_r ? 2 * k + 2 - blo : -1;
+            s_nbin[1] = has_l ? 2 * k - 1 - blo : -1;
         }
         __syncwarp();
+        // lanes sl == 0: y_{n+1}(k)[row] of their P_{n+1} part, one step ahead
+        double yv = 0.0;
+        if (sl == 0 && nt > 1) {
+            const double2 yy = y[(size_t)(2 * k + o) * nt + 1];
+            yv = part ? yy.y : yy.x;
+        }
         for (int n = 0; n < nt; ++n) {
-            bool ok = true;
-            if (waits) ok = wait_one(kg + d, n + 1, progress, abortf, status, lim);
-            ok = __all_sync(0xffffffffu, ok);                  // x_{<n}, P_n visible
-            if (!ok) break;
-            // the next right-hand side's data and its lag-2 terms (x_{n-1} of the four
-            // sources), loaded now, off the critical path
-            double2 yn1a = zero, yn1b = zero, x2[4] = {zero, zero, zero, zero};
-            if (lane == 0 && n + 1 < nt) {
-                yn1a = y[(size_t)(2 * k) * nt + n + 1];
-                yn1b = y[(size_t)(2 * k + 1) * nt + n + 1];
-                if (n >= 1) {
+            // ---- this lane's inputs: shared ones now, global ones polled until set
+            double2 u[kMaxInLane];
+            unsigned need = 0;
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (hs[e]) x2[e] = __ldcg(xs2[e] + n - 1);
-                }
-            }
-            double2 t1 = zero, t2 = zero;
-            if (inwin) {
-                const double2* P = xsw + (size_t)(n & 1) * 2 * nif_all + 2 * (kg + d);
-                double2 r1 = P[0], r2 = P[1];
-                if (n >= 1) {
-                    r1 = cfma(c10, xs0[n - 1], r1);
-                    if (h1) r1 = cfma(c11, xs1[n - 1], r1);
-                    r2 = cfma(c12, xs2w[n - 1], r2);
-                    if (h3) r2 = cfma(c13, xs3[n - 1], r2);
-                }
-                t1 = cfma(g0, r1, cmul(g1, r2));
-                t2 = cfma(g2, r1, cmul(g3, r2));
-            }
-            const double2 z1 = warp_sum(t1), z2 = warp_sum(t2);
-            int go = 1;
-            if (lane == 0) {
-                x[(size_t)(2 * k) * nt + n] = z1;
-                x[(size_t)(2 * k + 1) * nt + n] = z2;
-                cta_store_release(&s_xown, n + 1);
-                if (n + 1 < nt) {
-                    double2 q0, q1, q2, q3;
-                    if (hist_ge2(n + 1, x2, q0, q1, q2, q3)) {
-                        double2* P = xsw + (size_t)((n + 1) & 1) * 2 * nif_all + 2 * kg;
-                        P[0] = cadd(yn1a, cadd(q0, q1));
-                        P[1] = cadd(yn1b, cadd(q2, q3));
+            for (int t = 0; t < kMaxInLane; ++t) {
+                const int j = sl + 8 * t;
+                u[t] = zero;
+                if (j < nin) {
+                    const int ty = s_itype[j];
+                    if (ty == 0) {
+                        if (n >= 1) need |= 1u << t;
+                    } else if (ty == 1) {
+                        need |= 1u << t;
+                    } else if (ty <= 3) {
+                        u[t] = s_xo[ty - 2];      // x_{n-1} of this interface (0 at n = 0)
                     } else {
-                        go = 0;
-                        fail_local();
+                        u[t] = s_P[ty - 4];
                     }
                 }
-                if (go && publish) store_release(progress + (size_t)kg * kProgStride, n + 2);   // x_n and P_{n+1}
             }
-            go = __shfl_sync(0xffffffffu, go, 0);
-            if (!go) break;
+            bool ok = true;
+            long long polls = 0;
+            while (need) {
+#pragma unroll
+                for (int t = 0; t < kMaxInLane; ++t) {
+                    if (need & (1u << t)) {
+                        const int j = sl + 8 * t;
+                        const double2* p = (s_itype[j] == 0) ? x + s_ioff[j] + n - 1
+                                                              : P + s_ioff[j] + n;
+                        u[t] = ld_relaxed2(p);
+                        if (is_set(u[t])) need &= ~(1u << t);
+                    }
+                }
+                if (need && !poll_tick(polls, abortf, status, lim)) {
+                    ok = false;
+                    break;
+                }
+            }
+            if (!__all_sync(0xffffffffu, ok)) break;
+            // ---- x_n(k)
+            double acc = 0.0;
+#pragma unroll
+            for (int t = 0; t < kMaxInLane; ++t) {
+                const int j = sl + 8 * t;
+                if (j < nin) {
+                    const double2 a = s_wq[j][q];
+                    acc = fma(a.x, part ? u[t].y : u[t].x, fma(a.y, part ? u[t].x : u[t].y, acc));
+                }
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            if (sl == 0 && publish)
+                st_relaxed1(reinterpret_cast<double*>(x + (size_t)(2 * k + o) * nt + n) + part,
+                            acc);
+            // x_{n-1} of the neighbours' source blocks, for the lag-2 terms
+            if (q == 0 && n >= 1) {
+#pragma unroll
+                for (int t = 0; t < kMaxInLane; ++t) {
+                    const int j = sl + 8 * t;
+                    if (j == s_nbin[0]) s_nb[0] = u[t];
+                    if (j == s_nbin[1]) s_nb[1] = u[t];
+                }
+            }
+            __syncwarp();
+            // ---- P_{n+1}(k): row o (sources ea, eb), one term per slot
+            double accp = 0.0;
+            if (n + 1 < nt) {
+                const int ea = o ? 2 : 0, eb = o ? 3 : 1;
+                if (sl == 0) {
+                    accp = yv;
+                } else if (sl <= 2) {
+                    const int e = (sl == 1) ? ea : eb;
+                    if (cta_wait_ge(&s_hdone[e], n + 1, &s_stop)) {
+                        const double2 h = hp[(n + 1) % (LA + 1)][e];
+                        accp = part ? h.y : h.x;
+                    } else {
+                        ok = false;
+                    }
+                } else if (sl <= 6) {
+                    const int e = (sl & 1) ? ea : eb;       // sl 3, 5: ea; 4, 6: eb
+                    const int lag = (sl <= 4) ? 0 : 1;      // lag 2 or lag 3
+                    const double2 c = s_c23[lag][e];
+                    // x_{n-1} (lag 2) or x_{n-2} (lag 3) of source e
+                    const double2 v = lag ? s_l3[e]
+                                          : (e == 0) ? s_xo[1] : (e == 2) ? s_xo[0]
+                                          : (e == 1) ? s_nb[0] : s_nb[1];
+                    accp = fma(c.x, part ? v.y : v.x, (part ? c.y : -c.y) * (part ? v.x : v.y));
+                }
+                accp += __shfl_xor_sync(0xffffffffu, accp, 1);
+                accp += __shfl_xor_sync(0xffffffffu, accp, 2);
+                accp += __shfl_xor_sync(0xffffffffu, accp, 4);
+                if (sl == 0 && H > 0 && publish)
+                    st_relaxed1(reinterpret_cast<double*>(P + (size_t)(2 * k + o) * nt + n + 1) +
+                                    part,
+                                accp);
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) fail_local();
+                break;
+            }
+            // ---- hand the step over: recent values, own x_n and P_{n+1}, the CTA flags
+            if (lane == 0 && n >= 1) {
+                s_l3[0] = s_xo[1];
+                s_l3[2] = s_xo[0];
+                s_l3[1] = s_nb[0];
+                s_l3[3] = s_nb[1];
+            }
+            __syncwarp();
+            if (sl == 0) {
+                double* xo = reinterpret_cast<double*>(&s_xo[o]);
+                double* po = reinterpret_cast<double*>(&s_P[o]);
+                xo[part] = acc;
+                po[part] = accp;
+                if (n + 2 < nt) {
+                    const double2 yy = y[(size_t)(2 * k + o) * nt + n + 2];
+                    yv = part ? yy.y : yy.x;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                cta_store_release(&s_hused, n + 1);
+                cta_store_release(&s_xown, n + 1);
+            }
         }
     } else {
-        // ---- sweep form (H == 0) -------------------------------------------------
+        // ---- sweep form (sweeps >= 1) ----------------------------------------------
+        // Progress is counted in sub-steps: step n, sweep sw is complete when
+        // progress >= n (S+1) + sw + 1, S = sweeps; the step's values x_n are ordered
+        // by progress = (n+1)(S+1).
         const int S1 = sweeps + 1;
-        const double2* cs[4] = {nullptr, nullptr, nullptr, nullptr};
-        const double2* xs[4] = {nullptr, nullptr, nullptr, nullptr};
-        bool hsw[4] = {false, false, false, false};
         double2 D00 = zero, D01 = zero, D10 = zero, D11 = zero, cB0 = zero, cD0 = zero;
         double2 c1[4] = {zero, zero, zero, zero};
+        bool hs[4] = {false, false, false, false};
         const bool solver = (lane == 0);
         if (solver) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) source(k, e, hsw[e], cs[e], xs[e]);
             D00 = lag0[kg * 4 + 0];
             D01 = lag0[kg * 4 + 1];
             D10 = lag0[kg * 4 + 2];
             D11 = lag0[kg * 4 + 3];
-            cB0 = hsw[1] ? cs[1][0] : zero;
-            cD0 = hsw[3] ? cs[3][0] : zero;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) c1[e] = (hsw[e] && nt > 1) ? cs[e][1] : zero;
+            for (int e = 0; e < 4; ++e) {
+                const double2* cc;
+                causal_source(N, nt, cols, x, k, e, hs[e], cc, xsrc[e]);
+                if (hs[e] && nt > 1) c1[e] = cc[1];
+                if (hs[e] && e == 1) cB0 = cc[0];
+                if (hs[e] && e == 3) cD0 = cc[0];
+            }
         }
         for (int n = 0; n < nt; ++n) {
             // lanes 0 and 1 wait for the left and right neighbours' values < n
@@ -1225,15 +1486,19 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
             if (!ok) break;
             int go = 1;
             if (solver) {
-                // history of step n: lags >= 2 (the warps' sums and lag 2) + lag 1
+                // x_{n-1} of the sources (the lag-1 terms; lag 2 at the next step)
+                double2 x1[4] = {zero, zero, zero, zero};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (n >= 1 && hs[e]) x1[e] = __ldcg(xsrc[e] + n - 1);
                 double2 h[4];
-                if (!hist_ge2(n, nullptr, h[0], h[1], h[2], h[3])) {
+                if (!hist(n, 2, h)) {
                     go = 0;
                     fail_local();
                 } else {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (n >= 1 && hsw[e]) h[e] = cfma(c1[e], xs[e][n - 1], h[e]);
+                    for (int e = 0; e < 4; ++e) h[e] = cfma(c1[e], x1[e], h[e]);
+                    push_recent(x1);
                     const double2 r1 = cadd(y[(size_t)(2 * k) * nt + n], cadd(h[0], h[1]));
                     const double2 r2 = cadd(y[(size_t)(2 * k + 1) * nt + n], cadd(h[2], h[3]));
                     double2 z1 = cfma(D01, r2, cmul(D00, r1));
@@ -1250,8 +1515,8 @@ __global__ void __launch_bounds__(160, 5) k_causal_wave(int N, int nt, int sweep
                             break;
                         }
                         const double2 xr = has_r ? out[2 * (kg + 1)] : zero;       // r_{k+1}
-                        const double2 xl = has_l ? out[2 * (kg - 1) + 1] : zero;   // l_k
-                        const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xl, r2);
+                        const double2 xlk = has_l ? out[2 * (kg - 1) + 1] : zero;  // l_k
+                        const double2 e1 = cfma(cB0, xr, r1), e2 = cfma(cD0, xlk, r2);
                         z1 = cfma(D01, e2, cmul(D00, e1));
                         z2 = cfma(D11, e2, cmul(D10, e1));
                     }
@@ -1287,27 +1552,69 @@ size_t swr_causal_scratch_bytes(int N) {
 
 // Interfaces one cooperative launch can hold (all CTAs resident at once).
 int swr_causal_capacity(int) {
-    int dev = 0, nsm = 0, per = 0;
+    int dev = 0, nsm = 0, per = 0, perf = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_causal_wave<false>, 160, 0) !=
-            cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_causal_wave<false>,
+                                                      kCausalThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perf, k_causal_wave<true>,
+                                                      kCausalThreads, 0) != cudaSuccess)
         return 0;
-    int perw = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perw, k_causal_wave<true>, 160, 0) !=
-        cudaSuccess)
-        return 0;
-    return nsm * std::min(per, perw);
+    return nsm * std::min(per, perf);
 }
 
-// Single instance (inst == NULL): interfaces 0..N-2.  Batched plan: interfaces
-// k0 .. k0+nif_group-1 of the nif_total, whole instances only (a wave never
-// waits on an interface outside its instance).
+namespace {
+// Dynamic shared memory for a launch of ncta CTAs of kernel fn: as much as lets no more
+// than ceil(ncta / SMs) CTAs share an SM (the history sums of CTAs on one SM share its
+// FP64 pipes, so the CTAs are spread as far as the count allows), and the use made of
+// it: the four Toeplitz columns (4 nt complex) when they fit.  0 when nothing is gained.
+size_t causal_dyn_smem(const void* fn, int ncta, int nt, int* cols_smem) {
+    *cols_smem = 0;
+    int dev = 0, nsm = 0, smem_sm = 0, smem_optin = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+            cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess || nsm <= 0)
+        return 0;
+    const int per_sm = (ncta + nsm - 1) / nsm;
+    long long dyn = (long long)smem_sm / per_sm - reserved - (long long)fa.sharedSizeBytes;
+    dyn = std::min<long long>(dyn, (long long)smem_optin - (long long)fa.sharedSizeBytes);
+    dyn = (dyn / 1024) * 1024;
+    const long long need_cols = 4LL * nt * (long long)sizeof(double2);
+    if (dyn < 1024) return 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int fit = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, kCausalThreads, (size_t)dyn) !=
+            cudaSuccess ||
+        (long long)fit * nsm < ncta) {
+        cudaGetLastError();
+        return 0;
+    }
+    *cols_smem = (need_cols <= dyn) ? 1 : 0;
+    return (size_t)dyn;
+}
+}  // namespace
+
+// Single instance (inst == NULL): interfaces 0..N-2; x (and P) are preset here.
+// Batched plan: interfaces k0 .. k0+nif_group-1 of the nif_total, whole instances only
+// (a wave never waits on an interface outside its instance); the caller presets the
+// whole of x (and P) to the unset pattern (0xff bytes) before the first group when
+// sweeps == 0 or H >= 1.
 int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, const double2* y,
                       double2* x, int sweeps, void* scratch, int* status, cudaStream_t s,
                       const InstInfo* inst, const int* if_inst, int k0, int nif_group,
-                      int nif_total, const double2* Gw, int H) {
-    if (H < 0 || H > kWinMaxH || (H > 0 && !Gw)) return -2;
+                      int nif_total, const double2* Gw, int H, double2* P) {
+    if (H < 0 || H > kWinMaxH || (H > 0 && (!Gw || !P)) || (H > 0 && sweeps > 0)) return -2;
     const int nif = inst ? nif_total : N - 1;
     const int ncta = inst ? nif_group : N - 1;
     if (!inst) k0 = 0;
@@ -1318,17 +1625,32 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, c
     const int cap = swr_causal_capacity(nt);
     if (cap <= 0) return -1;
     if (ncta > cap) return -2;           // all CTAs must be resident at once
-    // this launch's progress counters and the abort flag start at zero
-    if (cudaMemsetAsync(progress + (size_t)k0 * kProgStride, 0,
-                        sizeof(int) * (size_t)ncta * kProgStride, s) != cudaSuccess ||
-        cudaMemsetAsync(abortf, 0, sizeof(int), s) != cudaSuccess)
-        return -1;
+    const bool flag = (sweeps == 0);
+    if (flag && H == 0) Gw = lag0;       // G_{k,k} = D_k^{-1}: the same [nif][1][4] layout
+    if (cudaMemsetAsync(abortf, 0, sizeof(int), s) != cudaSuccess) return -1;
+    if (flag) {
+        if (!inst) {
+            const size_t bytes = sizeof(double2) * (size_t)(2 * N - 2) * nt;
+            if (cudaMemsetAsync(x, 0xff, bytes, s) != cudaSuccess ||
+                (H > 0 && cudaMemsetAsync(P, 0xff, bytes, s) != cudaSuccess))
+                return -1;
+        }
+    } else if (cudaMemsetAsync(progress + (size_t)k0 * kProgStride, 0,
+                               sizeof(int) * (size_t)ncta * kProgStride, s) != cudaSuccess) {
+        return -1;   // this launch's progress counters start at zero
+    }
+    const void* fn = flag ? (const void*)k_causal_wave<true> : (const void*)k_causal_wave<false>;
+    // batched instances have their own nt: the columns go to shared memory only for one
+    // instance
+    int cols_smem = 0;
+    const size_t dyn = causal_dyn_smem(fn, ncta, nt, &cols_smem);
+    if (inst) cols_smem = 0;
     void* args[] = {(void*)&N, (void*)&nt, (void*)&sweeps, (void*)&cols, (void*)&lag0,
-                    (void*)&y, (void*)&x, (void*)&xsw, (void*)&progress, (void*)&abortf,
-                    (void*)&status, (void*)&inst, (void*)&if_inst, (void*)&k0, (void*)&nif,
-                    (void*)&Gw, (void*)&H};
-    const void* fn = (H > 0) ? (const void*)k_causal_wave<true> : (const void*)k_causal_wave<false>;
-    if (cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(160), args, 0, s) != cudaSuccess)
+                    (void*)&y, (void*)&x, (void*)&xsw, (void*)&P, (void*)&progress,
+                    (void*)&abortf, (void*)&status, (void*)&inst, (void*)&if_inst, (void*)&k0,
+                    (void*)&nif, (void*)&Gw, (void*)&H, (void*)&cols_smem};
+    if (cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(kCausalThreads), args, dyn, s) !=
+        cudaSuccess)
         return -1;
     swr_count_launch(1);
     return 0;

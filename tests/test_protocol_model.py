@@ -4,12 +4,13 @@ The kernel runs one CTA per interface, all resident.  In CTA k, warp 0 at time s
 polls (until they are set) the partial right-hand sides P_n(i) of the interfaces i
 within H and x_{n-1} of their sources (interfaces i-1, i, i+1); it then computes and
 publishes x_n(k), forms P_{n+1}(k) from the history sums of step n+1 and publishes it,
-and at the end of the step releases the consumed history slot and its own x_n.  Every published value is written once into an array preset to
-"unset".  Four history warps per CTA form the sums of the lags > LA of step m + LA from
-the values s <= m - 1 of their source (the CTA's own x, or a neighbour's, polled), and
-hand them over in a ring of LA + 1 slots: a warp refills a slot only when warp 0 has
-consumed the step it held (s_hused >= m - 1), and warp 0 reads step t only when the
-warp has filled it (s_hdone >= t).
+and at the end of the step releases the consumed history slot and its own x_n.  Every
+published value is written once into an array preset to "unset".  Four history warps
+per CTA form the sums of the lags > LA of step m + LA from the values s <= m - 1 of
+their source (the CTA's own x, or a neighbour's, polled), and hand them over in a ring
+of LA + 1 slots: a warp refills a slot only when warp 0 has consumed the step it held
+(s_hused >= m - 1), and warp 0 reads step t only when the warp has filled it
+(s_hdone >= t).
 
 This test runs that protocol as a state machine under many random interleavings (every
 wait, read and write a separate event) and checks that warp 0 always reads the step it

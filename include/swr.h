@@ -157,6 +157,11 @@ typedef struct swr_tuning {
                                 /* a system has <= 993 separators; -1 cluster-wide PCR   */
     int32_t debug;              /* 1: failing CUDA calls (2: also the launch-shape      */
                                 /* probes) reported on stderr; 0 (default) silent        */
+    int32_t history_fft;        /* causal substitution (CAUSAL preconditioner, direct   */
+                                /* solver), single-instance plans with nt >= 64 and no   */
+                                /* sweeps: 0 (default) the history sums of lags > 3 by   */
+                                /* blocks of 32 steps, the far blocks as 64-point FFT    */
+                                /* convolutions; -1 direct sums                         */
 } swr_tuning;
 
 typedef struct swr_info {

@@ -154,6 +154,10 @@ struct swr_plan_s {
     int causal_H = 0;              // >= 1: window form of the substitution (exact lag-0 solve)
     double2* d_Gw = nullptr;       // rows of the lag-0 inverse, [nif][2H+1][4]
     double2* d_Pwin = nullptr;     // window form: partial right-hand sides P_n, layout of y
+    // FFT form of the substitution's history sums (single instance, nt >= 64): the
+    // column-segment spectra (per build) and the launch's block spectra
+    double2* d_hspec = nullptr;
+    double2* d_xspec = nullptr;
     // S_0^3, S_0^4, S_1^2, S_1^4: per-end kernels (own, flux update) and s = 0 factors
     double2 *d_kap = nullptr, *d_kout = nullptr, *d_rho = nullptr;
     bool built = false;
@@ -917,13 +921,15 @@ int p_jump(swr_plan_t p) {
 int p_causal(swr_plan_t p, const double2* cols, const double2* lag0, const double2* y,
              double2* x) {
     // the window form applies to the plan's own operator (the rows of its lag-0 inverse)
-    const bool win = p->causal_H > 0 && cols == p->d_iface + p->nb;
+    const bool own = cols == p->d_iface + p->nb;   // the plan's own operator
+    const bool win = p->causal_H > 0 && own;
     const double2* Gw = win ? p->d_Gw : nullptr;
     const int H = win ? p->causal_H : 0;
     const int sweeps = win ? 0 : p->causal_sweeps;
     if (!p->batched)
         return swr_launch_causal(p->N, p->nt, cols, lag0, y, x, sweeps, p->d_hist, p->d_status,
-                                 p->s, nullptr, nullptr, 0, 0, 0, Gw, H, p->d_Pwin);
+                                 p->s, nullptr, nullptr, 0, 0, 0, Gw, H, p->d_Pwin,
+                                 own ? p->d_hspec : nullptr, p->d_xspec);
     // the values are the hand-off (sweeps == 0): x and the window's partial right-hand
     // sides start unset, once for all groups
     if (sweeps == 0) {
@@ -1465,7 +1471,8 @@ void swr_destroy(swr_plan_t p) {
     cudaFree(p->d_sys_build); cudaFree(p->d_sys_R); cudaFree(p->d_sys_final);
     cudaFree(p->d_status); cudaFree(p->d_scal); cudaFree(p->d_pit);
     cudaFree(p->d_urec); cudaFree(p->d_rec_base);
-    cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0); cudaFree(p->d_Gw); cudaFree(p->d_Pwin);
+    cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0); cudaFree(p->d_Gw);
+    cudaFree(p->d_Pwin); cudaFree(p->d_hspec); cudaFree(p->d_xspec);
     cudaFree(p->d_kap); cudaFree(p->d_kout); cudaFree(p->d_rho); cudaFree(p->d_long);
     Workspace& w = p->ws;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
@@ -1642,6 +1649,13 @@ static swr_status plan_create(const swr_desc* ds, int count, const swr_tuning* t
     if (!st) st = dalloc(&p->d_iface, nb + (size_t)p->ncols);
     if (!st) st = dalloc(&p->d_lag0, 4 * p->N);
     if (!st) st = dalloc(reinterpret_cast<char**>(&p->d_hist), swr_causal_scratch_bytes(p->N));
+    if (!st && !p->batched && p->tune.history_fft >= 0 && p->nt >= kHistFftMinNt &&
+        d->vkind == SWR_V_STATIC &&
+        (d->precond == SWR_PC_CAUSAL || d->solver == SWR_SOLVER_CAUSAL)) {
+        const size_t hs = (size_t)4 * (p->N - 1) * swr_hist_blocks(p->nt) * 64;
+        st = dalloc(&p->d_hspec, hs);
+        if (!st) st = dalloc(&p->d_xspec, hs);
+    }
     if (!st) st = dalloc(&p->d_gtmp, nb);
     if (!st) st = dalloc(&p->d_gtmp2, nb);
     if (!st) st = dalloc(&p->d_trace, (size_t)p->N * 2 * p->nt);
@@ -1886,6 +1900,7 @@ static swr_status build_body(swr_plan_t p, bool do_assemble) {
         if (st) return st;
         const double2* cols = p->d_iface + nb;
         LK(p_lag0(p, cols, p->d_lag0));
+        if (p->d_hspec) LK(swr_launch_hist_spectra(p->N, p->nt, cols, p->d_hspec, s));
         if (p->fftM)
             LK(swr_launch_col_spectra(p->N, p->nt, cols, p->d_spec, p->fftM, p->d_W, s,
                                       p->batched ? p->d_inst : nullptr, p->ninst));

@@ -319,7 +319,14 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0,
                       const double2* y, double2* x, int sweeps, void* scratch, int* status,
                       cudaStream_t s, const InstInfo* inst = nullptr, const int* if_inst = nullptr,
                       int k0 = 0, int nif_group = 0, int nif_total = 0,
-                      const double2* Gw = nullptr, int H = 0, double2* P = nullptr);
+                      const double2* Gw = nullptr, int H = 0, double2* P = nullptr,
+                      const double2* hspec = nullptr, double2* xspec = nullptr);
+// FFT form of the substitution's history sums (single instance, nt >= kHistFftMinNt):
+// column-segment spectra hspec and the launch's block spectra xspec, each
+// 4 (N-1) swr_hist_blocks(nt) 64 complex.
+constexpr int kHistFftMinNt = 64;
+int swr_hist_blocks(int nt);
+int swr_launch_hist_spectra(int N, int nt, const double2* cols, double2* hspec, cudaStream_t s);
 // Long subdomains (beyond one cluster): the whole grid marches every system of the list
 // (L = 16 factors), state in the scratch of swr_long_scratch_bytes(nsys, 16, P).
 size_t swr_long_scratch_bytes(int nsys, int L, int P);

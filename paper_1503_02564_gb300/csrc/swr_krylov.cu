@@ -1025,6 +1025,28 @@ __device__ __forceinline__ void causal_source(int N, int nt, const double2* cols
     xin = has ? x + (size_t)inb * nt : nullptr;
 }
 
+// 64-point transform by one warp (radix-2 Stockham as fft_stockham, one butterfly per
+// lane and stage), a and b 64-entry shared buffers; returns the buffer holding the result.
+// W: W^k = exp(-2 pi i k / 64), k < 32 (conjugated for the inverse; unscaled).
+__device__ __forceinline__ double2* warp_fft64(double2* a, double2* b, const double2* W,
+                                               bool inverse, int lane) {
+#pragma unroll
+    for (int st = 0; st < 6; ++st) {
+        const int m = 1 << st, l = 32 >> st;
+        const int j = lane >> st, kk = lane & (m - 1);
+        double2 w = W[j * m];
+        if (inverse) w.y = -w.y;
+        const double2 c0 = a[kk + j * m], c1 = a[kk + j * m + l * m];
+        b[kk + 2 * j * m] = cadd(c0, c1);
+        b[kk + 2 * j * m + m] = cmul(w, csub(c0, c1));
+        __syncwarp();
+        double2* tt = a;
+        a = b;
+        b = tt;
+    }
+    return a;
+}
+
 // One CTA of kCausalThreads per interface: warp 0 solves, warps 1, 2, 3 and 5 form the
 // history sums of sources 0..3 (warp 4, which would share warp 0's sub-partition, leaves at
 // once).  cols_smem: the dynamic shared memory holds the four Toeplitz columns (4 nt).
@@ -1033,7 +1055,8 @@ __global__ void __launch_bounds__(kCausalThreads, 4) k_causal_wave(
     int N, int nt, int sweeps, const double2* __restrict__ cols, const double2* __restrict__ lag0,
     const double2* __restrict__ y, double2* x, double2* xsw, double2* P, int* progress,
     int* abortf, int* status, const InstInfo* __restrict__ inst, const int* __restrict__ if_inst,
-    int k0, int nif_all, const double2* __restrict__ Gw, int H, int cols_smem) {
+    int k0, int nif_all, const double2* __restrict__ Gw, int H, int cols_smem,
+    const double2* __restrict__ hspec, double2* xspec, int nbt) {
     // lookahead: warp 0 adds the lags 2..LA itself, the history warps the lags > LA
     constexpr int LA = FLAG ? kLA : 2;
     extern __shared__ double2 s_cols[];  // [4][nt] when cols_smem
@@ -1049,6 +1072,11 @@ __global__ void __launch_bounds__(kCausalThreads, 4) k_causal_wave(
     __shared__ double2 s_wq[FLAG ? kMaxIn : 1][4];
     __shared__ double2 s_xo[2], s_P[2], s_nb[2], s_l3[4], s_c23[2][4];
     __shared__ int s_nbin[2];
+    // FFT form of the history: per history warp two blocks of source values and the
+    // transform's ping-pong buffers; the 32 twiddles of the 64-point transform
+    __shared__ double2 s_hx[FLAG ? 4 : 1][64];
+    __shared__ double2 s_hf[FLAG ? 4 : 1][128];
+    __shared__ double2 s_w64[32];
     // global interface kg (sweep values, progress, lag-0 blocks); local k within its
     // instance (blocks, columns)
     const int kg = k0 + blockIdx.x;
@@ -1069,6 +1097,11 @@ __global__ void __launch_bounds__(kCausalThreads, 4) k_causal_wave(
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double2 zero = make_double2(0.0, 0.0);
     if (threadIdx.x < 4 * (LA + 1)) hp[threadIdx.x >> 2][threadIdx.x & 3] = zero;
+    if (FLAG && hspec && threadIdx.x < 32) {   // W^k = exp(-2 pi i k / 64)
+        double sn, cs;
+        sincospi(-(double)threadIdx.x / 32.0, &sn, &cs);
+        s_w64[threadIdx.x] = make_double2(cs, sn);
+    }
     if (threadIdx.x < 4) s_hdone[threadIdx.x] = LA;   // steps 0..LA have no lag > LA
     if (threadIdx.x == 0) {
         s_xown = 0;
@@ -1095,6 +1128,115 @@ __global__ void __launch_bounds__(kCausalThreads, 4) k_causal_wave(
         }
         const bool own = (e == 0 || e == 2);
         const int nb = (e == 1) ? kg + 1 : kg - 1;
+        if constexpr (FLAG) {
+            if (hspec) {
+                // ---- FFT form of the history (single instance, nt >= 64) --------------
+                // Lags > LA of step t, t in output block K = t / 32 (tau = t mod 32), split
+                // at the blocks of 32 input steps:
+                //   near: input blocks K-1 and K, accumulated as each value x_s arrives
+                //         (lane tau adds c[t - s] x_s for its step t of block J = s / 32 and
+                //         of block J + 1; two accumulators, one per block parity);
+                //   far:  input blocks J <= K-2, sum_J IFFT(C_{K-J} . X_J)[32 + tau] with
+                //         X_J the 64-point transform of block J zero-padded and C_d that of
+                //         the column's segment c[(d-1) 32 .. (d+1) 32) (precomputed, / 64);
+                //         formed while block K-1 arrives: the transform of block K-2 at its
+                //         first value, one product term per value, the inverse at the 28th.
+                // The source's values are read once, as they arrive (kept per block in
+                // shared memory for the transform).
+                double2* sx = s_hx[e];                  // [2][32]: blocks of parity 0, 1
+                double2* fa = s_hf[e];                  // [2][64]: transform ping-pong
+                double2* xs = xspec + (size_t)(4 * kg + e) * nbt * 64;
+                const double2* cs = hspec + (size_t)(4 * kg + e) * nbt * 64;
+                // accumulators and far parts of the output blocks of parity 0 and 1
+                double2 A0 = zero, A1 = zero, F0 = zero, F1 = zero, Fa0 = zero, Fa1 = zero;
+                for (int m = 1; m + LA < nt; ++m) {
+                    bool ok = __all_sync(0xffffffffu, cta_wait_ge(&s_hused, m - 1, &s_stop));
+                    if (!ok) break;
+                    const int s = m - 1, J = s >> 5, sg = s & 31, t = m + LA;
+                    double2 v = zero;
+                    if (has) {
+                        if (own) {
+                            ok = __all_sync(0xffffffffu, cta_wait_ge(&s_xown, m, &s_stop));
+                            if (ok) v = __ldcg(xin + s);
+                        } else {
+                            long long polls = 0;
+                            bool o = true;
+                            if (lane == 0)
+                                while (!is_set(v = ld_relaxed2(xin + s)))
+                                    if (!poll_tick(polls, abortf, status, lim)) {
+                                        o = false;
+                                        break;
+                                    }
+                            ok = __shfl_sync(0xffffffffu, o, 0);
+                            v.x = __shfl_sync(0xffffffffu, v.x, 0);
+                            v.y = __shfl_sync(0xffffffffu, v.y, 0);
+                        }
+                        if (!ok) break;
+                    }
+                    if (lane == 0) sx[(J & 1) * 32 + sg] = v;
+                    if (sg == 0) {
+                        if (J & 1) A0 = zero;
+                        else A1 = zero;
+                    }
+                    // near: this value's terms for the steps of blocks J and J + 1
+                    if (has) {
+                        const int lc = lane - sg, ln = 32 + lane - sg;
+                        const double2 tc = (lc > LA) ? cc[lc] : zero;
+                        const double2 tn = (ln > LA) ? cc[ln] : zero;
+                        // block J's accumulator gets tc, block J + 1's gets tn
+                        const bool odd = J & 1;
+                        A0 = cfma(odd ? tn : tc, v, A0);
+                        A1 = cfma(odd ? tc : tn, v, A1);
+                    }
+                    // far part of block Kf = J + 1, formed during block J
+                    const int Kf = J + 1;
+                    if (has && Kf >= 2 && 32 * Kf < nt) {
+                        if (sg == 0) {
+                            __syncwarp();
+                            fa[lane] = sx[((J - 1) & 1) * 32 + lane];
+                            fa[32 + lane] = zero;
+                            __syncwarp();
+                            const double2* r = warp_fft64(fa, fa + 64, s_w64, false, lane);
+                            const double2 x0 = r[lane], x1 = r[32 + lane];
+                            xs[(size_t)(J - 1) * 64 + lane] = x0;
+                            xs[(size_t)(J - 1) * 64 + 32 + lane] = x1;
+                            Fa0 = Fa1 = zero;
+                            __syncwarp();
+                        }
+                        // terms q = 0 .. J-1 (X_q with C_{Kf-q}), spread over sg = 1 .. 26
+                        if (sg >= 1 && sg <= 26) {
+                            const int per = (J + 25) / 26;
+                            const int q0 = (sg - 1) * per, q1 = min(J, sg * per);
+                            for (int q = q0; q < q1; ++q) {
+                                const double2* xq = xs + (size_t)q * 64;
+                                const double2* cq = cs + (size_t)(Kf - q) * 64;
+                                Fa0 = cfma(__ldg(cq + lane), xq[lane], Fa0);
+                                Fa1 = cfma(__ldg(cq + 32 + lane), xq[32 + lane], Fa1);
+                            }
+                        }
+                        if (sg == 27) {
+                            fa[lane] = Fa0;
+                            fa[32 + lane] = Fa1;
+                            __syncwarp();
+                            const double2* r = warp_fft64(fa, fa + 64, s_w64, true, lane);
+                            if (Kf & 1) F1 = r[32 + lane];
+                            else F0 = r[32 + lane];
+                            __syncwarp();
+                        }
+                    } else if (sg == 27) {
+                        if (Kf & 1) F1 = zero;
+                        else F0 = zero;
+                    }
+                    // this step's sum: lane t mod 32
+                    if (lane == (t & 31)) {
+                        const int K = t >> 5;
+                        hp[t % (LA + 1)][e] = (K & 1) ? cadd(A1, F1) : cadd(A0, F0);
+                        cta_store_release(&s_hdone[e], t);
+                    }
+                }
+                return;
+            }
+        }
         for (int m = 1; m + LA < nt; ++m) {
             bool ok = __all_sync(0xffffffffu, cta_wait_ge(&s_hused, m - 1, &s_stop));
             if (!ok) break;
@@ -1535,6 +1677,52 @@ __global__ void __launch_bounds__(kCausalThreads, 4) k_causal_wave(
     if (lane == 0) cta_store_release(&s_stop, 1);   // releases history warps still waiting
 }
 
+// Spectra of the column segments for the FFT form of the history sums: for interface k,
+// source e (pair 4k + e) and d = 2 .. nbt-1, the 64-point transform of
+// c[(d-1) 32 .. (d+1) 32) (zero beyond nt), scaled by 1/64, at
+// hspec[((4k + e) nbt + d) 64 ..].  One CTA of 32 threads per pair.
+__global__ void __launch_bounds__(32) k_hist_spectra(int N, int nt, int nbt,
+                                                     const double2* __restrict__ cols,
+                                                     double2* __restrict__ hspec) {
+    __shared__ double2 a[128];
+    __shared__ double2 w64[32];
+    const int pair = blockIdx.x, kg = pair >> 2, e = pair & 3, lane = threadIdx.x;
+    double sn, cs;
+    sincospi(-(double)lane / 32.0, &sn, &cs);
+    w64[lane] = make_double2(cs, sn);
+    bool has;
+    const double2* cc;
+    double2* xin;
+    causal_source(N, nt, cols, nullptr, kg, e, has, cc, xin);
+    const double2 zero = make_double2(0.0, 0.0);
+    double2* out = hspec + (size_t)pair * nbt * 64;
+    for (int d = 0; d < nbt; ++d) {
+        if (d < 2 || !has) {
+            out[(size_t)d * 64 + lane] = zero;
+            out[(size_t)d * 64 + 32 + lane] = zero;
+            continue;
+        }
+        const int i0 = (d - 1) * 32 + lane, i1 = i0 + 32;
+        __syncwarp();
+        a[lane] = (i0 < nt) ? cc[i0] : zero;
+        a[32 + lane] = (i1 < nt) ? cc[i1] : zero;
+        __syncwarp();
+        const double2* r = warp_fft64(a, a + 64, w64, false, lane);
+        const double sc = 1.0 / 64.0;
+        out[(size_t)d * 64 + lane] = make_double2(r[lane].x * sc, r[lane].y * sc);
+        out[(size_t)d * 64 + 32 + lane] = make_double2(r[32 + lane].x * sc, r[32 + lane].y * sc);
+    }
+}
+
+int swr_hist_blocks(int nt) { return (nt + 31) / 32; }
+
+int swr_launch_hist_spectra(int N, int nt, const double2* cols, double2* hspec, cudaStream_t s) {
+    if (nt < kHistFftMinNt || N < 2) return -2;
+    k_hist_spectra<<<4 * (N - 1), 32, 0, s>>>(N, nt, swr_hist_blocks(nt), cols, hspec);
+    swr_count_launch(1);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 int swr_set_wait_hook(long long max_polls, int withhold) {
     const long long lim = max_polls > 0 ? max_polls : kWaitPolls;
     const int wh = withhold >= 0 ? withhold : -1;
@@ -1613,8 +1801,12 @@ size_t causal_dyn_smem(const void* fn, int ncta, int nt, int* cols_smem) {
 int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, const double2* y,
                       double2* x, int sweeps, void* scratch, int* status, cudaStream_t s,
                       const InstInfo* inst, const int* if_inst, int k0, int nif_group,
-                      int nif_total, const double2* Gw, int H, double2* P) {
+                      int nif_total, const double2* Gw, int H, double2* P,
+                      const double2* hspec, double2* xspec) {
     if (H < 0 || H > kWinMaxH || (H > 0 && (!Gw || !P)) || (H > 0 && sweeps > 0)) return -2;
+    // the FFT form of the history: single instance, value-polling form, nt >= 64
+    if (inst || sweeps > 0 || nt < kHistFftMinNt || !xspec) hspec = nullptr;
+    const int nbt = swr_hist_blocks(nt);
     const int nif = inst ? nif_total : N - 1;
     const int ncta = inst ? nif_group : N - 1;
     if (!inst) k0 = 0;
@@ -1648,7 +1840,8 @@ int swr_launch_causal(int N, int nt, const double2* cols, const double2* lag0, c
     void* args[] = {(void*)&N, (void*)&nt, (void*)&sweeps, (void*)&cols, (void*)&lag0,
                     (void*)&y, (void*)&x, (void*)&xsw, (void*)&P, (void*)&progress,
                     (void*)&abortf, (void*)&status, (void*)&inst, (void*)&if_inst, (void*)&k0,
-                    (void*)&nif, (void*)&Gw, (void*)&H, (void*)&cols_smem};
+                    (void*)&nif, (void*)&Gw, (void*)&H, (void*)&cols_smem, (void*)&hspec,
+                    (void*)&xspec, (void*)&nbt};
     if (cudaLaunchCooperativeKernel(fn, dim3(ncta), dim3(kCausalThreads), args, dyn, s) !=
         cudaSuccess)
         return -1;

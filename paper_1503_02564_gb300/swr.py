@@ -48,7 +48,7 @@ class swr_tuning(ctypes.Structure):
         ("toeplitz_fft", ctypes.c_int32), ("superpose", ctypes.c_int32),
         ("long_march", ctypes.c_int32), ("graph", ctypes.c_int32),
         ("tdep_precomp", ctypes.c_int32), ("two_level", ctypes.c_int32),
-        ("debug", ctypes.c_int32),
+        ("debug", ctypes.c_int32), ("history_fft", ctypes.c_int32),
     ]
 
 

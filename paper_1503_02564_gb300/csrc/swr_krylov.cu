@@ -840,16 +840,21 @@ __device__ bool wait_one(int nb, int target, const int* progress, int* abortf, i
 // psi^(m) decays like (|c| |D^{-1}|)^m); m runs to H + 4 over a window of H + 4
 // interfaces each side, and the blocks |j - k| <= H are kept:
 //     Gw[(k (2H+1) + j - k + H) 4 + {00, 01, 10, 11}] = (A0^{-1})_{k,j}.
-// One thread per interface.
+// One warp per interface (below).
 constexpr int kWinMaxH = 8;
-constexpr int kWinW = kWinMaxH + 4;
 
-__global__ void k_lag0_window(int N, int nt, const double2* __restrict__ cols,
-                              const double2* __restrict__ lag0, double2* __restrict__ Gw, int H,
-                              const InstInfo* __restrict__ inst, const int* __restrict__ if_inst,
-                              int nif_total) {
-    const int kg = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kg >= (inst ? nif_total : N - 1)) return;
+// One warp per interface k, lane q for block j = k + q - W of the window (2W + 1 <= 25
+// lanes): psi^(m) and the running sum live in the lanes' registers, the neighbours'
+// blocks come by shuffles.
+__global__ void __launch_bounds__(128) k_lag0_window(int N, int nt,
+                                                     const double2* __restrict__ cols,
+                                                     const double2* __restrict__ lag0,
+                                                     double2* __restrict__ Gw, int H,
+                                                     const InstInfo* __restrict__ inst,
+                                                     const int* __restrict__ if_inst,
+                                                     int nif_total) {
+    const int kg = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, q = threadIdx.x & 31;
+    if (kg >= (inst ? nif_total : N - 1)) return;   // whole warps leave together
     int k = kg;
     if (inst) {
         const InstInfo I = inst[if_inst[kg]];
@@ -860,50 +865,62 @@ __global__ void k_lag0_window(int N, int nt, const double2* __restrict__ cols,
     }
     const int nI = N - 1, W = H + 4;
     const double2 zero = make_double2(0.0, 0.0);
-    double2 psi[2 * kWinW + 1][4], nxt[2 * kWinW + 1][4], sum[2 * kWinW + 1][4];
-    for (int q = 0; q < 2 * W + 1; ++q)
-        for (int e = 0; e < 4; ++e) psi[q][e] = sum[q][e] = zero;
-    psi[W][0] = psi[W][3] = sum[W][0] = sum[W][3] = make_double2(1.0, 0.0);
-    auto cB = [&](int j) { return (j + 1 <= N - 2) ? cols[(size_t)(4 * (j + 1) + 1) * nt] : zero; };
-    auto cD = [&](int j) { return (j >= 1) ? cols[(size_t)(4 * j + 2) * nt] : zero; };
-    for (int m = 1; m <= W; ++m) {
-        for (int q = 0; q < 2 * W + 1; ++q) {
-            const int j = k + q - W;
-            for (int e = 0; e < 4; ++e) nxt[q][e] = zero;
-            if (j < 0 || j >= nI) continue;
-            // T = [cB_{j-1} psi_{j-1}[:,0] | cD_{j+1} psi_{j+1}[:,1]]
-            double2 t00 = zero, t10 = zero, t01 = zero, t11 = zero;
-            if (q > 0 && j - 1 >= 0) {
-                const double2 c = cB(j - 1);
-                t00 = cmul(c, psi[q - 1][0]);
-                t10 = cmul(c, psi[q - 1][2]);
-            }
-            if (q < 2 * W && j + 1 < nI) {
-                const double2 c = cD(j + 1);
-                t01 = cmul(c, psi[q + 1][1]);
-                t11 = cmul(c, psi[q + 1][3]);
-            }
-            const double2* Di = lag0 + (size_t)(kg + q - W) * 4;   // D_j^{-1}
-            nxt[q][0] = cfma(t00, Di[0], cmul(t01, Di[2]));
-            nxt[q][1] = cfma(t00, Di[1], cmul(t01, Di[3]));
-            nxt[q][2] = cfma(t10, Di[0], cmul(t11, Di[2]));
-            nxt[q][3] = cfma(t10, Di[1], cmul(t11, Di[3]));
-        }
-        for (int q = 0; q < 2 * W + 1; ++q)
-            for (int e = 0; e < 4; ++e) {
-                psi[q][e] = nxt[q][e];
-                sum[q][e] = cadd(sum[q][e], nxt[q][e]);
-            }
+    const int j = k + q - W;
+    const bool in = (q <= 2 * W) && j >= 0 && j < nI;
+    // this lane's constants: D_j^{-1}, cB_{j-1} (from the left block), cD_{j+1} (right)
+    double2 Di0 = zero, Di1 = zero, Di2 = zero, Di3 = zero, cBl = zero, cDr = zero;
+    if (in) {
+        const double2* Di = lag0 + (size_t)(kg + q - W) * 4;
+        Di0 = Di[0];
+        Di1 = Di[1];
+        Di2 = Di[2];
+        Di3 = Di[3];
+        if (q > 0 && j - 1 >= 0 && j <= N - 2) cBl = cols[(size_t)(4 * j + 1) * nt];
+        if (q < 2 * W && j + 1 < nI && j + 1 >= 1) cDr = cols[(size_t)(4 * (j + 1) + 2) * nt];
     }
-    const double2* Dk = lag0 + (size_t)kg * 4;
-    for (int d = -H; d <= H; ++d) {
-        const int q = W + d;
+    double2 p0 = zero, p1 = zero, p2 = zero, p3 = zero;
+    if (q == W) p0 = p3 = make_double2(1.0, 0.0);
+    double2 s0 = p0, s1 = p1, s2 = p2, s3 = p3;
+    auto shfl2 = [&](double2 v, int delta, bool up) {
+        double2 r;
+        r.x = up ? __shfl_up_sync(0xffffffffu, v.x, delta)
+                 : __shfl_down_sync(0xffffffffu, v.x, delta);
+        r.y = up ? __shfl_up_sync(0xffffffffu, v.y, delta)
+                 : __shfl_down_sync(0xffffffffu, v.y, delta);
+        return r;
+    };
+    for (int m = 1; m <= W; ++m) {
+        // T = [cB_{j-1} psi_{j-1}[:,0] | cD_{j+1} psi_{j+1}[:,1]]
+        const double2 l0 = shfl2(p0, 1, true), l2 = shfl2(p2, 1, true);
+        const double2 r1 = shfl2(p1, 1, false), r3 = shfl2(p3, 1, false);
+        const double2 t00 = cmul(cBl, l0), t10 = cmul(cBl, l2);
+        const double2 t01 = cmul(cDr, r1), t11 = cmul(cDr, r3);
+        double2 n0 = cfma(t00, Di0, cmul(t01, Di2));
+        double2 n1 = cfma(t00, Di1, cmul(t01, Di3));
+        double2 n2 = cfma(t10, Di0, cmul(t11, Di2));
+        double2 n3 = cfma(t10, Di1, cmul(t11, Di3));
+        if (!in) n0 = n1 = n2 = n3 = zero;
+        p0 = n0;
+        p1 = n1;
+        p2 = n2;
+        p3 = n3;
+        s0 = cadd(s0, n0);
+        s1 = cadd(s1, n1);
+        s2 = cadd(s2, n2);
+        s3 = cadd(s3, n3);
+    }
+    // row k of A0^{-1}: D_k^{-1} times the summed blocks, for |d| <= H
+    const int d = q - W;
+    auto from_w = [&](double2 v) {   // lane W's value: D_k^{-1}
+        return make_double2(__shfl_sync(0xffffffffu, v.x, W), __shfl_sync(0xffffffffu, v.y, W));
+    };
+    const double2 K0 = from_w(Di0), K1 = from_w(Di1), K2 = from_w(Di2), K3 = from_w(Di3);
+    if (d >= -H && d <= H) {
         double2* g = Gw + ((size_t)kg * (2 * H + 1) + d + H) * 4;
-        const double2* s = sum[q];
-        g[0] = cfma(Dk[0], s[0], cmul(Dk[1], s[2]));
-        g[1] = cfma(Dk[0], s[1], cmul(Dk[1], s[3]));
-        g[2] = cfma(Dk[2], s[0], cmul(Dk[3], s[2]));
-        g[3] = cfma(Dk[2], s[1], cmul(Dk[3], s[3]));
+        g[0] = cfma(K0, s0, cmul(K1, s2));
+        g[1] = cfma(K0, s1, cmul(K1, s3));
+        g[2] = cfma(K2, s0, cmul(K3, s2));
+        g[3] = cfma(K2, s1, cmul(K3, s3));
     }
 }
 
@@ -912,8 +929,8 @@ int swr_launch_lag0_window(int N, int nt, const double2* cols, const double2* la
                            int nif_total) {
     if (H < 1 || H > kWinMaxH) return -2;
     const int nif = inst ? nif_total : N - 1;
-    k_lag0_window<<<(nif + 63) / 64, 64, 0, s>>>(N, nt, cols, lag0, Gw, H, inst, if_inst,
-                                                 nif_total);
+    k_lag0_window<<<(nif + 3) / 4, 128, 0, s>>>(N, nt, cols, lag0, Gw, H, inst, if_inst,
+                                                nif_total);
     swr_count_launch(1);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -68,11 +68,13 @@ def parse():
                          "timedep: the time-dependent potential case (60001 nodes, 1000 steps, "
                          "N = 64, GMRES preconditioned by the mean-potential operator); "
                          "adjoint: the scaling step plus the misfit gradient dJ/dV by "
-                         "swr_adjoint (checkpoints every 50 steps); batch: 128 independent "
+                         "swr_adjoint (every step recorded when it fits, else checkpoints "
+                         "every 50); batch: 128 independent "
                          "instances (uneven partitions, 100-400 steps) in one batched plan, "
                          "reported beside one plan per instance; nonlinear: |u|^2 + V0 "
                          "(20001 nodes, 1000 steps, N = 32), preconditioned fixed point, then "
-                         "the misfit gradient dJ/dV0 by swr_adjoint (checkpoints every 50); "
+                         "the misfit gradient dJ/dV0 by swr_adjoint (the library's checkpoint "
+                         "interval); "
                          "tcs: the comparison of transmission conditions and interface solvers "
                          "in the setting of the paper's Section 6 (V=-x^2 on (-21,21), dx=1e-5, "
                          "N in {2,500}, random g0); fp64peak: the FP64 throughput probes "
@@ -160,7 +162,8 @@ def workload_name_nonlinear(nt=1000):
             "Robin p=sqrt(5)e^{-i pi/4}, inner fixed point to 1e-13 per step, outer fixed point "
             "preconditioned by the V0 interface operator to 1e-10 + final march; then "
             "J = ||u(T) - u_target||_M^2 and dJ/dV0 by swr_adjoint (monodomain discrete "
-            "adjoint, checkpoints every 50 steps)" % (nt * 5e-4, nt))
+            "adjoint, the library's checkpoint interval: every step recorded when it fits)"
+            % (nt * 5e-4, nt))
 
 
 def march_point_steps(wl):
@@ -973,7 +976,7 @@ def run_workload(args, workload, rank, world, local, dev, peak):
             if adjoint:
                 c["ev"][0].record()
                 c["J"] = c["plan"].misfit(c["uT"], c["tgt"], c["ubar"])
-                c["plan"].adjoint(c["ubar"], c["grad"], 50)
+                c["plan"].adjoint(c["ubar"], c["grad"], 0)
                 c["ev"][1].record()
         return infos
 
@@ -1076,7 +1079,7 @@ def run_workload(args, workload, rank, world, local, dev, peak):
                 if adjoint:
                     c["tgt"].copy_(h["tgt"], non_blocking=True)
                     c["plan"].misfit(c["uT"], c["tgt"], c["ubar"])
-                    c["plan"].adjoint(c["ubar"], c["grad"], 50)
+                    c["plan"].adjoint(c["ubar"], c["grad"], 0)
                     h["grad"].copy_(c["grad"], non_blocking=True)
             ev1.record()
             ev1.synchronize()
@@ -1143,7 +1146,7 @@ def run_workload(args, workload, rank, world, local, dev, peak):
                        workload_name_nonlinear(cases[0]["wl"].nt) if nonlin else
                        (workload_name(nsubs, args.tc, cases[0]["wl"].nt)
                         + ("; then J = ||u(T) - u_target||_M^2 and dJ/dV(x) by swr_adjoint, "
-                           "checkpoints every 50 steps" if adjoint else "")),
+                           "the library's checkpoint interval" if adjoint else "")),
                        "point_steps_per_step": ps_step,
                        "precond": "mean_potential" if (timedep or nonlin) else args.precond,
                        "l2": "flushed by a 256 MB write before each step",

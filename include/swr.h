@@ -322,7 +322,9 @@ swr_status swr_misfit(swr_plan_t p, const double *uT, const double *u_target, do
  *               dJ = Re(ubar^H M du_T) (swr_misfit returns it for the misfit);
  *   dJ_dV:      double[nx] (device), overwritten with dJ/dV_k for the nodal V;
  *               SWR_V_TIME: double[(nt + 1) nx], row m = dJ/dV(t_m, .) (the layout of V);
- *   ckpt_every: checkpoint interval K in time steps (<= 0: 50).
+ *   ckpt_every: checkpoint interval K in time steps (<= 0: every step recorded in one
+ *               segment when nt x nx complex take at most 1/8 of the free device memory,
+ *               else 50).
  * Method (static V): the discrete adjoint of the Crank-Nicolson march,
  * conjugated and scaled, is the same march run from (dt/2i) conj(ubar); it is
  * solved by SWR on the plan's own interface problem (same Toeplitz columns and

@@ -2290,7 +2290,18 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
     if (tdep && (march_kind(p, false) != MK_TSTAT || march_config(p, N, MK_TSTAT).L > 8))
         return SWR_ERR_UNSUPPORTED;
     const size_t nb = (size_t)p->nblk * nt;
-    const int K = std::max(1, std::min(ckpt_every > 0 ? ckpt_every : 50, nt));
+    // checkpoint interval: the caller's, else every step recorded (one segment, no
+    // re-march of the forward) when the record of nt steps takes at most an eighth of
+    // the free device memory, else 50
+    int Kdef = 50;
+    if (ckpt_every <= 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess &&
+            (size_t)nt * (size_t)nx * sizeof(double2) <= fr / 8)
+            Kdef = nt;
+        cudaGetLastError();
+    }
+    const int K = std::max(1, std::min(ckpt_every > 0 ? ckpt_every : Kdef, nt));
     const int C = (nt + K - 1) / K;
     swr_status st = SWR_OK;
     if (p->adj_K != K) {

@@ -293,7 +293,7 @@ class Plan:
                "swr_misfit")
         return J.value
 
-    def adjoint(self, ubar, grad, ckpt_every=50):
+    def adjoint(self, ubar, grad, ckpt_every=0):
         """grad <- dJ/dV for the M-weighted cotangent ubar of J at u(T) (after solve());
         grad has nx entries, or (nt + 1) nx for a time-dependent potential (the layout
         of V)."""
@@ -326,7 +326,7 @@ class SWRMisfit(torch.autograd.Function):
     transmission and GMRES; u0, u_target: complex128 CUDA tensors."""
 
     @staticmethod
-    def forward(ctx, V, plan, u0, u_target, ckpt_every=50):
+    def forward(ctx, V, plan, u0, u_target, ckpt_every=0):
         plan.build_interface(V, u0)
         uT = torch.empty(plan.nx, dtype=torch.complex128, device=V.device)
         plan.solve(None, False, uT)

@@ -36,12 +36,14 @@ FLOPS_PER_POINT_STEP_TDEP = 56     # plus the per-step factorisation (one comple
 FLOPS_PER_POINT_ITER_NL = 76
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flop x GHz (max SM clock)
 
-# DRAM bytes (read + write) per march launch, mean over the timed step's march launches, from
-# the ncu launch lists of the two workloads kept with the profiles; valid only for the march
-# sources they were taken from (sha256 prefix of swr_march.cu + swr_internal.cuh), null
-# otherwise.
-MARCH_TRAFFIC = {"sources": "d744ed0b72cab1ec",
-                 "scaling": 3119406144.0, "timedep": 6636897174.0}
+# DRAM bytes (read + write) per march launch, each scaled by the steps from a 100-step
+# single-launch ncu capture (profiles/k_march_static_N500_build.md and
+# profiles/launch_list_timedep.md): the scaling build writes the recorded states (598 MB per
+# 100 steps, 20 MB read), the V(t,x) march reads the streamed per-step factors (677 MB per
+# 100 steps, 3 MB written).  Valid only for the march sources they were taken from (sha256
+# prefix of swr_march.cu + swr_internal.cuh), null otherwise.
+MARCH_TRAFFIC = {"sources": "99af1785a54db446",
+                 "scaling": 3012000000.0, "timedep": 6803000000.0}
 
 
 def march_sources_hash():

@@ -157,6 +157,7 @@ struct swr_plan_s {
     // FFT form of the substitution's history sums (single instance, nt >= 64): the
     // column-segment spectra (per build) and the launch's block spectra
     double2* d_hspec = nullptr;
+    double2* d_hspec0 = nullptr;   // the same for L_0 (zero / mean-potential preconditioner)
     double2* d_xspec = nullptr;
     // S_0^3, S_0^4, S_1^2, S_1^4: per-end kernels (own, flux update) and s = 0 factors
     double2 *d_kap = nullptr, *d_kout = nullptr, *d_rho = nullptr;
@@ -929,7 +930,10 @@ int p_causal(swr_plan_t p, const double2* cols, const double2* lag0, const doubl
     if (!p->batched)
         return swr_launch_causal(p->N, p->nt, cols, lag0, y, x, sweeps, p->d_hist, p->d_status,
                                  p->s, nullptr, nullptr, 0, 0, 0, Gw, H, p->d_Pwin,
-                                 own ? p->d_hspec : nullptr, p->d_xspec);
+                                 own ? p->d_hspec
+                                 : (p->d_iface0 && cols == p->d_iface0 + p->nb) ? p->d_hspec0
+                                                                                  : nullptr,
+                                 p->d_xspec);
     // the values are the hand-off (sweeps == 0): x and the window's partial right-hand
     // sides start unset, once for all groups
     if (sweeps == 0) {
@@ -1472,7 +1476,8 @@ void swr_destroy(swr_plan_t p) {
     cudaFree(p->d_status); cudaFree(p->d_scal); cudaFree(p->d_pit);
     cudaFree(p->d_urec); cudaFree(p->d_rec_base);
     cudaFree(p->d_W); cudaFree(p->d_spec); cudaFree(p->d_spec0); cudaFree(p->d_Gw);
-    cudaFree(p->d_Pwin); cudaFree(p->d_hspec); cudaFree(p->d_xspec);
+    cudaFree(p->d_Pwin); cudaFree(p->d_hspec); cudaFree(p->d_hspec0);
+    cudaFree(p->d_xspec);
     cudaFree(p->d_kap); cudaFree(p->d_kout); cudaFree(p->d_rho); cudaFree(p->d_long);
     Workspace& w = p->ws;
     cudaFree(w.V); cudaFree(w.w); cudaFree(w.z); cudaFree(w.r); cudaFree(w.H); cudaFree(w.cs);
@@ -1649,12 +1654,17 @@ static swr_status plan_create(const swr_desc* ds, int count, const swr_tuning* t
     if (!st) st = dalloc(&p->d_iface, nb + (size_t)p->ncols);
     if (!st) st = dalloc(&p->d_lag0, 4 * p->N);
     if (!st) st = dalloc(reinterpret_cast<char**>(&p->d_hist), swr_causal_scratch_bytes(p->N));
-    if (!st && !p->batched && p->tune.history_fft >= 0 && p->nt >= kHistFftMinNt &&
-        d->vkind == SWR_V_STATIC &&
-        (d->precond == SWR_PC_CAUSAL || d->solver == SWR_SOLVER_CAUSAL)) {
+    if (!st && !p->batched && p->tune.history_fft >= 0 && p->nt >= kHistFftMinNt) {
+        // one set of column-segment spectra per operator the substitution applies to:
+        // the plan's own (static V, CAUSAL) and L_0 (zero / mean-potential preconditioner)
         const size_t hs = (size_t)4 * (p->N - 1) * swr_hist_blocks(p->nt) * 64;
-        st = dalloc(&p->d_hspec, hs);
-        if (!st) st = dalloc(&p->d_xspec, hs);
+        const bool own = d->vkind == SWR_V_STATIC &&
+                         (d->precond == SWR_PC_CAUSAL || d->solver == SWR_SOLVER_CAUSAL);
+        const bool pot = d->precond == SWR_PC_ZERO_POTENTIAL ||
+                         d->precond == SWR_PC_MEAN_POTENTIAL;
+        if (own) st = dalloc(&p->d_hspec, hs);
+        if (!st && pot) st = dalloc(&p->d_hspec0, hs);
+        if (!st && (own || pot)) st = dalloc(&p->d_xspec, hs);
     }
     if (!st) st = dalloc(&p->d_gtmp, nb);
     if (!st) st = dalloc(&p->d_gtmp2, nb);
@@ -1924,6 +1934,8 @@ static swr_status build_body(swr_plan_t p, bool do_assemble) {
                        p->d_iface0, nullptr, nullptr, p->d_u0, p->work_build_imp);
         if (st) return st;
         LK(p_lag0(p, p->d_iface0 + nb, p->d_lag0_0));
+        if (p->d_hspec0)
+            LK(swr_launch_hist_spectra(p->N, p->nt, p->d_iface0 + nb, p->d_hspec0, s));
         if (p->fftM)
             LK(swr_launch_col_spectra(p->N, p->nt, p->d_iface0 + nb, p->d_spec0, p->fftM,
                                       p->d_W, s, p->batched ? p->d_inst : nullptr, p->ninst));

@@ -91,3 +91,26 @@ def test_fft_history_solves_to_the_monodomain_solution(swr):
     assert info["residual"] < 1e-10
     assert rel(uT.cpu().numpy(), uTm) < 1e-9
     assert rel(g.cpu().numpy(), gs.ravel()) < 1e-9
+
+
+@pytest.mark.parametrize("nt", [100, 300])
+def test_fft_history_for_the_mean_potential_preconditioner(swr, nt):
+    """V(t,x) with the mean-potential preconditioner: the substitution runs on the
+    operator L_0 of the time-averaged potential, whose spectra are formed at each build."""
+    wl = W.config4(nsub=8, nx=8001, nt=nt)
+    out = []
+    for hf in (0, -1):
+        plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
+                        node_off=wl.off, p=wl.sigma, vkind=swr.SWR_V_TIME,
+                        precond=swr.SWR_PC_MEAN_POTENTIAL, tuning={"history_fft": hf})
+        plan.build_interface(torch.tensor(np.ascontiguousarray(wl.V).ravel(),
+                                          dtype=torch.float64, device="cuda"),
+                             torch.tensor(wl.u0, dtype=torch.complex128, device="cuda"))
+        y = torch.tensor(W.random_interface(wl.nblk, wl.nt, 4).ravel(),
+                         dtype=torch.complex128, device="cuda")
+        x = torch.full_like(y, complex("nan"))
+        plan.apply_precond(y, x)
+        plan.destroy()
+        out.append(x.cpu().numpy())
+    assert np.all(np.isfinite(out[0]))
+    assert rel(out[0], out[1]) < 1e-12

@@ -649,6 +649,468 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
     if (C > 1) cl.sync();
 }
 
+// ---------------------------------------------------------------------------
+// The nonlinear march of one system spread over a cluster of C > 1 CTAs with the
+// two-level separator solve of the constant-matrix march (FactorSet.tl_*): every inner iteration solves its separators with warp-shuffle PCR in blocks of 32
+// and a reduced system of at most 32 super-separators that warp 0 of every CTA solves,
+// with one cluster barrier, and a second one for the convergence test, where the
+// cluster-wide PCR took one per level.  MODE 0 (no record, no gradient), Robin or
+// Neumann ends.  Thread p = rank T + tid owns separator p and chunk p; T is a multiple
+// of 32.  Per step: the step-constant right-hand sides, the start of the fixed point,
+// then per inner iteration
+//   A  chunk right-hand sides with b_f(zeta), local LU solves;
+//   B  separator right-hand sides: a separator's own part (its right element) and the
+//      part of its left element, formed by the thread of the chunk on its left (the
+//      same thread's neighbour in the warp, or lane 31 of the warp before for a
+//      super-separator, which publishes it);
+//   C  super-chunk PCR in registers, publication, cluster barrier;
+//   D  the reduced system in warp 0 of every CTA (every CTA holds the new iterate at
+//      all super-separators), CTA barrier;
+//   E  super-chunk values; F  chunk values, change of the iterate, partial maxima;
+//   G  cluster barrier, the convergence test on all CTAs' partials (the same decision
+//      everywhere).
+// After the fixed point: v_n = zeta, u_n = 2 v_n - u_{n-1}, fluxes.
+// Shared memory: see k_march_nl_tl_smem_bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 nl_shup(double2 v, int d) {
+    return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 nl_shdn(double2 v, int d) {
+    return make_double2(__shfl_down_sync(0xffffffffu, v.x, d),
+                        __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+int swr_march_nl_tl_smem_bytes(int L, int T) {
+    const int W = T / 32;
+    // usep zsep xv ulst ylst zlst [T] each; pub [2][W][5]; usup, zsup ping-pong [3][33];
+    // step histories: chunk nodes [3][L][T], own separators [3][T], replicas [3][33];
+    // partial maxima [2][2] (8-byte words)
+    return (int)sizeof(double2) * (6 * T + 2 * W * 5 + 3 * 33 + 3 * L * T + 3 * T + 3 * 33) +
+           (int)sizeof(unsigned long long) * 4;
+}
+
+template <int L>
+__global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
+    const MarchArgs& a = na.m;
+    extern __shared__ double2 sm[];
+    const int T = a.T, P = a.P, C = a.C, nt = a.nt;
+    const int W = T / 32;
+    double2* usep = sm;              // [T] u at my separators
+    double2* zsep = usep + T;        // [T] the iterate at my separators
+    double2* xv = zsep + T;          // [T] the separators' new iterate (this iteration)
+    double2* ulst = xv + T;          // [T] chunk ends (last node): u, y, zeta
+    double2* ylst = ulst + T;
+    double2* zlst = ylst + T;
+    double2* pub = zlst + T;         // [2][W][5]
+    double2* usup = pub + 2 * W * 5; // [33] u at the super-separators (every CTA)
+    double2* zsb = usup + 33;        // [2][33] the iterate at the super-separators (ping-pong)
+    double2* hc = zsb + 2 * 33;      // [3][L][T] chunk iterates of steps n-2, n-3, n-4
+    double2* hs = hc + 3 * L * T;    // [3][T] own separators' iterates, same steps
+    double2* hq = hs + 3 * T;        // [3][33] super-separators' iterates, same steps
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(hq + 3 * 33);   // [2][2]
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
+    const int p = rank * T + tid;
+    const int sidx = blockIdx.x / C;
+    const double2 zero = make_double2(0.0, 0.0);
+    const bool valid = (p <= P) && (sidx < a.nsys);
+    MarchSys sy = {0, 0, 0, -1, -1, -1, -1, 0};
+    int j = 0, Pj = 0, Lp = 0, sp = 0, goff = 0, tcf = 0;
+    if (sidx < a.nsys) {
+        sy = a.sys[sidx];
+        j = sy.sub;
+        Pj = a.sub_P[j];
+        goff = a.sub_goff[j];
+        tcf = a.sub_tc[j];
+    }
+    if (valid) {
+        Lp = (p < P) ? a.clen[j * P + p] : 0;
+        sp = a.sep_pos[j * (P + 1) + p];
+    }
+    const int Q = (Pj + 31) / 32;
+    const int q = p >> 5;
+    const bool zero_u0 = (sy.flags & SYS_ZERO_U0) != 0;
+    const bool realsep = valid && (p <= Pj);
+    const bool sup = realsep && (lane == 0 || p == Pj);
+    const int qsup = (p == Pj) ? Q : q;
+    const int m = (32 * q < Pj) ? min(31, Pj - 1 - 32 * q) : 0;
+    const bool member = realsep && lane >= 1 && lane <= m;
+    const int rsup = (p + 1 == Pj) ? Q : (((p + 1) & 31) == 0 ? (p + 1) >> 5 : -1);
+    const size_t S = P + 1;
+    const double2* F = a.fac + (size_t)j * L * 4 * P + (p < P ? p : 0);
+    const double2* sE_l = a.sep + (size_t)(j * 3 + 0) * S;
+    const double2* sE_r = a.sep + (size_t)(j * 3 + 1) * S;
+    const double2* tpc = a.tl_pcr + (size_t)j * 10 * S + (valid ? p : 0);
+    const double2* tax = a.tl_aux + (size_t)j * 3 * S + (valid ? p : 0);
+    const double2* tred = a.tl_red + (size_t)j * 13 * 32 + lane;
+    const double cw = na.cw, coef = na.coef;
+    const bool le = (p == 0), re = (p == Pj);
+    const bool own_left = realsep && !le && lane != 0;   // the chunk on the left is in my warp
+
+    double2 u[L], z[L], f[L], y[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        u[i] = (valid && i < Lp && !zero_u0) ? a.u0[goff + sp + 1 + i] : zero;
+        z[i] = u[i];                                  // zeta^0 of step 1 is v_0 = u_0
+        f[i] = zero;
+        y[i] = zero;
+    }
+    {
+        const double2 u0s = (realsep && !zero_u0) ? a.u0[goff + sp] : zero;
+        usep[tid] = u0s;
+        zsep[tid] = u0s;
+    }
+    if (wl == 0 && lane <= Q && sidx < a.nsys) {
+        const int ps = (lane < Q) ? 32 * lane : Pj;
+        const double2 us = zero_u0 ? zero : a.u0[goff + a.sep_pos[j * S + ps]];
+        usup[lane] = us;
+        zsb[lane] = us;
+    }
+    if (tid < 4) red[tid] = 0ull;
+    cl.sync();
+
+    int cur = 0;                     // zsb + 33 cur: the super-separators' current iterate
+    int itg = 0;                     // inner iterations so far (parity of pub and red)
+    int itmax = 0;
+    unsigned long long itsum = 0;
+    bool nl_fail = false;
+    double2 lin = zero, rin = zero;
+    for (int t = 1; t <= nt; ++t) {
+        // ---- step-constant right-hand sides: chunks, and my separator's own part ------
+        double2 uf = zero, ul = zero;
+        if (valid && Lp > 0) {
+            const double2 uL = usep[tid];
+            const double2 uR = (rsup >= 0) ? usup[rsup] : usep[tid + 1];
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    const double2 left = (i == 0) ? uL : u[i - 1];
+                    double2 right;
+                    if (i + 1 < L)
+                        right = (i == Lp - 1) ? uR : u[i + 1];
+                    else
+                        right = uR;
+                    f[i] = make_double2(fma(4.0, u[i].x, left.x + right.x),
+                                        fma(4.0, u[i].y, left.y + right.y));
+                    if (i == 0) uf = u[i];
+                    ul = csel(i == Lp - 1, u[i], ul);
+                }
+            }
+            ulst[tid] = ul;
+        }
+        __syncwarp();
+        // own part: (2 or 4) u_s + u of the right chunk's first node, boundary data; the
+        // left chunk's last node joins it here (own_left) or through lane 31's part
+        double2 fown = zero;
+        if (realsep) {
+            const double2 us = usep[tid];
+            const double cs = (le || re) ? 2.0 : 4.0;
+            fown = make_double2(fma(cs, us.x, re ? 0.0 : uf.x), fma(cs, us.y, re ? 0.0 : uf.y));
+            if (own_left) fown = cadd(fown, ulst[tid - 1]);
+            if (le && (tcf & 1)) {
+                if (sy.flags & SYS_IMP_L)
+                    lin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                else
+                    lin = (sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l + t - 1] : zero;
+                fown = cfms(lin, a.inv_ik, fown);
+            }
+            if (re && (tcf & 2)) {
+                if (sy.flags & SYS_IMP_R)
+                    rin = (t == 1) ? make_double2(1.0, 0.0) : zero;
+                else
+                    rin = (sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r + t - 1] : zero;
+                fown = cfms(rin, a.inv_ik, fown);
+            }
+        }
+        // ---- start of the fixed point: cubic extrapolation (t >= 5), linear (t = 2..4)
+        auto predict = [&](double2 z1, double2 z2, double2 z3, double2 z4) -> double2 {
+            if (t >= 5)
+                return make_double2(fma(4.0, z1.x + z3.x, fma(-6.0, z2.x, -z4.x)),
+                                    fma(4.0, z1.y + z3.y, fma(-6.0, z2.y, -z4.y)));
+            if (t >= 2) return make_double2(fma(2.0, z1.x, -z2.x), fma(2.0, z1.y, -z2.y));
+            return z1;
+        };
+        if (valid && Lp > 0) {
+#pragma unroll
+            for (int i = 0; i < L; ++i) {
+                if (i < Lp) {
+                    double2* h = hc + (size_t)i * T + tid;        // steps n-2, n-3, n-4
+                    const double2 z2 = h[0], z3 = h[(size_t)L * T], z4 = h[(size_t)2 * L * T];
+                    h[(size_t)2 * L * T] = z3;
+                    h[(size_t)L * T] = z2;
+                    h[0] = z[i];
+                    z[i] = predict(z[i], z2, z3, z4);
+                }
+            }
+        }
+        if (realsep) {
+            const double2 z1 = zsep[tid], z2 = hs[tid], z3 = hs[T + tid], z4 = hs[2 * T + tid];
+            hs[2 * T + tid] = z3;
+            hs[T + tid] = z2;
+            hs[tid] = z1;
+            zsep[tid] = predict(z1, z2, z3, z4);
+        }
+        if (wl == 0 && lane <= Q) {
+            double2* zc = zsb + 33 * cur;
+            const double2 z1 = zc[lane], z2 = hq[lane], z3 = hq[33 + lane], z4 = hq[66 + lane];
+            hq[66 + lane] = z3;
+            hq[33 + lane] = z2;
+            hq[lane] = z1;
+            zc[lane] = predict(z1, z2, z3, z4);
+        }
+        __syncthreads();
+        // ---- inner fixed point (Eq. AvMNL), the stopping rule of k_march_nl ------------
+        int used = na.maxit;
+        double dm_prev = 0.0;
+        bool done = false;
+        for (int it = 0; it < na.maxit; ++it, ++itg) {
+            const int slot = (itg & 1) * W * 5, rs = itg & 1;
+            const double2* zc = zsb + 33 * cur;       // current iterate, super-separators
+            double2* zn = zsb + 33 * (cur ^ 1);       // the new one (warp 0, phase D)
+            // A: chunk right-hand side with b_f(zeta), local LU sweeps
+            double2 zl_own = zero;
+            if (valid && Lp > 0) {
+                const double2 zL = zsep[tid];
+                const double2 zR = (rsup >= 0) ? zc[rsup] : zsep[tid + 1];
+                double Wprev = coef * nrm2(zL);
+                double W0 = coef * nrm2(z[0]);
+                double2 zprev = zero, cprev = zero;
+#pragma unroll
+                for (int i = 0; i < L; ++i) {
+                    if (i < Lp) {
+                        const double2 zl_ = (i == 0) ? zL : z[i - 1];
+                        double2 zr_;
+                        if (i + 1 < L)
+                            zr_ = (i == Lp - 1) ? zR : z[i + 1];
+                        else
+                            zr_ = zR;
+                        const double Wr = coef * nrm2(zr_);
+                        const double2 sx = bf_sum(true, true, zl_, z[i], zr_, Wprev, W0, Wr);
+                        const double2 rhs = sub_bf(f[i], sx, cw);
+                        const double2 zz = (i == 0) ? rhs : cfms(cprev, zprev, rhs);
+                        y[i] = zz;
+                        zprev = zz;
+                        cprev = F[(i * 4 + 1) * P];
+                        Wprev = W0;
+                        W0 = Wr;
+                        zl_own = csel(i == Lp - 1, z[i], zl_own);
+                    }
+                }
+                double2 ynext = zero, yl = zero;
+#pragma unroll
+                for (int i = L - 1; i >= 0; --i) {
+                    if (i < Lp) {
+                        double2 yi = cmul(F[(i * 4 + 0) * P], y[i]);
+                        if (i != Lp - 1) yi = cfms(F[(i * 4 + 1) * P], ynext, yi);
+                        else yl = yi;
+                        y[i] = yi;
+                        ynext = yi;
+                    }
+                }
+                ylst[tid] = yl;
+                zlst[tid] = zl_own;
+            }
+            __syncwarp();
+            // B: separator right-hand sides.  Right element of separator p: nodes (p, first
+            // of chunk p); left element: (last of chunk p - 1, p).
+            double2 d = zero;
+            if (realsep) {
+                const double2 zs = zsep[tid];
+                const double W0 = coef * nrm2(zs);
+                double2 sb = zero;
+                if (!re) {
+                    const double2 zr_ = z[0];
+                    sb = bf_sum(false, true, zero, zs, zr_, 0.0, W0, coef * nrm2(zr_));
+                }
+                if (own_left) {
+                    const double2 zl_ = zlst[tid - 1];
+                    sb = cadd(sb, bf_sum(true, false, zl_, zs, zero, coef * nrm2(zl_), W0, 0.0));
+                }
+                d = sub_bf(fown, sb, cw);
+                if (own_left) d = cfms(sE_l[p], ylst[tid - 1], d);
+                if (!re) d = cfms(sE_r[p], y[0], d);
+            }
+            // lane 31: its chunk's part of the next super-separator's row (left element)
+            double2 p1 = zero;
+            if (valid && lane == 31 && p + 1 <= Pj) {
+                const double2 zs1 = zc[rsup];        // p + 1 is a super-separator
+                const double2 sl = bf_sum(true, false, zl_own, zs1, zero, coef * nrm2(zl_own),
+                                          coef * nrm2(zs1), 0.0);
+                p1 = cfms(sE_l[p + 1], ylst[tid], sub_bf(ulst[tid], sl, cw));
+            }
+            // C: super-chunk PCR in registers, publication, cluster barrier
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const int st = 1 << k;
+                const double2 dm = nl_shup(d, st), dp = nl_shdn(d, st);
+                if (member) d = cfma(tpc[(2 * k + 1) * S], dp, cfma(tpc[(2 * k) * S], dm, d));
+            }
+            if (member) d = cmul(d, tax[0]);
+            {
+                double2* pb = pub + slot + wl * 5;
+                if (lane == 0 && realsep) pb[0] = d;
+                if (lane == 31) pb[1] = p1;
+                if (lane == 1 && member) pb[2] = d;
+                if (member && lane == m) pb[3] = d;
+                if (p == Pj && lane != 0 && valid) pb[4] = d;
+            }
+            cl.sync();
+            if (tid == 0) {   // the next iteration's partial maxima start at zero
+                red[2 * (rs ^ 1) + 0] = 0ull;
+                red[2 * (rs ^ 1) + 1] = 0ull;
+            }
+            // D: the reduced system, warp 0 of every CTA: the new iterate at all
+            // super-separators
+            if (wl == 0 && sidx < a.nsys) {
+                double2 r = zero;
+                if (lane <= Q) {
+                    auto pubof = [&](int qq) -> const double2* {
+                        const int home = (32 * qq) / T;
+                        double2* base = (home == rank) ? pub : cl.map_shared_rank(pub, home);
+                        return base + slot + ((32 * qq) % T) / 32 * 5;
+                    };
+                    if (lane == Q && (Pj & 31) != 0) {
+                        r = pubof(Q - 1)[4];
+                    } else {
+                        r = pubof(lane)[0];
+                        if (lane >= 1) r = cadd(r, pubof(lane - 1)[1]);
+                    }
+                    const double2 cL = tred[11 * 32], cU = tred[12 * 32];
+                    if (lane >= 1 && (cL.x != 0.0 || cL.y != 0.0))
+                        r = cfms(cL, pubof(lane - 1)[3], r);
+                    if (lane < Q && (cU.x != 0.0 || cU.y != 0.0))
+                        r = cfms(cU, pubof(lane)[2], r);
+                }
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int st = 1 << k;
+                    if (st > Q) break;   // no neighbour within the Q + 1 unknowns: zero couplings
+                    const double2 rm = nl_shup(r, st), rp = nl_shdn(r, st);
+                    if (lane <= Q)
+                        r = cfma(tred[(2 * k + 1) * 32], rp, cfma(tred[(2 * k) * 32], rm, r));
+                }
+                if (lane <= Q) zn[lane] = cmul(r, tred[10 * 32]);
+            }
+            __syncthreads();
+            // E: separator values of the new iterate
+            double2 v = zero;
+            if (member) {
+                v = cfms(tax[S], zn[q], d);
+                v = cfms(tax[2 * S], zn[q + 1], v);
+            } else if (sup) {
+                v = zn[qsup];
+            }
+            xv[tid] = v;
+            __syncwarp();
+            // F: chunk values of the new iterate, the change, partial maxima
+            double dmax = 0.0, zmax = 0.0;
+            if (valid && Lp > 0) {
+                const double2 vR = (rsup >= 0) ? zn[rsup] : xv[tid + 1];
+#pragma unroll
+                for (int i = 0; i < L; ++i) {
+                    if (i < Lp) {
+                        double2 vi = cfms(F[(i * 4 + 2) * P], v, y[i]);
+                        vi = cfms(F[(i * 4 + 3) * P], vR, vi);
+                        dmax = fmax(dmax, nrm2(csub(vi, z[i])));
+                        zmax = fmax(zmax, nrm2(z[i]));
+                        z[i] = vi;
+                    }
+                }
+            }
+            if (realsep) {
+                const double2 zs = zsep[tid];
+                dmax = fmax(dmax, nrm2(csub(v, zs)));
+                zmax = fmax(zmax, nrm2(zs));
+                zsep[tid] = v;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+            }
+            if (lane == 0) {
+                atomicMax(red + 2 * rs + 0, dbits(dmax));
+                atomicMax(red + 2 * rs + 1, dbits(zmax));
+            }
+            // G: every CTA's partials, the same decision in every thread of the cluster
+            cl.sync();
+            double dm = 0.0, zm = 0.0;
+            for (int r = 0; r < C; ++r) {
+                const unsigned long long* b = (r == rank) ? red : cl.map_shared_rank(red, r);
+                dm = fmax(dm, __longlong_as_double((long long)b[2 * rs + 0]));
+                zm = fmax(zm, __longlong_as_double((long long)b[2 * rs + 1]));
+            }
+            cur ^= 1;                                  // the new iterate is current
+            const double lim = na.tol * na.tol * fmax(1.0, zm);
+            bool conv = dm <= lim;
+            if (!conv && it >= 1 && dm_prev > 0.0 && dm < 0.0625 * dm_prev) {
+                const double rho = sqrt(dm / dm_prev);
+                const double qf = rho / (1.0 - rho);
+                conv = dm * qf * qf <= lim;
+            }
+            dm_prev = dm;
+            if (conv) {
+                used = it + 1;
+                done = true;
+                ++itg;
+                break;
+            }
+        }
+        if (!done) nl_fail = true;      // cap reached without convergence
+        if (used > itmax) itmax = used;
+        itsum += (unsigned long long)used;
+        // ---- v_n = zeta: CN update and fluxes -----------------------------------------
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (valid && i < Lp) u[i] = make_double2(fma(2.0, z[i].x, -u[i].x), fma(2.0, z[i].y, -u[i].y));
+        if (realsep) {
+            const double2 v = zsep[tid];
+            const double2 uo = usep[tid];
+            usep[tid] = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
+            if (p == 0) {
+                if ((tcf & 1) && sy.out_a >= 0 && a.gout)
+                    a.gout[(size_t)sy.out_a + t - 1] = csub(cmul(a.two_sigma, v), lin);
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
+            }
+            if (p == Pj) {
+                if ((tcf & 2) && sy.out_b >= 0 && a.gout)
+                    a.gout[(size_t)sy.out_b + t - 1] = csub(cmul(a.two_sigma, v), rin);
+                if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
+            }
+        }
+        if (wl == 0 && lane <= Q) {
+            const double2 v = zsb[33 * cur + lane], uo = usup[lane];
+            usup[lane] = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
+        }
+        __syncthreads();
+    }
+    // ---- final state ----------------------------------------------------------------
+    bool bad = false;
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < L; ++i)
+            if (i < Lp) bad |= !cfinite(u[i]);
+        if ((sy.flags & SYS_WRITE_UT) && a.uT) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.uT[goff + sp + 1 + i] = u[i];
+        }
+        if (realsep) {
+            const double2 us = usep[tid];
+            bad |= !cfinite(us);
+            if ((sy.flags & SYS_WRITE_UT) && a.uT && (sp > 0 || !(tcf & 1))) a.uT[goff + sp] = us;
+        }
+        if (p == 0 && rank == 0) {
+            if (na.iters) atomicMax(na.iters + sidx, itmax);
+            if (na.pit) atomicAdd(na.pit, itsum * (unsigned long long)a.sub_n[j]);
+        }
+    }
+    if (bad) atomicOr(a.status, ST_NONFINITE);
+    if (nl_fail && p == 0 && valid) atomicOr(a.status, ST_NL_NOCONV);
+    cl.sync();   // keep this CTA's shared memory alive until every CTA of the cluster is done
+}
+
 template <int L>
 static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s, int mode) {
     // the previous three steps' iterates ([L][T] and separators each)
@@ -659,6 +1121,15 @@ static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s, int mode) {
     void (*kern)(const NlArgs) = k_march_nl<L, 0>;
     if (mode == 1) kern = k_march_nl<L, 1>;
     if (mode == 2) kern = k_march_nl<L, 2>;
+    // one system spread over a cluster with its two-level separator data: the two-level
+    // solve (Robin or Neumann ends).  A system alone in its CTA keeps the CTA-wide PCR,
+    // which measured faster there (its levels cost a CTA barrier, not a cluster one).
+    const MarchArgs& m = na.m;
+    if (mode == 0 && m.tl_pcr && m.two_level && !m.s02 && !m.kap && m.C > 1 &&
+        (m.T & 31) == 0) {
+        kern = k_march_nl_tl<L>;
+        smem = swr_march_nl_tl_smem_bytes(L, m.T);
+    }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
         return -1;
@@ -694,6 +1165,9 @@ int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef
     a.fac = fs.fac;
     a.sep = fs.sep;
     a.pcr = fs.pcr;
+    a.tl_pcr = fs.tl_ok ? fs.tl_pcr : nullptr;
+    a.tl_aux = fs.tl_aux;
+    a.tl_red = fs.tl_red;
     NlArgs na{a, cw, coef, tol, maxit, iters, pit};
     switch (fs.L) {
         case 4: return launch_nl_t<4>(na, ngroups, s, mode);

@@ -126,3 +126,34 @@ def test_cluster_path_is_bit_reproducible(vkind):
         outs.append(go.cpu().numpy().tobytes())
     plan.destroy()
     assert len(set(outs)) == 1
+
+
+
+def _nl_cluster_case(name):
+    if name == "c7_empty_cta":      # 501 separators on 7 CTAs of 96 threads: the last has none
+        return W.config5(nsub=8, nx=20001, nt=12)
+    if name == "c6":                # 401 separators on 6 CTAs
+        return W.config5(nsub=2, nx=4001, nt=12)
+    wl = W.config5(nsub=4, nx=5121, nt=12)   # uneven: 145, 257, 301, 325 separators on 5 CTAs
+    wl.off = np.array([0, 720, 2000, 3500, 5120], dtype=np.int32)
+    return wl
+
+
+@pytest.mark.parametrize("name", ["c7_empty_cta", "c6", "ragged_c5"])
+def test_nonlinear_two_level_cluster_march_matches_oracle(name):
+    """The nonlinear march of systems spread over a cluster with the two-level separator
+    solve (warp-shuffle PCR in blocks of 32 and a reduced system of the super-separators,
+    in the modelled launch shape with 4-node chunks), against the oracle's nonlinear R g
+    and against the same launch with the cluster-wide PCR."""
+    wl = _nl_cluster_case(name)
+    g = 0.05 * W.random_interface(wl.nblk, wl.nt, 43)
+    gi = torch.tensor(g.ravel(), dtype=torch.complex128, device="cuda")
+    outs = []
+    for tl in (0, -1):
+        plan = gpu_plan(wl, tuning={"autotune": -1, "two_level": tl})
+        go = torch.zeros_like(gi)
+        plan.apply_R(gi, go)
+        plan.destroy()
+        outs.append(go.cpu().numpy())
+    assert rel(outs[0], O.apply_R(problem(wl), g)) < TOL_MARCH
+    assert rel(outs[0], outs[1]) < 1e-11

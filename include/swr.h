@@ -138,7 +138,8 @@ typedef struct swr_desc {
  * swr_plan / swr_plan_batch use the defaults. */
 typedef struct swr_tuning {
     int32_t chunk_L;            /* chunk length of the partitioned marches: 0 (default)  */
-                                /* chosen per launch; 4, 8, 12 or 16 fixed              */
+                                /* chosen per launch; 4, 8, 12 or 16 fixed; the         */
+                                /* nonlinear march takes 2, 4 or 8 (2: nonlinear only)  */
     int32_t autotune;           /* launch shapes: 0 (default) measured by probe marches  */
                                 /* at the first build; -1 the modelled shape            */
     int32_t toeplitz_fft;       /* (I - L) x: 0 (default) FFT convolution for           */

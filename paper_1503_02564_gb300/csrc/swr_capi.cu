@@ -83,7 +83,7 @@ struct swr_plan_s {
     int *d_n = nullptr, *d_goff = nullptr, *d_loff = nullptr, *d_tc = nullptr;
     double2 *d_dg = nullptr, *d_od = nullptr;       // A - B for V (static) or V0
     double2 *d_dg0 = nullptr, *d_od0 = nullptr;     // A - B for V = 0
-    FactorSet fsL[4], fs0L[4];     // chunked factorisations for L = 4, 8, 16, 12 (V and V = 0)
+    FactorSet fsL[5], fs0L[5];     // chunked factorisations for L = 4, 8, 16, 12, 2 (V and V = 0)
     swr_tuning tune{};             // execution choices (swr_plan_ex; zero: defaults)
     int forceL = 0;                // tune.chunk_L (0: chosen per launch)
     bool autotune = true;          // tune.autotune >= 0: measured launch shapes
@@ -381,11 +381,13 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC, int fi
         L = fixL;
     } else if (kind == MK_TDEP) {
         L = 4;   // per-step refactorisation keeps LU, spikes and state in registers
+    } else if (kind == MK_NL && (p->forceL == 2 || p->forceL == 4 || p->forceL == 8)) {
+        L = p->forceL;
     } else if (kind == MK_NL || kind == MK_ADJ) {
         // state, right-hand side, iterate and solve (or the adjoint sums) per node
         // in registers: L <= 8
         L = ((long long)(chunks_for(p->nmax, 8) + 1) * nsys >= want) ? 8 : 4;
-    } else if (p->forceL) {
+    } else if (p->forceL && p->forceL != 2) {
         L = p->forceL;
     } else {
         for (int k = 0; k < 3; ++k) {
@@ -428,7 +430,7 @@ MarchCfg march_config(const swr_plan_t p, int nsys, int kind = MK_STATIC, int fi
     return c;
 }
 
-inline int lidx(int L) { return L == 4 ? 0 : (L == 8 ? 1 : (L == 16 ? 2 : 3)); }
+inline int lidx(int L) { return L == 4 ? 0 : (L == 8 ? 1 : (L == 16 ? 2 : (L == 2 ? 4 : 3))); }
 
 inline double2 cmul_h(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -642,8 +644,11 @@ swr_status tune_march(swr_plan_t p, int kind, bool zero_potential, const MarchSy
     const MarchCfg guess = march_config(p, nsys, kind);
     std::vector<int> Ls;
     if (kind == MK_TDEP) Ls = {4};
-    else if (kind == MK_NL || kind == MK_ADJ) Ls = {8, 4};
-    else if (p->forceL) Ls = {p->forceL};
+    else if (kind == MK_NL && (p->forceL == 2 || p->forceL == 4 || p->forceL == 8))
+        Ls = {p->forceL};
+    else if (kind == MK_NL) Ls = {8, 4, 2};   // 2: two warps per sub-partition for short systems
+    else if (kind == MK_ADJ) Ls = {8, 4};
+    else if (p->forceL && p->forceL != 2) Ls = {p->forceL};
     else Ls = {16, 12, 8, 4};   // 12: six systems of ~780 nodes in one 384-thread CTA
     std::vector<MarchCfg> cands;
     cands.push_back(guess);
@@ -1450,7 +1455,7 @@ void swr_destroy(swr_plan_t p) {
     cudaStreamSynchronize(p->s);
     cudaFree(p->d_n); cudaFree(p->d_goff); cudaFree(p->d_loff); cudaFree(p->d_tc);
     cudaFree(p->d_dg); cudaFree(p->d_od); cudaFree(p->d_dg0); cudaFree(p->d_od0);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 5; ++k) {
         swr_factor_free(p->fsL[k]);
         swr_factor_free(p->fs0L[k]);
     }
@@ -1499,8 +1504,8 @@ static swr_status plan_create(const swr_desc* ds, int count, const swr_tuning* t
     if (!ds || count < 1) return SWR_ERR_ARG;
     if (tuning) {
         const swr_tuning& u = *tuning;
-        if (!(u.chunk_L == 0 || u.chunk_L == 4 || u.chunk_L == 8 || u.chunk_L == 12 ||
-              u.chunk_L == 16) ||
+        if (!(u.chunk_L == 0 || u.chunk_L == 2 || u.chunk_L == 4 || u.chunk_L == 8 ||
+              u.chunk_L == 12 || u.chunk_L == 16) ||
             u.debug < 0)
             return SWR_ERR_ARG;
     }
@@ -1639,7 +1644,7 @@ static swr_status plan_create(const swr_desc* ds, int count, const swr_tuning* t
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
     if (p->nsm <= 0) p->nsm = 152;
-    p->forceL = p->tune.chunk_L;                 // 0, 4, 8, 12 or 16 (validated)
+    p->forceL = p->tune.chunk_L;                 // 0, 2, 4, 8, 12 or 16 (validated)
     p->autotune = p->tune.autotune >= 0;
     p->two_level = p->tune.two_level >= 0 ? 1 : 0;
     swr_status st = SWR_OK;

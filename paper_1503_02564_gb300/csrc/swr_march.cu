@@ -687,6 +687,11 @@ static int launch_factor_batch(FactorSet& fs, int N, const int* d_n, const int* 
     dim3 grid((fs.P + 127) / 128, N, nb);
     double2* fac = fs.fac + (size_t)t0 * fs.fstride;
     switch (fs.L) {
+        case 2:
+            k_factor_chunks<2><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
+                                                    fs.sep_pos, fs.clen, fac, fs.tips, status, ldd,
+                                                    fs.fstride);
+            break;
         case 4:
             k_factor_chunks<4><<<grid, 128, 0, s>>>(N, fs.P, d_n, d_loff, dg, od, fs.sub_P,
                                                     fs.sep_pos, fs.clen, fac, fs.tips, status, ldd,

@@ -1170,6 +1170,7 @@ int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef
     a.tl_red = fs.tl_red;
     NlArgs na{a, cw, coef, tol, maxit, iters, pit};
     switch (fs.L) {
+        case 2: return launch_nl_t<2>(na, ngroups, s, mode);
         case 4: return launch_nl_t<4>(na, ngroups, s, mode);
         case 8: return launch_nl_t<8>(na, ngroups, s, mode);
         default: return -2;

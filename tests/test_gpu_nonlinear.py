@@ -73,6 +73,23 @@ def test_nonlinear_apply_R_matches_oracle(case):
     assert rel(go.cpu().numpy(), O.apply_R(problem(wl), g)) < TOL_MARCH
 
 
+@pytest.mark.parametrize("case", ["config5_small", "config5_N16", "ragged"])
+@pytest.mark.parametrize("L", [2, 4, 8])
+def test_nonlinear_apply_R_fixed_chunk_length(case, L):
+    """The nonlinear march with each chunk length it is built for, in the modelled launch
+    shape: with 2-node chunks config5_small's subdomains (168 separators) spread over
+    clusters of two CTAs (two-level separator solve), the others run one per CTA; the
+    ragged case has a subdomain of three nodes (one chunk of one node)."""
+    wl = CASES[case]()
+    plan = gpu_plan(wl, tuning={"chunk_L": L, "autotune": -1})
+    g = 0.05 * W.random_interface(wl.nblk, wl.nt, 47)
+    gi = torch.tensor(g.ravel(), dtype=torch.complex128, device="cuda")
+    go = torch.zeros_like(gi)
+    plan.apply_R(gi, go)
+    plan.destroy()
+    assert rel(go.cpu().numpy(), O.apply_R(problem(wl), g)) < TOL_MARCH
+
+
 @pytest.mark.parametrize("precond", [0, 1, 3])
 def test_nonlinear_solve_reproduces_monodomain(precond):
     """precond 0 is the classical iteration g <- R_nl g, which needs a contracting

@@ -651,10 +651,11 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
 
 // ---------------------------------------------------------------------------
 // The nonlinear march of one system spread over a cluster of C > 1 CTAs with the
-// two-level separator solve of the constant-matrix march (FactorSet.tl_*): every inner iteration solves its separators with warp-shuffle PCR in blocks of 32
-// and a reduced system of at most 32 super-separators that warp 0 of every CTA solves,
-// with one cluster barrier, and a second one for the convergence test, where the
-// cluster-wide PCR took one per level.  MODE 0 (no record, no gradient), Robin or
+// two-level separator solve of the constant-matrix march (FactorSet.tl_*): every inner
+// iteration solves its separators with warp-shuffle PCR in blocks of 32 and a reduced
+// system of at most 32 super-separators that warp 0 of every CTA solves, with one cluster
+// barrier, and a second one for the convergence test, where the cluster-wide PCR took one
+// per level.  MODE 0 (no record, no gradient), Robin or
 // Neumann ends.  Thread p = rank T + tid owns separator p and chunk p; T is a multiple
 // of 32.  Per step: the step-constant right-hand sides, the start of the fixed point,
 // then per inner iteration

@@ -162,9 +162,9 @@ def workload_name_nonlinear(nt=1000):
     return ("swr_nonlinear: x in (-20,20), 20001 P1 nodes, T=%g dt=5e-4 (%d steps), N=32, "
             "V=|u|^2+V0, V0=-sum of 6 seeded Gaussian wells (depth 2-10), u0=sech(x)e^{2ix}, "
             "Robin p=sqrt(5)e^{-i pi/4}, inner fixed point to 1e-13 per step, outer fixed point "
-            "preconditioned by the V0 interface operator to 1e-10 + final march; then "
-            "J = ||u(T) - u_target||_M^2 and dJ/dV0 by swr_adjoint (monodomain discrete "
-            "adjoint, the library's checkpoint interval: every step recorded when it fits)"
+            "preconditioned by the V0 interface operator to 1e-10 + final march (recording "
+            "v_n of every step when it fits); then J = ||u(T) - u_target||_M^2 and dJ/dV0 by "
+            "swr_adjoint (monodomain discrete adjoint about the recorded v_n, one segment)"
             % (nt * 5e-4, nt))
 
 

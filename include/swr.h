@@ -273,6 +273,11 @@ swr_status swr_build_interface(swr_plan_t p, const double *V, const double *u0);
  * is their superposition weighted by the converged fluxes plus the zero-flux
  * march's final state; info->interface_jump then comes from the final residual
  * (v_j(b_j) - v_{j+1}(a_{j+1}) = ((R g - g)[l_{j+1}] - (R g - g)[r_j]) / 2p).
+ * SWR_V_NONLINEAR with Robin or Neumann ends (single instance): after a converged
+ * solve the final march also records v_n of every step (nt x nx complex, allocated
+ * once when that takes at most 1/8 of the free device memory, and kept for
+ * swr_adjoint), so that a following swr_adjoint with one checkpoint segment runs only
+ * the adjoint march.
  * g:    cplx[(2N-2) * nt]; on entry the initial guess g0 (ignored if
  *       g_is_initial == 0, then g0 = 0), on exit the converged interface vector.
  *       May be NULL (then g0 = 0 and the result is not returned).
@@ -324,8 +329,8 @@ swr_status swr_misfit(swr_plan_t p, const double *uT, const double *u_target, do
  *   dJ_dV:      double[nx] (device), overwritten with dJ/dV_k for the nodal V;
  *               SWR_V_TIME: double[(nt + 1) nx], row m = dJ/dV(t_m, .) (the layout of V);
  *   ckpt_every: checkpoint interval K in time steps (<= 0: every step recorded in one
- *               segment when nt x nx complex take at most 1/8 of the free device memory,
- *               else 50).
+ *               segment when nt x nx complex take at most 1/8 of the free device memory
+ *               or are already allocated, else 50).
  * Method (static V): the discrete adjoint of the Crank-Nicolson march,
  * conjugated and scaled, is the same march run from (dt/2i) conj(ubar); it is
  * solved by SWR on the plan's own interface problem (same Toeplitz columns and
@@ -344,6 +349,10 @@ swr_status swr_misfit(swr_plan_t p, const double *uT, const double *u_target, do
  * Re(v^T (dM_W/dW_k) w) = (2i/dt) M z, by the march's inner fixed point about the
  * recorded forward v_n (relative test nl_tol, cap nl_maxit: SWR_ERR_NOT_CONVERGED
  * when reached), z <- 2 w - z, and dJ/dV0_k = -2 Re sum_n w_n^T (dM_V/dV_k) v_n.
+ * With one segment (K = nt) the recorded v_n are the last swr_solve's final march
+ * when it recorded them (see swr_solve: the converged SWR trajectory, equal to the
+ * monodomain one to the solve's tolerance); otherwise, and with checkpoints, the
+ * monodomain forward march recomputes them.
  * The whole grid is one system on a thread-block cluster (at most 16 CTAs of 256
  * threads: nx <= 20476, or 36856 with 8-node chunks; SWR_ERR_UNSUPPORTED above).
  * Device memory: (ceil(nt/K) + K + 5) nx complex plus two interface vectors.

@@ -70,6 +70,9 @@ struct swr_plan_s {
     bool solved = false;
     // adjoint work, allocated by the first swr_adjoint (checkpoint interval adj_K)
     int adj_K = 0;
+    // nonlinear plans: d_slab holds v_n of every step of the last solve's final march
+    // (adj_K == nt), so swr_adjoint need not re-march the forward scheme
+    bool nl_rec = false;
     double2 *d_ckpt = nullptr, *d_slab = nullptr, *d_ya = nullptr, *d_yb = nullptr;
     double2 *d_dy = nullptr, *d_gy = nullptr;
     double *d_gint = nullptr, *d_gl = nullptr, *d_gr = nullptr, *d_part = nullptr;
@@ -571,9 +574,10 @@ int launch_cfg(swr_plan_t p, const MarchCfg& cfg, int kind, bool zero_potential,
     if (kind == MK_TDEP)
         return swr_launch_march_tdep(fs, a, p->d_V, p->nx, p->h, kappa,
                                      cmul_h(p->sigma0, p->inv_ik), cfg.ngroups, p->s);
-    if (kind == MK_NL)
+    if (kind == MK_NL)   // mode 0, or 1 recording v_n into seg.vrec
         return swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,
-                                   p->d.nl_maxit, nullptr, cfg.ngroups, p->s, 0, p->d_pit);
+                                   p->d.nl_maxit, nullptr, cfg.ngroups, p->s, seg.mode,
+                                   p->d_pit);
     const int rc = swr_launch_march(fs, a, ngroups, p->s, seg.mode);
     if (rc == 0 && (cfg.C > 1 || (cfg.G == 1 && !cfg.ragged)) && seg.mode == 0 &&
         fs.nsteps == 1 && fs.tl_ok && p->two_level)
@@ -588,13 +592,19 @@ inline int march_kind(swr_plan_t p, bool zero_potential) {
     return MK_STATIC;
 }
 
+// vrec (nonlinear marches only): also record v_n of every step, rows of nx values
 swr_status run_march(swr_plan_t p, bool zero_potential, const MarchSys* d_sys, int nsys,
                      const double2* gin, double2* gout, double2* uT, double2* trace,
-                     const double2* u0, long long work) {
+                     const double2* u0, long long work, double2* vrec = nullptr) {
     const int kind = march_kind(p, zero_potential);
     const MarchCfg cfg = march_config(p, nsys, kind);
     const int pi = prof_begin(p, kind == MK_NL ? 3 : 0, work);
     SegArgs sa;
+    if (vrec) {
+        if (kind != MK_NL) return SWR_ERR_UNSUPPORTED;
+        sa.mode = 1;
+        sa.vrec = vrec;
+    }
     if (p->cur_rev && !zero_potential) {   // time-reversed problem: last step's factors first
         sa.fstep0 = p->nt - 1;
         sa.frev = 1;
@@ -1953,6 +1963,7 @@ swr_status swr_build_interface(swr_plan_t p, const double* V, const double* u0) 
     t_debug = p ? p->tune.debug : 0;
     NvtxRange nvtx_range("swr_build_interface");
     if (!p || !V || !u0) return SWR_ERR_ARG;
+    p->nl_rec = false;
     cudaStream_t s = p->s;
     const size_t nb = (size_t)p->nb;
     const size_t nV = (p->d.vkind == SWR_V_TIME) ? (size_t)(p->nt + 1) * p->nx : p->nx;
@@ -2114,6 +2125,7 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
     NvtxRange nvtx_range("swr_solve");
     if (!p) return SWR_ERR_ARG;
     if (!p->built) return SWR_ERR_STATE;
+    p->nl_rec = false;
     cudaStream_t s = p->s;
     swr_info loc{};
     double2* g = g_ ? reinterpret_cast<double2*>(g_) : p->d_gtmp2;
@@ -2156,10 +2168,35 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
                                     p->d_if_inst, p->nif));
         }
     } else {
-        // final march (last step of Algorithms 1-3)
+        // final march (last step of Algorithms 1-3).  Nonlinear plans with Robin or Neumann
+        // ends also record v_n of every step when the record (nt x nx values) takes at most
+        // an eighth of the free device memory: that is the forward trajectory the gradient
+        // is linearised about (the converged SWR solution is the monodomain one), so
+        // swr_adjoint with one checkpoint segment skips its forward re-march.
+        double2* vrec = nullptr;
+        if (st == SWR_OK && p->d.vkind == SWR_V_NONLINEAR && p->d.tc < SWR_TC_S02 &&
+            !p->batched && !p->long_march) {
+            if (p->adj_K != p->nt) {
+                size_t fr = 0, tot = 0;
+                const size_t need = ((size_t)p->nt + 1) * (size_t)p->nx * sizeof(double2);
+                if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && need <= fr / 8) {
+                    cudaFree(p->d_ckpt);
+                    cudaFree(p->d_slab);
+                    p->d_ckpt = p->d_slab = nullptr;
+                    p->adj_K = 0;
+                    swr_status sa = dalloc(&p->d_ckpt, (size_t)p->nx);
+                    if (!sa) sa = dalloc(&p->d_slab, (size_t)p->nt * p->nx);
+                    if (sa) return sa;
+                    p->adj_K = p->nt;
+                }
+                cudaGetLastError();
+            }
+            if (p->adj_K == p->nt) vrec = p->d_slab;
+        }
         swr_status st2 = run_march(p, false, p->d_sys_final, p->N, g, p->d_gtmp, uT, p->d_trace,
-                                   p->d_u0, p->work_R);
+                                   p->d_u0, p->work_R, vrec);
         if (st2) return st2;
+        p->nl_rec = (vrec != nullptr);
         LK(p_jump(p));
     }
     CK(cudaEventRecord(p->ev[3], s));
@@ -2311,7 +2348,9 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
     // re-march of the forward) when the record of nt steps takes at most an eighth of
     // the free device memory, else 50
     int Kdef = 50;
-    if (ckpt_every <= 0) {
+    if (ckpt_every <= 0 && p->adj_K == nt) {
+        Kdef = nt;   // the record of nt steps is already allocated (and may hold the solve's)
+    } else if (ckpt_every <= 0) {
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) == cudaSuccess &&
             (size_t)nt * (size_t)nx * sizeof(double2) <= fr / 8)
@@ -2322,6 +2361,7 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
     const int C = (nt + K - 1) / K;
     swr_status st = SWR_OK;
     if (p->adj_K != K) {
+        p->nl_rec = false;
         cudaFree(p->d_ckpt);
         cudaFree(p->d_slab);
         p->d_ckpt = p->d_slab = nullptr;
@@ -2358,9 +2398,11 @@ swr_status swr_adjoint(swr_plan_t p, const double* ubar_, double* dJdV_, int32_t
         CK(cudaMemsetAsync(p->d_gr, 0, sizeof(double) * nx, s));
         double2* ycur = p->d_ya;
         double2* ynext = p->d_yb;
+        // one segment with the solve's record of v_n: the adjoint march alone
+        const bool rec = (C == 1 && p->nl_rec);
         for (int c = C - 1; c >= 0; --c) {
             const int Kc = std::min(K, nt - c * K);
-            if ((st = mono_nl_march(p, 1, p->d_ckpt + (size_t)c * nx, nullptr, Kc)) ||
+            if ((!rec && (st = mono_nl_march(p, 1, p->d_ckpt + (size_t)c * nx, nullptr, Kc))) ||
                 (st = mono_nl_march(p, 2, ycur, ynext, Kc)))
                 return st;
             std::swap(ycur, ynext);

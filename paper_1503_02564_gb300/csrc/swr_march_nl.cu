@@ -655,8 +655,8 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
 // iteration solves its separators with warp-shuffle PCR in blocks of 32 and a reduced
 // system of at most 32 super-separators that warp 0 of every CTA solves, with one cluster
 // barrier, and a second one for the convergence test, where the cluster-wide PCR took one
-// per level.  MODE 0 (no record, no gradient), Robin or
-// Neumann ends.  Thread p = rank T + tid owns separator p and chunk p; T is a multiple
+// per level.  MODE 0, or 1 (also record v_n of every step into a.vrec, as k_march_nl
+// does); Robin or Neumann ends.  Thread p = rank T + tid owns separator p and chunk p; T is a multiple
 // of 32.  Per step: the step-constant right-hand sides, the start of the fixed point,
 // then per inner iteration
 //   A  chunk right-hand sides with b_f(zeta), local LU solves;
@@ -690,7 +690,7 @@ int swr_march_nl_tl_smem_bytes(int L, int T) {
            (int)sizeof(unsigned long long) * 4;
 }
 
-template <int L>
+template <int L, int MODE>
 __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
     const MarchArgs& a = na.m;
     extern __shared__ double2 sm[];
@@ -1061,6 +1061,15 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
         if (!done) nl_fail = true;      // cap reached without convergence
         if (used > itmax) itmax = used;
         itsum += (unsigned long long)used;
+        if constexpr (MODE == 1) {   // record v_n (an interface node by its left subdomain)
+            double2* row = a.vrec + (size_t)(t - 1) * a.nxrec + goff + sp;
+            if (valid && Lp > 0) {
+#pragma unroll
+                for (int i = 0; i < L; ++i)
+                    if (i < Lp) row[1 + i] = z[i];
+            }
+            if (realsep && !(p == 0 && (tcf & 1))) row[0] = zsep[tid];
+        }
         // ---- v_n = zeta: CN update and fluxes -----------------------------------------
 #pragma unroll
         for (int i = 0; i < L; ++i)
@@ -1126,9 +1135,9 @@ static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s, int mode) {
     // solve (Robin or Neumann ends).  A system alone in its CTA keeps the CTA-wide PCR,
     // which measured faster there (its levels cost a CTA barrier, not a cluster one).
     const MarchArgs& m = na.m;
-    if (mode == 0 && m.tl_pcr && m.two_level && !m.s02 && !m.kap && m.C > 1 &&
+    if ((mode == 0 || mode == 1) && m.tl_pcr && m.two_level && !m.s02 && !m.kap && m.C > 1 &&
         (m.T & 31) == 0) {
-        kern = k_march_nl_tl<L>;
+        kern = (mode == 1) ? k_march_nl_tl<L, 1> : k_march_nl_tl<L, 0>;
         smem = swr_march_nl_tl_smem_bytes(L, m.T);
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=

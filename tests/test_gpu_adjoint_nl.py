@@ -44,6 +44,9 @@ CASES = {
 }
 
 
+LAST_ADJOINT_STATS = {}
+
+
 def gpu_gradient(wl, tgt, K=16, V=None, tc=None):
     from paper_1503_02564_gb300 import swr
     plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
@@ -59,7 +62,10 @@ def gpu_gradient(wl, tgt, K=16, V=None, tc=None):
     J = plan.misfit(uT, torch.tensor(tgt, dtype=torch.complex128, device="cuda"), ubar)
     grad = torch.empty(wl.nx, dtype=torch.float64, device="cuda")
     if K is not None:
+        plan.get_stats(reset=True)
         plan.adjoint(ubar, grad, K)
+        LAST_ADJOINT_STATS.clear()
+        LAST_ADJOINT_STATS.update(plan.get_stats())
     plan.destroy()
     return J, grad.cpu().numpy()
 
@@ -86,11 +92,33 @@ def test_nonlinear_adjoint_with_s02_plan():
 
 
 def test_nonlinear_checkpoint_interval_does_not_change_the_gradient():
+    """Checkpointed segments (the forward trajectory recomputed by the monodomain march
+    from checkpoints of u) give the same gradient for every interval."""
     wl = CASES["small"]()
     tgt = W.misfit_target(wl)
-    ref = gpu_gradient(wl, tgt, K=30)[1]
+    ref = gpu_gradient(wl, tgt, K=15)[1]
     for K in (1, 7, 29):
         assert rel(gpu_gradient(wl, tgt, K=K)[1], ref) < 1e-11, K
+
+
+@pytest.mark.parametrize("case", ["small", "N16", "one_cluster_20001"])
+def test_nonlinear_adjoint_from_the_solves_record(case):
+    """With one segment (K = nt) the adjoint march runs about the v_n that the solve's
+    final march recorded (the converged SWR trajectory, from the subdomain marches in
+    their tuned shapes); with two segments the monodomain march recomputes them.  The SWR
+    trajectory equals the monodomain one to the solve's tolerance (interface residual
+    below 1e-12 here), so the two gradients agree far below the oracle tolerance, and
+    both match the oracle's discrete adjoint."""
+    wl = CASES[case]()
+    tgt = W.misfit_target(wl)
+    J, g_rec = gpu_gradient(wl, tgt, K=wl.nt)
+    assert LAST_ADJOINT_STATS["nl_march_launches"] == 1      # the adjoint march alone
+    _, g_seg = gpu_gradient(wl, tgt, K=(wl.nt + 1) // 2)
+    assert LAST_ADJOINT_STATS["nl_march_launches"] == 5      # 1 + 2 x (record, adjoint)
+    _, go = O.adjoint_gradient_nl(problem(wl), tgt)
+    assert rel(g_rec, g_seg) < 1e-10
+    assert rel(g_rec, go) < 1e-8
+    assert rel(g_seg, go) < 1e-8
 
 
 def test_nonlinear_adjoint_against_central_differences():

@@ -1385,6 +1385,13 @@ swr_status mono_setup(swr_plan_t p) {
         cudaGetLastError();
         return SWR_ERR_CUDA;
     }
+    // two-level separator data with a reduced system over the whole CTA (thousands of
+    // separators); without it the march keeps the cluster-wide PCR
+    if (swr_launch_factor_tl(p->fsM, 1, p->d_mono + 2, p->d_mdg, p->d_mod, p->d_status, p->s,
+                             true) == -1) {
+        cudaGetLastError();
+        return SWR_ERR_CUDA;
+    }
     CK(cudaStreamSynchronize(p->s));
     return SWR_OK;
 }
@@ -1425,6 +1432,7 @@ swr_status mono_nl_march(swr_plan_t p, int mode, const double2* u0, double2* uT,
     a.gl = p->d_gl;
     a.gr = p->d_gr;
     a.h12 = p->h / 12.0;
+    a.two_level = p->two_level;
     const double kappa = 2.0 / p->d.dt * (p->h / 6.0);
     const int pi = prof_begin(p, 3, (long long)p->nx * nrun);
     const int rc = swr_launch_march_nl(fs, a, (p->h / 12.0) / kappa, p->d.nl_coef, p->d.nl_tol,

@@ -155,17 +155,23 @@ struct FactorSet {
     // P < kTlMaxSep): separators in warp blocks of 32, lane 0 of every block (and the
     // system's last separator) a super-separator, lanes 1..31 a super-chunk solved by
     // PCR with warp shuffles; the super-separators form a tridiagonal reduced system
-    // of at most 32 unknowns, solved by one warp.  Layout, per subdomain:
+    // of at most 32 unknowns, solved by one warp (tl_rs = 32, tl_rl = 5).  On request
+    // (swr_launch_factor_tl with wide) up to kTlMaxSepWide separators: the reduced
+    // system then has up to tl_rs = 256 unknowns, solved by PCR over a whole CTA
+    // (the nonlinear march only).  Layout, per subdomain:
     //   tl_pcr  [N][5][2][P+1]  super-chunk PCR coefficients (alpha, gamma), zero off it
     //   tl_aux  [N][3][P+1]     1/delta after the last level, spikes a (left), b (right)
-    //   tl_red  [N][13][32]     reduced system: 5 levels of (alpha, gamma), 1/delta,
-    //                           and the weights of y_last(q-1), y_first(q) in its RHS
+    //   tl_red  [N][2 tl_rl + 3][tl_rs]  reduced system: tl_rl levels of (alpha, gamma),
+    //                           1/delta, and the weights of y_last(q-1), y_first(q) in
+    //                           its right-hand side
     double2* tl_pcr = nullptr;
     double2* tl_aux = nullptr;
     double2* tl_red = nullptr;
+    int tl_rs = 32, tl_rl = 5;
     bool tl_ok = false;
 };
-constexpr int kTlMaxSep = 993;   // P + 1 <= 993: at most 32 super-separators
+constexpr int kTlMaxSep = 993;        // P + 1 <= 993: at most 32 super-separators
+constexpr int kTlMaxSepWide = 8161;   // P + 1 <= 8161: at most 256 super-separators
 
 struct MarchArgs {
     int nt, P, levels, C, G, T, nsys;
@@ -237,6 +243,7 @@ struct MarchArgs {
     const double2* tl_pcr;
     const double2* tl_aux;
     const double2* tl_red;
+    int tl_rs, tl_rl;     // reduced system: stride (32, or up to 256 wide) and PCR levels
     int two_level;        // 0: keep the cluster-wide PCR even when the data exists
     // per-step factors (V(t,x)): index of the factor set of this launch's step 1, and
     // frev != 0 to walk them backwards (the adjoint's time-reversed march)
@@ -286,9 +293,10 @@ void swr_factor_free(FactorSet& fs);
 int swr_launch_factor(FactorSet& fs, int N, const int* d_n, const int* d_loff, const double2* dg,
                       const double2* od, int* status, cudaStream_t s);
 // The two-level separator data (FactorSet.tl_*) after swr_launch_factor, for a constant
-// matrix with P + 1 <= kTlMaxSep; allocates it.  0, -1 (CUDA error) or -2 (not applicable).
+// matrix with P + 1 <= kTlMaxSep (wide: kTlMaxSepWide; the arrays are allocated here when
+// swr_factor_alloc did not).  0, -1 (CUDA error) or -2 (not applicable).
 int swr_launch_factor_tl(FactorSet& fs, int N, const int* d_loff, const double2* dg,
-                         const double2* od, int* status, cudaStream_t s);
+                         const double2* od, int* status, cudaStream_t s, bool wide = false);
 int swr_launch_march(const FactorSet& fs, MarchArgs a, int nsys_groups, cudaStream_t s,
                      int mode = 0);
 int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef, double tol,

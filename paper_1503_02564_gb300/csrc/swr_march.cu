@@ -483,124 +483,218 @@ __device__ void warp_pcr_coeffs(double2 L, double2 D, double2 U, int lane, int l
     dfin = D;
 }
 
+// Two-level separator data of one system per CTA (blockIdx.x = subdomain j).  Warp w
+// takes the warp blocks w, w + nw, ... of 32 separators: the separator rows (as
+// k_reduce_pcr), the super-chunk PCR coefficients and spikes of each block, and the
+// rows of its super-separator; then the reduced system over the Q + 1 super-separators:
+// with RS = 32 (Q <= 31) by warp 0 with shuffles, otherwise by the whole CTA with one
+// barrier per PCR level (RS <= blockDim.x).  tl_red [N][2 RL + 3][RS]: RL levels of
+// (alpha, gamma), 1/delta, and the weights of y_last(q-1), y_first(q) in the rows.
+// Dynamic shared memory: 13 RS double2.
 __global__ void __launch_bounds__(1024, 1) k_factor_two_level(
     int N, int P, const int* __restrict__ loff_, const double2* __restrict__ dg,
     const double2* __restrict__ od, const int* __restrict__ sub_P,
     const int* __restrict__ sep_pos, const double2* __restrict__ tips,
     double2* __restrict__ tl_pcr, double2* __restrict__ tl_aux, double2* __restrict__ tl_red,
-    int* status) {
+    int RS, int RL, int* status) {
     // per super-separator q: its row (lo, dd, up); per super-chunk q: the spikes at its
-    // first member (af, bf) and last member (al, bl)
-    __shared__ double2 s_lo[33], s_dd[33], s_up[33], s_af[33], s_bf[33], s_al[33], s_bl[33];
+    // first member (af, bf) and last member (al, bl); wide reduced PCR: rows L, D, U
+    extern __shared__ double2 fsm[];
+    double2 *s_lo = fsm, *s_dd = s_lo + RS, *s_up = s_dd + RS, *s_af = s_up + RS;
+    double2 *s_bf = s_af + RS, *s_al = s_bf + RS, *s_bl = s_al + RS;
+    double2 *w_l = s_bl + RS, *w_d = w_l + RS, *w_u = w_d + RS;
     const int j = blockIdx.x;
-    const int p = threadIdx.x, lane = p & 31, q = p >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
     const int Pj = sub_P[j];
     const int S = P + 1;
     const int Q = (Pj + 31) / 32;
     const double2 zero = make_double2(0.0, 0.0), one = make_double2(1.0, 0.0);
     const double2* T = tips + (size_t)j * P * 4;
     const int base = loff_[j];
-    // separator rows (as k_reduce_pcr); padding beyond Pj: identity rows
-    double2 lo = zero, dd = one, up = zero;
-    if (p <= Pj) {
-        const int s = sep_pos[j * S + p];
-        dd = dg[base + s];
-        if (p > 0) {
-            const double2 EL = od[base + s - 1];
-            dd = cfms(EL, T[(p - 1) * 4 + 3], dd);
-            lo = cmul(make_double2(-EL.x, -EL.y), T[(p - 1) * 4 + 2]);
-        }
-        if (p < Pj) {
-            const double2 ER = od[base + s];
-            dd = cfms(ER, T[p * 4 + 0], dd);
-            up = cmul(make_double2(-ER.x, -ER.y), T[p * 4 + 1]);
-        }
-    }
-    // super-separator rows: s_q = 32 q (q < Q) and s_Q = Pj
-    if ((lane == 0 && q < Q) || p == Pj) {
-        const int qi = (p == Pj) ? Q : q;
-        s_lo[qi] = lo;
-        s_dd[qi] = dd;
-        s_up[qi] = up;
-    }
-    // super-chunk q: lanes 1..m
-    const int m = (32 * q < Pj) ? min(31, Pj - 1 - 32 * q) : 0;
-    double2 e1 = (lane == 1) ? lo : zero, e2 = (lane == m) ? up : zero, dfin;
-    const bool keep = p < S;
-    warp_pcr_coeffs(lo, dd, up, lane, 1, m, tl_pcr + (size_t)j * 10 * S + (keep ? p : 0),
-                    (size_t)S, keep, e1, e2, dfin);
-    const bool member = lane >= 1 && lane <= m;
     bool bad = false;
-    double2 binv = one, sa = zero, sb = zero;
-    if (member) {
-        bad = !cfinite(dfin) || (dfin.x == 0.0 && dfin.y == 0.0);
-        binv = crcp(dfin);
-        sa = cmul(e1, binv);
-        sb = cmul(e2, binv);
-    }
-    if (keep) {
-        tl_aux[((size_t)j * 3 + 0) * S + p] = binv;
-        tl_aux[((size_t)j * 3 + 1) * S + p] = sa;
-        tl_aux[((size_t)j * 3 + 2) * S + p] = sb;
-    }
-    if (member && lane == 1) {
-        s_af[q] = sa;
-        s_bf[q] = sb;
-    }
-    if (member && lane == m) {
-        s_al[q] = sa;
-        s_bl[q] = sb;
+    const int nblk = (S + 31) / 32;
+    for (int q = wid; q < nblk; q += nw) {   // uniform per warp
+        const int p = 32 * q + lane;
+        // separator rows (as k_reduce_pcr); padding beyond Pj: identity rows
+        double2 lo = zero, dd = one, up = zero;
+        if (p <= Pj) {
+            const int s = sep_pos[j * S + p];
+            dd = dg[base + s];
+            if (p > 0) {
+                const double2 EL = od[base + s - 1];
+                dd = cfms(EL, T[(p - 1) * 4 + 3], dd);
+                lo = cmul(make_double2(-EL.x, -EL.y), T[(p - 1) * 4 + 2]);
+            }
+            if (p < Pj) {
+                const double2 ER = od[base + s];
+                dd = cfms(ER, T[p * 4 + 0], dd);
+                up = cmul(make_double2(-ER.x, -ER.y), T[p * 4 + 1]);
+            }
+        }
+        // super-separator rows: s_q = 32 q (q < Q) and s_Q = Pj
+        if ((lane == 0 && q < Q) || p == Pj) {
+            const int qi = (p == Pj) ? Q : q;
+            s_lo[qi] = lo;
+            s_dd[qi] = dd;
+            s_up[qi] = up;
+        }
+        // super-chunk q: lanes 1..m
+        const int m = (32 * q < Pj) ? min(31, Pj - 1 - 32 * q) : 0;
+        double2 e1 = (lane == 1) ? lo : zero, e2 = (lane == m) ? up : zero, dfin;
+        const bool keep = p < S;
+        warp_pcr_coeffs(lo, dd, up, lane, 1, m, tl_pcr + (size_t)j * 10 * S + (keep ? p : 0),
+                        (size_t)S, keep, e1, e2, dfin);
+        const bool member = lane >= 1 && lane <= m;
+        double2 binv = one, sa = zero, sb = zero;
+        if (member) {
+            bad |= !cfinite(dfin) || (dfin.x == 0.0 && dfin.y == 0.0);
+            binv = crcp(dfin);
+            sa = cmul(e1, binv);
+            sb = cmul(e2, binv);
+        }
+        if (keep) {
+            tl_aux[((size_t)j * 3 + 0) * S + p] = binv;
+            tl_aux[((size_t)j * 3 + 1) * S + p] = sa;
+            tl_aux[((size_t)j * 3 + 2) * S + p] = sb;
+        }
+        if (member && lane == 1) {
+            s_af[q] = sa;
+            s_bf[q] = sb;
+        }
+        if (member && lane == m) {
+            s_al[q] = sa;
+            s_bl[q] = sb;
+        }
     }
     __syncthreads();
-    // reduced system over the super-separators
-    if (q == 0) {
-        double2 RL = zero, RD = one, RU = zero, cL = zero, cU = zero;
-        if (lane <= Q) {
-            const int sq = (lane < Q) ? 32 * lane : Pj;
-            const int mprev = (lane >= 1) ? sq - 1 - 32 * (lane - 1) : 0;   // members of q-1
-            const int mcur = (lane < Q) ? min(31, Pj - 1 - sq) : 0;          // members of q
-            RD = s_dd[lane];
-            if (lane >= 1) {
-                if (mprev > 0) {
-                    RL = cmul(make_double2(-s_lo[lane].x, -s_lo[lane].y), s_al[lane - 1]);
-                    RD = cfms(s_lo[lane], s_bl[lane - 1], RD);
-                    cL = s_lo[lane];
-                } else {
-                    RL = s_lo[lane];
-                }
-            }
-            if (lane < Q) {
-                if (mcur > 0) {
-                    RU = cmul(make_double2(-s_up[lane].x, -s_up[lane].y), s_bf[lane]);
-                    RD = cfms(s_up[lane], s_af[lane], RD);
-                    cU = s_up[lane];
-                } else {
-                    RU = s_up[lane];
-                }
+    // reduced row of super-separator i (identity beyond Q): lower, diagonal, upper, and
+    // the weights of the neighbouring super-chunks' end values in its right-hand side
+    auto reduced_row = [&](int i, double2& RL_, double2& RD_, double2& RU_, double2& cL,
+                           double2& cU) {
+        RL_ = zero;
+        RD_ = one;
+        RU_ = zero;
+        cL = zero;
+        cU = zero;
+        if (i > Q) return;
+        const int sq = (i < Q) ? 32 * i : Pj;
+        const int mprev = (i >= 1) ? sq - 1 - 32 * (i - 1) : 0;   // members of block i-1
+        const int mcur = (i < Q) ? min(31, Pj - 1 - sq) : 0;       // members of block i
+        RD_ = s_dd[i];
+        if (i >= 1) {
+            if (mprev > 0) {
+                RL_ = cmul(make_double2(-s_lo[i].x, -s_lo[i].y), s_al[i - 1]);
+                RD_ = cfms(s_lo[i], s_bl[i - 1], RD_);
+                cL = s_lo[i];
+            } else {
+                RL_ = s_lo[i];
             }
         }
-        double2* R = tl_red + (size_t)j * 13 * 32;
-        double2 z1 = zero, z2 = zero, rfin;
-        warp_pcr_coeffs(RL, RD, RU, lane, 0, Q, R + lane, 32, true, z1, z2, rfin);
-        double2 rinv = one;
-        if (lane <= Q) {
-            bad |= !cfinite(rfin) || (rfin.x == 0.0 && rfin.y == 0.0);
-            rinv = crcp(rfin);
+        if (i < Q) {
+            if (mcur > 0) {
+                RU_ = cmul(make_double2(-s_up[i].x, -s_up[i].y), s_bf[i]);
+                RD_ = cfms(s_up[i], s_af[i], RD_);
+                cU = s_up[i];
+            } else {
+                RU_ = s_up[i];
+            }
         }
-        R[10 * 32 + lane] = rinv;
-        R[11 * 32 + lane] = cL;
-        R[12 * 32 + lane] = cU;
+    };
+    double2* R = tl_red + (size_t)j * (2 * RL + 3) * RS;
+    if (RS == 32) {
+        if (wid == 0) {
+            double2 RL_, RD_, RU_, cL, cU;
+            reduced_row(lane, RL_, RD_, RU_, cL, cU);
+            double2 z1 = zero, z2 = zero, rfin;
+            warp_pcr_coeffs(RL_, RD_, RU_, lane, 0, Q, R + lane, 32, true, z1, z2, rfin);
+            double2 rinv = one;
+            if (lane <= Q) {
+                bad |= !cfinite(rfin) || (rfin.x == 0.0 && rfin.y == 0.0);
+                rinv = crcp(rfin);
+            }
+            R[10 * 32 + lane] = rinv;
+            R[11 * 32 + lane] = cL;
+            R[12 * 32 + lane] = cU;
+        }
+    } else {
+        // wide: thread i < RS holds reduced row i (blockDim.x >= RS)
+        const int i = tid;
+        double2 RL_ = zero, RD_ = one, RU_ = zero, cL = zero, cU = zero;
+        if (i < RS) {
+            reduced_row(i, RL_, RD_, RU_, cL, cU);
+            w_l[i] = RL_;
+            w_d[i] = RD_;
+            w_u[i] = RU_;
+        }
+        __syncthreads();
+        for (int k = 0; k < RL; ++k) {
+            const int st = 1 << k;
+            double2 al = zero, ga = zero, nL = zero, nD = RD_, nU = zero;
+            if (i < RS) {
+                if (i <= Q && i - st >= 0) al = cmul(make_double2(-RL_.x, -RL_.y), crcp(w_d[i - st]));
+                if (i <= Q && i + st <= Q) ga = cmul(make_double2(-RU_.x, -RU_.y), crcp(w_d[i + st]));
+                if (i - st >= 0) {
+                    nL = cmul(al, w_l[i - st]);
+                    nD = cfma(al, w_u[i - st], nD);
+                }
+                if (i + st < RS) {
+                    nU = cmul(ga, w_u[i + st]);
+                    nD = cfma(ga, w_l[i + st], nD);
+                }
+                R[(size_t)(2 * k) * RS + i] = al;
+                R[(size_t)(2 * k + 1) * RS + i] = ga;
+            }
+            __syncthreads();
+            if (i < RS) {
+                RL_ = nL;
+                RD_ = nD;
+                RU_ = nU;
+                w_l[i] = nL;
+                w_d[i] = nD;
+                w_u[i] = nU;
+            }
+            __syncthreads();
+        }
+        if (i < RS) {
+            double2 rinv = one;
+            if (i <= Q) {
+                bad |= !cfinite(RD_) || (RD_.x == 0.0 && RD_.y == 0.0);
+                rinv = crcp(RD_);
+            }
+            R[(size_t)(2 * RL) * RS + i] = rinv;
+            R[(size_t)(2 * RL + 1) * RS + i] = cL;
+            R[(size_t)(2 * RL + 2) * RS + i] = cU;
+        }
     }
     if (bad) atomicOr(status, ST_SINGULAR);
 }
 
 int swr_launch_factor_tl(FactorSet& fs, int N, const int* d_loff, const double2* dg,
-                         const double2* od, int* status, cudaStream_t s) {
+                         const double2* od, int* status, cudaStream_t s, bool wide) {
     fs.tl_ok = false;
-    if (fs.nsteps != 1 || fs.P + 1 > kTlMaxSep || !fs.tl_pcr) return -2;
-    const int threads = std::max(32, ((fs.P + 1 + 31) / 32) * 32);   // one per separator
-    k_factor_two_level<<<N, threads, 0, s>>>(N, fs.P, d_loff, dg, od, fs.sub_P, fs.sep_pos,
-                                              fs.tips, fs.tl_pcr, fs.tl_aux, fs.tl_red, status);
+    if (fs.nsteps != 1) return -2;
+    const int S = fs.P + 1;
+    if (S > (wide ? kTlMaxSepWide : kTlMaxSep)) return -2;
+    const int Qmax = (fs.P + 31) / 32;
+    const int RS = (Qmax + 1 <= 32) ? 32 : ((Qmax + 1 + 31) / 32) * 32;
+    int RL = 0;
+    while ((1 << RL) < RS) ++RL;
+    if (!fs.tl_pcr) {   // wide data of a system beyond kTlMaxSep separators: on request
+        bool ok = cudaMalloc(&fs.tl_pcr, sizeof(double2) * (size_t)N * 10 * S) == cudaSuccess;
+        ok &= cudaMalloc(&fs.tl_aux, sizeof(double2) * (size_t)N * 3 * S) == cudaSuccess;
+        ok &= cudaMalloc(&fs.tl_red, sizeof(double2) * (size_t)N * (2 * RL + 3) * RS) ==
+              cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return -1;
+        }
+    }
+    fs.tl_rs = RS;
+    fs.tl_rl = RL;
+    const int threads = std::min(1024, std::max(RS, ((S + 31) / 32) * 32));
+    k_factor_two_level<<<N, threads, sizeof(double2) * 13 * RS, s>>>(
+        N, fs.P, d_loff, dg, od, fs.sub_P, fs.sep_pos, fs.tips, fs.tl_pcr, fs.tl_aux, fs.tl_red,
+        RS, RL, status);
     swr_count_launch(1);
     if (cudaGetLastError() != cudaSuccess) return -1;
     fs.tl_ok = true;
@@ -2086,9 +2180,12 @@ int swr_launch_march(const FactorSet& fs, MarchArgs a, int ngroups, cudaStream_t
             a.pstride = -a.pstride;
         }
     }
-    a.tl_pcr = fs.tl_ok ? fs.tl_pcr : nullptr;
+    // the constant-matrix two-level march reads the one-warp reduced system only
+    a.tl_pcr = (fs.tl_ok && fs.tl_rs == 32) ? fs.tl_pcr : nullptr;
     a.tl_aux = fs.tl_aux;
     a.tl_red = fs.tl_red;
+    a.tl_rs = fs.tl_rs;
+    a.tl_rl = fs.tl_rl;
     if (!a.two_level) a.tl_pcr = nullptr;
     // adjoint modes: L <= 8, Robin or S_0^2 (not the per-end kernels)
     if (mode != 0 && (fs.L > 8 || a.kap)) return -2;

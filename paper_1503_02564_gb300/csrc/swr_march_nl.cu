@@ -681,12 +681,15 @@ __device__ __forceinline__ double2 nl_shdn(double2 v, int d) {
                         __shfl_down_sync(0xffffffffu, v.y, d));
 }
 
-int swr_march_nl_tl_smem_bytes(int L, int T) {
+int swr_march_nl_tl_smem_bytes(int L, int T, int RS, int mode) {
     const int W = T / 32;
-    // usep zsep xv ulst ylst zlst [T] each; pub [2][W][5]; usup, zsup ping-pong [3][33];
-    // step histories: chunk nodes [3][L][T], own separators [3][T], replicas [3][33];
-    // partial maxima [2][2] (8-byte words)
-    return (int)sizeof(double2) * (6 * T + 2 * W * 5 + 3 * 33 + 3 * L * T + 3 * T + 3 * 33) +
+    // usep zsep xv ulst ylst zlst [T] each; pub [2][W][5]; usup [RS], zsb [2][RS]; step
+    // histories: chunk nodes [3][L][T], own separators [3][T], replicas [3][RS]; the wide
+    // reduced PCR [2][RS]; MODE 2: forward values vfc [L][T], vfsep and vflst [T], vfsup
+    // [RS], and the potential-form sums [L + 2][T] (doubles); partial maxima [2][2]
+    int n2 = 6 * T + 2 * W * 5 + 3 * RS + 3 * L * T + 3 * T + 3 * RS + 2 * RS;
+    if (mode == 2) n2 += L * T + 2 * T + RS;
+    return (int)sizeof(double2) * n2 + (mode == 2 ? (int)sizeof(double) * (L + 2) * T : 0) +
            (int)sizeof(unsigned long long) * 4;
 }
 
@@ -696,6 +699,7 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
     extern __shared__ double2 sm[];
     const int T = a.T, P = a.P, C = a.C, nt = a.nt;
     const int W = T / 32;
+    const int RS = a.tl_rs, RLv = a.tl_rl;   // reduced system: 32 (one warp) or wide
     double2* usep = sm;              // [T] u at my separators
     double2* zsep = usep + T;        // [T] the iterate at my separators
     double2* xv = zsep + T;          // [T] the separators' new iterate (this iteration)
@@ -703,12 +707,20 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
     double2* ylst = ulst + T;
     double2* zlst = ylst + T;
     double2* pub = zlst + T;         // [2][W][5]
-    double2* usup = pub + 2 * W * 5; // [33] u at the super-separators (every CTA)
-    double2* zsb = usup + 33;        // [2][33] the iterate at the super-separators (ping-pong)
-    double2* hc = zsb + 2 * 33;      // [3][L][T] chunk iterates of steps n-2, n-3, n-4
+    double2* usup = pub + 2 * W * 5; // [RS] u at the super-separators (every CTA)
+    double2* zsb = usup + RS;        // [2][RS] the iterate at the super-separators (ping-pong)
+    double2* hc = zsb + 2 * RS;      // [3][L][T] chunk iterates of steps n-2, n-3, n-4
     double2* hs = hc + 3 * L * T;    // [3][T] own separators' iterates, same steps
-    double2* hq = hs + 3 * T;        // [3][33] super-separators' iterates, same steps
-    unsigned long long* red = reinterpret_cast<unsigned long long*>(hq + 3 * 33);   // [2][2]
+    double2* hq = hs + 3 * T;        // [3][RS] super-separators' iterates, same steps
+    double2* rA = hq + 3 * RS;       // [2][RS] wide reduced PCR (ping-pong)
+    double2* rB = rA + RS;
+    double2* vfc = rB + RS;          // MODE 2 [L][T] forward values of my chunk's nodes
+    double2* vfsep = vfc + L * T;    // MODE 2 [T] at my separators, [T] at my chunk's end,
+    double2* vflst = vfsep + T;      //        [RS] at the super-separators
+    double2* vfsup = vflst + T;
+    double* gsm = reinterpret_cast<double*>(vfsup + RS);   // MODE 2 [L + 2][T] sums
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(
+        MODE == 2 ? (void*)(gsm + (L + 2) * T) : (void*)vfc);   // [2][2]
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, wl = tid >> 5;
@@ -744,7 +756,8 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
     const double2* sE_r = a.sep + (size_t)(j * 3 + 1) * S;
     const double2* tpc = a.tl_pcr + (size_t)j * 10 * S + (valid ? p : 0);
     const double2* tax = a.tl_aux + (size_t)j * 3 * S + (valid ? p : 0);
-    const double2* tred = a.tl_red + (size_t)j * 13 * 32 + lane;
+    const double2* trow = a.tl_red + (size_t)j * (2 * RLv + 3) * RS;
+    const double2* tred = trow + lane;   // one-warp reduced system (RS = 32)
     const double cw = na.cw, coef = na.coef;
     const bool le = (p == 0), re = (p == Pj);
     const bool own_left = realsep && !le && lane != 0;   // the chunk on the left is in my warp
@@ -762,22 +775,38 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
         usep[tid] = u0s;
         zsep[tid] = u0s;
     }
-    if (wl == 0 && lane <= Q && sidx < a.nsys) {
-        const int ps = (lane < Q) ? 32 * lane : Pj;
+    if (tid <= Q && sidx < a.nsys) {
+        const int ps = (tid < Q) ? 32 * tid : Pj;
         const double2 us = zero_u0 ? zero : a.u0[goff + a.sep_pos[j * S + ps]];
-        usup[lane] = us;
-        zsb[lane] = us;
+        usup[tid] = us;
+        zsb[tid] = us;
+    }
+    if constexpr (MODE == 2) {
+#pragma unroll
+        for (int i = 0; i < L + 2; ++i) gsm[i * T + tid] = 0.0;
     }
     if (tid < 4) red[tid] = 0ull;
     cl.sync();
 
-    int cur = 0;                     // zsb + 33 cur: the super-separators' current iterate
+    int cur = 0;                     // zsb + RS cur: the super-separators' current iterate
     int itg = 0;                     // inner iterations so far (parity of pub and red)
     int itmax = 0;
     unsigned long long itsum = 0;
     bool nl_fail = false;
     double2 lin = zero, rin = zero;
     for (int t = 1; t <= nt; ++t) {
+        if constexpr (MODE == 2) {   // forward values of the mirrored step
+            const double2* vrow = a.vfwd + (size_t)(nt - t) * a.nxrec + goff;
+            if (valid && Lp > 0) {
+#pragma unroll
+                for (int i = 0; i < L; ++i)
+                    if (i < Lp) vfc[i * T + tid] = vrow[sp + 1 + i];
+                vflst[tid] = vrow[sp + Lp];
+            }
+            if (realsep) vfsep[tid] = vrow[sp];
+            if (tid <= Q && sidx < a.nsys)
+                vfsup[tid] = vrow[a.sep_pos[j * S + ((tid < Q) ? 32 * tid : Pj)]];
+        }
         // ---- step-constant right-hand sides: chunks, and my separator's own part ------
         double2 uf = zero, ul = zero;
         if (valid && Lp > 0) {
@@ -852,13 +881,13 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
             hs[tid] = z1;
             zsep[tid] = predict(z1, z2, z3, z4);
         }
-        if (wl == 0 && lane <= Q) {
-            double2* zc = zsb + 33 * cur;
-            const double2 z1 = zc[lane], z2 = hq[lane], z3 = hq[33 + lane], z4 = hq[66 + lane];
-            hq[66 + lane] = z3;
-            hq[33 + lane] = z2;
-            hq[lane] = z1;
-            zc[lane] = predict(z1, z2, z3, z4);
+        if (tid <= Q) {
+            double2* zc = zsb + RS * cur;
+            const double2 z1 = zc[tid], z2 = hq[tid], z3 = hq[RS + tid], z4 = hq[2 * RS + tid];
+            hq[2 * RS + tid] = z3;
+            hq[RS + tid] = z2;
+            hq[tid] = z1;
+            zc[tid] = predict(z1, z2, z3, z4);
         }
         __syncthreads();
         // ---- inner fixed point (Eq. AvMNL), the stopping rule of k_march_nl ------------
@@ -867,8 +896,8 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
         bool done = false;
         for (int it = 0; it < na.maxit; ++it, ++itg) {
             const int slot = (itg & 1) * W * 5, rs = itg & 1;
-            const double2* zc = zsb + 33 * cur;       // current iterate, super-separators
-            double2* zn = zsb + 33 * (cur ^ 1);       // the new one (warp 0, phase D)
+            const double2* zc = zsb + RS * cur;       // current iterate, super-separators
+            double2* zn = zsb + RS * (cur ^ 1);       // the new one (phase D)
             // A: chunk right-hand side with b_f(zeta), local LU sweeps
             double2 zl_own = zero;
             if (valid && Lp > 0) {
@@ -876,6 +905,13 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
                 const double2 zR = (rsup >= 0) ? zc[rsup] : zsep[tid + 1];
                 double Wprev = coef * nrm2(zL);
                 double W0 = coef * nrm2(z[0]);
+                double2 vL = zero, vR = zero;
+                if constexpr (MODE == 2) {   // W from the forward values
+                    vL = vfsep[tid];
+                    vR = (rsup >= 0) ? vfsup[rsup] : vfsep[tid + 1];
+                    Wprev = coef * nrm2(vL);
+                    W0 = coef * nrm2(vfc[tid]);
+                }
                 double2 zprev = zero, cprev = zero;
 #pragma unroll
                 for (int i = 0; i < L; ++i) {
@@ -886,8 +922,20 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
                             zr_ = (i == Lp - 1) ? zR : z[i + 1];
                         else
                             zr_ = zR;
-                        const double Wr = coef * nrm2(zr_);
-                        const double2 sx = bf_sum(true, true, zl_, z[i], zr_, Wprev, W0, Wr);
+                        double Wr;
+                        double2 sx;
+                        if constexpr (MODE == 2) {
+                            const double2 vl = (i == 0) ? vL : vfc[(i > 0 ? i - 1 : 0) * T + tid];
+                            const double2 v0 = vfc[i * T + tid];
+                            const double2 vr = (i + 1 < L && i != Lp - 1)
+                                                   ? vfc[(i + 1 < L ? i + 1 : 0) * T + tid] : vR;
+                            Wr = coef * nrm2(vr);
+                            sx = cadd(bf_sum(true, true, zl_, z[i], zr_, Wprev, W0, Wr),
+                                      lin_term(true, true, vl, v0, vr, zl_, z[i], zr_, coef));
+                        } else {
+                            Wr = coef * nrm2(zr_);
+                            sx = bf_sum(true, true, zl_, z[i], zr_, Wprev, W0, Wr);
+                        }
                         const double2 rhs = sub_bf(f[i], sx, cw);
                         const double2 zz = (i == 0) ? rhs : cfms(cprev, zprev, rhs);
                         y[i] = zz;
@@ -918,15 +966,32 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
             double2 d = zero;
             if (realsep) {
                 const double2 zs = zsep[tid];
-                const double W0 = coef * nrm2(zs);
+                double2 vs = zs;                      // W at the separator: iterate or forward
+                if constexpr (MODE == 2) vs = vfsep[tid];
+                const double W0 = coef * nrm2(vs);
                 double2 sb = zero;
                 if (!re) {
                     const double2 zr_ = z[0];
-                    sb = bf_sum(false, true, zero, zs, zr_, 0.0, W0, coef * nrm2(zr_));
+                    if constexpr (MODE == 2) {
+                        const double2 vr = vfc[tid];
+                        sb = cadd(bf_sum(false, true, zero, zs, zr_, 0.0, W0, coef * nrm2(vr)),
+                                  lin_term(false, true, zero, vs, vr, zero, zs, zr_, coef));
+                    } else {
+                        sb = bf_sum(false, true, zero, zs, zr_, 0.0, W0, coef * nrm2(zr_));
+                    }
                 }
                 if (own_left) {
                     const double2 zl_ = zlst[tid - 1];
-                    sb = cadd(sb, bf_sum(true, false, zl_, zs, zero, coef * nrm2(zl_), W0, 0.0));
+                    if constexpr (MODE == 2) {
+                        const double2 vl = vflst[tid - 1];
+                        sb = cadd(sb, cadd(bf_sum(true, false, zl_, zs, zero, coef * nrm2(vl), W0,
+                                                  0.0),
+                                           lin_term(true, false, vl, vs, zero, zl_, zs, zero,
+                                                    coef)));
+                    } else {
+                        sb = cadd(sb, bf_sum(true, false, zl_, zs, zero, coef * nrm2(zl_), W0,
+                                             0.0));
+                    }
                 }
                 d = sub_bf(fown, sb, cw);
                 if (own_left) d = cfms(sE_l[p], ylst[tid - 1], d);
@@ -936,8 +1001,16 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
             double2 p1 = zero;
             if (valid && lane == 31 && p + 1 <= Pj) {
                 const double2 zs1 = zc[rsup];        // p + 1 is a super-separator
-                const double2 sl = bf_sum(true, false, zl_own, zs1, zero, coef * nrm2(zl_own),
-                                          coef * nrm2(zs1), 0.0);
+                double2 sl;
+                if constexpr (MODE == 2) {
+                    const double2 vl = vflst[tid], vs1 = vfsup[rsup];
+                    sl = cadd(bf_sum(true, false, zl_own, zs1, zero, coef * nrm2(vl),
+                                     coef * nrm2(vs1), 0.0),
+                              lin_term(true, false, vl, vs1, zero, zl_own, zs1, zero, coef));
+                } else {
+                    sl = bf_sum(true, false, zl_own, zs1, zero, coef * nrm2(zl_own),
+                                coef * nrm2(zs1), 0.0);
+                }
                 p1 = cfms(sE_l[p + 1], ylst[tid], sub_bf(ulst[tid], sl, cw));
             }
             // C: super-chunk PCR in registers, publication, cluster barrier
@@ -961,37 +1034,62 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
                 red[2 * (rs ^ 1) + 0] = 0ull;
                 red[2 * (rs ^ 1) + 1] = 0ull;
             }
-            // D: the reduced system, warp 0 of every CTA: the new iterate at all
-            // super-separators
-            if (wl == 0 && sidx < a.nsys) {
-                double2 r = zero;
-                if (lane <= Q) {
-                    auto pubof = [&](int qq) -> const double2* {
-                        const int home = (32 * qq) / T;
-                        double2* base = (home == rank) ? pub : cl.map_shared_rank(pub, home);
-                        return base + slot + ((32 * qq) % T) / 32 * 5;
-                    };
-                    if (lane == Q && (Pj & 31) != 0) {
-                        r = pubof(Q - 1)[4];
-                    } else {
-                        r = pubof(lane)[0];
-                        if (lane >= 1) r = cadd(r, pubof(lane - 1)[1]);
-                    }
-                    const double2 cL = tred[11 * 32], cU = tred[12 * 32];
-                    if (lane >= 1 && (cL.x != 0.0 || cL.y != 0.0))
-                        r = cfms(cL, pubof(lane - 1)[3], r);
-                    if (lane < Q && (cU.x != 0.0 || cU.y != 0.0))
-                        r = cfms(cU, pubof(lane)[2], r);
+            // D: the reduced system (every CTA holds the new iterate at all
+            // super-separators): row i's right-hand side from the published values
+            auto pubof = [&](int qq) -> const double2* {
+                const int home = (32 * qq) / T;
+                double2* base = (home == rank) ? pub : cl.map_shared_rank(pub, home);
+                return base + slot + ((32 * qq) % T) / 32 * 5;
+            };
+            auto reduced_rhs = [&](int i) -> double2 {
+                double2 r;
+                if (i == Q && (Pj & 31) != 0) {
+                    r = pubof(Q - 1)[4];
+                } else {
+                    r = pubof(i)[0];
+                    if (i >= 1) r = cadd(r, pubof(i - 1)[1]);
                 }
+                const double2 cL = trow[(2 * RLv + 1) * RS + i], cU = trow[(2 * RLv + 2) * RS + i];
+                if (i >= 1 && (cL.x != 0.0 || cL.y != 0.0)) r = cfms(cL, pubof(i - 1)[3], r);
+                if (i < Q && (cU.x != 0.0 || cU.y != 0.0)) r = cfms(cU, pubof(i)[2], r);
+                return r;
+            };
+            if (RS == 32) {   // warp 0: PCR by shuffles
+                if (wl == 0 && sidx < a.nsys) {
+                    double2 r = zero;
+                    if (lane <= Q) r = reduced_rhs(lane);
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const int st = 1 << k;
-                    if (st > Q) break;   // no neighbour within the Q + 1 unknowns: zero couplings
-                    const double2 rm = nl_shup(r, st), rp = nl_shdn(r, st);
-                    if (lane <= Q)
-                        r = cfma(tred[(2 * k + 1) * 32], rp, cfma(tred[(2 * k) * 32], rm, r));
+                    for (int k = 0; k < 5; ++k) {
+                        const int st = 1 << k;
+                        if (st > Q) break;   // no neighbour within the Q + 1 unknowns
+                        const double2 rm = nl_shup(r, st), rp = nl_shdn(r, st);
+                        if (lane <= Q)
+                            r = cfma(tred[(2 * k + 1) * 32], rp, cfma(tred[(2 * k) * 32], rm, r));
+                    }
+                    if (lane <= Q) zn[lane] = cmul(r, tred[10 * 32]);
                 }
-                if (lane <= Q) zn[lane] = cmul(r, tred[10 * 32]);
+            } else {          // wide: PCR over the CTA, one barrier per level (T >= RS)
+                double2 r = zero;
+                if (tid <= Q && sidx < a.nsys) r = reduced_rhs(tid);
+                if (tid < RS) rA[tid] = r;
+                __syncthreads();
+                double2* src = rA;
+                double2* dst = rB;
+                for (int k = 0; k < RLv; ++k) {
+                    const int st = 1 << k;
+                    if (st > Q) break;
+                    if (tid <= Q) {
+                        double2 v = src[tid];
+                        if (tid >= st) v = cfma(trow[(2 * k) * RS + tid], src[tid - st], v);
+                        if (tid + st <= Q) v = cfma(trow[(2 * k + 1) * RS + tid], src[tid + st], v);
+                        dst[tid] = v;
+                    }
+                    __syncthreads();
+                    double2* tmp = src;
+                    src = dst;
+                    dst = tmp;
+                }
+                if (tid <= Q) zn[tid] = cmul(src[tid], trow[(2 * RLv) * RS + tid]);
             }
             __syncthreads();
             // E: separator values of the new iterate
@@ -1043,7 +1141,8 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
                 zm = fmax(zm, __longlong_as_double((long long)b[2 * rs + 1]));
             }
             cur ^= 1;                                  // the new iterate is current
-            const double lim = na.tol * na.tol * fmax(1.0, zm);
+            // MODE 2 (linear in w): relative to max |w|^2, as in k_march_nl
+            const double lim = na.tol * na.tol * (MODE == 2 ? zm : fmax(1.0, zm));
             bool conv = dm <= lim;
             if (!conv && it >= 1 && dm_prev > 0.0 && dm < 0.0625 * dm_prev) {
                 const double rho = sqrt(dm / dm_prev);
@@ -1061,6 +1160,35 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
         if (!done) nl_fail = true;      // cap reached without convergence
         if (used > itmax) itmax = used;
         itsum += (unsigned long long)used;
+        if constexpr (MODE == 2) {
+            // potential form of w (this march) against the forward v, elements from
+            // separator p to separator p + 1 (as k_march_nl)
+            if (valid && p < Pj) {
+                const double2* zcv = zsb + RS * cur;
+                const double2 xL = zsep[tid], xR = (rsup >= 0) ? zcv[rsup] : zsep[tid + 1];
+                const double2 yL = vfsep[tid], yR = (rsup >= 0) ? vfsup[rsup] : vfsep[tid + 1];
+                const double h12 = a.h12;
+                double* g = gsm + tid;   // rows 0..L-1 interior nodes, L left end, L+1 right
+#pragma unroll
+                for (int e = 0; e <= L; ++e) {
+                    if (e <= Lp) {
+                        const int im = e > 0 ? e - 1 : 0, ic = e < L ? e : 0;
+                        const double2 xa = (e == 0) ? xL : z[im];
+                        const double2 ya = (e == 0) ? yL : vfc[im * T + tid];
+                        const double2 xb = (e < L) ? csel(e < Lp, z[ic], xR) : xR;
+                        const double2 yb = (e < L && e < Lp) ? vfc[ic * T + tid] : yR;
+                        const double sa = rmul(xa, ya), sb = rmul(xb, yb);
+                        const double c = rmul(xa, yb) + rmul(xb, ya);
+                        const double toa = h12 * (3.0 * sa + c + sb);
+                        const double tob = h12 * (sa + c + 3.0 * sb);
+                        if (e == 0) g[L * T] += toa;
+                        else g[im * T] += toa;
+                        if (e < Lp) g[ic * T] += tob;
+                        else g[(L + 1) * T] += tob;
+                    }
+                }
+            }
+        }
         if constexpr (MODE == 1) {   // record v_n (an interface node by its left subdomain)
             double2* row = a.vrec + (size_t)(t - 1) * a.nxrec + goff + sp;
             if (valid && Lp > 0) {
@@ -1089,11 +1217,21 @@ __global__ void __launch_bounds__(256, 1) k_march_nl_tl(const NlArgs na) {
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
             }
         }
-        if (wl == 0 && lane <= Q) {
-            const double2 v = zsb[33 * cur + lane], uo = usup[lane];
-            usup[lane] = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
+        if (tid <= Q) {
+            const double2 v = zsb[RS * cur + tid], uo = usup[tid];
+            usup[tid] = make_double2(fma(2.0, v.x, -uo.x), fma(2.0, v.y, -uo.y));
         }
         __syncthreads();
+    }
+    if constexpr (MODE == 2) {   // add this segment's sums (one writer per entry)
+        if (valid && p < Pj) {
+            const double* g = gsm + tid;
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.gint[goff + sp + 1 + i] += g[i * T];
+            a.gl[goff + sp] += g[L * T];
+            a.gr[goff + sp + Lp + 1] += g[(L + 1) * T];
+        }
     }
     // ---- final state ----------------------------------------------------------------
     bool bad = false;
@@ -1135,10 +1273,11 @@ static int launch_nl_t(NlArgs na, int ngroups, cudaStream_t s, int mode) {
     // solve (Robin or Neumann ends).  A system alone in its CTA keeps the CTA-wide PCR,
     // which measured faster there (its levels cost a CTA barrier, not a cluster one).
     const MarchArgs& m = na.m;
-    if ((mode == 0 || mode == 1) && m.tl_pcr && m.two_level && !m.s02 && !m.kap && m.C > 1 &&
-        (m.T & 31) == 0) {
-        kern = (mode == 1) ? k_march_nl_tl<L, 1> : k_march_nl_tl<L, 0>;
-        smem = swr_march_nl_tl_smem_bytes(L, m.T);
+    if (m.tl_pcr && m.two_level && !m.s02 && !m.kap && m.C > 1 && (m.T & 31) == 0 &&
+        (m.tl_rs == 32 || m.T >= m.tl_rs)) {
+        kern = (mode == 2) ? k_march_nl_tl<L, 2>
+                           : ((mode == 1) ? k_march_nl_tl<L, 1> : k_march_nl_tl<L, 0>);
+        smem = swr_march_nl_tl_smem_bytes(L, m.T, m.tl_rs, mode);
     }
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
         cudaSuccess)
@@ -1178,6 +1317,8 @@ int swr_launch_march_nl(const FactorSet& fs, MarchArgs a, double cw, double coef
     a.tl_pcr = fs.tl_ok ? fs.tl_pcr : nullptr;
     a.tl_aux = fs.tl_aux;
     a.tl_red = fs.tl_red;
+    a.tl_rs = fs.tl_rs;
+    a.tl_rl = fs.tl_rl;
     NlArgs na{a, cw, coef, tol, maxit, iters, pit};
     switch (fs.L) {
         case 2: return launch_nl_t<2>(na, ngroups, s, mode);

@@ -47,13 +47,13 @@ CASES = {
 LAST_ADJOINT_STATS = {}
 
 
-def gpu_gradient(wl, tgt, K=16, V=None, tc=None):
+def gpu_gradient(wl, tgt, K=16, V=None, tc=None, tuning=None):
     from paper_1503_02564_gb300 import swr
     plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
                     node_off=wl.off, p=wl.sigma, vkind=swr.SWR_V_NONLINEAR,
                     tc=swr.SWR_TC_ROBIN if tc is None else tc,
                     solver=swr.SWR_SOLVER_FIXED_POINT, precond=swr.SWR_PC_MEAN_POTENTIAL,
-                    maxit=500, tol_abs=1e-12, nl_tol=1e-13, nl_maxit=50)
+                    maxit=500, tol_abs=1e-12, nl_tol=1e-13, nl_maxit=50, tuning=tuning)
     Vt = torch.tensor(wl.V if V is None else V, dtype=torch.float64, device="cuda")
     plan.build_interface(Vt, torch.tensor(wl.u0, dtype=torch.complex128, device="cuda"))
     uT = torch.empty(wl.nx, dtype=torch.complex128, device="cuda")
@@ -78,6 +78,25 @@ def test_nonlinear_adjoint_gradient_matches_oracle(case):
     Jo, go = O.adjoint_gradient_nl(problem(wl), tgt)
     assert abs(J - Jo) <= 1e-10 * Jo
     assert rel(g, go) < 1e-8
+
+
+@pytest.mark.parametrize("case", ["small", "N16", "one_cluster_20001"])
+@pytest.mark.parametrize("K", [None, 4])
+def test_nonlinear_gradient_two_level_matches_cluster_pcr(case, K):
+    """The gradient's monodomain marches with the two-level separator solve (warp blocks
+    of 32 and a reduced system of the super-separators: 6 and 26 of them on clusters of 2
+    and 12 CTAs, solved by one warp; 126 on 16 CTAs of the 20001-node grid, solved by PCR
+    over each CTA) against the same marches with the cluster-wide PCR (two_level -1):
+    one segment about the solve's record (the adjoint march), and segments of 4 steps
+    (the forward march from checkpoints, its record, the adjoint march)."""
+    wl = CASES[case]()
+    tgt = W.misfit_target(wl)
+    Kr = wl.nt if K is None else K
+    _, g_tl = gpu_gradient(wl, tgt, K=Kr)
+    _, g_pcr = gpu_gradient(wl, tgt, K=Kr, tuning={"two_level": -1})
+    assert rel(g_tl, g_pcr) < 1e-11
+    _, go = O.adjoint_gradient_nl(problem(wl), tgt)
+    assert rel(g_tl, go) < 1e-8
 
 
 def test_nonlinear_adjoint_with_s02_plan():

@@ -2194,8 +2194,13 @@ swr_status swr_solve(swr_plan_t p, double* g_, int32_t g_is_initial, double* uT_
                     p->adj_K = 0;
                     swr_status sa = dalloc(&p->d_ckpt, (size_t)p->nx);
                     if (!sa) sa = dalloc(&p->d_slab, (size_t)p->nt * p->nx);
-                    if (sa) return sa;
-                    p->adj_K = p->nt;
+                    if (sa) {   // no record: the adjoint re-marches the forward scheme
+                        cudaFree(p->d_ckpt);
+                        cudaFree(p->d_slab);
+                        p->d_ckpt = p->d_slab = nullptr;
+                    } else {
+                        p->adj_K = p->nt;
+                    }
                 }
                 cudaGetLastError();
             }

@@ -860,10 +860,15 @@ int swr_march_smem_bytes(int T, int G, int stage_slots) {
 // potential form against recorded forward values (see MarchArgs).
 // GEN: the ends carry per-end kernels (a.kap, a.kout, a.rho: S_0^3, S_0^4, S_1^2, S_1^4),
 // a separate instantiation so that Robin and S_0^2 marches keep their registers.
-template <int L, int MODE, bool GEN = false>
+// LEAN: systems held by one CTA (C == 1) with Robin or Neumann ends (no S_0^2 history):
+// the cluster and history paths compiled out, which halves the register spills of the
+// 12-node chunks under their 168-register budget.
+template <int L, int MODE, bool GEN = false, bool LEAN = false>
 __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march_static(const MarchArgs a) {
     extern __shared__ double2 sm[];
-    const int T = a.T, G = a.G, P = a.P, C = a.C, nt = a.nt, levels = a.levels;
+    const int T = a.T, G = a.G, P = a.P, nt = a.nt, levels = a.levels;
+    const int C = LEAN ? 1 : a.C;
+    const bool s02v = !LEAN && a.s02;   // S_0^2 history terms
     const int S = T + G;
     double2* usep = sm;
     double2* dA = usep + S;
@@ -1031,13 +1036,13 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
     }
     if (valid) *SEP(usep, p) = (realsep && !zero_u0) ? a.u0[goff + sp] : zero;
     // S_0^2: the end traces start with v_0 = u_0 at the end
-    const bool hl = a.s02 && realsep && p == 0 && (tcf & 1);
-    const bool hr = a.s02 && realsep && p == Pj && (tcf & 2);
+    const bool hl = s02v && realsep && p == 0 && (tcf & 1);
+    const bool hr = s02v && realsep && p == Pj && (tcf & 2);
     // end traces v_0..v_{nt} at absolute steps: a launch marching a segment of the time
     // axis (steps ht0 + 1 ..) extends the traces the earlier segments left
     const int hst = a.hstride > 0 ? a.hstride : nt + 1, ht0 = a.ht0;
-    double2* hist_l = a.s02 ? a.hist + ((size_t)sidx * 2 + 0) * hst : nullptr;
-    double2* hist_r = a.s02 ? a.hist + ((size_t)sidx * 2 + 1) * hst : nullptr;
+    double2* hist_l = s02v ? a.hist + ((size_t)sidx * 2 + 0) * hst : nullptr;
+    double2* hist_r = s02v ? a.hist + ((size_t)sidx * 2 + 1) * hst : nullptr;
     // per-end kernels: h_0 = rho v_0; the flux weight on v_n is kout[0]
     constexpr bool gen = GEN;
     if (hl && ht0 == 0) hist_l[0] = zero_u0 ? zero : (gen ? cmul(a.rho[2 * j + 0], a.u0[goff + sp]) : a.u0[goff + sp]);
@@ -1115,7 +1120,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
             *CHK(ylst, p) = yl;
         }
         if (stage > 0) issue_fa(t < nt ? F + a.fstride : nullptr);
-        if (a.s02) {
+        if (s02v) {
             // history sums of the ends this CTA holds, one warp per end
             const int lane = tid & 31, w = tid >> 5, nw = T >> 5;
             if (C == 1) {
@@ -1195,7 +1200,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     else
                         lin = (live && sy.in_l >= 0 && a.gin) ? a.gin[(size_t)sy.in_l + a.t0 + t - 1] : zero;
                     f = cfms(lin, a.inv_ik, f);
-                    if (a.s02) f = cfma(hsum[hs_l], gen ? a.inv_ik : a.c2_ik, f);
+                    if (s02v) f = cfma(hsum[hs_l], gen ? a.inv_ik : a.c2_ik, f);
                 }
                 if (re && (tcf & 2)) {
                     if (sy.flags & SYS_IMP_R)
@@ -1203,7 +1208,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     else
                         rin = (live && sy.in_r >= 0 && a.gin) ? a.gin[(size_t)sy.in_r + a.t0 + t - 1] : zero;
                     f = cfms(rin, a.inv_ik, f);
-                    if (a.s02) f = cfma(hsum[hs_r], gen ? a.inv_ik : a.c2_ik, f);
+                    if (s02v) f = cfma(hsum[hs_r], gen ? a.inv_ik : a.c2_ik, f);
                 }
                 d = f;
                 const double2 El = (stage >= 1) ? stg[0 * T + tid] : sE_l[p];
@@ -1295,7 +1300,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     const double2 ts = gen ? a.kout[(size_t)(2 * j + 0) * a.kstride] : a.two_sigma;
                     double2 o = csub(cmul(ts, v), lin);
                     if (gen) o = cadd(o, hsum2[hs_l]);
-                    else if (a.s02) o = cfma(a.two_c2, hsum[hs_l], o);
+                    else if (s02v) o = cfma(a.two_c2, hsum[hs_l], o);
                     a.gout[(size_t)sy.out_a + a.t0 + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 0) * nt + t - 1] = v;
@@ -1306,7 +1311,7 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
                     const double2 ts = gen ? a.kout[(size_t)(2 * j + 1) * a.kstride] : a.two_sigma;
                     double2 o = csub(cmul(ts, v), rin);
                     if (gen) o = cadd(o, hsum2[hs_r]);
-                    else if (a.s02) o = cfma(a.two_c2, hsum[hs_r], o);
+                    else if (s02v) o = cfma(a.two_c2, hsum[hs_r], o);
                     a.gout[(size_t)sy.out_b + a.t0 + t - 1] = o;
                 }
                 if ((sy.flags & SYS_TRACE) && a.trace) a.trace[((size_t)sidx * 2 + 1) * nt + t - 1] = v;
@@ -2108,6 +2113,7 @@ static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s, int mode) {
     const int slots = a.stage == 2 ? 2 * a.levels + 3 + 4 * L : (a.stage == 1 ? 2 * a.levels + 3 : 0);
     int smem = swr_march_smem_bytes(a.T, a.G, slots);
     void (*kern)(const MarchArgs) = a.kap ? k_march_static<L, 0, true> : k_march_static<L, 0>;
+    if (!a.kap && !a.s02 && a.C == 1) kern = k_march_static<L, 0, false, true>;
     // a system spread over a cluster, or alone in its CTA: the two-level separator
     // solve (one cluster / CTA barrier per step) when its data was factored
     const bool one_system = (a.C > 1) || (a.G == 1 && !a.rag);

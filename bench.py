@@ -36,14 +36,18 @@ FLOPS_PER_POINT_STEP_TDEP = 56     # plus the per-step factorisation (one comple
 FLOPS_PER_POINT_ITER_NL = 76
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flop x GHz (max SM clock)
 
-# DRAM bytes (read + write) per march launch, each scaled by the steps from a 100-step
-# single-launch ncu capture (profiles/k_march_static_N500_build.md and
-# profiles/launch_list_timedep.md): the scaling build writes the recorded states (598 MB per
-# 100 steps, 20 MB read), the V(t,x) march reads the streamed per-step factors (677 MB per
-# 100 steps, 3 MB written).  Valid only for the march sources they were taken from (sha256
-# prefix of swr_march.cu + swr_internal.cuh), null otherwise.
-MARCH_TRAFFIC = {"sources": "99af1785a54db446",
-                 "scaling": 3012000000.0, "timedep": 6803000000.0}
+# DRAM bytes (read + write) per march launch, each scaled by the steps from 100-step
+# single-launch ncu captures (profiles/k_march_static_N500_build.md, launch_list_scaling.md,
+# launch_list_timedep.md).  Scaling step: the mean over its four build marches, the N = 500
+# build (lean k_march_static<12>: 19.3 MB read, 593.5 MB written per 100 steps, the recorded
+# states) standing for N = 256 and the N = 16 build (k_march_tl<12>: 19.2 / 546.7 MB) for
+# N = 64.  V(t,x) march: the streamed per-step factors, 677.2 MB read and 0.3 MB written per
+# 100 steps (captured on the general instantiation in the modelled cluster shape; the lean
+# one of the tuned shape streams the same factors, 7.1 MB per step in its 38-step probes).
+# Valid only for the march sources they were taken from (sha256 prefix of swr_march.cu +
+# swr_internal.cuh), null otherwise.
+MARCH_TRAFFIC = {"sources": "a53048c29edc645f",
+                 "scaling": 2947000000.0, "timedep": 6775000000.0}
 
 
 def march_sources_hash():

@@ -155,7 +155,8 @@ typedef struct swr_tuning {
                                 /* per build when they fit; -1 refactorised per step    */
     int32_t two_level;          /* systems spread over a cluster: 0 (default) two-level  */
                                 /* separator solve (one cluster barrier per step) when   */
-                                /* a system has <= 993 separators; -1 cluster-wide PCR   */
+                                /* a system has <= 993 separators (the nonlinear         */
+                                /* gradient's monodomain: <= 8161); -1 cluster-wide PCR  */
     int32_t debug;              /* 1: failing CUDA calls (2: also the launch-shape      */
                                 /* probes) reported on stderr; 0 (default) silent        */
     int32_t history_fft;        /* causal substitution (CAUSAL preconditioner, direct   */

@@ -1045,7 +1045,7 @@ def run_workload(args, workload, rank, world, local, dev, peak):
     if nonlin:
         # the nonlinear marches (forward SWR sweeps and the adjoint's monodomain marches)
         # dominate: their flops per node and inner iteration over their own device time
-        m_kernel = "k_march_nl_tl (forward sweeps) + k_march_nl (gradient marches)"
+        m_kernel = "k_march_nl_tl (forward sweeps and the gradient's monodomain marches)"
         achieved = FLOPS_PER_POINT_ITER_NL * nl_pit / (nl_ms * 1e-3) / 1e9 if nl_ms > 0 else 0.0
     # whole-step throughput from the library's own count of marched point-steps
     # (equal to the analytic count for the scaling step; GMRES-dependent otherwise)

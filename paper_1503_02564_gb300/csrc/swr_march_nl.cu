@@ -653,25 +653,28 @@ __global__ void __launch_bounds__(256, 1) k_march_nl(const NlArgs na) {
 // The nonlinear march of one system spread over a cluster of C > 1 CTAs with the
 // two-level separator solve of the constant-matrix march (FactorSet.tl_*): every inner
 // iteration solves its separators with warp-shuffle PCR in blocks of 32 and a reduced
-// system of at most 32 super-separators that warp 0 of every CTA solves, with one cluster
-// barrier, and a second one for the convergence test, where the cluster-wide PCR took one
-// per level.  MODE 0, or 1 (also record v_n of every step into a.vrec, as k_march_nl
-// does); Robin or Neumann ends.  Thread p = rank T + tid owns separator p and chunk p; T is a multiple
-// of 32.  Per step: the step-constant right-hand sides, the start of the fixed point,
-// then per inner iteration
+// system of the super-separators that every CTA solves redundantly (at most 32 unknowns:
+// warp 0 with shuffles; a wide system of up to tl_rs <= T unknowns: the whole CTA, one
+// barrier per PCR level), with one cluster barrier, and a second one for the convergence
+// test, where the cluster-wide PCR took one per level.  MODE 0; 1 also records v_n of
+// every step into a.vrec; 2 is the adjoint step of the nonlinear gradient (as k_march_nl:
+// the linearised term about the recorded forward values a.vfwd, a relative test, the
+// potential-form sums added to a.gint, a.gl, a.gr).  Robin or Neumann ends.  Thread
+// p = rank T + tid owns separator p and chunk p; T is a multiple of 32.  Per step: the
+// step-constant right-hand sides, the start of the fixed point, then per inner iteration
 //   A  chunk right-hand sides with b_f(zeta), local LU solves;
 //   B  separator right-hand sides: a separator's own part (its right element) and the
 //      part of its left element, formed by the thread of the chunk on its left (the
 //      same thread's neighbour in the warp, or lane 31 of the warp before for a
 //      super-separator, which publishes it);
 //   C  super-chunk PCR in registers, publication, cluster barrier;
-//   D  the reduced system in warp 0 of every CTA (every CTA holds the new iterate at
-//      all super-separators), CTA barrier;
+//   D  the reduced system in every CTA (every CTA holds the new iterate at all
+//      super-separators), CTA barrier;
 //   E  super-chunk values; F  chunk values, change of the iterate, partial maxima;
 //   G  cluster barrier, the convergence test on all CTAs' partials (the same decision
 //      everywhere).
 // After the fixed point: v_n = zeta, u_n = 2 v_n - u_{n-1}, fluxes.
-// Shared memory: see k_march_nl_tl_smem_bytes.
+// Shared memory: see swr_march_nl_tl_smem_bytes.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double2 nl_shup(double2 v, int d) {
     return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));

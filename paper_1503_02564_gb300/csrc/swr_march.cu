@@ -1393,15 +1393,17 @@ __global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march
 //      super-separator values (xsup) and their u (usup); one CTA barrier;
 //   E  super-chunk values x = yhat - a x_{s_q} - b x_{s_{q+1}};
 //   F  spike correction of the chunks, CN update, fluxes (as k_march_static).
-// MODE 0 only (no recorded v, no gradient), constant factors.
+// Constant factors.  MODE 0; 1 also records v of every step (a.vrec), 2 accumulates the
+// adjoint potential form against the recorded forward values (a.vfwd), both as
+// k_march_static does (L <= 8, no S_0^2 history).
 // ---------------------------------------------------------------------------
 int swr_march_tl_smem_bytes(int T) {
     const int W = T / 32;
     return (int)sizeof(double2) * (6 * T + 2 * W * 5 + 2 * 33 + 8);
 }
 
-template <int L, bool GEN>
-__global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const MarchArgs a) {
+template <int L, bool GEN, int MODE = 0>
+__global__ void __launch_bounds__((L == 16 || MODE == 2) ? 256 : 384, 1) k_march_tl(const MarchArgs a) {
     extern __shared__ double2 sm[];
     const int T = a.T, P = a.P, C = a.C, nt = a.nt;
     const int W = T / 32;
@@ -1465,6 +1467,11 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
         u[i] = (valid && i < Lp && !zero_u0) ? a.u0[goff + sp + 1 + i] : zero;
         y[i] = zero;
     }
+    // MODE 2: per-thread sums of the potential form (interior nodes of the chunk, and the
+    // one-sided parts of its two separators)
+    double ga_int[MODE == 2 ? L : 1], ga_l = 0.0, ga_r = 0.0;
+#pragma unroll
+    for (int i = 0; i < (MODE == 2 ? L : 1); ++i) ga_int[i] = 0.0;
     usep[tid] = (realsep && !zero_u0) ? a.u0[goff + sp] : zero;
     // replicas of the super-separators' u in every CTA (warp 0)
     if (wl == 0 && lane <= Q && sidx < a.nsys) {
@@ -1530,10 +1537,11 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
             yfst[tid] = y[0];
             ylst[tid] = yl;
         }
-        // history sums of the ends (the warps holding them)
-        if (wleft || wright) {
-            double2* hh = wleft ? hist_l : hist_r;
-            const int side = wleft ? 0 : 1;
+        // history sums of the ends (the warps holding them; a system of at most 32
+        // separators has both ends in warp 0 of its CTA, which then forms both sums)
+        for (int side = 0; side < 2; ++side) {
+            if (!(side == 0 ? wleft : wright)) continue;   // uniform over the warp
+            const double2* hh = side == 0 ? hist_l : hist_r;
             if (gen) {
                 const size_t ke = (size_t)(2 * j + side) * a.kstride;
                 double2 o1, o2;
@@ -1651,6 +1659,7 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
         xv[tid] = v;
         __syncwarp();
         // ---- F: spike correction, CN update, fluxes -------------------------------
+        double2 vv[MODE == 2 ? L : 1];
         if (valid && Lp > 0) {
             const double2 vR = (rsup >= 0) ? xsup[rsup] : xv[tid + 1];
 #pragma unroll
@@ -1658,9 +1667,41 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
                 if (i < Lp) {
                     double2 vi = cfms(F[(i * 4 + 2) * P], v, y[i]);
                     vi = cfms(F[(i * 4 + 3) * P], vR, vi);
+                    if constexpr (MODE == 1) a.vrec[(size_t)(t - 1) * a.nxrec + goff + sp + 1 + i] = vi;
+                    if constexpr (MODE == 2) vv[i] = vi;
                     u[i] = make_double2(fma(2.0, vi.x, -u[i].x), fma(2.0, vi.y, -u[i].y));
                 }
             }
+            if constexpr (MODE == 2) {
+                // elements e = 0..Lp from separator p (node sp) to separator p + 1 (node
+                // sp + Lp + 1); x = this march's v, y = the recorded forward v of the
+                // mirrored step
+                if (p < Pj) {
+                    const double2* yrow = a.vfwd + (size_t)(nt - t) * a.nxrec + goff + sp;
+                    const double h12 = a.h12;
+#pragma unroll
+                    for (int e = 0; e <= L; ++e) {
+                        if (e <= Lp) {
+                            const double2 xa = (e == 0) ? v : vv[e > 0 ? e - 1 : 0];
+                            const double2 xb = (e < L) ? csel(e < Lp, vv[e < L ? e : 0], vR) : vR;
+                            const double2 ya = yrow[e], yb = yrow[e + 1];
+                            const double sa = xa.x * ya.x - xa.y * ya.y;
+                            const double sb = xb.x * yb.x - xb.y * yb.y;
+                            const double c = (xa.x * yb.x - xa.y * yb.y) + (xb.x * ya.x - xb.y * ya.y);
+                            const double toa = h12 * (3.0 * sa + c + sb);
+                            const double tob = h12 * (sa + c + 3.0 * sb);
+                            if (e == 0) ga_l += toa;
+                            else ga_int[e > 0 ? e - 1 : 0] += toa;
+                            if (e < Lp) ga_int[e < L ? e : 0] += tob;
+                            else ga_r += tob;
+                        }
+                    }
+                }
+            }
+        }
+        if constexpr (MODE == 1) {   // an interface node is recorded by its left subdomain
+            if (realsep && !(p == 0 && (tcf & 1)))
+                a.vrec[(size_t)(t - 1) * a.nxrec + goff + sp] = v;
         }
         if (realsep) {
             const double2 uo = usep[tid];
@@ -1696,6 +1737,16 @@ __global__ void __launch_bounds__(L == 16 ? 256 : 384, 1) k_march_tl(const March
             if (realsep) __stcs(row + sp, usep[tid]);
         }
         __syncwarp();
+    }
+    if constexpr (MODE == 2) {
+        // add this segment's sums; every entry has exactly one writer per launch
+        if (valid && p < Pj) {
+#pragma unroll
+            for (int i = 0; i < L; ++i)
+                if (i < Lp) a.gint[goff + sp + 1 + i] += ga_int[i];
+            a.gl[goff + sp] += ga_l;
+            a.gr[goff + sp + Lp + 1] += ga_r;
+        }
     }
     // ---- final state ----------------------------------------------------------
     bool bad = false;
@@ -2125,6 +2176,13 @@ static int launch_march_t(MarchArgs a, int ngroups, cudaStream_t s, int mode) {
     if constexpr (L <= 8) {   // record and gradient modes exist for L <= 8
         if (mode == 1) kern = k_march_static<L, 1>;
         if (mode == 2) kern = k_march_static<L, 2>;
+        // ... and in the two-level form for a system spread over a cluster or alone in its
+        // CTA with Robin or Neumann ends
+        if ((mode == 1 || mode == 2) && one_system && a.stage == 0 && a.fstride == 0 &&
+            a.tl_pcr && !a.s02 && !a.kap && (a.T & 31) == 0 && (mode == 1 || a.T <= 256)) {
+            kern = (mode == 1) ? k_march_tl<L, false, 1> : k_march_tl<L, false, 2>;
+            smem = swr_march_tl_smem_bytes(a.T);
+        }
     }
     if (mode != 0 && a.kap) return -2;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=

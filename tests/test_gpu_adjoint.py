@@ -48,11 +48,12 @@ CASES = {
 }
 
 
-def gpu_gradient(wl, tgt, K=16, V=None, tc=None):
+def gpu_gradient(wl, tgt, K=16, V=None, tc=None, tuning=None):
     from paper_1503_02564_gb300 import swr
     plan = swr.Plan(nx=wl.nx, a0=wl.a0, b0=wl.b0, nt=wl.nt, dt=wl.dt, nsub=wl.nsub,
                     node_off=wl.off, p=wl.sigma, restart=100, maxit=1000, tol_abs=1e-13,
-                    precond=swr.SWR_PC_CAUSAL, tc=swr.SWR_TC_ROBIN if tc is None else tc)
+                    precond=swr.SWR_PC_CAUSAL, tc=swr.SWR_TC_ROBIN if tc is None else tc,
+                    tuning=tuning)
     Vt = torch.tensor(wl.V if V is None else V, dtype=torch.float64, device="cuda")
     plan.build_interface(Vt, torch.tensor(wl.u0, dtype=torch.complex128, device="cuda"))
     uT = torch.empty(wl.nx, dtype=torch.complex128, device="cuda")
@@ -75,6 +76,23 @@ def test_adjoint_gradient_matches_oracle(case, tc):
     Jo, go = O.adjoint_gradient(problem(wl), tgt)
     assert abs(J - Jo) <= 1e-10 * Jo
     assert rel(g, go) < 1e-8
+
+
+@pytest.mark.parametrize("case", ["eight_2500", "config2_N16_small"])
+def test_adjoint_two_level_record_and_gradient_marches(case):
+    """The record and gradient marches in the two-level form (k_march_tl modes 1 and 2:
+    eight 2501-node subdomains on clusters of seven CTAs, 500 separators each; sixteen
+    251-node subdomains alone in their CTAs), in the modelled launch shapes, against the
+    same marches with the cluster-wide or CTA-wide PCR (two_level -1), with checkpoints
+    every 5 steps, and against the oracle's discrete adjoint."""
+    wl = W.config2(nsub=8, nx=20001, nt=12) if case == "eight_2500" else CASES[case]()
+    tgt = target(wl)
+    J1, g1 = gpu_gradient(wl, tgt, K=5, tuning={"autotune": -1})
+    J2, g2 = gpu_gradient(wl, tgt, K=5, tuning={"autotune": -1, "two_level": -1})
+    assert rel(g1, g2) < 1e-11
+    Jo, go = O.adjoint_gradient(problem(wl), tgt)
+    assert abs(J1 - Jo) <= 1e-10 * Jo
+    assert rel(g1, go) < 1e-8
 
 
 @pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])

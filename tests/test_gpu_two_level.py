@@ -90,6 +90,24 @@ def test_two_level_march_matches_oracle_and_cluster_pcr(chunk, tc):
     assert rel(d1, d0) < 1e-12 and rel(c1, c0) < 1e-12 and rel(r1, r0) < 1e-12
 
 
+@pytest.mark.parametrize("tc", [O.TC_S02, O.TC_S14])
+@pytest.mark.parametrize("chunk", [4, 8])
+def test_two_level_short_systems_with_both_ends_in_one_warp(chunk, tc):
+    """Systems of at most 32 separators (61-node subdomains: 13 or 7 separators) alone in
+    their CTAs, with history terms at both ends: both ends sit in warp 0, which forms
+    both ends' history sums every step.  Against the oracle's d, columns and R g."""
+    wl = W.config2(nsub=6, nx=6 * 60 + 1, nt=20)
+    x = wl.x
+    wl.u0 = np.exp(2j * x) * (1.0 + 0.3 * np.sin(0.7 * x))
+    d1, c1, r1, g, st1 = build(wl, tc, chunk, 0)
+    assert st1["two_level_launches"] > 0, st1
+    P = O.Problem(wl.a0, wl.b0, wl.nx, wl.dt, wl.nt, wl.off.astype(np.int64), wl.u0, wl.V,
+                  tc=tc, sigma=wl.sigma)
+    assert rel(d1, O.build_d(P)) < TOL_MARCH
+    assert rel(c1, O.build_columns(P)) < TOL_MARCH
+    assert rel(r1, O.apply_R(P, g)) < TOL_MARCH
+
+
 @pytest.mark.parametrize("tc", [O.TC_ROBIN, O.TC_S02])
 def test_two_level_one_system_per_cta(tc):
     """About a hundred systems (the build of 34 subdomains): the modelled shape puts one

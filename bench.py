@@ -39,14 +39,15 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x FP64 FMA/clk x 2 flop x GHz (max
 # DRAM bytes (read + write) per march launch, each scaled by the steps from 100-step
 # single-launch ncu captures (profiles/k_march_static_N500_build.md, launch_list_scaling.md,
 # launch_list_timedep.md).  Scaling step: the mean over its four build marches, the N = 500
-# build (lean k_march_static<12>: 19.3 MB read, 593.5 MB written per 100 steps, the recorded
-# states) standing for N = 256 and the N = 16 build (k_march_tl<12>: 19.2 / 546.7 MB) for
+# build (lean k_march_static<12>: 19.1 MB read, 593.5 MB written per 100 steps, the recorded
+# states) standing for N = 256 and the N = 16 build (k_march_tl<12>: 19.2 / 547.0 MB) for
 # N = 64.  V(t,x) march: the streamed per-step factors, 677.2 MB read and 0.3 MB written per
-# 100 steps (captured on the general instantiation in the modelled cluster shape; the lean
-# one of the tuned shape streams the same factors, 7.1 MB per step in its 38-step probes).
-# Valid only for the march sources they were taken from (sha256 prefix of swr_march.cu +
+# 100 steps (captured on k_march_static's general instantiation in the modelled cluster
+# shape, whose code the later k_march_tl changes did not touch; the lean one of the tuned
+# shape streams the same factors, 7.1 MB per step in its 38-step probes).  Valid only for
+# the march sources they were taken from (sha256 prefix of swr_march.cu +
 # swr_internal.cuh), null otherwise.
-MARCH_TRAFFIC = {"sources": "a53048c29edc645f",
+MARCH_TRAFFIC = {"sources": "647131b39d98daf0",
                  "scaling": 2947000000.0, "timedep": 6775000000.0}
 
 
